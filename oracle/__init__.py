@@ -1,0 +1,263 @@
+"""Plain FP64 CPU oracle of the octree geometric multigrid (arXiv:1901.11370).
+
+TEST INFRASTRUCTURE ONLY: imported by ``tests/``, ``__graft_entry__.smoke()``
+and the CPU-baseline leg of ``bench.py``.  The CUDA library never links,
+imports or calls anything here, and nothing here calls it.
+
+``Oracle`` wraps ``mg_oracle.c`` (compiled with gcc on first use or by
+``build()``) through ctypes; every method maps to one C routine that cites
+the passage of the paper it follows.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "mg_oracle.c")
+_LIB = os.path.join(_HERE, "libmg_oracle.so")
+_lib = None
+
+_dp = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
+_ip = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
+
+
+def build(force=False):
+    """Compile the oracle into a shared library beside its source."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + ".%d.tmp" % os.getpid()
+        subprocess.check_call(["gcc", "-O2", "-std=c99", "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    build()
+    L = C.CDLL(_LIB)
+    L.or_create.restype = C.c_void_p
+    L.or_create.argtypes = [C.c_int, C.c_int, C.c_int, _ip, _dp, _ip, _dp, _dp, C.c_int,
+                            C.c_double, C.c_int, _ip]
+    L.or_last_error.restype = C.c_char_p
+    L.or_destroy.argtypes = [C.c_void_p]
+    L.or_num_levels.argtypes = [C.c_void_p]
+    L.or_level_info.argtypes = [C.c_void_p, C.c_int, _ip, _dp]
+    L.or_set_cycle.argtypes = [C.c_void_p, C.c_int, C.c_int]
+    L.or_set_homogeneous.argtypes = [C.c_void_p, C.c_int]
+    L.or_num_leaf_cells.restype = C.c_int64
+    L.or_num_leaf_cells.argtypes = [C.c_void_p]
+    L.or_leaf_blocks.restype = C.c_int64
+    L.or_leaf_blocks.argtypes = [C.c_void_p, C.c_void_p]
+    for name in ("or_set_rhs", "or_set_phi", "or_get_phi", "or_get_lam", "or_set_eps"):
+        getattr(L, name).argtypes = [C.c_void_p, _dp]
+    L.or_set_bc_plane.argtypes = [C.c_void_p, C.c_int, C.c_int, _dp]
+    L.or_refresh.argtypes = [C.c_void_p]
+    L.or_vcycle.argtypes = [C.c_void_p, C.c_int]
+    L.or_fmg.argtypes = [C.c_void_p]
+    L.or_residual_norm.argtypes = [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_void_p]
+    L.or_apply.argtypes = [C.c_void_p, _dp, _dp]
+    L.or_leaf_geometry.argtypes = [C.c_void_p, _dp, _dp]
+    L.or_eps_grad.argtypes = [C.c_void_p, _dp, _dp]
+    L.or_level_io.restype = C.c_int64
+    L.or_level_io.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_int]
+    L.or_level_blocks.argtypes = [C.c_void_p, C.c_int, _ip, _ip, _ip]
+    L.or_step.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int]
+    _lib = L
+    return L
+
+
+class Oracle:
+    """One mesh and its fields in the FP64 oracle."""
+
+    def __init__(self, dim, N, geom, bc_type, bc_val, base, lo, hi, refine=None,
+                 coarse_max=512, helm=0.0):
+        L = _load()
+        ref = np.ascontiguousarray(np.zeros((0, 4), np.int32) if refine is None else refine,
+                                   dtype=np.int32).reshape(-1, 4)
+        base3 = [int(b) for b in base] + [1] * (3 - len(base))
+        self._h = L.or_create(int(dim), int(N), int(geom), np.array(bc_type, np.int32),
+                              np.array(bc_val, np.float64), np.array(base3, np.int32),
+                              np.array(list(lo) + [0.0] * (3 - len(lo)), np.float64),
+                              np.array(list(hi) + [1.0] * (3 - len(hi)), np.float64),
+                              int(coarse_max), float(helm), len(ref), ref.ravel())
+        if not self._h:
+            raise ValueError("oracle: " + L.or_last_error().decode())
+        self.L = L
+        self.dim = dim
+        self.cyl = geom == 1
+        self._rhs = np.zeros(int(L.or_num_leaf_cells(self._h)))
+        self.n_leaf = int(L.or_num_leaf_cells(self._h))
+
+    @classmethod
+    def from_problem(cls, p, set_fields=True):
+        o = cls(p.dim, p.N, p.geom, p.bc_type, p.bc_val, p.base, p.lo, p.hi, p.refine,
+                p.coarse_max)
+        if set_fields:
+            from synth import workloads as W
+            o.set_bc_from_problem(p)
+            if p.eps is not None or p.eps_leaf is not None:
+                o.set_eps(W.leaf_field(p, "eps"))
+            o.set_rhs(W.leaf_field(p, "rhs"))
+        return o
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            self.L.or_destroy(self._h)
+            self._h = None
+
+    # -------------------------------------------------------------- mesh --
+    def levels(self):
+        out = []
+        for l in range(self.L.or_num_levels(self._h)):
+            iv = np.zeros(9, np.int32)
+            hv = np.zeros(3)
+            self.L.or_level_info(self._h, l, iv, hv)
+            out.append(dict(n=int(iv[0]), depth=int(iv[1]), nb=int(iv[2]),
+                            nblk=tuple(int(x) for x in iv[3:6]),
+                            ncell=tuple(int(x) for x in iv[6:9]), h=tuple(hv)))
+        return out
+
+    def leaf_blocks(self):
+        n = self.L.or_leaf_blocks(self._h, None)
+        out = np.zeros((n, 4), np.int32)
+        self.L.or_leaf_blocks(self._h, out.ctypes.data)
+        return out
+
+    def leaf_geometry(self):
+        v = np.zeros(self.n_leaf)
+        r = np.zeros(self.n_leaf)
+        self.L.or_leaf_geometry(self._h, v, r)
+        return v, r
+
+    # ------------------------------------------------------------ fields --
+    def set_rhs(self, f):
+        self._rhs = np.array(f, np.float64)
+        self.L.or_set_rhs(self._h, np.ascontiguousarray(f, np.float64))
+
+    def set_eps(self, e):
+        self.L.or_set_eps(self._h, np.ascontiguousarray(e, np.float64))
+
+    def set_phi(self, x):
+        self.L.or_set_phi(self._h, np.ascontiguousarray(x, np.float64))
+
+    def get_phi(self):
+        x = np.zeros(self.n_leaf)
+        self.L.or_get_phi(self._h, x)
+        return x
+
+    def set_bc_plane(self, face, level, vals):
+        self.L.or_set_bc_plane(self._h, face, level, np.ascontiguousarray(vals, np.float64))
+
+    def set_bc_from_problem(self, p):
+        from synth import workloads as W
+        if p.bc is None:
+            return
+        for l, info in enumerate(self.levels()):
+            for face in range(2 * p.dim):
+                v = W.bc_plane(p, face, info["ncell"], info["h"])
+                if v is not None:
+                    self.set_bc_plane(face, l, v)
+        self.L.or_refresh(self._h)
+
+    def set_homogeneous(self, on):
+        self.L.or_set_homogeneous(self._h, 1 if on else 0)
+        self.L.or_refresh(self._h)
+
+    # ------------------------------------------------------------ cycles --
+    def set_cycle(self, n_down=2, n_up=2):
+        self.L.or_set_cycle(self._h, n_down, n_up)
+
+    def vcycle(self, n=1):
+        self.L.or_vcycle(self._h, n)
+
+    def fmg(self):
+        self.L.or_fmg(self._h)
+
+    def residual_norm(self, want_res=False):
+        l2, li = C.c_double(), C.c_double()
+        res = np.zeros(self.n_leaf) if want_res else None
+        self.L.or_residual_norm(self._h, C.byref(l2), C.byref(li),
+                                res.ctypes.data if want_res else None)
+        return (l2.value, li.value, res) if want_res else (l2.value, li.value)
+
+    def apply(self, x):
+        out = np.zeros(self.n_leaf)
+        self.L.or_apply(self._h, np.ascontiguousarray(x, np.float64), out)
+        return out
+
+    def eps_grad(self, lam):
+        out = np.zeros(self.n_leaf)
+        if self.L.or_eps_grad(self._h, np.ascontiguousarray(lam, np.float64), out) != 0:
+            raise ValueError("oracle: " + self.L.or_last_error().decode())
+        return out
+
+    # -------------------------------------------------------- test hooks --
+    FIELDS = {"phi": 0, "f": 1, "eps": 2, "vold": 3, "lam": 4}
+
+    def level_get(self, l, which):
+        """Padded field of level l as [nb, (n+2)] * dim (ghost layer included)."""
+        info = self.levels()[l]
+        n = self.L.or_level_io(self._h, l, self.FIELDS[which], None, 1)
+        out = np.zeros(n)
+        self.L.or_level_io(self._h, l, self.FIELDS[which], out.ctypes.data, 1)
+        return out.reshape((info["nb"],) + (info["n"] + 2,) * self.dim)
+
+    def level_set(self, l, which, arr):
+        a = np.ascontiguousarray(arr, np.float64).ravel()
+        self.L.or_level_io(self._h, l, self.FIELDS[which], a.ctypes.data, 0)
+
+    def level_blocks(self, l):
+        nb = self.levels()[l]["nb"]
+        ijk = np.zeros(3 * nb, np.int32)
+        par = np.zeros(nb, np.int32)
+        hc = np.zeros(nb, np.int32)
+        self.L.or_level_blocks(self._h, l, ijk, par, hc)
+        return ijk.reshape(nb, 3), par, hc
+
+    def step(self, op, l=0, arg=0):
+        ops = {"ghost": 0, "smooth": 1, "restrict": 2, "prolong": 3, "coarse": 4}
+        self.L.or_step(self._h, ops[op], l, arg)
+
+    # ---------------------------------------------------- composite solve --
+    def solve(self, rel_tol=1e-10, max_cycles=50, fmg_first=True):
+        """phi = 0, then (optionally) one FMG cycle and V-cycles until the
+        composite residual drops by rel_tol.  Returns (cycles, history)."""
+        self.set_phi(np.zeros(self.n_leaf))
+        r0, _ = self.residual_norm()
+        hist = [r0]
+        cycles = 0
+        if fmg_first:
+            self.fmg()
+            cycles += 1
+            hist.append(self.residual_norm()[0])
+        while hist[-1] > rel_tol * r0 and cycles < max_cycles:
+            self.vcycle(1)
+            cycles += 1
+            hist.append(self.residual_norm()[0])
+        return cycles, hist
+
+    def adjoint(self, g, n_vcycles=12):
+        """lambda = A^-T g and dL/deps for a uniform mesh, given the converged
+        phi in the tree.  A^T = A on Cartesian meshes; in the cylindrical form
+        r_i A is symmetric, so A^T = diag(r) A diag(r)^-1 and
+        A (lambda / r) = g / r.  The solve is one FMG cycle plus n_vcycles
+        V-cycles with homogeneous boundary values."""
+        phi = self.get_phi()
+        rhs = self._rhs.copy()
+        _, rad = self.leaf_geometry()
+        self.set_homogeneous(True)
+        self.set_rhs(g / rad if self.cyl else g)
+        self.set_phi(np.zeros(self.n_leaf))
+        self.fmg()
+        self.vcycle(n_vcycles)
+        mu = self.get_phi()
+        lam = mu * rad if self.cyl else mu
+        self.set_homogeneous(False)
+        self.set_rhs(rhs)
+        self.set_phi(phi)
+        return lam, self.eps_grad(lam)

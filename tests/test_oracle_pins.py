@@ -1,0 +1,557 @@
+"""Pins of the FP64 oracle against facts fixed by the paper and by mathematics.
+
+Each test states what it pins.  None of them re-derives the oracle's own
+formula: they check closed forms, invariants, a printed table, identities
+derived independently, brute-force dense solves and convergence orders.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import Oracle
+from synth import workloads as W
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+DIR, NEU, PER, AXIS = W.BC_DIRICHLET, W.BC_NEUMANN, W.BC_PERIODIC, W.BC_AXIS
+
+
+def lin_problem(dim, refine, coef, bct=None, N=4, base=16, geom=0):
+    """Mesh with boundary planes taken from the linear function coef.x + 1."""
+    def phi(X, Y, Z):
+        return coef[0] * X + coef[1] * Y + (coef[2] * Z if dim == 3 else 0) + 1.0
+
+    def bc(face, X, Y, Z):
+        d, side = face // 2, face % 2
+        if (bct or (DIR,) * 6)[face] == NEU:
+            return np.full(np.shape(X), float(coef[d]))
+        return phi(X, Y, Z)
+    p = W.Problem("lin", dim, N, geom, (base, base, base if dim == 3 else 1),
+                  (0.0,) * 3, (1.0,) * 3, bct or (DIR,) * 6, (0.0,) * 6, refine, 512,
+                  rhs=None, bc=bc, exact=phi)
+    return p
+
+
+def amr_refine(dim, N, base, centre, radii, periodic=(False,) * 3):
+    return W.refine_spheres(dim, N, (base, base, base if dim == 3 else 1), (0, 0, 0),
+                            (1, 1, 1), centre, radii, periodic)
+
+
+# ---------------------------------------------------------------- levels --
+
+def test_coarse_levels_match_paper_table():
+    """Level construction (Sec. 2.5, table of added coarse grids)."""
+    rows = [list(map(int, ln.split())) for ln in open(os.path.join(GOLD, "coarse_levels_192x96.txt"))
+            if ln.strip() and not ln.startswith("#")]
+    o = Oracle(2, 8, 0, (DIR,) * 6, (0.0,) * 6, (192, 96), (0, 0), (2, 1), coarse_max=0)
+    lv = o.levels()[::-1]  # finest first
+    assert len(lv) == len(rows)
+    for info, (level, cx, cy, bs, bx, by) in zip(lv, rows):
+        assert info["depth"] == level - 1
+        assert info["ncell"][:2] == (cx, cy)
+        assert info["n"] == bs
+        assert info["nblk"][:2] == (bx, by)
+
+
+def test_coarsest_levels_of_the_workloads():
+    """cfg1 keeps 4 levels down to one 8^2 block; a 16^3-block grid stops at 8^3."""
+    o = Oracle(2, 8, 0, (DIR,) * 6, (0.0,) * 6, (64, 64), (0, 0), (1, 1))
+    assert [(l["n"], l["nblk"][:2]) for l in o.levels()] == [(8, (1, 1)), (8, (2, 2)), (8, (4, 4)), (8, (8, 8))]
+    o = Oracle(3, 16, 0, (DIR,) * 6, (0.0,) * 6, (64, 64, 64), (0,) * 3, (1,) * 3)
+    assert [(l["n"], l["nblk"]) for l in o.levels()] == [(8, (1, 1, 1)), (16, (1, 1, 1)), (16, (2, 2, 2)), (16, (4, 4, 4))]
+
+
+def test_unbalanced_mesh_rejected():
+    """2:1 balance is a precondition (Sec. 2.5, Sec. 2.7)."""
+    ref = np.array([[0, 0, 0, 0], [1, 0, 0, 0], [2, 1, 1, 0]], np.int32)
+    with pytest.raises(ValueError):
+        Oracle(2, 4, 0, (DIR,) * 6, (0.0,) * 6, (16, 16), (0, 0), (1, 1), ref)
+
+
+# -------------------------------------------------------------- operator --
+
+@pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("bcname", ["dirichlet", "neumann_x"])
+def test_operator_exact_on_linear_with_refinement(dim, bcname):
+    """Every ghost rule of Sec. 2.6 (same level, physical, refinement boundary)
+    and the mean restriction are exact on linear functions, so the composite
+    operator of a linear function vanishes on every leaf cell."""
+    N, base = 4, (16 if dim == 2 else 8)
+    ref = amr_refine(dim, N, base, (0.3, 0.6, 0.45), (0.35, 0.2))
+    assert len(ref) > 0
+    bct = None if bcname == "dirichlet" else (NEU, NEU, DIR, DIR, DIR, DIR)
+    coef = (0.7, -1.3, 0.4)
+    p = lin_problem(dim, ref, coef, bct, N=N, base=base)
+    o = Oracle.from_problem(p, set_fields=False)
+    o.set_bc_from_problem(p)
+    X, Y, Z, H = W.leaf_cell_centres(p)
+    Lx = o.apply(p.exact(X, Y, Z))
+    assert np.abs(Lx).max() < 1e-9 * (1.0 / H[:, 0].min() ** 2)
+
+
+def test_operator_quadratic_cartesian():
+    """Sec. 2.2 discretisation: exact on quadratics away from the boundary."""
+    p = lin_problem(3, np.zeros((0, 4), np.int32), (0, 0, 0), N=4, base=8)
+    o = Oracle.from_problem(p, set_fields=False)
+    X, Y, Z, H = W.leaf_cell_centres(p)
+    Lx = o.apply(X * X + 2 * Y * Y - 0.5 * Z * Z)
+    h = H[0, 0]
+    inner = (X > h) & (X < 1 - h) & (Y > h) & (Y < 1 - h) & (Z > h) & (Z < 1 - h)
+    np.testing.assert_allclose(Lx[inner], 2 + 4 - 1, rtol=0, atol=1e-9)
+
+
+def test_operator_quadratic_cylindrical():
+    """Cylindrical form: (1/r) d/dr (r d/dr r^2) = 4 and d^2/dz^2 z^2 = 2,
+    including the cells on the axis."""
+    p = lin_problem(2, np.zeros((0, 4), np.int32), (0, 0, 0),
+                    bct=(AXIS, DIR, DIR, DIR, PER, PER), N=4, base=16, geom=W.GEOM_CYL)
+    o = Oracle.from_problem(p, set_fields=False)
+    X, Y, Z, H = W.leaf_cell_centres(p)
+    h = H[0, 0]
+    inner = (X < 1 - h) & (Y > h) & (Y < 1 - h)
+    np.testing.assert_allclose(o.apply(X * X)[inner], 4.0, atol=1e-9)
+    np.testing.assert_allclose(o.apply(Y * Y)[inner], 2.0, atol=1e-9)
+    np.testing.assert_allclose(o.apply(np.full_like(X, 3.0))[inner], 0.0, atol=1e-9)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_harmonic_face_coefficient_exact_for_layers(dim):
+    """Sec. 2.2: with the harmonic mean of the two cell coefficients the
+    discrete flux across a material interface lying on a cell face is exact
+    for a layered medium, so the piecewise-linear solution with continuous
+    flux eps dphi/dx = q satisfies the discrete equation on every cell."""
+    base, N = 16, 4
+    e1, e2, q = 1.0, 10.0, 0.8
+
+    def phi(X, Y, Z):
+        return np.where(X < 0.5, q * X / e1, q * 0.5 / e1 + q * (X - 0.5) / e2) + 0.3
+
+    p = W.Problem("layers", dim, N, 0, (base, base, base if dim == 3 else 1), (0.0,) * 3,
+                  (1.0,) * 3, (DIR, DIR, NEU, NEU, NEU, NEU), (0.0,) * 6,
+                  np.zeros((0, 4), np.int32), 512, bc=lambda face, X, Y, Z: phi(X, Y, Z) if face < 2 else 0 * X)
+    o = Oracle.from_problem(p, set_fields=False)
+    o.set_bc_from_problem(p)
+    X, Y, Z, H = W.leaf_cell_centres(p)
+    o.set_eps(np.where(X < 0.5, e1, e2))
+    np.testing.assert_allclose(o.apply(phi(X, Y, Z)), 0.0, atol=1e-10)
+
+
+@pytest.mark.parametrize("case", ["2d_dir_eps", "3d_neu_per_eps", "cyl_eps"])
+def test_operator_symmetric_on_uniform_mesh(case):
+    """With homogeneous boundary values the uniform-mesh operator is symmetric
+    (r-weighted in the cylindrical form): <u, A v> = <A u, v>."""
+    rng = np.random.default_rng(3)
+    if case == "2d_dir_eps":
+        o = Oracle(2, 4, 0, (DIR, NEU, DIR, DIR, 0, 0), (0.0,) * 6, (16, 16), (0, 0), (1, 1))
+    elif case == "3d_neu_per_eps":
+        o = Oracle(3, 4, 0, (NEU, NEU, PER, PER, PER, PER), (0.0,) * 6, (8, 8, 8), (0,) * 3, (1,) * 3)
+    else:
+        o = Oracle(2, 4, 1, (AXIS, DIR, DIR, DIR, PER, PER), (0.0,) * 6, (16, 16), (0, 0), (1, 1))
+    o.set_eps(np.exp(rng.uniform(-1, 1, o.n_leaf)))
+    o.set_homogeneous(True)
+    _, rad = o.leaf_geometry()
+    w = rad if case == "cyl_eps" else np.ones(o.n_leaf)
+    u, v = rng.standard_normal(o.n_leaf), rng.standard_normal(o.n_leaf)
+    Au, Av = o.apply(u), o.apply(v)
+    a, b = np.dot(w * u, Av), np.dot(w * Au, v)
+    assert abs(a - b) <= 1e-12 * (abs(a) + np.linalg.norm(w * u) * np.linalg.norm(Av))
+
+
+# ---------------------------------------------------- refinement ghosts --
+
+def _flux_identity_residuals(dim):
+    N, base = 4, (16 if dim == 2 else 8)
+    ref = amr_refine(dim, N, base, (0.55, 0.4, 0.5), (0.3 if dim == 2 else 0.45,))
+    o = Oracle(dim, N, 0, (DIR,) * 6, (0.0,) * 6, (base,) * dim, (0,) * dim, (1,) * dim, ref)
+    rng = np.random.default_rng(7)
+    o.set_phi(rng.standard_normal(o.n_leaf))  # restricts covered cells, fills ghosts
+    levels = o.levels()
+    lf = len(levels) - 1
+    fine = o.level_get(lf, "phi")
+    coarse = o.level_get(lf - 1, "phi")
+    fijk, _, _ = o.level_blocks(lf)
+    cijk, _, _ = o.level_blocks(lf - 1)
+    fset = {tuple(x): b for b, x in enumerate(fijk.tolist())}
+    cset = {tuple(x): b for b, x in enumerate(cijk.tolist())}
+    nblk = levels[lf]["nblk"]
+    out = []
+    for b, q in enumerate(fijk.tolist()):
+        for d in range(dim):
+            for s in (0, 1):
+                nq = list(q)
+                nq[d] += 1 if s else -1
+                if nq[d] < 0 or nq[d] >= nblk[d] or tuple(nq) in fset:
+                    continue
+                # coarse neighbour block and the cells along this face
+                Fb = fine[b]
+                tang = [t for t in range(dim) if t != d]
+                for m in np.ndindex(*([N // 2] * (dim - 1))):
+                    ci = [0] * 3
+                    gsum, csum = 0.0, 0.0
+                    allc = []
+                    for sub in np.ndindex(*([2] * (dim - 1))):
+                        idx = [0] * dim
+                        for a, t in enumerate(tang):
+                            idx[t] = 2 * m[a] + sub[a]
+                        gidx, c_idx, d_idx = list(idx), list(idx), list(idx)
+                        gidx[d] = N if s else -1
+                        c_idx[d] = N - 1 if s else 0
+                        d_idx[d] = N - 2 if s else 1
+                        g = Fb[tuple(x + 1 for x in gidx[::-1])]
+                        c = Fb[tuple(x + 1 for x in c_idx[::-1])]
+                        dd = Fb[tuple(x + 1 for x in d_idx[::-1])]
+                        gsum += g
+                        csum += c
+                        allc += [c, dd]
+                    D = np.mean(allc)  # restriction of the 2^D fine cells
+                    # B: the coarse cell across the face
+                    G = [q[t] * N + (2 * m[tang.index(t)] if t != d else (N if s else -1)) for t in range(dim)]
+                    Gc = [x // 2 for x in G]
+                    cb = tuple(x // N for x in Gc) + (0,) * (3 - dim)
+                    lc = [Gc[t] - cb[t] * N for t in range(dim)]
+                    B = coarse[cset[cb]][tuple(x + 1 for x in lc[::-1])]
+                    # face flux equality: (2^(dim-1) fine faces of size h^(dim-1)) vs coarse face
+                    out.append((2 ** (dim - 2)) * (D - B) - (csum - gsum))
+                    del ci
+    return np.array(out)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_refinement_ghosts_conserve_flux(dim):
+    """Sec. 2.6: the refinement-boundary ghosts give the same coarse and summed
+    fine flux through a coarse face.  With H = 2h this reads
+    D - B = (c - g) + (a - h) in 2D and 2 (D - B) = sum_k (c_k - g_k) in 3D;
+    the printed 2D form with halves is off by a factor two (checked with
+    phi = x: D - B = 2h, c - g = a - h = h)."""
+    res = _flux_identity_residuals(dim)
+    assert len(res) > 0
+    assert np.abs(res).max() < 1e-12
+
+
+# ------------------------------------------------------------ transfers --
+
+def _set_level_linear(o, l, coef):
+    info = o.levels()[l]
+    n, dim = info["n"], o.dim
+    ijk, _, _ = o.level_blocks(l)
+    arr = np.zeros((info["nb"],) + (n + 2,) * dim)
+    idx = np.arange(-1, n + 1)
+    for b, q in enumerate(ijk):
+        grids = [(q[d] * n + idx + 0.5) * info["h"][d] for d in range(dim)]
+        mesh = np.meshgrid(*grids[::-1], indexing="ij")  # z, y, x order
+        val = np.ones_like(mesh[0])
+        for d in range(dim):
+            val = val + coef[d] * mesh[dim - 1 - d]
+        arr[b] = val
+    o.level_set(l, "phi", arr)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_prolongation_exact_on_linear(dim):
+    """Sec. 2.3, eqs. for 2D/3D interpolation: exact on linear functions."""
+    base = 32 if dim == 2 else 16
+    o = Oracle(dim, 4, 0, (DIR,) * 6, (0.0,) * 6, (base,) * dim, (0,) * dim, (1,) * dim)
+    lf = len(o.levels()) - 1
+    coef = (0.3, -0.8, 1.7)
+    _set_level_linear(o, lf - 1, coef)
+    o.level_set(lf - 1, "vold", np.zeros_like(o.level_get(lf - 1, "vold")))
+    o.level_set(lf, "phi", np.zeros_like(o.level_get(lf, "phi")))
+    o.step("prolong", lf)
+    info = o.levels()[lf]
+    fine = o.level_get(lf, "phi")
+    ijk, _, _ = o.level_blocks(lf)
+    n = info["n"]
+    idx = np.arange(n)
+    for b, q in enumerate(ijk):
+        grids = [(q[d] * n + idx + 0.5) * info["h"][d] for d in range(dim)]
+        mesh = np.meshgrid(*grids[::-1], indexing="ij")
+        want = 1.0 + sum(coef[d] * mesh[dim - 1 - d] for d in range(dim))
+        got = fine[b][(slice(1, n + 1),) * dim]
+        np.testing.assert_allclose(got, want, atol=1e-13)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_restriction_of_prolongation(dim):
+    """R P u = u + (H^2/8) Lap_H u (derived from the interpolation weights of
+    Sec. 2.3 and the mean restriction): in 2D the four children sum to
+    (8 u0 + 2 sum nb)/4, in 3D the eight to 2 u0 + sum nb."""
+    base = 32 if dim == 2 else 16
+    o = Oracle(dim, 4, 0, (DIR,) * 6, (0.0,) * 6, (base,) * dim, (0,) * dim, (1,) * dim)
+    lf = len(o.levels()) - 1
+    rng = np.random.default_rng(11)
+    u = rng.standard_normal(o.level_get(lf - 1, "phi").shape)
+    o.level_set(lf - 1, "phi", u)
+    o.level_set(lf - 1, "vold", np.zeros_like(u))
+    o.level_set(lf, "phi", np.zeros_like(o.level_get(lf, "phi")))
+    o.step("prolong", lf)
+    fine = o.level_get(lf, "phi")
+    fijk, fpar, _ = o.level_blocks(lf)
+    cinfo, finfo = o.levels()[lf - 1], o.levels()[lf]
+    n, cn = finfo["n"], cinfo["n"]
+    for b, q in enumerate(fijk):
+        pb = fpar[b]
+        F = fine[b][(slice(1, n + 1),) * dim]
+        # mean over children
+        if dim == 2:
+            R = 0.25 * (F[0::2, 0::2] + F[0::2, 1::2] + F[1::2, 0::2] + F[1::2, 1::2])
+        else:
+            R = sum(F[a::2, c::2, e::2] for a in (0, 1) for c in (0, 1) for e in (0, 1)) / 8.0
+        off = [(q[d] % 2) * (n // 2) if cn == n else 0 for d in range(dim)]
+        U = u[pb]
+        sl = tuple(slice(1 + off[d], 1 + off[d] + n // 2) for d in range(dim))[::-1]
+        u0 = U[sl]
+        nbsum = 0
+        for d in range(dim):
+            for s in (-1, 1):
+                sl2 = list(sl)
+                ax = dim - 1 - d
+                sl2[ax] = slice(sl[ax].start + s, sl[ax].stop + s)
+                nbsum = nbsum + U[tuple(sl2)]
+        np.testing.assert_allclose(R, u0 + (nbsum - 2 * dim * u0) / 8.0, atol=1e-13)
+
+
+def test_restriction_is_the_mean_and_conserves_volume_integral():
+    """Sec. 2.3: a covered cell holds the mean of its children, so sum V x is
+    the same on a refined patch and under it."""
+    dim, N, base = 2, 4, 16
+    ref = amr_refine(dim, N, base, (0.4, 0.4, 0), (0.3,))
+    o = Oracle(dim, N, 0, (DIR,) * 6, (0.0,) * 6, (base,) * dim, (0,) * dim, (1,) * dim, ref)
+    rng = np.random.default_rng(5)
+    o.set_phi(rng.standard_normal(o.n_leaf))
+    lv = o.levels()
+    lf = len(lv) - 1
+    fine, coarse = o.level_get(lf, "phi"), o.level_get(lf - 1, "phi")
+    fijk, fpar, _ = o.level_blocks(lf)
+    Vf, Vc = np.prod(lv[lf]["h"][:2]), np.prod(lv[lf - 1]["h"][:2])
+    for b, q in enumerate(fijk):
+        Fi = fine[b][1:N + 1, 1:N + 1]
+        off = [(q[d] % 2) * (N // 2) for d in range(2)]
+        Ci = coarse[fpar[b]][1 + off[1]:1 + off[1] + N // 2, 1 + off[0]:1 + off[0] + N // 2]
+        assert abs(Vf * Fi.sum() - Vc * Ci.sum()) < 1e-14 * Vc * (1 + np.abs(Ci).sum())
+
+
+# ------------------------------------------------------------- smoother --
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_red_black_sweeps_independent_of_block_size(dim):
+    """With ghosts refreshed after each colour and global parity, red-black
+    Gauss-Seidel on a uniform level does not depend on how the level is cut
+    into blocks."""
+    base = 32 if dim == 2 else 16
+    rng = np.random.default_rng(2)
+    res = []
+    for N in (4, 8):
+        o = Oracle(dim, N, 0, (DIR, NEU, DIR, DIR, DIR, DIR), (0.3, -0.2, 0, 0, 0, 0),
+                   (base,) * dim, (0,) * dim, (1,) * dim)
+        p = W.Problem("u", dim, N, 0, (base, base, base if dim == 3 else 1), (0,) * 3, (1,) * 3,
+                      (DIR,) * 6, (0,) * 6, np.zeros((0, 4), np.int32))
+        I, J, K, _ = W.leaf_cell_index(p)
+        key = (K * base + J) * base + I
+        vals = rng.standard_normal(base ** dim) if N == 4 else vals0
+        fvals = np.sin(np.arange(base ** dim)) if N == 4 else fvals0
+        vals0, fvals0 = vals, fvals
+        o.set_phi(vals[key])
+        o.set_rhs(fvals[key])
+        lf = len(o.levels()) - 1
+        for _ in range(3):
+            o.step("smooth", lf, 0)
+            o.step("smooth", lf, 1)
+        out = np.empty(base ** dim)
+        out[key] = o.get_phi()
+        res.append(out)
+    np.testing.assert_array_equal(res[0], res[1])
+
+
+# ------------------------------------------------- composite dense solve --
+
+def _dense(o):
+    n = o.n_leaf
+    b = o.apply(np.zeros(n))
+    A = np.empty((n, n))
+    for j in range(n):
+        e = np.zeros(n)
+        e[j] = 1.0
+        A[:, j] = o.apply(e) - b
+    return A, b
+
+
+DENSE_CASES = {
+    "2d_amr_dir_eps": dict(dim=2, N=4, base=8, bct=(DIR, DIR, NEU, DIR, 0, 0), radii=(0.3,), eps=True),
+    "3d_amr_dir": dict(dim=3, N=2, base=4, bct=(DIR,) * 6, radii=(0.4,), eps=False),
+    "3d_amr_dir_eps": dict(dim=3, N=4, base=8, bct=(DIR, NEU, DIR, DIR, DIR, DIR), radii=(0.3,), eps=True),
+    "cyl_amr_eps": dict(dim=2, N=4, base=8, bct=(AXIS, DIR, DIR, DIR, 0, 0), radii=(0.3,), eps=True, geom=1),
+    "2d_amr_periodic": dict(dim=2, N=4, base=8, bct=(PER, PER, PER, PER, 0, 0), radii=(0.3,), eps=False),
+}
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_periodic_composite_operator_is_conservative(dim):
+    """Constant coefficient, periodic, refined mesh: A 1 = 0 and, by the
+    flux-matching ghosts of Sec. 2.6, sum_i V_i (A x)_i = 0 for every x."""
+    N, base = 4, (8 if dim == 2 else 8)
+    per = (True, True, True)
+    ref = amr_refine(dim, N, base, (0.35, 0.6, 0.5), (0.3 if dim == 2 else 0.45,), per)
+    assert len(ref) > 0
+    o = Oracle(dim, N, 0, (PER,) * 6, (0.0,) * 6, (base,) * dim, (0,) * dim, (1,) * dim, ref)
+    vol, _ = o.leaf_geometry()
+    assert np.abs(o.apply(np.ones(o.n_leaf))).max() < 1e-10
+    x = np.random.default_rng(4).standard_normal(o.n_leaf)
+    Ax = o.apply(x)
+    assert abs(np.dot(vol, Ax)) < 1e-12 * np.dot(vol, np.abs(Ax))
+
+
+@pytest.mark.parametrize("case", sorted(DENSE_CASES))
+def test_vcycles_converge_to_dense_composite_solution(case):
+    """The V-cycle fixed point is the solution of the composite system
+    assembled column by column and solved by dense LU (numpy)."""
+    c = DENSE_CASES[case]
+    dim, N, base = c["dim"], c["N"], c["base"]
+    per = tuple(c["bct"][2 * d] == PER for d in range(3))
+    ref = amr_refine(dim, N, base, (0.35, 0.6, 0.5), c["radii"], per)
+    rng = np.random.default_rng(17)
+    o = Oracle(dim, N, c.get("geom", 0), c["bct"], (0.5, -0.25, 1.0, 0.0, 0.3, 0.0),
+               (base,) * dim, (0,) * dim, (1,) * dim, ref)
+    if c["eps"]:
+        o.set_eps(np.exp(0.5 * rng.standard_normal(o.n_leaf)))
+    f = rng.standard_normal(o.n_leaf)
+    A, b = _dense(o)
+    vol, _ = o.leaf_geometry()
+    if case.endswith("periodic"):
+        # singular: project f to the range, pick the zero-mean solution
+        f = f - np.dot(vol, f) / vol.sum()
+        M = np.block([[A, np.ones((o.n_leaf, 1))], [vol[None, :], np.zeros((1, 1))]])
+        x_ref = np.linalg.solve(M, np.concatenate([f - b, [0.0]]))[:-1]
+    else:
+        x_ref = np.linalg.solve(A, f - b)
+    o.set_rhs(f)
+    o.set_phi(np.zeros(o.n_leaf))
+    o.fmg()
+    o.vcycle(40)
+    x = o.get_phi()
+    if case.endswith("periodic"):
+        x = x - np.dot(vol, x) / vol.sum()
+    np.testing.assert_allclose(x, x_ref, rtol=0, atol=1e-11 * np.abs(x_ref).max())
+
+
+# --------------------------------------------------------- convergence ----
+
+def test_second_order_convergence_2d():
+    """Second-order discretisation (Sec. 2.2): the error of the converged
+    solution falls about 4x per halving of h (cfg-1 manufactured problem)."""
+    errs = []
+    for n in (32, 64, 128):
+        p = W.cfg1_poisson2d(n=n, N=8)
+        o = Oracle.from_problem(p)
+        o.solve(1e-11)
+        X, Y, Z, _ = W.leaf_cell_centres(p)
+        errs.append(np.abs(o.get_phi() - p.exact(X, Y, Z)).max())
+    r1, r2 = errs[0] / errs[1], errs[1] / errs[2]
+    assert 3.0 < r1 < 5.5 and 3.5 < r2 < 4.6, errs
+
+
+@pytest.mark.slow
+def test_paper_convergence_problem_3d():
+    """Sec. 3.1 (E1) at 32^3: the residual reaches machine precision after
+    about ten FMG cycles, the discretisation error after one or two, and a
+    centred two-level refinement lowers the max error by about 16-20x."""
+    p = W.conv3d_problem(n=32, N=8, refine="none")
+    o = Oracle.from_problem(p)
+    X, Y, Z, _ = W.leaf_cell_centres(p)
+    r0 = o.residual_norm()[0]
+    errs, res = [], []
+    for _ in range(10):
+        o.fmg()
+        res.append(o.residual_norm()[0] / r0)
+        errs.append(np.abs(o.get_phi() - p.exact(X, Y, Z)).max())
+    assert res[-1] < 1e-12, res
+    assert abs(errs[1] - errs[-1]) < 0.05 * errs[-1]
+    pc = W.conv3d_problem(n=32, N=8, refine="center")
+    oc = Oracle.from_problem(pc)
+    for _ in range(6):
+        oc.fmg()
+    Xc, Yc, Zc, _ = W.leaf_cell_centres(pc)
+    err_c = np.abs(oc.get_phi() - pc.exact(Xc, Yc, Zc)).max()
+    assert errs[-1] / err_c > 10.0, (errs[-1], err_c)
+
+
+def test_gaussian_closed_form_second_order():
+    """Sec. 3.2 closed form erf(r/s)/(4 pi r) as a Dirichlet problem: second
+    order convergence of the max error."""
+    errs = []
+    for n in (16, 32):
+        p = W.cfg2_gauss3d(base=n, N=8, radii=(), sigma=0.1)
+        o = Oracle.from_problem(p)
+        o.solve(1e-10)
+        X, Y, Z, _ = W.leaf_cell_centres(p)
+        errs.append(np.abs(o.get_phi() - p.exact(X, Y, Z)).max())
+    assert 3.0 < errs[0] / errs[1] < 5.0, errs
+
+
+def test_cylindrical_second_order():
+    """Cylindrical (r, z) form: phi = (1 - r^2) sin(pi z) with the axis at r = 0
+    converges at second order."""
+    def phi(X, Y, Z):
+        return (1 - X * X) * np.sin(math.pi * Y)
+
+    def rhs(X, Y, Z):
+        return -4 * np.sin(math.pi * Y) - (1 - X * X) * math.pi ** 2 * np.sin(math.pi * Y)
+    errs = []
+    for n in (32, 64):
+        p = W.Problem("cyl", 2, 8, W.GEOM_CYL, (n, n, 1), (0, 0, 0), (1, 1, 1),
+                      (AXIS, DIR, DIR, DIR, PER, PER), (0.0,) * 6, np.zeros((0, 4), np.int32),
+                      512, rhs=rhs, exact=phi)
+        o = Oracle.from_problem(p)
+        o.solve(1e-11)
+        X, Y, Z, _ = W.leaf_cell_centres(p)
+        errs.append(np.abs(o.get_phi() - phi(X, Y, Z)).max())
+    assert 3.5 < errs[0] / errs[1] < 4.5, errs
+
+
+# -------------------------------------------------------------- adjoint ----
+
+def _adjoint_case(case):
+    rng = np.random.default_rng(23)
+    if case == "2d":
+        o = Oracle(2, 4, 0, (DIR, NEU, DIR, DIR, 0, 0), (0.2, 0.1, -0.3, 0.0, 0, 0), (8, 8), (0, 0), (1, 1))
+    elif case == "3d":
+        o = Oracle(3, 4, 0, (NEU, NEU, PER, PER, DIR, DIR), (0.1, 0.0, 0, 0, 0.5, 0.0), (8, 8, 8), (0,) * 3, (1,) * 3)
+    else:
+        o = Oracle(2, 4, 1, (AXIS, DIR, DIR, DIR, 0, 0), (0, 0.4, 0, 0.1, 0, 0), (8, 8), (0, 0), (1, 1))
+    eps = np.exp(0.4 * rng.standard_normal(o.n_leaf))
+    f = rng.standard_normal(o.n_leaf)
+    t = rng.standard_normal(o.n_leaf)
+    return o, eps, f, t
+
+
+def _solve_exact(o, eps, f):
+    o.set_eps(eps)
+    o.set_rhs(f)
+    o.set_phi(np.zeros(o.n_leaf))
+    o.fmg()
+    o.vcycle(30)
+    return o.get_phi()
+
+
+@pytest.mark.parametrize("case", ["2d", "3d", "cyl"])
+def test_adjoint_matches_finite_differences(case):
+    """dL/df = lambda = A^-T dL/dphi and dL/deps from the face coefficients,
+    for L = 0.5 sum (phi - t)^2: central differences (exact for f since L is
+    quadratic in f; O(delta^2) for eps)."""
+    o, eps, f, t = _adjoint_case(case)
+    phi = _solve_exact(o, eps, f)
+    lam, geps = o.adjoint(phi - t, n_vcycles=30)
+
+    def loss(e, ff):
+        x = _solve_exact(o, e, ff)
+        return 0.5 * np.sum((x - t) ** 2)
+    rng = np.random.default_rng(1)
+    for c in rng.choice(o.n_leaf, 6, replace=False):
+        df = np.zeros(o.n_leaf)
+        df[c] = 1e-3
+        fd = (loss(eps, f + df) - loss(eps, f - df)) / 2e-3
+        assert abs(fd - lam[c]) < 1e-7 * (abs(lam[c]) + np.abs(lam).max() * 1e-3)
+        de = np.zeros(o.n_leaf)
+        de[c] = 1e-4 * eps[c]
+        fe = (loss(eps + de, f) - loss(eps - de, f)) / (2e-4 * eps[c])
+        assert abs(fe - geps[c]) < 1e-6 * (abs(geps[c]) + np.abs(geps).max() * 1e-2), (c, fe, geps[c])
