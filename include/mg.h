@@ -1,0 +1,184 @@
+/*
+ * mg.h -- C ABI of the GB300 octree geometric multigrid library
+ * (libmg_gb300.so).  The method is the cell-centred geometric multigrid for
+ * quadtree/octree AMR grids of Teunissen & Keppens, arXiv:1901.11370.
+ *
+ * Problem (Sec. 1, Sec. 2.2):  div(eps grad phi) - lambda phi = f  on a 2D/3D
+ * Cartesian or 2D cylindrical (r, z) domain, discretised with the 5/7-point
+ * second-order stencil on a 2:1 balanced quadtree/octree of blocks of N^D
+ * cells (Sec. 2.5).
+ *
+ * Conventions for every entry point:
+ *  - Every call returns an int status: MG_OK (0) or a negative MG_ERR_*; the
+ *    message of the last failure on the calling thread is mg_last_error().
+ *    Nothing throws across this boundary.
+ *  - "dev_" pointers are CUDA device pointers (global memory of the device
+ *    the tree was finalised on); "host_" pointers are host memory.  Pointers
+ *    are borrowed for the duration of the call only; the library copies what
+ *    it keeps.  Outputs go to caller-allocated buffers.
+ *  - Work is enqueued on the stream given to mg_tree_finalize.  Calls that
+ *    return numbers to the host (norms, mg_solve) synchronise that stream;
+ *    the others are asynchronous.
+ *  - Leaf data (one value per leaf cell) are ordered by leaf block -- depth
+ *    ascending, then the Morton code of the block coordinates (bit b of
+ *    i, j, k at bits 3b, 3b+1, 3b+2) -- and inside a block by cell with x
+ *    fastest.  mg_tree_leaf_blocks lists the blocks in that order.
+ *  - Faces are numbered 0:-x 1:+x 2:-y 3:+y 4:-z 5:+z; in the cylindrical
+ *    form x = r and y = z.
+ */
+#ifndef MG_GB300_H
+#define MG_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mg_tree mg_tree; /* opaque: mesh, level tables, device fields */
+
+enum {
+    MG_OK = 0,
+    MG_ERR_ARG = -1,            /* invalid argument or call order */
+    MG_ERR_BALANCE = -2,        /* mesh not 2:1 balanced across faces */
+    MG_ERR_CUDA = -3,           /* a CUDA runtime call failed */
+    MG_ERR_NOT_CONVERGED = -4,  /* mg_solve hit max_cycles */
+    MG_ERR_NAN = -5,            /* a residual norm is not finite */
+    MG_ERR_UNSUPPORTED = -9     /* valid request outside what is built */
+};
+enum { MG_CART = 0, MG_CYL = 1 };
+enum { MG_BC_DIRICHLET = 0, MG_BC_NEUMANN = 1, MG_BC_PERIODIC = 2, MG_BC_AXIS = 3 };
+enum { MG_FP64 = 0, MG_FP32_DC = 1 };
+
+/* Boundary condition per face (Sec. 2.6): Dirichlet phi = value at the face,
+ * Neumann d(phi)/dx_d = value, periodic (both faces of a dimension), or the
+ * symmetry axis r = 0 of the cylindrical form (zero flux). */
+typedef struct {
+    int type[6];
+    double value[6];
+} mg_bc;
+
+/* Cycle parameters (Sec. 2.4): n_down / n_up red-black Gauss-Seidel sweeps
+ * per level (paper default 2 / 2).  precision MG_FP32_DC runs the cycles in
+ * FP32 inside an FP64 defect-correction loop (mg_solve only); inner_cycles is
+ * the number of FP32 V-cycles per outer FP64 residual. */
+typedef struct {
+    int n_down, n_up;
+    int precision;
+    int inner_cycles;
+} mg_params;
+
+/*
+ * mg_tree_create -- start a mesh (Sec. 2.5, "the user indicates the block
+ * size and the size of the unrefined domain").  dim 2 or 3; block_size N
+ * (even, >= 2) cells per block edge; geometry MG_CART or MG_CYL (dim 2);
+ * base_cells[d] the unrefined grid (multiples of N; base_cells[2] ignored in
+ * 2D); lo/hi the domain corners; coarse_max_cells: below the base the block
+ * count is halved while every count is even, then the block size is halved
+ * while a level holds more than this many cells; the last level is solved
+ * exactly (dense FP64).  helmholtz: lambda >= 0.  *out receives the handle.
+ */
+int mg_tree_create(int dim, int block_size, int geometry, const mg_bc *bc,
+                   const int base_cells[3], const double lo[3], const double hi[3],
+                   int coarse_max_cells, double helmholtz, mg_tree **out);
+
+/*
+ * mg_tree_refine -- cover existing blocks by 2^D children (Sec. 2.5,
+ * "Copying the application's grid refinement").  host_entries holds n
+ * records (depth, i, j, k): depth 0 is the base grid.  Parents must exist
+ * (list shallower depths first or in any order; all are applied at build).
+ * 2:1 balance across faces is checked at build (MG_ERR_BALANCE).
+ */
+int mg_tree_refine(mg_tree *t, int n, const int32_t *host_entries);
+
+/* Mesh queries (build the host tables if not built yet; no device work).
+ * level_info: info[0..8] = N_l, depth, blocks, blocks per dim[3], cells per
+ * dim[3]; h[3] cell size.  Level 0 is the coarsest. */
+int mg_tree_num_levels(mg_tree *t, int *nlev);
+int mg_tree_level_info(mg_tree *t, int level, int32_t info[9], double h[3]);
+int mg_tree_num_leaf_cells(mg_tree *t, int64_t *n);
+int mg_tree_leaf_blocks(mg_tree *t, int32_t *host_out /* 4 per leaf block */);
+
+/*
+ * mg_set_bc_plane -- boundary values (Dirichlet a or Neumann b) at the face
+ * centres of one face of one level, replacing the constant of mg_bc there.
+ * host_vals has cells_t1 * cells_t2 entries, t1 < t2 the tangential
+ * dimensions, t1 fastest (2D: cells_t1 entries).  Call before finalize or
+ * after it (a later mg_set_phi or cycle picks it up).
+ */
+int mg_set_bc_plane(mg_tree *t, int face, int level, const double *host_vals);
+
+/* mg_tree_finalize -- build tables, allocate device fields (phi = 0, eps = 1,
+ * f = 0) and bind cuda_stream (a cudaStream_t, NULL = legacy default). */
+int mg_tree_finalize(mg_tree *t, void *cuda_stream);
+
+/* Leaf fields, device pointers, leaf order (see above). mg_set_phi also
+ * restricts the covered cells and refills every ghost layer. */
+int mg_set_rhs(mg_tree *t, const double *dev_f);
+int mg_set_eps(mg_tree *t, const double *dev_eps); /* eps > 0; coarse eps = mean of children */
+int mg_set_phi(mg_tree *t, const double *dev_phi);
+int mg_get_phi(mg_tree *t, double *dev_phi);
+
+/* mg_vcycle -- n_cycles FAS V-cycles on the whole tree (Sec. 2.4, eqs. for
+ * the coarse right-hand side and the coarse-grid correction), FP64. */
+int mg_vcycle(mg_tree *t, int n_cycles, const mg_params *p);
+
+/* mg_fmg -- one FMG cycle (Sec. 2.4 and the figure of the cycles), FP64. */
+int mg_fmg(mg_tree *t, const mg_params *p);
+
+/*
+ * mg_residual_norm -- composite residual r = f - L phi on the leaf cells
+ * after resetting every covered cell to the mean of its children:
+ * *l2 = sqrt(sum V r^2 / sum V) (the norm of Sec. 4.2), *linf = max |r|.
+ * dev_r (may be NULL) receives r in leaf order.  Synchronises the stream.
+ */
+int mg_residual_norm(mg_tree *t, double *l2, double *linf, double *dev_r);
+
+/*
+ * mg_solve -- from the current phi, cycle until the composite residual L2
+ * norm is at most rel_tol times its value for phi = 0, or max_cycles.
+ * MG_FP64: one FMG cycle if fmg_first, then V-cycles.  MG_FP32_DC: each
+ * outer step computes r = f - A phi in FP64, runs p->inner_cycles FP32
+ * V-cycles on A e = r (homogeneous boundary values, coarsest solve in FP64)
+ * and adds e to phi in FP64.  *cycles_done counts outer steps, *rel_out the
+ * final relative residual.  Returns MG_ERR_NOT_CONVERGED at max_cycles.
+ */
+int mg_solve(mg_tree *t, double rel_tol, int max_cycles, int fmg_first,
+             const mg_params *p, int *cycles_done, double *rel_out);
+
+/*
+ * mg_adjoint -- for a loss L(phi) at the current (converged) phi:
+ * dev_dLdf = lambda = A^-T dev_dLdphi, and dev_dLdeps[c] = dL/d eps_c
+ * through the harmonic face coefficients (Sec. 2.2).  Cartesian: A^T = A;
+ * cylindrical: r_i A is symmetric, so A (lambda/r) = g/r.  The adjoint solve
+ * runs one FMG cycle and n_cycles V-cycles with homogeneous boundary
+ * values.  Meshes with refinement boundaries return MG_ERR_UNSUPPORTED.
+ * dev_dLdeps may be NULL.  phi is left unchanged.
+ */
+int mg_adjoint(mg_tree *t, const double *dev_dLdphi, double *dev_dLdf, double *dev_dLdeps,
+               const mg_params *p, int n_cycles);
+
+/*
+ * Instrumentation (the paper has no counterpart; used by the benchmark).
+ * mg_launch_count: number of CUDA kernels this tree has launched so far.
+ * mg_time_sweeps: runs n_sweeps red-black sweeps on `level` (FP64 fields,
+ * a real smoothing step: phi changes) with CUDA events around every kernel
+ * on the tree's stream.  out[0] = mean ms of one smoother launch (one
+ * colour), out[1] = mean ms of one ghost-fill launch, out[2] = algorithmic
+ * bytes of one smoother launch (read phi, f, eps and the face ghosts once,
+ * write phi once), out[3] = algorithmic bytes of one ghost-fill launch
+ * (read the source cells, write the ghosts once).  Synchronises the stream.
+ */
+int mg_launch_count(mg_tree *t, int64_t *n);
+int mg_time_sweeps(mg_tree *t, int level, int n_sweeps, double out[4]);
+
+/* mg_tree_destroy -- free device and host memory (synchronises the stream). */
+int mg_tree_destroy(mg_tree *t);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *mg_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

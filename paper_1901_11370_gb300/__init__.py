@@ -1,0 +1,175 @@
+"""GB300-native octree geometric multigrid (Teunissen & Keppens, arXiv:1901.11370).
+
+``Tree`` wraps one mesh of the CUDA library (include/mg.h).  Fields are
+torch CUDA tensors in leaf order (see ``synth`` / include/mg.h); torch
+provides device memory and the stream, the library does every step.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import MGError, check  # noqa: F401
+
+MG_CART, MG_CYL = 0, 1
+MG_FP64, MG_FP32_DC = 0, 1
+
+
+def _ptr(t: torch.Tensor):
+    assert t.is_cuda and t.dtype == torch.float64 and t.is_contiguous(), "need a contiguous CUDA float64 tensor"
+    return C.c_void_p(t.data_ptr())
+
+
+def _params(n_down=2, n_up=2, precision=MG_FP64, inner_cycles=1):
+    return _lib.mg_params(n_down, n_up, precision, inner_cycles)
+
+
+class Tree:
+    """One quadtree/octree mesh and its device fields."""
+
+    def __init__(self, dim, N, geom, bc_type, bc_val, base, lo, hi, refine=None, coarse_max=512,
+                 helm=0.0, finalize=True):
+        L = _lib.load()
+        self.L = L
+        bc = _lib.mg_bc((C.c_int * 6)(*[int(x) for x in bc_type]), (C.c_double * 6)(*[float(x) for x in bc_val]))
+        b3 = (C.c_int * 3)(*([int(x) for x in base] + [1] * (3 - len(base))))
+        lo3 = (C.c_double * 3)(*([float(x) for x in lo] + [0.0] * (3 - len(lo))))
+        hi3 = (C.c_double * 3)(*([float(x) for x in hi] + [1.0] * (3 - len(hi))))
+        h = C.c_void_p()
+        check(L.mg_tree_create(dim, N, geom, C.byref(bc), b3, lo3, hi3, int(coarse_max), float(helm), C.byref(h)))
+        self._h = h
+        self.dim = dim
+        if refine is not None and len(refine):
+            ref = np.ascontiguousarray(refine, dtype=np.int32).reshape(-1, 4)
+            check(L.mg_tree_refine(self._h, len(ref), ref.ctypes.data_as(C.c_void_p)))
+        n = C.c_int64()
+        check(L.mg_tree_num_leaf_cells(self._h, C.byref(n)))
+        self.n_leaf = n.value
+        self.finalized = False
+        if finalize:
+            self.finalize()
+
+    @classmethod
+    def from_problem(cls, p, set_fields=True, device="cuda"):
+        from synth import workloads as W
+        t = cls(p.dim, p.N, p.geom, p.bc_type, p.bc_val, p.base, p.lo, p.hi, p.refine, p.coarse_max,
+                finalize=False)
+        if p.bc is not None:
+            for l, info in enumerate(t.levels()):
+                for face in range(2 * p.dim):
+                    v = W.bc_plane(p, face, info["ncell"], info["h"])
+                    if v is not None:
+                        t.set_bc_plane(face, l, v)
+        t.finalize()
+        if set_fields:
+            if p.eps is not None or p.eps_leaf is not None:
+                t.set_eps(torch.from_numpy(W.leaf_field(p, "eps")).to(device))
+            t.set_rhs(torch.from_numpy(W.leaf_field(p, "rhs")).to(device))
+        return t
+
+    def finalize(self):
+        stream = torch.cuda.current_stream().cuda_stream
+        check(self.L.mg_tree_finalize(self._h, C.c_void_p(stream)))
+        self.finalized = True
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            self.L.mg_tree_destroy(h)
+            self._h = None
+
+    # --------------------------------------------------------------- mesh --
+    def levels(self):
+        n = C.c_int()
+        check(self.L.mg_tree_num_levels(self._h, C.byref(n)))
+        out = []
+        for l in range(n.value):
+            info = np.zeros(9, np.int32)
+            h = (C.c_double * 3)()
+            check(self.L.mg_tree_level_info(self._h, l, info.ctypes.data_as(C.c_void_p), h))
+            out.append(dict(n=int(info[0]), depth=int(info[1]), nb=int(info[2]),
+                            nblk=tuple(int(x) for x in info[3:6]), ncell=tuple(int(x) for x in info[6:9]),
+                            h=tuple(h)))
+        return out
+
+    def leaf_blocks(self):
+        nb = self.n_leaf // self.levels()[-1]["n"] ** self.dim  # leaf blocks all have N^D cells
+        out = np.zeros((nb, 4), np.int32)
+        check(self.L.mg_tree_leaf_blocks(self._h, out.ctypes.data_as(C.c_void_p)))
+        return out
+
+    def set_bc_plane(self, face, level, vals):
+        v = np.ascontiguousarray(vals, dtype=np.float64)
+        check(self.L.mg_set_bc_plane(self._h, face, level, v.ctypes.data_as(C.c_void_p)))
+
+    # ------------------------------------------------------------- fields --
+    def _leaf(self, t):
+        assert t.numel() == self.n_leaf, "leaf field has %d values, expected %d" % (t.numel(), self.n_leaf)
+        return _ptr(t)
+
+    def set_rhs(self, f):
+        check(self.L.mg_set_rhs(self._h, self._leaf(f)))
+
+    def set_eps(self, e):
+        check(self.L.mg_set_eps(self._h, self._leaf(e)))
+
+    def set_phi(self, x):
+        check(self.L.mg_set_phi(self._h, self._leaf(x)))
+
+    def get_phi(self, out=None):
+        out = torch.empty(self.n_leaf, dtype=torch.float64, device="cuda") if out is None else out
+        check(self.L.mg_get_phi(self._h, self._leaf(out)))
+        return out
+
+    # ------------------------------------------------------------- cycles --
+    def vcycle(self, n=1, n_down=2, n_up=2):
+        p = _params(n_down, n_up)
+        check(self.L.mg_vcycle(self._h, n, C.byref(p)))
+
+    def fmg(self, n_down=2, n_up=2):
+        p = _params(n_down, n_up)
+        check(self.L.mg_fmg(self._h, C.byref(p)))
+
+    def residual_norm(self, want_res=False):
+        l2, li = C.c_double(), C.c_double()
+        r = torch.empty(self.n_leaf, dtype=torch.float64, device="cuda") if want_res else None
+        check(self.L.mg_residual_norm(self._h, C.byref(l2), C.byref(li), _ptr(r) if want_res else None))
+        return (l2.value, li.value, r) if want_res else (l2.value, li.value)
+
+    def solve(self, rel_tol=1e-10, max_cycles=50, fmg_first=True, precision=MG_FP64, inner_cycles=1,
+              n_down=2, n_up=2, raise_on_fail=True):
+        p = _params(n_down, n_up, precision, inner_cycles)
+        cyc, rel = C.c_int(), C.c_double()
+        rc = self.L.mg_solve(self._h, float(rel_tol), int(max_cycles), int(bool(fmg_first)), C.byref(p),
+                             C.byref(cyc), C.byref(rel))
+        check(rc, allow=() if raise_on_fail else (-4,))
+        return cyc.value, rel.value
+
+    def launch_count(self):
+        n = C.c_int64()
+        check(self.L.mg_launch_count(self._h, C.byref(n)))
+        return n.value
+
+    def time_sweeps(self, level=-1, n_sweeps=4):
+        """(ms per smoother launch, ms per ghost launch, bytes per smoother
+        launch, bytes per ghost launch) on one level (default: the largest)."""
+        lv = self.levels()
+        if level < 0:
+            level = max(range(len(lv)), key=lambda l: lv[l]["nb"] * lv[l]["n"] ** self.dim)
+        out = (C.c_double * 4)()
+        check(self.L.mg_time_sweeps(self._h, level, n_sweeps, out))
+        return tuple(out), level
+
+    def adjoint(self, g, n_cycles=12, want_eps=True, n_down=2, n_up=2):
+        p = _params(n_down, n_up)
+        dLdf = torch.empty(self.n_leaf, dtype=torch.float64, device="cuda")
+        dLde = torch.empty(self.n_leaf, dtype=torch.float64, device="cuda") if want_eps else None
+        check(self.L.mg_adjoint(self._h, self._leaf(g.contiguous()), _ptr(dLdf), _ptr(dLde) if want_eps else None,
+                                C.byref(p), int(n_cycles)))
+        return dLdf, dLde
+
+
+from .autograd import MGSolve  # noqa: E402,F401

@@ -1,0 +1,129 @@
+// mg_internal.h -- shared between the host tree builder (mg_tree.cpp) and the
+// CUDA kernels and cycle driver (mg_kernels.cu).  Not part of the public ABI.
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/mg.h"
+
+namespace mg {
+
+// Per-block descriptor, one per block of every level (device table).
+// Storage is interior-only, block-major, x fastest; face ghosts live in a
+// separate array: block g owns 2*D faces of n^(D-1) values each at
+// ghost_off, face f = 2*d + side, tangential index t1 + n*t2 (t1 < t2 the
+// two dimensions other than d).
+struct BlockDesc {
+    long long cell_off;   // first interior cell in the field arrays
+    long long ghost_off;  // first ghost value in the ghost arrays
+    int n;                // cells per edge
+    int lev;              // level index (0 = coarsest)
+    int flags;            // bit 0: covered by children
+    int parent;           // global id of the parent block, -1 on level 0
+    int ijk[3];           // block coordinates on its level
+    int poff[3];          // offset of this block inside its parent, in parent cells
+    int nbr[6];           // >= 0 same-level neighbour id; -1 physical face;
+                          // <= -2: coarser neighbour, id = -2 - nbr
+};
+
+struct LevelDesc {
+    double h[3];
+    double inv_h2[3];
+    int ncell[3];
+    int n;
+    int first;            // global id of the first block
+    int nb;               // blocks on the level
+    int nref;             // of which the first nref are covered by children
+    long long bc_off[6];  // offset of the boundary plane of each face, -1: constant
+};
+
+// Scalars every kernel needs, passed by value.
+struct KParams {
+    const BlockDesc *B;
+    const LevelDesc *L;
+    const double *bcplanes;
+    double lo[3];
+    double bcv[6];
+    int bct[6];
+    double helm;
+    int geom;
+    int var_eps;
+    int homog;            // 1: boundary values read as zero
+};
+
+template <class T>
+struct Fields {
+    T *X = nullptr, *XG = nullptr;   // solution: interior + ghosts
+    T *F = nullptr;                  // right-hand side (interior)
+    T *E = nullptr, *EG = nullptr;   // coefficient: interior + ghosts (nullptr: eps = 1)
+    T *V = nullptr, *VG = nullptr;   // FAS copy v_old: interior + ghosts
+};
+
+struct LevelHost {
+    int n = 0, depth = 0;
+    int nblk[3] = {1, 1, 1}, ncell[3] = {1, 1, 1};
+    double h[3] = {1, 1, 1};
+    int first = 0, nb = 0, nref = 0;
+    long long cell_first = 0, ghost_first = 0, ncells = 0, nghost = 0;
+    std::vector<double> bc[6];
+};
+
+}  // namespace mg
+
+struct mg_tree {
+    int dim = 3, N = 8, geom = MG_CART, coarse_max = 512;
+    mg_bc bc{};
+    int base[3] = {1, 1, 1};
+    double lo[3] = {0, 0, 0}, hi[3] = {1, 1, 1};
+    double helm = 0.0;
+    std::vector<int32_t> refine;  // 4 per entry
+    bool built = false, finalized = false, singular = false, bc_dirty = false;
+    bool var_eps = false;
+    std::vector<mg::LevelHost> lev;
+    std::vector<mg::BlockDesc> blocks;
+    long long ncells = 0, nghost = 0, nleaf_cells = 0;
+
+    // device state
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    mg::BlockDesc *d_blocks = nullptr;
+    mg::LevelDesc *d_levels = nullptr;
+    double *d_bcplanes = nullptr;
+    long long n_bcplanes = 0;
+    mg::Fields<double> f64, adj;   // solve and adjoint solve (adj shares E/EG)
+    mg::Fields<float> f32;         // inner defect-correction cycles
+    double *d_r64 = nullptr;       // leaf residual scratch (FP64)
+    double *d_minv = nullptr;      // coarsest-level inverse, row-major ns x ns
+    int nc = 0, ns = 0;            // coarsest cells, system size (nc + singular)
+    bool minv_ok = false;
+    double *d_cvec = nullptr;      // coarsest residual vector (ns)
+    double *d_partials = nullptr;  // per-CTA norm partials (3 per CTA)
+    int n_partials = 0;
+    double *d_red = nullptr;       // reduced norms (3)
+    double *h_red = nullptr;       // pinned host copy
+    long long launches = 0;        // kernels launched so far
+};
+
+namespace mg {
+// cycle driver and kernels (mg_kernels.cu); all enqueue on t->stream
+template <class T> void vcycle(mg_tree *t, Fields<T> &F, int top, int nd, int nu, int homog);
+template <class T> void fmg(mg_tree *t, Fields<T> &F, int nd, int nu, int homog);
+template <class T> void refresh(mg_tree *t, Fields<T> &F, int homog);
+template <class T> void refresh_eps(mg_tree *t, Fields<T> &F);
+// composite residual of FP64 fields on the leaves; optional outputs:
+// r64 (FP64 leaf order), f32 (FP32 into the leaf cells of an FP32 field)
+void residual_norm(mg_tree *t, Fields<double> &F, int homog, double *out3, double *r64_leaf,
+                   float *f32_cells);
+void add_e_to_phi(mg_tree *t, const float *e, double *phi);
+void copy_eps_to_f32(mg_tree *t);
+void eps_grad(mg_tree *t, const double *lam_cells, const double *phi_cells, double *out_leaf);
+void scale_by_radius(mg_tree *t, const double *in_leaf, double *out_leaf, int divide);
+KParams kparams(mg_tree *t, int homog);
+int time_sweeps(mg_tree *t, int level, int n_sweeps, double *out4);
+int check_cuda(const char *what);
+}  // namespace mg
+
+void mg_set_error(const std::string &msg);

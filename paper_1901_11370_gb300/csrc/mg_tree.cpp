@@ -1,0 +1,730 @@
+// mg_tree.cpp -- host side of the GB300 octree geometric multigrid: mesh and
+// level construction (Sec. 2.5), device tables, the dense coarsest-level
+// inverse, and the C ABI declared in include/mg.h.
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "mg_internal.h"
+
+using namespace mg;
+
+static thread_local std::string g_err;
+void mg_set_error(const std::string &msg) { g_err = msg; }
+extern "C" const char *mg_last_error(void) { return g_err.c_str(); }
+
+#define CK(call)                                                                              \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess) {                                                              \
+            mg_set_error(std::string(#call) + ": " + cudaGetErrorString(e_));                 \
+            return MG_ERR_CUDA;                                                               \
+        }                                                                                     \
+    } while (0)
+
+static int fail(int code, const std::string &msg) {
+    g_err = msg;
+    return code;
+}
+
+static uint64_t morton3(int i, int j, int k) {
+    uint64_t c = 0;
+    for (int b = 0; b < 21; b++) {
+        c |= (uint64_t)((i >> b) & 1) << (3 * b);
+        c |= (uint64_t)((j >> b) & 1) << (3 * b + 1);
+        c |= (uint64_t)((k >> b) & 1) << (3 * b + 2);
+    }
+    return c;
+}
+
+static long long ipow(int n, int d) { return d == 2 ? (long long)n * n : (long long)n * n * n; }
+
+// ------------------------------------------------------------ create ----
+
+extern "C" int mg_tree_create(int dim, int block_size, int geometry, const mg_bc *bc, const int base_cells[3],
+                              const double lo[3], const double hi[3], int coarse_max_cells, double helmholtz,
+                              mg_tree **out) {
+    if (!out || !bc || !base_cells || !lo || !hi) return fail(MG_ERR_ARG, "null argument");
+    if (dim != 2 && dim != 3) return fail(MG_ERR_ARG, "dim must be 2 or 3");
+    if (block_size < 2 || block_size % 2) return fail(MG_ERR_ARG, "block_size must be even and >= 2");
+    if (geometry != MG_CART && !(geometry == MG_CYL && dim == 2)) return fail(MG_ERR_ARG, "bad geometry");
+    if (helmholtz < 0) return fail(MG_ERR_ARG, "helmholtz must be >= 0");
+    for (int d = 0; d < dim; d++) {
+        if (base_cells[d] < block_size || base_cells[d] % block_size)
+            return fail(MG_ERR_ARG, "base_cells must be positive multiples of block_size");
+        if (!(hi[d] > lo[d])) return fail(MG_ERR_ARG, "hi must exceed lo");
+        const bool p0 = bc->type[2 * d] == MG_BC_PERIODIC, p1 = bc->type[2 * d + 1] == MG_BC_PERIODIC;
+        if (p0 != p1) return fail(MG_ERR_ARG, "periodic faces must come in pairs");
+    }
+    for (int f = 0; f < 2 * dim; f++)
+        if (bc->type[f] < 0 || bc->type[f] > MG_BC_AXIS) return fail(MG_ERR_ARG, "bad boundary type");
+    if (geometry == MG_CYL && bc->type[1] == MG_BC_AXIS) return fail(MG_ERR_ARG, "axis must be the -r face");
+    mg_tree *t = new mg_tree();
+    t->dim = dim;
+    t->N = block_size;
+    t->geom = geometry;
+    t->bc = *bc;
+    for (int d = 0; d < 3; d++) {
+        t->base[d] = d < dim ? base_cells[d] : 1;
+        t->lo[d] = lo[d];
+        t->hi[d] = d < dim ? hi[d] : lo[d] + 1.0;
+    }
+    t->coarse_max = coarse_max_cells;
+    t->helm = helmholtz;
+    *out = t;
+    return MG_OK;
+}
+
+extern "C" int mg_tree_refine(mg_tree *t, int n, const int32_t *e) {
+    if (!t || n < 0 || (n > 0 && !e)) return fail(MG_ERR_ARG, "bad refine arguments");
+    if (t->built) return fail(MG_ERR_ARG, "refine after the mesh was built");
+    t->refine.insert(t->refine.end(), e, e + 4 * (size_t)n);
+    return MG_OK;
+}
+
+// ------------------------------------------------------------- build ----
+// Levels (Sec. 2.5): below the base grid the block count is halved while all
+// counts are even, then the block size is halved while the level holds more
+// than coarse_max cells; above it the refined levels.  Per level the
+// covered blocks come first, then the leaves, each in Morton order.
+
+static int build(mg_tree *t) {
+    if (t->built) return MG_OK;
+    const int D = t->dim;
+    struct Lv { int n, depth, nblk[3]; std::vector<std::array<int, 3>> b; };
+    std::vector<Lv> lv;
+    int nb0[3] = {1, 1, 1};
+    for (int d = 0; d < D; d++) nb0[d] = t->base[d] / t->N;
+    {
+        std::vector<Lv> coarse;
+        int n = t->N, b[3] = {nb0[0], nb0[1], nb0[2]};
+        while (true) {
+            long long cells = 1;
+            bool even = true;
+            for (int d = 0; d < D; d++) { cells *= (long long)n * b[d]; if (b[d] % 2) even = false; }
+            if (even) for (int d = 0; d < D; d++) b[d] /= 2;
+            else if (cells > t->coarse_max && n % 2 == 0) n /= 2;
+            else break;
+            Lv c;
+            c.n = n; c.depth = -(int)coarse.size() - 1;
+            for (int d = 0; d < 3; d++) c.nblk[d] = b[d];
+            coarse.push_back(c);
+            if (coarse.size() > 60) break;
+        }
+        std::reverse(coarse.begin(), coarse.end());
+        lv = coarse;
+        Lv base;
+        base.n = t->N; base.depth = 0;
+        for (int d = 0; d < 3; d++) base.nblk[d] = nb0[d];
+        lv.push_back(base);
+        for (auto &L : lv)
+            for (int k = 0; k < L.nblk[2]; k++)
+                for (int j = 0; j < L.nblk[1]; j++)
+                    for (int i = 0; i < L.nblk[0]; i++) L.b.push_back({i, j, k});
+    }
+    const int ibase = (int)lv.size() - 1;
+    int maxdepth = -1;
+    for (size_t e = 0; e < t->refine.size() / 4; e++) maxdepth = std::max(maxdepth, t->refine[4 * e]);
+    for (int r = 0; r <= maxdepth; r++) {
+        const Lv &P = lv[ibase + r];
+        std::vector<char> exists((size_t)P.nblk[0] * P.nblk[1] * P.nblk[2], 0), done(exists.size(), 0);
+        for (auto &q : P.b) exists[((size_t)q[2] * P.nblk[1] + q[1]) * P.nblk[0] + q[0]] = 1;
+        Lv C;
+        C.n = t->N; C.depth = r + 1;
+        for (int d = 0; d < 3; d++) C.nblk[d] = d < D ? 2 * P.nblk[d] : 1;
+        for (size_t e = 0; e < t->refine.size() / 4; e++) {
+            if (t->refine[4 * e] != r) continue;
+            int q[3] = {t->refine[4 * e + 1], t->refine[4 * e + 2], D == 3 ? t->refine[4 * e + 3] : 0};
+            bool ok = true;
+            for (int d = 0; d < 3; d++) ok = ok && q[d] >= 0 && q[d] < P.nblk[d];
+            size_t m = ok ? ((size_t)q[2] * P.nblk[1] + q[1]) * P.nblk[0] + q[0] : 0;
+            if (!ok || !exists[m]) return fail(MG_ERR_ARG, "refined block does not exist");
+            if (done[m]) continue;
+            done[m] = 1;
+            for (int c = 0; c < (1 << D); c++)
+                C.b.push_back({2 * q[0] + (c & 1), 2 * q[1] + ((c >> 1) & 1), D == 3 ? 2 * q[2] + ((c >> 2) & 1) : 0});
+        }
+        if (C.b.empty()) return fail(MG_ERR_ARG, "refinement depths must be contiguous");
+        lv.push_back(C);
+    }
+    const int nl = (int)lv.size();
+    // dense coordinate maps and "has children" flags
+    std::vector<std::vector<int>> map(nl);
+    std::vector<std::vector<char>> haschild(nl);
+    auto key = [&](int l, int i, int j, int k) { return ((size_t)k * lv[l].nblk[1] + j) * lv[l].nblk[0] + i; };
+    for (int l = 0; l < nl; l++) {
+        map[l].assign((size_t)lv[l].nblk[0] * lv[l].nblk[1] * lv[l].nblk[2], -1);
+        haschild[l].assign(lv[l].b.size(), 0);
+        for (size_t b = 0; b < lv[l].b.size(); b++) map[l][key(l, lv[l].b[b][0], lv[l].b[b][1], lv[l].b[b][2])] = (int)b;
+    }
+    auto parent_of = [&](int l, const std::array<int, 3> &q, int *pq, int *poff) {
+        const bool same = lv[l - 1].n == lv[l].n;
+        for (int d = 0; d < 3; d++) {
+            pq[d] = d < D ? (same ? q[d] / 2 : q[d]) : 0;
+            poff[d] = d < D ? (same ? (q[d] % 2) * (lv[l].n / 2) : 0) : 0;
+        }
+    };
+    for (int l = 1; l < nl; l++)
+        for (auto &q : lv[l].b) {
+            int pq[3], po[3];
+            parent_of(l, q, pq, po);
+            haschild[l - 1][map[l - 1][key(l - 1, pq[0], pq[1], pq[2])]] = 1;
+        }
+    // order: covered blocks, then leaves, Morton within each group
+    std::vector<std::vector<int>> order(nl);
+    for (int l = 0; l < nl; l++) {
+        std::vector<int> &o = order[l];
+        o.resize(lv[l].b.size());
+        for (size_t b = 0; b < o.size(); b++) o[b] = (int)b;
+        std::sort(o.begin(), o.end(), [&](int a, int c) {
+            if (haschild[l][a] != haschild[l][c]) return haschild[l][a] > haschild[l][c];
+            return morton3(lv[l].b[a][0], lv[l].b[a][1], lv[l].b[a][2]) <
+                   morton3(lv[l].b[c][0], lv[l].b[c][1], lv[l].b[c][2]);
+        });
+    }
+    // global ids and offsets
+    t->lev.assign(nl, LevelHost());
+    std::vector<std::vector<int>> gid(nl);
+    int g = 0;
+    long long co = 0, go = 0, leaf = 0;
+    for (int l = 0; l < nl; l++) {
+        LevelHost &L = t->lev[l];
+        L.n = lv[l].n; L.depth = lv[l].depth;
+        for (int d = 0; d < 3; d++) {
+            L.nblk[d] = lv[l].nblk[d];
+            L.ncell[d] = d < D ? lv[l].nblk[d] * lv[l].n : 1;
+            L.h[d] = d < D ? (t->hi[d] - t->lo[d]) / L.ncell[d] : 1.0;
+        }
+        L.first = g;
+        L.nb = (int)lv[l].b.size();
+        L.nref = 0;
+        for (int b = 0; b < L.nb; b++) L.nref += haschild[l][b];
+        L.cell_first = co;
+        L.ghost_first = go;
+        L.ncells = L.nb * ipow(L.n, D);
+        L.nghost = L.nb * 2LL * D * (D == 2 ? L.n : (long long)L.n * L.n);
+        leaf += (long long)(L.nb - L.nref) * ipow(L.n, D);
+        gid[l].assign(L.nb, -1);
+        for (int r = 0; r < L.nb; r++) gid[l][order[l][r]] = g + r;
+        g += L.nb;
+        co += L.ncells;
+        go += L.nghost;
+    }
+    t->ncells = co;
+    t->nghost = go;
+    t->nleaf_cells = leaf;
+    t->blocks.assign(g, BlockDesc());
+    for (int l = 0; l < nl; l++) {
+        const LevelHost &L = t->lev[l];
+        const long long C = ipow(L.n, D), F = 2LL * D * (D == 2 ? L.n : (long long)L.n * L.n);
+        for (int r = 0; r < L.nb; r++) {
+            const int b = order[l][r];
+            BlockDesc &B = t->blocks[L.first + r];
+            const auto &q = lv[l].b[b];
+            B.cell_off = L.cell_first + r * C;
+            B.ghost_off = L.ghost_first + r * F;
+            B.n = L.n;
+            B.lev = l;
+            B.flags = haschild[l][b] ? 1 : 0;
+            for (int d = 0; d < 3; d++) B.ijk[d] = q[d];
+            B.parent = -1;
+            for (int d = 0; d < 3; d++) B.poff[d] = 0;
+            if (l > 0) {
+                int pq[3];
+                parent_of(l, q, pq, B.poff);
+                B.parent = gid[l - 1][map[l - 1][key(l - 1, pq[0], pq[1], pq[2])]];
+            }
+            for (int f = 0; f < 6; f++) B.nbr[f] = -1;
+            for (int d = 0; d < D; d++)
+                for (int s = 0; s < 2; s++) {
+                    int nq[3] = {q[0], q[1], q[2]};
+                    nq[d] += s ? 1 : -1;
+                    if (nq[d] < 0 || nq[d] >= L.nblk[d]) {
+                        if (t->bc.type[2 * d + s] != MG_BC_PERIODIC) continue;  // physical face
+                        nq[d] = (nq[d] + L.nblk[d]) % L.nblk[d];
+                    }
+                    const int m = map[l][key(l, nq[0], nq[1], nq[2])];
+                    if (m >= 0) { B.nbr[2 * d + s] = gid[l][m]; continue; }
+                    // no same-level neighbour: the region one level coarser must exist (2:1)
+                    if (l == 0 || lv[l - 1].n != L.n) return fail(MG_ERR_BALANCE, "incomplete coarse level");
+                    int cq[3] = {0, 0, 0};
+                    for (int e = 0; e < D; e++) cq[e] = nq[e] / 2;
+                    const int cm = map[l - 1][key(l - 1, cq[0], cq[1], cq[2])];
+                    if (cm < 0) return fail(MG_ERR_BALANCE, "mesh is not 2:1 balanced across faces");
+                    B.nbr[2 * d + s] = -2 - gid[l - 1][cm];
+                }
+        }
+    }
+    t->singular = t->helm <= 0;
+    for (int f = 0; f < 2 * D; f++)
+        if (t->bc.type[f] == MG_BC_DIRICHLET) t->singular = false;
+    t->nc = (int)(t->lev[0].nb * ipow(t->lev[0].n, D));
+    t->ns = t->nc + (t->singular ? 1 : 0);
+    t->built = true;
+    return MG_OK;
+}
+
+extern "C" int mg_tree_num_levels(mg_tree *t, int *nlev) {
+    if (!t || !nlev) return fail(MG_ERR_ARG, "null argument");
+    int rc = build(t);
+    if (rc) return rc;
+    *nlev = (int)t->lev.size();
+    return MG_OK;
+}
+
+extern "C" int mg_tree_level_info(mg_tree *t, int level, int32_t info[9], double h[3]) {
+    if (!t || !info || !h) return fail(MG_ERR_ARG, "null argument");
+    int rc = build(t);
+    if (rc) return rc;
+    if (level < 0 || level >= (int)t->lev.size()) return fail(MG_ERR_ARG, "level out of range");
+    const LevelHost &L = t->lev[level];
+    info[0] = L.n; info[1] = L.depth; info[2] = L.nb;
+    for (int d = 0; d < 3; d++) { info[3 + d] = L.nblk[d]; info[6 + d] = L.ncell[d]; h[d] = L.h[d]; }
+    return MG_OK;
+}
+
+extern "C" int mg_tree_num_leaf_cells(mg_tree *t, int64_t *n) {
+    if (!t || !n) return fail(MG_ERR_ARG, "null argument");
+    int rc = build(t);
+    if (rc) return rc;
+    *n = t->nleaf_cells;
+    return MG_OK;
+}
+
+extern "C" int mg_tree_leaf_blocks(mg_tree *t, int32_t *out) {
+    if (!t || !out) return fail(MG_ERR_ARG, "null argument");
+    int rc = build(t);
+    if (rc) return rc;
+    long long m = 0;
+    for (const LevelHost &L : t->lev)
+        for (int r = L.nref; r < L.nb; r++) {
+            const BlockDesc &B = t->blocks[L.first + r];
+            out[4 * m] = L.depth;
+            out[4 * m + 1] = B.ijk[0];
+            out[4 * m + 2] = B.ijk[1];
+            out[4 * m + 3] = B.ijk[2];
+            m++;
+        }
+    return MG_OK;
+}
+
+// ------------------------------------------------ device allocation ----
+
+template <class T> static int dalloc(T **p, long long n) {
+    if (*p) return MG_OK;
+    CK(cudaMalloc((void **)p, sizeof(T) * (size_t)std::max(1LL, n)));
+    CK(cudaMemset(*p, 0, sizeof(T) * (size_t)std::max(1LL, n)));
+    return MG_OK;
+}
+
+template <class T> static int alloc_fields(mg_tree *t, Fields<T> &F, bool with_eps) {
+    int rc;
+    if ((rc = dalloc(&F.X, t->ncells)) || (rc = dalloc(&F.XG, t->nghost)) || (rc = dalloc(&F.F, t->ncells)) ||
+        (rc = dalloc(&F.V, t->ncells)) || (rc = dalloc(&F.VG, t->nghost)))
+        return rc;
+    if (with_eps && ((rc = dalloc(&F.E, t->ncells)) || (rc = dalloc(&F.EG, t->nghost)))) return rc;
+    return MG_OK;
+}
+
+template <class T> static void free_fields(Fields<T> &F, bool free_eps) {
+    cudaFree(F.X); cudaFree(F.XG); cudaFree(F.F); cudaFree(F.V); cudaFree(F.VG);
+    if (free_eps) { cudaFree(F.E); cudaFree(F.EG); }
+    F = Fields<T>();
+}
+
+static int upload_bc(mg_tree *t) {
+    std::vector<double> all;
+    std::vector<LevelDesc> ld(t->lev.size());
+    for (size_t l = 0; l < t->lev.size(); l++) {
+        const LevelHost &L = t->lev[l];
+        LevelDesc &d = ld[l];
+        for (int e = 0; e < 3; e++) {
+            d.h[e] = L.h[e];
+            d.inv_h2[e] = 1.0 / (L.h[e] * L.h[e]);
+            d.ncell[e] = L.ncell[e];
+        }
+        d.n = L.n; d.first = L.first; d.nb = L.nb; d.nref = L.nref;
+        for (int f = 0; f < 6; f++) {
+            d.bc_off[f] = -1;
+            if (!L.bc[f].empty()) {
+                d.bc_off[f] = (long long)all.size();
+                all.insert(all.end(), L.bc[f].begin(), L.bc[f].end());
+            }
+        }
+    }
+    if (!t->d_levels) CK(cudaMalloc((void **)&t->d_levels, sizeof(LevelDesc) * ld.size()));
+    CK(cudaMemcpy(t->d_levels, ld.data(), sizeof(LevelDesc) * ld.size(), cudaMemcpyHostToDevice));
+    if ((long long)all.size() > t->n_bcplanes) {
+        cudaFree(t->d_bcplanes);
+        t->d_bcplanes = nullptr;
+        CK(cudaMalloc((void **)&t->d_bcplanes, sizeof(double) * all.size()));
+        t->n_bcplanes = (long long)all.size();
+    }
+    if (!all.empty())
+        CK(cudaMemcpy(t->d_bcplanes, all.data(), sizeof(double) * all.size(), cudaMemcpyHostToDevice));
+    t->bc_dirty = false;
+    return MG_OK;
+}
+
+// Dense inverse of the coarsest-level operator with homogeneous boundary
+// values (bordered by sum V x = 0 when the problem has no Dirichlet face),
+// assembled row by row from the 5/7-point stencil and inverted by
+// Gauss-Jordan elimination with partial pivoting (FP64, host).
+static int build_coarse_inverse(mg_tree *t) {
+    const int D = t->dim;
+    const LevelHost &L = t->lev[0];
+    const int n = L.n, C = (int)ipow(n, D), nc = t->nc, ns = t->ns;
+    std::vector<double> eps(nc, 1.0);
+    if (t->var_eps) {
+        CK(cudaStreamSynchronize(t->stream));
+        CK(cudaMemcpy(eps.data(), t->f64.E, sizeof(double) * nc, cudaMemcpyDeviceToHost));
+    }
+    std::vector<int> rowmap((size_t)L.ncell[0] * L.ncell[1] * L.ncell[2]);
+    auto cellkey = [&](const int *G) { return ((size_t)G[2] * L.ncell[1] + G[1]) * L.ncell[0] + G[0]; };
+    for (int b = 0; b < L.nb; b++) {
+        const BlockDesc &B = t->blocks[L.first + b];
+        for (int c = 0; c < C; c++) {
+            int G[3] = {B.ijk[0] * n + c % n, B.ijk[1] * n + (c / n) % n, D == 3 ? B.ijk[2] * n + c / (n * n) : 0};
+            rowmap[cellkey(G)] = b * C + c;
+        }
+    }
+    std::vector<double> M((size_t)ns * ns, 0.0);
+    for (int b = 0; b < L.nb; b++) {
+        const BlockDesc &B = t->blocks[L.first + b];
+        for (int c = 0; c < C; c++) {
+            const int row = b * C + c;
+            int G[3] = {B.ijk[0] * n + c % n, B.ijk[1] * n + (c / n) % n, D == 3 ? B.ijk[2] * n + c / (n * n) : 0};
+            const double ri = t->lo[0] + (G[0] + 0.5) * L.h[0];
+            for (int d = 0; d < D; d++)
+                for (int s = 0; s < 2; s++) {
+                    int Q[3] = {G[0], G[1], G[2]};
+                    Q[d] += s ? 1 : -1;
+                    bool phys = false;
+                    if (Q[d] < 0 || Q[d] >= L.ncell[d]) {
+                        if (t->bc.type[2 * d + s] == MG_BC_PERIODIC) Q[d] = (Q[d] + L.ncell[d]) % L.ncell[d];
+                        else phys = true;
+                    }
+                    double w = 1.0 / (L.h[d] * L.h[d]);
+                    const int col = phys ? -1 : rowmap[cellkey(Q)];
+                    const double ec = eps[row], eo = phys ? ec : eps[col];
+                    w *= 2.0 * ec * eo / (ec + eo);
+                    if (t->geom == MG_CYL && d == 0) w *= (t->lo[0] + (G[0] + s) * L.h[0]) / ri;
+                    if (!phys) {
+                        M[(size_t)row * ns + col] += w;
+                        M[(size_t)row * ns + row] -= w;
+                    } else if (t->bc.type[2 * d + s] == MG_BC_DIRICHLET) {
+                        M[(size_t)row * ns + row] -= 2.0 * w;
+                    }
+                }
+            M[(size_t)row * ns + row] -= t->helm;
+            if (t->singular) {
+                double V = 1.0;
+                for (int d = 0; d < D; d++) V *= L.h[d];
+                if (t->geom == MG_CYL) V = 2.0 * M_PI * ri * L.h[0] * L.h[1];
+                M[(size_t)row * ns + nc] = 1.0;
+                M[(size_t)nc * ns + row] = V;
+            }
+        }
+    }
+    // Gauss-Jordan on [M | I]
+    std::vector<double> Inv((size_t)ns * ns, 0.0);
+    for (int i = 0; i < ns; i++) Inv[(size_t)i * ns + i] = 1.0;
+    for (int c = 0; c < ns; c++) {
+        int p = c;
+        for (int r = c + 1; r < ns; r++)
+            if (std::fabs(M[(size_t)r * ns + c]) > std::fabs(M[(size_t)p * ns + c])) p = r;
+        if (M[(size_t)p * ns + c] == 0.0) return fail(MG_ERR_ARG, "coarsest-level matrix is singular");
+        if (p != c)
+            for (int e = 0; e < ns; e++) {
+                std::swap(M[(size_t)c * ns + e], M[(size_t)p * ns + e]);
+                std::swap(Inv[(size_t)c * ns + e], Inv[(size_t)p * ns + e]);
+            }
+        const double piv = 1.0 / M[(size_t)c * ns + c];
+        for (int e = 0; e < ns; e++) { M[(size_t)c * ns + e] *= piv; Inv[(size_t)c * ns + e] *= piv; }
+        for (int r = 0; r < ns; r++) {
+            if (r == c) continue;
+            const double m = M[(size_t)r * ns + c];
+            if (m == 0.0) continue;
+            for (int e = 0; e < ns; e++) {
+                M[(size_t)r * ns + e] -= m * M[(size_t)c * ns + e];
+                Inv[(size_t)r * ns + e] -= m * Inv[(size_t)c * ns + e];
+            }
+        }
+    }
+    if (!t->d_minv) CK(cudaMalloc((void **)&t->d_minv, sizeof(double) * (size_t)ns * ns));
+    CK(cudaMemcpy(t->d_minv, Inv.data(), sizeof(double) * (size_t)ns * ns, cudaMemcpyHostToDevice));
+    t->minv_ok = true;
+    return MG_OK;
+}
+
+extern "C" int mg_tree_finalize(mg_tree *t, void *stream) {
+    if (!t) return fail(MG_ERR_ARG, "null tree");
+    if (t->finalized) return fail(MG_ERR_ARG, "already finalized");
+    int rc = build(t);
+    if (rc) return rc;
+    CK(cudaGetDevice(&t->device));
+    t->stream = (cudaStream_t)stream;
+    CK(cudaMalloc((void **)&t->d_blocks, sizeof(BlockDesc) * t->blocks.size()));
+    CK(cudaMemcpy(t->d_blocks, t->blocks.data(), sizeof(BlockDesc) * t->blocks.size(), cudaMemcpyHostToDevice));
+    if ((rc = upload_bc(t))) return rc;
+    if ((rc = alloc_fields(t, t->f64, false))) return rc;
+    int maxleaf = 0;
+    long long nleafb = 0;
+    for (auto &L : t->lev) { maxleaf = std::max(maxleaf, L.nb - L.nref); nleafb += L.nb - L.nref; }
+    t->n_partials = (int)nleafb;
+    if ((rc = dalloc(&t->d_partials, 3 * nleafb))) return rc;
+    if ((rc = dalloc(&t->d_red, 3))) return rc;
+    if ((rc = dalloc(&t->d_cvec, t->ns))) return rc;
+    CK(cudaMallocHost((void **)&t->h_red, 3 * sizeof(double)));
+    t->finalized = true;
+    if ((rc = build_coarse_inverse(t))) return rc;
+    refresh<double>(t, t->f64, 0);
+    return check_cuda("finalize");
+}
+
+#define NEED_FINAL(t)                                                            \
+    do {                                                                         \
+        if (!(t) || !(t)->finalized) return fail(MG_ERR_ARG, "tree not finalized"); \
+    } while (0)
+
+extern "C" int mg_set_bc_plane(mg_tree *t, int face, int level, const double *vals) {
+    if (!t || !vals) return fail(MG_ERR_ARG, "null argument");
+    int rc = build(t);
+    if (rc) return rc;
+    if (face < 0 || face >= 2 * t->dim || level < 0 || level >= (int)t->lev.size())
+        return fail(MG_ERR_ARG, "face or level out of range");
+    LevelHost &L = t->lev[level];
+    const int d = face / 2;
+    long long cnt = 1;
+    for (int e = 0; e < t->dim; e++)
+        if (e != d) cnt *= L.ncell[e];
+    L.bc[face].assign(vals, vals + cnt);
+    if (t->finalized) {
+        if ((rc = upload_bc(t))) return rc;
+        refresh<double>(t, t->f64, 0);
+        return check_cuda("set_bc_plane");
+    }
+    return MG_OK;
+}
+
+// copy between a leaf-order vector and the leaf cells of a pool field
+template <class T> static int leaf_copy(mg_tree *t, T *cells, const T *leaf, bool to_cells) {
+    long long off = 0;
+    for (auto &L : t->lev) {
+        const long long n = (long long)(L.nb - L.nref) * ipow(L.n, t->dim);
+        if (n == 0) continue;
+        const long long c0 = t->blocks[L.first + L.nref].cell_off;
+        if (to_cells)
+            CK(cudaMemcpyAsync(cells + c0, leaf + off, sizeof(T) * n, cudaMemcpyDeviceToDevice, t->stream));
+        else
+            CK(cudaMemcpyAsync((T *)leaf + off, cells + c0, sizeof(T) * n, cudaMemcpyDeviceToDevice, t->stream));
+        off += n;
+    }
+    return MG_OK;
+}
+
+extern "C" int mg_set_rhs(mg_tree *t, const double *f) {
+    NEED_FINAL(t);
+    if (!f) return fail(MG_ERR_ARG, "null rhs");
+    return leaf_copy(t, t->f64.F, f, true);
+}
+
+extern "C" int mg_set_phi(mg_tree *t, const double *x) {
+    NEED_FINAL(t);
+    if (!x) return fail(MG_ERR_ARG, "null phi");
+    int rc = leaf_copy(t, t->f64.X, x, true);
+    if (rc) return rc;
+    refresh<double>(t, t->f64, 0);
+    return check_cuda("set_phi");
+}
+
+extern "C" int mg_get_phi(mg_tree *t, double *x) {
+    NEED_FINAL(t);
+    if (!x) return fail(MG_ERR_ARG, "null phi");
+    return leaf_copy(t, t->f64.X, (const double *)x, false);
+}
+
+extern "C" int mg_set_eps(mg_tree *t, const double *e) {
+    NEED_FINAL(t);
+    if (!e) return fail(MG_ERR_ARG, "null eps");
+    int rc;
+    if ((rc = dalloc(&t->f64.E, t->ncells)) || (rc = dalloc(&t->f64.EG, t->nghost))) return rc;
+    t->var_eps = true;
+    if ((rc = leaf_copy(t, t->f64.E, e, true))) return rc;
+    refresh_eps<double>(t, t->f64);
+    t->adj.E = t->f64.E;
+    t->adj.EG = t->f64.EG;
+    if (t->f32.X) {
+        if ((rc = dalloc(&t->f32.E, t->ncells)) || (rc = dalloc(&t->f32.EG, t->nghost))) return rc;
+        copy_eps_to_f32(t);
+    }
+    if ((rc = check_cuda("set_eps"))) return rc;
+    return build_coarse_inverse(t);
+}
+
+static void params_or_default(const mg_params *p, mg_params *q) {
+    if (p) *q = *p;
+    else { q->n_down = 2; q->n_up = 2; q->precision = MG_FP64; q->inner_cycles = 1; }
+    if (q->inner_cycles < 1) q->inner_cycles = 1;
+}
+
+extern "C" int mg_vcycle(mg_tree *t, int n, const mg_params *p) {
+    NEED_FINAL(t);
+    mg_params q;
+    params_or_default(p, &q);
+    for (int c = 0; c < n; c++) vcycle<double>(t, t->f64, (int)t->lev.size() - 1, q.n_down, q.n_up, 0);
+    return check_cuda("vcycle");
+}
+
+extern "C" int mg_fmg(mg_tree *t, const mg_params *p) {
+    NEED_FINAL(t);
+    mg_params q;
+    params_or_default(p, &q);
+    fmg<double>(t, t->f64, q.n_down, q.n_up, 0);
+    return check_cuda("fmg");
+}
+
+extern "C" int mg_residual_norm(mg_tree *t, double *l2, double *linf, double *dev_r) {
+    NEED_FINAL(t);
+    if (!l2 || !linf) return fail(MG_ERR_ARG, "null output");
+    double o[3];
+    residual_norm(t, t->f64, 0, o, dev_r, nullptr);
+    int rc = check_cuda("residual_norm");
+    if (rc) return rc;
+    *l2 = std::sqrt(o[0] / o[1]);
+    *linf = o[2];
+    if (!std::isfinite(*l2) || !std::isfinite(*linf)) return fail(MG_ERR_NAN, "residual is not finite");
+    return MG_OK;
+}
+
+static int ensure_f32(mg_tree *t) {
+    int rc;
+    if ((rc = alloc_fields(t, t->f32, t->var_eps))) return rc;
+    if (t->var_eps) copy_eps_to_f32(t);
+    return MG_OK;
+}
+
+extern "C" int mg_solve(mg_tree *t, double rel_tol, int max_cycles, int fmg_first, const mg_params *p,
+                        int *cycles_done, double *rel_out) {
+    NEED_FINAL(t);
+    mg_params q;
+    params_or_default(p, &q);
+    const int top = (int)t->lev.size() - 1;
+    double o[3];
+    int cycles = 0, rc;
+    double rel = 1.0;
+    if (q.precision == MG_FP64) {
+        residual_norm(t, t->f64, 0, o, nullptr, nullptr);
+        const double r0 = std::sqrt(o[0] / o[1]);
+        if (fmg_first && max_cycles > 0) {
+            fmg<double>(t, t->f64, q.n_down, q.n_up, 0);
+            cycles++;
+            residual_norm(t, t->f64, 0, o, nullptr, nullptr);
+            rel = r0 > 0 ? std::sqrt(o[0] / o[1]) / r0 : 0.0;
+        } else {
+            rel = r0 > 0 ? 1.0 : 0.0;
+        }
+        while (rel > rel_tol && cycles < max_cycles) {
+            vcycle<double>(t, t->f64, top, q.n_down, q.n_up, 0);
+            cycles++;
+            residual_norm(t, t->f64, 0, o, nullptr, nullptr);
+            rel = std::sqrt(o[0] / o[1]) / r0;
+            if (!std::isfinite(rel)) break;
+        }
+    } else if (q.precision == MG_FP32_DC) {
+        if ((rc = ensure_f32(t))) return rc;
+        residual_norm(t, t->f64, 0, o, nullptr, t->f32.F);
+        const double r0 = std::sqrt(o[0] / o[1]);
+        rel = r0 > 0 ? 1.0 : 0.0;
+        while (rel > rel_tol && cycles < max_cycles) {
+            CK(cudaMemsetAsync(t->f32.X, 0, sizeof(float) * t->ncells, t->stream));
+            CK(cudaMemsetAsync(t->f32.XG, 0, sizeof(float) * t->nghost, t->stream));
+            if (fmg_first && cycles == 0) {
+                fmg<float>(t, t->f32, q.n_down, q.n_up, 1);
+                for (int c = 1; c < q.inner_cycles; c++) vcycle<float>(t, t->f32, top, q.n_down, q.n_up, 1);
+            } else {
+                for (int c = 0; c < q.inner_cycles; c++) vcycle<float>(t, t->f32, top, q.n_down, q.n_up, 1);
+            }
+            add_e_to_phi(t, t->f32.X, t->f64.X);
+            cycles++;
+            residual_norm(t, t->f64, 0, o, nullptr, t->f32.F);
+            rel = std::sqrt(o[0] / o[1]) / r0;
+            if (!std::isfinite(rel)) break;
+        }
+    } else {
+        return fail(MG_ERR_ARG, "unknown precision");
+    }
+    if ((rc = check_cuda("solve"))) return rc;
+    if (cycles_done) *cycles_done = cycles;
+    if (rel_out) *rel_out = rel;
+    if (!std::isfinite(rel)) return fail(MG_ERR_NAN, "residual is not finite");
+    if (rel > rel_tol) return fail(MG_ERR_NOT_CONVERGED, "max_cycles reached");
+    return MG_OK;
+}
+
+extern "C" int mg_adjoint(mg_tree *t, const double *g, double *dLdf, double *dLdeps, const mg_params *p,
+                          int n_cycles) {
+    NEED_FINAL(t);
+    if (!g || !dLdf) return fail(MG_ERR_ARG, "null argument");
+    for (const BlockDesc &B : t->blocks)
+        for (int f = 0; f < 2 * t->dim; f++)
+            if (B.nbr[f] <= -2) return fail(MG_ERR_UNSUPPORTED, "adjoint needs a mesh without refinement faces");
+    mg_params q;
+    params_or_default(p, &q);
+    int rc;
+    if ((rc = alloc_fields(t, t->adj, false))) return rc;
+    t->adj.E = t->f64.E;
+    t->adj.EG = t->f64.EG;
+    // rhs g (Cartesian) or g / r (cylindrical: A^T = diag(r) A diag(r)^-1)
+    if (t->geom == MG_CYL) {
+        scale_by_radius(t, g, dLdf, 1);
+        if ((rc = leaf_copy(t, t->adj.F, (const double *)dLdf, true))) return rc;
+    } else {
+        if ((rc = leaf_copy(t, t->adj.F, g, true))) return rc;
+    }
+    CK(cudaMemsetAsync(t->adj.X, 0, sizeof(double) * t->ncells, t->stream));
+    CK(cudaMemsetAsync(t->adj.XG, 0, sizeof(double) * t->nghost, t->stream));
+    fmg<double>(t, t->adj, q.n_down, q.n_up, 1);
+    const int top = (int)t->lev.size() - 1;
+    for (int c = 0; c < n_cycles; c++) vcycle<double>(t, t->adj, top, q.n_down, q.n_up, 1);
+    if ((rc = leaf_copy(t, t->adj.X, (const double *)dLdf, false))) return rc;
+    if (t->geom == MG_CYL) {
+        scale_by_radius(t, dLdf, dLdf, 0);
+        if ((rc = leaf_copy(t, t->adj.X, (const double *)dLdf, true))) return rc;
+        refresh<double>(t, t->adj, 1);
+    }
+    if (dLdeps) eps_grad(t, t->adj.X, t->f64.X, dLdeps);
+    return check_cuda("adjoint");
+}
+
+extern "C" int mg_launch_count(mg_tree *t, int64_t *n) {
+    if (!t || !n) return fail(MG_ERR_ARG, "null argument");
+    *n = t->launches;
+    return MG_OK;
+}
+
+extern "C" int mg_time_sweeps(mg_tree *t, int level, int n_sweeps, double out[4]) {
+    NEED_FINAL(t);
+    if (!out || n_sweeps < 1 || level < 0 || level >= (int)t->lev.size()) return fail(MG_ERR_ARG, "bad arguments");
+    int rc = time_sweeps(t, level, n_sweeps, out);
+    if (rc) return rc;
+    return check_cuda("time_sweeps");
+}
+
+extern "C" int mg_tree_destroy(mg_tree *t) {
+    if (!t) return MG_OK;
+    if (t->finalized) {
+        cudaStreamSynchronize(t->stream);
+        free_fields(t->f64, true);
+        free_fields(t->adj, false);
+        free_fields(t->f32, true);
+        cudaFree(t->d_blocks); cudaFree(t->d_levels); cudaFree(t->d_bcplanes);
+        cudaFree(t->d_r64); cudaFree(t->d_minv); cudaFree(t->d_cvec); cudaFree(t->d_partials); cudaFree(t->d_red);
+        cudaFreeHost(t->h_red);
+    }
+    delete t;
+    return MG_OK;
+}

@@ -313,7 +313,7 @@ def cfg1_poisson2d(n=64, N=8):
                    np.zeros((0, 4), np.int32), 512, rhs=rhs, exact=phi)
 
 
-def cfg2_gauss3d(base=128, N=8, seed=0, radii=(0.44, 0.22, 0.11), sigma=0.02, coarse_max=512):
+def cfg2_gauss3d(base=128, N=8, seed=0, radii=(0.3, 0.22, 0.14), sigma=0.02, coarse_max=512):
     """3D Poisson, octree of N^3 blocks, base^3 cells plus len(radii) levels in
     nested spheres around a seeded Gaussian source; Dirichlet from the
     closed-form potential."""
