@@ -252,8 +252,9 @@ def run_ours(args):
     barrier()
     e2e_ms = max_over_ranks(e0.elapsed_time(e1) / args.steps)
 
-    # roofline of the dominant kernel (red-black smoother) on the largest level
-    (ms_s, ms_g, b_s, b_g), lev = tree.time_sweeps(n_sweeps=8)
+    # roofline of the dominant kernel (fused red-black sweep) on the largest level
+    (ms_s, ms_g, b_s, b_g), lev = tree.time_sweeps(n_sweeps=8, precision=mg.MG_FP32_DC)
+    (ms_s64, _, b_s64, _), _ = tree.time_sweeps(n_sweeps=4, precision=mg.MG_FP64)
     peak, peak_kind = peak_hbm()
     achieved = b_s / (ms_s * 1e-3) / 1e9
     traffic = None
@@ -287,11 +288,12 @@ def run_ours(args):
         "e2e": {"value": total_unknowns / (e2e_ms * 1e-3), "unit": "unknowns/s", "ms_per_step": e2e_ms,
                 "h2d_bytes_per_step": n * 8, "d2h_bytes_per_step": n * 8},
         "gpu_launches": launches,
-        "roofline": {"bound": "hbm", "kernel": "k_smooth<double,3> (one colour, level %d)" % lev,
+        "roofline": {"bound": "hbm", "kernel": "k_sweep<float,3,8> (one colour, level %d)" % lev,
                      "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "alg_bytes_per_launch": b_s,
-                     "ms_per_launch": ms_s, "ghost_ms_per_launch": ms_g,
-                     "ghost_achieved_GBs": b_g / (ms_g * 1e-3) / 1e9},
+                     "ms_per_launch": ms_s,
+                     "fp64_sweep": {"ms_per_launch": ms_s64, "achieved_GBs": b_s64 / (ms_s64 * 1e-3) / 1e9},
+                     "ghost_fill_ms_per_launch": ms_g, "ghost_fill_achieved_GBs": b_g / (ms_g * 1e-3) / 1e9},
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"] = oracle_baseline(p, n)
@@ -301,6 +303,27 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_profile(kind):
+    """Small fixed launch sequences for ncu captures (not a benchmark):
+    sweeps64 -- one red-black sweep (2 smoother + 2 ghost launches) on the
+    largest level of the workload; solve32 / solve64 -- one solve after one
+    untimed warm-up solve."""
+    import torch
+    import paper_1901_11370_gb300 as mg
+    torch.cuda.set_device(0)
+    tree = mg.Tree.from_problem(problem())
+    zeros = torch.zeros(tree.n_leaf, dtype=torch.float64, device="cuda")
+    if kind in ("sweeps64", "sweeps32"):
+        tree.time_sweeps(n_sweeps=1, precision=mg.MG_FP64 if kind == "sweeps64" else mg.MG_FP32_DC)
+    else:
+        prec = mg.MG_FP32_DC if kind == "solve32" else mg.MG_FP64
+        for _ in range(2):
+            tree.set_phi(zeros)
+            tree.solve(TOL, MAX_CYCLES, fmg_first=True, precision=prec)
+    torch.cuda.synchronize()
+    print("profile %s done: %d launches" % (kind, tree.launch_count()))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -308,8 +331,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile", choices=["sweeps64", "sweeps32", "solve32", "solve64"], default=None)
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.profile:
+        run_profile(args.profile)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

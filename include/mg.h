@@ -44,6 +44,7 @@ enum {
     MG_ERR_CUDA = -3,           /* a CUDA runtime call failed */
     MG_ERR_NOT_CONVERGED = -4,  /* mg_solve hit max_cycles */
     MG_ERR_NAN = -5,            /* a residual norm is not finite */
+    MG_ERR_TIMEOUT = -6,        /* a bounded wait inside a kernel expired */
     MG_ERR_UNSUPPORTED = -9     /* valid request outside what is built */
 };
 enum { MG_CART = 0, MG_CYL = 1 };
@@ -161,16 +162,18 @@ int mg_adjoint(mg_tree *t, const double *dev_dLdphi, double *dev_dLdf, double *d
 /*
  * Instrumentation (the paper has no counterpart; used by the benchmark).
  * mg_launch_count: number of CUDA kernels this tree has launched so far.
- * mg_time_sweeps: runs n_sweeps red-black sweeps on `level` (FP64 fields,
- * a real smoothing step: phi changes) with CUDA events around every kernel
- * on the tree's stream.  out[0] = mean ms of one smoother launch (one
- * colour), out[1] = mean ms of one ghost-fill launch, out[2] = algorithmic
- * bytes of one smoother launch (read phi, f, eps and the face ghosts once,
- * write phi once), out[3] = algorithmic bytes of one ghost-fill launch
- * (read the source cells, write the ghosts once).  Synchronises the stream.
+ * mg_time_sweeps: runs n_sweeps red-black sweeps on `level` of the FP64
+ * (precision MG_FP64) or FP32 (MG_FP32_DC) fields -- a real smoothing step,
+ * the field changes -- each colour as one fused sweep launch followed by a
+ * full ghost-fill launch, with CUDA events around every kernel on the
+ * tree's stream.  out[0] = mean ms of one sweep launch (one colour, ghost
+ * pushes included), out[1] = mean ms of one full ghost-fill launch,
+ * out[2] = algorithmic bytes of one sweep launch (read x, f, eps and the
+ * face ghosts once, write x once), out[3] = algorithmic bytes of one ghost
+ * fill (read the source cells, write the ghosts once).  Synchronises.
  */
 int mg_launch_count(mg_tree *t, int64_t *n);
-int mg_time_sweeps(mg_tree *t, int level, int n_sweeps, double out[4]);
+int mg_time_sweeps(mg_tree *t, int level, int n_sweeps, int precision, double out[4]);
 
 /* mg_tree_destroy -- free device and host memory (synchronises the stream). */
 int mg_tree_destroy(mg_tree *t);

@@ -153,14 +153,14 @@ class Tree:
         check(self.L.mg_launch_count(self._h, C.byref(n)))
         return n.value
 
-    def time_sweeps(self, level=-1, n_sweeps=4):
-        """(ms per smoother launch, ms per ghost launch, bytes per smoother
-        launch, bytes per ghost launch) on one level (default: the largest)."""
+    def time_sweeps(self, level=-1, n_sweeps=4, precision=MG_FP64):
+        """(ms per sweep launch, ms per full ghost fill, bytes per sweep
+        launch, bytes per ghost fill) on one level (default: the largest)."""
         lv = self.levels()
         if level < 0:
             level = max(range(len(lv)), key=lambda l: lv[l]["nb"] * lv[l]["n"] ** self.dim)
         out = (C.c_double * 4)()
-        check(self.L.mg_time_sweeps(self._h, level, n_sweeps, out))
+        check(self.L.mg_time_sweeps(self._h, level, n_sweeps, precision, out))
         return tuple(out), level
 
     def adjoint(self, g, n_cycles=12, want_eps=True, n_down=2, n_up=2):

@@ -12,7 +12,7 @@ LIB_PATH = os.path.join(HERE, "libmg_gb300.so")
 
 MG_OK = 0
 ERRORS = {-1: "MG_ERR_ARG", -2: "MG_ERR_BALANCE", -3: "MG_ERR_CUDA", -4: "MG_ERR_NOT_CONVERGED",
-          -5: "MG_ERR_NAN", -9: "MG_ERR_UNSUPPORTED"}
+          -5: "MG_ERR_NAN", -6: "MG_ERR_TIMEOUT", -9: "MG_ERR_UNSUPPORTED"}
 
 # every entry point declared in include/mg.h
 EXPORTS = ["mg_tree_create", "mg_tree_refine", "mg_tree_num_levels", "mg_tree_level_info",
@@ -66,7 +66,7 @@ def load():
     L.mg_adjoint.argtypes = [vp, vp, vp, vp, C.POINTER(mg_params), C.c_int]
     L.mg_tree_destroy.argtypes = [vp]
     L.mg_launch_count.argtypes = [vp, C.POINTER(C.c_int64)]
-    L.mg_time_sweeps.argtypes = [vp, C.c_int, C.c_int, dp]
+    L.mg_time_sweeps.argtypes = [vp, C.c_int, C.c_int, C.c_int, dp]
     L.mg_last_error.restype = C.c_char_p
     _lib = L
     return L

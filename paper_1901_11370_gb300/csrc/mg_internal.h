@@ -27,7 +27,10 @@ struct BlockDesc {
     int poff[3];          // offset of this block inside its parent, in parent cells
     int nbr[6];           // >= 0 same-level neighbour id; -1 physical face;
                           // <= -2: coarser neighbour, id = -2 - nbr
+    long long push[6];    // same-level neighbour across face f: first ghost slot
+                          // of its face f^1 (ghost_off + (f^1) * face size), else -1
 };
+static_assert(sizeof(BlockDesc) % 16 == 0, "BlockDesc is copied with 16-byte bulk copies");
 
 struct LevelDesc {
     double h[3];
@@ -52,6 +55,7 @@ struct KParams {
     int geom;
     int var_eps;
     int homog;            // 1: boundary values read as zero
+    int *status;          // device status word: 1 = a bounded wait gave up
 };
 
 template <class T>
@@ -105,6 +109,8 @@ struct mg_tree {
     double *d_red = nullptr;       // reduced norms (3)
     double *h_red = nullptr;       // pinned host copy
     long long launches = 0;        // kernels launched so far
+    int *d_status = nullptr;       // device status word (0 = ok)
+    int nsm = 0;                   // multiprocessors of the device
 };
 
 namespace mg {
@@ -122,7 +128,7 @@ void copy_eps_to_f32(mg_tree *t);
 void eps_grad(mg_tree *t, const double *lam_cells, const double *phi_cells, double *out_leaf);
 void scale_by_radius(mg_tree *t, const double *in_leaf, double *out_leaf, int divide);
 KParams kparams(mg_tree *t, int homog);
-int time_sweeps(mg_tree *t, int level, int n_sweeps, double *out4);
+int time_sweeps(mg_tree *t, int level, int n_sweeps, int prec, double *out4);
 int check_cuda(const char *what);
 }  // namespace mg
 

@@ -8,6 +8,8 @@
 // tensor cores: the kernels are written for coalesced HBM access of whole
 // blocks, with neighbour faces served by L1/L2.
 #include <cmath>
+#include <algorithm>
+#include <cstdint>
 #include <cstdio>
 #include <vector>
 
@@ -17,8 +19,8 @@ namespace mg {
 
 static constexpr int kMaxThreads = 256;
 
-template <int D> __host__ __device__ __forceinline__ int cells_of(int n) { return D == 2 ? n * n : n * n * n; }
-template <int D> __host__ __device__ __forceinline__ int face_of(int n) { return D == 2 ? n : n * n; }
+template <int D> __host__ __device__ constexpr int cells_of(int n) { return D == 2 ? n * n : n * n * n; }
+template <int D> __host__ __device__ constexpr int face_of(int n) { return D == 2 ? n : n * n; }
 template <int D> __device__ __forceinline__ int cidx(int n, int i, int j, int k) {
     return D == 2 ? j * n + i : (k * n + j) * n + i;
 }
@@ -92,6 +94,90 @@ __device__ __forceinline__ void cell_of(int c, int n, int D, int &i, int &j, int
     k = D == 3 ? c / (n * n) : 0;
 }
 
+// Small integer triple handled with selects (no dynamically indexed arrays,
+// which would live in local memory).
+struct I3 {
+    int x, y, z;
+};
+__device__ __forceinline__ int get(const I3 &v, int d) { return d == 0 ? v.x : (d == 1 ? v.y : v.z); }
+__device__ __forceinline__ void put(I3 &v, int d, int val) {
+    v.x = d == 0 ? val : v.x;
+    v.y = d == 1 ? val : v.y;
+    v.z = d == 2 ? val : v.z;
+}
+// interior cell beside face cell u of face `face` (ghost side when ghost)
+template <int D> __device__ __forceinline__ I3 face_cell(int n, int face, int u, bool ghost) {
+    const int d = face >> 1, s = face & 1, a = u % n, c = u / n;
+    const int e = ghost ? (s ? n : -1) : (s ? n - 1 : 0);
+    if (D == 2) return d == 0 ? I3{e, a, 0} : I3{a, e, 0};
+    return d == 0 ? I3{e, a, c} : (d == 1 ? I3{a, e, c} : I3{a, c, e});
+}
+
+// Copy of the CTA's block descriptor in shared memory.
+__device__ __forceinline__ void stage_desc(const KParams &P, int g, BlockDesc &sb) {
+    static_assert(sizeof(BlockDesc) % 4 == 0, "descriptor copied as words");
+    if (threadIdx.x < sizeof(BlockDesc) / 4)
+        reinterpret_cast<int *>(&sb)[threadIdx.x] = reinterpret_cast<const int *>(P.B + g)[threadIdx.x];
+    __syncthreads();
+}
+
+// Boundary value a (Dirichlet) or b (Neumann) of physical face `face` at
+// the face cell beside interior cell ii of block b.
+__device__ __forceinline__ double bc_value(const KParams &P, const LevelDesc &L, const BlockDesc &b, int D,
+                                           int face, I3 ii) {
+    if (P.homog) return 0.0;
+    if (L.bc_off[face] < 0) return P.bcv[face];
+    const int d = face >> 1, n = b.n;
+    const int t1 = d == 0 ? 1 : 0, t2 = D == 2 ? -1 : (d == 2 ? 1 : 2);
+    long long idx = b.ijk[t1] * n + get(ii, t1);
+    if (t2 >= 0) idx += (long long)L.ncell[t1] * (b.ijk[t2] * n + get(ii, t2));
+    return P.bcplanes[L.bc_off[face] + idx];
+}
+
+// Physical-boundary ghost (Sec. 2.6): Dirichlet 2a - x_i, Neumann
+// x_i -/+ h b on the low/high face, axis x_i.
+template <class T>
+__device__ __forceinline__ T phys_ghost(const KParams &P, const LevelDesc &L, int face, T xi, double a) {
+    const int d = face >> 1, s = face & 1;
+    switch (P.bct[face]) {
+    case MG_BC_DIRICHLET: return (T)(2.0 * a) - xi;
+    case MG_BC_NEUMANN: return s ? xi + (T)(L.h[d] * a) : xi - (T)(L.h[d] * a);
+    default: return xi;
+    }
+}
+
+// Refinement-boundary ghost of fine block b on face `face` beside interior
+// cell ii (Sec. 2.6): B' = B + sum_t s_t (C_t - A_t)/8 from the coarser
+// neighbour q (its own ghosts supply A_t / C_t outside q), then
+// g = B'/2 + 3c/4 - d/4 with c = x(ii) and d the next cell inwards.  With
+// coef set, the coefficient ghost is B itself.
+template <class T, int D>
+__device__ __forceinline__ T cf_ghost(const KParams &P, const LevelDesc &L, const BlockDesc &b, int face, I3 ii,
+                                      T c, T dv, const T *__restrict__ X, const T *__restrict__ XG, int nbcode,
+                                      bool coef) {
+    const BlockDesc &q = P.B[-2 - nbcode];
+    const int n = b.n, qn = q.n, d = face >> 1, s = face & 1;
+    I3 G{b.ijk[0] * n + ii.x, b.ijk[1] * n + ii.y, b.ijk[2] * n + ii.z};
+    int gd = b.ijk[d] * n + (s ? n : -1);
+    const int nd = L.ncell[d];
+    gd = gd < 0 ? gd + nd : (gd >= nd ? gd - nd : gd);
+    put(G, d, gd);
+    const I3 lc{(G.x >> 1) - q.ijk[0] * qn, (G.y >> 1) - q.ijk[1] * qn, D == 3 ? (G.z >> 1) - q.ijk[2] * qn : 0};
+    const T B = X[q.cell_off + cidx<D>(qn, lc.x, lc.y, lc.z)];
+    if (coef) return B;
+    T Bp = B;
+#pragma unroll
+    for (int e = 0; e < D; e++) {
+        if (e == d) continue;
+        const T sg = (get(G, e) & 1) ? (T)1 : (T)-1;
+        const int ox = e == 0, oy = e == 1, oz = e == 2;
+        const T Av = load<T, D>(X, XG, q, lc.x - ox, lc.y - oy, lc.z - oz);
+        const T Cv = load<T, D>(X, XG, q, lc.x + ox, lc.y + oy, lc.z + oz);
+        Bp += sg * (Cv - Av) / (T)8;
+    }
+    return (T)0.5 * Bp + (T)0.75 * c - (T)0.25 * dv;
+}
+
 // ------------------------------------------------------------- ghosts ----
 // Face ghosts of every block in [first, first + gridDim.x) (Sec. 2.6):
 // same-level or periodic copy; physical boundary (Dirichlet 2a - x_i,
@@ -102,105 +188,427 @@ __device__ __forceinline__ void cell_of(int c, int n, int D, int &i, int &j, int
 template <class T, int D>
 __global__ void __launch_bounds__(kMaxThreads) k_ghost(KParams P, int first, T *__restrict__ X,
                                                        T *__restrict__ XG, int mode) {
-    const BlockDesc b = P.B[first + blockIdx.x];
+    __shared__ BlockDesc sb;
+    stage_desc(P, first + blockIdx.x, sb);
+    const BlockDesc &b = sb;
     const LevelDesc &L = P.L[b.lev];
     const int n = b.n, F = face_of<D>(n);
     for (int t = threadIdx.x; t < 2 * D * F; t += blockDim.x) {
         const int face = t / F, u = t - face * F, d = face >> 1, s = face & 1;
-        int ii[3] = {0, 0, 0};
-        {
-            int t1 = u % n, t2 = u / n, a = 0;
-            for (int e = 0; e < D; e++)
-                if (e != d) ii[e] = (a++ == 0) ? t1 : t2;
-        }
-        ii[d] = s ? n - 1 : 0;
+        const I3 ii = face_cell<D>(n, face, u, false);
         const int nb = b.nbr[face];
         T val;
         if (nb >= 0) {
             const BlockDesc &q = P.B[nb];
-            int jj[3] = {ii[0], ii[1], ii[2]};
-            jj[d] = s ? 0 : n - 1;
-            val = X[q.cell_off + cidx<D>(n, jj[0], jj[1], jj[2])];
+            I3 jj = ii;
+            put(jj, d, s ? 0 : n - 1);
+            val = X[q.cell_off + cidx<D>(n, jj.x, jj.y, jj.z)];
         } else if (nb == -1) {
-            const T xi = X[b.cell_off + cidx<D>(n, ii[0], ii[1], ii[2])];
-            if (mode == 1) {
-                val = xi;
-            } else {
-                double a = 0.0;
-                if (!P.homog) {
-                    if (L.bc_off[face] >= 0) {
-                        int G[3], t1 = -1, t2 = -1;
-                        for (int e = 0; e < 3; e++) G[e] = b.ijk[e] * n + ii[e];
-                        for (int e = 0; e < D; e++)
-                            if (e != d) { if (t1 < 0) t1 = e; else t2 = e; }
-                        long long idx = G[t1];
-                        if (t2 >= 0) idx += (long long)L.ncell[t1] * G[t2];
-                        a = P.bcplanes[L.bc_off[face] + idx];
-                    } else {
-                        a = P.bcv[face];
-                    }
-                }
-                switch (P.bct[face]) {
-                case MG_BC_DIRICHLET: val = (T)(2.0 * a) - xi; break;
-                case MG_BC_NEUMANN: val = s ? xi + (T)(L.h[d] * a) : xi - (T)(L.h[d] * a); break;
-                default: val = xi; break;
-                }
-            }
+            const T xi = X[b.cell_off + cidx<D>(n, ii.x, ii.y, ii.z)];
+            val = mode == 1 ? xi : phys_ghost<T>(P, L, face, xi, bc_value(P, L, b, D, face, ii));
         } else {
-            const BlockDesc &q = P.B[-2 - nb];
-            const int qn = q.n;
-            int G[3];
-            for (int e = 0; e < 3; e++) G[e] = b.ijk[e] * n + ii[e];
-            G[d] = b.ijk[d] * n + (s ? n : -1);
-            if (G[d] < 0) G[d] += L.ncell[d];
-            if (G[d] >= L.ncell[d]) G[d] -= L.ncell[d];
-            int lc[3] = {0, 0, 0};
-            for (int e = 0; e < D; e++) lc[e] = (G[e] >> 1) - q.ijk[e] * qn;
-            const T B = X[q.cell_off + cidx<D>(qn, lc[0], lc[1], lc[2])];
-            if (mode == 1) {
-                val = B;
-            } else {
-                T Bp = B;
-                for (int e = 0; e < D; e++) {
-                    if (e == d) continue;
-                    const T sg = (G[e] & 1) ? (T)1 : (T)-1;
-                    int la[3] = {lc[0], lc[1], lc[2]}, lb[3] = {lc[0], lc[1], lc[2]};
-                    la[e] -= 1;
-                    lb[e] += 1;
-                    const T Av = load<T, D>(X, XG, q, la[0], la[1], la[2]);
-                    const T Cv = load<T, D>(X, XG, q, lb[0], lb[1], lb[2]);
-                    Bp += sg * (Cv - Av) / (T)8;
-                }
-                int dd[3] = {ii[0], ii[1], ii[2]};
-                dd[d] = s ? n - 2 : 1;
-                const T c = X[b.cell_off + cidx<D>(n, ii[0], ii[1], ii[2])];
-                const T dv = X[b.cell_off + cidx<D>(n, dd[0], dd[1], dd[2])];
-                val = (T)0.5 * Bp + (T)0.75 * c - (T)0.25 * dv;
-            }
+            I3 dd = ii;
+            put(dd, d, s ? n - 2 : 1);
+            const T c = X[b.cell_off + cidx<D>(n, ii.x, ii.y, ii.z)];
+            const T dv = X[b.cell_off + cidx<D>(n, dd.x, dd.y, dd.z)];
+            val = cf_ghost<T, D>(P, L, b, face, ii, c, dv, X, XG, nb, mode == 1);
         }
         XG[b.ghost_off + face * F + u] = val;
     }
 }
 
 // --------------------------------------------------------- smoother -----
-// One colour of red-black Gauss-Seidel (Sec. 2.2): cells with
-// (I+J+K) % 2 == colour (global level indices) take the local solution
-// (sum w x_nb - f) / (sum w + lambda).  Cells of the other colour and all
-// ghosts are only read, so the update is order-independent.
-template <class T, int D>
-__global__ void __launch_bounds__(kMaxThreads) k_smooth(KParams P, int first, Fields<T> F, int colour) {
-    const BlockDesc b = P.B[first + blockIdx.x];
-    const LevelDesc &L = P.L[b.lev];
-    const int n = b.n, C = cells_of<D>(n);
-    const int par0 = (b.ijk[0] + b.ijk[1] + b.ijk[2]) * n;
-    for (int c = threadIdx.x; c < C; c += blockDim.x) {
-        int i, j, k;
-        cell_of(c, n, D, i, j, k);
-        if (((par0 + i + j + k) & 1) != colour) continue;
-        T lap, num, den, xc;
-        stencil<T, T, D>(P, L, b, F.X, F.XG, F.E, F.EG, i, j, k, lap, num, den, xc);
-        F.X[b.cell_off + c] = (num - F.F[b.cell_off + c]) / (den + (T)P.helm);
+// Fused red-black half-sweep: one CTA per block.
+//  1. the block and its face ghosts (and eps) are staged in shared memory,
+//     padded to (n+2)^D;
+//  2. every cell of the colour (one thread per colour cell) takes the local
+//     solution from its neighbours in shared memory; the block is written
+//     back whole with coalesced stores;
+//  3. the ghosts that depend on the updated cells are pushed: a same-level
+//     neighbour's ghost slot opposite an updated boundary cell, the block's
+//     own physical ghosts beside updated cells, and all its refinement-face
+//     ghosts (c or d changed).
+// The ghost state after the launch equals a full ghost fill of the level
+// after the colour (reading R1 of the oracle).  A CTA reads only ghost
+// slots beside cells of the updated colour, i.e. slots fed by the other
+// colour of its neighbours, so reads and pushes of concurrent CTAs never
+// touch the same slot.
+template <class T> struct Vec16;
+template <> struct Vec16<float> { using type = float4; };
+template <> struct Vec16<double> { using type = double2; };
+
+// 16-byte vector <-> VW consecutive shared-memory elements
+template <class T> __device__ __forceinline__ void vscatter(T *dst, const typename Vec16<T>::type &v) {
+    if constexpr (sizeof(T) == 4) { dst[0] = v.x; dst[1] = v.y; dst[2] = v.z; dst[3] = v.w; }
+    else { dst[0] = v.x; dst[1] = v.y; }
+}
+template <class T> __device__ __forceinline__ typename Vec16<T>::type vgather(const T *src) {
+    if constexpr (sizeof(T) == 4) return make_float4(src[0], src[1], src[2], src[3]);
+    else return make_double2(src[0], src[1]);
+}
+
+template <class T, int D, int NT>
+__global__ void __launch_bounds__(kMaxThreads) k_sweep(KParams P, int first, Fields<T> F, int colour) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ BlockDesc sb;
+    __shared__ long long s_ngo[6];
+    const int tid = threadIdx.x, nth = blockDim.x;
+    stage_desc(P, first + blockIdx.x, sb);
+    const BlockDesc &b = sb;
+    if (tid < 2 * D) {
+        const int nb = b.nbr[tid];
+        s_ngo[tid] = nb >= 0 ? P.B[nb].ghost_off : -1;
     }
+    const LevelDesc &L = P.L[b.lev];
+    const int n = NT ? NT : b.n;
+    const int C = cells_of<D>(n), Fc = face_of<D>(n), S = n + 2;
+    const int PAD = D == 2 ? S * S : S * S * S;
+    T *sx = reinterpret_cast<T *>(smem_raw);
+    T *se = sx + PAD;
+    const bool var = F.E != nullptr;
+    const int sy = S, sz = D == 3 ? S * S : 0;
+    auto sid = [&](int i, int j, int k) { return (D == 3 ? (k + 1) * sz : 0) + (j + 1) * sy + (i + 1); };
+    const int par0 = (b.ijk[0] + b.ijk[1] + b.ijk[2]) * n;
+    const int ncol = (n & 1) ? C : C / 2;
+    constexpr int VW = 16 / sizeof(T);
+    constexpr int CPT = NT ? ((cells_of<D>(NT) / 2 + kMaxThreads - 1) / kMaxThreads) : 1;
+
+    // 1. stage block + ghosts (+ eps), prefetch f of this thread's colour cells
+    if (NT) {
+        using V = typename Vec16<T>::type;
+        const V *src = reinterpret_cast<const V *>(F.X + b.cell_off);
+        for (int v = tid; v < C / VW; v += nth) {
+            const int c = v * VW, i = c % n, j = (c / n) % n, k = D == 3 ? c / (n * n) : 0;
+            vscatter<T>(sx + sid(i, j, k), src[v]);
+        }
+        const V *gsrc = reinterpret_cast<const V *>(F.XG + b.ghost_off);
+        for (int v = tid; v < 2 * D * Fc / VW; v += nth) {
+            const V val = gsrc[v];
+            const int t0 = v * VW, face = t0 / Fc, u0 = t0 - face * Fc;
+            const int step = (face >> 1) == 0 ? sy : 1;  // consecutive u: next t1 cell
+            const I3 q = face_cell<D>(n, face, u0, true);
+            T *dst = sx + sid(q.x, q.y, q.z);
+            if constexpr (sizeof(T) == 4) { dst[0] = val.x; dst[step] = val.y; dst[2 * step] = val.z; dst[3 * step] = val.w; }
+            else { dst[0] = val.x; dst[step] = val.y; }
+        }
+    } else {
+        for (int c = tid; c < C; c += nth) {
+            const int i = c % n, j = (c / n) % n, k = D == 3 ? c / (n * n) : 0;
+            sx[sid(i, j, k)] = F.X[b.cell_off + c];
+        }
+        for (int t = tid; t < 2 * D * Fc; t += nth) {
+            const I3 q = face_cell<D>(n, t / Fc, t % Fc, true);
+            sx[sid(q.x, q.y, q.z)] = F.XG[b.ghost_off + t];
+        }
+    }
+    if (var) {
+        for (int c = tid; c < C; c += nth) {
+            const int i = c % n, j = (c / n) % n, k = D == 3 ? c / (n * n) : 0;
+            se[sid(i, j, k)] = F.E[b.cell_off + c];
+        }
+        for (int t = tid; t < 2 * D * Fc; t += nth) {
+            const I3 q = face_cell<D>(n, t / Fc, t % Fc, true);
+            se[sid(q.x, q.y, q.z)] = F.EG[b.ghost_off + t];
+        }
+    }
+    // colour cell qi -> (i, j, k)
+    auto colour_cell = [&](int qi, int &i, int &j, int &k) -> bool {
+        if (n & 1) {
+            i = qi % n; j = (qi / n) % n; k = D == 3 ? qi / (n * n) : 0;
+            return ((par0 + i + j + k) & 1) == colour;
+        }
+        const int h = n >> 1, rr = qi / h, m = qi - rr * h;
+        j = rr % n;
+        k = D == 3 ? rr / n : 0;
+        i = 2 * m + ((colour + par0 + j + k) & 1);
+        return true;
+    };
+    int ci[CPT], cj[CPT], ck[CPT];
+    T fpre[CPT];
+    if (NT) {
+#pragma unroll
+        for (int r = 0; r < CPT; r++) {
+            const int qi = tid + r * nth;
+            ci[r] = -1;
+            if (qi >= ncol) continue;
+            int i, j, k;
+            if (!colour_cell(qi, i, j, k)) continue;
+            ci[r] = i; cj[r] = j; ck[r] = k;
+            fpre[r] = F.F[b.cell_off + cidx<D>(n, i, j, k)];
+        }
+    }
+    __syncthreads();
+
+    // 2. red-black update of this colour (Sec. 2.2)
+    const bool cyl = P.geom == MG_CYL;
+    const T helm = (T)P.helm;
+    const T w0 = (T)L.inv_h2[0], w1 = (T)L.inv_h2[1], w2 = (T)L.inv_h2[2];
+    const T inv_den = (T)1 / ((T)2 * (w0 + w1 + (D == 3 ? w2 : (T)0)) + helm);
+    auto update = [&](int i, int j, int k, T fc) {
+        const int c0 = sid(i, j, k);
+        T xnew;
+        if (!var && !cyl) {
+            T num = w0 * (sx[c0 - 1] + sx[c0 + 1]) + w1 * (sx[c0 - sy] + sx[c0 + sy]);
+            if (D == 3) num += w2 * (sx[c0 - sz] + sx[c0 + sz]);
+            xnew = (num - fc) * inv_den;
+        } else {
+            const T ec = var ? se[c0] : (T)1;
+            T num = 0, den = 0, ri = 0;
+            if (cyl) ri = (T)(P.lo[0] + (b.ijk[0] * n + i + 0.5) * L.h[0]);
+#pragma unroll
+            for (int d = 0; d < D; d++)
+#pragma unroll
+                for (int s = 0; s < 2; s++) {
+                    const int o = (s ? 1 : -1) * (d == 0 ? 1 : d == 1 ? sy : sz);
+                    T w = (T)L.inv_h2[d];
+                    if (var) {
+                        const T en = se[c0 + o];
+                        w *= (T)2 * ec * en / (ec + en);
+                    }
+                    if (cyl && d == 0) w *= (T)(P.lo[0] + (b.ijk[0] * n + i + s) * L.h[0]) / ri;
+                    num += w * sx[c0 + o];
+                    den += w;
+                }
+            xnew = (num - fc) / (den + helm);
+        }
+        sx[c0] = xnew;
+    };
+    if (NT) {
+#pragma unroll
+        for (int r = 0; r < CPT; r++)
+            if (ci[r] >= 0) update(ci[r], cj[r], ck[r], fpre[r]);
+    } else {
+        for (int qi = tid; qi < ncol; qi += nth) {
+            int i, j, k;
+            if (colour_cell(qi, i, j, k)) update(i, j, k, F.F[b.cell_off + cidx<D>(n, i, j, k)]);
+        }
+    }
+    __syncthreads();
+
+    // 3. write the block back, push the ghosts that depend on updated cells
+    if (NT) {
+        using V = typename Vec16<T>::type;
+        V *dst = reinterpret_cast<V *>(F.X + b.cell_off);
+        for (int v = tid; v < C / VW; v += nth) {
+            const int c = v * VW, i = c % n, j = (c / n) % n, k = D == 3 ? c / (n * n) : 0;
+            dst[v] = vgather<T>(sx + sid(i, j, k));
+        }
+    } else {
+        for (int c = tid; c < C; c += nth) {
+            const int i = c % n, j = (c / n) % n, k = D == 3 ? c / (n * n) : 0;
+            F.X[b.cell_off + c] = sx[sid(i, j, k)];
+        }
+    }
+    for (int t = tid; t < 2 * D * Fc; t += nth) {
+        const int face = t / Fc, u = t - face * Fc, d = face >> 1, s = face & 1;
+        const I3 ii = face_cell<D>(n, face, u, false);
+        const bool updated = ((par0 + ii.x + ii.y + ii.z) & 1) == colour;
+        const int nb = b.nbr[face];
+        const T xi = sx[sid(ii.x, ii.y, ii.z)];
+        if (nb >= 0) {
+            if (updated) F.XG[s_ngo[face] + (face ^ 1) * Fc + u] = xi;
+        } else if (nb == -1) {
+            if (updated) F.XG[b.ghost_off + t] = phys_ghost<T>(P, L, face, xi, bc_value(P, L, b, D, face, ii));
+        } else {
+            I3 dd = ii;
+            put(dd, d, s ? n - 2 : 1);
+            F.XG[b.ghost_off + t] = cf_ghost<T, D>(P, L, b, face, ii, xi, sx[sid(dd.x, dd.y, dd.z)], F.X, F.XG, nb,
+                                                   false);
+        }
+    }
+}
+
+// ------------------------------------------------ TMA bulk-copy sweep ---
+// Persistent variant of the fused sweep for 8- and 16-cell blocks.  Each
+// CTA walks blocks g = blockIdx.x, + gridDim.x, ...; the interior, the face
+// ghosts, f (and eps) of the next block arrive by cp.async.bulk into the
+// other half of a double buffer while the current block is updated; the
+// updated interior leaves by a bulk store.  Every mbarrier wait is bounded:
+// on expiry the kernel raises P.status and the CTA stops.
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t *bar, int count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_s2g(void *dst, const void *src, uint32_t bytes) {
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(smem_u32(src)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait0() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+
+static constexpr uint32_t kWaitLimit = 1u << 20;
+
+template <class T, int D, int NT>
+__global__ void __launch_bounds__(kMaxThreads, 5) k_sweep_tma(KParams P, int first, int nblocks, Fields<T> F,
+                                                           int colour) {
+    constexpr int n = NT, C = cells_of<D>(NT), FC = face_of<D>(NT), GH = 2 * D * FC;
+    constexpr int NCOL = C / 2, CPT = (NCOL + kMaxThreads - 1) / kMaxThreads;
+    constexpr int DESC = (int)(sizeof(BlockDesc) / sizeof(T));
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t bars[2];
+    __shared__ __align__(16) LevelDesc sL;
+    __shared__ int s_abort;
+    const bool var = F.E != nullptr;
+    // per stage: descriptor, x[C], ghosts[GH], f[C] (, eps[C], eps ghosts[GH])
+    const int stage_elems = DESC + 2 * C + GH + (var ? C + GH : 0);
+    T *stage0 = reinterpret_cast<T *>(smem_raw);
+    const int tid = threadIdx.x, nth = blockDim.x;
+    const uint32_t tx_bytes = (uint32_t)(sizeof(T) * stage_elems);
+    if (tid == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        fence_mbar_init();
+        s_abort = 0;
+    }
+    if (tid < (int)(sizeof(LevelDesc) / 4))
+        reinterpret_cast<int *>(&sL)[tid] = reinterpret_cast<const int *>(P.L + P.B[first].lev)[tid];
+    __syncthreads();
+    auto issue = [&](int it, int g) {  // thread 0 only
+        T *st = stage0 + (it & 1) * stage_elems;
+        const long long co = P.B[g].cell_off, go = P.B[g].ghost_off;
+        uint64_t *bar = &bars[it & 1];
+        fence_async_smem();
+        mbar_expect_tx(bar, tx_bytes);
+        bulk_g2s(st, P.B + g, sizeof(BlockDesc), bar);
+        bulk_g2s(st + DESC, F.X + co, sizeof(T) * C, bar);
+        bulk_g2s(st + DESC + C, F.XG + go, sizeof(T) * GH, bar);
+        bulk_g2s(st + DESC + C + GH, F.F + co, sizeof(T) * C, bar);
+        if (var) {
+            bulk_g2s(st + DESC + 2 * C + GH, F.E + co, sizeof(T) * C, bar);
+            bulk_g2s(st + DESC + 3 * C + GH, F.EG + go, sizeof(T) * GH, bar);
+        }
+    };
+    int g = blockIdx.x;
+    if (tid == 0 && g < nblocks) issue(0, first + g);
+    const LevelDesc &L = sL;
+    const bool cyl = P.geom == MG_CYL;
+    const T helm = (T)P.helm;
+    const T w0 = (T)L.inv_h2[0], w1 = (T)L.inv_h2[1], w2 = (T)L.inv_h2[2];
+    const T inv_den = (T)1 / ((T)2 * (w0 + w1 + (D == 3 ? w2 : (T)0)) + helm);
+    for (int it = 0; g < nblocks; it++, g += gridDim.x) {
+        {
+            uint32_t tries = 0;
+            while (!mbar_try_wait(&bars[it & 1], (it >> 1) & 1))
+                if (++tries > kWaitLimit) {
+                    atomicExch(P.status, 1);
+                    s_abort = 1;
+                    break;
+                }
+        }
+        __syncthreads();
+        if (s_abort) break;
+        // every thread is past the previous block: its stage may be refilled
+        // once its bulk store has read it
+        if (tid == 0 && g + (int)gridDim.x < nblocks) {
+            bulk_wait_read0();
+            issue(it + 1, first + g + gridDim.x);
+        }
+        T *st = stage0 + (it & 1) * stage_elems;
+        const BlockDesc &b = *reinterpret_cast<const BlockDesc *>(st);
+        T *xs = st + DESC, *gs = xs + C, *fs = gs + GH, *es = fs + C, *egs = es + C;
+        const int bi = b.ijk[0], bj = b.ijk[1], bk = b.ijk[2];
+        const int par0 = (bi + bj + bk) * n;
+        // neighbour (d, side) of cell (i,j,k): interior or the face ghost
+        auto nbv = [&](const T *xi, const T *gi, int i, int j, int k, int d, int s) -> T {
+            const int o = s ? 1 : -1;
+            if (d == 0) {
+                const int ii = i + o;
+                if (ii < 0 || ii >= n) return gi[(s ? 1 : 0) * FC + (D == 2 ? j : j + n * k)];
+                return xi[cidx<D>(n, ii, j, k)];
+            }
+            if (d == 1) {
+                const int jj = j + o;
+                if (jj < 0 || jj >= n) return gi[(s ? 3 : 2) * FC + (D == 2 ? i : i + n * k)];
+                return xi[cidx<D>(n, i, jj, k)];
+            }
+            const int kk = k + o;
+            if (kk < 0 || kk >= n) return gi[(s ? 5 : 4) * FC + i + n * j];
+            return xi[cidx<D>(n, i, j, kk)];
+        };
+#pragma unroll
+        for (int r = 0; r < CPT; r++) {
+            const int qi = tid + r * nth;
+            if (qi >= NCOL) continue;
+            const int h = n >> 1, rr = qi / h, m = qi - rr * h;
+            const int j = rr % n, k = D == 3 ? rr / n : 0;
+            const int i = 2 * m + ((colour + par0 + j + k) & 1);
+            const int c = cidx<D>(n, i, j, k);
+            T xnew;
+            if (!var && !cyl) {
+                T num = w0 * (nbv(xs, gs, i, j, k, 0, 0) + nbv(xs, gs, i, j, k, 0, 1)) +
+                        w1 * (nbv(xs, gs, i, j, k, 1, 0) + nbv(xs, gs, i, j, k, 1, 1));
+                if (D == 3) num += w2 * (nbv(xs, gs, i, j, k, 2, 0) + nbv(xs, gs, i, j, k, 2, 1));
+                xnew = (num - fs[c]) * inv_den;
+            } else {
+                const T ec = var ? es[c] : (T)1;
+                T num = 0, den = 0, ri = 0;
+                if (cyl) ri = (T)(P.lo[0] + (bi * n + i + 0.5) * L.h[0]);
+#pragma unroll
+                for (int d = 0; d < D; d++)
+#pragma unroll
+                    for (int s = 0; s < 2; s++) {
+                        T w = (T)L.inv_h2[d];
+                        if (var) {
+                            const T en = nbv(es, egs, i, j, k, d, s);
+                            w *= (T)2 * ec * en / (ec + en);
+                        }
+                        if (cyl && d == 0) w *= (T)(P.lo[0] + (bi * n + i + s) * L.h[0]) / ri;
+                        num += w * nbv(xs, gs, i, j, k, d, s);
+                        den += w;
+                    }
+                xnew = (num - fs[c]) / (den + helm);
+            }
+            xs[c] = xnew;  // cells of the other colour are not read by this colour
+        }
+        fence_async_smem();
+        __syncthreads();
+        if (tid == 0) {
+            bulk_s2g(F.X + b.cell_off, xs, sizeof(T) * C);
+            bulk_commit();
+        }
+        // ghost pushes beside updated cells (see k_sweep)
+        for (int t = tid; t < GH; t += nth) {
+            const int face = t / FC, u = t - face * FC, d = face >> 1, s = face & 1;
+            const I3 ii = face_cell<D>(n, face, u, false);
+            const bool updated = ((par0 + ii.x + ii.y + ii.z) & 1) == colour;
+            const int nb = b.nbr[face];
+            if (nb >= 0) {
+                if (updated) F.XG[b.push[face] + u] = xs[cidx<D>(n, ii.x, ii.y, ii.z)];
+            } else if (nb == -1) {
+                if (updated)
+                    F.XG[b.ghost_off + t] = phys_ghost<T>(P, L, face, xs[cidx<D>(n, ii.x, ii.y, ii.z)],
+                                                          bc_value(P, L, b, D, face, ii));
+            } else {
+                I3 dd = ii;
+                put(dd, d, s ? n - 2 : 1);
+                F.XG[b.ghost_off + t] = cf_ghost<T, D>(P, L, b, face, ii, xs[cidx<D>(n, ii.x, ii.y, ii.z)],
+                                                       xs[cidx<D>(n, dd.x, dd.y, dd.z)], F.X, F.XG, nb, false);
+            }
+        }
+    }
+    if (tid == 0) bulk_wait0();
 }
 
 // ------------------------------------------------------- transfers ------
@@ -213,7 +621,9 @@ __global__ void __launch_bounds__(kMaxThreads) k_restrict(KParams P, int first, 
                                                           const T *__restrict__ XG, const T *__restrict__ Fr,
                                                           const T *__restrict__ E, const T *__restrict__ EG,
                                                           T *__restrict__ Fdst, int with_res) {
-    const BlockDesc b = P.B[first + blockIdx.x];
+    __shared__ BlockDesc sb;
+    stage_desc(P, first + blockIdx.x, sb);
+    const BlockDesc &b = sb;
     const LevelDesc &L = P.L[b.lev];
     const BlockDesc &p = P.B[b.parent];
     const int n = b.n, m = n / 2, M = cells_of<D>(m);
@@ -241,7 +651,9 @@ __global__ void __launch_bounds__(kMaxThreads) k_restrict(KParams P, int first, 
 // Covered cells: f^H = R(r^h) + L^H v^H (eq. for the coarse right-hand side).
 template <class T, int D>
 __global__ void __launch_bounds__(kMaxThreads) k_fas_rhs(KParams P, int first, Fields<T> F) {
-    const BlockDesc b = P.B[first + blockIdx.x];
+    __shared__ BlockDesc sb;
+    stage_desc(P, first + blockIdx.x, sb);
+    const BlockDesc &b = sb;
     const LevelDesc &L = P.L[b.lev];
     const int n = b.n, C = cells_of<D>(n);
     for (int c = threadIdx.x; c < C; c += blockDim.x) {
@@ -259,7 +671,9 @@ __global__ void __launch_bounds__(kMaxThreads) k_fas_rhs(KParams P, int first, F
 // ghosts included).
 template <class T, int D>
 __global__ void __launch_bounds__(kMaxThreads) k_prolong(KParams P, int first, Fields<T> F) {
-    const BlockDesc b = P.B[first + blockIdx.x];
+    __shared__ BlockDesc sb;
+    stage_desc(P, first + blockIdx.x, sb);
+    const BlockDesc &b = sb;
     const BlockDesc &p = P.B[b.parent];
     const int n = b.n, C = cells_of<D>(n);
     for (int c = threadIdx.x; c < C; c += blockDim.x) {
@@ -289,7 +703,9 @@ __global__ void __launch_bounds__(kMaxThreads) k_resnorm(KParams P, int first, F
                                                          double *__restrict__ partials,
                                                          double *__restrict__ rleaf, long long leaf_base,
                                                          long long cell_base, float *__restrict__ f32) {
-    const BlockDesc b = P.B[first + blockIdx.x];
+    __shared__ BlockDesc sb;
+    stage_desc(P, first + blockIdx.x, sb);
+    const BlockDesc &b = sb;
     const LevelDesc &L = P.L[b.lev];
     const int n = b.n, C = cells_of<D>(n);
     double s2 = 0, sv = 0, mx = 0;
@@ -321,6 +737,156 @@ __global__ void __launch_bounds__(kMaxThreads) k_resnorm(KParams P, int first, F
     if (threadIdx.x == 0) {
         double a = 0, bb = 0, m = 0;
         for (int e = 0; e < nw; e++) { a += sh[0][e]; bb += sh[1][e]; m = fmax(m, sh[2][e]); }
+        partials[3 * blockIdx.x] = a;
+        partials[3 * blockIdx.x + 1] = bb;
+        partials[3 * blockIdx.x + 2] = m;
+    }
+}
+
+// Composite residual on the leaf blocks of one level, TMA-staged like the
+// sweep: x, the face ghosts and f (and eps) of the next block arrive by
+// cp.async.bulk while the current block is evaluated.  r = f - (L x - lambda x)
+// is formed in FP64 with the difference form sum_d w_d ((x_- - x_c) +
+// (x_+ - x_c)) (rounding error ~ eps |grad x| h rather than eps |x|).  Writes per-CTA partials (sum V r^2, sum V,
+// max |r|) and optionally r (leaf order) and (float) r into FP32 cells.
+template <int D, int NT>
+__global__ void __launch_bounds__(kMaxThreads, 4) k_resid_tma(KParams P, int first, int nblocks, Fields<double> F,
+                                                              double *__restrict__ partials,
+                                                              double *__restrict__ rleaf, long long leaf_base,
+                                                              float *__restrict__ f32) {
+    using T = double;
+    constexpr int n = NT, C = cells_of<D>(NT), FC = face_of<D>(NT), GH = 2 * D * FC;
+    constexpr int DESC = (int)(sizeof(BlockDesc) / sizeof(T));
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t bars[2];
+    __shared__ __align__(16) LevelDesc sL;
+    __shared__ int s_abort;
+    __shared__ double sred[3][kMaxThreads / 32];
+    const bool var = F.E != nullptr;
+    const int stage_elems = DESC + 2 * C + GH + (var ? C + GH : 0);
+    T *stage0 = reinterpret_cast<T *>(smem_raw);
+    const int tid = threadIdx.x, nth = blockDim.x;
+    const uint32_t tx_bytes = (uint32_t)(sizeof(T) * stage_elems);
+    if (tid == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        fence_mbar_init();
+        s_abort = 0;
+    }
+    if (tid < (int)(sizeof(LevelDesc) / 4))
+        reinterpret_cast<int *>(&sL)[tid] = reinterpret_cast<const int *>(P.L + P.B[first].lev)[tid];
+    __syncthreads();
+    auto issue = [&](int it, int g) {
+        T *st = stage0 + (it & 1) * stage_elems;
+        const long long co = P.B[g].cell_off, go = P.B[g].ghost_off;
+        uint64_t *bar = &bars[it & 1];
+        fence_async_smem();
+        mbar_expect_tx(bar, tx_bytes);
+        bulk_g2s(st, P.B + g, sizeof(BlockDesc), bar);
+        bulk_g2s(st + DESC, F.X + co, sizeof(T) * C, bar);
+        bulk_g2s(st + DESC + C, F.XG + go, sizeof(T) * GH, bar);
+        bulk_g2s(st + DESC + C + GH, F.F + co, sizeof(T) * C, bar);
+        if (var) {
+            bulk_g2s(st + DESC + 2 * C + GH, F.E + co, sizeof(T) * C, bar);
+            bulk_g2s(st + DESC + 3 * C + GH, F.EG + go, sizeof(T) * GH, bar);
+        }
+    };
+    int g = blockIdx.x;
+    if (tid == 0 && g < nblocks) issue(0, first + g);
+    const LevelDesc &L = sL;
+    const bool cyl = P.geom == MG_CYL;
+    const double w0 = L.inv_h2[0], w1 = L.inv_h2[1], w2 = L.inv_h2[2];
+    double vol = L.h[0] * L.h[1] * (D == 3 ? L.h[2] : 1.0);
+    double s2 = 0, sv = 0;
+    double mx = 0.0;
+    for (int it = 0; g < nblocks; it++, g += gridDim.x) {
+        {
+            uint32_t tries = 0;
+            while (!mbar_try_wait(&bars[it & 1], (it >> 1) & 1))
+                if (++tries > kWaitLimit) {
+                    atomicExch(P.status, 1);
+                    s_abort = 1;
+                    break;
+                }
+        }
+        __syncthreads();
+        if (s_abort) break;
+        if (tid == 0 && g + (int)gridDim.x < nblocks) issue(it + 1, first + g + gridDim.x);
+        const T *st = stage0 + (it & 1) * stage_elems;
+        const BlockDesc &b = *reinterpret_cast<const BlockDesc *>(st);
+        const T *xs = st + DESC, *gs = xs + C, *fs = gs + GH, *es = fs + C, *egs = es + C;
+        auto nbv = [&](const T *xi, const T *gi, int i, int j, int k, int d, int s) -> T {
+            const int o = s ? 1 : -1;
+            if (d == 0) {
+                const int ii = i + o;
+                if (ii < 0 || ii >= n) return gi[(s ? 1 : 0) * FC + (D == 2 ? j : j + n * k)];
+                return xi[cidx<D>(n, ii, j, k)];
+            }
+            if (d == 1) {
+                const int jj = j + o;
+                if (jj < 0 || jj >= n) return gi[(s ? 3 : 2) * FC + (D == 2 ? i : i + n * k)];
+                return xi[cidx<D>(n, i, jj, k)];
+            }
+            const int kk = k + o;
+            if (kk < 0 || kk >= n) return gi[(s ? 5 : 4) * FC + i + n * j];
+            return xi[cidx<D>(n, i, j, kk)];
+        };
+        double bs2 = 0;
+        for (int c = tid; c < C; c += nth) {
+            const int i = c % n, j = (c / n) % n, k = D == 3 ? c / (n * n) : 0;
+            const double xc = xs[c];
+            double lap;
+            if (!var && !cyl) {
+                lap = w0 * ((nbv(xs, gs, i, j, k, 0, 0) - xc) + (nbv(xs, gs, i, j, k, 0, 1) - xc));
+                lap = fma(w1, (nbv(xs, gs, i, j, k, 1, 0) - xc) + (nbv(xs, gs, i, j, k, 1, 1) - xc), lap);
+                if (D == 3) lap = fma(w2, (nbv(xs, gs, i, j, k, 2, 0) - xc) + (nbv(xs, gs, i, j, k, 2, 1) - xc), lap);
+            } else {
+                const double ec = var ? es[c] : 1.0;
+                double ri = 0;
+                if (cyl) ri = P.lo[0] + (b.ijk[0] * n + i + 0.5) * L.h[0];
+                lap = 0;
+#pragma unroll
+                for (int d = 0; d < D; d++)
+#pragma unroll
+                    for (int s = 0; s < 2; s++) {
+                        double w = L.inv_h2[d];
+                        if (var) {
+                            const double en = nbv(es, egs, i, j, k, d, s);
+                            w *= 2.0 * ec * en / (ec + en);
+                        }
+                        if (cyl && d == 0) w *= (P.lo[0] + (b.ijk[0] * n + i + s) * L.h[0]) / ri;
+                        lap += w * (nbv(xs, gs, i, j, k, d, s) - xc);
+                    }
+            }
+            const double r = fs[c] - (lap - P.helm * xc);
+            if (cyl) {
+                const double V = 2.0 * M_PI * (P.lo[0] + (b.ijk[0] * n + i + 0.5) * L.h[0]) * L.h[0] * L.h[1];
+                s2 = fma(V * r, r, s2);
+                sv += V;
+            } else {
+                bs2 = fma(r, r, bs2);
+            }
+            mx = fmax(mx, fabs(r));
+            if (f32) f32[b.cell_off + c] = (float)r;
+            if (rleaf) rleaf[leaf_base + (long long)g * C + c] = r;
+        }
+        if (!cyl) {
+            s2 = fma(vol, bs2, s2);
+            if (tid == 0) sv += vol * C;
+        }
+    }
+    if (tid == 0) bulk_wait0();
+    for (int o = 16; o > 0; o >>= 1) {
+        s2 += __shfl_down_sync(0xffffffffu, s2, o);
+        sv += __shfl_down_sync(0xffffffffu, sv, o);
+        mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, o));
+    }
+    const int w = tid >> 5, lane = tid & 31, nw = (nth + 31) >> 5;
+    if (lane == 0) { sred[0][w] = s2; sred[1][w] = sv; sred[2][w] = mx; }
+    __syncthreads();
+    if (tid == 0) {
+        double a = 0, bb = 0, m = 0;
+        for (int e = 0; e < nw; e++) { a += sred[0][e]; bb += sred[1][e]; m = fmax(m, sred[2][e]); }
         partials[3 * blockIdx.x] = a;
         partials[3 * blockIdx.x + 1] = bb;
         partials[3 * blockIdx.x + 2] = m;
@@ -408,7 +974,9 @@ __global__ void k_cast_f32(const double *__restrict__ a, float *__restrict__ b, 
 template <int D>
 __global__ void k_scale_r(KParams P, int first, const double *__restrict__ in, double *__restrict__ out,
                           long long leaf_base, int divide) {
-    const BlockDesc b = P.B[first + blockIdx.x];
+    __shared__ BlockDesc sb;
+    stage_desc(P, first + blockIdx.x, sb);
+    const BlockDesc &b = sb;
     const LevelDesc &L = P.L[b.lev];
     const int n = b.n, C = cells_of<D>(n);
     const long long base = leaf_base + (long long)blockIdx.x * C;
@@ -427,7 +995,9 @@ __global__ void __launch_bounds__(kMaxThreads) k_eps_grad(KParams P, int first, 
                                                           const double *__restrict__ Y, const double *__restrict__ YG,
                                                           const double *__restrict__ E, const double *__restrict__ EG,
                                                           double *__restrict__ out, long long leaf_base) {
-    const BlockDesc b = P.B[first + blockIdx.x];
+    __shared__ BlockDesc sb;
+    stage_desc(P, first + blockIdx.x, sb);
+    const BlockDesc &b = sb;
     const LevelDesc &L = P.L[b.lev];
     const int n = b.n, C = cells_of<D>(n);
     for (int c = threadIdx.x; c < C; c += blockDim.x) {
@@ -482,7 +1052,27 @@ KParams kparams(mg_tree *t, int homog) {
     P.geom = t->geom;
     P.var_eps = t->var_eps ? 1 : 0;
     P.homog = homog;
+    P.status = t->d_status;
     return P;
+}
+
+template <class K> static void set_smem(K kernel, size_t bytes) {
+    if (bytes > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+// resident CTAs per SM of a kernel at (threads, dynamic smem), queried once
+// per distinct request (host launch overhead stays off the hot path)
+template <class K> static int resident_ctas(K kernel, int threads, size_t smem) {
+    struct Entry { const void *k; int th; size_t sm; int per; };
+    static std::vector<Entry> cache;
+    for (const Entry &e : cache)
+        if (e.k == (const void *)kernel && e.th == threads && e.sm == smem) return e.per;
+    set_smem(kernel, smem);
+    int per = 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, threads, smem);
+    per = std::max(1, per);
+    cache.push_back({(const void *)kernel, threads, smem, per});
+    return per;
 }
 
 static int threads_for(int cells) {
@@ -497,15 +1087,33 @@ template <class T, int D> struct Launch {
         ++t->launches;
         k_ghost<T, D><<<L.nb, threads_for(2 * D * face_of<D>(L.n)), 0, t->stream>>>(P, L.first, X, XG, mode);
     }
-    static void smooth(mg_tree *t, const KParams &P, int l, Fields<T> &F, int sweeps) {
+    // one fused launch per colour (k_sweep), specialised for 8- and 16-cell blocks
+    static void sweep(mg_tree *t, const KParams &P, int l, Fields<T> &F, int colour) {
         const LevelHost &L = t->lev[l];
-        const int th = threads_for(cells_of<D>(L.n));
+        const int n = L.n, pad = D == 2 ? (n + 2) * (n + 2) : (n + 2) * (n + 2) * (n + 2);
+        const size_t sm = sizeof(T) * pad * (F.E ? 2 : 1);
+        const int th = threads_for((n & 1) ? cells_of<D>(n) : cells_of<D>(n) / 2);
+        ++t->launches;
+        const int C = cells_of<D>(n), GH = 2 * D * face_of<D>(n);
+        const size_t smt = 2 * (sizeof(BlockDesc) + sizeof(T) * (2 * C + GH + (F.E ? C + GH : 0)));
+        if ((n == 8 || n == 16) && smt <= 200 * 1024) {
+            const int thr = threads_for(C / 2);
+            auto kern = n == 8 ? k_sweep_tma<T, D, 8> : k_sweep_tma<T, D, 16>;
+            const int grid = std::min(L.nb, resident_ctas(kern, thr, smt) * t->nsm);
+            kern<<<grid, thr, smt, t->stream>>>(P, L.first, L.nb, F, colour);
+        } else if (n == 8) {
+            k_sweep<T, D, 8><<<L.nb, th, sm, t->stream>>>(P, L.first, F, colour);
+        } else if (n == 16) {
+            set_smem(k_sweep<T, D, 16>, sm);
+            k_sweep<T, D, 16><<<L.nb, th, sm, t->stream>>>(P, L.first, F, colour);
+        } else {
+            set_smem(k_sweep<T, D, 0>, sm);
+            k_sweep<T, D, 0><<<L.nb, th, sm, t->stream>>>(P, L.first, F, colour);
+        }
+    }
+    static void smooth(mg_tree *t, const KParams &P, int l, Fields<T> &F, int sweeps) {
         for (int s = 0; s < sweeps; s++)
-            for (int colour = 0; colour < 2; colour++) {
-                ++t->launches;
-                k_smooth<T, D><<<L.nb, th, 0, t->stream>>>(P, L.first, F, colour);
-                ghost(t, P, l, F.X, F.XG, 0);
-            }
+            for (int colour = 0; colour < 2; colour++) sweep(t, P, l, F, colour);
     }
     // downward FAS step from level l to l-1 (Sec. 2.4)
     static void restrict_fas(mg_tree *t, const KParams &P, int l, Fields<T> &F) {
@@ -624,9 +1232,20 @@ static void residual_norm_d(mg_tree *t, Fields<double> &F, int homog, double *ou
         if (nleaf <= 0) continue;
         const long long cell_base = t->blocks[L.first + L.nref].cell_off;
         ++t->launches;
-        k_resnorm<D><<<nleaf, threads_for(cells_of<D>(L.n)), 0, t->stream>>>(
-            P, L.first + L.nref, F, t->d_partials + 3 * slot, r64_leaf, leaf_base, cell_base, f32_cells);
-        slot += nleaf;
+        const int C = cells_of<D>(L.n), GH = 2 * D * face_of<D>(L.n);
+        const size_t smt = 2 * (sizeof(BlockDesc) + sizeof(double) * (2 * C + GH + (F.E ? C + GH : 0)));
+        if ((L.n == 8 || L.n == 16) && smt <= 200 * 1024) {
+            auto kern = L.n == 8 ? k_resid_tma<D, 8> : k_resid_tma<D, 16>;
+            const int thr = threads_for(C);
+            const int grid = std::min(nleaf, resident_ctas(kern, thr, smt) * t->nsm);
+            kern<<<grid, thr, smt, t->stream>>>(P, L.first + L.nref, nleaf, F, t->d_partials + 3 * slot, r64_leaf,
+                                               leaf_base, f32_cells);
+            slot += grid;
+        } else {
+            k_resnorm<D><<<nleaf, threads_for(C), 0, t->stream>>>(P, L.first + L.nref, F, t->d_partials + 3 * slot,
+                                                                  r64_leaf, leaf_base, cell_base, f32_cells);
+            slot += nleaf;
+        }
         leaf_base += (long long)nleaf * cells_of<D>(L.n);
     }
     ++t->launches;
@@ -685,21 +1304,21 @@ void eps_grad(mg_tree *t, const double *lam_cells, const double *phi_cells, doub
 }
 
 template <int D>
-static int time_sweeps_d(mg_tree *t, int level, int n_sweeps, double *out) {
+static int time_sweeps_d(mg_tree *t, int level, int n_sweeps, int prec, double *out) {
     const KParams P = kparams(t, 0);
     const LevelHost &L = t->lev[level];
-    const int th = threads_for(cells_of<D>(L.n));
     std::vector<cudaEvent_t> ev(8 * n_sweeps);
     for (auto &e : ev) cudaEventCreate(&e);
     int m = 0;
     for (int s = 0; s < n_sweeps; s++)
         for (int colour = 0; colour < 2; colour++) {
             cudaEventRecord(ev[m++], t->stream);
-            ++t->launches;
-            k_smooth<double, D><<<L.nb, th, 0, t->stream>>>(P, L.first, t->f64, colour);
+            if (prec == 1) Launch<float, D>::sweep(t, P, level, t->f32, colour);
+            else Launch<double, D>::sweep(t, P, level, t->f64, colour);
             cudaEventRecord(ev[m++], t->stream);
             cudaEventRecord(ev[m++], t->stream);
-            Launch<double, D>::ghost(t, P, level, t->f64.X, t->f64.XG, 0);
+            if (prec == 1) Launch<float, D>::ghost(t, P, level, t->f32.X, t->f32.XG, 0);
+            else Launch<double, D>::ghost(t, P, level, t->f64.X, t->f64.XG, 0);
             cudaEventRecord(ev[m++], t->stream);
         }
     cudaStreamSynchronize(t->stream);
@@ -714,16 +1333,17 @@ static int time_sweeps_d(mg_tree *t, int level, int n_sweeps, double *out) {
     for (auto &e : ev) cudaEventDestroy(e);
     const int nl = 2 * n_sweeps;
     const double cells = (double)L.nb * cells_of<D>(L.n), ghosts = (double)L.nb * 2 * D * face_of<D>(L.n);
-    const double per = t->var_eps ? 32.0 : 24.0;
+    const double w = prec == 1 ? 4.0 : 8.0;
     out[0] = ts / nl;
     out[1] = tg / nl;
-    out[2] = cells * per + ghosts * (t->var_eps ? 16.0 : 8.0);
-    out[3] = ghosts * 16.0;
+    out[2] = cells * w * (t->var_eps ? 4.0 : 3.0) + ghosts * w * (t->var_eps ? 2.0 : 1.0);
+    out[3] = ghosts * w * 2.0;
     return MG_OK;
 }
 
-int time_sweeps(mg_tree *t, int level, int n_sweeps, double *out4) {
-    return t->dim == 2 ? time_sweeps_d<2>(t, level, n_sweeps, out4) : time_sweeps_d<3>(t, level, n_sweeps, out4);
+int time_sweeps(mg_tree *t, int level, int n_sweeps, int prec, double *out4) {
+    return t->dim == 2 ? time_sweeps_d<2>(t, level, n_sweeps, prec, out4)
+                       : time_sweeps_d<3>(t, level, n_sweeps, prec, out4);
 }
 
 int check_cuda(const char *what) {

@@ -202,6 +202,8 @@ static int build(mg_tree *t) {
         L.nb = (int)lv[l].b.size();
         L.nref = 0;
         for (int b = 0; b < L.nb; b++) L.nref += haschild[l][b];
+        co = (co + 31) / 32 * 32;  // 32-element (128/256-byte) aligned levels
+        go = (go + 31) / 32 * 32;
         L.cell_first = co;
         L.ghost_first = go;
         L.ncells = L.nb * ipow(L.n, D);
@@ -237,7 +239,7 @@ static int build(mg_tree *t) {
                 parent_of(l, q, pq, B.poff);
                 B.parent = gid[l - 1][map[l - 1][key(l - 1, pq[0], pq[1], pq[2])]];
             }
-            for (int f = 0; f < 6; f++) B.nbr[f] = -1;
+            for (int f = 0; f < 6; f++) { B.nbr[f] = -1; B.push[f] = -1; }
             for (int d = 0; d < D; d++)
                 for (int s = 0; s < 2; s++) {
                     int nq[3] = {q[0], q[1], q[2]};
@@ -247,7 +249,13 @@ static int build(mg_tree *t) {
                         nq[d] = (nq[d] + L.nblk[d]) % L.nblk[d];
                     }
                     const int m = map[l][key(l, nq[0], nq[1], nq[2])];
-                    if (m >= 0) { B.nbr[2 * d + s] = gid[l][m]; continue; }
+                    if (m >= 0) {
+                        B.nbr[2 * d + s] = gid[l][m];
+                        const long long Fd = D == 2 ? L.n : (long long)L.n * L.n;
+                        const int rn = gid[l][m] - L.first;  // neighbour's rank in the level
+                        B.push[2 * d + s] = L.ghost_first + rn * 2LL * D * Fd + ((2 * d + s) ^ 1) * Fd;
+                        continue;
+                    }
                     // no same-level neighbour: the region one level coarser must exist (2:1)
                     if (l == 0 || lv[l - 1].n != L.n) return fail(MG_ERR_BALANCE, "incomplete coarse level");
                     int cq[3] = {0, 0, 0};
@@ -258,6 +266,12 @@ static int build(mg_tree *t) {
                 }
         }
     }
+    // red and black must alternate across periodic faces on every smoothed
+    // level (the fused sweep relies on it); the coarsest level is solved directly
+    for (int l = 1; l < nl; l++)
+        for (int d = 0; d < D; d++)
+            if (t->bc.type[2 * d] == MG_BC_PERIODIC && t->lev[l].ncell[d] % 2)
+                return fail(MG_ERR_UNSUPPORTED, "odd periodic extent on a smoothed level");
     t->singular = t->helm <= 0;
     for (int f = 0; f < 2 * D; f++)
         if (t->bc.type[f] == MG_BC_DIRICHLET) t->singular = false;
@@ -466,6 +480,7 @@ extern "C" int mg_tree_finalize(mg_tree *t, void *stream) {
     int rc = build(t);
     if (rc) return rc;
     CK(cudaGetDevice(&t->device));
+    CK(cudaDeviceGetAttribute(&t->nsm, cudaDevAttrMultiProcessorCount, t->device));
     t->stream = (cudaStream_t)stream;
     CK(cudaMalloc((void **)&t->d_blocks, sizeof(BlockDesc) * t->blocks.size()));
     CK(cudaMemcpy(t->d_blocks, t->blocks.data(), sizeof(BlockDesc) * t->blocks.size(), cudaMemcpyHostToDevice));
@@ -477,6 +492,7 @@ extern "C" int mg_tree_finalize(mg_tree *t, void *stream) {
     t->n_partials = (int)nleafb;
     if ((rc = dalloc(&t->d_partials, 3 * nleafb))) return rc;
     if ((rc = dalloc(&t->d_red, 3))) return rc;
+    if ((rc = dalloc(&t->d_status, 1))) return rc;
     if ((rc = dalloc(&t->d_cvec, t->ns))) return rc;
     CK(cudaMallocHost((void **)&t->h_red, 3 * sizeof(double)));
     t->finalized = true;
@@ -489,6 +505,18 @@ extern "C" int mg_tree_finalize(mg_tree *t, void *stream) {
     do {                                                                         \
         if (!(t) || !(t)->finalized) return fail(MG_ERR_ARG, "tree not finalized"); \
     } while (0)
+
+// device status word: a bounded wait inside a kernel gave up (reported once)
+static int check_status(mg_tree *t) {
+    int st = 0;
+    CK(cudaStreamSynchronize(t->stream));
+    CK(cudaMemcpy(&st, t->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (st) {
+        CK(cudaMemset(t->d_status, 0, sizeof(int)));
+        return fail(MG_ERR_TIMEOUT, "a bounded wait in a sweep kernel expired");
+    }
+    return MG_OK;
+}
 
 extern "C" int mg_set_bc_plane(mg_tree *t, int face, int level, const double *vals) {
     if (!t || !vals) return fail(MG_ERR_ARG, "null argument");
@@ -593,7 +621,7 @@ extern "C" int mg_residual_norm(mg_tree *t, double *l2, double *linf, double *de
     double o[3];
     residual_norm(t, t->f64, 0, o, dev_r, nullptr);
     int rc = check_cuda("residual_norm");
-    if (rc) return rc;
+    if (rc || (rc = check_status(t))) return rc;
     *l2 = std::sqrt(o[0] / o[1]);
     *linf = o[2];
     if (!std::isfinite(*l2) || !std::isfinite(*linf)) return fail(MG_ERR_NAN, "residual is not finite");
@@ -657,7 +685,7 @@ extern "C" int mg_solve(mg_tree *t, double rel_tol, int max_cycles, int fmg_firs
     } else {
         return fail(MG_ERR_ARG, "unknown precision");
     }
-    if ((rc = check_cuda("solve"))) return rc;
+    if ((rc = check_cuda("solve")) || (rc = check_status(t))) return rc;
     if (cycles_done) *cycles_done = cycles;
     if (rel_out) *rel_out = rel;
     if (!std::isfinite(rel)) return fail(MG_ERR_NAN, "residual is not finite");
@@ -706,10 +734,16 @@ extern "C" int mg_launch_count(mg_tree *t, int64_t *n) {
     return MG_OK;
 }
 
-extern "C" int mg_time_sweeps(mg_tree *t, int level, int n_sweeps, double out[4]) {
+static int ensure_f32(mg_tree *t);
+
+extern "C" int mg_time_sweeps(mg_tree *t, int level, int n_sweeps, int precision, double out[4]) {
     NEED_FINAL(t);
-    if (!out || n_sweeps < 1 || level < 0 || level >= (int)t->lev.size()) return fail(MG_ERR_ARG, "bad arguments");
-    int rc = time_sweeps(t, level, n_sweeps, out);
+    if (!out || n_sweeps < 1 || level < 0 || level >= (int)t->lev.size() ||
+        (precision != MG_FP64 && precision != MG_FP32_DC))
+        return fail(MG_ERR_ARG, "bad arguments");
+    int rc;
+    if (precision == MG_FP32_DC && (rc = ensure_f32(t))) return rc;
+    rc = time_sweeps(t, level, n_sweeps, precision, out);
     if (rc) return rc;
     return check_cuda("time_sweeps");
 }
@@ -722,7 +756,7 @@ extern "C" int mg_tree_destroy(mg_tree *t) {
         free_fields(t->adj, false);
         free_fields(t->f32, true);
         cudaFree(t->d_blocks); cudaFree(t->d_levels); cudaFree(t->d_bcplanes);
-        cudaFree(t->d_r64); cudaFree(t->d_minv); cudaFree(t->d_cvec); cudaFree(t->d_partials); cudaFree(t->d_red);
+        cudaFree(t->d_r64); cudaFree(t->d_minv); cudaFree(t->d_cvec); cudaFree(t->d_partials); cudaFree(t->d_red); cudaFree(t->d_status);
         cudaFreeHost(t->h_red);
     }
     delete t;

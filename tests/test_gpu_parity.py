@@ -62,6 +62,7 @@ def small_cases():
         "cyl_amr": W.cyl_ring_tree(11, force_k=4),
         "cyl_odd_k3": W.cyl_ring_tree(12, force_k=3),
         "varcoef3d_singular": W.cfg3_varcoef3d(n=32, N=8, contrast=10.0),
+        "varcoef3d_b16": W.cfg3_varcoef3d(n=64, N=16, contrast=10.0, seed=3),
         "block2_3d": W.Problem("b2", 3, 2, 0, (8, 8, 8), (0,) * 3, (1,) * 3, (0, 1, 0, 0, 0, 0), (0.1, 0.2, 0, 0, 0, 0),
                                W.refine_spheres(3, 2, (8,) * 3, (0,) * 3, (1,) * 3, (0.5, 0.5, 0.5), (0.3,)), 8,
                                rhs=lambda X, Y, Z: X * Y - Z),
