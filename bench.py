@@ -100,6 +100,30 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def kernel_sha1(name):
+    """sha1 of one kernel template's source text in mg_kernels.cu."""
+    import hashlib
+    src = open(os.path.join(ROOT, "paper_1901_11370_gb300", "csrc", "mg_kernels.cu")).read()
+    i = src.index(name + "(")
+    start = src.rfind("template", 0, i)
+    end = src.index("\n}\n", i) + 3
+    return hashlib.sha1(src[start:end].encode()).hexdigest()
+
+
+def measured_traffic(kernel, fname):
+    """DRAM bytes per cell from a committed ncu summary, or None when the
+    kernel source changed since the capture."""
+    path = os.path.join(ROOT, "profiles", fname)
+    try:
+        kv = dict(ln.split(":", 1) for ln in open(path) if ":" in ln and not ln.startswith("#"))
+        kv = {k.strip(): v.strip() for k, v in kv.items()}
+        if kv.get("kernel") == kernel and kv.get("source_sha1") == kernel_sha1(kernel):
+            return float(kv["dram_bytes_per_cell"])
+    except Exception:
+        pass
+    return None
+
+
 def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -257,18 +281,10 @@ def run_ours(args):
     (ms_s64, _, b_s64, _), _ = tree.time_sweeps(n_sweeps=4, precision=mg.MG_FP64)
     peak, peak_kind = peak_hbm()
     achieved = b_s / (ms_s * 1e-3) / 1e9
-    traffic = None
-    tpath = os.path.join(ROOT, "profiles", "smooth_traffic.json")
-    if os.path.exists(tpath):
-        try:
-            tj = json.load(open(tpath))
-            src = open(os.path.join(ROOT, "paper_1901_11370_gb300", "csrc", "mg_kernels.cu"), "rb").read()
-            import hashlib
-            if tj.get("source_sha1") == hashlib.sha1(src).hexdigest():
-                lv = tree.levels()[lev]
-                traffic = tj["dram_bytes_per_cell"] * lv["nb"] * lv["n"] ** 3
-        except Exception:
-            traffic = None
+    traffic = measured_traffic("k_sweep_tma", "k_sweep_tma_f32_traffic.txt")
+    if traffic is not None:
+        lv = tree.levels()[lev]
+        traffic *= lv["nb"] * lv["n"] ** 3
 
     total_unknowns = n * world
     value = total_unknowns / (ms_mixed * 1e-3)
