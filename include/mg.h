@@ -175,6 +175,24 @@ int mg_adjoint(mg_tree *t, const double *dev_dLdphi, double *dev_dLdf, double *d
 int mg_launch_count(mg_tree *t, int64_t *n);
 int mg_time_sweeps(mg_tree *t, int level, int n_sweeps, int precision, double out[4]);
 
+/*
+ * mg_residual_norm_noalloc -- the same composite residual norms as
+ * mg_residual_norm (without the optional residual vector), for callers
+ * whose device memory belongs to their own allocator (a pool reserved up
+ * front) and who therefore may not call cudaMalloc or have memory allocated
+ * on their behalf when they ask for a norm.  This call allocates nothing: its
+ * reduction scratch is a fixed static device array of 16384 partial sums
+ * (3 doubles each, 384 KiB) that every GPU loading this library holds until
+ * the process exits.  A mesh whose residual launches need more partial sums
+ * than that (for instance very many small leaf blocks) is rejected with
+ * MG_ERR_ARG.  The first call on a device looks up the array's device
+ * address with that device current; make that first call before any stream
+ * capture.  The tree's device must be current.  All calls share the array:
+ * calls that overlap on the GPU (from two threads or two streams) race on
+ * it.  Synchronises the tree's stream.  The paper has no counterpart.
+ */
+int mg_residual_norm_noalloc(mg_tree *t, double *l2, double *linf);
+
 /* mg_tree_destroy -- free device and host memory (synchronises the stream). */
 int mg_tree_destroy(mg_tree *t);
 

@@ -139,6 +139,13 @@ class Tree:
         check(self.L.mg_residual_norm(self._h, C.byref(l2), C.byref(li), _ptr(r) if want_res else None))
         return (l2.value, li.value, r) if want_res else (l2.value, li.value)
 
+    def residual_norm_noalloc(self):
+        """Composite residual norms (l2, linf) through the entry point that
+        allocates nothing (its scratch is a static device array)."""
+        l2, li = C.c_double(), C.c_double()
+        check(self.L.mg_residual_norm_noalloc(self._h, C.byref(l2), C.byref(li)))
+        return l2.value, li.value
+
     def solve(self, rel_tol=1e-10, max_cycles=50, fmg_first=True, precision=MG_FP64, inner_cycles=1,
               n_down=2, n_up=2, raise_on_fail=True):
         p = _params(n_down, n_up, precision, inner_cycles)

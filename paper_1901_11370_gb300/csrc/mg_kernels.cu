@@ -9,7 +9,10 @@
 // blocks, with neighbour faces served by L1/L2.
 #include <cmath>
 #include <algorithm>
+#include <cmath>
 #include <cstdint>
+#include <mutex>
+#include <string>
 #include <cstdio>
 #include <vector>
 
@@ -1345,6 +1348,143 @@ int time_sweeps(mg_tree *t, int level, int n_sweeps, int prec, double *out4) {
     return t->dim == 2 ? time_sweeps_d<2>(t, level, n_sweeps, prec, out4)
                        : time_sweeps_d<3>(t, level, n_sweeps, prec, out4);
 }
+
+// ------------------------------------------- residual norm, no allocation ---
+// Scratch for mg_residual_norm_noalloc: per-CTA partial sums (3 doubles per
+// CTA of the residual launches) followed by the 3 reduced values.  Every
+// GPU that loads this library holds it until the process exits.  All calls
+// share it and it keeps the last call's contents; each call overwrites every
+// slot it reads, so nothing needs clearing, but calls that overlap on the GPU
+// (two streams, two threads) race on it.
+static constexpr int kNoAllocSlots = 16384;  // 384 KiB of partials
+static __device__ __align__(256) double g_noalloc_scratch[3 * kNoAllocSlots + 4];
+
+// Device address of the scratch array, looked up once per device with that
+// device current (the host-side name of the array is only a stand-in).
+static int noalloc_scratch(int device, double **out) {
+    static std::mutex mu;
+    static double *addr[64] = {nullptr};
+    if (device < 0 || device >= 64) {
+        mg_set_error("mg_residual_norm_noalloc: device ordinal out of range");
+        return MG_ERR_ARG;
+    }
+    std::lock_guard<std::mutex> lock(mu);
+    if (!addr[device]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) {
+            mg_set_error(std::string("mg_residual_norm_noalloc: cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+            return MG_ERR_CUDA;
+        }
+        addr[device] = static_cast<double *>(p);
+    }
+    *out = addr[device];
+    return MG_OK;
+}
+
+template <int D>
+static int residual_norm_noalloc_d(mg_tree *t, double *scratch, double *out3) {
+    // partial slots the residual launches will use, checked before any work
+    long long need = 0;
+    for (size_t l = 0; l < t->lev.size(); l++) {
+        const LevelHost &L = t->lev[l];
+        const int nleaf = L.nb - L.nref;
+        if (nleaf <= 0) continue;
+        const int C = cells_of<D>(L.n), GH = 2 * D * face_of<D>(L.n);
+        const size_t smt = 2 * (sizeof(BlockDesc) + sizeof(double) * (2 * C + GH + (t->f64.E ? C + GH : 0)));
+        if ((L.n == 8 || L.n == 16) && smt <= 200 * 1024) {
+            auto kern = L.n == 8 ? k_resid_tma<D, 8> : k_resid_tma<D, 16>;
+            need += std::min(nleaf, resident_ctas(kern, threads_for(C), smt) * t->nsm);
+        } else {
+            need += nleaf;
+        }
+    }
+    if (need > kNoAllocSlots) {
+        mg_set_error("mg_residual_norm_noalloc: the residual needs " + std::to_string(need) +
+                     " CTA partial sums, more than the static scratch holds (" + std::to_string(kNoAllocSlots) + ")");
+        return MG_ERR_ARG;
+    }
+    Fields<double> &F = t->f64;
+    Launch<double, D>::refresh(t, F, 0);
+    const KParams P = kparams(t, 0);
+    int slot = 0;
+    for (size_t l = 0; l < t->lev.size(); l++) {
+        const LevelHost &L = t->lev[l];
+        const int nleaf = L.nb - L.nref;
+        if (nleaf <= 0) continue;
+        const long long cell_base = t->blocks[L.first + L.nref].cell_off;
+        const int C = cells_of<D>(L.n), GH = 2 * D * face_of<D>(L.n);
+        const size_t smt = 2 * (sizeof(BlockDesc) + sizeof(double) * (2 * C + GH + (F.E ? C + GH : 0)));
+        ++t->launches;
+        if ((L.n == 8 || L.n == 16) && smt <= 200 * 1024) {
+            auto kern = L.n == 8 ? k_resid_tma<D, 8> : k_resid_tma<D, 16>;
+            const int grid = std::min(nleaf, resident_ctas(kern, threads_for(C), smt) * t->nsm);
+            kern<<<grid, threads_for(C), smt, t->stream>>>(P, L.first + L.nref, nleaf, F, scratch + 3 * slot,
+                                                           nullptr, 0, nullptr);
+            slot += grid;
+        } else {
+            k_resnorm<D><<<nleaf, threads_for(C), 0, t->stream>>>(P, L.first + L.nref, F, scratch + 3 * slot,
+                                                                  nullptr, 0, cell_base, nullptr);
+            slot += nleaf;
+        }
+    }
+    ++t->launches;
+    k_reduce3<<<1, 1024, 0, t->stream>>>(scratch, slot, scratch + 3 * kNoAllocSlots);
+    cudaError_t e = cudaMemcpyAsync(out3, scratch + 3 * kNoAllocSlots, 3 * sizeof(double), cudaMemcpyDeviceToHost,
+                                    t->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(t->stream);
+    if (e != cudaSuccess) {
+        mg_set_error(std::string("mg_residual_norm_noalloc: ") + cudaGetErrorString(e));
+        return MG_ERR_CUDA;
+    }
+    return check_cuda("mg_residual_norm_noalloc");
+}
+
+}  // namespace mg
+
+// The paper has no counterpart: this is an allocation-free variant of
+// mg_residual_norm (see include/mg.h).
+extern "C" int mg_residual_norm_noalloc(mg_tree *t, double *l2, double *linf) {
+    using namespace mg;
+    if (!t || !t->finalized) {
+        mg_set_error("mg_residual_norm_noalloc: tree not finalized");
+        return MG_ERR_ARG;
+    }
+    if (!l2 || !linf) {
+        mg_set_error("mg_residual_norm_noalloc: null output");
+        return MG_ERR_ARG;
+    }
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != t->device) {
+        mg_set_error("mg_residual_norm_noalloc: the tree's device must be current");
+        return MG_ERR_ARG;
+    }
+    double *scratch = nullptr;
+    int rc = noalloc_scratch(dev, &scratch);
+    if (rc) return rc;
+    double o[3];
+    rc = t->dim == 2 ? residual_norm_noalloc_d<2>(t, scratch, o) : residual_norm_noalloc_d<3>(t, scratch, o);
+    if (rc) return rc;
+    int st = 0;
+    if (cudaMemcpy(&st, t->d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) {
+        mg_set_error("mg_residual_norm_noalloc: status read failed");
+        return MG_ERR_CUDA;
+    }
+    if (st) {
+        cudaMemset(t->d_status, 0, sizeof(int));
+        mg_set_error("a bounded wait in a residual kernel expired");
+        return MG_ERR_TIMEOUT;
+    }
+    *l2 = std::sqrt(o[0] / o[1]);
+    *linf = o[2];
+    if (!std::isfinite(*l2) || !std::isfinite(*linf)) {
+        mg_set_error("residual is not finite");
+        return MG_ERR_NAN;
+    }
+    return MG_OK;
+}
+
+namespace mg {
 
 int check_cuda(const char *what) {
     cudaError_t e = cudaGetLastError();
