@@ -2,6 +2,7 @@
 // CUDA kernels and cycle driver (mg_kernels.cu).  Not part of the public ABI.
 #pragma once
 #include <cstdint>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -111,6 +112,16 @@ struct mg_tree {
     long long launches = 0;        // kernels launched so far
     int *d_status = nullptr;       // device status word (0 = ok)
     int nsm = 0;                   // multiprocessors of the device
+    // CUDA graphs of whole cycle sequences, keyed by what they enqueue; a
+    // private non-blocking stream is used for capture (the user stream may
+    // be the legacy default stream, which cannot be captured)
+    struct Graph {
+        cudaGraphExec_t exec;
+        long long launches;
+    };
+    std::map<std::string, Graph> graphs;
+    cudaStream_t cap_stream = nullptr;
+    bool use_graphs = true;
 };
 
 namespace mg {
@@ -123,6 +134,8 @@ template <class T> void refresh_eps(mg_tree *t, Fields<T> &F);
 // r64 (FP64 leaf order), f32 (FP32 into the leaf cells of an FP32 field)
 void residual_norm(mg_tree *t, Fields<double> &F, int homog, double *out3, double *r64_leaf,
                    float *f32_cells);
+void residual_enqueue(mg_tree *t, Fields<double> &F, int homog, double *r64_leaf, float *f32_cells);
+void residual_wait(mg_tree *t, double *out3);
 void add_e_to_phi(mg_tree *t, const float *e, double *phi);
 void copy_eps_to_f32(mg_tree *t);
 void eps_grad(mg_tree *t, const double *lam_cells, const double *phi_cells, double *out_leaf);

@@ -697,6 +697,352 @@ __global__ void __launch_bounds__(kMaxThreads) k_prolong(KParams P, int first, F
     }
 }
 
+// ------------------------------------------- transfers with ghost pushes ---
+// Push the ghosts that depend on the cells of one face of block b after those
+// cells changed: the same-level neighbour's slot opposite each cell, or the
+// block's own physical or refinement ghost.  `val(ii)` returns the new value
+// of interior cell ii of b (an in-range cell index triple).
+template <class T, int D, class ValFn>
+__device__ __forceinline__ void push_face_cell(const KParams &P, const LevelDesc &L, const BlockDesc &b, int face,
+                                               int u, I3 ii, T *__restrict__ X, T *__restrict__ XG, ValFn val) {
+    const int n = b.n, Fc = face_of<D>(n), d = face >> 1, s = face & 1;
+    const int nb = b.nbr[face];
+    const T c = val(ii);
+    if (nb >= 0) {
+        XG[b.push[face] + u] = c;
+    } else if (nb == -1) {
+        XG[b.ghost_off + face * Fc + u] = phys_ghost<T>(P, L, face, c, bc_value(P, L, b, D, face, ii));
+    } else {
+        I3 dd = ii;
+        put(dd, d, s ? n - 2 : 1);
+        XG[b.ghost_off + face * Fc + u] = cf_ghost<T, D>(P, L, b, face, ii, c, val(dd), X, XG, nb, false);
+    }
+}
+
+// Restriction with the FAS residual (Sec. 2.3, 2.4) for fine block b, fused
+// with the ghost update of the parent level: the parent cells under b receive
+// the mean of their children (and the mean child residual goes to the
+// parent's right-hand side); then every parent ghost that depends on those
+// cells is pushed.  Each parent face cell belongs to exactly one child, so
+// every ghost slot has one writer.  Needs n >= 4 (a child octant then holds
+// the two parent layers c and d of a refinement ghost).
+template <class T, int D>
+__global__ void __launch_bounds__(kMaxThreads) k_restrict_push(KParams P, int first, Fields<T> F) {
+    __shared__ BlockDesc sb, sp;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *oct = reinterpret_cast<T *>(smem_raw);
+    stage_desc(P, first + blockIdx.x, sb);
+    const BlockDesc &b = sb;
+    stage_desc(P, b.parent, sp);
+    const BlockDesc &p = sp;
+    const LevelDesc &L = P.L[b.lev];
+    const LevelDesc &PL = P.L[p.lev];
+    const int n = b.n, m = n / 2, M = cells_of<D>(m), pn = p.n;
+    for (int c = threadIdx.x; c < M; c += blockDim.x) {
+        int ci, cj, ck;
+        cell_of(c, m, D, ci, cj, ck);
+        T sx = 0, sr = 0;
+#pragma unroll 1
+        for (int ch = 0; ch < (1 << D); ch++) {
+            const int fi = 2 * ci + (ch & 1), fj = 2 * cj + ((ch >> 1) & 1), fk = D == 3 ? 2 * ck + ((ch >> 2) & 1) : 0;
+            T lap, num, den, xc;
+            stencil<T, T, D>(P, L, b, F.X, F.XG, F.E, F.EG, fi, fj, fk, lap, num, den, xc);
+            sx += xc;
+            sr += F.F[b.cell_off + cidx<D>(n, fi, fj, fk)] - (lap - (T)P.helm * xc);
+        }
+        const T xv = sx / (T)(1 << D);
+        const int pc = cidx<D>(pn, b.poff[0] + ci, b.poff[1] + cj, b.poff[2] + ck);
+        F.X[p.cell_off + pc] = xv;
+        F.F[p.cell_off + pc] = sr / (T)(1 << D);
+        oct[c] = xv;
+    }
+    __syncthreads();
+    const int Fm = face_of<D>(m);
+    auto val = [&](I3 q) {  // parent cell q, inside this child's octant
+        return oct[cidx<D>(m, q.x - b.poff[0], q.y - b.poff[1], q.z - b.poff[2])];
+    };
+    for (int t = threadIdx.x; t < 2 * D * Fm; t += blockDim.x) {
+        const int face = t / Fm, v = t - face * Fm, d = face >> 1, s = face & 1;
+        const int off = d == 0 ? b.poff[0] : d == 1 ? b.poff[1] : b.poff[2];
+        if (s ? (off + m != pn) : (off != 0)) continue;  // octant not on this parent face
+        I3 ii = face_cell<D>(m, face, v, false);       // octant-local cell on the face
+        ii.x += b.poff[0];
+        ii.y += b.poff[1];
+        ii.z += D == 3 ? b.poff[2] : 0;
+        put(ii, d, s ? pn - 1 : 0);
+        int u;  // parent face index t1 + pn t2
+        if (D == 2) u = d == 0 ? ii.y : ii.x;
+        else u = d == 0 ? ii.y + pn * ii.z : (d == 1 ? ii.x + pn * ii.z : ii.x + pn * ii.y);
+        push_face_cell<T, D>(P, PL, p, face, u, ii, F.X, F.XG, val);
+    }
+}
+
+// Covered cells: f^H = R(r^h) + L^H v^H (eq. for the coarse right-hand side),
+// and the FAS copy v_old = v^H with its ghosts (only covered blocks are read
+// by the prolongation).
+template <class T, int D>
+__global__ void __launch_bounds__(kMaxThreads) k_fas_rhs_vold(KParams P, int first, Fields<T> F) {
+    __shared__ BlockDesc sb;
+    stage_desc(P, first + blockIdx.x, sb);
+    const BlockDesc &b = sb;
+    const LevelDesc &L = P.L[b.lev];
+    const int n = b.n, C = cells_of<D>(n), G = 2 * D * face_of<D>(n);
+    for (int c = threadIdx.x; c < C; c += blockDim.x) {
+        int i, j, k;
+        cell_of(c, n, D, i, j, k);
+        T lap, num, den, xc;
+        stencil<T, T, D>(P, L, b, F.X, F.XG, F.E, F.EG, i, j, k, lap, num, den, xc);
+        F.F[b.cell_off + c] += lap - (T)P.helm * xc;
+        F.V[b.cell_off + c] = xc;
+    }
+    for (int t = threadIdx.x; t < G; t += blockDim.x) F.VG[b.ghost_off + t] = F.XG[b.ghost_off + t];
+}
+
+// Coarse-grid correction fused with the fine-level ghost update: every cell
+// of block b changes, so after the correction all its face ghosts that
+// depend on its cells are pushed (the kernel reads only the coarser level's
+// fields and its own interior, never this level's ghosts).
+template <class T, int D>
+__global__ void __launch_bounds__(kMaxThreads) k_prolong_push(KParams P, int first, Fields<T> F) {
+    __shared__ BlockDesc sb, sp;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *xs = reinterpret_cast<T *>(smem_raw);
+    stage_desc(P, first + blockIdx.x, sb);
+    const BlockDesc &b = sb;
+    stage_desc(P, b.parent, sp);
+    const BlockDesc &p = sp;
+    const LevelDesc &L = P.L[b.lev];
+    const int n = b.n, C = cells_of<D>(n);
+    for (int c = threadIdx.x; c < C; c += blockDim.x) {
+        int i, j, k;
+        cell_of(c, n, D, i, j, k);
+        const int I0 = b.ijk[0] * n + i, I1 = b.ijk[1] * n + j, I2 = b.ijk[2] * n + k;
+        const int c0 = b.poff[0] + i / 2, c1 = b.poff[1] + j / 2, c2 = D == 3 ? b.poff[2] + k / 2 : 0;
+        const T v0 = load<T, D>(F.X, F.XG, p, c0, c1, c2) - load<T, D>(F.V, F.VG, p, c0, c1, c2);
+        const int sx = (I0 & 1) ? 1 : -1, sy = (I1 & 1) ? 1 : -1, sz = (I2 & 1) ? 1 : -1;
+        T nbs = load<T, D>(F.X, F.XG, p, c0 + sx, c1, c2) - load<T, D>(F.V, F.VG, p, c0 + sx, c1, c2);
+        nbs += load<T, D>(F.X, F.XG, p, c0, c1 + sy, c2) - load<T, D>(F.V, F.VG, p, c0, c1 + sy, c2);
+        if (D == 3) nbs += load<T, D>(F.X, F.XG, p, c0, c1, c2 + sz) - load<T, D>(F.V, F.VG, p, c0, c1, c2 + sz);
+        const T val = D == 2 ? ((T)2 * v0 + nbs) / (T)4 : (v0 + nbs) / (T)4;
+        const T xn = F.X[b.cell_off + c] + val;
+        F.X[b.cell_off + c] = xn;
+        xs[c] = xn;
+    }
+    __syncthreads();
+    const int Fc = face_of<D>(n);
+    auto val = [&](I3 q) { return xs[cidx<D>(n, q.x, q.y, q.z)]; };
+    for (int t = threadIdx.x; t < 2 * D * Fc; t += blockDim.x) {
+        const int face = t / Fc, u = t - face * Fc;
+        push_face_cell<T, D>(P, L, b, face, u, face_cell<D>(n, face, u, false), F.X, F.XG, val);
+    }
+}
+
+// Coarse-grid correction for 8- and 16-cell blocks: the parent's correction
+// c = x - x_old on the octant under block b and its face halo (coarse ghosts
+// where the halo leaves the parent) is staged once in shared memory; the
+// fine block moves with 16-byte vector loads and stores; then the fine
+// ghosts are pushed as in k_prolong_push (same arithmetic order).
+template <class T, int D, int NT>
+__global__ void __launch_bounds__(kMaxThreads) k_prolong_box(KParams P, int first, Fields<T> F) {
+    constexpr int n = NT, m = NT / 2, C = cells_of<D>(NT), B = m + 2, BOX = D == 2 ? B * B : B * B * B;
+    constexpr int VW = 16 / sizeof(T);
+    __shared__ BlockDesc sb, sp;
+    __shared__ __align__(16) T box[BOX];
+    __shared__ __align__(16) T xs[C];
+    stage_desc(P, first + blockIdx.x, sb);
+    const BlockDesc &b = sb;
+    stage_desc(P, b.parent, sp);
+    const BlockDesc &p = sp;
+    const LevelDesc &L = P.L[b.lev];
+    const int pn = p.n, tid = threadIdx.x, nth = blockDim.x;
+    auto bid = [](int a, int c, int e) { return D == 2 ? c * B + a : (e * B + c) * B + a; };
+    for (int q = tid; q < BOX; q += nth) {
+        const int a = q % B, c = (q / B) % B, e = D == 3 ? q / (B * B) : 1;
+        const int out = (a == 0 || a == B - 1) + (c == 0 || c == B - 1) + (D == 3 && (e == 0 || e == B - 1));
+        if (out > 1) continue;  // edge / corner of the box: never read
+        const int pi = b.poff[0] + a - 1, pj = b.poff[1] + c - 1, pk = D == 3 ? b.poff[2] + e - 1 : 0;
+        box[bid(a, c, e)] = load<T, D>(F.X, F.XG, p, pi, pj, pk) - load<T, D>(F.V, F.VG, p, pi, pj, pk);
+    }
+    using V = typename Vec16<T>::type;
+    const V *src = reinterpret_cast<const V *>(F.X + b.cell_off);
+    for (int v = tid; v < C / VW; v += nth) vscatter<T>(xs + v * VW, src[v]);
+    __syncthreads();
+    const int px = (b.ijk[0] * n) & 1, py = (b.ijk[1] * n) & 1, pz = (b.ijk[2] * n) & 1;
+    for (int c = tid; c < C; c += nth) {
+        const int i = c % n, j = (c / n) % n, k = D == 3 ? c / (n * n) : 0;
+        const int a = i / 2 + 1, cc = j / 2 + 1, e = D == 3 ? k / 2 + 1 : 1;
+        const int sx = ((px + i) & 1) ? 1 : -1, sy = ((py + j) & 1) ? 1 : -1, sz = ((pz + k) & 1) ? 1 : -1;
+        const T v0 = box[bid(a, cc, e)];
+        T nbs = box[bid(a + sx, cc, e)];
+        nbs += box[bid(a, cc + sy, e)];
+        if (D == 3) nbs += box[bid(a, cc, e + sz)];
+        const T val = D == 2 ? ((T)2 * v0 + nbs) / (T)4 : (v0 + nbs) / (T)4;
+        xs[c] = xs[c] + val;
+    }
+    __syncthreads();
+    V *dst = reinterpret_cast<V *>(F.X + b.cell_off);
+    for (int v = tid; v < C / VW; v += nth) dst[v] = vgather<T>(xs + v * VW);
+    constexpr int Fc = face_of<D>(NT);
+    auto val = [&](I3 q) { return xs[cidx<D>(n, q.x, q.y, q.z)]; };
+    for (int t = tid; t < 2 * D * Fc; t += nth) {
+        const int face = t / Fc, u = t - face * Fc;
+        push_face_cell<T, D>(P, L, b, face, u, face_cell<D>(n, face, u, false), F.X, F.XG, val);
+    }
+    (void)pn;
+}
+
+// Restriction with the FAS residual for 8- and 16-cell blocks, persistent
+// and TMA-staged like the sweep: the child block (descriptor, x, ghosts, f,
+// eps) and its parent's descriptor arrive by cp.async.bulk; child residuals
+// are formed from shared memory, then each parent cell under the child gets
+// the mean of its children and the parent-level ghosts are pushed (see
+// k_restrict_push).
+template <class T, int D, int NT>
+__global__ void __launch_bounds__(kMaxThreads, 4) k_restrict_tma(KParams P, int first, int nblocks, Fields<T> F) {
+    constexpr int n = NT, m = NT / 2, C = cells_of<D>(NT), FC = face_of<D>(NT), GH = 2 * D * FC;
+    constexpr int M = cells_of<D>(m);
+    constexpr int DESC = (int)(sizeof(BlockDesc) / sizeof(T));
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t bars[2];
+    __shared__ __align__(16) LevelDesc sL, sPL;
+    __shared__ int s_abort;
+    __shared__ __align__(16) T rs[C];
+    const bool var = F.E != nullptr;
+    const int stage_elems = 2 * DESC + 2 * C + GH + (var ? C + GH : 0);
+    T *stage0 = reinterpret_cast<T *>(smem_raw);
+    const int tid = threadIdx.x, nth = blockDim.x;
+    const uint32_t tx_bytes = (uint32_t)(sizeof(T) * stage_elems);
+    if (tid == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        fence_mbar_init();
+        s_abort = 0;
+    }
+    if (tid < (int)(sizeof(LevelDesc) / 4)) {
+        const BlockDesc &b0 = P.B[first];
+        reinterpret_cast<int *>(&sL)[tid] = reinterpret_cast<const int *>(P.L + b0.lev)[tid];
+        reinterpret_cast<int *>(&sPL)[tid] = reinterpret_cast<const int *>(P.L + P.B[b0.parent].lev)[tid];
+    }
+    __syncthreads();
+    auto issue = [&](int it, int g) {
+        T *st = stage0 + (it & 1) * stage_elems;
+        const long long co = P.B[g].cell_off, go = P.B[g].ghost_off;
+        const int par = P.B[g].parent;
+        uint64_t *bar = &bars[it & 1];
+        fence_async_smem();
+        mbar_expect_tx(bar, tx_bytes);
+        bulk_g2s(st, P.B + g, sizeof(BlockDesc), bar);
+        bulk_g2s(st + DESC, P.B + par, sizeof(BlockDesc), bar);
+        bulk_g2s(st + 2 * DESC, F.X + co, sizeof(T) * C, bar);
+        bulk_g2s(st + 2 * DESC + C, F.XG + go, sizeof(T) * GH, bar);
+        bulk_g2s(st + 2 * DESC + C + GH, F.F + co, sizeof(T) * C, bar);
+        if (var) {
+            bulk_g2s(st + 2 * DESC + 2 * C + GH, F.E + co, sizeof(T) * C, bar);
+            bulk_g2s(st + 2 * DESC + 3 * C + GH, F.EG + go, sizeof(T) * GH, bar);
+        }
+    };
+    int g = blockIdx.x;
+    if (tid == 0 && g < nblocks) issue(0, first + g);
+    const LevelDesc &L = sL, &PL = sPL;
+    const bool cyl = P.geom == MG_CYL;
+    for (int it = 0; g < nblocks; it++, g += gridDim.x) {
+        {
+            uint32_t tries = 0;
+            while (!mbar_try_wait(&bars[it & 1], (it >> 1) & 1))
+                if (++tries > kWaitLimit) {
+                    atomicExch(P.status, 1);
+                    s_abort = 1;
+                    break;
+                }
+        }
+        __syncthreads();
+        if (s_abort) break;
+        if (tid == 0 && g + (int)gridDim.x < nblocks) issue(it + 1, first + g + gridDim.x);
+        const T *st = stage0 + (it & 1) * stage_elems;
+        const BlockDesc &b = *reinterpret_cast<const BlockDesc *>(st);
+        const BlockDesc &p = *reinterpret_cast<const BlockDesc *>(st + DESC);
+        const T *xs = st + 2 * DESC, *gs = xs + C, *fs = gs + GH, *es = fs + C, *egs = es + C;
+        auto nbv = [&](const T *xi, const T *gi, int i, int j, int k, int d, int s) -> T {
+            const int o = s ? 1 : -1;
+            if (d == 0) {
+                const int ii = i + o;
+                if (ii < 0 || ii >= n) return gi[(s ? 1 : 0) * FC + (D == 2 ? j : j + n * k)];
+                return xi[cidx<D>(n, ii, j, k)];
+            }
+            if (d == 1) {
+                const int jj = j + o;
+                if (jj < 0 || jj >= n) return gi[(s ? 3 : 2) * FC + (D == 2 ? i : i + n * k)];
+                return xi[cidx<D>(n, i, jj, k)];
+            }
+            const int kk = k + o;
+            if (kk < 0 || kk >= n) return gi[(s ? 5 : 4) * FC + i + n * j];
+            return xi[cidx<D>(n, i, j, kk)];
+        };
+        // child residuals (same arithmetic as the stencil helper)
+        for (int c = tid; c < C; c += nth) {
+            const int i = c % n, j = (c / n) % n, k = D == 3 ? c / (n * n) : 0;
+            const T xc = xs[c];
+            const T ec = var ? es[c] : (T)1;
+            T lap = 0, ri = 0;
+            if (cyl) ri = (T)(P.lo[0] + (b.ijk[0] * n + i + 0.5) * L.h[0]);
+#pragma unroll
+            for (int d = 0; d < D; d++)
+#pragma unroll
+                for (int s = 0; s < 2; s++) {
+                    T w = (T)L.inv_h2[d];
+                    if (var) {
+                        const T en = nbv(es, egs, i, j, k, d, s);
+                        w *= (T)2 * ec * en / (ec + en);
+                    }
+                    if (cyl && d == 0) w *= (T)(P.lo[0] + (b.ijk[0] * n + i + s) * L.h[0]) / ri;
+                    lap += w * (nbv(xs, gs, i, j, k, d, s) - xc);
+                }
+            rs[c] = fs[c] - (lap - (T)P.helm * xc);
+        }
+        __syncthreads();
+        const int pn = p.n;
+        for (int c = tid; c < M; c += nth) {
+            const int ci = c % m, cj = (c / m) % m, ck = D == 3 ? c / (m * m) : 0;
+            T sx = 0, sr = 0;
+#pragma unroll
+            for (int ch = 0; ch < (1 << D); ch++) {
+                const int fc = cidx<D>(n, 2 * ci + (ch & 1), 2 * cj + ((ch >> 1) & 1), D == 3 ? 2 * ck + ((ch >> 2) & 1) : 0);
+                sx += xs[fc];
+                sr += rs[fc];
+            }
+            const int pc = cidx<D>(pn, b.poff[0] + ci, b.poff[1] + cj, b.poff[2] + ck);
+            F.X[p.cell_off + pc] = sx / (T)(1 << D);
+            F.F[p.cell_off + pc] = sr / (T)(1 << D);
+        }
+        __syncthreads();  // rs is reused below for the octant values
+        for (int c = tid; c < M; c += nth) {
+            const int ci = c % m, cj = (c / m) % m, ck = D == 3 ? c / (m * m) : 0;
+            T sx = 0;
+#pragma unroll
+            for (int ch = 0; ch < (1 << D); ch++)
+                sx += xs[cidx<D>(n, 2 * ci + (ch & 1), 2 * cj + ((ch >> 1) & 1), D == 3 ? 2 * ck + ((ch >> 2) & 1) : 0)];
+            rs[c] = sx / (T)(1 << D);
+        }
+        __syncthreads();
+        const int Fm = face_of<D>(m);
+        auto val = [&](I3 q) { return rs[cidx<D>(m, q.x - b.poff[0], q.y - b.poff[1], q.z - b.poff[2])]; };
+        for (int t = tid; t < 2 * D * Fm; t += nth) {
+            const int face = t / Fm, v = t - face * Fm, d = face >> 1, s = face & 1;
+            const int off = d == 0 ? b.poff[0] : d == 1 ? b.poff[1] : b.poff[2];
+            if (s ? (off + m != pn) : (off != 0)) continue;
+            I3 ii = face_cell<D>(m, face, v, false);
+            ii.x += b.poff[0];
+            ii.y += b.poff[1];
+            ii.z += D == 3 ? b.poff[2] : 0;
+            put(ii, d, s ? pn - 1 : 0);
+            int u;
+            if (D == 2) u = d == 0 ? ii.y : ii.x;
+            else u = d == 0 ? ii.y + pn * ii.z : (d == 1 ? ii.x + pn * ii.z : ii.x + pn * ii.y);
+            push_face_cell<T, D>(P, PL, p, face, u, ii, F.X, F.XG, val);
+        }
+    }
+}
+
 // ------------------------------------------------------ residual norm ---
 // Composite residual on leaf blocks [first, first + gridDim.x): per-CTA
 // partial sums of V r^2 and V and the max |r| (warp shuffles, then shared
@@ -1118,10 +1464,33 @@ template <class T, int D> struct Launch {
         for (int s = 0; s < sweeps; s++)
             for (int colour = 0; colour < 2; colour++) sweep(t, P, l, F, colour);
     }
-    // downward FAS step from level l to l-1 (Sec. 2.4)
+    // downward FAS step from level l to l-1 (Sec. 2.4): restriction with the
+    // parent-level ghost pushes, then f^H and v_old on the covered blocks
     static void restrict_fas(mg_tree *t, const KParams &P, int l, Fields<T> &F) {
         const LevelHost &L = t->lev[l], &C = t->lev[l - 1];
         ++t->launches;
+        const int C8 = cells_of<D>(L.n), GH8 = 2 * D * face_of<D>(L.n);
+        const size_t smt = 2 * (2 * sizeof(BlockDesc) + sizeof(T) * (2 * C8 + GH8 + (F.E ? C8 + GH8 : 0)));
+        if ((L.n == 8 || L.n == 16) && smt + sizeof(T) * C8 <= 200 * 1024) {
+            auto kern = L.n == 8 ? k_restrict_tma<T, D, 8> : k_restrict_tma<T, D, 16>;
+            const int thr = threads_for(C8);
+            const int grid = std::min(L.nb, resident_ctas(kern, thr, smt) * t->nsm);
+            kern<<<grid, thr, smt, t->stream>>>(P, L.first, L.nb, F);
+            if (C.nref > 0) {
+                ++t->launches;
+                k_fas_rhs_vold<T, D><<<C.nref, threads_for(cells_of<D>(C.n)), 0, t->stream>>>(P, C.first, F);
+            }
+            return;
+        }
+        if (L.n >= 4) {
+            k_restrict_push<T, D><<<L.nb, threads_for(cells_of<D>(L.n / 2)), sizeof(T) * cells_of<D>(L.n / 2),
+                                    t->stream>>>(P, L.first, F);
+            if (C.nref > 0) {
+                ++t->launches;
+                k_fas_rhs_vold<T, D><<<C.nref, threads_for(cells_of<D>(C.n)), 0, t->stream>>>(P, C.first, F);
+            }
+            return;
+        }
         k_restrict<T, D><<<L.nb, threads_for(cells_of<D>(L.n / 2)), 0, t->stream>>>(P, L.first, F.X, F.XG, F.F,
                                                                                      F.E, F.EG, F.F, 1);
         ghost(t, P, l - 1, F.X, F.XG, 0);
@@ -1136,8 +1505,13 @@ template <class T, int D> struct Launch {
     static void prolong(mg_tree *t, const KParams &P, int l, Fields<T> &F) {
         const LevelHost &L = t->lev[l];
         ++t->launches;
-        k_prolong<T, D><<<L.nb, threads_for(cells_of<D>(L.n)), 0, t->stream>>>(P, L.first, F);
-        ghost(t, P, l, F.X, F.XG, 0);
+        if (L.n == 8 && t->lev[l - 1].n == 8) {
+            k_prolong_box<T, D, 8><<<L.nb, threads_for(cells_of<D>(8) / 2), 0, t->stream>>>(P, L.first, F);
+            return;
+        }
+        const size_t sm = sizeof(T) * cells_of<D>(L.n);
+        set_smem(k_prolong_push<T, D>, sm);
+        k_prolong_push<T, D><<<L.nb, threads_for(cells_of<D>(L.n)), sm, t->stream>>>(P, L.first, F);
     }
     static void coarse(mg_tree *t, const KParams &P, Fields<T> &F) {
         const LevelHost &L = t->lev[0];
@@ -1254,6 +1628,17 @@ static void residual_norm_d(mg_tree *t, Fields<double> &F, int homog, double *ou
     ++t->launches;
     k_reduce3<<<1, 1024, 0, t->stream>>>(t->d_partials, slot, t->d_red);
     cudaMemcpyAsync(t->h_red, t->d_red, 3 * sizeof(double), cudaMemcpyDeviceToHost, t->stream);
+    (void)out3;
+}
+
+// enqueue only (no synchronisation: usable inside a stream capture); the
+// reduced values land in the pinned t->h_red
+void residual_enqueue(mg_tree *t, Fields<double> &F, int homog, double *r64_leaf, float *f32_cells) {
+    if (t->dim == 2) residual_norm_d<2>(t, F, homog, nullptr, r64_leaf, f32_cells);
+    else residual_norm_d<3>(t, F, homog, nullptr, r64_leaf, f32_cells);
+}
+
+void residual_wait(mg_tree *t, double *out3) {
     cudaStreamSynchronize(t->stream);
     out3[0] = t->h_red[0];
     out3[1] = t->h_red[1];
@@ -1261,8 +1646,8 @@ static void residual_norm_d(mg_tree *t, Fields<double> &F, int homog, double *ou
 }
 
 void residual_norm(mg_tree *t, Fields<double> &F, int homog, double *out3, double *r64_leaf, float *f32_cells) {
-    if (t->dim == 2) residual_norm_d<2>(t, F, homog, out3, r64_leaf, f32_cells);
-    else residual_norm_d<3>(t, F, homog, out3, r64_leaf, f32_cells);
+    residual_enqueue(t, F, homog, r64_leaf, f32_cells);
+    residual_wait(t, out3);
 }
 
 void add_e_to_phi(mg_tree *t, const float *e, double *phi) {

@@ -349,7 +349,10 @@ template <class T> static void free_fields(Fields<T> &F, bool free_eps) {
     F = Fields<T>();
 }
 
+static void drop_graphs(mg_tree *t);
+
 static int upload_bc(mg_tree *t) {
+    drop_graphs(t);
     std::vector<double> all;
     std::vector<LevelDesc> ld(t->lev.size());
     for (size_t l = 0; l < t->lev.size(); l++) {
@@ -495,6 +498,7 @@ extern "C" int mg_tree_finalize(mg_tree *t, void *stream) {
     if ((rc = dalloc(&t->d_status, 1))) return rc;
     if ((rc = dalloc(&t->d_cvec, t->ns))) return rc;
     CK(cudaMallocHost((void **)&t->h_red, 3 * sizeof(double)));
+    CK(cudaStreamCreateWithFlags(&t->cap_stream, cudaStreamNonBlocking));
     t->finalized = true;
     if ((rc = build_coarse_inverse(t))) return rc;
     refresh<double>(t, t->f64, 0);
@@ -515,6 +519,51 @@ static int check_status(mg_tree *t) {
         CK(cudaMemset(t->d_status, 0, sizeof(int)));
         return fail(MG_ERR_TIMEOUT, "a bounded wait in a sweep kernel expired");
     }
+    return MG_OK;
+}
+
+// Graphs of cycle sequences: captured once per key on the private capture
+// stream, replayed on the user stream.  Pointers baked into the captured
+// kernels (fields, tables, boundary planes) are stable until a call that
+// reallocates or rebinds them, which drops every graph.
+static void drop_graphs(mg_tree *t) {
+    for (auto &kv : t->graphs) cudaGraphExecDestroy(kv.second.exec);
+    t->graphs.clear();
+}
+
+template <class Fn> static int run_graph(mg_tree *t, const std::string &key, Fn &&enqueue) {
+    if (!t->use_graphs) {
+        enqueue();
+        return check_cuda("enqueue");
+    }
+    auto it = t->graphs.find(key);
+    if (it == t->graphs.end()) {
+        cudaStream_t user = t->stream;
+        const long long l0 = t->launches;
+        CK(cudaStreamSynchronize(user));
+        t->stream = t->cap_stream;
+        cudaError_t e = cudaStreamBeginCapture(t->cap_stream, cudaStreamCaptureModeRelaxed);
+        if (e == cudaSuccess) enqueue();
+        cudaGraph_t g = nullptr;
+        cudaError_t e2 = cudaStreamEndCapture(t->cap_stream, &g);
+        t->stream = user;
+        cudaGetLastError();
+        if (e != cudaSuccess || e2 != cudaSuccess || !g) {
+            if (g) cudaGraphDestroy(g);
+            t->use_graphs = false;  // capture unavailable: launch directly from now on
+            t->launches = l0;
+            enqueue();
+            return check_cuda("enqueue");
+        }
+        cudaGraphExec_t exec = nullptr;
+        e = cudaGraphInstantiate(&exec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return fail(MG_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+        it = t->graphs.emplace(key, mg_tree::Graph{exec, t->launches - l0}).first;
+        t->launches = l0;
+    }
+    t->launches += it->second.launches;
+    CK(cudaGraphLaunch(it->second.exec, t->stream));
     return MG_OK;
 }
 
@@ -580,6 +629,7 @@ extern "C" int mg_set_eps(mg_tree *t, const double *e) {
     if (!e) return fail(MG_ERR_ARG, "null eps");
     int rc;
     if ((rc = dalloc(&t->f64.E, t->ncells)) || (rc = dalloc(&t->f64.EG, t->nghost))) return rc;
+    if (!t->var_eps) drop_graphs(t);  // eps pointers enter the captured kernels
     t->var_eps = true;
     if ((rc = leaf_copy(t, t->f64.E, e, true))) return rc;
     refresh_eps<double>(t, t->f64);
@@ -603,7 +653,11 @@ extern "C" int mg_vcycle(mg_tree *t, int n, const mg_params *p) {
     NEED_FINAL(t);
     mg_params q;
     params_or_default(p, &q);
-    for (int c = 0; c < n; c++) vcycle<double>(t, t->f64, (int)t->lev.size() - 1, q.n_down, q.n_up, 0);
+    const std::string key = "v64:" + std::to_string(q.n_down) + ":" + std::to_string(q.n_up);
+    for (int c = 0; c < n; c++) {
+        int rc = run_graph(t, key, [&] { vcycle<double>(t, t->f64, (int)t->lev.size() - 1, q.n_down, q.n_up, 0); });
+        if (rc) return rc;
+    }
     return check_cuda("vcycle");
 }
 
@@ -611,7 +665,9 @@ extern "C" int mg_fmg(mg_tree *t, const mg_params *p) {
     NEED_FINAL(t);
     mg_params q;
     params_or_default(p, &q);
-    fmg<double>(t, t->f64, q.n_down, q.n_up, 0);
+    const std::string key = "fmg64:" + std::to_string(q.n_down) + ":" + std::to_string(q.n_up);
+    int rc = run_graph(t, key, [&] { fmg<double>(t, t->f64, q.n_down, q.n_up, 0); });
+    if (rc) return rc;
     return check_cuda("fmg");
 }
 
@@ -630,6 +686,7 @@ extern "C" int mg_residual_norm(mg_tree *t, double *l2, double *linf, double *de
 
 static int ensure_f32(mg_tree *t) {
     int rc;
+    if (!t->f32.X) drop_graphs(t);
     if ((rc = alloc_fields(t, t->f32, t->var_eps))) return rc;
     if (t->var_eps) copy_eps_to_f32(t);
     return MG_OK;
@@ -644,41 +701,59 @@ extern "C" int mg_solve(mg_tree *t, double rel_tol, int max_cycles, int fmg_firs
     double o[3];
     int cycles = 0, rc;
     double rel = 1.0;
+    const std::string sfx = ":" + std::to_string(q.n_down) + ":" + std::to_string(q.n_up);
+    // each step is one graph: the cycle(s) and the FP64 composite residual,
+    // whose norms arrive in pinned host memory; the host only waits
     if (q.precision == MG_FP64) {
-        residual_norm(t, t->f64, 0, o, nullptr, nullptr);
+        if ((rc = run_graph(t, "res64", [&] { residual_enqueue(t, t->f64, 0, nullptr, nullptr); }))) return rc;
+        residual_wait(t, o);
         const double r0 = std::sqrt(o[0] / o[1]);
-        if (fmg_first && max_cycles > 0) {
-            fmg<double>(t, t->f64, q.n_down, q.n_up, 0);
+        rel = r0 > 0 ? 1.0 : 0.0;
+        if (fmg_first && max_cycles > 0 && rel > 0) {
+            rc = run_graph(t, "fmg64+res" + sfx, [&] {
+                fmg<double>(t, t->f64, q.n_down, q.n_up, 0);
+                residual_enqueue(t, t->f64, 0, nullptr, nullptr);
+            });
+            if (rc) return rc;
+            residual_wait(t, o);
             cycles++;
-            residual_norm(t, t->f64, 0, o, nullptr, nullptr);
-            rel = r0 > 0 ? std::sqrt(o[0] / o[1]) / r0 : 0.0;
-        } else {
-            rel = r0 > 0 ? 1.0 : 0.0;
+            rel = std::sqrt(o[0] / o[1]) / r0;
         }
         while (rel > rel_tol && cycles < max_cycles) {
-            vcycle<double>(t, t->f64, top, q.n_down, q.n_up, 0);
+            rc = run_graph(t, "v64+res" + sfx, [&] {
+                vcycle<double>(t, t->f64, top, q.n_down, q.n_up, 0);
+                residual_enqueue(t, t->f64, 0, nullptr, nullptr);
+            });
+            if (rc) return rc;
+            residual_wait(t, o);
             cycles++;
-            residual_norm(t, t->f64, 0, o, nullptr, nullptr);
             rel = std::sqrt(o[0] / o[1]) / r0;
             if (!std::isfinite(rel)) break;
         }
     } else if (q.precision == MG_FP32_DC) {
         if ((rc = ensure_f32(t))) return rc;
-        residual_norm(t, t->f64, 0, o, nullptr, t->f32.F);
+        if ((rc = run_graph(t, "res64f32", [&] { residual_enqueue(t, t->f64, 0, nullptr, t->f32.F); }))) return rc;
+        residual_wait(t, o);
         const double r0 = std::sqrt(o[0] / o[1]);
         rel = r0 > 0 ? 1.0 : 0.0;
+        const std::string ki = sfx + ":" + std::to_string(q.inner_cycles);
         while (rel > rel_tol && cycles < max_cycles) {
-            CK(cudaMemsetAsync(t->f32.X, 0, sizeof(float) * t->ncells, t->stream));
-            CK(cudaMemsetAsync(t->f32.XG, 0, sizeof(float) * t->nghost, t->stream));
-            if (fmg_first && cycles == 0) {
-                fmg<float>(t, t->f32, q.n_down, q.n_up, 1);
-                for (int c = 1; c < q.inner_cycles; c++) vcycle<float>(t, t->f32, top, q.n_down, q.n_up, 1);
-            } else {
-                for (int c = 0; c < q.inner_cycles; c++) vcycle<float>(t, t->f32, top, q.n_down, q.n_up, 1);
-            }
-            add_e_to_phi(t, t->f32.X, t->f64.X);
+            const bool first_fmg = fmg_first && cycles == 0;
+            rc = run_graph(t, (first_fmg ? "dc-fmg" : "dc-v") + ki, [&] {
+                cudaMemsetAsync(t->f32.X, 0, sizeof(float) * t->ncells, t->stream);
+                cudaMemsetAsync(t->f32.XG, 0, sizeof(float) * t->nghost, t->stream);
+                if (first_fmg) {
+                    fmg<float>(t, t->f32, q.n_down, q.n_up, 1);
+                    for (int c = 1; c < q.inner_cycles; c++) vcycle<float>(t, t->f32, top, q.n_down, q.n_up, 1);
+                } else {
+                    for (int c = 0; c < q.inner_cycles; c++) vcycle<float>(t, t->f32, top, q.n_down, q.n_up, 1);
+                }
+                add_e_to_phi(t, t->f32.X, t->f64.X);
+                residual_enqueue(t, t->f64, 0, nullptr, t->f32.F);
+            });
+            if (rc) return rc;
+            residual_wait(t, o);
             cycles++;
-            residual_norm(t, t->f64, 0, o, nullptr, t->f32.F);
             rel = std::sqrt(o[0] / o[1]) / r0;
             if (!std::isfinite(rel)) break;
         }
@@ -758,6 +833,8 @@ extern "C" int mg_tree_destroy(mg_tree *t) {
         cudaFree(t->d_blocks); cudaFree(t->d_levels); cudaFree(t->d_bcplanes);
         cudaFree(t->d_r64); cudaFree(t->d_minv); cudaFree(t->d_cvec); cudaFree(t->d_partials); cudaFree(t->d_red); cudaFree(t->d_status);
         cudaFreeHost(t->h_red);
+        drop_graphs(t);
+        if (t->cap_stream) cudaStreamDestroy(t->cap_stream);
     }
     delete t;
     return MG_OK;
