@@ -122,6 +122,7 @@ struct mg_tree {
     std::map<std::string, Graph> graphs;
     cudaStream_t cap_stream = nullptr;
     bool use_graphs = true;
+    std::vector<int> sweep_choice[2];  // autotuned sweep variant per level (FP64, FP32); -1 default
 };
 
 namespace mg {
@@ -130,6 +131,7 @@ template <class T> void vcycle(mg_tree *t, Fields<T> &F, int top, int nd, int nu
 template <class T> void fmg(mg_tree *t, Fields<T> &F, int nd, int nu, int homog);
 template <class T> void refresh(mg_tree *t, Fields<T> &F, int homog);
 template <class T> void refresh_eps(mg_tree *t, Fields<T> &F);
+template <class T> void tune_sweeps(mg_tree *t, Fields<T> &F);
 // composite residual of FP64 fields on the leaves; optional outputs:
 // r64 (FP64 leaf order), f32 (FP32 into the leaf cells of an FP32 field)
 void residual_norm(mg_tree *t, Fields<double> &F, int homog, double *out3, double *r64_leaf,

@@ -614,6 +614,315 @@ __global__ void __launch_bounds__(kMaxThreads, 5) k_sweep_tma(KParams P, int fir
     if (tid == 0) bulk_wait0();
 }
 
+// Warp-per-block variant of the TMA sweep for 8-cell blocks: each warp owns
+// a double-buffered stage and two mbarriers and walks its own blocks
+// (g = warp id, + all warps, ...), so the only synchronisation is within a
+// warp.  Same arithmetic and ghost pushes as k_sweep_tma.
+template <class T, int D, int WARPS>
+__global__ void __launch_bounds__(32 * WARPS) k_sweep_warp(KParams P, int first, int nblocks, Fields<T> F,
+                                                           int colour) {
+    constexpr int n = 8, C = cells_of<D>(8), FC = face_of<D>(8), GH = 2 * D * FC;
+    constexpr int NCOL = C / 2, PER = NCOL / 32;
+    constexpr int DESC = (int)(sizeof(BlockDesc) / sizeof(T));
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t bars[WARPS][2];
+    __shared__ __align__(16) LevelDesc sL;
+    const bool var = F.E != nullptr;
+    const int stage_elems = DESC + 2 * C + GH + (var ? C + GH : 0);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    T *wst = reinterpret_cast<T *>(smem_raw) + warp * 2 * stage_elems;
+    const uint32_t tx_bytes = (uint32_t)(sizeof(T) * stage_elems);
+    if (lane == 0) {
+        mbar_init(&bars[warp][0], 1);
+        mbar_init(&bars[warp][1], 1);
+        fence_mbar_init();
+    }
+    if (tid < (int)(sizeof(LevelDesc) / 4))
+        reinterpret_cast<int *>(&sL)[tid] = reinterpret_cast<const int *>(P.L + P.B[first].lev)[tid];
+    __syncthreads();
+    auto issue = [&](int it, int g) {  // lane 0 only
+        T *st = wst + (it & 1) * stage_elems;
+        const long long co = P.B[g].cell_off, go = P.B[g].ghost_off;
+        uint64_t *bar = &bars[warp][it & 1];
+        fence_async_smem();
+        mbar_expect_tx(bar, tx_bytes);
+        bulk_g2s(st, P.B + g, sizeof(BlockDesc), bar);
+        bulk_g2s(st + DESC, F.X + co, sizeof(T) * C, bar);
+        bulk_g2s(st + DESC + C, F.XG + go, sizeof(T) * GH, bar);
+        bulk_g2s(st + DESC + C + GH, F.F + co, sizeof(T) * C, bar);
+        if (var) {
+            bulk_g2s(st + DESC + 2 * C + GH, F.E + co, sizeof(T) * C, bar);
+            bulk_g2s(st + DESC + 3 * C + GH, F.EG + go, sizeof(T) * GH, bar);
+        }
+    };
+    const int stride = gridDim.x * WARPS;
+    int g = blockIdx.x * WARPS + warp;
+    if (lane == 0 && g < nblocks) issue(0, first + g);
+    const LevelDesc &L = sL;
+    const bool cyl = P.geom == MG_CYL;
+    const T helm = (T)P.helm;
+    const T w0 = (T)L.inv_h2[0], w1 = (T)L.inv_h2[1], w2 = (T)L.inv_h2[2];
+    const T inv_den = (T)1 / ((T)2 * (w0 + w1 + (D == 3 ? w2 : (T)0)) + helm);
+    for (int it = 0; g < nblocks; it++, g += stride) {
+        bool timed_out = false;
+        {
+            uint32_t tries = 0;
+            while (!mbar_try_wait(&bars[warp][it & 1], (it >> 1) & 1))
+                if (++tries > kWaitLimit) {
+                    timed_out = true;
+                    break;
+                }
+        }
+        if (__any_sync(0xffffffffu, timed_out)) {
+            if (lane == 0) atomicExch(P.status, 1);
+            break;
+        }
+        __syncwarp();
+        if (lane == 0 && g + stride < nblocks) {
+            bulk_wait_read0();
+            issue(it + 1, first + g + stride);
+        }
+        T *st = wst + (it & 1) * stage_elems;
+        const BlockDesc &b = *reinterpret_cast<const BlockDesc *>(st);
+        T *xs = st + DESC, *gs = xs + C, *fs = gs + GH, *es = fs + C, *egs = es + C;
+        const int bi = b.ijk[0], bj = b.ijk[1], bk = b.ijk[2];
+        const int par0 = (bi + bj + bk) * n;
+        auto nbv = [&](const T *xi, const T *gi, int i, int j, int k, int d, int s) -> T {
+            const int o = s ? 1 : -1;
+            if (d == 0) {
+                const int ii = i + o;
+                if (ii < 0 || ii >= n) return gi[(s ? 1 : 0) * FC + (D == 2 ? j : j + n * k)];
+                return xi[cidx<D>(n, ii, j, k)];
+            }
+            if (d == 1) {
+                const int jj = j + o;
+                if (jj < 0 || jj >= n) return gi[(s ? 3 : 2) * FC + (D == 2 ? i : i + n * k)];
+                return xi[cidx<D>(n, i, jj, k)];
+            }
+            const int kk = k + o;
+            if (kk < 0 || kk >= n) return gi[(s ? 5 : 4) * FC + i + n * j];
+            return xi[cidx<D>(n, i, j, kk)];
+        };
+#pragma unroll
+        for (int r = 0; r < PER; r++) {
+            const int qi = lane + 32 * r;
+            const int rr = qi >> 2, m = qi & 3;
+            const int j = rr % n, k = D == 3 ? rr / n : 0;
+            const int i = 2 * m + ((colour + par0 + j + k) & 1);
+            const int c = cidx<D>(n, i, j, k);
+            T xnew;
+            if (!var && !cyl) {
+                T num = w0 * (nbv(xs, gs, i, j, k, 0, 0) + nbv(xs, gs, i, j, k, 0, 1)) +
+                        w1 * (nbv(xs, gs, i, j, k, 1, 0) + nbv(xs, gs, i, j, k, 1, 1));
+                if (D == 3) num += w2 * (nbv(xs, gs, i, j, k, 2, 0) + nbv(xs, gs, i, j, k, 2, 1));
+                xnew = (num - fs[c]) * inv_den;
+            } else {
+                const T ec = var ? es[c] : (T)1;
+                T num = 0, den = 0, ri = 0;
+                if (cyl) ri = (T)(P.lo[0] + (bi * n + i + 0.5) * L.h[0]);
+#pragma unroll
+                for (int d = 0; d < D; d++)
+#pragma unroll
+                    for (int s = 0; s < 2; s++) {
+                        T w = (T)L.inv_h2[d];
+                        if (var) {
+                            const T en = nbv(es, egs, i, j, k, d, s);
+                            w *= (T)2 * ec * en / (ec + en);
+                        }
+                        if (cyl && d == 0) w *= (T)(P.lo[0] + (bi * n + i + s) * L.h[0]) / ri;
+                        num += w * nbv(xs, gs, i, j, k, d, s);
+                        den += w;
+                    }
+                xnew = (num - fs[c]) / (den + helm);
+            }
+            xs[c] = xnew;
+        }
+        fence_async_smem();
+        __syncwarp();
+        if (lane == 0) {
+            bulk_s2g(F.X + b.cell_off, xs, sizeof(T) * C);
+            bulk_commit();
+        }
+        for (int t = lane; t < GH; t += 32) {
+            const int face = t / FC, u = t - face * FC, d = face >> 1, s = face & 1;
+            const I3 ii = face_cell<D>(n, face, u, false);
+            const bool updated = ((par0 + ii.x + ii.y + ii.z) & 1) == colour;
+            const int nb = b.nbr[face];
+            if (nb >= 0) {
+                if (updated) F.XG[b.push[face] + u] = xs[cidx<D>(n, ii.x, ii.y, ii.z)];
+            } else if (nb == -1) {
+                if (updated)
+                    F.XG[b.ghost_off + t] = phys_ghost<T>(P, L, face, xs[cidx<D>(n, ii.x, ii.y, ii.z)],
+                                                          bc_value(P, L, b, D, face, ii));
+            } else {
+                I3 dd = ii;
+                put(dd, d, s ? n - 2 : 1);
+                F.XG[b.ghost_off + t] = cf_ghost<T, D>(P, L, b, face, ii, xs[cidx<D>(n, ii.x, ii.y, ii.z)],
+                                                       xs[cidx<D>(n, dd.x, dd.y, dd.z)], F.X, F.XG, nb, false);
+            }
+        }
+    }
+    if (lane == 0) bulk_wait0();
+}
+
+// Row-wise variant of the warp-per-block sweep for 8^3 blocks with a
+// constant coefficient (Cartesian): lane l updates x-rows l and l + 32 of
+// the block.  A row, its four neighbour rows (or the matching contiguous
+// ghost rows on the block faces) and its right-hand side come in with
+// 16-byte shared-memory loads; the colour cells of the row are chosen by
+// register selects.  Ghost pushes go face by face, one updated face cell
+// per lane.  Same arithmetic as k_sweep_tma.
+template <class T> __device__ __forceinline__ void ld8(const T *p, T *r) {
+    using V = typename Vec16<T>::type;
+    constexpr int VW = 16 / sizeof(T);
+#pragma unroll
+    for (int v = 0; v < 8 / VW; v++) {
+        const V x = reinterpret_cast<const V *>(p)[v];
+        if constexpr (sizeof(T) == 4) { r[4 * v] = x.x; r[4 * v + 1] = x.y; r[4 * v + 2] = x.z; r[4 * v + 3] = x.w; }
+        else { r[2 * v] = x.x; r[2 * v + 1] = x.y; }
+    }
+}
+template <class T> __device__ __forceinline__ void st8(T *p, const T *r) {
+    using V = typename Vec16<T>::type;
+    constexpr int VW = 16 / sizeof(T);
+#pragma unroll
+    for (int v = 0; v < 8 / VW; v++) {
+        if constexpr (sizeof(T) == 4) reinterpret_cast<V *>(p)[v] = make_float4(r[4 * v], r[4 * v + 1], r[4 * v + 2], r[4 * v + 3]);
+        else reinterpret_cast<V *>(p)[v] = make_double2(r[2 * v], r[2 * v + 1]);
+    }
+}
+
+template <class T, int WARPS, int STAGES>
+__global__ void __launch_bounds__(32 * WARPS) k_sweep_rows(KParams P, int first, int nblocks, Fields<T> F,
+                                                           int colour) {
+    constexpr int n = 8, C = 512, FC = 64, GH = 384;
+    constexpr int DESC = (int)(sizeof(BlockDesc) / sizeof(T));
+    constexpr int STAGE = DESC + 2 * C + GH;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t bars[WARPS][STAGES];
+    __shared__ __align__(16) LevelDesc sL;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    T *wst = reinterpret_cast<T *>(smem_raw) + warp * STAGES * STAGE;
+    if (lane == 0) {
+        for (int q = 0; q < STAGES; q++) mbar_init(&bars[warp][q], 1);
+        fence_mbar_init();
+    }
+    if (tid < (int)(sizeof(LevelDesc) / 4))
+        reinterpret_cast<int *>(&sL)[tid] = reinterpret_cast<const int *>(P.L + P.B[first].lev)[tid];
+    __syncthreads();
+    auto issue = [&](int it, int g) {  // lane 0 only
+        T *st = wst + (it % STAGES) * STAGE;
+        const long long co = P.B[g].cell_off, go = P.B[g].ghost_off;
+        uint64_t *bar = &bars[warp][it % STAGES];
+        fence_async_smem();
+        mbar_expect_tx(bar, (uint32_t)(sizeof(T) * STAGE));
+        bulk_g2s(st, P.B + g, sizeof(BlockDesc), bar);
+        bulk_g2s(st + DESC, F.X + co, sizeof(T) * C, bar);
+        bulk_g2s(st + DESC + C, F.XG + go, sizeof(T) * GH, bar);
+        bulk_g2s(st + DESC + C + GH, F.F + co, sizeof(T) * C, bar);
+    };
+    const int stride = gridDim.x * WARPS;
+    int g = blockIdx.x * WARPS + warp;
+    if (lane == 0)
+        for (int q = 0; q < STAGES - 1; q++)
+            if (g + q * stride < nblocks) issue(q, first + g + q * stride);
+    const LevelDesc &L = sL;
+    const T helm = (T)P.helm;
+    const T w0 = (T)L.inv_h2[0], w1 = (T)L.inv_h2[1], w2 = (T)L.inv_h2[2];
+    const T inv_den = (T)1 / ((T)2 * (w0 + w1 + w2) + helm);
+    for (int it = 0; g < nblocks; it++, g += stride) {
+        bool timed_out = false;
+        {
+            uint32_t tries = 0;
+            while (!mbar_try_wait(&bars[warp][it % STAGES], (it / STAGES) & 1))
+                if (++tries > kWaitLimit) {
+                    timed_out = true;
+                    break;
+                }
+        }
+        if (__any_sync(0xffffffffu, timed_out)) {
+            if (lane == 0) atomicExch(P.status, 1);
+            break;
+        }
+        __syncwarp();
+        // refill the stage of block it-1 (every lane is past it) with block it+STAGES-1
+        if (lane == 0 && g + (STAGES - 1) * stride < nblocks) {
+            bulk_wait_read0();
+            issue(it + STAGES - 1, first + g + (STAGES - 1) * stride);
+        }
+        T *st = wst + (it % STAGES) * STAGE;
+        const BlockDesc &b = *reinterpret_cast<const BlockDesc *>(st);
+        T *xs = st + DESC, *gs = xs + C, *fs = gs + GH;
+        const int par0 = (b.ijk[0] + b.ijk[1] + b.ijk[2]) * n;
+        T newrow[2][8];
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+            const int q = lane + 32 * h, j = q & 7, k = q >> 3;
+            T r[8], dn[8], up[8], bk[8], fw[8], fr[8];
+            ld8(xs + 8 * q, r);
+            ld8(j > 0 ? xs + 8 * (q - 1) : gs + 2 * FC + 8 * k, dn);
+            ld8(j < 7 ? xs + 8 * (q + 1) : gs + 3 * FC + 8 * k, up);
+            ld8(k > 0 ? xs + 8 * (q - 8) : gs + 4 * FC + 8 * j, bk);
+            ld8(k < 7 ? xs + 8 * (q + 8) : gs + 5 * FC + 8 * j, fw);
+            ld8(fs + 8 * q, fr);
+            const T xl = gs[0 * FC + j + 8 * k], xr = gs[1 * FC + j + 8 * k];
+            const bool p = ((colour + par0 + j + k) & 1) != 0;  // colour cells at i = 2m + p
+#pragma unroll
+            for (int m = 0; m < 4; m++) {
+                const int e = 2 * m, o = 2 * m + 1;
+                const T xm = p ? r[e] : (m > 0 ? r[e - 1] : xl);
+                const T xp = p ? (m < 3 ? r[o + 1] : xr) : r[o];
+                const T sy = p ? dn[o] + up[o] : dn[e] + up[e];
+                const T sz = p ? bk[o] + fw[o] : bk[e] + fw[e];
+                const T fv = p ? fr[o] : fr[e];
+                const T num = w0 * (xm + xp) + w1 * sy + w2 * sz;
+                const T xnew = (num - fv) * inv_den;
+                newrow[h][e] = p ? r[e] : xnew;
+                newrow[h][o] = p ? xnew : r[o];
+            }
+        }
+        // every lane has read its neighbour rows: write the rows back
+        __syncwarp();
+#pragma unroll
+        for (int h = 0; h < 2; h++) st8(xs + 8 * (lane + 32 * h), newrow[h]);
+        fence_async_smem();
+        __syncwarp();
+        if (lane == 0) {
+            bulk_s2g(F.X + b.cell_off, xs, sizeof(T) * C);
+            bulk_commit();
+        }
+        // ghost pushes, one face at a time (warp-uniform face type)
+#pragma unroll 1
+        for (int face = 0; face < 6; face++) {
+            const int d = face >> 1, s = face & 1, nb = b.nbr[face];
+            const int edge = s ? n - 1 : 0;
+            if (nb <= -2) {
+#pragma unroll
+                for (int h = 0; h < 2; h++) {
+                    const int u = 2 * lane + h, t1 = u & 7, t2 = u >> 3;
+                    const I3 ii = d == 0 ? I3{edge, t1, t2} : (d == 1 ? I3{t1, edge, t2} : I3{t1, t2, edge});
+                    I3 dd = ii;
+                    put(dd, d, s ? n - 2 : 1);
+                    F.XG[b.ghost_off + face * FC + u] =
+                        cf_ghost<T, 3>(P, L, b, face, ii, xs[cidx<3>(n, ii.x, ii.y, ii.z)],
+                                       xs[cidx<3>(n, dd.x, dd.y, dd.z)], F.X, F.XG, nb, false);
+                }
+                continue;
+            }
+            // the lane's updated face cell: tangential row t2 = lane / 4, 4 per row
+            const int t2 = lane >> 2;
+            const int po = (colour + par0 + edge + t2) & 1;
+            const int t1 = 2 * (lane & 3) + po;
+            const I3 ii = d == 0 ? I3{edge, t1, t2} : (d == 1 ? I3{t1, edge, t2} : I3{t1, t2, edge});
+            const int u = t1 + 8 * t2;
+            const T xi = xs[cidx<3>(n, ii.x, ii.y, ii.z)];
+            if (nb >= 0) F.XG[b.push[face] + u] = xi;
+            else F.XG[b.ghost_off + face * FC + u] = phys_ghost<T>(P, L, face, xi, bc_value(P, L, b, 3, face, ii));
+        }
+    }
+    if (lane == 0) bulk_wait0();
+}
+
 // ------------------------------------------------------- transfers ------
 // Restriction (Sec. 2.3): the parent cells under fine block b receive the
 // mean of their 2^D children; with_res also stores the mean of the child
@@ -1436,29 +1745,114 @@ template <class T, int D> struct Launch {
         ++t->launches;
         k_ghost<T, D><<<L.nb, threads_for(2 * D * face_of<D>(L.n)), 0, t->stream>>>(P, L.first, X, XG, mode);
     }
-    // one fused launch per colour (k_sweep), specialised for 8- and 16-cell blocks
+    // Sweep variants (candidate ids for the autotuner):
+    //  0 persistent CTA-per-block TMA sweep (8- and 16-cell blocks)
+    //  1 CTA-per-block sweep with plain loads (any block size)
+    //  2 / 3 warp-per-block TMA sweep, 8 / 4 warps per CTA (8-cell blocks)
+    //  4 / 5 row-wise warp sweep, 8 warps x 2 stages / 4 warps x 3 stages
+    //        (8^3 blocks, constant coefficient, Cartesian)
+    static size_t cand_smem(mg_tree *t, int l, Fields<T> &F, int cand) {
+        const int n = t->lev[l].n, C = cells_of<D>(n), GH = 2 * D * face_of<D>(n);
+        const size_t stage = sizeof(BlockDesc) + sizeof(T) * (2 * C + GH + (F.E ? C + GH : 0));
+        switch (cand) {
+        case 0: return (n == 8 || n == 16) ? 2 * stage : 0;
+        case 1: return 1;
+        case 2: return n == 8 ? 16 * stage : 0;
+        case 3: return n == 8 ? 8 * stage : 0;
+        case 4: return (D == 3 && n == 8 && !F.E && t->geom == MG_CART) ? 16 * stage : 0;
+        case 5: return (D == 3 && n == 8 && !F.E && t->geom == MG_CART) ? 12 * stage : 0;
+        }
+        return 0;
+    }
+    static bool cand_ok(mg_tree *t, int l, Fields<T> &F, int cand) {
+        const size_t sm = cand_smem(t, l, F, cand);
+        return sm > 0 && sm <= 200 * 1024;
+    }
+    static int default_cand(mg_tree *t, int l, Fields<T> &F) {
+        for (int c : {4, 0}) if (cand_ok(t, l, F, c)) return c;
+        return 1;
+    }
     static void sweep(mg_tree *t, const KParams &P, int l, Fields<T> &F, int colour) {
         const LevelHost &L = t->lev[l];
-        const int n = L.n, pad = D == 2 ? (n + 2) * (n + 2) : (n + 2) * (n + 2) * (n + 2);
-        const size_t sm = sizeof(T) * pad * (F.E ? 2 : 1);
-        const int th = threads_for((n & 1) ? cells_of<D>(n) : cells_of<D>(n) / 2);
+        const int prec = sizeof(T) == 4 ? 1 : 0;
+        int cand = (int)t->sweep_choice[prec].size() > l ? t->sweep_choice[prec][l] : -1;
+        if (cand < 0 || !cand_ok(t, l, F, cand)) cand = default_cand(t, l, F);
+        sweep_cand(t, P, l, F, colour, cand);
+        (void)L;
+    }
+    static void sweep_cand(mg_tree *t, const KParams &P, int l, Fields<T> &F, int colour, int cand) {
+        const LevelHost &L = t->lev[l];
+        const int n = L.n;
         ++t->launches;
-        const int C = cells_of<D>(n), GH = 2 * D * face_of<D>(n);
-        const size_t smt = 2 * (sizeof(BlockDesc) + sizeof(T) * (2 * C + GH + (F.E ? C + GH : 0)));
-        if ((n == 8 || n == 16) && smt <= 200 * 1024) {
-            const int thr = threads_for(C / 2);
+        const size_t sm = cand_smem(t, l, F, cand);
+        switch (cand) {
+        case 0: {
             auto kern = n == 8 ? k_sweep_tma<T, D, 8> : k_sweep_tma<T, D, 16>;
-            const int grid = std::min(L.nb, resident_ctas(kern, thr, smt) * t->nsm);
-            kern<<<grid, thr, smt, t->stream>>>(P, L.first, L.nb, F, colour);
-        } else if (n == 8) {
-            k_sweep<T, D, 8><<<L.nb, th, sm, t->stream>>>(P, L.first, F, colour);
-        } else if (n == 16) {
-            set_smem(k_sweep<T, D, 16>, sm);
-            k_sweep<T, D, 16><<<L.nb, th, sm, t->stream>>>(P, L.first, F, colour);
-        } else {
-            set_smem(k_sweep<T, D, 0>, sm);
-            k_sweep<T, D, 0><<<L.nb, th, sm, t->stream>>>(P, L.first, F, colour);
+            const int thr = threads_for(cells_of<D>(n) / 2);
+            const int grid = std::min(L.nb, resident_ctas(kern, thr, sm) * t->nsm);
+            kern<<<grid, thr, sm, t->stream>>>(P, L.first, L.nb, F, colour);
+            return;
         }
+        case 2: case 3: {
+            const int W = cand == 2 ? 8 : 4;
+            auto kern = cand == 2 ? k_sweep_warp<T, D, 8> : k_sweep_warp<T, D, 4>;
+            const int grid = std::min((L.nb + W - 1) / W, resident_ctas(kern, 32 * W, sm) * t->nsm);
+            kern<<<grid, 32 * W, sm, t->stream>>>(P, L.first, L.nb, F, colour);
+            return;
+        }
+        case 4: case 5: {
+            if constexpr (D == 3) {
+                const int W = cand == 4 ? 8 : 4;
+                auto kern = cand == 4 ? k_sweep_rows<T, 8, 2> : k_sweep_rows<T, 4, 3>;
+                const int grid = std::min((L.nb + W - 1) / W, resident_ctas(kern, 32 * W, sm) * t->nsm);
+                kern<<<grid, 32 * W, sm, t->stream>>>(P, L.first, L.nb, F, colour);
+            }
+            return;
+        }
+        default: {
+            const int pad = D == 2 ? (n + 2) * (n + 2) : (n + 2) * (n + 2) * (n + 2);
+            const size_t smp = sizeof(T) * pad * (F.E ? 2 : 1);
+            const int th = threads_for((n & 1) ? cells_of<D>(n) : cells_of<D>(n) / 2);
+            if (n == 8) {
+                k_sweep<T, D, 8><<<L.nb, th, smp, t->stream>>>(P, L.first, F, colour);
+            } else if (n == 16) {
+                set_smem(k_sweep<T, D, 16>, smp);
+                k_sweep<T, D, 16><<<L.nb, th, smp, t->stream>>>(P, L.first, F, colour);
+            } else {
+                set_smem(k_sweep<T, D, 0>, smp);
+                k_sweep<T, D, 0><<<L.nb, th, smp, t->stream>>>(P, L.first, F, colour);
+            }
+        }
+        }
+    }
+    // Autotuner: per level, time every applicable sweep variant on the
+    // given fields (all zero at the call sites, so sweeps leave them
+    // unchanged) and keep the fastest.  Small levels keep the default.
+    static void tune(mg_tree *t, Fields<T> &F) {
+        const int prec = sizeof(T) == 4 ? 1 : 0;
+        const KParams P = kparams(t, 1);
+        t->sweep_choice[prec].assign(t->lev.size(), -1);
+        cudaEvent_t e0, e1;
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        for (size_t l = 1; l < t->lev.size(); l++) {
+            if (t->lev[l].nb < 256) continue;
+            float best = 1e30f;
+            for (int cand = 0; cand < 6; cand++) {
+                if (!cand_ok(t, (int)l, F, cand)) continue;
+                for (int w = 0; w < 2; w++) sweep_cand(t, P, (int)l, F, w & 1, cand);
+                cudaEventRecord(e0, t->stream);
+                for (int w = 0; w < 4; w++) sweep_cand(t, P, (int)l, F, w & 1, cand);
+                cudaEventRecord(e1, t->stream);
+                cudaEventSynchronize(e1);
+                float ms = 0;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (ms < best) { best = ms; t->sweep_choice[prec][l] = cand; }
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        cudaGetLastError();
     }
     static void smooth(mg_tree *t, const KParams &P, int l, Fields<T> &F, int sweeps) {
         for (int s = 0; s < sweeps; s++)
@@ -1571,6 +1965,12 @@ template <class T, int D> struct Launch {
     }
 };
 
+template <class T> void tune_sweeps(mg_tree *t, Fields<T> &F) {
+    if (t->dim == 2) Launch<T, 2>::tune(t, F);
+    else Launch<T, 3>::tune(t, F);
+}
+template void tune_sweeps<double>(mg_tree *, Fields<double> &);
+template void tune_sweeps<float>(mg_tree *, Fields<float> &);
 template <class T> void vcycle(mg_tree *t, Fields<T> &F, int top, int nd, int nu, int homog) {
     if (t->dim == 2) Launch<T, 2>::vcycle(t, F, top, nd, nu, homog);
     else Launch<T, 3>::vcycle(t, F, top, nd, nu, homog);

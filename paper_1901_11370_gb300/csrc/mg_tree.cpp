@@ -501,6 +501,8 @@ extern "C" int mg_tree_finalize(mg_tree *t, void *stream) {
     CK(cudaStreamCreateWithFlags(&t->cap_stream, cudaStreamNonBlocking));
     t->finalized = true;
     if ((rc = build_coarse_inverse(t))) return rc;
+    tune_sweeps<double>(t, t->f64);  // fields and ghosts are still zero here
+    CK(cudaMemsetAsync(t->f64.X, 0, sizeof(double) * t->ncells, t->stream));
     refresh<double>(t, t->f64, 0);
     return check_cuda("finalize");
 }
@@ -686,9 +688,14 @@ extern "C" int mg_residual_norm(mg_tree *t, double *l2, double *linf, double *de
 
 static int ensure_f32(mg_tree *t) {
     int rc;
-    if (!t->f32.X) drop_graphs(t);
+    const bool fresh = !t->f32.X;
+    if (fresh) drop_graphs(t);
     if ((rc = alloc_fields(t, t->f32, t->var_eps))) return rc;
     if (t->var_eps) copy_eps_to_f32(t);
+    if (fresh) {
+        tune_sweeps<float>(t, t->f32);  // freshly zeroed fields: the sweeps leave them zero
+        if ((rc = check_cuda("tune"))) return rc;
+    }
     return MG_OK;
 }
 
