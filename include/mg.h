@@ -173,6 +173,11 @@ int mg_adjoint(mg_tree *t, const double *dev_dLdphi, double *dev_dLdf, double *d
  * fill (read the source cells, write the ghosts once).  Synchronises.
  */
 int mg_launch_count(mg_tree *t, int64_t *n);
+/* mg_sweep_variant: the sweep kernel variant the autotuner chose for a level
+ * and precision (MG_FP64 / MG_FP32_DC): 0 persistent CTA-per-block TMA,
+ * 1 CTA-per-block plain loads, 2 / 3 warp-per-block TMA (8 / 4 warps),
+ * 4 / 5 row-wise warp TMA (8 warps x 2 stages / 4 warps x 3 stages). */
+int mg_sweep_variant(mg_tree *t, int precision, int level, int *variant);
 int mg_time_sweeps(mg_tree *t, int level, int n_sweeps, int precision, double out[4]);
 
 /*

@@ -160,6 +160,15 @@ class Tree:
         check(self.L.mg_launch_count(self._h, C.byref(n)))
         return n.value
 
+    SWEEP_VARIANTS = {0: "k_sweep_tma (CTA per block)", 1: "k_sweep (plain loads)", 2: "k_sweep_warp<8 warps>",
+                      3: "k_sweep_warp<4 warps>", 4: "k_sweep_rows<8 warps, 2 stages>",
+                      5: "k_sweep_rows<4 warps, 3 stages>", -1: "untuned"}
+
+    def sweep_variant(self, level, precision=MG_FP64):
+        v = C.c_int()
+        check(self.L.mg_sweep_variant(self._h, precision, level, C.byref(v)))
+        return v.value
+
     def time_sweeps(self, level=-1, n_sweeps=4, precision=MG_FP64):
         """(ms per sweep launch, ms per full ghost fill, bytes per sweep
         launch, bytes per ghost fill) on one level (default: the largest)."""

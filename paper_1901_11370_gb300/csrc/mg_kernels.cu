@@ -1970,6 +1970,17 @@ template <class T> void tune_sweeps(mg_tree *t, Fields<T> &F) {
     else Launch<T, 3>::tune(t, F);
 }
 template void tune_sweeps<double>(mg_tree *, Fields<double> &);
+int sweep_variant(mg_tree *t, int prec, int level) {
+    if (prec == 1 && !t->f32.X) return -1;
+    if (t->dim == 2) {
+        int c = (int)t->sweep_choice[prec].size() > level ? t->sweep_choice[prec][level] : -1;
+        if (prec == 1) return c >= 0 && Launch<float, 2>::cand_ok(t, level, t->f32, c) ? c : Launch<float, 2>::default_cand(t, level, t->f32);
+        return c >= 0 && Launch<double, 2>::cand_ok(t, level, t->f64, c) ? c : Launch<double, 2>::default_cand(t, level, t->f64);
+    }
+    int c = (int)t->sweep_choice[prec].size() > level ? t->sweep_choice[prec][level] : -1;
+    if (prec == 1) return c >= 0 && Launch<float, 3>::cand_ok(t, level, t->f32, c) ? c : Launch<float, 3>::default_cand(t, level, t->f32);
+    return c >= 0 && Launch<double, 3>::cand_ok(t, level, t->f64, c) ? c : Launch<double, 3>::default_cand(t, level, t->f64);
+}
 template void tune_sweeps<float>(mg_tree *, Fields<float> &);
 template <class T> void vcycle(mg_tree *t, Fields<T> &F, int top, int nd, int nu, int homog) {
     if (t->dim == 2) Launch<T, 2>::vcycle(t, F, top, nd, nu, homog);

@@ -816,6 +816,14 @@ extern "C" int mg_launch_count(mg_tree *t, int64_t *n) {
     return MG_OK;
 }
 
+extern "C" int mg_sweep_variant(mg_tree *t, int precision, int level, int *variant) {
+    NEED_FINAL(t);
+    if (!variant || level < 0 || level >= (int)t->lev.size() || (precision != MG_FP64 && precision != MG_FP32_DC))
+        return fail(MG_ERR_ARG, "bad arguments");
+    *variant = sweep_variant(t, precision == MG_FP32_DC ? 1 : 0, level);
+    return MG_OK;
+}
+
 static int ensure_f32(mg_tree *t);
 
 extern "C" int mg_time_sweeps(mg_tree *t, int level, int n_sweeps, int precision, double out[4]) {
