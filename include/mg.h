@@ -160,6 +160,21 @@ int mg_adjoint(mg_tree *t, const double *dev_dLdphi, double *dev_dLdf, double *d
                const mg_params *p, int n_cycles);
 
 /*
+ * Divergence cleaning (Sec. 4.1, eqs. for the projection method and the
+ * central-difference divergence), Cartesian meshes:
+ * mg_divergence: dev_divB = sum_d (B_d(c+e_d) - B_d(c-e_d)) / (2 h_d) on the
+ *   leaf cells.  dev_B holds dim leaf arrays (x, y[, z]) back to back; each
+ *   component is restricted to covered cells and ghost-filled with the rules
+ *   of Sec. 2.6 (physical faces copy the interior value).
+ * mg_project: dev_Bnew = dev_B - grad phi with second-order central
+ *   differences of the current phi (dim leaf arrays back to back).
+ * A cleaning step is mg_divergence, mg_set_rhs (projected to zero mean when
+ * no face is Dirichlet), mg_solve and mg_project.
+ */
+int mg_divergence(mg_tree *t, const double *dev_B, double *dev_divB);
+int mg_project(mg_tree *t, const double *dev_B, double *dev_Bnew);
+
+/*
  * Instrumentation (the paper has no counterpart; used by the benchmark).
  * mg_launch_count: number of CUDA kernels this tree has launched so far.
  * mg_time_sweeps: runs n_sweeps red-black sweeps on `level` of the FP64

@@ -67,6 +67,8 @@ def _load():
     L.or_level_io.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_int]
     L.or_level_blocks.argtypes = [C.c_void_p, C.c_int, _ip, _ip, _ip]
     L.or_step.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int]
+    L.or_divergence.argtypes = [C.c_void_p, _dp, _dp]
+    L.or_project.argtypes = [C.c_void_p, _dp, _dp]
     _lib = L
     return L
 
@@ -90,6 +92,7 @@ class Oracle:
         self.L = L
         self.dim = dim
         self.cyl = geom == 1
+        self._singular = all(int(t) != 0 for t in list(bc_type)[:2 * dim])
         self._rhs = np.zeros(int(L.or_num_leaf_cells(self._h)))
         self.n_leaf = int(L.or_num_leaf_cells(self._h))
 
@@ -195,6 +198,35 @@ class Oracle:
         if self.L.or_eps_grad(self._h, np.ascontiguousarray(lam, np.float64), out) != 0:
             raise ValueError("oracle: " + self.L.or_last_error().decode())
         return out
+
+    # ------------------------------------------------ divergence cleaning --
+    def divergence(self, B):
+        """Second-order central divergence of a leaf vector field (dim, n_leaf)."""
+        B = np.ascontiguousarray(B, np.float64).reshape(self.dim, self.n_leaf)
+        out = np.zeros(self.n_leaf)
+        if self.L.or_divergence(self._h, B.ravel(), out) != 0:
+            raise ValueError("oracle: " + self.L.or_last_error().decode())
+        return out
+
+    def project(self, B):
+        """B - grad(phi) with the current phi (central differences)."""
+        B = np.ascontiguousarray(B, np.float64).reshape(self.dim, self.n_leaf)
+        out = np.zeros_like(B)
+        if self.L.or_project(self._h, B.ravel(), out.ravel()) != 0:
+            raise ValueError("oracle: " + self.L.or_last_error().decode())
+        return out
+
+    def clean(self, B, rel_tol=1e-12, max_cycles=60):
+        """Divergence cleaning (Sec. 4.1): solve Lap phi = div B (right-hand side
+        projected to zero volume-weighted mean when no face is Dirichlet), then
+        B - grad phi.  Returns (B_new, div B, cycles)."""
+        f = self.divergence(B)
+        vol, _ = self.leaf_geometry()
+        if self._singular:
+            f = f - np.dot(vol, f) / vol.sum()
+        self.set_rhs(f)
+        cycles, _ = self.solve(rel_tol, max_cycles)
+        return self.project(B), f, cycles
 
     # -------------------------------------------------------- test hooks --
     FIELDS = {"phi": 0, "f": 1, "eps": 2, "vold": 3, "lam": 4}

@@ -48,7 +48,7 @@
 
 enum { GEOM_CART = 0, GEOM_CYL = 1 };
 enum { BC_DIR = 0, BC_NEU = 1, BC_PER = 2, BC_AXIS = 3 };
-enum { F_PHI = 0, F_EPS = 1, F_LAM = 2 };
+enum { F_PHI = 0, F_EPS = 1, F_LAM = 2, F_VEC = 3 };
 
 typedef struct {
     int n;        /* cells per block edge */
@@ -94,7 +94,7 @@ static int pidx(const Tree *T, int n, int i, int j, int k) {
     return ((k + 1) * (n + 2) + (j + 1)) * (n + 2) + (i + 1);
 }
 static double *fld(Lev *lv, int which) {
-    return which == F_PHI ? lv->phi : which == F_EPS ? lv->eps : lv->lam;
+    return which == F_PHI ? lv->phi : which == F_EPS ? lv->eps : lv->lam;  /* F_VEC uses lam storage */
 }
 static int mapidx(const Lev *lv, const int *q) {
     return (q[2] * lv->nblk[1] + q[1]) * lv->nblk[0] + q[0];
@@ -399,7 +399,7 @@ static void ghost_fill(Tree *T, int l, int which) {
                         double xi = xb[pidx(T, n, ii[0], ii[1], ii[2])];
                         if (phys) {
                             int G[3]; cell_global(lv, b, ii[0], ii[1], ii[2], G);
-                            if (which == F_EPS) { *g = xi; continue; }
+                            if (which == F_EPS || which == F_VEC) { *g = xi; continue; }
                             int hom = T->homog || which == F_LAM;
                             double v = hom ? 0.0 : bc_value(T, lv, face, G);
                             switch (T->bct[face]) {
@@ -988,6 +988,79 @@ int or_step(void *h, int op, int l, int arg) {
     case 3: prolong_correct(T, l); break;
     case 4: coarse_solve(T); break;
     default: return -1;
+    }
+    return 0;
+}
+
+/* ------------------------------------------------ divergence cleaning --- */
+
+/*
+ * Cell-centred second-order divergence of a vector field given on the leaf
+ * cells (Sec. 4.1, eq. for the central-difference divergence):
+ * div B = sum_d (B_d(c + e_d) - B_d(c - e_d)) / (2 h_d).  Each component is
+ * restricted to covered cells and ghost-filled with the rules of Sec. 2.6
+ * (refinement ghosts interpolated like phi; physical faces copy the interior
+ * value).  B holds dim leaf arrays back to back.  Cartesian meshes only.
+ */
+int or_divergence(void *h, const double *B, double *out) {
+    Tree *T = h;
+    if (T->geom != GEOM_CART) { snprintf(g_err, sizeof g_err, "divergence: Cartesian meshes only"); return -1; }
+    int64_t nl = or_num_leaf_cells(h);
+    for (int64_t m = 0; m < nl; m++) out[m] = 0.0;
+    for (int d = 0; d < T->dim; d++) {
+        leaf_loop(T, (double *)(B + (size_t)d * nl), 3, 0);
+        refresh_field(T, F_VEC);
+        int64_t m = 0;
+        for (int l = 0; l < T->nlev; l++) {
+            Lev *lv = &T->L[l];
+            int n = lv->n, ps = P(T, n), nk = T->dim == 3 ? n : 1;
+            for (int b = 0; b < lv->nb; b++) {
+                if (lv->haschild[b]) continue;
+                const double *x = lv->lam + (size_t)b * ps;
+                for (int k = 0; k < nk; k++)
+                    for (int j = 0; j < n; j++)
+                        for (int i = 0; i < n; i++) {
+                            int qm[3] = {i, j, k}, qp[3] = {i, j, k};
+                            qm[d] -= 1; qp[d] += 1;
+                            out[m++] += (x[pidx(T, n, qp[0], qp[1], qp[2])] - x[pidx(T, n, qm[0], qm[1], qm[2])]) /
+                                        (2.0 * lv->h[d]);
+                        }
+            }
+        }
+    }
+    return 0;
+}
+
+/*
+ * Projection step B_new = B - grad phi (Sec. 4.1, eq. for the cleaned field),
+ * grad phi by second-order central differences of the current phi (ghosts
+ * from the refresh of phi).  Cartesian meshes only.
+ */
+int or_project(void *h, const double *B, double *out) {
+    Tree *T = h;
+    if (T->geom != GEOM_CART) { snprintf(g_err, sizeof g_err, "projection: Cartesian meshes only"); return -1; }
+    refresh(T);
+    int64_t nl = or_num_leaf_cells(h);
+    for (int d = 0; d < T->dim; d++) {
+        int64_t m = 0;
+        for (int l = 0; l < T->nlev; l++) {
+            Lev *lv = &T->L[l];
+            int n = lv->n, ps = P(T, n), nk = T->dim == 3 ? n : 1;
+            for (int b = 0; b < lv->nb; b++) {
+                if (lv->haschild[b]) continue;
+                const double *x = lv->phi + (size_t)b * ps;
+                for (int k = 0; k < nk; k++)
+                    for (int j = 0; j < n; j++)
+                        for (int i = 0; i < n; i++) {
+                            int qm[3] = {i, j, k}, qp[3] = {i, j, k};
+                            qm[d] -= 1; qp[d] += 1;
+                            double gd = (x[pidx(T, n, qp[0], qp[1], qp[2])] - x[pidx(T, n, qm[0], qm[1], qm[2])]) /
+                                        (2.0 * lv->h[d]);
+                            out[(size_t)d * nl + m] = B[(size_t)d * nl + m] - gd;
+                            m++;
+                        }
+            }
+        }
     }
     return 0;
 }

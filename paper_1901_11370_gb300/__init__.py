@@ -155,6 +155,43 @@ class Tree:
         check(rc, allow=() if raise_on_fail else (-4,))
         return cyc.value, rel.value
 
+    # ------------------------------------------------ divergence cleaning --
+    def divergence(self, B):
+        """Central-difference divergence of a leaf vector field (dim, n_leaf)."""
+        B = B.contiguous().view(-1)
+        assert B.numel() == self.dim * self.n_leaf
+        out = torch.empty(self.n_leaf, dtype=torch.float64, device="cuda")
+        check(self.L.mg_divergence(self._h, _ptr(B), _ptr(out)))
+        return out
+
+    def project(self, B):
+        """B - grad(phi) with the current phi."""
+        B = B.contiguous().view(-1)
+        assert B.numel() == self.dim * self.n_leaf
+        out = torch.empty_like(B)
+        check(self.L.mg_project(self._h, _ptr(B), _ptr(out)))
+        return out.view(self.dim, self.n_leaf)
+
+    def leaf_volumes(self):
+        """Cell volume of every leaf cell (Cartesian), leaf order, on the GPU."""
+        lv = {l["depth"]: np.prod(l["h"][:self.dim]) for l in self.levels()}
+        lb = self.leaf_blocks()
+        per = self.n_leaf // len(lb)
+        return torch.from_numpy(np.repeat([lv[int(d)] for d in lb[:, 0]], per)).cuda()
+
+    def clean(self, B, rel_tol=1e-10, max_cycles=60, precision=MG_FP64, singular=False):
+        """Divergence cleaning (Sec. 4.1): Lap phi = div B, then B - grad phi.
+        singular (no Dirichlet face): the right-hand side is first projected
+        to zero volume-weighted mean.  Returns (B_new, div B, cycles, rel)."""
+        f = self.divergence(B)
+        if singular:
+            vol = self.leaf_volumes()
+            f = f - torch.dot(vol, f) / vol.sum()
+        self.set_rhs(f.contiguous())
+        self.set_phi(torch.zeros_like(f))
+        cyc, rel = self.solve(rel_tol, max_cycles, fmg_first=True, precision=precision, raise_on_fail=False)
+        return self.project(B), f, cyc, rel
+
     def launch_count(self):
         n = C.c_int64()
         check(self.L.mg_launch_count(self._h, C.byref(n)))
@@ -188,4 +225,4 @@ class Tree:
         return dLdf, dLde
 
 
-from .autograd import MGSolve  # noqa: E402,F401
+from .autograd import CleanB, MGSolve  # noqa: E402,F401

@@ -19,7 +19,8 @@ EXPORTS = ["mg_tree_create", "mg_tree_refine", "mg_tree_num_levels", "mg_tree_le
            "mg_tree_num_leaf_cells", "mg_tree_leaf_blocks", "mg_set_bc_plane", "mg_tree_finalize",
            "mg_set_rhs", "mg_set_eps", "mg_set_phi", "mg_get_phi", "mg_vcycle", "mg_fmg",
            "mg_residual_norm", "mg_solve", "mg_adjoint", "mg_tree_destroy", "mg_last_error",
-           "mg_launch_count", "mg_time_sweeps", "mg_residual_norm_noalloc", "mg_sweep_variant"]
+           "mg_launch_count", "mg_time_sweeps", "mg_residual_norm_noalloc", "mg_sweep_variant",
+           "mg_divergence", "mg_project"]
 
 
 class MGError(RuntimeError):
@@ -69,6 +70,8 @@ def load():
     L.mg_time_sweeps.argtypes = [vp, C.c_int, C.c_int, C.c_int, dp]
     L.mg_residual_norm_noalloc.argtypes = [vp, dp, dp]
     L.mg_sweep_variant.argtypes = [vp, C.c_int, C.c_int, ip]
+    L.mg_divergence.argtypes = [vp, vp, vp]
+    L.mg_project.argtypes = [vp, vp, vp]
     L.mg_last_error.restype = C.c_char_p
     _lib = L
     return L

@@ -30,3 +30,22 @@ class MGSolve(torch.autograd.Function):
         tree.set_phi(phi)
         dLdf, dLde = tree.adjoint(g.contiguous(), n_cycles=ctx.adj_cycles, want_eps=ctx.has_eps)
         return None, dLdf, (dLde if ctx.has_eps else None), None, None, None
+
+
+class CleanB(torch.autograd.Function):
+    """Divergence cleaning B_new = B - grad A^+ P div B (Sec. 4.1) on a
+    uniform periodic Cartesian mesh.  There the central gradient and
+    divergence satisfy G^T = -D and the zero-mean solve and the mean
+    projection P are symmetric, so the map is self-adjoint: the backward
+    pass applies the same cleaning to the incoming gradient."""
+
+    @staticmethod
+    def forward(ctx, tree, B, rel_tol=1e-12, max_cycles=80):
+        Bn, _, _, _ = tree.clean(B.detach(), rel_tol, max_cycles, singular=True)
+        ctx.tree, ctx.rel_tol, ctx.max_cycles = tree, rel_tol, max_cycles
+        return Bn
+
+    @staticmethod
+    def backward(ctx, g):
+        gB, _, _, _ = ctx.tree.clean(g.contiguous(), ctx.rel_tol, ctx.max_cycles, singular=True)
+        return None, gB, None, None

@@ -133,6 +133,8 @@ template <class T> void refresh(mg_tree *t, Fields<T> &F, int homog);
 template <class T> void refresh_eps(mg_tree *t, Fields<T> &F);
 template <class T> void tune_sweeps(mg_tree *t, Fields<T> &F);
 int sweep_variant(mg_tree *t, int prec, int level);
+void divergence(mg_tree *t, const double *B, double *out);
+void project(mg_tree *t, const double *B, double *Bout);
 // composite residual of FP64 fields on the leaves; optional outputs:
 // r64 (FP64 leaf order), f32 (FP32 into the leaf cells of an FP32 field)
 void residual_norm(mg_tree *t, Fields<double> &F, int homog, double *out3, double *r64_leaf,

@@ -187,7 +187,9 @@ __device__ __forceinline__ T cf_ghost(const KParams &P, const LevelDesc &L, cons
 // Neumann x_i -/+ h b, axis x_i); refinement boundary
 // g = B'/2 + 3c/4 - d/4 with B' = B + sum_t s_t (C_t - A_t)/8 read from the
 // coarser block and its own ghosts.  mode 1 (coefficient): physical ghosts
-// copy the interior value, refinement ghosts take B.
+// copy the interior value, refinement ghosts take B.  mode 2 (a vector
+// component): physical ghosts copy the interior value, refinement ghosts
+// are interpolated as for phi.
 template <class T, int D>
 __global__ void __launch_bounds__(kMaxThreads) k_ghost(KParams P, int first, T *__restrict__ X,
                                                        T *__restrict__ XG, int mode) {
@@ -208,7 +210,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_ghost(KParams P, int first, T *
             val = X[q.cell_off + cidx<D>(n, jj.x, jj.y, jj.z)];
         } else if (nb == -1) {
             const T xi = X[b.cell_off + cidx<D>(n, ii.x, ii.y, ii.z)];
-            val = mode == 1 ? xi : phys_ghost<T>(P, L, face, xi, bc_value(P, L, b, D, face, ii));
+            val = mode >= 1 ? xi : phys_ghost<T>(P, L, face, xi, bc_value(P, L, b, D, face, ii));
         } else {
             I3 dd = ii;
             put(dd, d, s ? n - 2 : 1);
@@ -1352,6 +1354,53 @@ __global__ void __launch_bounds__(kMaxThreads, 4) k_restrict_tma(KParams P, int 
     }
 }
 
+// ---------------------------------------------- divergence cleaning -----
+// Second-order central differences on leaf blocks (Sec. 4.1): component d of
+// a vector field X (with ghosts) adds (X(c+e_d) - X(c-e_d)) / (2 h_d) to the
+// divergence; the projection writes B_d - (phi(c+e_d) - phi(c-e_d)) / (2 h_d).
+template <int D>
+__global__ void __launch_bounds__(kMaxThreads) k_div_comp(KParams P, int first, const double *__restrict__ X,
+                                                          const double *__restrict__ XG, int d,
+                                                          double *__restrict__ out, long long leaf_base, int add) {
+    __shared__ BlockDesc sb;
+    stage_desc(P, first + blockIdx.x, sb);
+    const BlockDesc &b = sb;
+    const LevelDesc &L = P.L[b.lev];
+    const int n = b.n, C = cells_of<D>(n);
+    const double s2h = 0.5 / L.h[d];
+    for (int c = threadIdx.x; c < C; c += blockDim.x) {
+        int i, j, k;
+        cell_of(c, n, D, i, j, k);
+        const int ox = d == 0, oy = d == 1, oz = d == 2;
+        const double v = (load<double, D>(X, XG, b, i + ox, j + oy, k + oz) -
+                          load<double, D>(X, XG, b, i - ox, j - oy, k - oz)) * s2h;
+        const long long m = leaf_base + (long long)blockIdx.x * C + c;
+        out[m] = add ? out[m] + v : v;
+    }
+}
+
+template <int D>
+__global__ void __launch_bounds__(kMaxThreads) k_grad_sub(KParams P, int first, const double *__restrict__ X,
+                                                          const double *__restrict__ XG, int d,
+                                                          const double *__restrict__ Bin, double *__restrict__ Bout,
+                                                          long long leaf_base) {
+    __shared__ BlockDesc sb;
+    stage_desc(P, first + blockIdx.x, sb);
+    const BlockDesc &b = sb;
+    const LevelDesc &L = P.L[b.lev];
+    const int n = b.n, C = cells_of<D>(n);
+    const double s2h = 0.5 / L.h[d];
+    for (int c = threadIdx.x; c < C; c += blockDim.x) {
+        int i, j, k;
+        cell_of(c, n, D, i, j, k);
+        const int ox = d == 0, oy = d == 1, oz = d == 2;
+        const double gd = (load<double, D>(X, XG, b, i + ox, j + oy, k + oz) -
+                           load<double, D>(X, XG, b, i - ox, j - oy, k - oz)) * s2h;
+        const long long m = leaf_base + (long long)blockIdx.x * C + c;
+        Bout[m] = Bin[m] - gd;
+    }
+}
+
 // ------------------------------------------------------ residual norm ---
 // Composite residual on leaf blocks [first, first + gridDim.x): per-CTA
 // partial sums of V r^2 and V and the max |r| (warp shuffles, then shared
@@ -1940,7 +1989,7 @@ template <class T, int D> struct Launch {
         }
     }
     // covered cells <- mean of children (finest first), then all ghosts
-    static void refresh(mg_tree *t, Fields<T> &F, int homog) {
+    static void refresh(mg_tree *t, Fields<T> &F, int homog, int mode = 0) {
         const KParams P = kparams(t, homog);
         const int top = (int)t->lev.size() - 1;
         for (int l = top; l >= 1; l--) {
@@ -1949,7 +1998,7 @@ template <class T, int D> struct Launch {
             k_restrict<T, D><<<L.nb, threads_for(cells_of<D>(L.n / 2)), 0, t->stream>>>(P, L.first, F.X, F.XG, F.F,
                                                                                          F.E, F.EG, F.F, 0);
         }
-        for (int l = 0; l <= top; l++) ghost(t, P, l, F.X, F.XG, 0);
+        for (int l = 0; l <= top; l++) ghost(t, P, l, F.X, F.XG, mode);
     }
     static void refresh_eps(mg_tree *t, Fields<T> &F) {
         const KParams P = kparams(t, 0);
@@ -2281,6 +2330,57 @@ extern "C" int mg_residual_norm_noalloc(mg_tree *t, double *l2, double *linf) {
 }
 
 namespace mg {
+
+template <int D> static void divergence_d(mg_tree *t, const double *B, double *out) {
+    const KParams P = kparams(t, 1);
+    for (int d = 0; d < D; d++) {
+        // component d into the scratch field, covered cells and ghosts refreshed
+        long long off = 0;
+        for (auto &L : t->lev) {
+            const long long n = (long long)(L.nb - L.nref) * cells_of<D>(L.n);
+            if (n == 0) continue;
+            cudaMemcpyAsync(t->adj.X + t->blocks[L.first + L.nref].cell_off, B + (long long)d * t->nleaf_cells + off,
+                            sizeof(double) * n, cudaMemcpyDeviceToDevice, t->stream);
+            off += n;
+        }
+        Launch<double, D>::refresh(t, t->adj, 1, 2);
+        long long leaf_base = 0;
+        for (auto &L : t->lev) {
+            const int nleaf = L.nb - L.nref;
+            if (nleaf <= 0) continue;
+            ++t->launches;
+            k_div_comp<D><<<nleaf, threads_for(cells_of<D>(L.n)), 0, t->stream>>>(
+                P, L.first + L.nref, t->adj.X, t->adj.XG, d, out, leaf_base, d > 0);
+            leaf_base += (long long)nleaf * cells_of<D>(L.n);
+        }
+    }
+}
+
+template <int D> static void project_d(mg_tree *t, const double *B, double *Bout) {
+    Launch<double, D>::refresh(t, t->f64, 0);
+    const KParams P = kparams(t, 0);
+    for (int d = 0; d < D; d++) {
+        long long leaf_base = 0;
+        for (auto &L : t->lev) {
+            const int nleaf = L.nb - L.nref;
+            if (nleaf <= 0) continue;
+            ++t->launches;
+            k_grad_sub<D><<<nleaf, threads_for(cells_of<D>(L.n)), 0, t->stream>>>(
+                P, L.first + L.nref, t->f64.X, t->f64.XG, d, B + (long long)d * t->nleaf_cells,
+                Bout + (long long)d * t->nleaf_cells, leaf_base);
+            leaf_base += (long long)nleaf * cells_of<D>(L.n);
+        }
+    }
+}
+
+void divergence(mg_tree *t, const double *B, double *out) {
+    if (t->dim == 2) divergence_d<2>(t, B, out);
+    else divergence_d<3>(t, B, out);
+}
+void project(mg_tree *t, const double *B, double *Bout) {
+    if (t->dim == 2) project_d<2>(t, B, Bout);
+    else project_d<3>(t, B, Bout);
+}
 
 int check_cuda(const char *what) {
     cudaError_t e = cudaGetLastError();

@@ -838,6 +838,24 @@ extern "C" int mg_time_sweeps(mg_tree *t, int level, int n_sweeps, int precision
     return check_cuda("time_sweeps");
 }
 
+extern "C" int mg_divergence(mg_tree *t, const double *B, double *divB) {
+    NEED_FINAL(t);
+    if (!B || !divB) return fail(MG_ERR_ARG, "null argument");
+    if (t->geom != MG_CART) return fail(MG_ERR_UNSUPPORTED, "divergence: Cartesian meshes only");
+    int rc;
+    if ((rc = alloc_fields(t, t->adj, false))) return rc;
+    divergence(t, B, divB);
+    return check_cuda("divergence");
+}
+
+extern "C" int mg_project(mg_tree *t, const double *B, double *Bnew) {
+    NEED_FINAL(t);
+    if (!B || !Bnew) return fail(MG_ERR_ARG, "null argument");
+    if (t->geom != MG_CART) return fail(MG_ERR_UNSUPPORTED, "projection: Cartesian meshes only");
+    project(t, B, Bnew);
+    return check_cuda("project");
+}
+
 extern "C" int mg_tree_destroy(mg_tree *t) {
     if (!t) return MG_OK;
     if (t->finalized) {

@@ -555,3 +555,73 @@ def test_adjoint_matches_finite_differences(case):
         de[c] = 1e-4 * eps[c]
         fe = (loss(eps + de, f) - loss(eps - de, f)) / (2e-4 * eps[c])
         assert abs(fe - geps[c]) < 1e-6 * (abs(geps[c]) + np.abs(geps).max() * 1e-2), (c, fe, geps[c])
+
+
+# ---------------------------------------------------- divergence cleaning --
+
+def test_divergence_and_gradient_exact_on_linear_fields():
+    """Sec. 4.1 central differences with the Sec. 2.6 ghosts: exact for linear
+    fields on every cell not beside a physical face (refinement faces
+    included, since the ghosts are exact on linear functions)."""
+    dim, N, base = 3, 4, 16
+    ref = amr_refine(dim, N, base, (0.45, 0.5, 0.55), (0.3, 0.15))
+    o = Oracle(dim, N, 0, (0, 1, 0, 0, 1, 0), (0.0,) * 6, (base,) * 3, (0,) * 3, (1,) * 3, ref)
+    p = W.Problem("lin", dim, N, 0, (base,) * 3, (0,) * 3, (1,) * 3, (0,) * 6, (0,) * 6, ref)
+    X, Y, Z, H = W.leaf_cell_centres(p)
+    B = np.stack([0.3 * X - Y + 2 * Z, 1.5 * Y + X, -0.7 * Z + 0.2 * X * 0 + Y])
+    d = o.divergence(B)
+    h = H[:, 0]
+    inner = (X > h) & (X < 1 - h) & (Y > h) & (Y < 1 - h) & (Z > h) & (Z < 1 - h)
+    np.testing.assert_allclose(d[inner], 0.3 + 1.5 - 0.7, atol=1e-11)
+    o.set_phi(2 * X - 3 * Y + 0.5 * Z)
+    Bn = o.project(np.zeros((3, o.n_leaf)))
+    for comp, want in zip(Bn, (-2.0, 3.0, -0.5)):
+        np.testing.assert_allclose(comp[inner], want, atol=1e-11)
+
+
+def test_central_divergence_is_minus_adjoint_of_gradient_periodic():
+    """On a uniform periodic mesh the central divergence and gradient satisfy
+    <u, D B> = -<G u, B> (summation by parts)."""
+    rng = np.random.default_rng(9)
+    o = Oracle(3, 4, 0, (2,) * 6, (0.0,) * 6, (8, 8, 8), (0,) * 3, (1,) * 3)
+    u = rng.standard_normal(o.n_leaf)
+    B = rng.standard_normal((3, o.n_leaf))
+    o.set_phi(u)
+    Gu = -o.project(np.zeros((3, o.n_leaf)))
+    a, b = np.dot(u, o.divergence(B)), -np.sum(Gu * B)
+    assert abs(a - b) < 1e-12 * (abs(a) + np.abs(u).sum())
+
+
+def test_divergence_second_order_periodic():
+    """Second-order convergence of the central divergence on a smooth field."""
+    errs = []
+    for n in (16, 32):
+        o = Oracle(3, 8, 0, (2,) * 6, (0.0,) * 6, (n,) * 3, (0,) * 3, (1,) * 3)
+        p = W.Problem("u", 3, 8, 0, (n,) * 3, (0,) * 3, (1,) * 3, (2,) * 6, (0,) * 6, np.zeros((0, 4), np.int32))
+        X, Y, Z, _ = W.leaf_cell_centres(p)
+        B = np.stack([np.sin(2 * np.pi * X), np.cos(2 * np.pi * Y), np.sin(2 * np.pi * Z)])
+        ex = 2 * np.pi * (np.cos(2 * np.pi * X) - np.sin(2 * np.pi * Y) + np.cos(2 * np.pi * Z))
+        errs.append(np.abs(o.divergence(B) - ex).max())
+    assert 3.6 < errs[0] / errs[1] < 4.4, errs
+
+
+def test_cleaning_adjoint_is_the_cleaning_of_g_periodic():
+    """On a uniform periodic mesh B_new = B - G A^+ P D B is a self-adjoint
+    map (G^T = -D, A^+ and the mean projection P symmetric), so for
+    L = 0.5 sum |B_new - B_t|^2 the gradient is clean(B_new - B_t); central
+    differences of L agree (L is quadratic in B)."""
+    rng = np.random.default_rng(12)
+    o = Oracle(3, 4, 0, (2,) * 6, (0.0,) * 6, (8, 8, 8), (0,) * 3, (1,) * 3)
+    B = rng.standard_normal((3, o.n_leaf))
+    Bt = rng.standard_normal((3, o.n_leaf))
+
+    def loss(Bx):
+        Bn, _, _ = o.clean(Bx, rel_tol=1e-14, max_cycles=80)
+        return 0.5 * np.sum((Bn - Bt) ** 2), Bn
+    L0, Bn = loss(B)
+    grad, _, _ = o.clean(Bn - Bt, rel_tol=1e-14, max_cycles=80)
+    for comp, c in ((0, 5), (1, 77), (2, 300), (0, 411)):
+        dB = np.zeros_like(B)
+        dB[comp, c] = 1e-3
+        fd = (loss(B + dB)[0] - loss(B - dB)[0]) / 2e-3
+        assert abs(fd - grad[comp, c]) < 1e-7 * (abs(grad[comp, c]) + np.abs(grad).max() * 1e-3), (fd, grad[comp, c])
