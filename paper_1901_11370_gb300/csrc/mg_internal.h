@@ -42,7 +42,10 @@ struct LevelDesc {
     int nb;               // blocks on the level
     int nref;             // of which the first nref are covered by children
     long long bc_off[6];  // offset of the boundary plane of each face, -1: constant
+    double inv_diag;      // 1 / (2 sum_d 1/h_d^2 + lambda): constant-coefficient Gauss-Seidel divisor
+    double pad_;
 };
+static_assert(sizeof(LevelDesc) % 16 == 0, "LevelDesc is copied with 16-byte bulk copies");
 
 // Scalars every kernel needs, passed by value.
 struct KParams {
@@ -57,6 +60,20 @@ struct KParams {
     int var_eps;
     int homog;            // 1: boundary values read as zero
     int *status;          // device status word: 1 = a bounded wait gave up
+    int uniform;          // 1: every block of a launch shares one level descriptor
+};
+
+// Coarsest level of one tree of a pool (one tree, or a batch of trees):
+// a contiguous range of blocks solved exactly by its dense inverse.
+struct TreeCoarse {
+    int first, nb, n;     // blocks of the coarsest level
+    int nc, ns;           // cells, system size (nc + 1 when bordered)
+    int singular;         // bordered by sum V x = 0
+    int group;            // group index of the coarsest level
+    int lvl;              // index of its level descriptor
+    long long cell0;      // first cell of the level
+    long long minv_off;   // offset of the ns x ns inverse (row-major)
+    long long cvec_off;   // offset of the residual vector (ns)
 };
 
 template <class T>
@@ -67,6 +84,9 @@ struct Fields {
     T *V = nullptr, *VG = nullptr;   // FAS copy v_old: interior + ghosts
 };
 
+// A level of one tree; in a pool of several trees (a batch), a segment:
+// a contiguous block range of one block size at one depth from the top
+// ("group"), covered blocks first.
 struct LevelHost {
     int n = 0, depth = 0;
     int nblk[3] = {1, 1, 1}, ncell[3] = {1, 1, 1};
@@ -74,6 +94,9 @@ struct LevelHost {
     int first = 0, nb = 0, nref = 0;
     long long cell_first = 0, ghost_first = 0, ncells = 0, nghost = 0;
     std::vector<double> bc[6];
+    int group = 0;      // cycle group (0 = coarsest)
+    int coarsest = 0;   // 1: coarsest level of its tree(s), solved exactly
+    int parent_same_n = 0;  // 1: every block's parent has the same block size
 };
 
 }  // namespace mg
@@ -87,7 +110,13 @@ struct mg_tree {
     std::vector<int32_t> refine;  // 4 per entry
     bool built = false, finalized = false, singular = false, bc_dirty = false;
     bool var_eps = false;
-    std::vector<mg::LevelHost> lev;
+    std::vector<mg::LevelHost> lev;           // levels (one tree) or segments (batch)
+    std::vector<mg::LevelHost> tl;            // batch only: level descriptors per (tree, level)
+    std::vector<std::vector<int>> groups;     // segments of each group, coarsest group first
+    std::vector<mg::TreeCoarse> tcoarse;      // coarsest level of each tree
+    mg::TreeCoarse *d_tcoarse = nullptr;
+    bool is_batch = false;
+    int max_nc = 0;                           // largest coarsest-level system
     std::vector<mg::BlockDesc> blocks;
     long long ncells = 0, nghost = 0, nleaf_cells = 0;
 
@@ -101,8 +130,9 @@ struct mg_tree {
     mg::Fields<double> f64, adj;   // solve and adjoint solve (adj shares E/EG)
     mg::Fields<float> f32;         // inner defect-correction cycles
     double *d_r64 = nullptr;       // leaf residual scratch (FP64)
-    double *d_minv = nullptr;      // coarsest-level inverse, row-major ns x ns
-    int nc = 0, ns = 0;            // coarsest cells, system size (nc + singular)
+    double *d_minv = nullptr;      // coarsest-level inverses, row-major ns x ns per tree
+    long long minv_total = 0, cvec_total = 0;
+    int nc = 0, ns = 0;            // coarsest cells, system size (nc + singular) -- one tree
     bool minv_ok = false;
     double *d_cvec = nullptr;      // coarsest residual vector (ns)
     double *d_partials = nullptr;  // per-CTA norm partials (3 per CTA)
@@ -147,6 +177,10 @@ void eps_grad(mg_tree *t, const double *lam_cells, const double *phi_cells, doub
 void scale_by_radius(mg_tree *t, const double *in_leaf, double *out_leaf, int divide);
 KParams kparams(mg_tree *t, int homog);
 int time_sweeps(mg_tree *t, int level, int n_sweeps, int prec, double *out4);
+// batch: per-tree composite residual sums (3 per tree, on the host after wait)
+void residual_enqueue_trees(mg_tree *t, Fields<double> &F, float *f32_cells, double *d_tree3);
+// copies between a concatenated per-tree leaf array and the pool cells
+void leaf_runs_copy(mg_tree *t, double *cells, const double *leaf, bool to_cells);
 int check_cuda(const char *what);
 }  // namespace mg
 

@@ -470,7 +470,7 @@ __global__ void __launch_bounds__(kMaxThreads, 5) k_sweep_tma(KParams P, int fir
                                                            int colour) {
     constexpr int n = NT, C = cells_of<D>(NT), FC = face_of<D>(NT), GH = 2 * D * FC;
     constexpr int NCOL = C / 2, CPT = (NCOL + kMaxThreads - 1) / kMaxThreads;
-    constexpr int DESC = (int)(sizeof(BlockDesc) / sizeof(T));
+    constexpr int DESC = (int)((sizeof(BlockDesc) + sizeof(LevelDesc)) / sizeof(T));
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bars[2];
     __shared__ __align__(16) LevelDesc sL;
@@ -497,6 +497,7 @@ __global__ void __launch_bounds__(kMaxThreads, 5) k_sweep_tma(KParams P, int fir
         fence_async_smem();
         mbar_expect_tx(bar, tx_bytes);
         bulk_g2s(st, P.B + g, sizeof(BlockDesc), bar);
+        bulk_g2s(reinterpret_cast<char *>(st) + sizeof(BlockDesc), P.L + P.B[g].lev, sizeof(LevelDesc), bar);
         bulk_g2s(st + DESC, F.X + co, sizeof(T) * C, bar);
         bulk_g2s(st + DESC + C, F.XG + go, sizeof(T) * GH, bar);
         bulk_g2s(st + DESC + C + GH, F.F + co, sizeof(T) * C, bar);
@@ -507,11 +508,9 @@ __global__ void __launch_bounds__(kMaxThreads, 5) k_sweep_tma(KParams P, int fir
     };
     int g = blockIdx.x;
     if (tid == 0 && g < nblocks) issue(0, first + g);
-    const LevelDesc &L = sL;
+    // level descriptor: CTA-wide copy when every block shares it, else per block
     const bool cyl = P.geom == MG_CYL;
     const T helm = (T)P.helm;
-    const T w0 = (T)L.inv_h2[0], w1 = (T)L.inv_h2[1], w2 = (T)L.inv_h2[2];
-    const T inv_den = (T)1 / ((T)2 * (w0 + w1 + (D == 3 ? w2 : (T)0)) + helm);
     for (int it = 0; g < nblocks; it++, g += gridDim.x) {
         {
             uint32_t tries = 0;
@@ -532,6 +531,9 @@ __global__ void __launch_bounds__(kMaxThreads, 5) k_sweep_tma(KParams P, int fir
         }
         T *st = stage0 + (it & 1) * stage_elems;
         const BlockDesc &b = *reinterpret_cast<const BlockDesc *>(st);
+        const LevelDesc &L = *reinterpret_cast<const LevelDesc *>(reinterpret_cast<const char *>(st) + sizeof(BlockDesc));
+        const T w0 = (T)L.inv_h2[0], w1 = (T)L.inv_h2[1], w2 = (T)L.inv_h2[2];
+        const T inv_den = (T)L.inv_diag;
         T *xs = st + DESC, *gs = xs + C, *fs = gs + GH, *es = fs + C, *egs = es + C;
         const int bi = b.ijk[0], bj = b.ijk[1], bk = b.ijk[2];
         const int par0 = (bi + bj + bk) * n;
@@ -625,7 +627,7 @@ __global__ void __launch_bounds__(32 * WARPS) k_sweep_warp(KParams P, int first,
                                                            int colour) {
     constexpr int n = 8, C = cells_of<D>(8), FC = face_of<D>(8), GH = 2 * D * FC;
     constexpr int NCOL = C / 2, PER = NCOL / 32;
-    constexpr int DESC = (int)(sizeof(BlockDesc) / sizeof(T));
+    constexpr int DESC = (int)((sizeof(BlockDesc) + sizeof(LevelDesc)) / sizeof(T));
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bars[WARPS][2];
     __shared__ __align__(16) LevelDesc sL;
@@ -649,6 +651,7 @@ __global__ void __launch_bounds__(32 * WARPS) k_sweep_warp(KParams P, int first,
         fence_async_smem();
         mbar_expect_tx(bar, tx_bytes);
         bulk_g2s(st, P.B + g, sizeof(BlockDesc), bar);
+        bulk_g2s(reinterpret_cast<char *>(st) + sizeof(BlockDesc), P.L + P.B[g].lev, sizeof(LevelDesc), bar);
         bulk_g2s(st + DESC, F.X + co, sizeof(T) * C, bar);
         bulk_g2s(st + DESC + C, F.XG + go, sizeof(T) * GH, bar);
         bulk_g2s(st + DESC + C + GH, F.F + co, sizeof(T) * C, bar);
@@ -660,11 +663,9 @@ __global__ void __launch_bounds__(32 * WARPS) k_sweep_warp(KParams P, int first,
     const int stride = gridDim.x * WARPS;
     int g = blockIdx.x * WARPS + warp;
     if (lane == 0 && g < nblocks) issue(0, first + g);
-    const LevelDesc &L = sL;
+    // level descriptor: CTA-wide copy when every block shares it, else per block
     const bool cyl = P.geom == MG_CYL;
     const T helm = (T)P.helm;
-    const T w0 = (T)L.inv_h2[0], w1 = (T)L.inv_h2[1], w2 = (T)L.inv_h2[2];
-    const T inv_den = (T)1 / ((T)2 * (w0 + w1 + (D == 3 ? w2 : (T)0)) + helm);
     for (int it = 0; g < nblocks; it++, g += stride) {
         bool timed_out = false;
         {
@@ -686,6 +687,9 @@ __global__ void __launch_bounds__(32 * WARPS) k_sweep_warp(KParams P, int first,
         }
         T *st = wst + (it & 1) * stage_elems;
         const BlockDesc &b = *reinterpret_cast<const BlockDesc *>(st);
+        const LevelDesc &L = *reinterpret_cast<const LevelDesc *>(reinterpret_cast<const char *>(st) + sizeof(BlockDesc));
+        const T w0 = (T)L.inv_h2[0], w1 = (T)L.inv_h2[1], w2 = (T)L.inv_h2[2];
+        const T inv_den = (T)L.inv_diag;
         T *xs = st + DESC, *gs = xs + C, *fs = gs + GH, *es = fs + C, *egs = es + C;
         const int bi = b.ijk[0], bj = b.ijk[1], bk = b.ijk[2];
         const int par0 = (bi + bj + bk) * n;
@@ -798,7 +802,7 @@ template <class T, int WARPS, int STAGES>
 __global__ void __launch_bounds__(32 * WARPS) k_sweep_rows(KParams P, int first, int nblocks, Fields<T> F,
                                                            int colour) {
     constexpr int n = 8, C = 512, FC = 64, GH = 384;
-    constexpr int DESC = (int)(sizeof(BlockDesc) / sizeof(T));
+    constexpr int DESC = (int)((sizeof(BlockDesc) + sizeof(LevelDesc)) / sizeof(T));
     constexpr int STAGE = DESC + 2 * C + GH;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bars[WARPS][STAGES];
@@ -819,6 +823,7 @@ __global__ void __launch_bounds__(32 * WARPS) k_sweep_rows(KParams P, int first,
         fence_async_smem();
         mbar_expect_tx(bar, (uint32_t)(sizeof(T) * STAGE));
         bulk_g2s(st, P.B + g, sizeof(BlockDesc), bar);
+        bulk_g2s(reinterpret_cast<char *>(st) + sizeof(BlockDesc), P.L + P.B[g].lev, sizeof(LevelDesc), bar);
         bulk_g2s(st + DESC, F.X + co, sizeof(T) * C, bar);
         bulk_g2s(st + DESC + C, F.XG + go, sizeof(T) * GH, bar);
         bulk_g2s(st + DESC + C + GH, F.F + co, sizeof(T) * C, bar);
@@ -828,10 +833,8 @@ __global__ void __launch_bounds__(32 * WARPS) k_sweep_rows(KParams P, int first,
     if (lane == 0)
         for (int q = 0; q < STAGES - 1; q++)
             if (g + q * stride < nblocks) issue(q, first + g + q * stride);
-    const LevelDesc &L = sL;
+    // level descriptor: CTA-wide copy when every block shares it, else per block
     const T helm = (T)P.helm;
-    const T w0 = (T)L.inv_h2[0], w1 = (T)L.inv_h2[1], w2 = (T)L.inv_h2[2];
-    const T inv_den = (T)1 / ((T)2 * (w0 + w1 + w2) + helm);
     for (int it = 0; g < nblocks; it++, g += stride) {
         bool timed_out = false;
         {
@@ -854,6 +857,9 @@ __global__ void __launch_bounds__(32 * WARPS) k_sweep_rows(KParams P, int first,
         }
         T *st = wst + (it % STAGES) * STAGE;
         const BlockDesc &b = *reinterpret_cast<const BlockDesc *>(st);
+        const LevelDesc &L = *reinterpret_cast<const LevelDesc *>(reinterpret_cast<const char *>(st) + sizeof(BlockDesc));
+        const T w0 = (T)L.inv_h2[0], w1 = (T)L.inv_h2[1], w2 = (T)L.inv_h2[2];
+        const T inv_den = (T)L.inv_diag;
         T *xs = st + DESC, *gs = xs + C, *fs = gs + GH;
         const int par0 = (b.ijk[0] + b.ijk[1] + b.ijk[2]) * n;
         T newrow[2][8];
@@ -1212,7 +1218,7 @@ template <class T, int D, int NT>
 __global__ void __launch_bounds__(kMaxThreads, 4) k_restrict_tma(KParams P, int first, int nblocks, Fields<T> F) {
     constexpr int n = NT, m = NT / 2, C = cells_of<D>(NT), FC = face_of<D>(NT), GH = 2 * D * FC;
     constexpr int M = cells_of<D>(m);
-    constexpr int DESC = (int)(sizeof(BlockDesc) / sizeof(T));
+    constexpr int DESC = (int)((sizeof(BlockDesc) + sizeof(LevelDesc)) / sizeof(T));
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bars[2];
     __shared__ __align__(16) LevelDesc sL, sPL;
@@ -1243,7 +1249,9 @@ __global__ void __launch_bounds__(kMaxThreads, 4) k_restrict_tma(KParams P, int 
         fence_async_smem();
         mbar_expect_tx(bar, tx_bytes);
         bulk_g2s(st, P.B + g, sizeof(BlockDesc), bar);
+        bulk_g2s(reinterpret_cast<char *>(st) + sizeof(BlockDesc), P.L + P.B[g].lev, sizeof(LevelDesc), bar);
         bulk_g2s(st + DESC, P.B + par, sizeof(BlockDesc), bar);
+        bulk_g2s(reinterpret_cast<char *>(st + DESC) + sizeof(BlockDesc), P.L + P.B[par].lev, sizeof(LevelDesc), bar);
         bulk_g2s(st + 2 * DESC, F.X + co, sizeof(T) * C, bar);
         bulk_g2s(st + 2 * DESC + C, F.XG + go, sizeof(T) * GH, bar);
         bulk_g2s(st + 2 * DESC + C + GH, F.F + co, sizeof(T) * C, bar);
@@ -1254,7 +1262,7 @@ __global__ void __launch_bounds__(kMaxThreads, 4) k_restrict_tma(KParams P, int 
     };
     int g = blockIdx.x;
     if (tid == 0 && g < nblocks) issue(0, first + g);
-    const LevelDesc &L = sL, &PL = sPL;
+    // level descriptor: CTA-wide copy when every block shares it, else per block
     const bool cyl = P.geom == MG_CYL;
     for (int it = 0; g < nblocks; it++, g += gridDim.x) {
         {
@@ -1272,6 +1280,8 @@ __global__ void __launch_bounds__(kMaxThreads, 4) k_restrict_tma(KParams P, int 
         const T *st = stage0 + (it & 1) * stage_elems;
         const BlockDesc &b = *reinterpret_cast<const BlockDesc *>(st);
         const BlockDesc &p = *reinterpret_cast<const BlockDesc *>(st + DESC);
+        const LevelDesc &L = *reinterpret_cast<const LevelDesc *>(reinterpret_cast<const char *>(st) + sizeof(BlockDesc));
+        const LevelDesc &PL = *reinterpret_cast<const LevelDesc *>(reinterpret_cast<const char *>(st + DESC) + sizeof(BlockDesc));
         const T *xs = st + 2 * DESC, *gs = xs + C, *fs = gs + GH, *es = fs + C, *egs = es + C;
         auto nbv = [&](const T *xi, const T *gi, int i, int j, int k, int d, int s) -> T {
             const int o = s ? 1 : -1;
@@ -1463,7 +1473,7 @@ __global__ void __launch_bounds__(kMaxThreads, 4) k_resid_tma(KParams P, int fir
                                                               float *__restrict__ f32) {
     using T = double;
     constexpr int n = NT, C = cells_of<D>(NT), FC = face_of<D>(NT), GH = 2 * D * FC;
-    constexpr int DESC = (int)(sizeof(BlockDesc) / sizeof(T));
+    constexpr int DESC = (int)((sizeof(BlockDesc) + sizeof(LevelDesc)) / sizeof(T));
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bars[2];
     __shared__ __align__(16) LevelDesc sL;
@@ -1490,6 +1500,7 @@ __global__ void __launch_bounds__(kMaxThreads, 4) k_resid_tma(KParams P, int fir
         fence_async_smem();
         mbar_expect_tx(bar, tx_bytes);
         bulk_g2s(st, P.B + g, sizeof(BlockDesc), bar);
+        bulk_g2s(reinterpret_cast<char *>(st) + sizeof(BlockDesc), P.L + P.B[g].lev, sizeof(LevelDesc), bar);
         bulk_g2s(st + DESC, F.X + co, sizeof(T) * C, bar);
         bulk_g2s(st + DESC + C, F.XG + go, sizeof(T) * GH, bar);
         bulk_g2s(st + DESC + C + GH, F.F + co, sizeof(T) * C, bar);
@@ -1500,10 +1511,8 @@ __global__ void __launch_bounds__(kMaxThreads, 4) k_resid_tma(KParams P, int fir
     };
     int g = blockIdx.x;
     if (tid == 0 && g < nblocks) issue(0, first + g);
-    const LevelDesc &L = sL;
+    // level descriptor: CTA-wide copy when every block shares it, else per block
     const bool cyl = P.geom == MG_CYL;
-    const double w0 = L.inv_h2[0], w1 = L.inv_h2[1], w2 = L.inv_h2[2];
-    double vol = L.h[0] * L.h[1] * (D == 3 ? L.h[2] : 1.0);
     double s2 = 0, sv = 0;
     double mx = 0.0;
     for (int it = 0; g < nblocks; it++, g += gridDim.x) {
@@ -1521,6 +1530,9 @@ __global__ void __launch_bounds__(kMaxThreads, 4) k_resid_tma(KParams P, int fir
         if (tid == 0 && g + (int)gridDim.x < nblocks) issue(it + 1, first + g + gridDim.x);
         const T *st = stage0 + (it & 1) * stage_elems;
         const BlockDesc &b = *reinterpret_cast<const BlockDesc *>(st);
+        const LevelDesc &L = *reinterpret_cast<const LevelDesc *>(reinterpret_cast<const char *>(st) + sizeof(BlockDesc));
+        const double w0 = L.inv_h2[0], w1 = L.inv_h2[1], w2 = L.inv_h2[2];
+        double vol = L.h[0] * L.h[1] * (D == 3 ? L.h[2] : 1.0);
         const T *xs = st + DESC, *gs = xs + C, *fs = gs + GH, *es = fs + C, *egs = es + C;
         auto nbv = [&](const T *xi, const T *gi, int i, int j, int k, int d, int s) -> T {
             const int o = s ? 1 : -1;
@@ -1668,6 +1680,57 @@ __global__ void k_coarse_apply(const double *__restrict__ minv, int ns, int nc, 
     if (lane == 0) X[row] = (T)((double)X[row] + s);  // level-0 cells come first in the pool
 }
 
+// Exact coarsest solves of several trees at once (one CTA per tree): r = f -
+// L x in FP64 for every cell of the tree's coarsest level, with -sum V x
+// appended for the zero-mean constraint; then dx = Minv r, one warp per row.
+// Trees whose coarsest group is not selected (group > top, or >= top when
+// strict) are skipped.
+template <class T, int D>
+__global__ void __launch_bounds__(1024) k_coarse_resid_b(KParams P, const TreeCoarse *__restrict__ TC, int top,
+                                                          int strict, Fields<T> F, double *__restrict__ cvec) {
+    const TreeCoarse tc = TC[blockIdx.x];
+    if (strict ? tc.group >= top : tc.group > top) return;
+    const int n = tc.n, C = cells_of<D>(n);
+    double wx = 0;
+    for (int row = threadIdx.x; row < tc.nc; row += blockDim.x) {
+        const BlockDesc &b = P.B[tc.first + row / C];
+        const LevelDesc &L = P.L[b.lev];
+        int i, j, k;
+        cell_of(row % C, n, D, i, j, k);
+        double lap, num, den, xc;
+        stencil<double, T, D>(P, L, b, F.X, F.XG, F.E, F.EG, i, j, k, lap, num, den, xc);
+        cvec[tc.cvec_off + row] = (double)F.F[b.cell_off + row % C] - (lap - P.helm * xc);
+        double V = 1.0;
+        for (int d = 0; d < D; d++) V *= L.h[d];
+        if (P.geom == MG_CYL) V = 2.0 * M_PI * (P.lo[0] + (b.ijk[0] * n + i + 0.5) * L.h[0]) * L.h[0] * L.h[1];
+        wx += V * xc;
+    }
+    if (!tc.singular) return;
+    for (int o = 16; o > 0; o >>= 1) wx += __shfl_down_sync(0xffffffffu, wx, o);
+    __shared__ double sh[32];
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = wx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double sum = 0;
+        for (int e = 0; e < (int)((blockDim.x + 31) >> 5); e++) sum += sh[e];
+        cvec[tc.cvec_off + tc.nc] = -sum;
+    }
+}
+
+template <class T>
+__global__ void k_coarse_apply_b(const TreeCoarse *__restrict__ TC, int top, int strict,
+                                 const double *__restrict__ minv, const double *__restrict__ cvec, T *__restrict__ X) {
+    const TreeCoarse tc = TC[blockIdx.y];
+    if (strict ? tc.group >= top : tc.group > top) return;
+    const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (row >= tc.nc) return;
+    double sacc = 0;
+    const double *mr = minv + tc.minv_off + (long long)row * tc.ns;
+    for (int c = lane; c < tc.ns; c += 32) sacc += mr[c] * cvec[tc.cvec_off + c];
+    for (int o = 16; o > 0; o >>= 1) sacc += __shfl_down_sync(0xffffffffu, sacc, o);
+    if (lane == 0) X[tc.cell0 + row] = (T)((double)X[tc.cell0 + row] + sacc);
+}
+
 // --------------------------------------------------- elementwise ops ----
 __global__ void k_add_e(const float *__restrict__ e, double *__restrict__ x, long long n) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
@@ -1760,6 +1823,7 @@ KParams kparams(mg_tree *t, int homog) {
     P.var_eps = t->var_eps ? 1 : 0;
     P.homog = homog;
     P.status = t->d_status;
+    P.uniform = t->is_batch ? 0 : 1;
     return P;
 }
 
@@ -1802,7 +1866,7 @@ template <class T, int D> struct Launch {
     //        (8^3 blocks, constant coefficient, Cartesian)
     static size_t cand_smem(mg_tree *t, int l, Fields<T> &F, int cand) {
         const int n = t->lev[l].n, C = cells_of<D>(n), GH = 2 * D * face_of<D>(n);
-        const size_t stage = sizeof(BlockDesc) + sizeof(T) * (2 * C + GH + (F.E ? C + GH : 0));
+        const size_t stage = sizeof(BlockDesc) + sizeof(LevelDesc) + sizeof(T) * (2 * C + GH + (F.E ? C + GH : 0));
         switch (cand) {
         case 0: return (n == 8 || n == 16) ? 2 * stage : 0;
         case 1: return 1;
@@ -1886,18 +1950,27 @@ template <class T, int D> struct Launch {
         cudaEventCreate(&e1);
         for (size_t l = 1; l < t->lev.size(); l++) {
             if (t->lev[l].nb < 256) continue;
-            float best = 1e30f;
-            for (int cand = 0; cand < 6; cand++) {
-                if (!cand_ok(t, (int)l, F, cand)) continue;
-                for (int w = 0; w < 2; w++) sweep_cand(t, P, (int)l, F, w & 1, cand);
-                cudaEventRecord(e0, t->stream);
+            std::vector<int> cands;
+            for (int cand = 0; cand < 6; cand++)
+                if (cand_ok(t, (int)l, F, cand)) cands.push_back(cand);
+            // warm-up (clocks, caches, first-launch costs), then the minimum
+            // over three interleaved rounds of four launches per candidate
+            for (int cand : cands)
                 for (int w = 0; w < 4; w++) sweep_cand(t, P, (int)l, F, w & 1, cand);
-                cudaEventRecord(e1, t->stream);
-                cudaEventSynchronize(e1);
-                float ms = 0;
-                cudaEventElapsedTime(&ms, e0, e1);
-                if (ms < best) { best = ms; t->sweep_choice[prec][l] = cand; }
-            }
+            std::vector<float> best(cands.size(), 1e30f);
+            for (int round = 0; round < 3; round++)
+                for (size_t ci = 0; ci < cands.size(); ci++) {
+                    cudaEventRecord(e0, t->stream);
+                    for (int w = 0; w < 4; w++) sweep_cand(t, P, (int)l, F, w & 1, cands[ci]);
+                    cudaEventRecord(e1, t->stream);
+                    cudaEventSynchronize(e1);
+                    float ms = 0;
+                    cudaEventElapsedTime(&ms, e0, e1);
+                    best[ci] = std::min(best[ci], ms);
+                }
+            float bmin = 1e30f;
+            for (size_t ci = 0; ci < cands.size(); ci++)
+                if (best[ci] < bmin) { bmin = best[ci]; t->sweep_choice[prec][l] = cands[ci]; }
         }
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
@@ -1907,48 +1980,53 @@ template <class T, int D> struct Launch {
         for (int s = 0; s < sweeps; s++)
             for (int colour = 0; colour < 2; colour++) sweep(t, P, l, F, colour);
     }
-    // downward FAS step from level l to l-1 (Sec. 2.4): restriction with the
-    // parent-level ghost pushes, then f^H and v_old on the covered blocks
-    static void restrict_fas(mg_tree *t, const KParams &P, int l, Fields<T> &F) {
-        const LevelHost &L = t->lev[l], &C = t->lev[l - 1];
-        ++t->launches;
-        const int C8 = cells_of<D>(L.n), GH8 = 2 * D * face_of<D>(L.n);
-        const size_t smt = 2 * (2 * sizeof(BlockDesc) + sizeof(T) * (2 * C8 + GH8 + (F.E ? C8 + GH8 : 0)));
-        if ((L.n == 8 || L.n == 16) && smt + sizeof(T) * C8 <= 200 * 1024) {
-            auto kern = L.n == 8 ? k_restrict_tma<T, D, 8> : k_restrict_tma<T, D, 16>;
-            const int thr = threads_for(C8);
-            const int grid = std::min(L.nb, resident_ctas(kern, thr, smt) * t->nsm);
-            kern<<<grid, thr, smt, t->stream>>>(P, L.first, L.nb, F);
-            if (C.nref > 0) {
-                ++t->launches;
-                k_fas_rhs_vold<T, D><<<C.nref, threads_for(cells_of<D>(C.n)), 0, t->stream>>>(P, C.first, F);
-            }
-            return;
-        }
-        if (L.n >= 4) {
-            k_restrict_push<T, D><<<L.nb, threads_for(cells_of<D>(L.n / 2)), sizeof(T) * cells_of<D>(L.n / 2),
-                                    t->stream>>>(P, L.first, F);
-            if (C.nref > 0) {
-                ++t->launches;
-                k_fas_rhs_vold<T, D><<<C.nref, threads_for(cells_of<D>(C.n)), 0, t->stream>>>(P, C.first, F);
-            }
-            return;
-        }
-        k_restrict<T, D><<<L.nb, threads_for(cells_of<D>(L.n / 2)), 0, t->stream>>>(P, L.first, F.X, F.XG, F.F,
-                                                                                     F.E, F.EG, F.F, 1);
-        ghost(t, P, l - 1, F.X, F.XG, 0);
-        cudaMemcpyAsync(F.V + C.cell_first, F.X + C.cell_first, sizeof(T) * C.ncells, cudaMemcpyDeviceToDevice, t->stream);
-        cudaMemcpyAsync(F.VG + C.ghost_first, F.XG + C.ghost_first, sizeof(T) * C.nghost, cudaMemcpyDeviceToDevice,
-                        t->stream);
-        if (C.nref > 0) {
+    // Downward FAS step from group g to g-1 (Sec. 2.4): every non-coarsest
+    // segment of g restricts into its parents (pushing the parent-level
+    // ghosts), then f^H and v_old are formed on the covered blocks of g-1.
+    static void restrict_group(mg_tree *t, const KParams &P, int g, Fields<T> &F) {
+        bool plain = false;
+        for (int l : t->groups[g]) {
+            const LevelHost &L = t->lev[l];
+            if (L.coarsest) continue;
             ++t->launches;
-            k_fas_rhs<T, D><<<C.nref, threads_for(cells_of<D>(C.n)), 0, t->stream>>>(P, C.first, F);
+            const int C8 = cells_of<D>(L.n), GH8 = 2 * D * face_of<D>(L.n);
+            const size_t smt = 2 * (2 * (sizeof(BlockDesc) + sizeof(LevelDesc)) + sizeof(T) * (2 * C8 + GH8 + (F.E ? C8 + GH8 : 0)));
+            if ((L.n == 8 || L.n == 16) && smt + sizeof(T) * C8 <= 200 * 1024) {
+                auto kern = L.n == 8 ? k_restrict_tma<T, D, 8> : k_restrict_tma<T, D, 16>;
+                const int thr = threads_for(C8);
+                const int grid = std::min(L.nb, resident_ctas(kern, thr, smt) * t->nsm);
+                kern<<<grid, thr, smt, t->stream>>>(P, L.first, L.nb, F);
+            } else if (L.n >= 4) {
+                k_restrict_push<T, D><<<L.nb, threads_for(cells_of<D>(L.n / 2)), sizeof(T) * cells_of<D>(L.n / 2),
+                                        t->stream>>>(P, L.first, F);
+            } else {
+                k_restrict<T, D><<<L.nb, threads_for(cells_of<D>(L.n / 2)), 0, t->stream>>>(P, L.first, F.X, F.XG,
+                                                                                             F.F, F.E, F.EG, F.F, 1);
+                plain = true;
+            }
+        }
+        for (int c : t->groups[g - 1]) {
+            const LevelHost &C = t->lev[c];
+            if (plain) {
+                ghost(t, P, c, F.X, F.XG, 0);
+                cudaMemcpyAsync(F.V + C.cell_first, F.X + C.cell_first, sizeof(T) * C.ncells, cudaMemcpyDeviceToDevice,
+                                t->stream);
+                cudaMemcpyAsync(F.VG + C.ghost_first, F.XG + C.ghost_first, sizeof(T) * C.nghost,
+                                cudaMemcpyDeviceToDevice, t->stream);
+            }
+        }
+        for (int c : t->groups[g - 1]) {
+            const LevelHost &C = t->lev[c];
+            if (C.nref <= 0) continue;
+            ++t->launches;
+            if (plain) k_fas_rhs<T, D><<<C.nref, threads_for(cells_of<D>(C.n)), 0, t->stream>>>(P, C.first, F);
+            else k_fas_rhs_vold<T, D><<<C.nref, threads_for(cells_of<D>(C.n)), 0, t->stream>>>(P, C.first, F);
         }
     }
     static void prolong(mg_tree *t, const KParams &P, int l, Fields<T> &F) {
         const LevelHost &L = t->lev[l];
         ++t->launches;
-        if (L.n == 8 && t->lev[l - 1].n == 8) {
+        if (L.n == 8 && L.parent_same_n) {
             k_prolong_box<T, D, 8><<<L.nb, threads_for(cells_of<D>(8) / 2), 0, t->stream>>>(P, L.first, F);
             return;
         }
@@ -1956,61 +2034,73 @@ template <class T, int D> struct Launch {
         set_smem(k_prolong_push<T, D>, sm);
         k_prolong_push<T, D><<<L.nb, threads_for(cells_of<D>(L.n)), sm, t->stream>>>(P, L.first, F);
     }
-    static void coarse(mg_tree *t, const KParams &P, Fields<T> &F) {
-        const LevelHost &L = t->lev[0];
+    // exact coarsest solves of the trees whose coarsest group is below `top`
+    // (strict) or at most `top`; then ghost fills of the coarsest segments
+    static void coarse(mg_tree *t, const KParams &P, Fields<T> &F, int top, int strict) {
+        const int ntr = (int)t->tcoarse.size();
         ++t->launches;
-        k_coarse_resid<T, D><<<1, 1024, 0, t->stream>>>(P, L.nb, F, t->d_cvec, t->singular ? 1 : 0);
+        k_coarse_resid_b<T, D><<<ntr, 1024, 0, t->stream>>>(P, t->d_tcoarse, top, strict, F, t->d_cvec);
         const int rows_per_cta = 8;
         ++t->launches;
-        k_coarse_apply<T><<<(t->nc + rows_per_cta - 1) / rows_per_cta, 32 * rows_per_cta, 0, t->stream>>>(
-            t->d_minv, t->ns, t->nc, t->d_cvec, F.X);
-        ghost(t, P, 0, F.X, F.XG, 0);
+        k_coarse_apply_b<T><<<dim3((t->max_nc + rows_per_cta - 1) / rows_per_cta, ntr), 32 * rows_per_cta, 0,
+                              t->stream>>>(t->d_tcoarse, top, strict, t->d_minv, t->d_cvec, F.X);
+        for (size_t l = 0; l < t->lev.size(); l++)
+            if (t->lev[l].coarsest && t->lev[l].group <= top) ghost(t, P, (int)l, F.X, F.XG, 0);
     }
-    static void vcycle(mg_tree *t, Fields<T> &F, int top, int nd, int nu, int homog) {
+    static void vcycle(mg_tree *t, Fields<T> &F, int top, int nd, int nu, int homog, int strict = 0) {
         const KParams P = kparams(t, homog);
-        for (int l = top; l >= 1; l--) {
-            smooth(t, P, l, F, nd);
-            restrict_fas(t, P, l, F);
+        for (int g = top; g >= 1; g--) {
+            for (int l : t->groups[g])
+                if (!t->lev[l].coarsest) smooth(t, P, l, F, nd);
+            restrict_group(t, P, g, F);
         }
-        coarse(t, P, F);
-        for (int l = 1; l <= top; l++) {
-            prolong(t, P, l, F);
-            smooth(t, P, l, F, nu);
-        }
+        coarse(t, P, F, top, strict);
+        for (int g = 1; g <= top; g++)
+            for (int l : t->groups[g])
+                if (!t->lev[l].coarsest) {
+                    prolong(t, P, l, F);
+                    smooth(t, P, l, F, nu);
+                }
     }
     static void fmg(mg_tree *t, Fields<T> &F, int nd, int nu, int homog) {
         const KParams P = kparams(t, homog);
-        const int top = (int)t->lev.size() - 1;
-        for (int l = top; l >= 1; l--) restrict_fas(t, P, l, F);
-        coarse(t, P, F);
-        for (int l = 1; l <= top; l++) {
-            prolong(t, P, l, F);
-            vcycle(t, F, l, nd, nu, homog);
+        const int top = (int)t->groups.size() - 1;
+        for (int g = top; g >= 1; g--) restrict_group(t, P, g, F);
+        coarse(t, P, F, top, 0);
+        for (int g = 1; g <= top; g++) {
+            for (int l : t->groups[g])
+                if (!t->lev[l].coarsest) prolong(t, P, l, F);
+            vcycle(t, F, g, nd, nu, homog, 1);
         }
     }
     // covered cells <- mean of children (finest first), then all ghosts
     static void refresh(mg_tree *t, Fields<T> &F, int homog, int mode = 0) {
         const KParams P = kparams(t, homog);
-        const int top = (int)t->lev.size() - 1;
-        for (int l = top; l >= 1; l--) {
-            const LevelHost &L = t->lev[l];
-            ++t->launches;
-            k_restrict<T, D><<<L.nb, threads_for(cells_of<D>(L.n / 2)), 0, t->stream>>>(P, L.first, F.X, F.XG, F.F,
-                                                                                         F.E, F.EG, F.F, 0);
-        }
-        for (int l = 0; l <= top; l++) ghost(t, P, l, F.X, F.XG, mode);
+        const int top = (int)t->groups.size() - 1;
+        for (int g = top; g >= 1; g--)
+            for (int l : t->groups[g]) {
+                const LevelHost &L = t->lev[l];
+                if (L.coarsest) continue;
+                ++t->launches;
+                k_restrict<T, D><<<L.nb, threads_for(cells_of<D>(L.n / 2)), 0, t->stream>>>(P, L.first, F.X, F.XG,
+                                                                                             F.F, F.E, F.EG, F.F, 0);
+            }
+        for (int g = 0; g <= top; g++)
+            for (int l : t->groups[g]) ghost(t, P, l, F.X, F.XG, mode);
     }
     static void refresh_eps(mg_tree *t, Fields<T> &F) {
         const KParams P = kparams(t, 0);
-        const int top = (int)t->lev.size() - 1;
-        for (int l = top; l >= 1; l--) {
-            const LevelHost &L = t->lev[l];
-            ++t->launches;
-            k_restrict<T, D><<<L.nb, threads_for(cells_of<D>(L.n / 2)), 0, t->stream>>>(P, L.first, F.E, F.EG,
-                                                                                         nullptr, nullptr, nullptr,
-                                                                                         nullptr, 0);
-        }
-        for (int l = 0; l <= top; l++) ghost(t, P, l, F.E, F.EG, 1);
+        const int top = (int)t->groups.size() - 1;
+        for (int g = top; g >= 1; g--)
+            for (int l : t->groups[g]) {
+                const LevelHost &L = t->lev[l];
+                if (L.coarsest) continue;
+                ++t->launches;
+                k_restrict<T, D><<<L.nb, threads_for(cells_of<D>(L.n / 2)), 0, t->stream>>>(
+                    P, L.first, F.E, F.EG, nullptr, nullptr, nullptr, nullptr, 0);
+            }
+        for (int g = 0; g <= top; g++)
+            for (int l : t->groups[g]) ghost(t, P, l, F.E, F.EG, 1);
     }
 };
 
@@ -2070,7 +2160,7 @@ static void residual_norm_d(mg_tree *t, Fields<double> &F, int homog, double *ou
         const long long cell_base = t->blocks[L.first + L.nref].cell_off;
         ++t->launches;
         const int C = cells_of<D>(L.n), GH = 2 * D * face_of<D>(L.n);
-        const size_t smt = 2 * (sizeof(BlockDesc) + sizeof(double) * (2 * C + GH + (F.E ? C + GH : 0)));
+        const size_t smt = 2 * (sizeof(BlockDesc) + sizeof(LevelDesc) + sizeof(double) * (2 * C + GH + (F.E ? C + GH : 0)));
         if ((L.n == 8 || L.n == 16) && smt <= 200 * 1024) {
             auto kern = L.n == 8 ? k_resid_tma<D, 8> : k_resid_tma<D, 16>;
             const int thr = threads_for(C);
@@ -2236,7 +2326,7 @@ static int residual_norm_noalloc_d(mg_tree *t, double *scratch, double *out3) {
         const int nleaf = L.nb - L.nref;
         if (nleaf <= 0) continue;
         const int C = cells_of<D>(L.n), GH = 2 * D * face_of<D>(L.n);
-        const size_t smt = 2 * (sizeof(BlockDesc) + sizeof(double) * (2 * C + GH + (t->f64.E ? C + GH : 0)));
+        const size_t smt = 2 * (sizeof(BlockDesc) + sizeof(LevelDesc) + sizeof(double) * (2 * C + GH + (t->f64.E ? C + GH : 0)));
         if ((L.n == 8 || L.n == 16) && smt <= 200 * 1024) {
             auto kern = L.n == 8 ? k_resid_tma<D, 8> : k_resid_tma<D, 16>;
             need += std::min(nleaf, resident_ctas(kern, threads_for(C), smt) * t->nsm);
@@ -2259,7 +2349,7 @@ static int residual_norm_noalloc_d(mg_tree *t, double *scratch, double *out3) {
         if (nleaf <= 0) continue;
         const long long cell_base = t->blocks[L.first + L.nref].cell_off;
         const int C = cells_of<D>(L.n), GH = 2 * D * face_of<D>(L.n);
-        const size_t smt = 2 * (sizeof(BlockDesc) + sizeof(double) * (2 * C + GH + (F.E ? C + GH : 0)));
+        const size_t smt = 2 * (sizeof(BlockDesc) + sizeof(LevelDesc) + sizeof(double) * (2 * C + GH + (F.E ? C + GH : 0)));
         ++t->launches;
         if ((L.n == 8 || L.n == 16) && smt <= 200 * 1024) {
             auto kern = L.n == 8 ? k_resid_tma<D, 8> : k_resid_tma<D, 16>;

@@ -3,6 +3,8 @@
 // inverse, and the C ABI declared in include/mg.h.
 #include <algorithm>
 #include <array>
+#include <atomic>
+#include <thread>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -277,6 +279,21 @@ static int build(mg_tree *t) {
         if (t->bc.type[f] == MG_BC_DIRICHLET) t->singular = false;
     t->nc = (int)(t->lev[0].nb * ipow(t->lev[0].n, D));
     t->ns = t->nc + (t->singular ? 1 : 0);
+    t->groups.assign(nl, {});
+    for (int l = 0; l < nl; l++) {
+        t->lev[l].group = l;
+        t->lev[l].coarsest = l == 0;
+        t->lev[l].parent_same_n = l > 0 && t->lev[l - 1].n == t->lev[l].n;
+        t->groups[l] = {l};
+    }
+    TreeCoarse tc{};
+    tc.first = t->lev[0].first; tc.nb = t->lev[0].nb; tc.n = t->lev[0].n;
+    tc.nc = t->nc; tc.ns = t->ns; tc.singular = t->singular ? 1 : 0; tc.group = 0; tc.lvl = 0;
+    tc.cell0 = t->lev[0].cell_first; tc.minv_off = 0; tc.cvec_off = 0;
+    t->tcoarse = {tc};
+    t->minv_total = (long long)t->ns * t->ns;
+    t->cvec_total = t->ns;
+    t->max_nc = t->nc;
     t->built = true;
     return MG_OK;
 }
@@ -354,9 +371,10 @@ static void drop_graphs(mg_tree *t);
 static int upload_bc(mg_tree *t) {
     drop_graphs(t);
     std::vector<double> all;
-    std::vector<LevelDesc> ld(t->lev.size());
-    for (size_t l = 0; l < t->lev.size(); l++) {
-        const LevelHost &L = t->lev[l];
+    const std::vector<LevelHost> &src = t->is_batch ? t->tl : t->lev;
+    std::vector<LevelDesc> ld(src.size());
+    for (size_t l = 0; l < src.size(); l++) {
+        const LevelHost &L = src[l];
         LevelDesc &d = ld[l];
         for (int e = 0; e < 3; e++) {
             d.h[e] = L.h[e];
@@ -364,6 +382,12 @@ static int upload_bc(mg_tree *t) {
             d.ncell[e] = L.ncell[e];
         }
         d.n = L.n; d.first = L.first; d.nb = L.nb; d.nref = L.nref;
+        {
+            double sw = 0;
+            for (int e = 0; e < t->dim; e++) sw += d.inv_h2[e];
+            d.inv_diag = 1.0 / (2.0 * sw + t->helm);
+            d.pad_ = 0;
+        }
         for (int f = 0; f < 6; f++) {
             d.bc_off[f] = -1;
             if (!L.bc[f].empty()) {
@@ -390,27 +414,26 @@ static int upload_bc(mg_tree *t) {
 // values (bordered by sum V x = 0 when the problem has no Dirichlet face),
 // assembled row by row from the 5/7-point stencil and inverted by
 // Gauss-Jordan elimination with partial pivoting (FP64, host).
-static int build_coarse_inverse(mg_tree *t) {
+// Dense inverse of one tree's coarsest-level operator with homogeneous
+// boundary values (bordered by sum V x = 0 when the problem has no
+// Dirichlet face), assembled row by row from the 5/7-point stencil and
+// inverted by Gauss-Jordan elimination with partial pivoting (FP64, host).
+static std::string coarse_inverse_one(const mg_tree *t, const TreeCoarse &tc, const LevelHost &L,
+                                      const double *eps, double *Inv) {
     const int D = t->dim;
-    const LevelHost &L = t->lev[0];
-    const int n = L.n, C = (int)ipow(n, D), nc = t->nc, ns = t->ns;
-    std::vector<double> eps(nc, 1.0);
-    if (t->var_eps) {
-        CK(cudaStreamSynchronize(t->stream));
-        CK(cudaMemcpy(eps.data(), t->f64.E, sizeof(double) * nc, cudaMemcpyDeviceToHost));
-    }
+    const int n = L.n, C = (int)ipow(n, D), nc = tc.nc, ns = tc.ns;
     std::vector<int> rowmap((size_t)L.ncell[0] * L.ncell[1] * L.ncell[2]);
     auto cellkey = [&](const int *G) { return ((size_t)G[2] * L.ncell[1] + G[1]) * L.ncell[0] + G[0]; };
-    for (int b = 0; b < L.nb; b++) {
-        const BlockDesc &B = t->blocks[L.first + b];
+    for (int b = 0; b < tc.nb; b++) {
+        const BlockDesc &B = t->blocks[tc.first + b];
         for (int c = 0; c < C; c++) {
             int G[3] = {B.ijk[0] * n + c % n, B.ijk[1] * n + (c / n) % n, D == 3 ? B.ijk[2] * n + c / (n * n) : 0};
             rowmap[cellkey(G)] = b * C + c;
         }
     }
     std::vector<double> M((size_t)ns * ns, 0.0);
-    for (int b = 0; b < L.nb; b++) {
-        const BlockDesc &B = t->blocks[L.first + b];
+    for (int b = 0; b < tc.nb; b++) {
+        const BlockDesc &B = t->blocks[tc.first + b];
         for (int c = 0; c < C; c++) {
             const int row = b * C + c;
             int G[3] = {B.ijk[0] * n + c % n, B.ijk[1] * n + (c / n) % n, D == 3 ? B.ijk[2] * n + c / (n * n) : 0};
@@ -426,7 +449,7 @@ static int build_coarse_inverse(mg_tree *t) {
                     }
                     double w = 1.0 / (L.h[d] * L.h[d]);
                     const int col = phys ? -1 : rowmap[cellkey(Q)];
-                    const double ec = eps[row], eo = phys ? ec : eps[col];
+                    const double ec = eps ? eps[row] : 1.0, eo = phys ? ec : (eps ? eps[col] : 1.0);
                     w *= 2.0 * ec * eo / (ec + eo);
                     if (t->geom == MG_CYL && d == 0) w *= (t->lo[0] + (G[0] + s) * L.h[0]) / ri;
                     if (!phys) {
@@ -437,7 +460,7 @@ static int build_coarse_inverse(mg_tree *t) {
                     }
                 }
             M[(size_t)row * ns + row] -= t->helm;
-            if (t->singular) {
+            if (tc.singular) {
                 double V = 1.0;
                 for (int d = 0; d < D; d++) V *= L.h[d];
                 if (t->geom == MG_CYL) V = 2.0 * M_PI * ri * L.h[0] * L.h[1];
@@ -447,13 +470,13 @@ static int build_coarse_inverse(mg_tree *t) {
         }
     }
     // Gauss-Jordan on [M | I]
-    std::vector<double> Inv((size_t)ns * ns, 0.0);
+    for (size_t i = 0; i < (size_t)ns * ns; i++) Inv[i] = 0.0;
     for (int i = 0; i < ns; i++) Inv[(size_t)i * ns + i] = 1.0;
     for (int c = 0; c < ns; c++) {
         int p = c;
         for (int r = c + 1; r < ns; r++)
             if (std::fabs(M[(size_t)r * ns + c]) > std::fabs(M[(size_t)p * ns + c])) p = r;
-        if (M[(size_t)p * ns + c] == 0.0) return fail(MG_ERR_ARG, "coarsest-level matrix is singular");
+        if (M[(size_t)p * ns + c] == 0.0) return "coarsest-level matrix is singular";
         if (p != c)
             for (int e = 0; e < ns; e++) {
                 std::swap(M[(size_t)c * ns + e], M[(size_t)p * ns + e]);
@@ -471,8 +494,36 @@ static int build_coarse_inverse(mg_tree *t) {
             }
         }
     }
-    if (!t->d_minv) CK(cudaMalloc((void **)&t->d_minv, sizeof(double) * (size_t)ns * ns));
-    CK(cudaMemcpy(t->d_minv, Inv.data(), sizeof(double) * (size_t)ns * ns, cudaMemcpyHostToDevice));
+    return "";
+}
+
+// Inverses of every tree's coarsest level (trees in parallel host threads).
+int build_coarse_inverse(mg_tree *t) {
+    std::vector<double> eps;
+    if (t->var_eps) {
+        CK(cudaStreamSynchronize(t->stream));
+        eps.resize(t->ncells);
+        CK(cudaMemcpy(eps.data(), t->f64.E, sizeof(double) * t->ncells, cudaMemcpyDeviceToHost));
+    }
+    std::vector<double> inv(t->minv_total);
+    std::vector<std::string> errs(t->tcoarse.size());
+    const int nthr = (int)std::max<unsigned>(1, std::min<unsigned>(std::thread::hardware_concurrency(), 64));
+    std::atomic<int> next(0);
+    auto work = [&]() {
+        for (int i = next++; i < (int)t->tcoarse.size(); i = next++) {
+            const TreeCoarse &tc = t->tcoarse[i];
+            const LevelHost &L = t->is_batch ? t->tl[tc.lvl] : t->lev[tc.lvl];
+            errs[i] = coarse_inverse_one(t, tc, L, t->var_eps ? eps.data() + tc.cell0 : nullptr, inv.data() + tc.minv_off);
+        }
+    };
+    std::vector<std::thread> pool;
+    for (int k = 1; k < std::min<int>(nthr, (int)t->tcoarse.size()); k++) pool.emplace_back(work);
+    work();
+    for (auto &th : pool) th.join();
+    for (auto &e : errs)
+        if (!e.empty()) return fail(MG_ERR_ARG, e);
+    if (!t->d_minv) CK(cudaMalloc((void **)&t->d_minv, sizeof(double) * (size_t)std::max(1LL, t->minv_total)));
+    CK(cudaMemcpy(t->d_minv, inv.data(), sizeof(double) * (size_t)t->minv_total, cudaMemcpyHostToDevice));
     t->minv_ok = true;
     return MG_OK;
 }
@@ -496,7 +547,9 @@ extern "C" int mg_tree_finalize(mg_tree *t, void *stream) {
     if ((rc = dalloc(&t->d_partials, 3 * nleafb))) return rc;
     if ((rc = dalloc(&t->d_red, 3))) return rc;
     if ((rc = dalloc(&t->d_status, 1))) return rc;
-    if ((rc = dalloc(&t->d_cvec, t->ns))) return rc;
+    if ((rc = dalloc(&t->d_cvec, t->cvec_total))) return rc;
+    CK(cudaMalloc((void **)&t->d_tcoarse, sizeof(TreeCoarse) * t->tcoarse.size()));
+    CK(cudaMemcpy(t->d_tcoarse, t->tcoarse.data(), sizeof(TreeCoarse) * t->tcoarse.size(), cudaMemcpyHostToDevice));
     CK(cudaMallocHost((void **)&t->h_red, 3 * sizeof(double)));
     CK(cudaStreamCreateWithFlags(&t->cap_stream, cudaStreamNonBlocking));
     t->finalized = true;
@@ -657,7 +710,7 @@ extern "C" int mg_vcycle(mg_tree *t, int n, const mg_params *p) {
     params_or_default(p, &q);
     const std::string key = "v64:" + std::to_string(q.n_down) + ":" + std::to_string(q.n_up);
     for (int c = 0; c < n; c++) {
-        int rc = run_graph(t, key, [&] { vcycle<double>(t, t->f64, (int)t->lev.size() - 1, q.n_down, q.n_up, 0); });
+        int rc = run_graph(t, key, [&] { vcycle<double>(t, t->f64, (int)t->groups.size() - 1, q.n_down, q.n_up, 0); });
         if (rc) return rc;
     }
     return check_cuda("vcycle");
@@ -704,7 +757,7 @@ extern "C" int mg_solve(mg_tree *t, double rel_tol, int max_cycles, int fmg_firs
     NEED_FINAL(t);
     mg_params q;
     params_or_default(p, &q);
-    const int top = (int)t->lev.size() - 1;
+    const int top = (int)t->groups.size() - 1;
     double o[3];
     int cycles = 0, rc;
     double rel = 1.0;
@@ -798,7 +851,7 @@ extern "C" int mg_adjoint(mg_tree *t, const double *g, double *dLdf, double *dLd
     CK(cudaMemsetAsync(t->adj.X, 0, sizeof(double) * t->ncells, t->stream));
     CK(cudaMemsetAsync(t->adj.XG, 0, sizeof(double) * t->nghost, t->stream));
     fmg<double>(t, t->adj, q.n_down, q.n_up, 1);
-    const int top = (int)t->lev.size() - 1;
+    const int top = (int)t->groups.size() - 1;
     for (int c = 0; c < n_cycles; c++) vcycle<double>(t, t->adj, top, q.n_down, q.n_up, 1);
     if ((rc = leaf_copy(t, t->adj.X, (const double *)dLdf, false))) return rc;
     if (t->geom == MG_CYL) {
@@ -864,7 +917,7 @@ extern "C" int mg_tree_destroy(mg_tree *t) {
         free_fields(t->adj, false);
         free_fields(t->f32, true);
         cudaFree(t->d_blocks); cudaFree(t->d_levels); cudaFree(t->d_bcplanes);
-        cudaFree(t->d_r64); cudaFree(t->d_minv); cudaFree(t->d_cvec); cudaFree(t->d_partials); cudaFree(t->d_red); cudaFree(t->d_status);
+        cudaFree(t->d_r64); cudaFree(t->d_minv); cudaFree(t->d_cvec); cudaFree(t->d_partials); cudaFree(t->d_red); cudaFree(t->d_status); cudaFree(t->d_tcoarse);
         cudaFreeHost(t->h_red);
         drop_graphs(t);
         if (t->cap_stream) cudaStreamDestroy(t->cap_stream);
