@@ -35,7 +35,8 @@
 extern "C" {
 #endif
 
-typedef struct mg_tree mg_tree; /* opaque: mesh, level tables, device fields */
+typedef struct mg_tree mg_tree;   /* opaque: mesh, level tables, device fields */
+typedef struct mg_batch mg_batch; /* opaque: many independent trees solved together */
 
 enum {
     MG_OK = 0,
@@ -215,6 +216,66 @@ int mg_residual_norm_noalloc(mg_tree *t, double *l2, double *linf);
 
 /* mg_tree_destroy -- free device and host memory (synchronises the stream). */
 int mg_tree_destroy(mg_tree *t);
+
+/* ------------------------------------------------------------- batch ----
+ * Many independent trees solved together: every smoothing, transfer and
+ * residual step is one launch over the blocks of all trees (the trees'
+ * cycles are those of Sec. 2.4, run side by side), each tree keeps its own
+ * exact coarsest-level solve, and a whole cycle plus its per-tree residual
+ * norms is replayed as one CUDA graph.
+ *
+ * mg_batch_create -- merge n trees into a batch with its own device
+ *   storage on `stream`.  The trees are read (mesh, refinement, boundary
+ *   planes set with mg_set_bc_plane) and may be finalized or not; the batch
+ *   keeps no reference to them, so they may be destroyed afterwards.  All
+ *   trees must share dim, geometry, boundary types and values, lambda and
+ *   lo; block size, base grid, hi and refinement may differ.
+ *   MG_ERR_ARG on a mismatch, MG_ERR_BALANCE / MG_ERR_UNSUPPORTED as for
+ *   mg_tree_finalize, MG_ERR_CUDA on allocation failure.
+ *
+ * Leaf data of a batch are the trees' leaf arrays (each in its tree's leaf
+ * order) concatenated in tree order; mg_batch_leaf_offsets gives the n + 1
+ * offsets (host_off[i] = first value of tree i, host_off[n] = total). */
+int mg_batch_create(int n, mg_tree *const *trees, void *stream, mg_batch **out);
+int mg_batch_leaf_offsets(mg_batch *b, int64_t *host_off);
+
+/* Field I/O (FP64 device arrays of host_off[n] values), as mg_set_rhs,
+ * mg_set_eps, mg_set_phi and mg_get_phi for every tree at once. */
+int mg_batch_set_rhs(mg_batch *b, const double *dev_f);
+int mg_batch_set_eps(mg_batch *b, const double *dev_eps);
+int mg_batch_set_phi(mg_batch *b, const double *dev_phi);
+int mg_batch_get_phi(mg_batch *b, double *dev_phi);
+
+/* mg_batch_vcycle / mg_batch_fmg -- n V-cycles / one FMG cycle of every
+ * tree (FP64), as mg_vcycle / mg_fmg. */
+int mg_batch_vcycle(mg_batch *b, int n_cycles, const mg_params *p);
+int mg_batch_fmg(mg_batch *b, const mg_params *p);
+
+/* mg_batch_residual_norms -- composite residual norms of every tree, as
+ * mg_residual_norm: host_l2[i], host_linf[i] for tree i (n values each).
+ * Synchronises the stream. */
+int mg_batch_residual_norms(mg_batch *b, double *host_l2, double *host_linf);
+
+/* mg_batch_solve -- as mg_solve, cycling all trees together until every
+ * tree's residual is at most rel_tol times its initial residual (a tree
+ * that has converged keeps cycling with the others).  host_rel (optional,
+ * n values) receives each tree's final relative residual; *cycles_done the
+ * number of cycles.  MG_ERR_NOT_CONVERGED when some tree is above rel_tol
+ * after max_cycles. */
+int mg_batch_solve(mg_batch *b, double rel_tol, int max_cycles, int fmg_first, const mg_params *p,
+                   int *cycles_done, double *host_rel);
+
+/* Introspection: kernels launched so far; the segments (launch units) of
+ * the batch -- per segment host_info = {block size, group, blocks, covered
+ * blocks, coarsest flag, parent has the same block size}; and sweep timing
+ * on one segment, as mg_time_sweeps. */
+int mg_batch_launch_count(mg_batch *b, int64_t *n);
+int mg_batch_num_segments(mg_batch *b, int *nseg, int *ngroups);
+int mg_batch_segment_info(mg_batch *b, int seg, int32_t host_info[6]);
+int mg_batch_time_sweeps(mg_batch *b, int segment, int n_sweeps, int precision, double host_out[4]);
+
+/* mg_batch_destroy -- free the batch (synchronises its stream). */
+int mg_batch_destroy(mg_batch *b);
 
 /* Message of the last failed call on this thread ("" if none). */
 const char *mg_last_error(void);

@@ -53,7 +53,9 @@ class Tree:
             self.finalize()
 
     @classmethod
-    def from_problem(cls, p, set_fields=True, device="cuda"):
+    def from_problem(cls, p, set_fields=True, device="cuda", finalize=True):
+        """Tree of a synthetic problem with its boundary planes; finalize=False
+        leaves it on the host (e.g. as a member of a Batch, which copies it)."""
         from synth import workloads as W
         t = cls(p.dim, p.N, p.geom, p.bc_type, p.bc_val, p.base, p.lo, p.hi, p.refine, p.coarse_max,
                 finalize=False)
@@ -63,6 +65,8 @@ class Tree:
                     v = W.bc_plane(p, face, info["ncell"], info["h"])
                     if v is not None:
                         t.set_bc_plane(face, l, v)
+        if not finalize:
+            return t
         t.finalize()
         if set_fields:
             if p.eps is not None or p.eps_leaf is not None:
@@ -223,6 +227,99 @@ class Tree:
         check(self.L.mg_adjoint(self._h, self._leaf(g.contiguous()), _ptr(dLdf), _ptr(dLde) if want_eps else None,
                                 C.byref(p), int(n_cycles)))
         return dLdf, dLde
+
+
+class Batch:
+    """Many independent trees solved together (one launch per segment over
+    the blocks of all trees).  Leaf fields are the trees' leaf arrays
+    concatenated in tree order; ``offsets[i]:offsets[i+1]`` is tree i."""
+
+    def __init__(self, trees):
+        L = _lib.load()
+        self.L = L
+        self.trees = list(trees)
+        arr = (C.c_void_p * len(self.trees))(*[t._h.value for t in self.trees])
+        h = C.c_void_p()
+        stream = torch.cuda.current_stream().cuda_stream
+        check(L.mg_batch_create(len(self.trees), arr, C.c_void_p(stream), C.byref(h)))
+        self._h = h
+        off = np.zeros(len(self.trees) + 1, np.int64)
+        check(L.mg_batch_leaf_offsets(self._h, off.ctypes.data_as(C.c_void_p)))
+        self.offsets = off
+        self.n_leaf = int(off[-1])
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            self.L.mg_batch_destroy(h)
+            self._h = None
+
+    def _leaf(self, t):
+        assert t.numel() == self.n_leaf, "batch leaf field has %d values, expected %d" % (t.numel(), self.n_leaf)
+        return _ptr(t)
+
+    def set_rhs(self, f):
+        check(self.L.mg_batch_set_rhs(self._h, self._leaf(f)))
+
+    def set_eps(self, e):
+        check(self.L.mg_batch_set_eps(self._h, self._leaf(e)))
+
+    def set_phi(self, x):
+        check(self.L.mg_batch_set_phi(self._h, self._leaf(x)))
+
+    def get_phi(self, out=None):
+        out = torch.empty(self.n_leaf, dtype=torch.float64, device="cuda") if out is None else out
+        check(self.L.mg_batch_get_phi(self._h, self._leaf(out)))
+        return out
+
+    def vcycle(self, n=1, n_down=2, n_up=2):
+        p = _params(n_down, n_up)
+        check(self.L.mg_batch_vcycle(self._h, n, C.byref(p)))
+
+    def fmg(self, n_down=2, n_up=2):
+        p = _params(n_down, n_up)
+        check(self.L.mg_batch_fmg(self._h, C.byref(p)))
+
+    def residual_norms(self):
+        n = len(self.trees)
+        l2, li = np.zeros(n), np.zeros(n)
+        check(self.L.mg_batch_residual_norms(self._h, l2.ctypes.data_as(C.c_void_p), li.ctypes.data_as(C.c_void_p)))
+        return l2, li
+
+    def solve(self, rel_tol=1e-10, max_cycles=50, fmg_first=True, precision=MG_FP64, inner_cycles=1,
+              n_down=2, n_up=2, raise_on_fail=True):
+        p = _params(n_down, n_up, precision, inner_cycles)
+        cyc = C.c_int()
+        rel = np.zeros(len(self.trees))
+        rc = self.L.mg_batch_solve(self._h, float(rel_tol), int(max_cycles), int(bool(fmg_first)), C.byref(p),
+                                   C.byref(cyc), rel.ctypes.data_as(C.c_void_p))
+        check(rc, allow=() if raise_on_fail else (-4,))
+        return cyc.value, rel
+
+    def launch_count(self):
+        n = C.c_int64()
+        check(self.L.mg_batch_launch_count(self._h, C.byref(n)))
+        return n.value
+
+    def segments(self):
+        ns, ng = C.c_int(), C.c_int()
+        check(self.L.mg_batch_num_segments(self._h, C.byref(ns), C.byref(ng)))
+        out = []
+        for s in range(ns.value):
+            info = np.zeros(6, np.int32)
+            check(self.L.mg_batch_segment_info(self._h, s, info.ctypes.data_as(C.c_void_p)))
+            out.append(dict(n=int(info[0]), group=int(info[1]), nb=int(info[2]), nref=int(info[3]),
+                            coarsest=bool(info[4]), parent_same_n=bool(info[5])))
+        return out
+
+    def time_sweeps(self, segment=-1, n_sweeps=4, precision=MG_FP64):
+        seg = self.segments()
+        if segment < 0:
+            segment = max((s for s in range(len(seg)) if not seg[s]["coarsest"]),
+                          key=lambda s: seg[s]["nb"] * seg[s]["n"] ** self.trees[0].dim)
+        out = (C.c_double * 4)()
+        check(self.L.mg_batch_time_sweeps(self._h, segment, n_sweeps, precision, out))
+        return tuple(out), segment
 
 
 from .autograd import CleanB, MGSolve  # noqa: E402,F401

@@ -117,6 +117,13 @@ struct mg_tree {
     mg::TreeCoarse *d_tcoarse = nullptr;
     bool is_batch = false;
     int max_nc = 0;                           // largest coarsest-level system
+    // batch only: leaf runs (pool cell, concatenated leaf index, count) for
+    // I/O, first leaf of each tree, and the residual slots of each tree
+    std::vector<long long> run_cell, run_leaf, run_len, tree_leaf_off;
+    long long *d_runs = nullptr;              // run chunks (cell, leaf, length), 3 per chunk
+    int n_runs = 0;
+    int *d_slot_off = nullptr, *d_slots = nullptr;
+    double *d_tree3 = nullptr, *h_tree3 = nullptr;
     std::vector<mg::BlockDesc> blocks;
     long long ncells = 0, nghost = 0, nleaf_cells = 0;
 

@@ -1470,7 +1470,7 @@ template <int D, int NT>
 __global__ void __launch_bounds__(kMaxThreads, 4) k_resid_tma(KParams P, int first, int nblocks, Fields<double> F,
                                                               double *__restrict__ partials,
                                                               double *__restrict__ rleaf, long long leaf_base,
-                                                              float *__restrict__ f32) {
+                                                              float *__restrict__ f32, int per_block = 0) {
     using T = double;
     constexpr int n = NT, C = cells_of<D>(NT), FC = face_of<D>(NT), GH = 2 * D * FC;
     constexpr int DESC = (int)((sizeof(BlockDesc) + sizeof(LevelDesc)) / sizeof(T));
@@ -1593,6 +1593,29 @@ __global__ void __launch_bounds__(kMaxThreads, 4) k_resid_tma(KParams P, int fir
             s2 = fma(vol, bs2, s2);
             if (tid == 0) sv += vol * C;
         }
+        if (per_block) {  // this block's sums into its own slot (per-tree norms of a batch)
+            double a = s2, bb = sv, mm = mx;
+            for (int o = 16; o > 0; o >>= 1) {
+                a += __shfl_down_sync(0xffffffffu, a, o);
+                bb += __shfl_down_sync(0xffffffffu, bb, o);
+                mm = fmax(mm, __shfl_down_sync(0xffffffffu, mm, o));
+            }
+            const int w = tid >> 5, lane = tid & 31, nw = (nth + 31) >> 5;
+            if (lane == 0) { sred[0][w] = a; sred[1][w] = bb; sred[2][w] = mm; }
+            __syncthreads();
+            if (tid == 0) {
+                double x = 0, y = 0, z = 0;
+                for (int e = 0; e < nw; e++) { x += sred[0][e]; y += sred[1][e]; z = fmax(z, sred[2][e]); }
+                partials[3LL * g] = x;
+                partials[3LL * g + 1] = y;
+                partials[3LL * g + 2] = z;
+            }
+            s2 = 0; sv = 0; mx = 0;
+        }
+    }
+    if (per_block) {
+        if (tid == 0) bulk_wait0();
+        return;
     }
     if (tid == 0) bulk_wait0();
     for (int o = 16; o > 0; o >>= 1) {
@@ -1609,6 +1632,36 @@ __global__ void __launch_bounds__(kMaxThreads, 4) k_resid_tma(KParams P, int fir
         partials[3 * blockIdx.x] = a;
         partials[3 * blockIdx.x + 1] = bb;
         partials[3 * blockIdx.x + 2] = m;
+    }
+}
+
+// Per-tree sums of per-block residual partials (slots listed per tree).
+__global__ void __launch_bounds__(256) k_reduce_trees(const double *__restrict__ partials,
+                                                      const int *__restrict__ slot_off,
+                                                      const int *__restrict__ slots, double *__restrict__ out) {
+    const int tr = blockIdx.x;
+    double a = 0, b = 0, m = 0;
+    for (int e = slot_off[tr] + threadIdx.x; e < slot_off[tr + 1]; e += blockDim.x) {
+        const long long q = 3LL * slots[e];
+        a += partials[q];
+        b += partials[q + 1];
+        m = fmax(m, partials[q + 2]);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, o);
+        b += __shfl_down_sync(0xffffffffu, b, o);
+        m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
+    }
+    __shared__ double sh[3][8];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) { sh[0][w] = a; sh[1][w] = b; sh[2][w] = m; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double x = 0, y = 0, z = 0;
+        for (int e = 0; e < (int)(blockDim.x >> 5); e++) { x += sh[0][e]; y += sh[1][e]; z = fmax(z, sh[2][e]); }
+        out[3 * tr] = x;
+        out[3 * tr + 1] = y;
+        out[3 * tr + 2] = z;
     }
 }
 
@@ -2166,7 +2219,7 @@ static void residual_norm_d(mg_tree *t, Fields<double> &F, int homog, double *ou
             const int thr = threads_for(C);
             const int grid = std::min(nleaf, resident_ctas(kern, thr, smt) * t->nsm);
             kern<<<grid, thr, smt, t->stream>>>(P, L.first + L.nref, nleaf, F, t->d_partials + 3 * slot, r64_leaf,
-                                               leaf_base, f32_cells);
+                                               leaf_base, f32_cells, 0);
             slot += grid;
         } else {
             k_resnorm<D><<<nleaf, threads_for(C), 0, t->stream>>>(P, L.first + L.nref, F, t->d_partials + 3 * slot,
@@ -2186,6 +2239,61 @@ static void residual_norm_d(mg_tree *t, Fields<double> &F, int homog, double *ou
 void residual_enqueue(mg_tree *t, Fields<double> &F, int homog, double *r64_leaf, float *f32_cells) {
     if (t->dim == 2) residual_norm_d<2>(t, F, homog, nullptr, r64_leaf, f32_cells);
     else residual_norm_d<3>(t, F, homog, nullptr, r64_leaf, f32_cells);
+}
+
+// Batch: composite residual with one partial per leaf block, reduced per
+// tree into d_tree3 (3 values per tree), copied to the pinned t->h_tree3.
+template <int D> static void residual_trees_d(mg_tree *t, Fields<double> &F, float *f32) {
+    Launch<double, D>::refresh(t, F, 0);
+    const KParams P = kparams(t, 0);
+    int slot = 0;
+    for (size_t l = 0; l < t->lev.size(); l++) {
+        const LevelHost &L = t->lev[l];
+        const int nleaf = L.nb - L.nref;
+        if (nleaf <= 0) continue;
+        const long long cell_base = t->blocks[L.first + L.nref].cell_off;
+        ++t->launches;
+        const int C = cells_of<D>(L.n), GH = 2 * D * face_of<D>(L.n);
+        const size_t smt = 2 * (sizeof(BlockDesc) + sizeof(LevelDesc) + sizeof(double) * (2 * C + GH + (F.E ? C + GH : 0)));
+        if ((L.n == 8 || L.n == 16) && smt <= 200 * 1024) {
+            auto kern = L.n == 8 ? k_resid_tma<D, 8> : k_resid_tma<D, 16>;
+            const int thr = threads_for(C);
+            const int grid = std::min(nleaf, resident_ctas(kern, thr, smt) * t->nsm);
+            kern<<<grid, thr, smt, t->stream>>>(P, L.first + L.nref, nleaf, F, t->d_partials + 3LL * slot, nullptr, 0,
+                                               f32, 1);
+        } else {
+            k_resnorm<D><<<nleaf, threads_for(C), 0, t->stream>>>(P, L.first + L.nref, F, t->d_partials + 3LL * slot,
+                                                                  nullptr, 0, cell_base, f32);
+        }
+        slot += nleaf;
+    }
+    ++t->launches;
+    k_reduce_trees<<<(int)t->tcoarse.size(), 256, 0, t->stream>>>(t->d_partials, t->d_slot_off, t->d_slots,
+                                                                   t->d_tree3);
+    cudaMemcpyAsync(t->h_tree3, t->d_tree3, 3 * sizeof(double) * t->tcoarse.size(), cudaMemcpyDeviceToHost,
+                    t->stream);
+}
+
+// Batch leaf I/O: one CTA per run chunk (pool cell, leaf index, length),
+// copying between the concatenated per-tree leaf arrays and the pool.
+__global__ void __launch_bounds__(256) k_runs_copy(const long long *__restrict__ runs, double *cells, double *leaf,
+                                                   int to_cells) {
+    const long long c0 = runs[3LL * blockIdx.x], l0 = runs[3LL * blockIdx.x + 1], len = runs[3LL * blockIdx.x + 2];
+    if (to_cells)
+        for (long long i = threadIdx.x; i < len; i += blockDim.x) cells[c0 + i] = leaf[l0 + i];
+    else
+        for (long long i = threadIdx.x; i < len; i += blockDim.x) leaf[l0 + i] = cells[c0 + i];
+}
+
+void leaf_runs_copy(mg_tree *t, double *cells, const double *leaf, bool to_cells) {
+    if (t->n_runs == 0) return;
+    ++t->launches;
+    k_runs_copy<<<t->n_runs, 256, 0, t->stream>>>(t->d_runs, cells, const_cast<double *>(leaf), to_cells ? 1 : 0);
+}
+
+void residual_enqueue_trees(mg_tree *t, Fields<double> &F, float *f32_cells, double *) {
+    if (t->dim == 2) residual_trees_d<2>(t, F, f32_cells);
+    else residual_trees_d<3>(t, F, f32_cells);
 }
 
 void residual_wait(mg_tree *t, double *out3) {
@@ -2355,7 +2463,7 @@ static int residual_norm_noalloc_d(mg_tree *t, double *scratch, double *out3) {
             auto kern = L.n == 8 ? k_resid_tma<D, 8> : k_resid_tma<D, 16>;
             const int grid = std::min(nleaf, resident_ctas(kern, threads_for(C), smt) * t->nsm);
             kern<<<grid, threads_for(C), smt, t->stream>>>(P, L.first + L.nref, nleaf, F, scratch + 3 * slot,
-                                                           nullptr, 0, nullptr);
+                                                           nullptr, 0, nullptr, 0);
             slot += grid;
         } else {
             k_resnorm<D><<<nleaf, threads_for(C), 0, t->stream>>>(P, L.first + L.nref, F, scratch + 3 * slot,

@@ -7,6 +7,8 @@
 #include <thread>
 #include <cmath>
 #include <cstring>
+#include <map>
+#include <tuple>
 #include <string>
 #include <vector>
 
@@ -644,6 +646,14 @@ extern "C" int mg_set_bc_plane(mg_tree *t, int face, int level, const double *va
 
 // copy between a leaf-order vector and the leaf cells of a pool field
 template <class T> static int leaf_copy(mg_tree *t, T *cells, const T *leaf, bool to_cells) {
+    if (t->is_batch) {
+        if constexpr (sizeof(T) == sizeof(double)) {
+            leaf_runs_copy(t, cells, leaf, to_cells);
+            return MG_OK;
+        } else {
+            return fail(MG_ERR_UNSUPPORTED, "batch leaf copies are FP64");
+        }
+    }
     long long off = 0;
     for (auto &L : t->lev) {
         const long long n = (long long)(L.nb - L.nref) * ipow(L.n, t->dim);
@@ -919,9 +929,413 @@ extern "C" int mg_tree_destroy(mg_tree *t) {
         cudaFree(t->d_blocks); cudaFree(t->d_levels); cudaFree(t->d_bcplanes);
         cudaFree(t->d_r64); cudaFree(t->d_minv); cudaFree(t->d_cvec); cudaFree(t->d_partials); cudaFree(t->d_red); cudaFree(t->d_status); cudaFree(t->d_tcoarse);
         cudaFreeHost(t->h_red);
+        cudaFree(t->d_runs); cudaFree(t->d_slot_off); cudaFree(t->d_slots); cudaFree(t->d_tree3);
+        cudaFreeHost(t->h_tree3);
         drop_graphs(t);
         if (t->cap_stream) cudaStreamDestroy(t->cap_stream);
     }
     delete t;
+    return MG_OK;
+}
+
+// ------------------------------------------------------------- batch ----
+// A batch merges many independent trees into one pool so that every cycle
+// step is one launch over the blocks of all trees.  Levels are aligned from
+// the top: level l of a tree with L levels joins group G - L + l (G the
+// largest level count), so the finest levels of all trees form the top
+// group and each tree still sees its own V-cycle (Sec. 2.4) in its own
+// order.  A group is split into segments, one per (block size, coarsest,
+// parent block size); a segment holds the covered blocks of its trees
+// first, then the leaves, tree by tree, Morton order within a tree.  A
+// tree's coarsest level stays contiguous for its exact solve; the level
+// descriptors are kept per (tree, level), since trees differ in spacing.
+
+struct mg_batch {
+    mg_tree *pool = nullptr;
+    int ntrees = 0;
+};
+
+static int merge_trees(mg_tree *P, int n, mg_tree *const *trees) {
+    const int D = trees[0]->dim;
+    int G = 0;
+    for (int i = 0; i < n; i++) G = std::max(G, (int)trees[i]->lev.size());
+    struct Key {
+        int group, coarsest, n, psn, solo;
+        bool operator<(const Key &o) const {
+            return std::tie(group, coarsest, n, psn, solo) < std::tie(o.group, o.coarsest, o.n, o.psn, o.solo);
+        }
+    };
+    std::map<Key, std::vector<std::pair<int, int>>> segs;  // members (tree, level) in tree order
+    std::vector<int> tl_off(n + 1, 0);
+    for (int i = 0; i < n; i++) {
+        const mg_tree *T = trees[i];
+        const int nl = (int)T->lev.size();
+        for (int l = 0; l < nl; l++) {
+            const LevelHost &L = T->lev[l];
+            // a coarsest level holding leaves gets a segment of its own, so
+            // that both its covered prefix and its contiguity hold
+            const int solo = (l == 0 && L.nref < L.nb) ? i : -1;
+            segs[Key{G - nl + l, l == 0, L.n, L.parent_same_n, solo}].push_back({i, l});
+        }
+        tl_off[i + 1] = tl_off[i] + nl;
+    }
+    P->tl.clear();
+    for (int i = 0; i < n; i++)
+        for (const LevelHost &L : trees[i]->lev) P->tl.push_back(L);
+    for (int i = 0; i < n; i++)
+        for (int l = 0; l < (int)trees[i]->lev.size(); l++) P->tl[tl_off[i] + l].group = G - (int)trees[i]->lev.size() + l;
+    // block ids and storage
+    std::vector<std::vector<int>> nid(n);
+    std::vector<int> btree;  // pool block -> tree
+    for (int i = 0; i < n; i++) nid[i].assign(trees[i]->blocks.size(), -1);
+    P->lev.clear();
+    P->groups.assign(G, {});
+    P->blocks.clear();
+    long long co = 0, go = 0;
+    int g = 0;
+    for (auto &kv : segs) {
+        const Key &k = kv.first;
+        LevelHost S;
+        S.n = k.n;
+        S.group = k.group;
+        S.coarsest = k.coarsest;
+        S.parent_same_n = k.psn;
+        S.first = g;
+        co = (co + 31) / 32 * 32;
+        go = (go + 31) / 32 * 32;
+        S.cell_first = co;
+        S.ghost_first = go;
+        const long long C = ipow(k.n, D), F = 2LL * D * (D == 2 ? k.n : (long long)k.n * k.n);
+        for (int part = 0; part < 2; part++)  // covered blocks, then leaves
+            for (auto &m : kv.second) {
+                const mg_tree *T = trees[m.first];
+                const LevelHost &L = T->lev[m.second];
+                const int r0 = part == 0 ? 0 : L.nref, r1 = part == 0 ? L.nref : L.nb;
+                for (int r = r0; r < r1; r++) {
+                    BlockDesc B = T->blocks[L.first + r];
+                    const int id = (int)P->blocks.size();
+                    nid[m.first][L.first + r] = id;
+                    B.cell_off = co + (long long)(id - S.first) * C;
+                    B.ghost_off = go + (long long)(id - S.first) * F;
+                    B.lev = tl_off[m.first] + m.second;
+                    P->blocks.push_back(B);
+                    btree.push_back(m.first);
+                }
+                if (part == 0) S.nref += L.nref;
+            }
+        S.nb = (int)P->blocks.size() - S.first;
+        S.ncells = S.nb * C;
+        S.nghost = S.nb * F;
+        co += S.ncells;
+        go += S.nghost;
+        g += S.nb;
+        P->groups[k.group].push_back((int)P->lev.size());
+        P->lev.push_back(S);
+    }
+    P->ncells = co;
+    P->nghost = go;
+    // links: parents, neighbours and ghost push slots in pool ids
+    for (size_t b = 0; b < P->blocks.size(); b++) {
+        BlockDesc &B = P->blocks[b];
+        const std::vector<int> &m = nid[btree[b]];
+        if (B.parent >= 0) B.parent = m[B.parent];
+        for (int f = 0; f < 6; f++) {
+            if (B.nbr[f] >= 0) B.nbr[f] = m[B.nbr[f]];
+            else if (B.nbr[f] <= -2) B.nbr[f] = -2 - m[-2 - B.nbr[f]];
+        }
+    }
+    for (auto &B : P->blocks)
+        for (int f = 0; f < 6; f++) {
+            B.push[f] = -1;
+            if (B.nbr[f] >= 0) {
+                const long long Fd = D == 2 ? B.n : (long long)B.n * B.n;
+                B.push[f] = P->blocks[B.nbr[f]].ghost_off + (f ^ 1) * Fd;
+            }
+        }
+    // coarsest level of every tree
+    P->tcoarse.clear();
+    P->minv_total = P->cvec_total = 0;
+    P->max_nc = 0;
+    for (int i = 0; i < n; i++) {
+        const mg_tree *T = trees[i];
+        const LevelHost &L0 = T->lev[0];
+        TreeCoarse tc{};
+        tc.first = nid[i][L0.first];
+        for (int r = 0; r < L0.nb; r++)
+            if (nid[i][L0.first + r] != tc.first + r) return fail(MG_ERR_ARG, "internal: coarsest level not contiguous");
+        tc.nb = L0.nb;
+        tc.n = L0.n;
+        tc.nc = (int)(L0.nb * ipow(L0.n, D));
+        tc.singular = T->singular ? 1 : 0;
+        tc.ns = tc.nc + tc.singular;
+        tc.group = G - (int)T->lev.size();
+        tc.lvl = tl_off[i];
+        tc.cell0 = P->blocks[tc.first].cell_off;
+        tc.minv_off = P->minv_total;
+        tc.cvec_off = P->cvec_total;
+        P->minv_total += (long long)tc.ns * tc.ns;
+        P->cvec_total += tc.ns;
+        P->max_nc = std::max(P->max_nc, tc.nc);
+        P->tcoarse.push_back(tc);
+    }
+    // leaf runs: tree i's leaf order is its levels in order, leaf blocks in
+    // order; in the pool each (tree, level) leaf range is one contiguous run
+    P->run_cell.clear(); P->run_leaf.clear(); P->run_len.clear();
+    P->tree_leaf_off.assign(n + 1, 0);
+    long long leaf = 0;
+    for (int i = 0; i < n; i++) {
+        const mg_tree *T = trees[i];
+        P->tree_leaf_off[i] = leaf;
+        for (const LevelHost &L : T->lev) {
+            const int nleaf = L.nb - L.nref;
+            if (nleaf <= 0) continue;
+            const int b0 = nid[i][L.first + L.nref];
+            for (int r = 1; r < nleaf; r++)
+                if (nid[i][L.first + L.nref + r] != b0 + r) return fail(MG_ERR_ARG, "internal: leaf run not contiguous");
+            const long long len = nleaf * ipow(L.n, D);
+            P->run_cell.push_back(P->blocks[b0].cell_off);
+            P->run_leaf.push_back(leaf);
+            P->run_len.push_back(len);
+            leaf += len;
+        }
+    }
+    P->tree_leaf_off[n] = leaf;
+    P->nleaf_cells = leaf;
+    P->singular = trees[0]->singular;
+    P->nc = P->max_nc;
+    P->ns = P->max_nc + (P->singular ? 1 : 0);
+    return MG_OK;
+}
+
+static int batch_device_tables(mg_tree *P, int n) {
+    // run chunks of at most 8192 values, one CTA each
+    std::vector<long long> runs;
+    for (size_t r = 0; r < P->run_len.size(); r++)
+        for (long long o = 0; o < P->run_len[r]; o += 8192) {
+            runs.push_back(P->run_cell[r] + o);
+            runs.push_back(P->run_leaf[r] + o);
+            runs.push_back(std::min<long long>(8192, P->run_len[r] - o));
+        }
+    P->n_runs = (int)(runs.size() / 3);
+    CK(cudaMalloc((void **)&P->d_runs, sizeof(long long) * std::max<size_t>(3, runs.size())));
+    if (!runs.empty()) CK(cudaMemcpy(P->d_runs, runs.data(), sizeof(long long) * runs.size(), cudaMemcpyHostToDevice));
+    // residual slots: one per leaf block, in the order the residual pass
+    // visits them (segments in order, leaf blocks in order), listed per tree
+    std::vector<std::vector<int>> per(n);
+    std::vector<int> tree_of(P->blocks.size(), 0);
+    {
+        // the tree of a block is the tree of its level descriptor
+        std::vector<int> tl_tree(P->tl.size(), 0);
+        for (int i = 0; i < n; i++) {
+            const int lo_ = P->tcoarse[i].lvl, hi_ = i + 1 < n ? P->tcoarse[i + 1].lvl : (int)P->tl.size();
+            for (int l = lo_; l < hi_; l++) tl_tree[l] = i;
+        }
+        for (size_t b = 0; b < P->blocks.size(); b++) tree_of[b] = tl_tree[P->blocks[b].lev];
+    }
+    int slot = 0;
+    for (const LevelHost &L : P->lev)
+        for (int r = L.nref; r < L.nb; r++) per[tree_of[L.first + r]].push_back(slot++);
+    std::vector<int> off(n + 1, 0), slots;
+    for (int i = 0; i < n; i++) {
+        off[i + 1] = off[i] + (int)per[i].size();
+        slots.insert(slots.end(), per[i].begin(), per[i].end());
+    }
+    CK(cudaMalloc((void **)&P->d_slot_off, sizeof(int) * (n + 1)));
+    CK(cudaMemcpy(P->d_slot_off, off.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice));
+    CK(cudaMalloc((void **)&P->d_slots, sizeof(int) * std::max<size_t>(1, slots.size())));
+    if (!slots.empty()) CK(cudaMemcpy(P->d_slots, slots.data(), sizeof(int) * slots.size(), cudaMemcpyHostToDevice));
+    CK(cudaMalloc((void **)&P->d_tree3, sizeof(double) * 3 * n));
+    CK(cudaMallocHost((void **)&P->h_tree3, sizeof(double) * 3 * n));
+    return MG_OK;
+}
+
+extern "C" int mg_batch_create(int n, mg_tree *const *trees, void *stream, mg_batch **out) {
+    if (!out || !trees || n < 1) return fail(MG_ERR_ARG, "need at least one tree");
+    *out = nullptr;
+    for (int i = 0; i < n; i++) {
+        if (!trees[i]) return fail(MG_ERR_ARG, "null tree");
+        int rc = build(trees[i]);
+        if (rc) return rc;
+    }
+    const mg_tree *A = trees[0];
+    for (int i = 1; i < n; i++) {
+        const mg_tree *T = trees[i];
+        bool same = T->dim == A->dim && T->geom == A->geom && T->helm == A->helm;
+        for (int f = 0; f < 6; f++)
+            same = same && T->bc.type[f] == A->bc.type[f] && T->bc.value[f] == A->bc.value[f];
+        for (int d = 0; d < 3; d++) same = same && T->lo[d] == A->lo[d];
+        if (!same) return fail(MG_ERR_ARG, "batch trees differ in dimension, geometry, boundary conditions, lambda or lo");
+    }
+    mg_tree *P = new mg_tree();
+    P->dim = A->dim; P->N = A->N; P->geom = A->geom; P->bc = A->bc; P->helm = A->helm;
+    for (int d = 0; d < 3; d++) { P->lo[d] = A->lo[d]; P->hi[d] = A->hi[d]; }
+    P->is_batch = true;
+    int rc = merge_trees(P, n, trees);
+    if (rc) { delete P; return rc; }
+    P->built = true;
+    if ((rc = mg_tree_finalize(P, stream)) || (rc = batch_device_tables(P, n))) {
+        mg_tree_destroy(P);
+        return rc;
+    }
+    mg_batch *b = new mg_batch();
+    b->pool = P;
+    b->ntrees = n;
+    *out = b;
+    return MG_OK;
+}
+
+#define NEED_BATCH(b)                                                     \
+    do {                                                                  \
+        if (!(b) || !(b)->pool) return fail(MG_ERR_ARG, "null batch");    \
+    } while (0)
+
+extern "C" int mg_batch_leaf_offsets(mg_batch *b, int64_t *off) {
+    NEED_BATCH(b);
+    if (!off) return fail(MG_ERR_ARG, "null output");
+    for (int i = 0; i <= b->ntrees; i++) off[i] = b->pool->tree_leaf_off[i];
+    return MG_OK;
+}
+
+extern "C" int mg_batch_set_rhs(mg_batch *b, const double *f) { NEED_BATCH(b); return mg_set_rhs(b->pool, f); }
+extern "C" int mg_batch_set_phi(mg_batch *b, const double *x) { NEED_BATCH(b); return mg_set_phi(b->pool, x); }
+extern "C" int mg_batch_get_phi(mg_batch *b, double *x) { NEED_BATCH(b); return mg_get_phi(b->pool, x); }
+extern "C" int mg_batch_set_eps(mg_batch *b, const double *e) { NEED_BATCH(b); return mg_set_eps(b->pool, e); }
+extern "C" int mg_batch_vcycle(mg_batch *b, int n, const mg_params *p) { NEED_BATCH(b); return mg_vcycle(b->pool, n, p); }
+extern "C" int mg_batch_fmg(mg_batch *b, const mg_params *p) { NEED_BATCH(b); return mg_fmg(b->pool, p); }
+
+static int batch_norms_wait(mg_tree *P, int n, double *l2, double *linf) {
+    CK(cudaStreamSynchronize(P->stream));
+    for (int i = 0; i < n; i++) {
+        const double *o = P->h_tree3 + 3 * i;
+        l2[i] = o[1] > 0 ? std::sqrt(o[0] / o[1]) : 0.0;
+        if (linf) linf[i] = o[2];
+    }
+    return MG_OK;
+}
+
+extern "C" int mg_batch_residual_norms(mg_batch *b, double *l2, double *linf) {
+    NEED_BATCH(b);
+    if (!l2 || !linf) return fail(MG_ERR_ARG, "null output");
+    mg_tree *P = b->pool;
+    residual_enqueue_trees(P, P->f64, nullptr, nullptr);
+    int rc = check_cuda("batch residual");
+    if (rc || (rc = batch_norms_wait(P, b->ntrees, l2, linf)) || (rc = check_status(P))) return rc;
+    for (int i = 0; i < b->ntrees; i++)
+        if (!std::isfinite(l2[i]) || !std::isfinite(linf[i])) return fail(MG_ERR_NAN, "residual is not finite");
+    return MG_OK;
+}
+
+// Cycles until every tree's composite residual is below rel_tol times its
+// initial one (all trees cycle together; a converged tree keeps cycling).
+extern "C" int mg_batch_solve(mg_batch *b, double rel_tol, int max_cycles, int fmg_first, const mg_params *p,
+                              int *cycles_done, double *rel_out) {
+    NEED_BATCH(b);
+    mg_tree *t = b->pool;
+    const int n = b->ntrees;
+    mg_params q;
+    params_or_default(p, &q);
+    const int top = (int)t->groups.size() - 1;
+    std::vector<double> r0(n), l2(n), rel(n, 1.0);
+    int cycles = 0, rc;
+    const std::string sfx = ":" + std::to_string(q.n_down) + ":" + std::to_string(q.n_up);
+    auto update = [&](bool first) -> double {
+        batch_norms_wait(t, n, l2.data(), nullptr);
+        double worst = 0;
+        for (int i = 0; i < n; i++) {
+            if (first) { r0[i] = l2[i]; rel[i] = r0[i] > 0 ? 1.0 : 0.0; }
+            else rel[i] = r0[i] > 0 ? l2[i] / r0[i] : 0.0;
+            worst = std::isfinite(rel[i]) ? std::max(worst, rel[i]) : rel[i];
+        }
+        return worst;
+    };
+    double worst;
+    if (q.precision == MG_FP64) {
+        if ((rc = run_graph(t, "b-res64", [&] { residual_enqueue_trees(t, t->f64, nullptr, nullptr); }))) return rc;
+        worst = update(true);
+        if (fmg_first && max_cycles > 0 && worst > 0) {
+            rc = run_graph(t, "b-fmg64+res" + sfx, [&] {
+                fmg<double>(t, t->f64, q.n_down, q.n_up, 0);
+                residual_enqueue_trees(t, t->f64, nullptr, nullptr);
+            });
+            if (rc) return rc;
+            cycles++;
+            worst = update(false);
+        }
+        while (worst > rel_tol && cycles < max_cycles) {
+            rc = run_graph(t, "b-v64+res" + sfx, [&] {
+                vcycle<double>(t, t->f64, top, q.n_down, q.n_up, 0);
+                residual_enqueue_trees(t, t->f64, nullptr, nullptr);
+            });
+            if (rc) return rc;
+            cycles++;
+            worst = update(false);
+            if (!std::isfinite(worst)) break;
+        }
+    } else if (q.precision == MG_FP32_DC) {
+        if ((rc = ensure_f32(t))) return rc;
+        if ((rc = run_graph(t, "b-res64f32", [&] { residual_enqueue_trees(t, t->f64, t->f32.F, nullptr); }))) return rc;
+        worst = update(true);
+        const std::string ki = sfx + ":" + std::to_string(q.inner_cycles);
+        while (worst > rel_tol && cycles < max_cycles) {
+            const bool first_fmg = fmg_first && cycles == 0;
+            rc = run_graph(t, (first_fmg ? "b-dc-fmg" : "b-dc-v") + ki, [&] {
+                cudaMemsetAsync(t->f32.X, 0, sizeof(float) * t->ncells, t->stream);
+                cudaMemsetAsync(t->f32.XG, 0, sizeof(float) * t->nghost, t->stream);
+                if (first_fmg) {
+                    fmg<float>(t, t->f32, q.n_down, q.n_up, 1);
+                    for (int c = 1; c < q.inner_cycles; c++) vcycle<float>(t, t->f32, top, q.n_down, q.n_up, 1);
+                } else {
+                    for (int c = 0; c < q.inner_cycles; c++) vcycle<float>(t, t->f32, top, q.n_down, q.n_up, 1);
+                }
+                add_e_to_phi(t, t->f32.X, t->f64.X);
+                residual_enqueue_trees(t, t->f64, t->f32.F, nullptr);
+            });
+            if (rc) return rc;
+            cycles++;
+            worst = update(false);
+            if (!std::isfinite(worst)) break;
+        }
+    } else {
+        return fail(MG_ERR_ARG, "unknown precision");
+    }
+    if ((rc = check_cuda("batch solve")) || (rc = check_status(t))) return rc;
+    if (cycles_done) *cycles_done = cycles;
+    if (rel_out)
+        for (int i = 0; i < n; i++) rel_out[i] = rel[i];
+    if (!std::isfinite(worst)) return fail(MG_ERR_NAN, "residual is not finite");
+    if (worst > rel_tol) return fail(MG_ERR_NOT_CONVERGED, "max_cycles reached");
+    return MG_OK;
+}
+
+extern "C" int mg_batch_launch_count(mg_batch *b, int64_t *n) {
+    NEED_BATCH(b);
+    return mg_launch_count(b->pool, n);
+}
+
+extern "C" int mg_batch_time_sweeps(mg_batch *b, int level, int n_sweeps, int precision, double out[4]) {
+    NEED_BATCH(b);
+    return mg_time_sweeps(b->pool, level, n_sweeps, precision, out);
+}
+
+extern "C" int mg_batch_num_segments(mg_batch *b, int *nseg, int *ngroups) {
+    NEED_BATCH(b);
+    if (!nseg || !ngroups) return fail(MG_ERR_ARG, "null output");
+    *nseg = (int)b->pool->lev.size();
+    *ngroups = (int)b->pool->groups.size();
+    return MG_OK;
+}
+
+extern "C" int mg_batch_segment_info(mg_batch *b, int seg, int32_t info[6]) {
+    NEED_BATCH(b);
+    if (!info || seg < 0 || seg >= (int)b->pool->lev.size()) return fail(MG_ERR_ARG, "bad arguments");
+    const LevelHost &L = b->pool->lev[seg];
+    info[0] = L.n; info[1] = L.group; info[2] = L.nb; info[3] = L.nref; info[4] = L.coarsest; info[5] = L.parent_same_n;
+    return MG_OK;
+}
+
+extern "C" int mg_batch_destroy(mg_batch *b) {
+    if (!b) return MG_OK;
+    mg_tree_destroy(b->pool);
+    delete b;
     return MG_OK;
 }
