@@ -203,7 +203,8 @@ class Tree:
 
     SWEEP_VARIANTS = {0: "k_sweep_tma (CTA per block)", 1: "k_sweep (plain loads)", 2: "k_sweep_warp<8 warps>",
                       3: "k_sweep_warp<4 warps>", 4: "k_sweep_rows<8 warps, 2 stages>",
-                      5: "k_sweep_rows<4 warps, 3 stages>", -1: "untuned"}
+                      5: "k_sweep_rows<4 warps, 3 stages>", 6: "k_sweep_flat (thread per colour cell)",
+                      -1: "untuned"}
 
     def sweep_variant(self, level, precision=MG_FP64):
         v = C.c_int()

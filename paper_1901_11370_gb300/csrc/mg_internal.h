@@ -97,6 +97,8 @@ struct LevelHost {
     int group = 0;      // cycle group (0 = coarsest)
     int coarsest = 0;   // 1: coarsest level of its tree(s), solved exactly
     int parent_same_n = 0;  // 1: every block's parent has the same block size
+    int has_cf = 0;         // 1: some block has a refinement face (coarser neighbour)
+    std::vector<int> parents;  // segments holding the parents of its blocks
 };
 
 }  // namespace mg

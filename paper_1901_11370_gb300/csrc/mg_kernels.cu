@@ -1864,6 +1864,181 @@ __global__ void __launch_bounds__(kMaxThreads) k_eps_grad(KParams P, int first, 
 
 // ------------------------------------------------------------ driver ----
 
+// ----------------------------------------------- flat small-block path ---
+// Segments of tiny blocks (at most kFlatCells cells, the halved block sizes
+// of the levels below the base grid) run one thread per work item across
+// all blocks of the segment instead of one CTA per block.  Same arithmetic
+// as the CTA kernels, read straight from global memory.
+constexpr int kFlatCells = 16;
+
+// ghost slot t of every block: as k_ghost
+template <class T, int D>
+__global__ void __launch_bounds__(256) k_ghost_flat(KParams P, int first, int nblocks, int n, T *__restrict__ X,
+                                                    T *__restrict__ XG, int mode) {
+    const int F = face_of<D>(n), G = 2 * D * F;
+    const long long total = (long long)nblocks * G;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int g = first + (int)(idx / G), t = (int)(idx % G);
+        const BlockDesc &b = P.B[g];
+        const LevelDesc &L = P.L[b.lev];
+        const int face = t / F, u = t - face * F, d = face >> 1, s = face & 1;
+        const I3 ii = face_cell<D>(n, face, u, false);
+        const int nb = b.nbr[face];
+        T val;
+        if (nb >= 0) {
+            const BlockDesc &q = P.B[nb];
+            I3 jj = ii;
+            put(jj, d, s ? 0 : n - 1);
+            val = X[q.cell_off + cidx<D>(n, jj.x, jj.y, jj.z)];
+        } else if (nb == -1) {
+            const T xi = X[b.cell_off + cidx<D>(n, ii.x, ii.y, ii.z)];
+            val = mode >= 1 ? xi : phys_ghost<T>(P, L, face, xi, bc_value(P, L, b, D, face, ii));
+        } else {
+            I3 dd = ii;
+            put(dd, d, s ? n - 2 : 1);
+            const T c = X[b.cell_off + cidx<D>(n, ii.x, ii.y, ii.z)];
+            const T dv = X[b.cell_off + cidx<D>(n, dd.x, dd.y, dd.z)];
+            val = cf_ghost<T, D>(P, L, b, face, ii, c, dv, X, XG, nb, mode == 1);
+        }
+        XG[b.ghost_off + t] = val;
+    }
+}
+
+// red-black half-sweep, one thread per cell of the colour, pushing the
+// same-level and physical ghosts fed by its cell (segments without
+// refinement faces; reads touch only slots of the other colour, as in the
+// CTA sweep)
+template <class T, int D>
+__global__ void __launch_bounds__(256) k_sweep_flat(KParams P, int first, int nblocks, int n, Fields<T> F, int colour) {
+    const int C = cells_of<D>(n), Fc = face_of<D>(n), ncol = (n & 1) ? C : C / 2;
+    const long long total = (long long)nblocks * ncol;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int g = first + (int)(idx / ncol), qi = (int)(idx % ncol);
+        const BlockDesc &b = P.B[g];
+        const LevelDesc &L = P.L[b.lev];
+        const int par0 = (b.ijk[0] + b.ijk[1] + b.ijk[2]) * n;
+        int i, j, k;
+        if (n & 1) {
+            i = qi % n; j = (qi / n) % n; k = D == 3 ? qi / (n * n) : 0;
+            if (((par0 + i + j + k) & 1) != colour) continue;
+        } else {
+            const int h = n >> 1, rr = qi / h, m = qi - rr * h;
+            j = rr % n;
+            k = D == 3 ? rr / n : 0;
+            i = 2 * m + ((colour + par0 + j + k) & 1);
+        }
+        const int c = cidx<D>(n, i, j, k);
+        T lap, num, den, xc;
+        stencil<T, T, D>(P, L, b, F.X, F.XG, F.E, F.EG, i, j, k, lap, num, den, xc);
+        const T xnew = (num - F.F[b.cell_off + c]) / (den + (T)P.helm);
+        F.X[b.cell_off + c] = xnew;
+        const I3 ii{i, j, k};
+#pragma unroll
+        for (int face = 0; face < 2 * D; face++) {
+            const int d = face >> 1, s = face & 1;
+            if (get(ii, d) != (s ? n - 1 : 0)) continue;
+            int u;
+            if (D == 2) u = d == 0 ? j : i;
+            else u = d == 0 ? j + n * k : (d == 1 ? i + n * k : i + n * j);
+            const int nb = b.nbr[face];
+            if (nb >= 0) F.XG[b.push[face] + u] = xnew;
+            else if (nb == -1) F.XG[b.ghost_off + face * Fc + u] = phys_ghost<T>(P, L, face, xnew, bc_value(P, L, b, D, face, ii));
+        }
+    }
+}
+
+// covered cells <- mean of their children, one thread per parent cell
+// (with_res: mean child residual into Fdst); as k_restrict, no ghost push
+template <class T, int D>
+__global__ void __launch_bounds__(256) k_restrict_flat(KParams P, int first, int nblocks, int n, T *__restrict__ X,
+                                                       const T *__restrict__ XG, const T *__restrict__ Fr,
+                                                       const T *__restrict__ E, const T *__restrict__ EG,
+                                                       T *__restrict__ Fdst, int with_res) {
+    const int m = n / 2, M = cells_of<D>(m);
+    const long long total = (long long)nblocks * M;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int g = first + (int)(idx / M), c = (int)(idx % M);
+        const BlockDesc &b = P.B[g];
+        const LevelDesc &L = P.L[b.lev];
+        const BlockDesc &p = P.B[b.parent];
+        int ci, cj, ck;
+        cell_of(c, m, D, ci, cj, ck);
+        T sx = 0, sr = 0;
+#pragma unroll 1
+        for (int ch = 0; ch < (1 << D); ch++) {
+            const int fi = 2 * ci + (ch & 1), fj = 2 * cj + ((ch >> 1) & 1), fk = D == 3 ? 2 * ck + ((ch >> 2) & 1) : 0;
+            const int fc = cidx<D>(n, fi, fj, fk);
+            sx += X[b.cell_off + fc];
+            if (with_res) {
+                T lap, num, den, xc;
+                stencil<T, T, D>(P, L, b, X, XG, E, EG, fi, fj, fk, lap, num, den, xc);
+                sr += Fr[b.cell_off + fc] - (lap - (T)P.helm * xc);
+            }
+        }
+        const int pc = cidx<D>(p.n, b.poff[0] + ci, b.poff[1] + cj, b.poff[2] + ck);
+        X[p.cell_off + pc] = sx / (T)(1 << D);
+        if (with_res) Fdst[p.cell_off + pc] = sr / (T)(1 << D);
+    }
+}
+
+// covered cells: f^H += L^H v^H (Sec. 2.4); vold also keeps v_old = v^H and
+// its ghosts (items past the cells copy the ghost slots)
+template <class T, int D>
+__global__ void __launch_bounds__(256) k_fas_flat(KParams P, int first, int nblocks, int n, Fields<T> F, int vold) {
+    const int C = cells_of<D>(n), G = 2 * D * face_of<D>(n);
+    const long long ncells = (long long)nblocks * C, total = ncells + (vold ? (long long)nblocks * G : 0);
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        if (idx < ncells) {
+            const int g = first + (int)(idx / C), c = (int)(idx % C);
+            const BlockDesc &b = P.B[g];
+            const LevelDesc &L = P.L[b.lev];
+            int i, j, k;
+            cell_of(c, n, D, i, j, k);
+            T lap, num, den, xc;
+            stencil<T, T, D>(P, L, b, F.X, F.XG, F.E, F.EG, i, j, k, lap, num, den, xc);
+            F.F[b.cell_off + c] += lap - (T)P.helm * xc;
+            if (vold) F.V[b.cell_off + c] = xc;
+        } else {
+            const long long e = idx - ncells;
+            const BlockDesc &b = P.B[first + (int)(e / G)];
+            const long long o = b.ghost_off + e % G;
+            F.VG[o] = F.XG[o];
+        }
+    }
+}
+
+// coarse-grid correction x^h += P(x^H - x^H_old) (as k_prolong), one
+// thread per fine cell, no ghost push (a ghost fill follows)
+template <class T, int D>
+__global__ void __launch_bounds__(256) k_prolong_flat(KParams P, int first, int nblocks, int n, Fields<T> F) {
+    const int C = cells_of<D>(n);
+    const long long total = (long long)nblocks * C;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int g = first + (int)(idx / C), c = (int)(idx % C);
+        const BlockDesc &b = P.B[g];
+        const BlockDesc &p = P.B[b.parent];
+        int i, j, k;
+        cell_of(c, n, D, i, j, k);
+        const int I0 = b.ijk[0] * n + i, I1 = b.ijk[1] * n + j, I2 = b.ijk[2] * n + k;
+        const int c0x = b.poff[0] + i / 2, c0y = b.poff[1] + j / 2, c0z = D == 3 ? b.poff[2] + k / 2 : 0;
+        const T c0 = load<T, D>(F.X, F.XG, p, c0x, c0y, c0z) - load<T, D>(F.V, F.VG, p, c0x, c0y, c0z);
+        T nbs = 0;
+#pragma unroll
+        for (int d = 0; d < D; d++) {
+            const int o = ((d == 0 ? I0 : d == 1 ? I1 : I2) & 1) ? 1 : -1;
+            const int qx = c0x + (d == 0 ? o : 0), qy = c0y + (d == 1 ? o : 0), qz = c0z + (d == 2 ? o : 0);
+            nbs += load<T, D>(F.X, F.XG, p, qx, qy, qz) - load<T, D>(F.V, F.VG, p, qx, qy, qz);
+        }
+        const T val = D == 2 ? ((T)2 * c0 + nbs) / (T)4 : (c0 + nbs) / (T)4;
+        F.X[b.cell_off + c] += val;
+    }
+}
+
 KParams kparams(mg_tree *t, int homog) {
     KParams P;
     P.B = t->d_blocks;
@@ -1905,10 +2080,19 @@ static int threads_for(int cells) {
 }
 
 template <class T, int D> struct Launch {
+    static bool is_flat(const LevelHost &L) { return cells_of<D>(L.n) <= kFlatCells; }
+    static int flat_grid(mg_tree *t, long long items) {
+        return (int)std::max<long long>(1, std::min<long long>((items + 255) / 256, 8LL * t->nsm));
+    }
     static void ghost(mg_tree *t, const KParams &P, int l, T *X, T *XG, int mode) {
         const LevelHost &L = t->lev[l];
         if (L.nb == 0) return;
         ++t->launches;
+        if (is_flat(L)) {
+            k_ghost_flat<T, D><<<flat_grid(t, (long long)L.nb * 2 * D * face_of<D>(L.n)), 256, 0, t->stream>>>(
+                P, L.first, L.nb, L.n, X, XG, mode);
+            return;
+        }
         k_ghost<T, D><<<L.nb, threads_for(2 * D * face_of<D>(L.n)), 0, t->stream>>>(P, L.first, X, XG, mode);
     }
     // Sweep variants (candidate ids for the autotuner):
@@ -1917,6 +2101,7 @@ template <class T, int D> struct Launch {
     //  2 / 3 warp-per-block TMA sweep, 8 / 4 warps per CTA (8-cell blocks)
     //  4 / 5 row-wise warp sweep, 8 warps x 2 stages / 4 warps x 3 stages
     //        (8^3 blocks, constant coefficient, Cartesian)
+    //  6 flat sweep, one thread per colour cell (tiny blocks, no refinement faces)
     static size_t cand_smem(mg_tree *t, int l, Fields<T> &F, int cand) {
         const int n = t->lev[l].n, C = cells_of<D>(n), GH = 2 * D * face_of<D>(n);
         const size_t stage = sizeof(BlockDesc) + sizeof(LevelDesc) + sizeof(T) * (2 * C + GH + (F.E ? C + GH : 0));
@@ -1927,6 +2112,7 @@ template <class T, int D> struct Launch {
         case 3: return n == 8 ? 8 * stage : 0;
         case 4: return (D == 3 && n == 8 && !F.E && t->geom == MG_CART) ? 16 * stage : 0;
         case 5: return (D == 3 && n == 8 && !F.E && t->geom == MG_CART) ? 12 * stage : 0;
+        case 6: return (is_flat(t->lev[l]) && !t->lev[l].has_cf) ? 1 : 0;
         }
         return 0;
     }
@@ -1935,7 +2121,7 @@ template <class T, int D> struct Launch {
         return sm > 0 && sm <= 200 * 1024;
     }
     static int default_cand(mg_tree *t, int l, Fields<T> &F) {
-        for (int c : {4, 0}) if (cand_ok(t, l, F, c)) return c;
+        for (int c : {6, 4, 0}) if (cand_ok(t, l, F, c)) return c;
         return 1;
     }
     static void sweep(mg_tree *t, const KParams &P, int l, Fields<T> &F, int colour) {
@@ -1975,6 +2161,12 @@ template <class T, int D> struct Launch {
             }
             return;
         }
+        case 6: {
+            const int ncol = (n & 1) ? cells_of<D>(n) : cells_of<D>(n) / 2;
+            k_sweep_flat<T, D><<<flat_grid(t, (long long)L.nb * ncol), 256, 0, t->stream>>>(P, L.first, L.nb, n, F,
+                                                                                          colour);
+            return;
+        }
         default: {
             const int pad = D == 2 ? (n + 2) * (n + 2) : (n + 2) * (n + 2) * (n + 2);
             const size_t smp = sizeof(T) * pad * (F.E ? 2 : 1);
@@ -2004,7 +2196,7 @@ template <class T, int D> struct Launch {
         for (size_t l = 1; l < t->lev.size(); l++) {
             if (t->lev[l].nb < 256) continue;
             std::vector<int> cands;
-            for (int cand = 0; cand < 6; cand++)
+            for (int cand = 0; cand < 7; cand++)
                 if (cand_ok(t, (int)l, F, cand)) cands.push_back(cand);
             // warm-up (clocks, caches, first-launch costs), then the minimum
             // over three interleaved rounds of four launches per candidate
@@ -2037,14 +2229,20 @@ template <class T, int D> struct Launch {
     // segment of g restricts into its parents (pushing the parent-level
     // ghosts), then f^H and v_old are formed on the covered blocks of g-1.
     static void restrict_group(mg_tree *t, const KParams &P, int g, Fields<T> &F) {
-        bool plain = false;
+        // parent segments fed by a restriction without ghost push get a
+        // ghost fill before their FAS right-hand side
+        std::vector<char> plain(t->lev.size(), 0);
         for (int l : t->groups[g]) {
             const LevelHost &L = t->lev[l];
             if (L.coarsest) continue;
             ++t->launches;
             const int C8 = cells_of<D>(L.n), GH8 = 2 * D * face_of<D>(L.n);
             const size_t smt = 2 * (2 * (sizeof(BlockDesc) + sizeof(LevelDesc)) + sizeof(T) * (2 * C8 + GH8 + (F.E ? C8 + GH8 : 0)));
-            if ((L.n == 8 || L.n == 16) && smt + sizeof(T) * C8 <= 200 * 1024) {
+            if (is_flat(L)) {
+                k_restrict_flat<T, D><<<flat_grid(t, (long long)L.nb * cells_of<D>(L.n / 2)), 256, 0, t->stream>>>(
+                    P, L.first, L.nb, L.n, F.X, F.XG, F.F, F.E, F.EG, F.F, 1);
+                for (int q : L.parents) plain[q] = 1;
+            } else if ((L.n == 8 || L.n == 16) && smt + sizeof(T) * C8 <= 200 * 1024) {
                 auto kern = L.n == 8 ? k_restrict_tma<T, D, 8> : k_restrict_tma<T, D, 16>;
                 const int thr = threads_for(C8);
                 const int grid = std::min(L.nb, resident_ctas(kern, thr, smt) * t->nsm);
@@ -2055,30 +2253,31 @@ template <class T, int D> struct Launch {
             } else {
                 k_restrict<T, D><<<L.nb, threads_for(cells_of<D>(L.n / 2)), 0, t->stream>>>(P, L.first, F.X, F.XG,
                                                                                              F.F, F.E, F.EG, F.F, 1);
-                plain = true;
+                for (int q : L.parents) plain[q] = 1;
             }
         }
-        for (int c : t->groups[g - 1]) {
-            const LevelHost &C = t->lev[c];
-            if (plain) {
-                ghost(t, P, c, F.X, F.XG, 0);
-                cudaMemcpyAsync(F.V + C.cell_first, F.X + C.cell_first, sizeof(T) * C.ncells, cudaMemcpyDeviceToDevice,
-                                t->stream);
-                cudaMemcpyAsync(F.VG + C.ghost_first, F.XG + C.ghost_first, sizeof(T) * C.nghost,
-                                cudaMemcpyDeviceToDevice, t->stream);
-            }
-        }
+        for (int c : t->groups[g - 1])
+            if (plain[c]) ghost(t, P, c, F.X, F.XG, 0);
         for (int c : t->groups[g - 1]) {
             const LevelHost &C = t->lev[c];
             if (C.nref <= 0) continue;
             ++t->launches;
-            if (plain) k_fas_rhs<T, D><<<C.nref, threads_for(cells_of<D>(C.n)), 0, t->stream>>>(P, C.first, F);
-            else k_fas_rhs_vold<T, D><<<C.nref, threads_for(cells_of<D>(C.n)), 0, t->stream>>>(P, C.first, F);
+            if (is_flat(C))
+                k_fas_flat<T, D><<<flat_grid(t, (long long)C.nref * (cells_of<D>(C.n) + 2 * D * face_of<D>(C.n))), 256,
+                                   0, t->stream>>>(P, C.first, C.nref, C.n, F, 1);
+            else
+                k_fas_rhs_vold<T, D><<<C.nref, threads_for(cells_of<D>(C.n)), 0, t->stream>>>(P, C.first, F);
         }
     }
     static void prolong(mg_tree *t, const KParams &P, int l, Fields<T> &F) {
         const LevelHost &L = t->lev[l];
         ++t->launches;
+        if (is_flat(L)) {
+            k_prolong_flat<T, D><<<flat_grid(t, (long long)L.nb * cells_of<D>(L.n)), 256, 0, t->stream>>>(
+                P, L.first, L.nb, L.n, F);
+            ghost(t, P, l, F.X, F.XG, 0);
+            return;
+        }
         if (L.n == 8 && L.parent_same_n) {
             k_prolong_box<T, D, 8><<<L.nb, threads_for(cells_of<D>(8) / 2), 0, t->stream>>>(P, L.first, F);
             return;
@@ -2135,8 +2334,12 @@ template <class T, int D> struct Launch {
                 const LevelHost &L = t->lev[l];
                 if (L.coarsest) continue;
                 ++t->launches;
-                k_restrict<T, D><<<L.nb, threads_for(cells_of<D>(L.n / 2)), 0, t->stream>>>(P, L.first, F.X, F.XG,
-                                                                                             F.F, F.E, F.EG, F.F, 0);
+                if (is_flat(L))
+                    k_restrict_flat<T, D><<<flat_grid(t, (long long)L.nb * cells_of<D>(L.n / 2)), 256, 0, t->stream>>>(
+                        P, L.first, L.nb, L.n, F.X, F.XG, F.F, F.E, F.EG, F.F, 0);
+                else
+                    k_restrict<T, D><<<L.nb, threads_for(cells_of<D>(L.n / 2)), 0, t->stream>>>(P, L.first, F.X, F.XG,
+                                                                                                 F.F, F.E, F.EG, F.F, 0);
             }
         for (int g = 0; g <= top; g++)
             for (int l : t->groups[g]) ghost(t, P, l, F.X, F.XG, mode);
@@ -2149,8 +2352,12 @@ template <class T, int D> struct Launch {
                 const LevelHost &L = t->lev[l];
                 if (L.coarsest) continue;
                 ++t->launches;
-                k_restrict<T, D><<<L.nb, threads_for(cells_of<D>(L.n / 2)), 0, t->stream>>>(
-                    P, L.first, F.E, F.EG, nullptr, nullptr, nullptr, nullptr, 0);
+                if (is_flat(L))
+                    k_restrict_flat<T, D><<<flat_grid(t, (long long)L.nb * cells_of<D>(L.n / 2)), 256, 0, t->stream>>>(
+                        P, L.first, L.nb, L.n, F.E, F.EG, nullptr, nullptr, nullptr, nullptr, 0);
+                else
+                    k_restrict<T, D><<<L.nb, threads_for(cells_of<D>(L.n / 2)), 0, t->stream>>>(
+                        P, L.first, F.E, F.EG, nullptr, nullptr, nullptr, nullptr, 0);
             }
         for (int g = 0; g <= top; g++)
             for (int l : t->groups[g]) ghost(t, P, l, F.E, F.EG, 1);

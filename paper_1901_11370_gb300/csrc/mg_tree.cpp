@@ -530,11 +530,30 @@ int build_coarse_inverse(mg_tree *t) {
     return MG_OK;
 }
 
+// per segment: refinement faces present, and the segments of its parents
+static void annotate_segments(mg_tree *t) {
+    std::vector<int> seg(t->blocks.size(), 0);
+    for (size_t l = 0; l < t->lev.size(); l++)
+        for (int b = 0; b < t->lev[l].nb; b++) seg[t->lev[l].first + b] = (int)l;
+    for (LevelHost &L : t->lev) {
+        L.has_cf = 0;
+        L.parents.clear();
+        for (int b = L.first; b < L.first + L.nb; b++) {
+            const BlockDesc &B = t->blocks[b];
+            for (int f = 0; f < 2 * t->dim; f++)
+                if (B.nbr[f] <= -2) L.has_cf = 1;
+            if (B.parent >= 0 && std::find(L.parents.begin(), L.parents.end(), seg[B.parent]) == L.parents.end())
+                L.parents.push_back(seg[B.parent]);
+        }
+    }
+}
+
 extern "C" int mg_tree_finalize(mg_tree *t, void *stream) {
     if (!t) return fail(MG_ERR_ARG, "null tree");
     if (t->finalized) return fail(MG_ERR_ARG, "already finalized");
     int rc = build(t);
     if (rc) return rc;
+    annotate_segments(t);
     CK(cudaGetDevice(&t->device));
     CK(cudaDeviceGetAttribute(&t->nsm, cudaDevAttrMultiProcessorCount, t->device));
     t->stream = (cudaStream_t)stream;
