@@ -12,6 +12,9 @@ than L2, so no flush is needed between steps.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
+The line also carries "batch": the 512-tree cylindrical forest solved as one
+batch (mixed precision and FP64, per-tree relative residual 1e-10).
+
 N > 1 (torchrun): every rank solves its own replica (the workload is one
 tree; the method does not shard here), value = all ranks' unknowns / max
 time.  --impl reference times the FP64 CPU oracle on a bounded sample.
@@ -284,7 +287,8 @@ def run_ours(args):
     var32 = tree.sweep_variant(lev, mg.MG_FP32_DC)
     var64 = tree.sweep_variant(lev, mg.MG_FP64)
     kname = {0: "k_sweep_tma", 1: "k_sweep", 2: "k_sweep_warp", 3: "k_sweep_warp", 4: "k_sweep_rows",
-             5: "k_sweep_rows"}.get(var32, "k_sweep")
+             5: "k_sweep_rows", 6: "k_sweep_flat", 7: "k_sweep_rows", 8: "k_sweep_rows",
+             9: "k_sweep_rows"}.get(var32, "k_sweep")
     traffic = measured_traffic(kname, "sweep_f32_traffic.txt")
     if traffic is not None:
         lv = tree.levels()[lev]
@@ -317,12 +321,61 @@ def run_ours(args):
                                     "variant": tree.SWEEP_VARIANTS.get(var64)},
                      "ghost_fill_ms_per_launch": ms_g, "ghost_fill_achieved_GBs": b_g / (ms_g * 1e-3) / 1e9},
     }
+    if not args.no_batch:
+        del tree
+        result["batch"] = batch_measure(args, mg, W, barrier, max_over_ranks)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"] = oracle_baseline(p, n)
     if rank == 0:
         print(json.dumps(result))
     if dist is not None:
         dist.destroy_process_group()
+
+
+BATCH_WORKLOAD = ("batch of 512 independent 2D cylindrical (r,z) trees, side 16k cells with k ~ U{2..32} in 16^2 "
+                  "blocks, 0-2 AMR levels around a seeded ring point, eps = 1 + 0.5 sin(2 pi z), Dirichlet 0 at "
+                  "r = 1, z = 0, z = 1, axis at r = 0, Gaussian source of width 0.03")
+
+
+def batch_measure(args, mg, W, barrier, max_over_ranks):
+    """The batched form: every tree of the forest solved to 1e-10 (per-tree
+    relative residual) in one pool, FP32 + FP64 defect correction against
+    the plain FP64 cycles, each solve one graph-replayed sequence."""
+    import numpy as np
+    import torch
+    probs = [W.cyl_ring_tree(i) for i in range(512)]
+    b = mg.Batch([mg.Tree.from_problem(q, finalize=False) for q in probs])
+    b.set_eps(torch.from_numpy(np.concatenate([W.leaf_field(q, "eps") for q in probs])).cuda())
+    b.set_rhs(torch.from_numpy(np.concatenate([W.leaf_field(q, "rhs") for q in probs])).cuda())
+    zeros = torch.zeros(b.n_leaf, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def solve(prec):
+        b.set_phi(zeros)
+        return b.solve(TOL, MAX_CYCLES, fmg_first=True, precision=prec)
+
+    out = {"workload": BATCH_WORKLOAD, "trees": len(probs), "unknowns": b.n_leaf, "segments": len(b.segments())}
+    steps = max(1, min(args.steps, 3))
+    for name, prec in (("fp32_dc", mg.MG_FP32_DC), ("fp64", mg.MG_FP64)):
+        solve(prec)
+        barrier()
+        l0 = b.launch_count()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            cyc, rel = solve(prec)
+        e1.record(stream)
+        barrier()
+        ms = max_over_ranks(e0.elapsed_time(e1) / steps)
+        out[name] = {"value": b.n_leaf / (ms * 1e-3), "unit": "unknowns/s", "ms_per_step": ms, "cycles_to_tol": cyc,
+                     "max_final_rel_residual": float(rel.max()), "gpu_launches_per_step": (b.launch_count() - l0) / steps}
+    out["fp32_dc_over_fp64"] = out["fp32_dc"]["value"] / out["fp64"]["value"]
+    (ms_s, _, b_s, _), seg = b.time_sweeps(n_sweeps=8, precision=mg.MG_FP32_DC)
+    peak, peak_kind = peak_hbm()
+    out["sweep_roofline"] = {"segment": seg, "blocks": b.segments()[seg]["nb"], "ms_per_launch": ms_s,
+                             "alg_bytes_per_launch": b_s, "achieved": b_s / (ms_s * 1e-3) / 1e9, "peak": peak,
+                             "peak_kind": peak_kind, "frac": b_s / (ms_s * 1e-3) / 1e9 / peak}
+    return out
 
 
 def run_profile(kind):
@@ -359,6 +412,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 512-tree batch measurement")
     ap.add_argument("--profile", choices=["sweeps64", "sweeps32", "solve32", "solve64"], default=None)
     args = ap.parse_args()
     if args.profile:

@@ -189,11 +189,22 @@ int mg_project(mg_tree *t, const double *dev_B, double *dev_Bnew);
  * fill (read the source cells, write the ghosts once).  Synchronises.
  */
 int mg_launch_count(mg_tree *t, int64_t *n);
-/* mg_sweep_variant: the sweep kernel variant the autotuner chose for a level
- * and precision (MG_FP64 / MG_FP32_DC): 0 persistent CTA-per-block TMA,
+/* mg_sweep_variant: the sweep kernel variant in use for a level and
+ * precision (MG_FP64 / MG_FP32_DC): 0 persistent CTA-per-block TMA,
  * 1 CTA-per-block plain loads, 2 / 3 warp-per-block TMA (8 / 4 warps),
- * 4 / 5 row-wise warp TMA (8 warps x 2 stages / 4 warps x 3 stages). */
+ * 4 / 5 row-wise warp TMA (8 warps x 2 stages / 4 warps x 3 stages),
+ * 6 one thread per colour cell (blocks of at most 16 cells without
+ * refinement faces), 7 / 8 / 9 row-wise warp TMA with the right-hand side
+ * loaded into registers (FP32; 8 x 3, 4 x 4, 8 x 2).  Variants 2-5 and 7-9
+ * need 8^D blocks (4, 5, 7-9: 3D, constant coefficient, Cartesian).
+ *
+ * mg_set_sweep_variant: override the autotuner -- use `variant` on `level`
+ * (level -1: on every level where it applies; variant -1: back to the
+ * automatic choice).  MG_ERR_ARG when a single level is named and the
+ * variant does not apply there.  Every variant computes the same red-black
+ * half-sweep; this call exists to test and time them one by one. */
 int mg_sweep_variant(mg_tree *t, int precision, int level, int *variant);
+int mg_set_sweep_variant(mg_tree *t, int precision, int level, int variant);
 int mg_time_sweeps(mg_tree *t, int level, int n_sweeps, int precision, double out[4]);
 
 /*

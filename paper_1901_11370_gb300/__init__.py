@@ -204,12 +204,20 @@ class Tree:
     SWEEP_VARIANTS = {0: "k_sweep_tma (CTA per block)", 1: "k_sweep (plain loads)", 2: "k_sweep_warp<8 warps>",
                       3: "k_sweep_warp<4 warps>", 4: "k_sweep_rows<8 warps, 2 stages>",
                       5: "k_sweep_rows<4 warps, 3 stages>", 6: "k_sweep_flat (thread per colour cell)",
-                      -1: "untuned"}
+                      7: "k_sweep_rows<8 warps, 3 stages, f in registers>",
+                      8: "k_sweep_rows<4 warps, 4 stages, f in registers>",
+                      9: "k_sweep_rows<8 warps, 2 stages, f in registers>", -1: "untuned"}
 
     def sweep_variant(self, level, precision=MG_FP64):
         v = C.c_int()
         check(self.L.mg_sweep_variant(self._h, precision, level, C.byref(v)))
         return v.value
+
+    def set_sweep_variant(self, variant, level=-1, precision=MG_FP64):
+        """Pin the sweep kernel variant (see SWEEP_VARIANTS) on one level or on
+        every level where it applies (level -1); variant -1 restores the
+        autotuned choice."""
+        check(self.L.mg_set_sweep_variant(self._h, precision, level, variant))
 
     def time_sweeps(self, level=-1, n_sweeps=4, precision=MG_FP64):
         """(ms per sweep launch, ms per full ghost fill, bytes per sweep

@@ -172,6 +172,8 @@ template <class T> void refresh(mg_tree *t, Fields<T> &F, int homog);
 template <class T> void refresh_eps(mg_tree *t, Fields<T> &F);
 template <class T> void tune_sweeps(mg_tree *t, Fields<T> &F);
 int sweep_variant(mg_tree *t, int prec, int level);
+constexpr int kNumSweepVariants = 10;
+bool sweep_variant_ok(mg_tree *t, int prec, int level, int variant);
 void divergence(mg_tree *t, const double *B, double *out);
 void project(mg_tree *t, const double *B, double *Bout);
 // composite residual of FP64 fields on the leaves; optional outputs:

@@ -798,12 +798,14 @@ template <class T> __device__ __forceinline__ void st8(T *p, const T *r) {
     }
 }
 
-template <class T, int WARPS, int STAGES>
+// FG: f is not staged; each lane loads the right-hand side of its two rows
+// straight into registers one block ahead (smaller stages, more in flight).
+template <class T, int WARPS, int STAGES, bool FG = false>
 __global__ void __launch_bounds__(32 * WARPS) k_sweep_rows(KParams P, int first, int nblocks, Fields<T> F,
                                                            int colour) {
     constexpr int n = 8, C = 512, FC = 64, GH = 384;
     constexpr int DESC = (int)((sizeof(BlockDesc) + sizeof(LevelDesc)) / sizeof(T));
-    constexpr int STAGE = DESC + 2 * C + GH;
+    constexpr int STAGE = DESC + C + GH + (FG ? 0 : C);
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bars[WARPS][STAGES];
     __shared__ __align__(16) LevelDesc sL;
@@ -826,10 +828,31 @@ __global__ void __launch_bounds__(32 * WARPS) k_sweep_rows(KParams P, int first,
         bulk_g2s(reinterpret_cast<char *>(st) + sizeof(BlockDesc), P.L + P.B[g].lev, sizeof(LevelDesc), bar);
         bulk_g2s(st + DESC, F.X + co, sizeof(T) * C, bar);
         bulk_g2s(st + DESC + C, F.XG + go, sizeof(T) * GH, bar);
-        bulk_g2s(st + DESC + C + GH, F.F + co, sizeof(T) * C, bar);
+        if (!FG) bulk_g2s(st + DESC + C + GH, F.F + co, sizeof(T) * C, bar);
     };
     const int stride = gridDim.x * WARPS;
     int g = blockIdx.x * WARPS + warp;
+    T fnx[16], fcur[16];
+    auto loadf = [&](int gb) {  // rows lane and lane + 32 of block gb
+        const T *fp = F.F + P.B[gb].cell_off;
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+            using V = typename Vec16<T>::type;
+            constexpr int VW = 16 / sizeof(T);
+            const V *vp = reinterpret_cast<const V *>(fp + 8 * (lane + 32 * h));
+#pragma unroll
+            for (int v = 0; v < 8 / VW; v++) {
+                const V x = __ldg(vp + v);
+                if constexpr (sizeof(T) == 4) {
+                    fnx[8 * h + 4 * v] = x.x; fnx[8 * h + 4 * v + 1] = x.y;
+                    fnx[8 * h + 4 * v + 2] = x.z; fnx[8 * h + 4 * v + 3] = x.w;
+                } else {
+                    fnx[8 * h + 2 * v] = x.x; fnx[8 * h + 2 * v + 1] = x.y;
+                }
+            }
+        }
+    };
+    if (FG && g < nblocks) loadf(first + g);
     if (lane == 0)
         for (int q = 0; q < STAGES - 1; q++)
             if (g + q * stride < nblocks) issue(q, first + g + q * stride);
@@ -855,6 +878,11 @@ __global__ void __launch_bounds__(32 * WARPS) k_sweep_rows(KParams P, int first,
             bulk_wait_read0();
             issue(it + STAGES - 1, first + g + (STAGES - 1) * stride);
         }
+        if (FG) {
+#pragma unroll
+            for (int e = 0; e < 16; e++) fcur[e] = fnx[e];
+            if (g + stride < nblocks) loadf(first + g + stride);
+        }
         T *st = wst + (it % STAGES) * STAGE;
         const BlockDesc &b = *reinterpret_cast<const BlockDesc *>(st);
         const LevelDesc &L = *reinterpret_cast<const LevelDesc *>(reinterpret_cast<const char *>(st) + sizeof(BlockDesc));
@@ -872,7 +900,12 @@ __global__ void __launch_bounds__(32 * WARPS) k_sweep_rows(KParams P, int first,
             ld8(j < 7 ? xs + 8 * (q + 1) : gs + 3 * FC + 8 * k, up);
             ld8(k > 0 ? xs + 8 * (q - 8) : gs + 4 * FC + 8 * j, bk);
             ld8(k < 7 ? xs + 8 * (q + 8) : gs + 5 * FC + 8 * j, fw);
-            ld8(fs + 8 * q, fr);
+            if (FG) {
+#pragma unroll
+                for (int e = 0; e < 8; e++) fr[e] = fcur[8 * h + e];
+            } else {
+                ld8(fs + 8 * q, fr);
+            }
             const T xl = gs[0 * FC + j + 8 * k], xr = gs[1 * FC + j + 8 * k];
             const bool p = ((colour + par0 + j + k) & 1) != 0;  // colour cells at i = 2m + p
 #pragma unroll
@@ -2102,6 +2135,8 @@ template <class T, int D> struct Launch {
     //  4 / 5 row-wise warp sweep, 8 warps x 2 stages / 4 warps x 3 stages
     //        (8^3 blocks, constant coefficient, Cartesian)
     //  6 flat sweep, one thread per colour cell (tiny blocks, no refinement faces)
+    //  7 / 8 / 9 row-wise warp sweep with f in registers (FP32): 8 warps x 3
+    //        stages / 4 warps x 4 stages / 8 warps x 2 stages
     static size_t cand_smem(mg_tree *t, int l, Fields<T> &F, int cand) {
         const int n = t->lev[l].n, C = cells_of<D>(n), GH = 2 * D * face_of<D>(n);
         const size_t stage = sizeof(BlockDesc) + sizeof(LevelDesc) + sizeof(T) * (2 * C + GH + (F.E ? C + GH : 0));
@@ -2113,6 +2148,11 @@ template <class T, int D> struct Launch {
         case 4: return (D == 3 && n == 8 && !F.E && t->geom == MG_CART) ? 16 * stage : 0;
         case 5: return (D == 3 && n == 8 && !F.E && t->geom == MG_CART) ? 12 * stage : 0;
         case 6: return (is_flat(t->lev[l]) && !t->lev[l].has_cf) ? 1 : 0;
+        case 7: case 8: case 9: {
+            if (!(D == 3 && n == 8 && !F.E && t->geom == MG_CART && sizeof(T) == 4)) return 0;
+            const size_t sfg = sizeof(BlockDesc) + sizeof(LevelDesc) + sizeof(T) * (C + GH);
+            return (cand == 7 ? 24 : 16) * sfg;
+        }
         }
         return 0;
     }
@@ -2152,10 +2192,13 @@ template <class T, int D> struct Launch {
             kern<<<grid, 32 * W, sm, t->stream>>>(P, L.first, L.nb, F, colour);
             return;
         }
-        case 4: case 5: {
+        case 4: case 5: case 7: case 8: case 9: {
             if constexpr (D == 3) {
-                const int W = cand == 4 ? 8 : 4;
-                auto kern = cand == 4 ? k_sweep_rows<T, 8, 2> : k_sweep_rows<T, 4, 3>;
+                const int W = (cand == 5 || cand == 8) ? 4 : 8;
+                auto kern = cand == 4 ? k_sweep_rows<T, 8, 2> : cand == 5 ? k_sweep_rows<T, 4, 3>
+                          : cand == 7 ? k_sweep_rows<T, 8, 3, true> : cand == 8 ? k_sweep_rows<T, 4, 4, true>
+                                      : k_sweep_rows<T, 8, 2, true>;
+                set_smem(kern, sm);
                 const int grid = std::min((L.nb + W - 1) / W, resident_ctas(kern, 32 * W, sm) * t->nsm);
                 kern<<<grid, 32 * W, sm, t->stream>>>(P, L.first, L.nb, F, colour);
             }
@@ -2196,7 +2239,7 @@ template <class T, int D> struct Launch {
         for (size_t l = 1; l < t->lev.size(); l++) {
             if (t->lev[l].nb < 256) continue;
             std::vector<int> cands;
-            for (int cand = 0; cand < 7; cand++)
+            for (int cand = 0; cand < kNumSweepVariants; cand++)
                 if (cand_ok(t, (int)l, F, cand)) cands.push_back(cand);
             // warm-up (clocks, caches, first-launch costs), then the minimum
             // over three interleaved rounds of four launches per candidate
@@ -2381,6 +2424,16 @@ int sweep_variant(mg_tree *t, int prec, int level) {
     return c >= 0 && Launch<double, 3>::cand_ok(t, level, t->f64, c) ? c : Launch<double, 3>::default_cand(t, level, t->f64);
 }
 template void tune_sweeps<float>(mg_tree *, Fields<float> &);
+bool sweep_variant_ok(mg_tree *t, int prec, int level, int variant) {
+    if (variant < 0 || variant >= kNumSweepVariants) return false;
+    if (prec == 1) {
+        if (!t->f32.X) return false;
+        return t->dim == 2 ? Launch<float, 2>::cand_ok(t, level, t->f32, variant)
+                           : Launch<float, 3>::cand_ok(t, level, t->f32, variant);
+    }
+    return t->dim == 2 ? Launch<double, 2>::cand_ok(t, level, t->f64, variant)
+                       : Launch<double, 3>::cand_ok(t, level, t->f64, variant);
+}
 template <class T> void vcycle(mg_tree *t, Fields<T> &F, int top, int nd, int nu, int homog) {
     if (t->dim == 2) Launch<T, 2>::vcycle(t, F, top, nd, nu, homog);
     else Launch<T, 3>::vcycle(t, F, top, nd, nu, homog);

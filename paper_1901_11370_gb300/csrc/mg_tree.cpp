@@ -908,6 +908,27 @@ extern "C" int mg_sweep_variant(mg_tree *t, int precision, int level, int *varia
 
 static int ensure_f32(mg_tree *t);
 
+extern "C" int mg_set_sweep_variant(mg_tree *t, int precision, int level, int variant) {
+    NEED_FINAL(t);
+    if ((precision != MG_FP64 && precision != MG_FP32_DC) || level < -1 || level >= (int)t->lev.size() ||
+        variant < -1 || variant >= kNumSweepVariants)
+        return fail(MG_ERR_ARG, "bad arguments");
+    int rc;
+    if (precision == MG_FP32_DC && (rc = ensure_f32(t))) return rc;
+    const int prec = precision == MG_FP32_DC ? 1 : 0;
+    std::vector<int> &ch = t->sweep_choice[prec];
+    if (ch.size() != t->lev.size()) ch.assign(t->lev.size(), -1);
+    if (level >= 0 && variant >= 0 && !sweep_variant_ok(t, prec, level, variant))
+        return fail(MG_ERR_ARG, "sweep variant does not apply to this level");
+    for (int l = 0; l < (int)t->lev.size(); l++) {
+        if (level >= 0 && l != level) continue;
+        if (variant < 0) ch[l] = -1;
+        else if (sweep_variant_ok(t, prec, l, variant)) ch[l] = variant;
+    }
+    drop_graphs(t);  // captured cycles hold the previous choice
+    return MG_OK;
+}
+
 extern "C" int mg_time_sweeps(mg_tree *t, int level, int n_sweeps, int precision, double out[4]) {
     NEED_FINAL(t);
     if (!out || n_sweeps < 1 || level < 0 || level >= (int)t->lev.size() ||
