@@ -778,23 +778,32 @@ __global__ void __launch_bounds__(32 * WARPS) k_sweep_warp(KParams P, int first,
 // 16-byte shared-memory loads; the colour cells of the row are chosen by
 // register selects.  Ghost pushes go face by face, one updated face cell
 // per lane.  Same arithmetic as k_sweep_tma.
-template <class T> __device__ __forceinline__ void ld8(const T *p, T *r) {
+// Rows of 8 values.  FP32 rows are 32 B apart, so the lanes of a
+// quarter-warp reading the same half of their rows would meet twice on
+// every bank; with sw = 1 a lane takes the halves in the other order, and
+// its registers then hold the row rotated by 4 (r[e] = element e ^ 4).
+template <class T> __device__ __forceinline__ void ld8(const T *p, T *r, int sw = 0) {
     using V = typename Vec16<T>::type;
-    constexpr int VW = 16 / sizeof(T);
+    if constexpr (sizeof(T) == 4) {
+        const V a = reinterpret_cast<const V *>(p)[sw], b = reinterpret_cast<const V *>(p)[sw ^ 1];
+        r[0] = a.x; r[1] = a.y; r[2] = a.z; r[3] = a.w;
+        r[4] = b.x; r[5] = b.y; r[6] = b.z; r[7] = b.w;
+    } else {
 #pragma unroll
-    for (int v = 0; v < 8 / VW; v++) {
-        const V x = reinterpret_cast<const V *>(p)[v];
-        if constexpr (sizeof(T) == 4) { r[4 * v] = x.x; r[4 * v + 1] = x.y; r[4 * v + 2] = x.z; r[4 * v + 3] = x.w; }
-        else { r[2 * v] = x.x; r[2 * v + 1] = x.y; }
+        for (int v = 0; v < 4; v++) {
+            const V x = reinterpret_cast<const V *>(p)[v];
+            r[2 * v] = x.x; r[2 * v + 1] = x.y;
+        }
     }
 }
-template <class T> __device__ __forceinline__ void st8(T *p, const T *r) {
+template <class T> __device__ __forceinline__ void st8(T *p, const T *r, int sw = 0) {
     using V = typename Vec16<T>::type;
-    constexpr int VW = 16 / sizeof(T);
+    if constexpr (sizeof(T) == 4) {
+        reinterpret_cast<V *>(p)[sw] = make_float4(r[0], r[1], r[2], r[3]);
+        reinterpret_cast<V *>(p)[sw ^ 1] = make_float4(r[4], r[5], r[6], r[7]);
+    } else {
 #pragma unroll
-    for (int v = 0; v < 8 / VW; v++) {
-        if constexpr (sizeof(T) == 4) reinterpret_cast<V *>(p)[v] = make_float4(r[4 * v], r[4 * v + 1], r[4 * v + 2], r[4 * v + 3]);
-        else reinterpret_cast<V *>(p)[v] = make_double2(r[2 * v], r[2 * v + 1]);
+        for (int v = 0; v < 4; v++) reinterpret_cast<V *>(p)[v] = make_double2(r[2 * v], r[2 * v + 1]);
     }
 }
 
@@ -832,6 +841,7 @@ __global__ void __launch_bounds__(32 * WARPS) k_sweep_rows(KParams P, int first,
     };
     const int stride = gridDim.x * WARPS;
     int g = blockIdx.x * WARPS + warp;
+    const int sw = sizeof(T) == 4 ? (lane >> 2) & 1 : 0;  // row half order of this lane (see ld8)
     T fnx[16], fcur[16];
     auto loadf = [&](int gb) {  // rows lane and lane + 32 of block gb
         const T *fp = F.F + P.B[gb].cell_off;
@@ -842,7 +852,7 @@ __global__ void __launch_bounds__(32 * WARPS) k_sweep_rows(KParams P, int first,
             const V *vp = reinterpret_cast<const V *>(fp + 8 * (lane + 32 * h));
 #pragma unroll
             for (int v = 0; v < 8 / VW; v++) {
-                const V x = __ldg(vp + v);
+                const V x = __ldg(vp + (sizeof(T) == 4 ? (v ^ sw) : v));
                 if constexpr (sizeof(T) == 4) {
                     fnx[8 * h + 4 * v] = x.x; fnx[8 * h + 4 * v + 1] = x.y;
                     fnx[8 * h + 4 * v + 2] = x.z; fnx[8 * h + 4 * v + 3] = x.w;
@@ -895,24 +905,31 @@ __global__ void __launch_bounds__(32 * WARPS) k_sweep_rows(KParams P, int first,
         for (int h = 0; h < 2; h++) {
             const int q = lane + 32 * h, j = q & 7, k = q >> 3;
             T r[8], dn[8], up[8], bk[8], fw[8], fr[8];
-            ld8(xs + 8 * q, r);
-            ld8(j > 0 ? xs + 8 * (q - 1) : gs + 2 * FC + 8 * k, dn);
-            ld8(j < 7 ? xs + 8 * (q + 1) : gs + 3 * FC + 8 * k, up);
-            ld8(k > 0 ? xs + 8 * (q - 8) : gs + 4 * FC + 8 * j, bk);
-            ld8(k < 7 ? xs + 8 * (q + 8) : gs + 5 * FC + 8 * j, fw);
+            ld8(xs + 8 * q, r, sw);
+            ld8(j > 0 ? xs + 8 * (q - 1) : gs + 2 * FC + 8 * k, dn, sw);
+            ld8(j < 7 ? xs + 8 * (q + 1) : gs + 3 * FC + 8 * k, up, sw);
+            ld8(k > 0 ? xs + 8 * (q - 8) : gs + 4 * FC + 8 * j, bk, sw);
+            ld8(k < 7 ? xs + 8 * (q + 8) : gs + 5 * FC + 8 * j, fw, sw);
             if (FG) {
 #pragma unroll
                 for (int e = 0; e < 8; e++) fr[e] = fcur[8 * h + e];
             } else {
-                ld8(fs + 8 * q, fr);
+                ld8(fs + 8 * q, fr, sw);
             }
             const T xl = gs[0 * FC + j + 8 * k], xr = gs[1 * FC + j + 8 * k];
             const bool p = ((colour + par0 + j + k) & 1) != 0;  // colour cells at i = 2m + p
+            // register e holds element e ^ 4 sw (same parity); the x
+            // neighbours that cross a row half come from the other end
 #pragma unroll
             for (int m = 0; m < 4; m++) {
                 const int e = 2 * m, o = 2 * m + 1;
-                const T xm = p ? r[e] : (m > 0 ? r[e - 1] : xl);
-                const T xp = p ? (m < 3 ? r[o + 1] : xr) : r[o];
+                T lft = m > 0 ? r[e - 1] : xl, rgt = m < 3 ? r[o + 1] : xr;
+                if (m == 0) lft = sw ? r[7] : xl;
+                if (m == 2) lft = sw ? xl : r[3];
+                if (m == 1) rgt = sw ? xr : r[4];
+                if (m == 3) rgt = sw ? r[0] : xr;
+                const T xm = p ? r[e] : lft;
+                const T xp = p ? rgt : r[o];
                 const T sy = p ? dn[o] + up[o] : dn[e] + up[e];
                 const T sz = p ? bk[o] + fw[o] : bk[e] + fw[e];
                 const T fv = p ? fr[o] : fr[e];
@@ -925,7 +942,7 @@ __global__ void __launch_bounds__(32 * WARPS) k_sweep_rows(KParams P, int first,
         // every lane has read its neighbour rows: write the rows back
         __syncwarp();
 #pragma unroll
-        for (int h = 0; h < 2; h++) st8(xs + 8 * (lane + 32 * h), newrow[h]);
+        for (int h = 0; h < 2; h++) st8(xs + 8 * (lane + 32 * h), newrow[h], sw);
         fence_async_smem();
         __syncwarp();
         if (lane == 0) {
@@ -1239,6 +1256,199 @@ __global__ void __launch_bounds__(kMaxThreads) k_prolong_box(KParams P, int firs
         push_face_cell<T, D>(P, L, b, face, u, face_cell<D>(n, face, u, false), F.X, F.XG, val);
     }
     (void)pn;
+}
+
+// Ghost fill by pushing (8- and 16-cell blocks), persistent and
+// TMA-staged: each block stages its own interior and writes every ghost slot
+// its cells feed -- the opposite slot of each same-level neighbour, its own
+// physical ghosts and its own refinement ghosts (Sec. 2.6) -- so all reads
+// of the level are contiguous.  Every slot of a launch has exactly one
+// writer; refinement ghosts read only the coarser level.  mode as k_ghost.
+template <class T, int D, int NT>
+__global__ void __launch_bounds__(kMaxThreads) k_ghost_tma(KParams P, int first, int nblocks, T *__restrict__ X,
+                                                           T *__restrict__ XG, int mode) {
+    constexpr int n = NT, C = cells_of<D>(NT), FC = face_of<D>(NT), GH = 2 * D * FC;
+    constexpr int DESC = (int)((sizeof(BlockDesc) + sizeof(LevelDesc)) / sizeof(T));
+    constexpr int STAGE = DESC + C;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t bars[2];
+    __shared__ int s_abort;
+    T *stage0 = reinterpret_cast<T *>(smem_raw);
+    const int tid = threadIdx.x, nth = blockDim.x;
+    if (tid == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        fence_mbar_init();
+        s_abort = 0;
+    }
+    __syncthreads();
+    auto issue = [&](int it, int g) {  // thread 0 only
+        T *st = stage0 + (it & 1) * STAGE;
+        uint64_t *bar = &bars[it & 1];
+        fence_async_smem();
+        mbar_expect_tx(bar, (uint32_t)(sizeof(T) * STAGE));
+        bulk_g2s(st, P.B + g, sizeof(BlockDesc), bar);
+        bulk_g2s(reinterpret_cast<char *>(st) + sizeof(BlockDesc), P.L + P.B[g].lev, sizeof(LevelDesc), bar);
+        bulk_g2s(st + DESC, X + P.B[g].cell_off, sizeof(T) * C, bar);
+    };
+    int g = blockIdx.x;
+    if (tid == 0 && g < nblocks) issue(0, first + g);
+    for (int it = 0; g < nblocks; it++, g += gridDim.x) {
+        {
+            uint32_t tries = 0;
+            while (!mbar_try_wait(&bars[it & 1], (it >> 1) & 1))
+                if (++tries > kWaitLimit) {
+                    atomicExch(P.status, 1);
+                    s_abort = 1;
+                    break;
+                }
+        }
+        __syncthreads();
+        if (s_abort) break;
+        if (tid == 0 && g + (int)gridDim.x < nblocks) issue(it + 1, first + g + gridDim.x);
+        const T *st = stage0 + (it & 1) * STAGE;
+        const BlockDesc &b = *reinterpret_cast<const BlockDesc *>(st);
+        const LevelDesc &L = *reinterpret_cast<const LevelDesc *>(reinterpret_cast<const char *>(st) + sizeof(BlockDesc));
+        const T *xs = st + DESC;
+        for (int t = tid; t < GH; t += nth) {
+            const int face = t / FC, u = t - face * FC, d = face >> 1, s = face & 1;
+            const I3 ii = face_cell<D>(n, face, u, false);
+            const T xi = xs[cidx<D>(n, ii.x, ii.y, ii.z)];
+            const int nb = b.nbr[face];
+            if (nb >= 0) {
+                XG[b.push[face] + u] = xi;
+            } else if (nb == -1) {
+                XG[b.ghost_off + t] = mode >= 1 ? xi : phys_ghost<T>(P, L, face, xi, bc_value(P, L, b, D, face, ii));
+            } else {
+                I3 dd = ii;
+                put(dd, d, s ? n - 2 : 1);
+                XG[b.ghost_off + t] = cf_ghost<T, D>(P, L, b, face, ii, xi, xs[cidx<D>(n, dd.x, dd.y, dd.z)], X, XG, nb,
+                                                     mode == 1);
+            }
+        }
+        __syncthreads();  // stage reads done before it is refilled
+    }
+}
+
+// Coarse-grid correction, persistent and TMA-staged (8- and 16-cell
+// blocks): per child block the descriptors, the child interior and the
+// parent's x, x_old and their ghosts arrive by cp.async.bulk into one stage
+// of a double buffer; x^H - x^H_old on the octant under the child and its
+// face halo goes to a small box, every fine cell takes
+// (2 c0 + cx + cy)/4 (2D) or (c0 + cx + cy + cz)/4 (3D) of it (Sec. 2.3),
+// the child leaves by a bulk store and its face ghosts are pushed as in
+// k_prolong_push.  pn is the parent block size (NT or NT/2, uniform per
+// launch).  Bounded waits as in the sweeps.
+template <class T, int D, int NT>
+__global__ void __launch_bounds__(kMaxThreads) k_prolong_tma(KParams P, int first, int nblocks, Fields<T> F, int pn) {
+    constexpr int n = NT, m = NT / 2, C = cells_of<D>(NT), FC = face_of<D>(NT), B = m + 2;
+    constexpr int BOX = D == 2 ? B * B : B * B * B;
+    constexpr int DESC = (int)((sizeof(BlockDesc) + sizeof(LevelDesc)) / sizeof(T));
+    constexpr int PD = (int)(sizeof(BlockDesc) / sizeof(T));
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t bars[2];
+    __shared__ int s_abort;
+    __shared__ __align__(16) T box[BOX];
+    const int Cp = D == 2 ? pn * pn : pn * pn * pn, FCp = D == 2 ? pn : pn * pn, GHp = 2 * D * FCp;
+    const int stage_elems = DESC + PD + C + 2 * (Cp + GHp);
+    T *stage0 = reinterpret_cast<T *>(smem_raw);
+    const int tid = threadIdx.x, nth = blockDim.x;
+    const uint32_t tx_bytes = (uint32_t)(sizeof(T) * stage_elems);
+    if (tid == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        fence_mbar_init();
+        s_abort = 0;
+    }
+    __syncthreads();
+    auto issue = [&](int it, int g) {  // thread 0 only
+        T *st = stage0 + (it & 1) * stage_elems;
+        const BlockDesc *bd = P.B + g;
+        const int par = bd->parent;
+        const long long co = bd->cell_off, pco = P.B[par].cell_off, pgo = P.B[par].ghost_off;
+        uint64_t *bar = &bars[it & 1];
+        fence_async_smem();
+        mbar_expect_tx(bar, tx_bytes);
+        bulk_g2s(st, bd, sizeof(BlockDesc), bar);
+        bulk_g2s(reinterpret_cast<char *>(st) + sizeof(BlockDesc), P.L + bd->lev, sizeof(LevelDesc), bar);
+        bulk_g2s(st + DESC, P.B + par, sizeof(BlockDesc), bar);
+        T *d = st + DESC + PD;
+        bulk_g2s(d, F.X + co, sizeof(T) * C, bar);
+        bulk_g2s(d + C, F.X + pco, sizeof(T) * Cp, bar);
+        bulk_g2s(d + C + Cp, F.XG + pgo, sizeof(T) * GHp, bar);
+        bulk_g2s(d + C + Cp + GHp, F.V + pco, sizeof(T) * Cp, bar);
+        bulk_g2s(d + C + 2 * Cp + GHp, F.VG + pgo, sizeof(T) * GHp, bar);
+    };
+    int g = blockIdx.x;
+    if (tid == 0 && g < nblocks) issue(0, first + g);
+    auto bid = [](int a, int c, int e) { return D == 2 ? c * B + a : (e * B + c) * B + a; };
+    for (int it = 0; g < nblocks; it++, g += gridDim.x) {
+        {
+            uint32_t tries = 0;
+            while (!mbar_try_wait(&bars[it & 1], (it >> 1) & 1))
+                if (++tries > kWaitLimit) {
+                    atomicExch(P.status, 1);
+                    s_abort = 1;
+                    break;
+                }
+        }
+        __syncthreads();
+        if (s_abort) break;
+        if (tid == 0 && g + (int)gridDim.x < nblocks) {
+            bulk_wait_read0();  // the other stage's store has left shared memory
+            issue(it + 1, first + g + gridDim.x);
+        }
+        T *st = stage0 + (it & 1) * stage_elems;
+        const BlockDesc &b = *reinterpret_cast<const BlockDesc *>(st);
+        const LevelDesc &L = *reinterpret_cast<const LevelDesc *>(reinterpret_cast<const char *>(st) + sizeof(BlockDesc));
+        T *xs = st + DESC + PD;
+        const T *px = xs + C, *pg = px + Cp, *pv = pg + GHp, *pvg = pv + Cp;
+        // parent value at (i, j, k), at most one coordinate outside the parent
+        auto pval = [&](const T *xi, const T *gi, int i, int j, int k) -> T {
+            if (i < 0) return gi[0 * FCp + (D == 2 ? j : j + pn * k)];
+            if (i >= pn) return gi[1 * FCp + (D == 2 ? j : j + pn * k)];
+            if (j < 0) return gi[2 * FCp + (D == 2 ? i : i + pn * k)];
+            if (j >= pn) return gi[3 * FCp + (D == 2 ? i : i + pn * k)];
+            if (D == 3) {
+                if (k < 0) return gi[4 * FCp + i + pn * j];
+                if (k >= pn) return gi[5 * FCp + i + pn * j];
+            }
+            return xi[cidx<D>(pn, i, j, k)];
+        };
+        for (int q = tid; q < BOX; q += nth) {
+            const int a = q % B, c = (q / B) % B, e = D == 3 ? q / (B * B) : 1;
+            const int out = (a == 0 || a == B - 1) + (c == 0 || c == B - 1) + (D == 3 && (e == 0 || e == B - 1));
+            if (out > 1) continue;  // edge / corner of the box: never read
+            const int pi = b.poff[0] + a - 1, pj = b.poff[1] + c - 1, pk = D == 3 ? b.poff[2] + e - 1 : 0;
+            box[bid(a, c, e)] = pval(px, pg, pi, pj, pk) - pval(pv, pvg, pi, pj, pk);
+        }
+        __syncthreads();
+        const int ox = (b.ijk[0] * n) & 1, oy = (b.ijk[1] * n) & 1, oz = (b.ijk[2] * n) & 1;
+        for (int c = tid; c < C; c += nth) {
+            const int i = c % n, j = (c / n) % n, k = D == 3 ? c / (n * n) : 0;
+            const int a = i / 2 + 1, cc = j / 2 + 1, e = D == 3 ? k / 2 + 1 : 1;
+            const int sx = ((ox + i) & 1) ? 1 : -1, sy = ((oy + j) & 1) ? 1 : -1, sz = ((oz + k) & 1) ? 1 : -1;
+            const T v0 = box[bid(a, cc, e)];
+            T nbs = box[bid(a + sx, cc, e)];
+            nbs += box[bid(a, cc + sy, e)];
+            if (D == 3) nbs += box[bid(a, cc, e + sz)];
+            const T val = D == 2 ? ((T)2 * v0 + nbs) / (T)4 : (v0 + nbs) / (T)4;
+            xs[c] = xs[c] + val;
+        }
+        fence_async_smem();
+        __syncthreads();
+        if (tid == 0) {
+            bulk_s2g(F.X + b.cell_off, xs, sizeof(T) * C);
+            bulk_commit();
+        }
+        auto val = [&](I3 q) { return xs[cidx<D>(n, q.x, q.y, q.z)]; };
+        for (int t = tid; t < 2 * D * FC; t += nth) {
+            const int face = t / FC, u = t - face * FC;
+            push_face_cell<T, D>(P, L, b, face, u, face_cell<D>(n, face, u, false), F.X, F.XG, val);
+        }
+        __syncthreads();  // box and stage reads done before the next block
+    }
+    if (tid == 0) bulk_wait0();
 }
 
 // Restriction with the FAS residual for 8- and 16-cell blocks, persistent
@@ -2121,6 +2331,17 @@ template <class T, int D> struct Launch {
         const LevelHost &L = t->lev[l];
         if (L.nb == 0) return;
         ++t->launches;
+        if (L.n == 8 || L.n == 16) {
+            const size_t smt = 2 * (sizeof(BlockDesc) + sizeof(LevelDesc) + sizeof(T) * cells_of<D>(L.n));
+            if (smt <= 200 * 1024) {
+                auto kern = L.n == 8 ? k_ghost_tma<T, D, 8> : k_ghost_tma<T, D, 16>;
+                set_smem(kern, smt);
+                const int thr = threads_for(2 * D * face_of<D>(L.n));
+                const int grid = std::min(L.nb, resident_ctas(kern, thr, smt) * t->nsm);
+                kern<<<grid, thr, smt, t->stream>>>(P, L.first, L.nb, X, XG, mode);
+                return;
+            }
+        }
         if (is_flat(L)) {
             k_ghost_flat<T, D><<<flat_grid(t, (long long)L.nb * 2 * D * face_of<D>(L.n)), 256, 0, t->stream>>>(
                 P, L.first, L.nb, L.n, X, XG, mode);
@@ -2312,9 +2533,24 @@ template <class T, int D> struct Launch {
                 k_fas_rhs_vold<T, D><<<C.nref, threads_for(cells_of<D>(C.n)), 0, t->stream>>>(P, C.first, F);
         }
     }
+    static size_t prolong_tma_smem(const LevelHost &L) {
+        const int n = L.n, pn = L.parent_same_n ? n : n / 2;
+        const size_t Cp = cells_of<D>(pn), GHp = 2 * D * face_of<D>(pn);
+        return 2 * (sizeof(BlockDesc) + sizeof(LevelDesc) + sizeof(BlockDesc) +
+                    sizeof(T) * (cells_of<D>(n) + 2 * (Cp + GHp)));
+    }
     static void prolong(mg_tree *t, const KParams &P, int l, Fields<T> &F) {
         const LevelHost &L = t->lev[l];
         ++t->launches;
+        if ((L.n == 8 || L.n == 16) && prolong_tma_smem(L) <= 200 * 1024) {
+            const size_t smt = prolong_tma_smem(L);
+            auto kern = L.n == 8 ? k_prolong_tma<T, D, 8> : k_prolong_tma<T, D, 16>;
+            set_smem(kern, smt);
+            const int thr = threads_for(cells_of<D>(L.n) / 2);
+            const int grid = std::min(L.nb, resident_ctas(kern, thr, smt) * t->nsm);
+            kern<<<grid, thr, smt, t->stream>>>(P, L.first, L.nb, F, L.parent_same_n ? L.n : L.n / 2);
+            return;
+        }
         if (is_flat(L)) {
             k_prolong_flat<T, D><<<flat_grid(t, (long long)L.nb * cells_of<D>(L.n)), 256, 0, t->stream>>>(
                 P, L.first, L.nb, L.n, F);
