@@ -180,7 +180,9 @@ void project(mg_tree *t, const double *B, double *Bout);
 // r64 (FP64 leaf order), f32 (FP32 into the leaf cells of an FP32 field)
 void residual_norm(mg_tree *t, Fields<double> &F, int homog, double *out3, double *r64_leaf,
                    float *f32_cells);
-void residual_enqueue(mg_tree *t, Fields<double> &F, int homog, double *r64_leaf, float *f32_cells);
+// want_max: also the max norm (solve loops read only the L2 norm)
+void residual_enqueue(mg_tree *t, Fields<double> &F, int homog, double *r64_leaf, float *f32_cells,
+                      bool want_max = false);
 void residual_wait(mg_tree *t, double *out3);
 void add_e_to_phi(mg_tree *t, const float *e, double *phi);
 void copy_eps_to_f32(mg_tree *t);
@@ -189,7 +191,7 @@ void scale_by_radius(mg_tree *t, const double *in_leaf, double *out_leaf, int di
 KParams kparams(mg_tree *t, int homog);
 int time_sweeps(mg_tree *t, int level, int n_sweeps, int prec, double *out4);
 // batch: per-tree composite residual sums (3 per tree, on the host after wait)
-void residual_enqueue_trees(mg_tree *t, Fields<double> &F, float *f32_cells, double *d_tree3);
+void residual_enqueue_trees(mg_tree *t, Fields<double> &F, float *f32_cells, bool want_max);
 // copies between a concatenated per-tree leaf array and the pool cells
 void leaf_runs_copy(mg_tree *t, double *cells, const double *leaf, bool to_cells);
 int check_cuda(const char *what);

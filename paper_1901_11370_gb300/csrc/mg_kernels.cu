@@ -52,6 +52,12 @@ __device__ __forceinline__ T load(const T *__restrict__ X, const T *__restrict__
     return X[b.cell_off + cidx<D>(n, i, j, k)];
 }
 
+// Quotient for the operator's coefficients and the Gauss-Seidel update: the
+// FP32 smoother (an inner solver under FP64 defect correction) takes the
+// fast reciprocal-based intrinsic; FP64 keeps the correctly rounded division.
+template <class T> __device__ __forceinline__ T qdiv(T a, T b) { return a / b; }
+template <> __device__ __forceinline__ float qdiv<float>(float a, float b) { return __fdividef(a, b); }
+
 // 5/7-point row at a cell (Sec. 2.2): for every face the weight
 // w = eps_f * kappa_f / h_d^2 (eps_f harmonic mean of the two cells, kappa
 // r_f/r_i on r-faces of the cylindrical form), giving
@@ -67,7 +73,8 @@ __device__ __forceinline__ void stencil(const KParams &P, const LevelDesc &L, co
     if (E) ec = (A)E[b.cell_off + cidx<D>(n, i, j, k)];
     lap = 0; num = 0; den = 0;
     A ri = 0;
-    if (P.geom == MG_CYL) ri = (A)(P.lo[0] + (b.ijk[0] * n + i + 0.5) * L.h[0]);
+    const A lo0 = (A)P.lo[0], h0 = (A)L.h[0];
+    if (P.geom == MG_CYL) ri = lo0 + ((A)(b.ijk[0] * n + i) + (A)0.5) * h0;
 #pragma unroll
     for (int d = 0; d < D; d++) {
 #pragma unroll
@@ -78,11 +85,11 @@ __device__ __forceinline__ void stencil(const KParams &P, const LevelDesc &L, co
             A w = (A)L.inv_h2[d];
             if (E) {
                 const A en = (A)load<T, D>(E, EG, b, ii, jj, kk);
-                w *= (A)2 * ec * en / (ec + en);
+                w *= qdiv<A>((A)2 * ec * en, ec + en);
             }
             if (P.geom == MG_CYL && d == 0) {
-                const A rf = (A)(P.lo[0] + (b.ijk[0] * n + i + s) * L.h[0]);
-                w *= rf / ri;
+                const A rf = lo0 + (A)(b.ijk[0] * n + i + s) * h0;
+                w *= qdiv<A>(rf, ri);
             }
             lap += w * (xn - xc);
             num += w * xn;
@@ -265,6 +272,8 @@ __global__ void __launch_bounds__(kMaxThreads) k_sweep(KParams P, int first, Fie
         s_ngo[tid] = nb >= 0 ? P.B[nb].ghost_off : -1;
     }
     const LevelDesc &L = P.L[b.lev];
+    const T lo0 = (T)P.lo[0], h0 = (T)L.h[0];  // operator scalars in the kernel precision
+    const T ih0 = (T)L.inv_h2[0], ih1 = (T)L.inv_h2[1], ih2 = (T)L.inv_h2[2];
     const int n = NT ? NT : b.n;
     const int C = cells_of<D>(n), Fc = face_of<D>(n), S = n + 2;
     const int PAD = D == 2 ? S * S : S * S * S;
@@ -359,22 +368,22 @@ __global__ void __launch_bounds__(kMaxThreads) k_sweep(KParams P, int first, Fie
         } else {
             const T ec = var ? se[c0] : (T)1;
             T num = 0, den = 0, ri = 0;
-            if (cyl) ri = (T)(P.lo[0] + (b.ijk[0] * n + i + 0.5) * L.h[0]);
+            if (cyl) ri = lo0 + ((T)(b.ijk[0] * n + i) + (T)0.5) * h0;
 #pragma unroll
             for (int d = 0; d < D; d++)
 #pragma unroll
                 for (int s = 0; s < 2; s++) {
                     const int o = (s ? 1 : -1) * (d == 0 ? 1 : d == 1 ? sy : sz);
-                    T w = (T)L.inv_h2[d];
+                    T w = d == 0 ? ih0 : (d == 1 ? ih1 : ih2);
                     if (var) {
                         const T en = se[c0 + o];
-                        w *= (T)2 * ec * en / (ec + en);
+                        w *= qdiv<T>((T)2 * ec * en, ec + en);
                     }
-                    if (cyl && d == 0) w *= (T)(P.lo[0] + (b.ijk[0] * n + i + s) * L.h[0]) / ri;
+                    if (cyl && d == 0) w *= qdiv<T>(lo0 + (T)(b.ijk[0] * n + i + s) * h0, ri);
                     num += w * sx[c0 + o];
                     den += w;
                 }
-            xnew = (num - fc) / (den + helm);
+            xnew = qdiv<T>(num - fc, den + helm);
         }
         sx[c0] = xnew;
     };
@@ -532,6 +541,8 @@ __global__ void __launch_bounds__(kMaxThreads, 5) k_sweep_tma(KParams P, int fir
         T *st = stage0 + (it & 1) * stage_elems;
         const BlockDesc &b = *reinterpret_cast<const BlockDesc *>(st);
         const LevelDesc &L = *reinterpret_cast<const LevelDesc *>(reinterpret_cast<const char *>(st) + sizeof(BlockDesc));
+        const T lo0 = (T)P.lo[0], h0 = (T)L.h[0];  // operator scalars in the kernel precision
+        const T ih0 = (T)L.inv_h2[0], ih1 = (T)L.inv_h2[1], ih2 = (T)L.inv_h2[2];
         const T w0 = (T)L.inv_h2[0], w1 = (T)L.inv_h2[1], w2 = (T)L.inv_h2[2];
         const T inv_den = (T)L.inv_diag;
         T *xs = st + DESC, *gs = xs + C, *fs = gs + GH, *es = fs + C, *egs = es + C;
@@ -571,21 +582,21 @@ __global__ void __launch_bounds__(kMaxThreads, 5) k_sweep_tma(KParams P, int fir
             } else {
                 const T ec = var ? es[c] : (T)1;
                 T num = 0, den = 0, ri = 0;
-                if (cyl) ri = (T)(P.lo[0] + (bi * n + i + 0.5) * L.h[0]);
+                if (cyl) ri = lo0 + ((T)(bi * n + i) + (T)0.5) * h0;
 #pragma unroll
                 for (int d = 0; d < D; d++)
 #pragma unroll
                     for (int s = 0; s < 2; s++) {
-                        T w = (T)L.inv_h2[d];
+                        T w = d == 0 ? ih0 : (d == 1 ? ih1 : ih2);
                         if (var) {
                             const T en = nbv(es, egs, i, j, k, d, s);
-                            w *= (T)2 * ec * en / (ec + en);
+                            w *= qdiv<T>((T)2 * ec * en, ec + en);
                         }
-                        if (cyl && d == 0) w *= (T)(P.lo[0] + (bi * n + i + s) * L.h[0]) / ri;
+                        if (cyl && d == 0) w *= qdiv<T>(lo0 + (T)(bi * n + i + s) * h0, ri);
                         num += w * nbv(xs, gs, i, j, k, d, s);
                         den += w;
                     }
-                xnew = (num - fs[c]) / (den + helm);
+                xnew = qdiv<T>(num - fs[c], den + helm);
             }
             xs[c] = xnew;  // cells of the other colour are not read by this colour
         }
@@ -688,6 +699,8 @@ __global__ void __launch_bounds__(32 * WARPS) k_sweep_warp(KParams P, int first,
         T *st = wst + (it & 1) * stage_elems;
         const BlockDesc &b = *reinterpret_cast<const BlockDesc *>(st);
         const LevelDesc &L = *reinterpret_cast<const LevelDesc *>(reinterpret_cast<const char *>(st) + sizeof(BlockDesc));
+        const T lo0 = (T)P.lo[0], h0 = (T)L.h[0];  // operator scalars in the kernel precision
+        const T ih0 = (T)L.inv_h2[0], ih1 = (T)L.inv_h2[1], ih2 = (T)L.inv_h2[2];
         const T w0 = (T)L.inv_h2[0], w1 = (T)L.inv_h2[1], w2 = (T)L.inv_h2[2];
         const T inv_den = (T)L.inv_diag;
         T *xs = st + DESC, *gs = xs + C, *fs = gs + GH, *es = fs + C, *egs = es + C;
@@ -725,21 +738,21 @@ __global__ void __launch_bounds__(32 * WARPS) k_sweep_warp(KParams P, int first,
             } else {
                 const T ec = var ? es[c] : (T)1;
                 T num = 0, den = 0, ri = 0;
-                if (cyl) ri = (T)(P.lo[0] + (bi * n + i + 0.5) * L.h[0]);
+                if (cyl) ri = lo0 + ((T)(bi * n + i) + (T)0.5) * h0;
 #pragma unroll
                 for (int d = 0; d < D; d++)
 #pragma unroll
                     for (int s = 0; s < 2; s++) {
-                        T w = (T)L.inv_h2[d];
+                        T w = d == 0 ? ih0 : (d == 1 ? ih1 : ih2);
                         if (var) {
                             const T en = nbv(es, egs, i, j, k, d, s);
-                            w *= (T)2 * ec * en / (ec + en);
+                            w *= qdiv<T>((T)2 * ec * en, ec + en);
                         }
-                        if (cyl && d == 0) w *= (T)(P.lo[0] + (bi * n + i + s) * L.h[0]) / ri;
+                        if (cyl && d == 0) w *= qdiv<T>(lo0 + (T)(bi * n + i + s) * h0, ri);
                         num += w * nbv(xs, gs, i, j, k, d, s);
                         den += w;
                     }
-                xnew = (num - fs[c]) / (den + helm);
+                xnew = qdiv<T>(num - fs[c], den + helm);
             }
             xs[c] = xnew;
         }
@@ -1330,6 +1343,119 @@ __global__ void __launch_bounds__(kMaxThreads) k_ghost_tma(KParams P, int first,
     }
 }
 
+// FAS right-hand side of covered blocks (Sec. 2.4), persistent and
+// TMA-staged (8- and 16-cell blocks): f^H += L^H x^H - lambda x^H from the
+// staged block, its ghosts (and eps); f^H, v_old = x^H and its ghosts leave
+// by bulk stores.  Same arithmetic as the stencil helper.
+template <class T, int D, int NT>
+__global__ void __launch_bounds__(kMaxThreads) k_fas_tma(KParams P, int first, int nblocks, Fields<T> F) {
+    constexpr int n = NT, C = cells_of<D>(NT), FC = face_of<D>(NT), GH = 2 * D * FC;
+    constexpr int DESC = (int)((sizeof(BlockDesc) + sizeof(LevelDesc)) / sizeof(T));
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t bars[2];
+    __shared__ int s_abort;
+    const bool var = F.E != nullptr;
+    const int stage_elems = DESC + 2 * C + GH + (var ? C + GH : 0);
+    T *stage0 = reinterpret_cast<T *>(smem_raw);
+    const int tid = threadIdx.x, nth = blockDim.x;
+    const uint32_t tx_bytes = (uint32_t)(sizeof(T) * stage_elems);
+    if (tid == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        fence_mbar_init();
+        s_abort = 0;
+    }
+    __syncthreads();
+    auto issue = [&](int it, int g) {  // thread 0 only
+        T *st = stage0 + (it & 1) * stage_elems;
+        const long long co = P.B[g].cell_off, go = P.B[g].ghost_off;
+        uint64_t *bar = &bars[it & 1];
+        fence_async_smem();
+        mbar_expect_tx(bar, tx_bytes);
+        bulk_g2s(st, P.B + g, sizeof(BlockDesc), bar);
+        bulk_g2s(reinterpret_cast<char *>(st) + sizeof(BlockDesc), P.L + P.B[g].lev, sizeof(LevelDesc), bar);
+        bulk_g2s(st + DESC, F.X + co, sizeof(T) * C, bar);
+        bulk_g2s(st + DESC + C, F.XG + go, sizeof(T) * GH, bar);
+        bulk_g2s(st + DESC + C + GH, F.F + co, sizeof(T) * C, bar);
+        if (var) {
+            bulk_g2s(st + DESC + 2 * C + GH, F.E + co, sizeof(T) * C, bar);
+            bulk_g2s(st + DESC + 3 * C + GH, F.EG + go, sizeof(T) * GH, bar);
+        }
+    };
+    const bool cyl = P.geom == MG_CYL;
+    int g = blockIdx.x;
+    if (tid == 0 && g < nblocks) issue(0, first + g);
+    for (int it = 0; g < nblocks; it++, g += gridDim.x) {
+        {
+            uint32_t tries = 0;
+            while (!mbar_try_wait(&bars[it & 1], (it >> 1) & 1))
+                if (++tries > kWaitLimit) {
+                    atomicExch(P.status, 1);
+                    s_abort = 1;
+                    break;
+                }
+        }
+        __syncthreads();
+        if (s_abort) break;
+        if (tid == 0 && g + (int)gridDim.x < nblocks) {
+            bulk_wait_read0();  // the other stage's stores have left shared memory
+            issue(it + 1, first + g + gridDim.x);
+        }
+        T *st = stage0 + (it & 1) * stage_elems;
+        const BlockDesc &b = *reinterpret_cast<const BlockDesc *>(st);
+        const LevelDesc &L = *reinterpret_cast<const LevelDesc *>(reinterpret_cast<const char *>(st) + sizeof(BlockDesc));
+        const T lo0 = (T)P.lo[0], h0 = (T)L.h[0];  // operator scalars in the kernel precision
+        const T ih0 = (T)L.inv_h2[0], ih1 = (T)L.inv_h2[1], ih2 = (T)L.inv_h2[2];
+        const T *xs = st + DESC, *gs = xs + C, *es = gs + C + GH, *egs = es + C;
+        T *fs = st + DESC + C + GH;
+        auto nbv = [&](const T *xi, const T *gi, int i, int j, int k, int d, int s) -> T {
+            const int o = s ? 1 : -1;
+            if (d == 0) {
+                const int ii = i + o;
+                if (ii < 0 || ii >= n) return gi[(s ? 1 : 0) * FC + (D == 2 ? j : j + n * k)];
+                return xi[cidx<D>(n, ii, j, k)];
+            }
+            if (d == 1) {
+                const int jj = j + o;
+                if (jj < 0 || jj >= n) return gi[(s ? 3 : 2) * FC + (D == 2 ? i : i + n * k)];
+                return xi[cidx<D>(n, i, jj, k)];
+            }
+            const int kk = k + o;
+            if (kk < 0 || kk >= n) return gi[(s ? 5 : 4) * FC + i + n * j];
+            return xi[cidx<D>(n, i, j, kk)];
+        };
+        for (int c = tid; c < C; c += nth) {
+            const int i = c % n, j = (c / n) % n, k = D == 3 ? c / (n * n) : 0;
+            const T xc = xs[c];
+            const T ec = var ? es[c] : (T)1;
+            T lap = 0, ri = 0;
+            if (cyl) ri = lo0 + ((T)(b.ijk[0] * n + i) + (T)0.5) * h0;
+#pragma unroll
+            for (int d = 0; d < D; d++)
+#pragma unroll
+                for (int s = 0; s < 2; s++) {
+                    T w = d == 0 ? ih0 : (d == 1 ? ih1 : ih2);
+                    if (var) {
+                        const T en = nbv(es, egs, i, j, k, d, s);
+                        w *= qdiv<T>((T)2 * ec * en, ec + en);
+                    }
+                    if (cyl && d == 0) w *= qdiv<T>(lo0 + (T)(b.ijk[0] * n + i + s) * h0, ri);
+                    lap += w * (nbv(xs, gs, i, j, k, d, s) - xc);
+                }
+            fs[c] += lap - (T)P.helm * xc;
+        }
+        fence_async_smem();
+        __syncthreads();
+        if (tid == 0) {
+            bulk_s2g(F.F + b.cell_off, fs, sizeof(T) * C);
+            bulk_s2g(F.V + b.cell_off, xs, sizeof(T) * C);
+            bulk_s2g(F.VG + b.ghost_off, gs, sizeof(T) * GH);
+            bulk_commit();
+        }
+    }
+    if (tid == 0) bulk_wait0();
+}
+
 // Coarse-grid correction, persistent and TMA-staged (8- and 16-cell
 // blocks): per child block the descriptors, the child interior and the
 // parent's x, x_old and their ghosts arrive by cp.async.bulk into one stage
@@ -1524,6 +1650,8 @@ __global__ void __launch_bounds__(kMaxThreads, 4) k_restrict_tma(KParams P, int 
         const BlockDesc &b = *reinterpret_cast<const BlockDesc *>(st);
         const BlockDesc &p = *reinterpret_cast<const BlockDesc *>(st + DESC);
         const LevelDesc &L = *reinterpret_cast<const LevelDesc *>(reinterpret_cast<const char *>(st) + sizeof(BlockDesc));
+        const T lo0 = (T)P.lo[0], h0 = (T)L.h[0];  // operator scalars in the kernel precision
+        const T ih0 = (T)L.inv_h2[0], ih1 = (T)L.inv_h2[1], ih2 = (T)L.inv_h2[2];
         const LevelDesc &PL = *reinterpret_cast<const LevelDesc *>(reinterpret_cast<const char *>(st + DESC) + sizeof(BlockDesc));
         const T *xs = st + 2 * DESC, *gs = xs + C, *fs = gs + GH, *es = fs + C, *egs = es + C;
         auto nbv = [&](const T *xi, const T *gi, int i, int j, int k, int d, int s) -> T {
@@ -1548,17 +1676,17 @@ __global__ void __launch_bounds__(kMaxThreads, 4) k_restrict_tma(KParams P, int 
             const T xc = xs[c];
             const T ec = var ? es[c] : (T)1;
             T lap = 0, ri = 0;
-            if (cyl) ri = (T)(P.lo[0] + (b.ijk[0] * n + i + 0.5) * L.h[0]);
+            if (cyl) ri = lo0 + ((T)(b.ijk[0] * n + i) + (T)0.5) * h0;
 #pragma unroll
             for (int d = 0; d < D; d++)
 #pragma unroll
                 for (int s = 0; s < 2; s++) {
-                    T w = (T)L.inv_h2[d];
+                    T w = d == 0 ? ih0 : (d == 1 ? ih1 : ih2);
                     if (var) {
                         const T en = nbv(es, egs, i, j, k, d, s);
-                        w *= (T)2 * ec * en / (ec + en);
+                        w *= qdiv<T>((T)2 * ec * en, ec + en);
                     }
-                    if (cyl && d == 0) w *= (T)(P.lo[0] + (b.ijk[0] * n + i + s) * L.h[0]) / ri;
+                    if (cyl && d == 0) w *= qdiv<T>(lo0 + (T)(b.ijk[0] * n + i + s) * h0, ri);
                     lap += w * (nbv(xs, gs, i, j, k, d, s) - xc);
                 }
             rs[c] = fs[c] - (lap - (T)P.helm * xc);
@@ -1709,7 +1837,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_resnorm(KParams P, int first, F
 // is formed in FP64 with the difference form sum_d w_d ((x_- - x_c) +
 // (x_+ - x_c)) (rounding error ~ eps |grad x| h rather than eps |x|).  Writes per-CTA partials (sum V r^2, sum V,
 // max |r|) and optionally r (leaf order) and (float) r into FP32 cells.
-template <int D, int NT>
+template <int D, int NT, bool MX = true>
 __global__ void __launch_bounds__(kMaxThreads, 4) k_resid_tma(KParams P, int first, int nblocks, Fields<double> F,
                                                               double *__restrict__ partials,
                                                               double *__restrict__ rleaf, long long leaf_base,
@@ -1755,6 +1883,7 @@ __global__ void __launch_bounds__(kMaxThreads, 4) k_resid_tma(KParams P, int fir
     int g = blockIdx.x;
     if (tid == 0 && g < nblocks) issue(0, first + g);
     // level descriptor: CTA-wide copy when every block shares it, else per block
+    const bool helm0 = P.helm == 0.0;  // Poisson: no lambda term
     const bool cyl = P.geom == MG_CYL;
     double s2 = 0, sv = 0;
     double mx = 0.0;
@@ -1820,7 +1949,7 @@ __global__ void __launch_bounds__(kMaxThreads, 4) k_resid_tma(KParams P, int fir
                         lap += w * (nbv(xs, gs, i, j, k, d, s) - xc);
                     }
             }
-            const double r = fs[c] - (lap - P.helm * xc);
+            const double r = helm0 ? fs[c] - lap : fs[c] - (lap - P.helm * xc);
             if (cyl) {
                 const double V = 2.0 * M_PI * (P.lo[0] + (b.ijk[0] * n + i + 0.5) * L.h[0]) * L.h[0] * L.h[1];
                 s2 = fma(V * r, r, s2);
@@ -1828,7 +1957,7 @@ __global__ void __launch_bounds__(kMaxThreads, 4) k_resid_tma(KParams P, int fir
             } else {
                 bs2 = fma(r, r, bs2);
             }
-            mx = fmax(mx, fabs(r));
+            if (MX) mx = fmax(mx, fabs(r));
             if (f32) f32[b.cell_off + c] = (float)r;
             if (rleaf) rleaf[leaf_base + (long long)g * C + c] = r;
         }
@@ -2175,7 +2304,7 @@ __global__ void __launch_bounds__(256) k_sweep_flat(KParams P, int first, int nb
         const int c = cidx<D>(n, i, j, k);
         T lap, num, den, xc;
         stencil<T, T, D>(P, L, b, F.X, F.XG, F.E, F.EG, i, j, k, lap, num, den, xc);
-        const T xnew = (num - F.F[b.cell_off + c]) / (den + (T)P.helm);
+        const T xnew = qdiv<T>(num - F.F[b.cell_off + c], den + (T)P.helm);
         F.X[b.cell_off + c] = xnew;
         const I3 ii{i, j, k};
 #pragma unroll
@@ -2526,7 +2655,15 @@ template <class T, int D> struct Launch {
             const LevelHost &C = t->lev[c];
             if (C.nref <= 0) continue;
             ++t->launches;
-            if (is_flat(C))
+            const int Cc = cells_of<D>(C.n), Gc = 2 * D * face_of<D>(C.n);
+            const size_t smf = 2 * (sizeof(BlockDesc) + sizeof(LevelDesc) + sizeof(T) * (2 * Cc + Gc + (F.E ? Cc + Gc : 0)));
+            if ((C.n == 8 || C.n == 16) && smf <= 200 * 1024) {
+                auto kern = C.n == 8 ? k_fas_tma<T, D, 8> : k_fas_tma<T, D, 16>;
+                set_smem(kern, smf);
+                const int thr = threads_for(cells_of<D>(C.n));
+                const int grid = std::min(C.nref, resident_ctas(kern, thr, smf) * t->nsm);
+                kern<<<grid, thr, smf, t->stream>>>(P, C.first, C.nref, F);
+            } else if (is_flat(C))
                 k_fas_flat<T, D><<<flat_grid(t, (long long)C.nref * (cells_of<D>(C.n) + 2 * D * face_of<D>(C.n))), 256,
                                    0, t->stream>>>(P, C.first, C.nref, C.n, F, 1);
             else
@@ -2697,7 +2834,7 @@ template void refresh_eps<float>(mg_tree *, Fields<float> &);
 
 template <int D>
 static void residual_norm_d(mg_tree *t, Fields<double> &F, int homog, double *out3, double *r64_leaf,
-                            float *f32_cells) {
+                            float *f32_cells, bool want_max = true) {
     Launch<double, D>::refresh(t, F, homog);
     const KParams P = kparams(t, homog);
     int slot = 0;
@@ -2711,7 +2848,8 @@ static void residual_norm_d(mg_tree *t, Fields<double> &F, int homog, double *ou
         const int C = cells_of<D>(L.n), GH = 2 * D * face_of<D>(L.n);
         const size_t smt = 2 * (sizeof(BlockDesc) + sizeof(LevelDesc) + sizeof(double) * (2 * C + GH + (F.E ? C + GH : 0)));
         if ((L.n == 8 || L.n == 16) && smt <= 200 * 1024) {
-            auto kern = L.n == 8 ? k_resid_tma<D, 8> : k_resid_tma<D, 16>;
+            auto kern = want_max ? (L.n == 8 ? k_resid_tma<D, 8, true> : k_resid_tma<D, 16, true>)
+                                 : (L.n == 8 ? k_resid_tma<D, 8, false> : k_resid_tma<D, 16, false>);
             const int thr = threads_for(C);
             const int grid = std::min(nleaf, resident_ctas(kern, thr, smt) * t->nsm);
             kern<<<grid, thr, smt, t->stream>>>(P, L.first + L.nref, nleaf, F, t->d_partials + 3 * slot, r64_leaf,
@@ -2732,14 +2870,14 @@ static void residual_norm_d(mg_tree *t, Fields<double> &F, int homog, double *ou
 
 // enqueue only (no synchronisation: usable inside a stream capture); the
 // reduced values land in the pinned t->h_red
-void residual_enqueue(mg_tree *t, Fields<double> &F, int homog, double *r64_leaf, float *f32_cells) {
-    if (t->dim == 2) residual_norm_d<2>(t, F, homog, nullptr, r64_leaf, f32_cells);
-    else residual_norm_d<3>(t, F, homog, nullptr, r64_leaf, f32_cells);
+void residual_enqueue(mg_tree *t, Fields<double> &F, int homog, double *r64_leaf, float *f32_cells, bool want_max) {
+    if (t->dim == 2) residual_norm_d<2>(t, F, homog, nullptr, r64_leaf, f32_cells, want_max);
+    else residual_norm_d<3>(t, F, homog, nullptr, r64_leaf, f32_cells, want_max);
 }
 
 // Batch: composite residual with one partial per leaf block, reduced per
 // tree into d_tree3 (3 values per tree), copied to the pinned t->h_tree3.
-template <int D> static void residual_trees_d(mg_tree *t, Fields<double> &F, float *f32) {
+template <int D> static void residual_trees_d(mg_tree *t, Fields<double> &F, float *f32, bool want_max) {
     Launch<double, D>::refresh(t, F, 0);
     const KParams P = kparams(t, 0);
     int slot = 0;
@@ -2752,7 +2890,8 @@ template <int D> static void residual_trees_d(mg_tree *t, Fields<double> &F, flo
         const int C = cells_of<D>(L.n), GH = 2 * D * face_of<D>(L.n);
         const size_t smt = 2 * (sizeof(BlockDesc) + sizeof(LevelDesc) + sizeof(double) * (2 * C + GH + (F.E ? C + GH : 0)));
         if ((L.n == 8 || L.n == 16) && smt <= 200 * 1024) {
-            auto kern = L.n == 8 ? k_resid_tma<D, 8> : k_resid_tma<D, 16>;
+            auto kern = want_max ? (L.n == 8 ? k_resid_tma<D, 8, true> : k_resid_tma<D, 16, true>)
+                                 : (L.n == 8 ? k_resid_tma<D, 8, false> : k_resid_tma<D, 16, false>);
             const int thr = threads_for(C);
             const int grid = std::min(nleaf, resident_ctas(kern, thr, smt) * t->nsm);
             kern<<<grid, thr, smt, t->stream>>>(P, L.first + L.nref, nleaf, F, t->d_partials + 3LL * slot, nullptr, 0,
@@ -2787,9 +2926,9 @@ void leaf_runs_copy(mg_tree *t, double *cells, const double *leaf, bool to_cells
     k_runs_copy<<<t->n_runs, 256, 0, t->stream>>>(t->d_runs, cells, const_cast<double *>(leaf), to_cells ? 1 : 0);
 }
 
-void residual_enqueue_trees(mg_tree *t, Fields<double> &F, float *f32_cells, double *) {
-    if (t->dim == 2) residual_trees_d<2>(t, F, f32_cells);
-    else residual_trees_d<3>(t, F, f32_cells);
+void residual_enqueue_trees(mg_tree *t, Fields<double> &F, float *f32_cells, bool want_max) {
+    if (t->dim == 2) residual_trees_d<2>(t, F, f32_cells, want_max);
+    else residual_trees_d<3>(t, F, f32_cells, want_max);
 }
 
 void residual_wait(mg_tree *t, double *out3) {
@@ -2800,7 +2939,7 @@ void residual_wait(mg_tree *t, double *out3) {
 }
 
 void residual_norm(mg_tree *t, Fields<double> &F, int homog, double *out3, double *r64_leaf, float *f32_cells) {
-    residual_enqueue(t, F, homog, r64_leaf, f32_cells);
+    residual_enqueue(t, F, homog, r64_leaf, f32_cells, true);
     residual_wait(t, out3);
 }
 

@@ -1257,7 +1257,7 @@ extern "C" int mg_batch_residual_norms(mg_batch *b, double *l2, double *linf) {
     NEED_BATCH(b);
     if (!l2 || !linf) return fail(MG_ERR_ARG, "null output");
     mg_tree *P = b->pool;
-    residual_enqueue_trees(P, P->f64, nullptr, nullptr);
+    residual_enqueue_trees(P, P->f64, nullptr, true);
     int rc = check_cuda("batch residual");
     if (rc || (rc = batch_norms_wait(P, b->ntrees, l2, linf)) || (rc = check_status(P))) return rc;
     for (int i = 0; i < b->ntrees; i++)
@@ -1290,12 +1290,12 @@ extern "C" int mg_batch_solve(mg_batch *b, double rel_tol, int max_cycles, int f
     };
     double worst;
     if (q.precision == MG_FP64) {
-        if ((rc = run_graph(t, "b-res64", [&] { residual_enqueue_trees(t, t->f64, nullptr, nullptr); }))) return rc;
+        if ((rc = run_graph(t, "b-res64", [&] { residual_enqueue_trees(t, t->f64, nullptr, false); }))) return rc;
         worst = update(true);
         if (fmg_first && max_cycles > 0 && worst > 0) {
             rc = run_graph(t, "b-fmg64+res" + sfx, [&] {
                 fmg<double>(t, t->f64, q.n_down, q.n_up, 0);
-                residual_enqueue_trees(t, t->f64, nullptr, nullptr);
+                residual_enqueue_trees(t, t->f64, nullptr, false);
             });
             if (rc) return rc;
             cycles++;
@@ -1304,7 +1304,7 @@ extern "C" int mg_batch_solve(mg_batch *b, double rel_tol, int max_cycles, int f
         while (worst > rel_tol && cycles < max_cycles) {
             rc = run_graph(t, "b-v64+res" + sfx, [&] {
                 vcycle<double>(t, t->f64, top, q.n_down, q.n_up, 0);
-                residual_enqueue_trees(t, t->f64, nullptr, nullptr);
+                residual_enqueue_trees(t, t->f64, nullptr, false);
             });
             if (rc) return rc;
             cycles++;
@@ -1313,7 +1313,7 @@ extern "C" int mg_batch_solve(mg_batch *b, double rel_tol, int max_cycles, int f
         }
     } else if (q.precision == MG_FP32_DC) {
         if ((rc = ensure_f32(t))) return rc;
-        if ((rc = run_graph(t, "b-res64f32", [&] { residual_enqueue_trees(t, t->f64, t->f32.F, nullptr); }))) return rc;
+        if ((rc = run_graph(t, "b-res64f32", [&] { residual_enqueue_trees(t, t->f64, t->f32.F, false); }))) return rc;
         worst = update(true);
         const std::string ki = sfx + ":" + std::to_string(q.inner_cycles);
         while (worst > rel_tol && cycles < max_cycles) {
@@ -1328,7 +1328,7 @@ extern "C" int mg_batch_solve(mg_batch *b, double rel_tol, int max_cycles, int f
                     for (int c = 0; c < q.inner_cycles; c++) vcycle<float>(t, t->f32, top, q.n_down, q.n_up, 1);
                 }
                 add_e_to_phi(t, t->f32.X, t->f64.X);
-                residual_enqueue_trees(t, t->f64, t->f32.F, nullptr);
+                residual_enqueue_trees(t, t->f64, t->f32.F, false);
             });
             if (rc) return rc;
             cycles++;
