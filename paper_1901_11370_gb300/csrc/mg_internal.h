@@ -82,6 +82,7 @@ struct Fields {
     T *F = nullptr;                  // right-hand side (interior)
     T *E = nullptr, *EG = nullptr;   // coefficient: interior + ghosts (nullptr: eps = 1)
     T *V = nullptr, *VG = nullptr;   // FAS copy v_old: interior + ghosts
+    T *W = nullptr;                  // face coefficients, 2D per cell ([face][cell] per block); nullptr: on the fly
 };
 
 // A level of one tree; in a pool of several trees (a batch), a segment:
@@ -139,6 +140,7 @@ struct mg_tree {
     mg::Fields<double> f64, adj;   // solve and adjoint solve (adj shares E/EG)
     mg::Fields<float> f32;         // inner defect-correction cycles
     double *d_r64 = nullptr;       // leaf residual scratch (FP64)
+    double *d_wface = nullptr;     // FP64 face coefficients (variable eps or cylindrical form)
     double *d_minv = nullptr;      // coarsest-level inverses, row-major ns x ns per tree
     long long minv_total = 0, cvec_total = 0;
     int nc = 0, ns = 0;            // coarsest cells, system size (nc + singular) -- one tree
@@ -186,6 +188,8 @@ void residual_enqueue(mg_tree *t, Fields<double> &F, int homog, double *r64_leaf
 void residual_wait(mg_tree *t, double *out3);
 void add_e_to_phi(mg_tree *t, const float *e, double *phi);
 void copy_eps_to_f32(mg_tree *t);
+// FP64 face coefficients of every cell into t->d_wface (eps ghosts current)
+void face_coef(mg_tree *t);
 void eps_grad(mg_tree *t, const double *lam_cells, const double *phi_cells, double *out_leaf);
 void scale_by_radius(mg_tree *t, const double *in_leaf, double *out_leaf, int divide);
 KParams kparams(mg_tree *t, int homog);

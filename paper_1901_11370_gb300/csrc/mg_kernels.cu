@@ -1850,8 +1850,8 @@ __global__ void __launch_bounds__(kMaxThreads, 4) k_resid_tma(KParams P, int fir
     __shared__ __align__(16) LevelDesc sL;
     __shared__ int s_abort;
     __shared__ double sred[3][kMaxThreads / 32];
-    const bool var = F.E != nullptr;
-    const int stage_elems = DESC + 2 * C + GH + (var ? C + GH : 0);
+    const bool var = F.E != nullptr, wc = F.W != nullptr;  // wc: precomputed face coefficients
+    const int stage_elems = DESC + 2 * C + GH + (wc ? 2 * D * C : (var ? C + GH : 0));
     T *stage0 = reinterpret_cast<T *>(smem_raw);
     const int tid = threadIdx.x, nth = blockDim.x;
     const uint32_t tx_bytes = (uint32_t)(sizeof(T) * stage_elems);
@@ -1861,8 +1861,6 @@ __global__ void __launch_bounds__(kMaxThreads, 4) k_resid_tma(KParams P, int fir
         fence_mbar_init();
         s_abort = 0;
     }
-    if (tid < (int)(sizeof(LevelDesc) / 4))
-        reinterpret_cast<int *>(&sL)[tid] = reinterpret_cast<const int *>(P.L + P.B[first].lev)[tid];
     __syncthreads();
     auto issue = [&](int it, int g) {
         T *st = stage0 + (it & 1) * stage_elems;
@@ -1875,14 +1873,15 @@ __global__ void __launch_bounds__(kMaxThreads, 4) k_resid_tma(KParams P, int fir
         bulk_g2s(st + DESC, F.X + co, sizeof(T) * C, bar);
         bulk_g2s(st + DESC + C, F.XG + go, sizeof(T) * GH, bar);
         bulk_g2s(st + DESC + C + GH, F.F + co, sizeof(T) * C, bar);
-        if (var) {
+        if (wc) {
+            bulk_g2s(st + DESC + 2 * C + GH, F.W + co * (2 * D), sizeof(T) * 2 * D * C, bar);
+        } else if (var) {
             bulk_g2s(st + DESC + 2 * C + GH, F.E + co, sizeof(T) * C, bar);
             bulk_g2s(st + DESC + 3 * C + GH, F.EG + go, sizeof(T) * GH, bar);
         }
     };
     int g = blockIdx.x;
     if (tid == 0 && g < nblocks) issue(0, first + g);
-    // level descriptor: CTA-wide copy when every block shares it, else per block
     const bool helm0 = P.helm == 0.0;  // Poisson: no lambda term
     const bool cyl = P.geom == MG_CYL;
     double s2 = 0, sv = 0;
@@ -1931,6 +1930,13 @@ __global__ void __launch_bounds__(kMaxThreads, 4) k_resid_tma(KParams P, int fir
                 lap = w0 * ((nbv(xs, gs, i, j, k, 0, 0) - xc) + (nbv(xs, gs, i, j, k, 0, 1) - xc));
                 lap = fma(w1, (nbv(xs, gs, i, j, k, 1, 0) - xc) + (nbv(xs, gs, i, j, k, 1, 1) - xc), lap);
                 if (D == 3) lap = fma(w2, (nbv(xs, gs, i, j, k, 2, 0) - xc) + (nbv(xs, gs, i, j, k, 2, 1) - xc), lap);
+            } else if (wc) {
+                const double *ws = es + c;  // coefficients [face][cell]
+                lap = 0;
+#pragma unroll
+                for (int d = 0; d < D; d++)
+#pragma unroll
+                    for (int s = 0; s < 2; s++) lap += ws[(2 * d + s) * C] * (nbv(xs, gs, i, j, k, d, s) - xc);
             } else {
                 const double ec = var ? es[c] : 1.0;
                 double ri = 0;
@@ -2235,6 +2241,59 @@ __global__ void __launch_bounds__(kMaxThreads) k_eps_grad(KParams P, int first, 
 }
 
 // ------------------------------------------------------------ driver ----
+
+// Face coefficients of the FP64 operator (Sec. 2.2), one thread per cell:
+// w = (1/h_d^2) * 2 eps_c eps_n / (eps_c + eps_n) * (r_face / r_cell), the
+// same expression and order as the residual kernel evaluates on the fly.
+// Stored per block as [face][cell] after cell_off * 2D.
+template <int D>
+__global__ void __launch_bounds__(256) k_face_coef(KParams P, int first, int nblocks, int n,
+                                                   const double *__restrict__ E, const double *__restrict__ EG,
+                                                   double *__restrict__ W) {
+    const int C = cells_of<D>(n);
+    const long long total = (long long)nblocks * C;
+    const bool cyl = P.geom == MG_CYL;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const BlockDesc &b = P.B[first + (int)(idx / C)];
+        const LevelDesc &L = P.L[b.lev];
+        const int c = (int)(idx % C);
+        int i, j, k;
+        cell_of(c, n, D, i, j, k);
+        const double ec = E ? E[b.cell_off + c] : 1.0;
+        double ri = 0;
+        if (cyl) ri = P.lo[0] + (b.ijk[0] * n + i + 0.5) * L.h[0];
+        double *w_out = W + b.cell_off * (2 * D) + c;
+#pragma unroll
+        for (int d = 0; d < D; d++)
+#pragma unroll
+            for (int s = 0; s < 2; s++) {
+                double w = L.inv_h2[d];
+                if (E) {
+                    const int o = s ? 1 : -1;
+                    const double en = load<double, D>(E, EG, b, i + (d == 0 ? o : 0), j + (d == 1 ? o : 0),
+                                                      k + (d == 2 ? o : 0));
+                    w *= 2.0 * ec * en / (ec + en);
+                }
+                if (cyl && d == 0) w *= (P.lo[0] + (b.ijk[0] * n + i + s) * L.h[0]) / ri;
+                w_out[(2 * d + s) * C] = w;
+            }
+    }
+}
+
+void face_coef(mg_tree *t) {
+    const KParams P = kparams(t, 0);
+    for (const LevelHost &L : t->lev) {
+        if (L.nb == 0) continue;
+        ++t->launches;
+        const long long items = (long long)L.nb * (t->dim == 2 ? L.n * L.n : L.n * L.n * L.n);
+        const int grid = (int)std::max<long long>(1, std::min<long long>((items + 255) / 256, 8LL * t->nsm));
+        if (t->dim == 2)
+            k_face_coef<2><<<grid, 256, 0, t->stream>>>(P, L.first, L.nb, L.n, t->f64.E, t->f64.EG, t->d_wface);
+        else
+            k_face_coef<3><<<grid, 256, 0, t->stream>>>(P, L.first, L.nb, L.n, t->f64.E, t->f64.EG, t->d_wface);
+    }
+}
 
 // ----------------------------------------------- flat small-block path ---
 // Segments of tiny blocks (at most kFlatCells cells, the halved block sizes
@@ -2832,6 +2891,13 @@ template void refresh<float>(mg_tree *, Fields<float> &, int);
 template void refresh_eps<double>(mg_tree *, Fields<double> &);
 template void refresh_eps<float>(mg_tree *, Fields<float> &);
 
+// bytes of the two stages of k_resid_tma for n-cell blocks
+template <int D> static size_t resid_smem(int n, const Fields<double> &F) {
+    const int C = cells_of<D>(n), GH = 2 * D * face_of<D>(n);
+    return 2 * (sizeof(BlockDesc) + sizeof(LevelDesc) +
+                sizeof(double) * (2 * C + GH + (F.W ? 2 * D * C : (F.E ? C + GH : 0))));
+}
+
 template <int D>
 static void residual_norm_d(mg_tree *t, Fields<double> &F, int homog, double *out3, double *r64_leaf,
                             float *f32_cells, bool want_max = true) {
@@ -2846,7 +2912,7 @@ static void residual_norm_d(mg_tree *t, Fields<double> &F, int homog, double *ou
         const long long cell_base = t->blocks[L.first + L.nref].cell_off;
         ++t->launches;
         const int C = cells_of<D>(L.n), GH = 2 * D * face_of<D>(L.n);
-        const size_t smt = 2 * (sizeof(BlockDesc) + sizeof(LevelDesc) + sizeof(double) * (2 * C + GH + (F.E ? C + GH : 0)));
+        const size_t smt = resid_smem<D>(L.n, F);
         if ((L.n == 8 || L.n == 16) && smt <= 200 * 1024) {
             auto kern = want_max ? (L.n == 8 ? k_resid_tma<D, 8, true> : k_resid_tma<D, 16, true>)
                                  : (L.n == 8 ? k_resid_tma<D, 8, false> : k_resid_tma<D, 16, false>);
@@ -2888,7 +2954,7 @@ template <int D> static void residual_trees_d(mg_tree *t, Fields<double> &F, flo
         const long long cell_base = t->blocks[L.first + L.nref].cell_off;
         ++t->launches;
         const int C = cells_of<D>(L.n), GH = 2 * D * face_of<D>(L.n);
-        const size_t smt = 2 * (sizeof(BlockDesc) + sizeof(LevelDesc) + sizeof(double) * (2 * C + GH + (F.E ? C + GH : 0)));
+        const size_t smt = resid_smem<D>(L.n, F);
         if ((L.n == 8 || L.n == 16) && smt <= 200 * 1024) {
             auto kern = want_max ? (L.n == 8 ? k_resid_tma<D, 8, true> : k_resid_tma<D, 16, true>)
                                  : (L.n == 8 ? k_resid_tma<D, 8, false> : k_resid_tma<D, 16, false>);
@@ -3069,7 +3135,8 @@ static int residual_norm_noalloc_d(mg_tree *t, double *scratch, double *out3) {
         const int nleaf = L.nb - L.nref;
         if (nleaf <= 0) continue;
         const int C = cells_of<D>(L.n), GH = 2 * D * face_of<D>(L.n);
-        const size_t smt = 2 * (sizeof(BlockDesc) + sizeof(LevelDesc) + sizeof(double) * (2 * C + GH + (t->f64.E ? C + GH : 0)));
+        const size_t smt = resid_smem<D>(L.n, t->f64);
+        (void)GH;
         if ((L.n == 8 || L.n == 16) && smt <= 200 * 1024) {
             auto kern = L.n == 8 ? k_resid_tma<D, 8> : k_resid_tma<D, 16>;
             need += std::min(nleaf, resident_ctas(kern, threads_for(C), smt) * t->nsm);
@@ -3092,7 +3159,7 @@ static int residual_norm_noalloc_d(mg_tree *t, double *scratch, double *out3) {
         if (nleaf <= 0) continue;
         const long long cell_base = t->blocks[L.first + L.nref].cell_off;
         const int C = cells_of<D>(L.n), GH = 2 * D * face_of<D>(L.n);
-        const size_t smt = 2 * (sizeof(BlockDesc) + sizeof(LevelDesc) + sizeof(double) * (2 * C + GH + (F.E ? C + GH : 0)));
+        const size_t smt = resid_smem<D>(L.n, F);
         ++t->launches;
         if ((L.n == 8 || L.n == 16) && smt <= 200 * 1024) {
             auto kern = L.n == 8 ? k_resid_tma<D, 8> : k_resid_tma<D, 16>;

@@ -575,6 +575,11 @@ extern "C" int mg_tree_finalize(mg_tree *t, void *stream) {
     CK(cudaStreamCreateWithFlags(&t->cap_stream, cudaStreamNonBlocking));
     t->finalized = true;
     if ((rc = build_coarse_inverse(t))) return rc;
+    if (t->geom == MG_CYL) {  // r-face factors: precomputed FP64 face coefficients
+        if ((rc = dalloc(&t->d_wface, t->ncells * 2 * t->dim))) return rc;
+        t->f64.W = t->d_wface;
+        face_coef(t);
+    }
     tune_sweeps<double>(t, t->f64);  // fields and ghosts are still zero here
     CK(cudaMemsetAsync(t->f64.X, 0, sizeof(double) * t->ncells, t->stream));
     refresh<double>(t, t->f64, 0);
@@ -717,7 +722,11 @@ extern "C" int mg_set_eps(mg_tree *t, const double *e) {
     t->var_eps = true;
     if ((rc = leaf_copy(t, t->f64.E, e, true))) return rc;
     refresh_eps<double>(t, t->f64);
+    if ((rc = dalloc(&t->d_wface, t->ncells * 2 * t->dim))) return rc;
+    t->f64.W = t->d_wface;  // precomputed FP64 face coefficients for the residual
+    face_coef(t);
     t->adj.E = t->f64.E;
+    t->adj.W = t->f64.W;
     t->adj.EG = t->f64.EG;
     if (t->f32.X) {
         if ((rc = dalloc(&t->f32.E, t->ncells)) || (rc = dalloc(&t->f32.EG, t->nghost))) return rc;
@@ -869,6 +878,7 @@ extern "C" int mg_adjoint(mg_tree *t, const double *g, double *dLdf, double *dLd
     int rc;
     if ((rc = alloc_fields(t, t->adj, false))) return rc;
     t->adj.E = t->f64.E;
+    t->adj.W = t->f64.W;
     t->adj.EG = t->f64.EG;
     // rhs g (Cartesian) or g / r (cylindrical: A^T = diag(r) A diag(r)^-1)
     if (t->geom == MG_CYL) {
@@ -967,7 +977,7 @@ extern "C" int mg_tree_destroy(mg_tree *t) {
         free_fields(t->adj, false);
         free_fields(t->f32, true);
         cudaFree(t->d_blocks); cudaFree(t->d_levels); cudaFree(t->d_bcplanes);
-        cudaFree(t->d_r64); cudaFree(t->d_minv); cudaFree(t->d_cvec); cudaFree(t->d_partials); cudaFree(t->d_red); cudaFree(t->d_status); cudaFree(t->d_tcoarse);
+        cudaFree(t->d_r64); cudaFree(t->d_wface); cudaFree(t->d_minv); cudaFree(t->d_cvec); cudaFree(t->d_partials); cudaFree(t->d_red); cudaFree(t->d_status); cudaFree(t->d_tcoarse);
         cudaFreeHost(t->h_red);
         cudaFree(t->d_runs); cudaFree(t->d_slot_off); cudaFree(t->d_slots); cudaFree(t->d_tree3);
         cudaFreeHost(t->h_tree3);
