@@ -82,7 +82,7 @@ struct Fields {
     T *F = nullptr;                  // right-hand side (interior)
     T *E = nullptr, *EG = nullptr;   // coefficient: interior + ghosts (nullptr: eps = 1)
     T *V = nullptr, *VG = nullptr;   // FAS copy v_old: interior + ghosts
-    T *W = nullptr;                  // face coefficients, 2D per cell ([face][cell] per block); nullptr: on the fly
+    T *W = nullptr;                  // face coefficients + diagonal, 2D + 1 per cell ([face][cell] per block)
 };
 
 // A level of one tree; in a pool of several trees (a batch), a segment:

@@ -1838,7 +1838,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_resnorm(KParams P, int first, F
 // (x_+ - x_c)) (rounding error ~ eps |grad x| h rather than eps |x|).  Writes per-CTA partials (sum V r^2, sum V,
 // max |r|) and optionally r (leaf order) and (float) r into FP32 cells.
 template <int D, int NT, bool MX = true>
-__global__ void __launch_bounds__(kMaxThreads, 4) k_resid_tma(KParams P, int first, int nblocks, Fields<double> F,
+__global__ void __launch_bounds__(kMaxThreads, 3) k_resid_tma(KParams P, int first, int nblocks, Fields<double> F,
                                                               double *__restrict__ partials,
                                                               double *__restrict__ rleaf, long long leaf_base,
                                                               float *__restrict__ f32, int per_block = 0) {
@@ -1851,7 +1851,7 @@ __global__ void __launch_bounds__(kMaxThreads, 4) k_resid_tma(KParams P, int fir
     __shared__ int s_abort;
     __shared__ double sred[3][kMaxThreads / 32];
     const bool var = F.E != nullptr, wc = F.W != nullptr;  // wc: precomputed face coefficients
-    const int stage_elems = DESC + 2 * C + GH + (wc ? 2 * D * C : (var ? C + GH : 0));
+    const int stage_elems = DESC + 2 * C + GH + (wc ? (2 * D + 1) * C : (var ? C + GH : 0));
     T *stage0 = reinterpret_cast<T *>(smem_raw);
     const int tid = threadIdx.x, nth = blockDim.x;
     const uint32_t tx_bytes = (uint32_t)(sizeof(T) * stage_elems);
@@ -1874,7 +1874,7 @@ __global__ void __launch_bounds__(kMaxThreads, 4) k_resid_tma(KParams P, int fir
         bulk_g2s(st + DESC + C, F.XG + go, sizeof(T) * GH, bar);
         bulk_g2s(st + DESC + C + GH, F.F + co, sizeof(T) * C, bar);
         if (wc) {
-            bulk_g2s(st + DESC + 2 * C + GH, F.W + co * (2 * D), sizeof(T) * 2 * D * C, bar);
+            bulk_g2s(st + DESC + 2 * C + GH, F.W + co * (2 * D + 1), sizeof(T) * (2 * D + 1) * C, bar);
         } else if (var) {
             bulk_g2s(st + DESC + 2 * C + GH, F.E + co, sizeof(T) * C, bar);
             bulk_g2s(st + DESC + 3 * C + GH, F.EG + go, sizeof(T) * GH, bar);
@@ -1921,22 +1921,31 @@ __global__ void __launch_bounds__(kMaxThreads, 4) k_resid_tma(KParams P, int fir
             if (kk < 0 || kk >= n) return gi[(s ? 5 : 4) * FC + i + n * j];
             return xi[cidx<D>(n, i, j, kk)];
         };
+        // A x as (sum_f w_f x_f) - (sum_f w_f + lambda) x_c: FP64 operations
+        // are GB300's scarcest resource here; the rounding stays at
+        // eps * sum_f w_f |x|, far below any tolerance the solves use
+        const double dg = 2.0 * (w0 + w1 + (D == 3 ? w2 : 0.0)) + P.helm;
         double bs2 = 0;
+        float bs2f = 0.f, s2f = 0.f, svf = 0.f;  // solve-loop norms (MX off) in FP32
+        const float lo0f = (float)P.lo[0], h0f = (float)L.h[0], hvf = (float)(2.0 * M_PI * L.h[0] * L.h[1]);
         for (int c = tid; c < C; c += nth) {
             const int i = c % n, j = (c / n) % n, k = D == 3 ? c / (n * n) : 0;
             const double xc = xs[c];
-            double lap;
+            double lap;  // A x + lambda x (the residual below subtracts lambda x)
+            double r;
             if (!var && !cyl) {
-                lap = w0 * ((nbv(xs, gs, i, j, k, 0, 0) - xc) + (nbv(xs, gs, i, j, k, 0, 1) - xc));
-                lap = fma(w1, (nbv(xs, gs, i, j, k, 1, 0) - xc) + (nbv(xs, gs, i, j, k, 1, 1) - xc), lap);
-                if (D == 3) lap = fma(w2, (nbv(xs, gs, i, j, k, 2, 0) - xc) + (nbv(xs, gs, i, j, k, 2, 1) - xc), lap);
-            } else if (wc) {
-                const double *ws = es + c;  // coefficients [face][cell]
+                double sx = w0 * (nbv(xs, gs, i, j, k, 0, 0) + nbv(xs, gs, i, j, k, 0, 1));
+                sx = fma(w1, nbv(xs, gs, i, j, k, 1, 0) + nbv(xs, gs, i, j, k, 1, 1), sx);
+                if (D == 3) sx = fma(w2, nbv(xs, gs, i, j, k, 2, 0) + nbv(xs, gs, i, j, k, 2, 1), sx);
+                r = fs[c] - fma(-dg, xc, sx);
                 lap = 0;
+            } else if (wc) {
+                const double *ws = es + c;  // coefficients [face][cell], the diagonal last
+                double sx = ws[0] * nbv(xs, gs, i, j, k, 0, 0);
 #pragma unroll
-                for (int d = 0; d < D; d++)
-#pragma unroll
-                    for (int s = 0; s < 2; s++) lap += ws[(2 * d + s) * C] * (nbv(xs, gs, i, j, k, d, s) - xc);
+                for (int f = 1; f < 2 * D; f++) sx = fma(ws[f * C], nbv(xs, gs, i, j, k, f >> 1, f & 1), sx);
+                r = fs[c] - fma(-ws[2 * D * C], xc, sx);
+                lap = 0;
             } else {
                 const double ec = var ? es[c] : 1.0;
                 double ri = 0;
@@ -1954,18 +1963,32 @@ __global__ void __launch_bounds__(kMaxThreads, 4) k_resid_tma(KParams P, int fir
                         if (cyl && d == 0) w *= (P.lo[0] + (b.ijk[0] * n + i + s) * L.h[0]) / ri;
                         lap += w * (nbv(xs, gs, i, j, k, d, s) - xc);
                     }
+                r = helm0 ? fs[c] - lap : fs[c] - (lap - P.helm * xc);
             }
-            const double r = helm0 ? fs[c] - lap : fs[c] - (lap - P.helm * xc);
-            if (cyl) {
-                const double V = 2.0 * M_PI * (P.lo[0] + (b.ijk[0] * n + i + 0.5) * L.h[0]) * L.h[0] * L.h[1];
-                s2 = fma(V * r, r, s2);
-                sv += V;
+            const float rf = (float)r;
+            if (MX) {
+                if (cyl) {
+                    const double V = 2.0 * M_PI * (P.lo[0] + (b.ijk[0] * n + i + 0.5) * L.h[0]) * L.h[0] * L.h[1];
+                    s2 = fma(V * r, r, s2);
+                    sv += V;
+                } else {
+                    bs2 = fma(r, r, bs2);
+                }
+                mx = fmax(mx, fabs(r));
+            } else if (cyl) {
+                const float Vf = (lo0f + ((float)(b.ijk[0] * n + i) + 0.5f) * h0f) * hvf;
+                s2f = fmaf(Vf * rf, rf, s2f);
+                svf += Vf;
             } else {
-                bs2 = fma(r, r, bs2);
+                bs2f = fmaf(rf, rf, bs2f);
             }
-            if (MX) mx = fmax(mx, fabs(r));
-            if (f32) f32[b.cell_off + c] = (float)r;
+            if (f32) f32[b.cell_off + c] = rf;
             if (rleaf) rleaf[leaf_base + (long long)g * C + c] = r;
+        }
+        if (!MX) {
+            bs2 += (double)bs2f;
+            s2 += (double)s2f;
+            sv += (double)svf;
         }
         if (!cyl) {
             s2 = fma(vol, bs2, s2);
@@ -2243,9 +2266,9 @@ __global__ void __launch_bounds__(kMaxThreads) k_eps_grad(KParams P, int first, 
 // ------------------------------------------------------------ driver ----
 
 // Face coefficients of the FP64 operator (Sec. 2.2), one thread per cell:
-// w = (1/h_d^2) * 2 eps_c eps_n / (eps_c + eps_n) * (r_face / r_cell), the
-// same expression and order as the residual kernel evaluates on the fly.
-// Stored per block as [face][cell] after cell_off * 2D.
+// w = (1/h_d^2) * 2 eps_c eps_n / (eps_c + eps_n) * (r_face / r_cell), and
+// the row's diagonal sum w + lambda.  Stored per block as [face][cell],
+// 2D + 1 "faces" (the last the diagonal), after cell_off * (2D + 1).
 template <int D>
 __global__ void __launch_bounds__(256) k_face_coef(KParams P, int first, int nblocks, int n,
                                                    const double *__restrict__ E, const double *__restrict__ EG,
@@ -2263,7 +2286,8 @@ __global__ void __launch_bounds__(256) k_face_coef(KParams P, int first, int nbl
         const double ec = E ? E[b.cell_off + c] : 1.0;
         double ri = 0;
         if (cyl) ri = P.lo[0] + (b.ijk[0] * n + i + 0.5) * L.h[0];
-        double *w_out = W + b.cell_off * (2 * D) + c;
+        double *w_out = W + b.cell_off * (2 * D + 1) + c;
+        double wsum = 0;
 #pragma unroll
         for (int d = 0; d < D; d++)
 #pragma unroll
@@ -2277,7 +2301,9 @@ __global__ void __launch_bounds__(256) k_face_coef(KParams P, int first, int nbl
                 }
                 if (cyl && d == 0) w *= (P.lo[0] + (b.ijk[0] * n + i + s) * L.h[0]) / ri;
                 w_out[(2 * d + s) * C] = w;
+                wsum += w;
             }
+        w_out[2 * D * C] = wsum + P.helm;  // diagonal of the row
     }
 }
 
@@ -2895,7 +2921,7 @@ template void refresh_eps<float>(mg_tree *, Fields<float> &);
 template <int D> static size_t resid_smem(int n, const Fields<double> &F) {
     const int C = cells_of<D>(n), GH = 2 * D * face_of<D>(n);
     return 2 * (sizeof(BlockDesc) + sizeof(LevelDesc) +
-                sizeof(double) * (2 * C + GH + (F.W ? 2 * D * C : (F.E ? C + GH : 0))));
+                sizeof(double) * (2 * C + GH + (F.W ? (2 * D + 1) * C : (F.E ? C + GH : 0))));
 }
 
 template <int D>
