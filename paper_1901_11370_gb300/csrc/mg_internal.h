@@ -43,7 +43,11 @@ struct LevelDesc {
     int nref;             // of which the first nref are covered by children
     long long bc_off[6];  // offset of the boundary plane of each face, -1: constant
     double inv_diag;      // 1 / (2 sum_d 1/h_d^2 + lambda): constant-coefficient Gauss-Seidel divisor
-    double pad_;
+    double diag;          // 2 sum_d 1/h_d^2 + lambda: the constant-coefficient row diagonal
+    double vol;           // cell volume (Cartesian)
+    // FP32 copies, so that FP32 kernels do no FP64 arithmetic or conversion
+    float inv_h2f[3];
+    float inv_diagf, h0f, hvf;  // 1/diag, h_0, 2 pi h_0 h_1 (cylindrical volume per unit r)
 };
 static_assert(sizeof(LevelDesc) % 16 == 0, "LevelDesc is copied with 16-byte bulk copies");
 
@@ -61,6 +65,7 @@ struct KParams {
     int homog;            // 1: boundary values read as zero
     int *status;          // device status word: 1 = a bounded wait gave up
     int uniform;          // 1: every block of a launch shares one level descriptor
+    float lo0f;           // lo[0] in FP32 (cylindrical radius in FP32 kernels)
 };
 
 // Coarsest level of one tree of a pool (one tree, or a batch of trees):
@@ -118,6 +123,8 @@ struct mg_tree {
     std::vector<std::vector<int>> groups;     // segments of each group, coarsest group first
     std::vector<mg::TreeCoarse> tcoarse;      // coarsest level of each tree
     mg::TreeCoarse *d_tcoarse = nullptr;
+    int2 *d_coarse_chunks = nullptr;          // (tree, first row) per chunk of the coarse apply
+    int n_coarse_chunks = 0;
     bool is_batch = false;
     int max_nc = 0;                           // largest coarsest-level system
     // batch only: leaf runs (pool cell, concatenated leaf index, count) for
@@ -175,6 +182,7 @@ template <class T> void refresh_eps(mg_tree *t, Fields<T> &F);
 template <class T> void tune_sweeps(mg_tree *t, Fields<T> &F);
 int sweep_variant(mg_tree *t, int prec, int level);
 constexpr int kNumSweepVariants = 10;
+constexpr int kCoarseRows = 8;  // rows of one tree per CTA of the coarse apply
 bool sweep_variant_ok(mg_tree *t, int prec, int level, int variant);
 void divergence(mg_tree *t, const double *B, double *out);
 void project(mg_tree *t, const double *B, double *Bout);

@@ -58,6 +58,17 @@ __device__ __forceinline__ T load(const T *__restrict__ X, const T *__restrict__
 template <class T> __device__ __forceinline__ T qdiv(T a, T b) { return a / b; }
 template <> __device__ __forceinline__ float qdiv<float>(float a, float b) { return __fdividef(a, b); }
 
+// Level and launch scalars in the kernel precision (FP32 copies are stored,
+// so FP32 kernels never convert from double).
+template <class T> __device__ __forceinline__ T lv_ih(const LevelDesc &L, int d) { return (T)L.inv_h2[d]; }
+template <> __device__ __forceinline__ float lv_ih<float>(const LevelDesc &L, int d) { return L.inv_h2f[d]; }
+template <class T> __device__ __forceinline__ T lv_idiag(const LevelDesc &L) { return (T)L.inv_diag; }
+template <> __device__ __forceinline__ float lv_idiag<float>(const LevelDesc &L) { return L.inv_diagf; }
+template <class T> __device__ __forceinline__ T lv_h0(const LevelDesc &L) { return (T)L.h[0]; }
+template <> __device__ __forceinline__ float lv_h0<float>(const LevelDesc &L) { return L.h0f; }
+template <class T> __device__ __forceinline__ T kp_lo0(const KParams &P) { return (T)P.lo[0]; }
+template <> __device__ __forceinline__ float kp_lo0<float>(const KParams &P) { return P.lo0f; }
+
 // 5/7-point row at a cell (Sec. 2.2): for every face the weight
 // w = eps_f * kappa_f / h_d^2 (eps_f harmonic mean of the two cells, kappa
 // r_f/r_i on r-faces of the cylindrical form), giving
@@ -73,7 +84,7 @@ __device__ __forceinline__ void stencil(const KParams &P, const LevelDesc &L, co
     if (E) ec = (A)E[b.cell_off + cidx<D>(n, i, j, k)];
     lap = 0; num = 0; den = 0;
     A ri = 0;
-    const A lo0 = (A)P.lo[0], h0 = (A)L.h[0];
+    const A lo0 = kp_lo0<A>(P), h0 = lv_h0<A>(L);
     if (P.geom == MG_CYL) ri = lo0 + ((A)(b.ijk[0] * n + i) + (A)0.5) * h0;
 #pragma unroll
     for (int d = 0; d < D; d++) {
@@ -82,7 +93,7 @@ __device__ __forceinline__ void stencil(const KParams &P, const LevelDesc &L, co
             const int o = s ? 1 : -1;
             const int ii = i + (d == 0 ? o : 0), jj = j + (d == 1 ? o : 0), kk = k + (d == 2 ? o : 0);
             const A xn = (A)load<T, D>(X, XG, b, ii, jj, kk);
-            A w = (A)L.inv_h2[d];
+            A w = lv_ih<A>(L, d);
             if (E) {
                 const A en = (A)load<T, D>(E, EG, b, ii, jj, kk);
                 w *= qdiv<A>((A)2 * ec * en, ec + en);
@@ -149,9 +160,9 @@ __device__ __forceinline__ double bc_value(const KParams &P, const LevelDesc &L,
 template <class T>
 __device__ __forceinline__ T phys_ghost(const KParams &P, const LevelDesc &L, int face, T xi, double a) {
     const int d = face >> 1, s = face & 1;
-    switch (P.bct[face]) {
-    case MG_BC_DIRICHLET: return (T)(2.0 * a) - xi;
-    case MG_BC_NEUMANN: return s ? xi + (T)(L.h[d] * a) : xi - (T)(L.h[d] * a);
+    switch (P.bct[face]) {  // homogeneous values (correction cycles): no FP64 work
+    case MG_BC_DIRICHLET: return P.homog ? -xi : (T)(2.0 * a) - xi;
+    case MG_BC_NEUMANN: return P.homog ? xi : (s ? xi + (T)(L.h[d] * a) : xi - (T)(L.h[d] * a));
     default: return xi;
     }
 }
@@ -272,8 +283,8 @@ __global__ void __launch_bounds__(kMaxThreads) k_sweep(KParams P, int first, Fie
         s_ngo[tid] = nb >= 0 ? P.B[nb].ghost_off : -1;
     }
     const LevelDesc &L = P.L[b.lev];
-    const T lo0 = (T)P.lo[0], h0 = (T)L.h[0];  // operator scalars in the kernel precision
-    const T ih0 = (T)L.inv_h2[0], ih1 = (T)L.inv_h2[1], ih2 = (T)L.inv_h2[2];
+    const T lo0 = kp_lo0<T>(P), h0 = lv_h0<T>(L);  // operator scalars in the kernel precision
+    const T ih0 = lv_ih<T>(L, 0), ih1 = lv_ih<T>(L, 1), ih2 = lv_ih<T>(L, 2);
     const int n = NT ? NT : b.n;
     const int C = cells_of<D>(n), Fc = face_of<D>(n), S = n + 2;
     const int PAD = D == 2 ? S * S : S * S * S;
@@ -356,7 +367,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_sweep(KParams P, int first, Fie
     // 2. red-black update of this colour (Sec. 2.2)
     const bool cyl = P.geom == MG_CYL;
     const T helm = (T)P.helm;
-    const T w0 = (T)L.inv_h2[0], w1 = (T)L.inv_h2[1], w2 = (T)L.inv_h2[2];
+    const T w0 = lv_ih<T>(L, 0), w1 = lv_ih<T>(L, 1), w2 = lv_ih<T>(L, 2);
     const T inv_den = (T)1 / ((T)2 * (w0 + w1 + (D == 3 ? w2 : (T)0)) + helm);
     auto update = [&](int i, int j, int k, T fc) {
         const int c0 = sid(i, j, k);
@@ -541,10 +552,10 @@ __global__ void __launch_bounds__(kMaxThreads, 5) k_sweep_tma(KParams P, int fir
         T *st = stage0 + (it & 1) * stage_elems;
         const BlockDesc &b = *reinterpret_cast<const BlockDesc *>(st);
         const LevelDesc &L = *reinterpret_cast<const LevelDesc *>(reinterpret_cast<const char *>(st) + sizeof(BlockDesc));
-        const T lo0 = (T)P.lo[0], h0 = (T)L.h[0];  // operator scalars in the kernel precision
-        const T ih0 = (T)L.inv_h2[0], ih1 = (T)L.inv_h2[1], ih2 = (T)L.inv_h2[2];
-        const T w0 = (T)L.inv_h2[0], w1 = (T)L.inv_h2[1], w2 = (T)L.inv_h2[2];
-        const T inv_den = (T)L.inv_diag;
+        const T lo0 = kp_lo0<T>(P), h0 = lv_h0<T>(L);  // operator scalars in the kernel precision
+        const T ih0 = lv_ih<T>(L, 0), ih1 = lv_ih<T>(L, 1), ih2 = lv_ih<T>(L, 2);
+        const T w0 = lv_ih<T>(L, 0), w1 = lv_ih<T>(L, 1), w2 = lv_ih<T>(L, 2);
+        const T inv_den = lv_idiag<T>(L);
         T *xs = st + DESC, *gs = xs + C, *fs = gs + GH, *es = fs + C, *egs = es + C;
         const int bi = b.ijk[0], bj = b.ijk[1], bk = b.ijk[2];
         const int par0 = (bi + bj + bk) * n;
@@ -699,10 +710,10 @@ __global__ void __launch_bounds__(32 * WARPS) k_sweep_warp(KParams P, int first,
         T *st = wst + (it & 1) * stage_elems;
         const BlockDesc &b = *reinterpret_cast<const BlockDesc *>(st);
         const LevelDesc &L = *reinterpret_cast<const LevelDesc *>(reinterpret_cast<const char *>(st) + sizeof(BlockDesc));
-        const T lo0 = (T)P.lo[0], h0 = (T)L.h[0];  // operator scalars in the kernel precision
-        const T ih0 = (T)L.inv_h2[0], ih1 = (T)L.inv_h2[1], ih2 = (T)L.inv_h2[2];
-        const T w0 = (T)L.inv_h2[0], w1 = (T)L.inv_h2[1], w2 = (T)L.inv_h2[2];
-        const T inv_den = (T)L.inv_diag;
+        const T lo0 = kp_lo0<T>(P), h0 = lv_h0<T>(L);  // operator scalars in the kernel precision
+        const T ih0 = lv_ih<T>(L, 0), ih1 = lv_ih<T>(L, 1), ih2 = lv_ih<T>(L, 2);
+        const T w0 = lv_ih<T>(L, 0), w1 = lv_ih<T>(L, 1), w2 = lv_ih<T>(L, 2);
+        const T inv_den = lv_idiag<T>(L);
         T *xs = st + DESC, *gs = xs + C, *fs = gs + GH, *es = fs + C, *egs = es + C;
         const int bi = b.ijk[0], bj = b.ijk[1], bk = b.ijk[2];
         const int par0 = (bi + bj + bk) * n;
@@ -909,8 +920,8 @@ __global__ void __launch_bounds__(32 * WARPS) k_sweep_rows(KParams P, int first,
         T *st = wst + (it % STAGES) * STAGE;
         const BlockDesc &b = *reinterpret_cast<const BlockDesc *>(st);
         const LevelDesc &L = *reinterpret_cast<const LevelDesc *>(reinterpret_cast<const char *>(st) + sizeof(BlockDesc));
-        const T w0 = (T)L.inv_h2[0], w1 = (T)L.inv_h2[1], w2 = (T)L.inv_h2[2];
-        const T inv_den = (T)L.inv_diag;
+        const T w0 = lv_ih<T>(L, 0), w1 = lv_ih<T>(L, 1), w2 = lv_ih<T>(L, 2);
+        const T inv_den = lv_idiag<T>(L);
         T *xs = st + DESC, *gs = xs + C, *fs = gs + GH;
         const int par0 = (b.ijk[0] + b.ijk[1] + b.ijk[2]) * n;
         T newrow[2][8];
@@ -1031,52 +1042,6 @@ __global__ void __launch_bounds__(kMaxThreads) k_restrict(KParams P, int first, 
     }
 }
 
-// Covered cells: f^H = R(r^h) + L^H v^H (eq. for the coarse right-hand side).
-template <class T, int D>
-__global__ void __launch_bounds__(kMaxThreads) k_fas_rhs(KParams P, int first, Fields<T> F) {
-    __shared__ BlockDesc sb;
-    stage_desc(P, first + blockIdx.x, sb);
-    const BlockDesc &b = sb;
-    const LevelDesc &L = P.L[b.lev];
-    const int n = b.n, C = cells_of<D>(n);
-    for (int c = threadIdx.x; c < C; c += blockDim.x) {
-        int i, j, k;
-        cell_of(c, n, D, i, j, k);
-        T lap, num, den, xc;
-        stencil<T, T, D>(P, L, b, F.X, F.XG, F.E, F.EG, i, j, k, lap, num, den, xc);
-        F.F[b.cell_off + c] += lap - (T)P.helm * xc;
-    }
-}
-
-// Coarse-grid correction (Sec. 2.4, Sec. 2.3): x^h += P(x^H - x^H_old), P the
-// nearest-neighbour linear interpolation, 2D (2 c0 + c_x + c_y)/4, 3D
-// (c0 + c_x + c_y + c_z)/4, neighbours on the fine cell's side (coarse
-// ghosts included).
-template <class T, int D>
-__global__ void __launch_bounds__(kMaxThreads) k_prolong(KParams P, int first, Fields<T> F) {
-    __shared__ BlockDesc sb;
-    stage_desc(P, first + blockIdx.x, sb);
-    const BlockDesc &b = sb;
-    const BlockDesc &p = P.B[b.parent];
-    const int n = b.n, C = cells_of<D>(n);
-    for (int c = threadIdx.x; c < C; c += blockDim.x) {
-        int i, j, k;
-        cell_of(c, n, D, i, j, k);
-        const int I[3] = {b.ijk[0] * n + i, b.ijk[1] * n + j, b.ijk[2] * n + k};
-        const int cc[3] = {b.poff[0] + i / 2, b.poff[1] + j / 2, D == 3 ? b.poff[2] + k / 2 : 0};
-        const T c0 = load<T, D>(F.X, F.XG, p, cc[0], cc[1], cc[2]) - load<T, D>(F.V, F.VG, p, cc[0], cc[1], cc[2]);
-        T nbs = 0;
-#pragma unroll
-        for (int d = 0; d < D; d++) {
-            int q[3] = {cc[0], cc[1], cc[2]};
-            q[d] += (I[d] & 1) ? 1 : -1;
-            nbs += load<T, D>(F.X, F.XG, p, q[0], q[1], q[2]) - load<T, D>(F.V, F.VG, p, q[0], q[1], q[2]);
-        }
-        const T val = D == 2 ? ((T)2 * c0 + nbs) / (T)4 : (c0 + nbs) / (T)4;
-        F.X[b.cell_off + c] += val;
-    }
-}
-
 // ------------------------------------------- transfers with ghost pushes ---
 // Push the ghosts that depend on the cells of one face of block b after those
 // cells changed: the same-level neighbour's slot opposite each cell, or the
@@ -1178,8 +1143,11 @@ __global__ void __launch_bounds__(kMaxThreads) k_fas_rhs_vold(KParams P, int fir
     for (int t = threadIdx.x; t < G; t += blockDim.x) F.VG[b.ghost_off + t] = F.XG[b.ghost_off + t];
 }
 
-// Coarse-grid correction fused with the fine-level ghost update: every cell
-// of block b changes, so after the correction all its face ghosts that
+// Coarse-grid correction (Sec. 2.4, 2.3): x^h += P(x^H - x^H_old), P the
+// nearest-neighbour linear interpolation -- 2D (2 c0 + c_x + c_y)/4, 3D
+// (c0 + c_x + c_y + c_z)/4 with the neighbours on the fine cell's side
+// (coarse ghosts included).  Fused with the fine-level ghost update: every
+// cell of block b changes, so after the correction all its face ghosts that
 // depend on its cells are pushed (the kernel reads only the coarser level's
 // fields and its own interior, never this level's ghosts).
 template <class T, int D>
@@ -1215,60 +1183,6 @@ __global__ void __launch_bounds__(kMaxThreads) k_prolong_push(KParams P, int fir
         const int face = t / Fc, u = t - face * Fc;
         push_face_cell<T, D>(P, L, b, face, u, face_cell<D>(n, face, u, false), F.X, F.XG, val);
     }
-}
-
-// Coarse-grid correction for 8- and 16-cell blocks: the parent's correction
-// c = x - x_old on the octant under block b and its face halo (coarse ghosts
-// where the halo leaves the parent) is staged once in shared memory; the
-// fine block moves with 16-byte vector loads and stores; then the fine
-// ghosts are pushed as in k_prolong_push (same arithmetic order).
-template <class T, int D, int NT>
-__global__ void __launch_bounds__(kMaxThreads) k_prolong_box(KParams P, int first, Fields<T> F) {
-    constexpr int n = NT, m = NT / 2, C = cells_of<D>(NT), B = m + 2, BOX = D == 2 ? B * B : B * B * B;
-    constexpr int VW = 16 / sizeof(T);
-    __shared__ BlockDesc sb, sp;
-    __shared__ __align__(16) T box[BOX];
-    __shared__ __align__(16) T xs[C];
-    stage_desc(P, first + blockIdx.x, sb);
-    const BlockDesc &b = sb;
-    stage_desc(P, b.parent, sp);
-    const BlockDesc &p = sp;
-    const LevelDesc &L = P.L[b.lev];
-    const int pn = p.n, tid = threadIdx.x, nth = blockDim.x;
-    auto bid = [](int a, int c, int e) { return D == 2 ? c * B + a : (e * B + c) * B + a; };
-    for (int q = tid; q < BOX; q += nth) {
-        const int a = q % B, c = (q / B) % B, e = D == 3 ? q / (B * B) : 1;
-        const int out = (a == 0 || a == B - 1) + (c == 0 || c == B - 1) + (D == 3 && (e == 0 || e == B - 1));
-        if (out > 1) continue;  // edge / corner of the box: never read
-        const int pi = b.poff[0] + a - 1, pj = b.poff[1] + c - 1, pk = D == 3 ? b.poff[2] + e - 1 : 0;
-        box[bid(a, c, e)] = load<T, D>(F.X, F.XG, p, pi, pj, pk) - load<T, D>(F.V, F.VG, p, pi, pj, pk);
-    }
-    using V = typename Vec16<T>::type;
-    const V *src = reinterpret_cast<const V *>(F.X + b.cell_off);
-    for (int v = tid; v < C / VW; v += nth) vscatter<T>(xs + v * VW, src[v]);
-    __syncthreads();
-    const int px = (b.ijk[0] * n) & 1, py = (b.ijk[1] * n) & 1, pz = (b.ijk[2] * n) & 1;
-    for (int c = tid; c < C; c += nth) {
-        const int i = c % n, j = (c / n) % n, k = D == 3 ? c / (n * n) : 0;
-        const int a = i / 2 + 1, cc = j / 2 + 1, e = D == 3 ? k / 2 + 1 : 1;
-        const int sx = ((px + i) & 1) ? 1 : -1, sy = ((py + j) & 1) ? 1 : -1, sz = ((pz + k) & 1) ? 1 : -1;
-        const T v0 = box[bid(a, cc, e)];
-        T nbs = box[bid(a + sx, cc, e)];
-        nbs += box[bid(a, cc + sy, e)];
-        if (D == 3) nbs += box[bid(a, cc, e + sz)];
-        const T val = D == 2 ? ((T)2 * v0 + nbs) / (T)4 : (v0 + nbs) / (T)4;
-        xs[c] = xs[c] + val;
-    }
-    __syncthreads();
-    V *dst = reinterpret_cast<V *>(F.X + b.cell_off);
-    for (int v = tid; v < C / VW; v += nth) dst[v] = vgather<T>(xs + v * VW);
-    constexpr int Fc = face_of<D>(NT);
-    auto val = [&](I3 q) { return xs[cidx<D>(n, q.x, q.y, q.z)]; };
-    for (int t = tid; t < 2 * D * Fc; t += nth) {
-        const int face = t / Fc, u = t - face * Fc;
-        push_face_cell<T, D>(P, L, b, face, u, face_cell<D>(n, face, u, false), F.X, F.XG, val);
-    }
-    (void)pn;
 }
 
 // Ghost fill by pushing (8- and 16-cell blocks), persistent and
@@ -1404,8 +1318,8 @@ __global__ void __launch_bounds__(kMaxThreads) k_fas_tma(KParams P, int first, i
         T *st = stage0 + (it & 1) * stage_elems;
         const BlockDesc &b = *reinterpret_cast<const BlockDesc *>(st);
         const LevelDesc &L = *reinterpret_cast<const LevelDesc *>(reinterpret_cast<const char *>(st) + sizeof(BlockDesc));
-        const T lo0 = (T)P.lo[0], h0 = (T)L.h[0];  // operator scalars in the kernel precision
-        const T ih0 = (T)L.inv_h2[0], ih1 = (T)L.inv_h2[1], ih2 = (T)L.inv_h2[2];
+        const T lo0 = kp_lo0<T>(P), h0 = lv_h0<T>(L);  // operator scalars in the kernel precision
+        const T ih0 = lv_ih<T>(L, 0), ih1 = lv_ih<T>(L, 1), ih2 = lv_ih<T>(L, 2);
         const T *xs = st + DESC, *gs = xs + C, *es = gs + C + GH, *egs = es + C;
         T *fs = st + DESC + C + GH;
         auto nbv = [&](const T *xi, const T *gi, int i, int j, int k, int d, int s) -> T {
@@ -1650,8 +1564,8 @@ __global__ void __launch_bounds__(kMaxThreads, 4) k_restrict_tma(KParams P, int 
         const BlockDesc &b = *reinterpret_cast<const BlockDesc *>(st);
         const BlockDesc &p = *reinterpret_cast<const BlockDesc *>(st + DESC);
         const LevelDesc &L = *reinterpret_cast<const LevelDesc *>(reinterpret_cast<const char *>(st) + sizeof(BlockDesc));
-        const T lo0 = (T)P.lo[0], h0 = (T)L.h[0];  // operator scalars in the kernel precision
-        const T ih0 = (T)L.inv_h2[0], ih1 = (T)L.inv_h2[1], ih2 = (T)L.inv_h2[2];
+        const T lo0 = kp_lo0<T>(P), h0 = lv_h0<T>(L);  // operator scalars in the kernel precision
+        const T ih0 = lv_ih<T>(L, 0), ih1 = lv_ih<T>(L, 1), ih2 = lv_ih<T>(L, 2);
         const LevelDesc &PL = *reinterpret_cast<const LevelDesc *>(reinterpret_cast<const char *>(st + DESC) + sizeof(BlockDesc));
         const T *xs = st + 2 * DESC, *gs = xs + C, *fs = gs + GH, *es = fs + C, *egs = es + C;
         auto nbv = [&](const T *xi, const T *gi, int i, int j, int k, int d, int s) -> T {
@@ -1903,7 +1817,7 @@ __global__ void __launch_bounds__(kMaxThreads, 3) k_resid_tma(KParams P, int fir
         const BlockDesc &b = *reinterpret_cast<const BlockDesc *>(st);
         const LevelDesc &L = *reinterpret_cast<const LevelDesc *>(reinterpret_cast<const char *>(st) + sizeof(BlockDesc));
         const double w0 = L.inv_h2[0], w1 = L.inv_h2[1], w2 = L.inv_h2[2];
-        double vol = L.h[0] * L.h[1] * (D == 3 ? L.h[2] : 1.0);
+        const double vol = L.vol;
         const T *xs = st + DESC, *gs = xs + C, *fs = gs + GH, *es = fs + C, *egs = es + C;
         auto nbv = [&](const T *xi, const T *gi, int i, int j, int k, int d, int s) -> T {
             const int o = s ? 1 : -1;
@@ -1924,10 +1838,10 @@ __global__ void __launch_bounds__(kMaxThreads, 3) k_resid_tma(KParams P, int fir
         // A x as (sum_f w_f x_f) - (sum_f w_f + lambda) x_c: FP64 operations
         // are GB300's scarcest resource here; the rounding stays at
         // eps * sum_f w_f |x|, far below any tolerance the solves use
-        const double dg = 2.0 * (w0 + w1 + (D == 3 ? w2 : 0.0)) + P.helm;
+        const double dg = L.diag;
         double bs2 = 0;
         float bs2f = 0.f, s2f = 0.f, svf = 0.f;  // solve-loop norms (MX off) in FP32
-        const float lo0f = (float)P.lo[0], h0f = (float)L.h[0], hvf = (float)(2.0 * M_PI * L.h[0] * L.h[1]);
+        const float lo0f = P.lo0f, h0f = L.h0f, hvf = L.hvf;
         for (int c = tid; c < C; c += nth) {
             const int i = c % n, j = (c / n) % n, k = D == 3 ? c / (n * n) : 0;
             const double xc = xs[c];
@@ -2089,51 +2003,6 @@ __global__ void __launch_bounds__(1024) k_reduce3(const double *__restrict__ par
     }
 }
 
-// ------------------------------------------------------ coarsest level --
-// Exact coarsest solve: r = f - L x in FP64 for every cell of level 0 (one
-// CTA), with -sum V x appended for the zero-mean constraint; then
-// dx = Minv r, one warp per row.
-template <class T, int D>
-__global__ void __launch_bounds__(1024) k_coarse_resid(KParams P, int nb, Fields<T> F, double *cvec, int singular) {
-    const BlockDesc b0 = P.B[0];
-    const LevelDesc &L = P.L[0];
-    const int n = b0.n, C = cells_of<D>(n), nc = nb * C;
-    double wx = 0;
-    for (int row = threadIdx.x; row < nc; row += blockDim.x) {
-        const BlockDesc &b = P.B[row / C];
-        int i, j, k;
-        cell_of(row % C, n, D, i, j, k);
-        double lap, num, den, xc;
-        stencil<double, T, D>(P, L, b, F.X, F.XG, F.E, F.EG, i, j, k, lap, num, den, xc);
-        cvec[row] = (double)F.F[b.cell_off + row % C] - (lap - P.helm * xc);
-        double V = 1.0;
-        for (int d = 0; d < D; d++) V *= L.h[d];
-        if (P.geom == MG_CYL) V = 2.0 * M_PI * (P.lo[0] + (b.ijk[0] * n + i + 0.5) * L.h[0]) * L.h[0] * L.h[1];
-        wx += V * xc;
-    }
-    if (!singular) return;
-    for (int o = 16; o > 0; o >>= 1) wx += __shfl_down_sync(0xffffffffu, wx, o);
-    __shared__ double sh[32];
-    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = wx;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double s = 0;
-        for (int e = 0; e < (int)((blockDim.x + 31) >> 5); e++) s += sh[e];
-        cvec[nc] = -s;
-    }
-}
-
-template <class T>
-__global__ void k_coarse_apply(const double *__restrict__ minv, int ns, int nc, const double *__restrict__ cvec,
-                               T *__restrict__ X) {
-    const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
-    if (row >= nc) return;
-    double s = 0;
-    for (int c = lane; c < ns; c += 32) s += minv[(long long)row * ns + c] * cvec[c];
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-    if (lane == 0) X[row] = (T)((double)X[row] + s);  // level-0 cells come first in the pool
-}
-
 // Exact coarsest solves of several trees at once (one CTA per tree): r = f -
 // L x in FP64 for every cell of the tree's coarsest level, with -sum V x
 // appended for the zero-mean constraint; then dx = Minv r, one warp per row.
@@ -2171,12 +2040,16 @@ __global__ void __launch_bounds__(1024) k_coarse_resid_b(KParams P, const TreeCo
     }
 }
 
+// One CTA per chunk of kCoarseRows rows of one tree (chunk list built on
+// the host), one warp per row.
 template <class T>
-__global__ void k_coarse_apply_b(const TreeCoarse *__restrict__ TC, int top, int strict,
-                                 const double *__restrict__ minv, const double *__restrict__ cvec, T *__restrict__ X) {
-    const TreeCoarse tc = TC[blockIdx.y];
+__global__ void k_coarse_apply_b(const TreeCoarse *__restrict__ TC, const int2 *__restrict__ chunks, int top,
+                                 int strict, const double *__restrict__ minv, const double *__restrict__ cvec,
+                                 T *__restrict__ X) {
+    const int2 ch = chunks[blockIdx.x];  // (tree, first row)
+    const TreeCoarse tc = TC[ch.x];
     if (strict ? tc.group >= top : tc.group > top) return;
-    const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    const int row = ch.y + (threadIdx.x >> 5), lane = threadIdx.x & 31;
     if (row >= tc.nc) return;
     double sacc = 0;
     const double *mr = minv + tc.minv_off + (long long)row * tc.ns;
@@ -2509,6 +2382,7 @@ KParams kparams(mg_tree *t, int homog) {
     P.homog = homog;
     P.status = t->d_status;
     P.uniform = t->is_batch ? 0 : 1;
+    P.lo0f = (float)t->lo[0];
     return P;
 }
 
@@ -2779,10 +2653,6 @@ template <class T, int D> struct Launch {
             ghost(t, P, l, F.X, F.XG, 0);
             return;
         }
-        if (L.n == 8 && L.parent_same_n) {
-            k_prolong_box<T, D, 8><<<L.nb, threads_for(cells_of<D>(8) / 2), 0, t->stream>>>(P, L.first, F);
-            return;
-        }
         const size_t sm = sizeof(T) * cells_of<D>(L.n);
         set_smem(k_prolong_push<T, D>, sm);
         k_prolong_push<T, D><<<L.nb, threads_for(cells_of<D>(L.n)), sm, t->stream>>>(P, L.first, F);
@@ -2793,10 +2663,9 @@ template <class T, int D> struct Launch {
         const int ntr = (int)t->tcoarse.size();
         ++t->launches;
         k_coarse_resid_b<T, D><<<ntr, 1024, 0, t->stream>>>(P, t->d_tcoarse, top, strict, F, t->d_cvec);
-        const int rows_per_cta = 8;
         ++t->launches;
-        k_coarse_apply_b<T><<<dim3((t->max_nc + rows_per_cta - 1) / rows_per_cta, ntr), 32 * rows_per_cta, 0,
-                              t->stream>>>(t->d_tcoarse, top, strict, t->d_minv, t->d_cvec, F.X);
+        k_coarse_apply_b<T><<<t->n_coarse_chunks, 32 * kCoarseRows, 0, t->stream>>>(
+            t->d_tcoarse, t->d_coarse_chunks, top, strict, t->d_minv, t->d_cvec, F.X);
         for (size_t l = 0; l < t->lev.size(); l++)
             if (t->lev[l].coarsest && t->lev[l].group <= top) ghost(t, P, (int)l, F.X, F.XG, 0);
     }

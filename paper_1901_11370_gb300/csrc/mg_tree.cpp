@@ -387,8 +387,13 @@ static int upload_bc(mg_tree *t) {
         {
             double sw = 0;
             for (int e = 0; e < t->dim; e++) sw += d.inv_h2[e];
-            d.inv_diag = 1.0 / (2.0 * sw + t->helm);
-            d.pad_ = 0;
+            d.diag = 2.0 * sw + t->helm;
+            d.inv_diag = 1.0 / d.diag;
+            d.vol = L.h[0] * L.h[1] * (t->dim == 3 ? L.h[2] : 1.0);
+            for (int e = 0; e < 3; e++) d.inv_h2f[e] = (float)d.inv_h2[e];
+            d.inv_diagf = (float)d.inv_diag;
+            d.h0f = (float)L.h[0];
+            d.hvf = (float)(2.0 * M_PI * L.h[0] * L.h[1]);
         }
         for (int f = 0; f < 6; f++) {
             d.bc_off[f] = -1;
@@ -571,6 +576,14 @@ extern "C" int mg_tree_finalize(mg_tree *t, void *stream) {
     if ((rc = dalloc(&t->d_cvec, t->cvec_total))) return rc;
     CK(cudaMalloc((void **)&t->d_tcoarse, sizeof(TreeCoarse) * t->tcoarse.size()));
     CK(cudaMemcpy(t->d_tcoarse, t->tcoarse.data(), sizeof(TreeCoarse) * t->tcoarse.size(), cudaMemcpyHostToDevice));
+    {  // work list of the coarse apply: kCoarseRows rows of one tree per CTA
+        std::vector<int2> ch;
+        for (size_t i = 0; i < t->tcoarse.size(); i++)
+            for (int r = 0; r < t->tcoarse[i].nc; r += kCoarseRows) ch.push_back(make_int2((int)i, r));
+        t->n_coarse_chunks = (int)ch.size();
+        CK(cudaMalloc((void **)&t->d_coarse_chunks, sizeof(int2) * std::max<size_t>(1, ch.size())));
+        CK(cudaMemcpy(t->d_coarse_chunks, ch.data(), sizeof(int2) * ch.size(), cudaMemcpyHostToDevice));
+    }
     CK(cudaMallocHost((void **)&t->h_red, 3 * sizeof(double)));
     CK(cudaStreamCreateWithFlags(&t->cap_stream, cudaStreamNonBlocking));
     t->finalized = true;
@@ -977,7 +990,7 @@ extern "C" int mg_tree_destroy(mg_tree *t) {
         free_fields(t->adj, false);
         free_fields(t->f32, true);
         cudaFree(t->d_blocks); cudaFree(t->d_levels); cudaFree(t->d_bcplanes);
-        cudaFree(t->d_r64); cudaFree(t->d_wface); cudaFree(t->d_minv); cudaFree(t->d_cvec); cudaFree(t->d_partials); cudaFree(t->d_red); cudaFree(t->d_status); cudaFree(t->d_tcoarse);
+        cudaFree(t->d_r64); cudaFree(t->d_wface); cudaFree(t->d_minv); cudaFree(t->d_cvec); cudaFree(t->d_partials); cudaFree(t->d_red); cudaFree(t->d_status); cudaFree(t->d_tcoarse); cudaFree(t->d_coarse_chunks);
         cudaFreeHost(t->h_red);
         cudaFree(t->d_runs); cudaFree(t->d_slot_off); cudaFree(t->d_slots); cudaFree(t->d_tree3);
         cudaFreeHost(t->h_tree3);
