@@ -46,6 +46,8 @@ enum {
     MG_ERR_NOT_CONVERGED = -4,  /* mg_solve hit max_cycles */
     MG_ERR_NAN = -5,            /* a residual norm is not finite */
     MG_ERR_TIMEOUT = -6,        /* a bounded wait inside a kernel expired */
+    MG_ERR_INCOMPATIBLE_RHS = -7, /* singular problem whose residual mean cannot vanish */
+    MG_ERR_STATE = -8,          /* call out of order (before finalize, refine after build, ...) */
     MG_ERR_UNSUPPORTED = -9     /* valid request outside what is built */
 };
 enum { MG_CART = 0, MG_CYL = 1 };
@@ -138,7 +140,11 @@ int mg_residual_norm(mg_tree *t, double *l2, double *linf, double *dev_r);
 
 /*
  * mg_solve -- from the current phi, cycle until the composite residual L2
- * norm is at most rel_tol times its value for phi = 0, or max_cycles.
+ * norm is at most rel_tol times its value at the starting phi, or
+ * max_cycles.  On a singular problem (no Dirichlet face, lambda = 0) the
+ * volume-weighted mean of the residual cannot change; when it exceeds
+ * rel_tol times the starting residual norm the call returns
+ * MG_ERR_INCOMPATIBLE_RHS before cycling (project f first).
  * MG_FP64: one FMG cycle if fmg_first, then V-cycles.  MG_FP32_DC: each
  * outer step computes r = f - A phi in FP64, runs p->inner_cycles FP32
  * V-cycles on A e = r (homogeneous boundary values, coarsest solve in FP64)

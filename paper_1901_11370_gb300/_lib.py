@@ -12,7 +12,8 @@ LIB_PATH = os.path.join(HERE, "libmg_gb300.so")
 
 MG_OK = 0
 ERRORS = {-1: "MG_ERR_ARG", -2: "MG_ERR_BALANCE", -3: "MG_ERR_CUDA", -4: "MG_ERR_NOT_CONVERGED",
-          -5: "MG_ERR_NAN", -6: "MG_ERR_TIMEOUT", -9: "MG_ERR_UNSUPPORTED"}
+          -5: "MG_ERR_NAN", -6: "MG_ERR_TIMEOUT", -7: "MG_ERR_INCOMPATIBLE_RHS", -8: "MG_ERR_STATE",
+          -9: "MG_ERR_UNSUPPORTED"}
 
 # every entry point declared in include/mg.h
 EXPORTS = ["mg_tree_create", "mg_tree_refine", "mg_tree_num_levels", "mg_tree_level_info",

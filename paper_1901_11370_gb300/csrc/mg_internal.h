@@ -194,6 +194,8 @@ void residual_norm(mg_tree *t, Fields<double> &F, int homog, double *out3, doubl
 void residual_enqueue(mg_tree *t, Fields<double> &F, int homog, double *r64_leaf, float *f32_cells,
                       bool want_max = false);
 void residual_wait(mg_tree *t, double *out3);
+// volume-weighted mean of a leaf-order FP64 field (synchronises the stream)
+double leaf_mean(mg_tree *t, const double *rleaf);
 void add_e_to_phi(mg_tree *t, const float *e, double *phi);
 void copy_eps_to_f32(mg_tree *t);
 // FP64 face coefficients of every cell into t->d_wface (eps ghosts current)

@@ -2899,6 +2899,64 @@ void residual_wait(mg_tree *t, double *out3) {
     out3[2] = t->h_red[2];
 }
 
+// Volume-weighted sum of a leaf-order field (one CTA per leaf block):
+// partials (sum V r, sum V, 0).  For singular problems sum V r of the
+// residual does not depend on phi (the operator maps into zero weighted mean).
+template <int D>
+__global__ void __launch_bounds__(256) k_leaf_vsum(KParams P, int first, const double *__restrict__ rleaf,
+                                                   long long leaf_base, double *__restrict__ partials) {
+    const BlockDesc &b = P.B[first + blockIdx.x];
+    const LevelDesc &L = P.L[b.lev];
+    const int n = b.n, C = cells_of<D>(n);
+    double a = 0, v = 0;
+    for (int c = threadIdx.x; c < C; c += blockDim.x) {
+        double V = L.vol;
+        if (P.geom == MG_CYL) V = 2.0 * M_PI * (P.lo[0] + (b.ijk[0] * n + c % n + 0.5) * L.h[0]) * L.h[0] * L.h[1];
+        a = fma(V, rleaf[leaf_base + (long long)blockIdx.x * C + c], a);
+        v += V;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, o);
+        v += __shfl_down_sync(0xffffffffu, v, o);
+    }
+    __shared__ double sh[2][8];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) { sh[0][w] = a; sh[1][w] = v; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double x = 0, y = 0;
+        for (int e = 0; e < (int)(blockDim.x >> 5); e++) { x += sh[0][e]; y += sh[1][e]; }
+        partials[3 * blockIdx.x] = x;
+        partials[3 * blockIdx.x + 1] = y;
+        partials[3 * blockIdx.x + 2] = 0;
+    }
+}
+
+// sum V r / sum V over the leaves of r (leaf order); synchronises the stream
+double leaf_mean(mg_tree *t, const double *rleaf) {
+    const KParams P = kparams(t, 0);
+    int slot = 0;
+    long long leaf_base = 0;
+    for (const LevelHost &L : t->lev) {
+        const int nleaf = L.nb - L.nref;
+        if (nleaf <= 0) continue;
+        ++t->launches;
+        if (t->dim == 2)
+            k_leaf_vsum<2><<<nleaf, 256, 0, t->stream>>>(P, L.first + L.nref, rleaf, leaf_base, t->d_partials + 3LL * slot);
+        else
+            k_leaf_vsum<3><<<nleaf, 256, 0, t->stream>>>(P, L.first + L.nref, rleaf, leaf_base, t->d_partials + 3LL * slot);
+        slot += nleaf;
+        leaf_base += (long long)nleaf * (t->dim == 2 ? L.n * L.n : L.n * L.n * L.n);
+    }
+    ++t->launches;
+    k_reduce3<<<1, 1024, 0, t->stream>>>(t->d_partials, slot, t->d_red);
+    double o[3];
+    cudaMemcpyAsync(t->h_red, t->d_red, 3 * sizeof(double), cudaMemcpyDeviceToHost, t->stream);
+    cudaStreamSynchronize(t->stream);
+    for (int e = 0; e < 3; e++) o[e] = t->h_red[e];
+    return o[1] > 0 ? o[0] / o[1] : 0.0;
+}
+
 void residual_norm(mg_tree *t, Fields<double> &F, int homog, double *out3, double *r64_leaf, float *f32_cells) {
     residual_enqueue(t, F, homog, r64_leaf, f32_cells, true);
     residual_wait(t, out3);

@@ -84,7 +84,7 @@ extern "C" int mg_tree_create(int dim, int block_size, int geometry, const mg_bc
 
 extern "C" int mg_tree_refine(mg_tree *t, int n, const int32_t *e) {
     if (!t || n < 0 || (n > 0 && !e)) return fail(MG_ERR_ARG, "bad refine arguments");
-    if (t->built) return fail(MG_ERR_ARG, "refine after the mesh was built");
+    if (t->built) return fail(MG_ERR_STATE, "refine after the mesh was built");
     t->refine.insert(t->refine.end(), e, e + 4 * (size_t)n);
     return MG_OK;
 }
@@ -555,7 +555,7 @@ static void annotate_segments(mg_tree *t) {
 
 extern "C" int mg_tree_finalize(mg_tree *t, void *stream) {
     if (!t) return fail(MG_ERR_ARG, "null tree");
-    if (t->finalized) return fail(MG_ERR_ARG, "already finalized");
+    if (t->finalized) return fail(MG_ERR_STATE, "already finalized");
     int rc = build(t);
     if (rc) return rc;
     annotate_segments(t);
@@ -601,7 +601,8 @@ extern "C" int mg_tree_finalize(mg_tree *t, void *stream) {
 
 #define NEED_FINAL(t)                                                            \
     do {                                                                         \
-        if (!(t) || !(t)->finalized) return fail(MG_ERR_ARG, "tree not finalized"); \
+        if (!(t)) return fail(MG_ERR_ARG, "null tree");                           \
+        if (!(t)->finalized) return fail(MG_ERR_STATE, "tree not finalized");     \
     } while (0)
 
 // device status word: a bounded wait inside a kernel gave up (reported once)
@@ -813,6 +814,19 @@ extern "C" int mg_solve(mg_tree *t, double rel_tol, int max_cycles, int fmg_firs
     int cycles = 0, rc;
     double rel = 1.0;
     const std::string sfx = ":" + std::to_string(q.n_down) + ":" + std::to_string(q.n_up);
+    if (t->singular && !t->is_batch) {
+        // no Dirichlet face and lambda = 0: the weighted mean of the residual
+        // does not change with phi, so its size bounds what cycles can reach
+        if ((rc = dalloc(&t->d_r64, t->nleaf_cells))) return rc;
+        residual_norm(t, t->f64, 0, o, t->d_r64, nullptr);
+        const double l2 = std::sqrt(o[0] / o[1]), mean = std::fabs(leaf_mean(t, t->d_r64));
+        if ((rc = check_cuda("compatibility")) != MG_OK) return rc;
+        if (l2 > 0 && mean > rel_tol * l2)
+            return fail(MG_ERR_INCOMPATIBLE_RHS,
+                        "the residual's volume-weighted mean (" + std::to_string(mean / l2) +
+                            " of its norm) cannot be removed on a problem without Dirichlet faces: "
+                            "project f to a compatible right-hand side");
+    }
     // each step is one graph: the cycle(s) and the FP64 composite residual,
     // whose norms arrive in pinned host memory; the host only waits
     if (q.precision == MG_FP64) {

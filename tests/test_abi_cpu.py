@@ -94,3 +94,16 @@ def test_python_layer_has_no_fallback():
             assert "oracle" not in open(os.path.join(ROOT, "paper_1901_11370_gb300", f)).read().split("import")[0] or True
             body = open(os.path.join(ROOT, "paper_1901_11370_gb300", f)).read()
             assert "from oracle" not in body and "import oracle" not in body, f
+
+
+def test_calls_out_of_order_return_state_error(lib):
+    """Lifecycle errors (MG_ERR_STATE): refinement after the mesh was built,
+    field calls before finalize (checked before any device pointer is used)."""
+    import ctypes as C
+    import paper_1901_11370_gb300 as mg
+    t = mg.Tree(2, 8, 0, (0,) * 6, (0,) * 6, (32, 32), (0, 0), (1, 1), finalize=False)
+    t.levels()  # builds the level tables
+    ref = np.array([[0, 0, 0, 0]], np.int32)
+    assert t.L.mg_tree_refine(t._h, 1, ref.ctypes.data_as(C.c_void_p)) == -8
+    assert t.L.mg_set_rhs(t._h, None) == -8
+    assert t.L.mg_vcycle(t._h, 1, None) == -8

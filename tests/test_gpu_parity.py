@@ -266,3 +266,23 @@ def test_cleaning_autograd_matches_oracle(mg):
     grad_o, _, _ = o.clean(Bn_o - Bt, rel_tol=1e-13, max_cycles=80)
     assert rel_diff(Bn.detach().cpu().numpy(), Bn_o) < 1e-9
     assert rel_diff(Bg.grad.cpu().numpy(), grad_o) < 1e-9
+
+
+def test_incompatible_rhs_is_reported(mg):
+    """A singular problem (periodic and homogeneous Neumann faces) with a
+    right-hand side of nonzero mean cannot reach a small residual: mg_solve
+    says so (MG_ERR_INCOMPATIBLE_RHS) instead of cycling; the projected
+    right-hand side solves."""
+    import torch
+    p = W.cfg3_varcoef3d(n=16, N=8, seed=4, contrast=5.0)
+    t = mg.Tree.from_problem(p)
+    f = torch.from_numpy(W.leaf_field(p, "rhs")).cuda() + 0.5
+    t.set_rhs(f)
+    with pytest.raises(mg.MGError) as e:
+        t.solve(1e-10, 20)
+    assert e.value.code == -7
+    vol = t.leaf_volumes()
+    t.set_rhs(f - torch.dot(vol, f) / vol.sum())
+    t.set_phi(torch.zeros_like(f))
+    cyc, rel = t.solve(1e-10, 40)
+    assert rel <= 1e-10
