@@ -486,7 +486,7 @@ __device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier
 static constexpr uint32_t kWaitLimit = 1u << 20;
 
 template <class T, int D, int NT>
-__global__ void __launch_bounds__(kMaxThreads, 5) k_sweep_tma(KParams P, int first, int nblocks, Fields<T> F,
+__global__ void __launch_bounds__(kMaxThreads, (D == 3 && NT == 16) ? 1 : 5) k_sweep_tma(KParams P, int first, int nblocks, Fields<T> F,
                                                            int colour) {
     constexpr int n = NT, C = cells_of<D>(NT), FC = face_of<D>(NT), GH = 2 * D * FC;
     constexpr int NCOL = C / 2, CPT = (NCOL + kMaxThreads - 1) / kMaxThreads;
@@ -495,9 +495,9 @@ __global__ void __launch_bounds__(kMaxThreads, 5) k_sweep_tma(KParams P, int fir
     __shared__ __align__(8) uint64_t bars[2];
     __shared__ __align__(16) LevelDesc sL;
     __shared__ int s_abort;
-    const bool var = F.E != nullptr;
-    // per stage: descriptor, x[C], ghosts[GH], f[C] (, eps[C], eps ghosts[GH])
-    const int stage_elems = DESC + 2 * C + GH + (var ? C + GH : 0);
+    const bool var = F.E != nullptr, wc = F.W != nullptr;  // wc: precomputed face coefficients (FP64)
+    // per stage: descriptor, x[C], ghosts[GH], f[C] (, eps[C], eps ghosts[GH] | coefficients[(2D+1) C])
+    const int stage_elems = DESC + 2 * C + GH + (wc ? (2 * D + 1) * C : (var ? C + GH : 0));
     T *stage0 = reinterpret_cast<T *>(smem_raw);
     const int tid = threadIdx.x, nth = blockDim.x;
     const uint32_t tx_bytes = (uint32_t)(sizeof(T) * stage_elems);
@@ -521,7 +521,9 @@ __global__ void __launch_bounds__(kMaxThreads, 5) k_sweep_tma(KParams P, int fir
         bulk_g2s(st + DESC, F.X + co, sizeof(T) * C, bar);
         bulk_g2s(st + DESC + C, F.XG + go, sizeof(T) * GH, bar);
         bulk_g2s(st + DESC + C + GH, F.F + co, sizeof(T) * C, bar);
-        if (var) {
+        if (wc) {
+            bulk_g2s(st + DESC + 2 * C + GH, F.W + co * (2 * D + 1), sizeof(T) * (2 * D + 1) * C, bar);
+        } else if (var) {
             bulk_g2s(st + DESC + 2 * C + GH, F.E + co, sizeof(T) * C, bar);
             bulk_g2s(st + DESC + 3 * C + GH, F.EG + go, sizeof(T) * GH, bar);
         }
@@ -590,6 +592,12 @@ __global__ void __launch_bounds__(kMaxThreads, 5) k_sweep_tma(KParams P, int fir
                         w1 * (nbv(xs, gs, i, j, k, 1, 0) + nbv(xs, gs, i, j, k, 1, 1));
                 if (D == 3) num += w2 * (nbv(xs, gs, i, j, k, 2, 0) + nbv(xs, gs, i, j, k, 2, 1));
                 xnew = (num - fs[c]) * inv_den;
+            } else if (wc) {  // same terms and order as below, coefficients read
+                const T *ws = es + c;
+                T num = ws[0] * nbv(xs, gs, i, j, k, 0, 0);
+#pragma unroll
+                for (int f = 1; f < 2 * D; f++) num += ws[f * C] * nbv(xs, gs, i, j, k, f >> 1, f & 1);
+                xnew = qdiv<T>(num - fs[c], ws[2 * D * C]);
             } else {
                 const T ec = var ? es[c] : (T)1;
                 T num = 0, den = 0, ri = 0;
@@ -1268,8 +1276,8 @@ __global__ void __launch_bounds__(kMaxThreads) k_fas_tma(KParams P, int first, i
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bars[2];
     __shared__ int s_abort;
-    const bool var = F.E != nullptr;
-    const int stage_elems = DESC + 2 * C + GH + (var ? C + GH : 0);
+    const bool var = F.E != nullptr, wc = F.W != nullptr;
+    const int stage_elems = DESC + 2 * C + GH + (wc ? 2 * D * C : (var ? C + GH : 0));
     T *stage0 = reinterpret_cast<T *>(smem_raw);
     const int tid = threadIdx.x, nth = blockDim.x;
     const uint32_t tx_bytes = (uint32_t)(sizeof(T) * stage_elems);
@@ -1291,7 +1299,9 @@ __global__ void __launch_bounds__(kMaxThreads) k_fas_tma(KParams P, int first, i
         bulk_g2s(st + DESC, F.X + co, sizeof(T) * C, bar);
         bulk_g2s(st + DESC + C, F.XG + go, sizeof(T) * GH, bar);
         bulk_g2s(st + DESC + C + GH, F.F + co, sizeof(T) * C, bar);
-        if (var) {
+        if (wc) {
+            bulk_g2s(st + DESC + 2 * C + GH, F.W + co * (2 * D + 1), sizeof(T) * 2 * D * C, bar);
+        } else if (var) {
             bulk_g2s(st + DESC + 2 * C + GH, F.E + co, sizeof(T) * C, bar);
             bulk_g2s(st + DESC + 3 * C + GH, F.EG + go, sizeof(T) * GH, bar);
         }
@@ -1341,6 +1351,13 @@ __global__ void __launch_bounds__(kMaxThreads) k_fas_tma(KParams P, int first, i
         for (int c = tid; c < C; c += nth) {
             const int i = c % n, j = (c / n) % n, k = D == 3 ? c / (n * n) : 0;
             const T xc = xs[c];
+            if (wc) {  // same terms and order as below, coefficients read
+                T lap = 0;
+#pragma unroll
+                for (int f = 0; f < 2 * D; f++) lap += es[f * C + c] * (nbv(xs, gs, i, j, k, f >> 1, f & 1) - xc);
+                fs[c] += lap - (T)P.helm * xc;
+                continue;
+            }
             const T ec = var ? es[c] : (T)1;
             T lap = 0, ri = 0;
             if (cyl) ri = lo0 + ((T)(b.ijk[0] * n + i) + (T)0.5) * h0;
@@ -1507,8 +1524,8 @@ __global__ void __launch_bounds__(kMaxThreads, 4) k_restrict_tma(KParams P, int 
     __shared__ __align__(16) LevelDesc sL, sPL;
     __shared__ int s_abort;
     __shared__ __align__(16) T rs[C];
-    const bool var = F.E != nullptr;
-    const int stage_elems = 2 * DESC + 2 * C + GH + (var ? C + GH : 0);
+    const bool var = F.E != nullptr, wc = F.W != nullptr;
+    const int stage_elems = 2 * DESC + 2 * C + GH + (wc ? 2 * D * C : (var ? C + GH : 0));
     T *stage0 = reinterpret_cast<T *>(smem_raw);
     const int tid = threadIdx.x, nth = blockDim.x;
     const uint32_t tx_bytes = (uint32_t)(sizeof(T) * stage_elems);
@@ -1538,7 +1555,9 @@ __global__ void __launch_bounds__(kMaxThreads, 4) k_restrict_tma(KParams P, int 
         bulk_g2s(st + 2 * DESC, F.X + co, sizeof(T) * C, bar);
         bulk_g2s(st + 2 * DESC + C, F.XG + go, sizeof(T) * GH, bar);
         bulk_g2s(st + 2 * DESC + C + GH, F.F + co, sizeof(T) * C, bar);
-        if (var) {
+        if (wc) {
+            bulk_g2s(st + 2 * DESC + 2 * C + GH, F.W + co * (2 * D + 1), sizeof(T) * 2 * D * C, bar);
+        } else if (var) {
             bulk_g2s(st + 2 * DESC + 2 * C + GH, F.E + co, sizeof(T) * C, bar);
             bulk_g2s(st + 2 * DESC + 3 * C + GH, F.EG + go, sizeof(T) * GH, bar);
         }
@@ -1588,6 +1607,13 @@ __global__ void __launch_bounds__(kMaxThreads, 4) k_restrict_tma(KParams P, int 
         for (int c = tid; c < C; c += nth) {
             const int i = c % n, j = (c / n) % n, k = D == 3 ? c / (n * n) : 0;
             const T xc = xs[c];
+            if (wc) {  // same terms and order as below, coefficients read
+                T lap = 0;
+#pragma unroll
+                for (int f = 0; f < 2 * D; f++) lap += es[f * C + c] * (nbv(xs, gs, i, j, k, f >> 1, f & 1) - xc);
+                rs[c] = fs[c] - (lap - (T)P.helm * xc);
+                continue;
+            }
             const T ec = var ? es[c] : (T)1;
             T lap = 0, ri = 0;
             if (cyl) ri = lo0 + ((T)(b.ijk[0] * n + i) + (T)0.5) * h0;
@@ -2448,9 +2474,13 @@ template <class T, int D> struct Launch {
     //        stages / 4 warps x 4 stages / 8 warps x 2 stages
     static size_t cand_smem(mg_tree *t, int l, Fields<T> &F, int cand) {
         const int n = t->lev[l].n, C = cells_of<D>(n), GH = 2 * D * face_of<D>(n);
+        // stage of the kernels that read eps (k_sweep_warp, k_sweep_rows) and
+        // of k_sweep_tma, which reads the face coefficients when present
         const size_t stage = sizeof(BlockDesc) + sizeof(LevelDesc) + sizeof(T) * (2 * C + GH + (F.E ? C + GH : 0));
+        const size_t stage_tma = F.W ? sizeof(BlockDesc) + sizeof(LevelDesc) + sizeof(T) * (2 * C + GH + (2 * D + 1) * C)
+                                     : stage;
         switch (cand) {
-        case 0: return (n == 8 || n == 16) ? 2 * stage : 0;
+        case 0: return (n == 8 || n == 16) ? 2 * stage_tma : 0;
         case 1: return 1;
         case 2: return n == 8 ? 16 * stage : 0;
         case 3: return n == 8 ? 8 * stage : 0;
@@ -2589,7 +2619,8 @@ template <class T, int D> struct Launch {
             if (L.coarsest) continue;
             ++t->launches;
             const int C8 = cells_of<D>(L.n), GH8 = 2 * D * face_of<D>(L.n);
-            const size_t smt = 2 * (2 * (sizeof(BlockDesc) + sizeof(LevelDesc)) + sizeof(T) * (2 * C8 + GH8 + (F.E ? C8 + GH8 : 0)));
+            const size_t smt = 2 * (2 * (sizeof(BlockDesc) + sizeof(LevelDesc)) +
+                                    sizeof(T) * (2 * C8 + GH8 + (F.W ? 2 * D * C8 : (F.E ? C8 + GH8 : 0))));
             if (is_flat(L)) {
                 k_restrict_flat<T, D><<<flat_grid(t, (long long)L.nb * cells_of<D>(L.n / 2)), 256, 0, t->stream>>>(
                     P, L.first, L.nb, L.n, F.X, F.XG, F.F, F.E, F.EG, F.F, 1);
@@ -2615,7 +2646,8 @@ template <class T, int D> struct Launch {
             if (C.nref <= 0) continue;
             ++t->launches;
             const int Cc = cells_of<D>(C.n), Gc = 2 * D * face_of<D>(C.n);
-            const size_t smf = 2 * (sizeof(BlockDesc) + sizeof(LevelDesc) + sizeof(T) * (2 * Cc + Gc + (F.E ? Cc + Gc : 0)));
+            const size_t smf = 2 * (sizeof(BlockDesc) + sizeof(LevelDesc) +
+                                    sizeof(T) * (2 * Cc + Gc + (F.W ? 2 * D * Cc : (F.E ? Cc + Gc : 0))));
             if ((C.n == 8 || C.n == 16) && smf <= 200 * 1024) {
                 auto kern = C.n == 8 ? k_fas_tma<T, D, 8> : k_fas_tma<T, D, 16>;
                 set_smem(kern, smf);
