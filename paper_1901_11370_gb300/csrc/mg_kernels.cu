@@ -2508,6 +2508,20 @@ static int threads_for(int cells) {
     return t < 32 ? 32 : (t > kMaxThreads ? kMaxThreads : t);
 }
 
+// CTA size of the TMA transfer kernels (restriction, prolongation, FAS
+// right-hand side, ghost fill): their phases are uneven (all cells, then a
+// parent octant, then face cells), so small CTAs waste less at barriers.
+// 128 threads measured best on GB300 (mixed solve of the 20M-unknown tree:
+// 19.8 ms at 256, 18.8 at 128, 19.1 at 64); MG_TRANSFER_THREADS overrides.
+static int transfer_threads(int want) {
+    static int cap = [] {
+        const char *e = std::getenv("MG_TRANSFER_THREADS");
+        const int v = e ? std::atoi(e) : 128;
+        return (v >= 32 && v <= kMaxThreads && v % 32 == 0) ? v : 128;
+    }();
+    return std::min(want, cap);
+}
+
 template <class T, int D> struct Launch {
     static bool is_flat(const LevelHost &L) { return cells_of<D>(L.n) <= kFlatCells; }
     static int flat_grid(mg_tree *t, long long items) {
@@ -2522,7 +2536,7 @@ template <class T, int D> struct Launch {
             if (smt <= 200 * 1024) {
                 auto kern = L.n == 8 ? k_ghost_tma<T, D, 8> : k_ghost_tma<T, D, 16>;
                 set_smem(kern, smt);
-                const int thr = threads_for(2 * D * face_of<D>(L.n));
+                const int thr = transfer_threads(threads_for(2 * D * face_of<D>(L.n)));
                 const int grid = std::min(L.nb, resident_ctas(kern, thr, smt) * t->nsm);
                 launch_k(kern, grid, thr, smt, t->stream, P, L.first, L.nb, X, XG, mode);
                 return;
@@ -2697,7 +2711,7 @@ template <class T, int D> struct Launch {
                 for (int q : L.parents) plain[q] = 1;
             } else if ((L.n == 8 || L.n == 16) && smt + sizeof(T) * C8 <= 200 * 1024) {
                 auto kern = L.n == 8 ? k_restrict_tma<T, D, 8> : k_restrict_tma<T, D, 16>;
-                const int thr = threads_for(C8);
+                const int thr = transfer_threads(threads_for(C8));
                 const int grid = std::min(L.nb, resident_ctas(kern, thr, smt) * t->nsm);
                 launch_k(kern, grid, thr, smt, t->stream, P, L.first, L.nb, F);
             } else if (L.n >= 4) {
@@ -2720,7 +2734,7 @@ template <class T, int D> struct Launch {
             if ((C.n == 8 || C.n == 16) && smf <= 200 * 1024) {
                 auto kern = C.n == 8 ? k_fas_tma<T, D, 8> : k_fas_tma<T, D, 16>;
                 set_smem(kern, smf);
-                const int thr = threads_for(cells_of<D>(C.n));
+                const int thr = transfer_threads(threads_for(cells_of<D>(C.n)));
                 const int grid = std::min(C.nref, resident_ctas(kern, thr, smf) * t->nsm);
                 launch_k(kern, grid, thr, smf, t->stream, P, C.first, C.nref, F);
             } else if (is_flat(C))
@@ -2742,7 +2756,7 @@ template <class T, int D> struct Launch {
             const size_t smt = prolong_tma_smem(L);
             auto kern = L.n == 8 ? k_prolong_tma<T, D, 8> : k_prolong_tma<T, D, 16>;
             set_smem(kern, smt);
-            const int thr = threads_for(cells_of<D>(L.n) / 2);
+            const int thr = transfer_threads(threads_for(cells_of<D>(L.n) / 2));
             const int grid = std::min(L.nb, resident_ctas(kern, thr, smt) * t->nsm);
             launch_k(kern, grid, thr, smt, t->stream, P, L.first, L.nb, F, L.parent_same_n ? L.n : L.n / 2);
             return;
