@@ -288,7 +288,7 @@ def run_ours(args):
     var64 = tree.sweep_variant(lev, mg.MG_FP64)
     kname = {0: "k_sweep_tma", 1: "k_sweep", 2: "k_sweep_warp", 3: "k_sweep_warp", 4: "k_sweep_rows",
              5: "k_sweep_rows", 6: "k_sweep_flat", 7: "k_sweep_rows", 8: "k_sweep_rows",
-             9: "k_sweep_rows"}.get(var32, "k_sweep")
+             9: "k_sweep_rows", 10: "k_sweep_tma"}.get(var32, "k_sweep")
     traffic = measured_traffic(kname, "sweep_f32_traffic.txt")
     if traffic is not None:
         lv = tree.levels()[lev]

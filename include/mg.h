@@ -201,7 +201,8 @@ int mg_launch_count(mg_tree *t, int64_t *n);
  * 4 / 5 row-wise warp TMA (8 warps x 2 stages / 4 warps x 3 stages),
  * 6 one thread per colour cell (blocks of at most 16 cells without
  * refinement faces), 7 / 8 / 9 row-wise warp TMA with the right-hand side
- * loaded into registers (FP32; 8 x 3, 4 x 4, 8 x 2).  Variants 2-5 and 7-9
+ * loaded into registers (FP32; 8 x 3, 4 x 4, 8 x 2), 10 variant 0 with
+ * half-width CTAs (two colour cells per thread).  Variants 2-5 and 7-9
  * need 8^D blocks (4, 5, 7-9: 3D, constant coefficient, Cartesian).
  *
  * mg_set_sweep_variant: override the autotuner -- use `variant` on `level`

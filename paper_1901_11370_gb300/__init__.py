@@ -206,7 +206,8 @@ class Tree:
                       5: "k_sweep_rows<4 warps, 3 stages>", 6: "k_sweep_flat (thread per colour cell)",
                       7: "k_sweep_rows<8 warps, 3 stages, f in registers>",
                       8: "k_sweep_rows<4 warps, 4 stages, f in registers>",
-                      9: "k_sweep_rows<8 warps, 2 stages, f in registers>", -1: "untuned"}
+                      9: "k_sweep_rows<8 warps, 2 stages, f in registers>",
+                      10: "k_sweep_tma (CTA per block, half-width CTAs)", -1: "untuned"}
 
     def sweep_variant(self, level, precision=MG_FP64):
         v = C.c_int()

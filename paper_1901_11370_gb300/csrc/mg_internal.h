@@ -181,7 +181,7 @@ template <class T> void refresh(mg_tree *t, Fields<T> &F, int homog);
 template <class T> void refresh_eps(mg_tree *t, Fields<T> &F);
 template <class T> void tune_sweeps(mg_tree *t, Fields<T> &F);
 int sweep_variant(mg_tree *t, int prec, int level);
-constexpr int kNumSweepVariants = 10;
+constexpr int kNumSweepVariants = 11;
 constexpr int kCoarseRows = 8;  // rows of one tree per CTA of the coarse apply
 bool sweep_variant_ok(mg_tree *t, int prec, int level, int variant);
 void divergence(mg_tree *t, const double *B, double *out);

@@ -110,6 +110,12 @@ template <> __device__ __forceinline__ float lv_h0<float>(const LevelDesc &L) { 
 template <class T> __device__ __forceinline__ T kp_lo0(const KParams &P) { return (T)P.lo[0]; }
 template <> __device__ __forceinline__ float kp_lo0<float>(const KParams &P) { return P.lo0f; }
 
+// threads per CTA of the TMA sweep for NCOL colour cells per block
+__host__ __device__ constexpr int sweep_tma_threads(int ncol, bool half) {
+    const int full = ncol < 32 ? 32 : (ncol > kMaxThreads ? kMaxThreads : ncol);
+    return half ? (full / 2 < 32 ? 32 : full / 2) : full;
+}
+
 // 5/7-point row at a cell (Sec. 2.2): for every face the weight
 // w = eps_f * kappa_f / h_d^2 (eps_f harmonic mean of the two cells, kappa
 // r_f/r_i on r-faces of the cylindrical form), giving
@@ -528,12 +534,14 @@ __device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier
 
 static constexpr uint32_t kWaitLimit = 1u << 20;
 
-template <class T, int D, int NT>
+// HALF: half as many threads per CTA (two colour cells each), which wastes
+// less at the CTA barriers on levels with few blocks per SM.
+template <class T, int D, int NT, bool HALF = false>
 __global__ void __launch_bounds__(kMaxThreads, (D == 3 && NT == 16) ? 1 : 5) k_sweep_tma(KParams P, int first, int nblocks, Fields<T> F,
                                                            int colour) {
     pdl_entry();
     constexpr int n = NT, C = cells_of<D>(NT), FC = face_of<D>(NT), GH = 2 * D * FC;
-    constexpr int NCOL = C / 2, CPT = (NCOL + kMaxThreads - 1) / kMaxThreads;
+    constexpr int NCOL = C / 2, TPB = sweep_tma_threads(NCOL, HALF), CPT = (NCOL + TPB - 1) / TPB;
     constexpr int DESC = (int)((sizeof(BlockDesc) + sizeof(LevelDesc)) / sizeof(T));
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bars[2];
@@ -2557,6 +2565,7 @@ template <class T, int D> struct Launch {
     //  6 flat sweep, one thread per colour cell (tiny blocks, no refinement faces)
     //  7 / 8 / 9 row-wise warp sweep with f in registers (FP32): 8 warps x 3
     //        stages / 4 warps x 4 stages / 8 warps x 2 stages
+    // 10 candidate 0 with half the threads per CTA (two colour cells each)
     static size_t cand_smem(mg_tree *t, int l, Fields<T> &F, int cand) {
         const int n = t->lev[l].n, C = cells_of<D>(n), GH = 2 * D * face_of<D>(n);
         // stage of the kernels that read eps (k_sweep_warp, k_sweep_rows) and
@@ -2566,6 +2575,9 @@ template <class T, int D> struct Launch {
                                      : stage;
         switch (cand) {
         case 0: return (n == 8 || n == 16) ? 2 * stage_tma : 0;
+        case 10:  // half-width TMA sweep: only where it differs from candidate 0
+            return ((n == 8 || n == 16) && cells_of<D>(n) / 2 >= 64 && cells_of<D>(n) / 2 <= 2 * kMaxThreads)
+                       ? 2 * stage_tma : 0;
         case 1: return 1;
         case 2: return n == 8 ? 16 * stage : 0;
         case 3: return n == 8 ? 8 * stage : 0;
@@ -2602,9 +2614,11 @@ template <class T, int D> struct Launch {
         ++t->launches;
         const size_t sm = cand_smem(t, l, F, cand);
         switch (cand) {
-        case 0: {
-            auto kern = n == 8 ? k_sweep_tma<T, D, 8> : k_sweep_tma<T, D, 16>;
-            const int thr = threads_for(cells_of<D>(n) / 2);
+        case 0: case 10: {
+            const bool half = cand == 10;
+            auto kern = n == 8 ? (half ? k_sweep_tma<T, D, 8, true> : k_sweep_tma<T, D, 8>)
+                               : (half ? k_sweep_tma<T, D, 16, true> : k_sweep_tma<T, D, 16>);
+            const int thr = sweep_tma_threads(cells_of<D>(n) / 2, half);
             const int grid = std::min(L.nb, resident_ctas(kern, thr, sm) * t->nsm);
             launch_k(kern, grid, thr, sm, t->stream, P, L.first, L.nb, F, colour);
             return;

@@ -40,7 +40,7 @@ def applied(t, variant, prec):
     return [l for l in range(len(t.levels())) if t.sweep_variant(l, prec) == variant]
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5, 6])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5, 6, 10])
 @pytest.mark.parametrize("name", sorted(CASES))
 def test_fp64_variant_matches_oracle(mg, name, variant):
     p = CASES[name]()
@@ -55,7 +55,7 @@ def test_fp64_variant_matches_oracle(mg, name, variant):
     assert np.abs(phi - ref).max() <= TOL * np.abs(ref).max()
 
 
-@pytest.mark.parametrize("variant", [0, 2, 3, 4, 5, 7, 8, 9])
+@pytest.mark.parametrize("variant", [0, 2, 3, 4, 5, 7, 8, 9, 10])
 def test_fp32_variant_solves_to_tolerance(mg, variant):
     p = CASES["gauss3d_b8"]()
     t = mg.Tree.from_problem(p)
