@@ -895,7 +895,7 @@ template <class T> __device__ __forceinline__ void st8(T *p, const T *r, int sw 
 // FG: f is not staged; each lane loads the right-hand side of its two rows
 // straight into registers one block ahead (smaller stages, more in flight).
 template <class T, int WARPS, int STAGES, bool FG = false>
-__global__ void __launch_bounds__(32 * WARPS) k_sweep_rows(KParams P, int first, int nblocks, Fields<T> F,
+__global__ void __launch_bounds__(32 * WARPS, WARPS == 8 ? ((FG && STAGES == 2) ? 3 : 2) : 3) k_sweep_rows(KParams P, int first, int nblocks, Fields<T> F,
                                                            int colour) {
     pdl_entry();
     constexpr int n = 8, C = 512, FC = 64, GH = 384;
