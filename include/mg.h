@@ -62,14 +62,26 @@ typedef struct {
     double value[6];
 } mg_bc;
 
-/* Cycle parameters (Sec. 2.4): n_down / n_up red-black Gauss-Seidel sweeps
- * per level (paper default 2 / 2).  precision MG_FP32_DC runs the cycles in
- * FP32 inside an FP64 defect-correction loop (mg_solve only); inner_cycles is
- * the number of FP32 V-cycles per outer FP64 residual. */
+/* Smoothers: red-black Gauss-Seidel (Sec. 2.2, the default) or weighted
+ * Jacobi (the smoother of the paper's scaling runs, Sec. 3.3): every cell of
+ * a level takes x + omega (x_GS - x), x_GS its local solution from the values
+ * before the step, then the ghosts are refreshed. */
+enum { MG_SMOOTH_RBGS = 0, MG_SMOOTH_JACOBI = 1 };
+
+/* Cycle parameters (Sec. 2.4): n_down / n_up smoothing steps per level
+ * (paper default 2 / 2; one red-black sweep or one Jacobi step each).
+ * precision MG_FP32_DC runs the cycles in FP32 inside an FP64
+ * defect-correction loop (mg_solve only); inner_cycles is the number of FP32
+ * V-cycles per outer FP64 residual.  smoother MG_SMOOTH_RBGS or
+ * MG_SMOOTH_JACOBI; omega the Jacobi weight (<= 0: 4/5 in 2D, 6/7 in 3D;
+ * at most 1).  A NULL mg_params means 2 / 2, FP64, one inner cycle, red-black
+ * Gauss-Seidel. */
 typedef struct {
     int n_down, n_up;
     int precision;
     int inner_cycles;
+    int smoother;
+    double omega;
 } mg_params;
 
 /*

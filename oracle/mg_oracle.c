@@ -34,7 +34,13 @@
  *      solve, then for each finer level prolong the correction and run one
  *      V-cycle topped at that level -- Sec. 2.4 and its figure caption;
  *  R8  residual norm: composite residual on leaf cells after restricting
- *      covered cells bottom-up, volume-weighted L2 and max norm.
+ *      covered cells bottom-up, volume-weighted L2 and max norm;
+ *  R13 the optional Jacobi smoother (the one the paper's scaling runs use,
+ *      Sec. 3.3; its weight is not stated) is weighted Jacobi over every
+ *      cell of the level, x <- x + omega (x_GS - x) with x_GS the local
+ *      solution from the old values, then a ghost refresh; omega defaults
+ *      to the standard smoothing weight of the 5/7-point Laplacian, 4/5 in
+ *      2D and 6/7 in 3D.
  */
 #include <math.h>
 #include <stdint.h>
@@ -76,6 +82,8 @@ typedef struct {
     Lev *L;
     int homog; /* 1: physical boundary values treated as zero */
     int n_down, n_up;
+    int smoother;   /* 0 red-black Gauss-Seidel, 1 weighted Jacobi (R13) */
+    double omega;   /* Jacobi weight */
     /* coarsest-level dense factorisation */
     int nc, nsys, singular, lu_ok;
     double *lu;
@@ -196,6 +204,7 @@ void *or_create(int dim, int N, int geom, const int *bct, const double *bcv,
     memcpy(T->bct, bct, sizeof(int) * 6); memcpy(T->bcv, bcv, sizeof(double) * 6);
     for (int d = 0; d < 3; d++) { T->base[d] = d < dim ? base[d] : 1; T->lo[d] = lo[d]; T->hi[d] = hi[d]; }
     T->n_down = 2; T->n_up = 2;
+    T->smoother = 0; T->omega = dim == 2 ? 0.8 : 6.0 / 7.0;
 
     /* coarse levels: list of (n, nblk) from the base downwards */
     int cn[64], cb[64][3], nco = 0;
@@ -327,6 +336,13 @@ int or_level_info(void *h, int l, int *out /* n, depth, nb, nblk[3], ncell[3] */
     return 0;
 }
 void or_set_cycle(void *h, int n_down, int n_up) { Tree *T = h; T->n_down = n_down; T->n_up = n_up; }
+/* smoother 0: red-black Gauss-Seidel; 1: weighted Jacobi with weight omega
+ * (omega <= 0: 4/5 in 2D, 6/7 in 3D) -- reading R13 */
+void or_set_smoother(void *h, int smoother, double omega) {
+    Tree *T = h;
+    T->smoother = smoother;
+    T->omega = omega > 0 ? omega : (T->dim == 2 ? 0.8 : 6.0 / 7.0);
+}
 void or_set_homogeneous(void *h, int on) { ((Tree *)h)->homog = on; }
 
 /* --------------------------------------------------------- geometry ----- */
@@ -526,8 +542,49 @@ static void smooth_colour(Tree *T, int l, int colour) {
     ghost_fill(T, l, F_PHI);
 }
 
+/*
+ * One weighted-Jacobi step (reading R13): every cell of the level takes
+ * x + omega (x_GS - x), x_GS the local solution computed from the values
+ * before the step (ghosts included); ghosts are refreshed afterwards.
+ */
+static void smooth_jacobi(Tree *T, int l) {
+    Lev *lv = &T->L[l];
+    int n = lv->n, ps = P(T, n), nk = T->dim == 3 ? n : 1;
+    double *old = malloc(sizeof(double) * (size_t)lv->nb * ps);
+    memcpy(old, lv->phi, sizeof(double) * (size_t)lv->nb * ps);
+    for (int b = 0; b < lv->nb; b++) {
+        const double *xo = old + (size_t)b * ps;
+        double *x = lv->phi + (size_t)b * ps, *f = lv->f + (size_t)b * ps;
+        for (int k = 0; k < nk; k++)
+            for (int j = 0; j < n; j++)
+                for (int i = 0; i < n; i++) {
+                    double w[6], num = 0.0, den = 0.0;
+                    face_weights(T, lv, b, i, j, k, w);
+                    for (int d = 0; d < T->dim; d++)
+                        for (int s = 0; s < 2; s++) {
+                            int q[3] = {i, j, k};
+                            q[d] += s ? 1 : -1;
+                            num += w[2 * d + s] * xo[pidx(T, n, q[0], q[1], q[2])];
+                            den += w[2 * d + s];
+                        }
+                    int c = pidx(T, n, i, j, k);
+                    double xgs = (num - f[c]) / (den + T->helm);
+                    x[c] = xo[c] + T->omega * (xgs - xo[c]);
+                }
+    }
+    free(old);
+    ghost_fill(T, l, F_PHI);
+}
+
 static void smooth(Tree *T, int l, int nsweeps) {
-    for (int s = 0; s < nsweeps; s++) { smooth_colour(T, l, 0); smooth_colour(T, l, 1); }
+    for (int s = 0; s < nsweeps; s++) {
+        if (T->smoother == 1) {
+            smooth_jacobi(T, l);
+        } else {
+            smooth_colour(T, l, 0);
+            smooth_colour(T, l, 1);
+        }
+    }
 }
 
 /* ------------------------------------------------ transfers and cycles -- */
@@ -987,6 +1044,7 @@ int or_step(void *h, int op, int l, int arg) {
     case 2: restrict_fas(T, l); break;
     case 3: prolong_correct(T, l); break;
     case 4: coarse_solve(T); break;
+    case 5: smooth_jacobi(T, l); break;
     default: return -1;
     }
     return 0;

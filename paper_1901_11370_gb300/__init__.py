@@ -16,6 +16,7 @@ from ._lib import MGError, check  # noqa: F401
 
 MG_CART, MG_CYL = 0, 1
 MG_FP64, MG_FP32_DC = 0, 1
+MG_SMOOTH_RBGS, MG_SMOOTH_JACOBI = 0, 1
 
 
 def _ptr(t: torch.Tensor):
@@ -23,8 +24,8 @@ def _ptr(t: torch.Tensor):
     return C.c_void_p(t.data_ptr())
 
 
-def _params(n_down=2, n_up=2, precision=MG_FP64, inner_cycles=1):
-    return _lib.mg_params(n_down, n_up, precision, inner_cycles)
+def _params(n_down=2, n_up=2, precision=MG_FP64, inner_cycles=1, smoother=MG_SMOOTH_RBGS, omega=0.0):
+    return _lib.mg_params(n_down, n_up, precision, inner_cycles, smoother, float(omega))
 
 
 class Tree:
@@ -129,12 +130,12 @@ class Tree:
         return out
 
     # ------------------------------------------------------------- cycles --
-    def vcycle(self, n=1, n_down=2, n_up=2):
-        p = _params(n_down, n_up)
+    def vcycle(self, n=1, n_down=2, n_up=2, smoother=MG_SMOOTH_RBGS, omega=0.0):
+        p = _params(n_down, n_up, smoother=smoother, omega=omega)
         check(self.L.mg_vcycle(self._h, n, C.byref(p)))
 
-    def fmg(self, n_down=2, n_up=2):
-        p = _params(n_down, n_up)
+    def fmg(self, n_down=2, n_up=2, smoother=MG_SMOOTH_RBGS, omega=0.0):
+        p = _params(n_down, n_up, smoother=smoother, omega=omega)
         check(self.L.mg_fmg(self._h, C.byref(p)))
 
     def residual_norm(self, want_res=False):
@@ -151,8 +152,8 @@ class Tree:
         return l2.value, li.value
 
     def solve(self, rel_tol=1e-10, max_cycles=50, fmg_first=True, precision=MG_FP64, inner_cycles=1,
-              n_down=2, n_up=2, raise_on_fail=True):
-        p = _params(n_down, n_up, precision, inner_cycles)
+              n_down=2, n_up=2, raise_on_fail=True, smoother=MG_SMOOTH_RBGS, omega=0.0):
+        p = _params(n_down, n_up, precision, inner_cycles, smoother, omega)
         cyc, rel = C.c_int(), C.c_double()
         rc = self.L.mg_solve(self._h, float(rel_tol), int(max_cycles), int(bool(fmg_first)), C.byref(p),
                              C.byref(cyc), C.byref(rel))
@@ -230,8 +231,8 @@ class Tree:
         check(self.L.mg_time_sweeps(self._h, level, n_sweeps, precision, out))
         return tuple(out), level
 
-    def adjoint(self, g, n_cycles=12, want_eps=True, n_down=2, n_up=2):
-        p = _params(n_down, n_up)
+    def adjoint(self, g, n_cycles=12, want_eps=True, n_down=2, n_up=2, smoother=MG_SMOOTH_RBGS, omega=0.0):
+        p = _params(n_down, n_up, smoother=smoother, omega=omega)
         dLdf = torch.empty(self.n_leaf, dtype=torch.float64, device="cuda")
         dLde = torch.empty(self.n_leaf, dtype=torch.float64, device="cuda") if want_eps else None
         check(self.L.mg_adjoint(self._h, self._leaf(g.contiguous()), _ptr(dLdf), _ptr(dLde) if want_eps else None,
@@ -282,12 +283,12 @@ class Batch:
         check(self.L.mg_batch_get_phi(self._h, self._leaf(out)))
         return out
 
-    def vcycle(self, n=1, n_down=2, n_up=2):
-        p = _params(n_down, n_up)
+    def vcycle(self, n=1, n_down=2, n_up=2, smoother=MG_SMOOTH_RBGS, omega=0.0):
+        p = _params(n_down, n_up, smoother=smoother, omega=omega)
         check(self.L.mg_batch_vcycle(self._h, n, C.byref(p)))
 
-    def fmg(self, n_down=2, n_up=2):
-        p = _params(n_down, n_up)
+    def fmg(self, n_down=2, n_up=2, smoother=MG_SMOOTH_RBGS, omega=0.0):
+        p = _params(n_down, n_up, smoother=smoother, omega=omega)
         check(self.L.mg_batch_fmg(self._h, C.byref(p)))
 
     def residual_norms(self):
@@ -297,8 +298,8 @@ class Batch:
         return l2, li
 
     def solve(self, rel_tol=1e-10, max_cycles=50, fmg_first=True, precision=MG_FP64, inner_cycles=1,
-              n_down=2, n_up=2, raise_on_fail=True):
-        p = _params(n_down, n_up, precision, inner_cycles)
+              n_down=2, n_up=2, raise_on_fail=True, smoother=MG_SMOOTH_RBGS, omega=0.0):
+        p = _params(n_down, n_up, precision, inner_cycles, smoother, omega)
         cyc = C.c_int()
         rel = np.zeros(len(self.trees))
         rc = self.L.mg_batch_solve(self._h, float(rel_tol), int(max_cycles), int(bool(fmg_first)), C.byref(p),

@@ -88,6 +88,7 @@ struct Fields {
     T *E = nullptr, *EG = nullptr;   // coefficient: interior + ghosts (nullptr: eps = 1)
     T *V = nullptr, *VG = nullptr;   // FAS copy v_old: interior + ghosts
     T *W = nullptr;                  // face coefficients + diagonal, 2D + 1 per cell ([face][cell] per block)
+    T *J = nullptr;                  // Jacobi scratch (cells), owned by the tree
 };
 
 // A level of one tree; in a pool of several trees (a batch), a segment:
@@ -148,6 +149,10 @@ struct mg_tree {
     mg::Fields<float> f32;         // inner defect-correction cycles
     double *d_r64 = nullptr;       // leaf residual scratch (FP64)
     double *d_wface = nullptr;     // FP64 face coefficients (variable eps or cylindrical form)
+    double *d_jac64 = nullptr;     // Jacobi scratch, FP64 and FP32 cycles
+    float *d_jac32 = nullptr;
+    int smoother = MG_SMOOTH_RBGS; // of the current call (mg_params)
+    double omega = 0.8;            // Jacobi weight of the current call
     double *d_minv = nullptr;      // coarsest-level inverses, row-major ns x ns per tree
     long long minv_total = 0, cvec_total = 0;
     int nc = 0, ns = 0;            // coarsest cells, system size (nc + singular) -- one tree

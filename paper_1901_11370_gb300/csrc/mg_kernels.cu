@@ -2446,6 +2446,28 @@ __global__ void __launch_bounds__(256) k_fas_flat(KParams P, int first, int nblo
     }
 }
 
+// One weighted-Jacobi step of a segment (reading R13), one thread per cell:
+// J = x + omega (x_GS - x), x_GS the local solution from the values before
+// the step (the caller copies J back and refreshes the ghosts).
+template <class T, int D>
+__global__ void __launch_bounds__(256) k_jacobi_flat(KParams P, int first, int nblocks, int n, Fields<T> F, T omega) {
+    pdl_entry();
+    const int C = cells_of<D>(n);
+    const long long total = (long long)nblocks * C;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const BlockDesc &b = P.B[first + (int)(idx / C)];
+        const LevelDesc &L = P.L[b.lev];
+        const int c = (int)(idx % C);
+        int i, j, k;
+        cell_of(c, n, D, i, j, k);
+        T lap, num, den, xc;
+        stencil<T, T, D>(P, L, b, F.X, F.XG, F.E, F.EG, i, j, k, lap, num, den, xc);
+        const T xgs = qdiv<T>(num - F.F[b.cell_off + c], den + (T)P.helm);
+        F.J[b.cell_off + c] = xc + omega * (xgs - xc);
+    }
+}
+
 // coarse-grid correction x^h += P(x^H - x^H_old) (as k_prolong), one
 // thread per fine cell, no ghost push (a ghost fill follows)
 template <class T, int D>
@@ -2702,9 +2724,23 @@ template <class T, int D> struct Launch {
         cudaEventDestroy(e1);
         cudaGetLastError();
     }
+    static void jacobi(mg_tree *t, const KParams &P, int l, Fields<T> &F) {
+        const LevelHost &L = t->lev[l];
+        ++t->launches;
+        launch_k(k_jacobi_flat<T, D>, flat_grid(t, L.ncells), 256, 0, t->stream, P, L.first, L.nb, L.n, F,
+                 (T)t->omega);
+        cudaMemcpyAsync(F.X + L.cell_first, F.J + L.cell_first, sizeof(T) * L.ncells, cudaMemcpyDeviceToDevice,
+                        t->stream);
+        ghost(t, P, l, F.X, F.XG, 0);
+    }
     static void smooth(mg_tree *t, const KParams &P, int l, Fields<T> &F, int sweeps) {
-        for (int s = 0; s < sweeps; s++)
+        for (int s = 0; s < sweeps; s++) {
+            if (t->smoother == MG_SMOOTH_JACOBI && F.J) {
+                jacobi(t, P, l, F);
+                continue;
+            }
             for (int colour = 0; colour < 2; colour++) sweep(t, P, l, F, colour);
+        }
     }
     // Downward FAS step from group g to g-1 (Sec. 2.4): every non-coarsest
     // segment of g restricts into its parents (pushing the parent-level

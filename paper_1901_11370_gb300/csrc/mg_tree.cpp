@@ -752,15 +752,44 @@ extern "C" int mg_set_eps(mg_tree *t, const double *e) {
 
 static void params_or_default(const mg_params *p, mg_params *q) {
     if (p) *q = *p;
-    else { q->n_down = 2; q->n_up = 2; q->precision = MG_FP64; q->inner_cycles = 1; }
+    else { q->n_down = 2; q->n_up = 2; q->precision = MG_FP64; q->inner_cycles = 1; q->smoother = MG_SMOOTH_RBGS; q->omega = 0; }
     if (q->inner_cycles < 1) q->inner_cycles = 1;
+}
+
+// Parameters of one call: defaults, validation, the smoother and its Jacobi
+// weight on the tree (read by the cycle driver), the Jacobi scratch of the
+// precisions in use.  *key gets the graph-key suffix of these parameters.
+static int use_params(mg_tree *t, const mg_params *p, mg_params *q, std::string *key) {
+    params_or_default(p, q);
+    if (q->smoother != MG_SMOOTH_RBGS && q->smoother != MG_SMOOTH_JACOBI) return fail(MG_ERR_ARG, "unknown smoother");
+    double om = q->omega > 0 ? q->omega : (t->dim == 2 ? 0.8 : 6.0 / 7.0);
+    if (q->smoother == MG_SMOOTH_JACOBI && !(om > 0 && om <= 1.0)) return fail(MG_ERR_ARG, "Jacobi weight must be in (0, 1]");
+    q->omega = om;
+    t->smoother = q->smoother;
+    t->omega = om;
+    int rc;
+    if (q->smoother == MG_SMOOTH_JACOBI) {
+        if ((rc = dalloc(&t->d_jac64, t->ncells))) return rc;
+        t->f64.J = t->adj.J = t->d_jac64;
+        if (q->precision == MG_FP32_DC) {
+            if ((rc = dalloc(&t->d_jac32, t->ncells))) return rc;
+            t->f32.J = t->d_jac32;
+        }
+    }
+    char buf[96];
+    snprintf(buf, sizeof(buf), ":%d:%d:s%d:%a", q->n_down, q->n_up, q->smoother,
+             q->smoother == MG_SMOOTH_JACOBI ? om : 0.0);
+    if (key) *key = buf;
+    return MG_OK;
 }
 
 extern "C" int mg_vcycle(mg_tree *t, int n, const mg_params *p) {
     NEED_FINAL(t);
     mg_params q;
-    params_or_default(p, &q);
-    const std::string key = "v64:" + std::to_string(q.n_down) + ":" + std::to_string(q.n_up);
+    std::string pk;
+    int prc = use_params(t, p, &q, &pk);
+    if (prc) return prc;
+    const std::string key = "v64" + pk;
     for (int c = 0; c < n; c++) {
         int rc = run_graph(t, key, [&] { vcycle<double>(t, t->f64, (int)t->groups.size() - 1, q.n_down, q.n_up, 0); });
         if (rc) return rc;
@@ -771,8 +800,10 @@ extern "C" int mg_vcycle(mg_tree *t, int n, const mg_params *p) {
 extern "C" int mg_fmg(mg_tree *t, const mg_params *p) {
     NEED_FINAL(t);
     mg_params q;
-    params_or_default(p, &q);
-    const std::string key = "fmg64:" + std::to_string(q.n_down) + ":" + std::to_string(q.n_up);
+    std::string pk;
+    int prc = use_params(t, p, &q, &pk);
+    if (prc) return prc;
+    const std::string key = "fmg64" + pk;
     int rc = run_graph(t, key, [&] { fmg<double>(t, t->f64, q.n_down, q.n_up, 0); });
     if (rc) return rc;
     return check_cuda("fmg");
@@ -808,12 +839,13 @@ extern "C" int mg_solve(mg_tree *t, double rel_tol, int max_cycles, int fmg_firs
                         int *cycles_done, double *rel_out) {
     NEED_FINAL(t);
     mg_params q;
-    params_or_default(p, &q);
+    std::string sfx;
+    int rc;
+    if ((rc = use_params(t, p, &q, &sfx))) return rc;
     const int top = (int)t->groups.size() - 1;
     double o[3];
-    int cycles = 0, rc;
+    int cycles = 0;
     double rel = 1.0;
-    const std::string sfx = ":" + std::to_string(q.n_down) + ":" + std::to_string(q.n_up);
     if (t->singular && !t->is_batch) {
         // no Dirichlet face and lambda = 0: the weighted mean of the residual
         // does not change with phi, so its size bounds what cycles can reach
@@ -901,8 +933,8 @@ extern "C" int mg_adjoint(mg_tree *t, const double *g, double *dLdf, double *dLd
         for (int f = 0; f < 2 * t->dim; f++)
             if (B.nbr[f] <= -2) return fail(MG_ERR_UNSUPPORTED, "adjoint needs a mesh without refinement faces");
     mg_params q;
-    params_or_default(p, &q);
     int rc;
+    if ((rc = use_params(t, p, &q, nullptr))) return rc;
     if ((rc = alloc_fields(t, t->adj, false))) return rc;
     t->adj.E = t->f64.E;
     t->adj.W = t->f64.W;
@@ -1004,7 +1036,7 @@ extern "C" int mg_tree_destroy(mg_tree *t) {
         free_fields(t->adj, false);
         free_fields(t->f32, true);
         cudaFree(t->d_blocks); cudaFree(t->d_levels); cudaFree(t->d_bcplanes);
-        cudaFree(t->d_r64); cudaFree(t->d_wface); cudaFree(t->d_minv); cudaFree(t->d_cvec); cudaFree(t->d_partials); cudaFree(t->d_red); cudaFree(t->d_status); cudaFree(t->d_tcoarse); cudaFree(t->d_coarse_chunks);
+        cudaFree(t->d_r64); cudaFree(t->d_wface); cudaFree(t->d_jac64); cudaFree(t->d_jac32); cudaFree(t->d_minv); cudaFree(t->d_cvec); cudaFree(t->d_partials); cudaFree(t->d_red); cudaFree(t->d_status); cudaFree(t->d_tcoarse); cudaFree(t->d_coarse_chunks);
         cudaFreeHost(t->h_red);
         cudaFree(t->d_runs); cudaFree(t->d_slot_off); cudaFree(t->d_slots); cudaFree(t->d_tree3);
         cudaFreeHost(t->h_tree3);
@@ -1310,11 +1342,12 @@ extern "C" int mg_batch_solve(mg_batch *b, double rel_tol, int max_cycles, int f
     mg_tree *t = b->pool;
     const int n = b->ntrees;
     mg_params q;
-    params_or_default(p, &q);
+    std::string sfx;
+    int rc;
+    if ((rc = use_params(t, p, &q, &sfx))) return rc;
     const int top = (int)t->groups.size() - 1;
     std::vector<double> r0(n), l2(n), rel(n, 1.0);
-    int cycles = 0, rc;
-    const std::string sfx = ":" + std::to_string(q.n_down) + ":" + std::to_string(q.n_up);
+    int cycles = 0;
     auto update = [&](bool first) -> double {
         batch_norms_wait(t, n, l2.data(), nullptr);
         double worst = 0;

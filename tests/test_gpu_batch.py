@@ -191,3 +191,19 @@ def test_batch_rejects_mismatched_trees(mg):
     p2 = W.cyl_ring_tree(40, force_k=2)
     with pytest.raises(mg.MGError):
         mg.Batch([mg.Tree.from_problem(p1, finalize=False), mg.Tree.from_problem(p2, finalize=False)])
+
+
+def test_batch_jacobi_matches_oracle_per_tree(mg):
+    """The Jacobi smoother in a batch: every tree matches the oracle's
+    Jacobi cycles."""
+    probs = FORESTS["cyl"]
+    b = make_batch(mg, probs)
+    b.fmg(smoother=mg.MG_SMOOTH_JACOBI)
+    b.vcycle(2, smoother=mg.MG_SMOOTH_JACOBI)
+    phi = b.get_phi().cpu().numpy()
+    for i, p in enumerate(probs):
+        o = Oracle.from_problem(p)
+        o.set_smoother(jacobi=True)
+        o.fmg()
+        o.vcycle(2)
+        assert rel_diff(phi[b.offsets[i]:b.offsets[i + 1]], o.get_phi()) < TOL, p.name

@@ -434,6 +434,57 @@ def test_vcycles_converge_to_dense_composite_solution(case):
     np.testing.assert_allclose(x, x_ref, rtol=0, atol=1e-11 * np.abs(x_ref).max())
 
 
+@pytest.mark.parametrize("dim,omega", [(2, 0.8), (3, 2.0 / 3.0)])
+def test_jacobi_damps_the_checkerboard_by_one_minus_two_omega(dim, omega):
+    """Weighted Jacobi (reading R13) computes every cell from the values
+    before the step: on a uniform periodic grid the checkerboard
+    (-1)^(I+J+K) is an eigenvector of one step with factor 1 - 2 omega for
+    any spacing (each neighbour is -x_c, so the local solution is -x_c).
+    A Gauss-Seidel update or a missing weight gives another factor."""
+    N, base = 4, 8
+    h = (1.0, 0.5, 2.0)[:dim]  # anisotropic cells
+    o = Oracle(dim, N, 0, (PER,) * 6, (0.0,) * 6, (base,) * dim, (0,) * dim, h, np.zeros((0, 4), np.int32))
+    o.set_smoother(jacobi=True, omega=omega)
+    top = len(o.levels()) - 1
+    n = o.levels()[top]["n"]
+    ijk, _, _ = o.level_blocks(top)
+    x = np.zeros_like(o.level_get(top, "phi"))
+    for b in range(x.shape[0]):
+        idx = np.indices((n,) * dim)
+        par = sum(ijk[b, d] * n + idx[::-1][d] for d in range(dim)) % 2
+        x[b][(slice(1, n + 1),) * dim] = 1.0 - 2.0 * par
+    o.level_set(top, "phi", x)
+    o.level_set(top, "f", np.zeros_like(x))
+    o.step("ghost", top)
+    before = o.level_get(top, "phi")
+    o.step("jacobi", top)
+    after = o.level_get(top, "phi")
+    inner = (slice(None),) + (slice(1, n + 1),) * dim
+    np.testing.assert_allclose(after[inner], (1.0 - 2.0 * omega) * before[inner], rtol=0, atol=1e-14)
+
+
+@pytest.mark.parametrize("case", ["2d_amr_dir_eps", "3d_amr_dir_eps", "cyl_amr_eps"])
+def test_jacobi_vcycles_converge_to_dense_composite_solution(case):
+    """V-cycles with the Jacobi smoother reach the same composite solution
+    (dense LU of the system assembled column by column)."""
+    c = DENSE_CASES[case]
+    dim, N, base = c["dim"], c["N"], c["base"]
+    ref = amr_refine(dim, N, base, (0.35, 0.6, 0.5), c["radii"])
+    rng = np.random.default_rng(23)
+    o = Oracle(dim, N, c.get("geom", 0), c["bct"], (0.5, -0.25, 1.0, 0.0, 0.3, 0.0),
+               (base,) * dim, (0,) * dim, (1,) * dim, ref)
+    o.set_eps(np.exp(0.5 * rng.standard_normal(o.n_leaf)))
+    f = rng.standard_normal(o.n_leaf)
+    A, b = _dense(o)
+    x_ref = np.linalg.solve(A, f - b)
+    o.set_smoother(jacobi=True)
+    o.set_rhs(f)
+    o.set_phi(np.zeros(o.n_leaf))
+    o.fmg()
+    o.vcycle(60)
+    np.testing.assert_allclose(o.get_phi(), x_ref, rtol=0, atol=1e-10 * np.abs(x_ref).max())
+
+
 # --------------------------------------------------------- convergence ----
 
 def test_second_order_convergence_2d():
