@@ -185,12 +185,19 @@ int mg_adjoint(mg_tree *t, const double *dev_dLdphi, double *dev_dLdf, double *d
  *   leaf cells.  dev_B holds dim leaf arrays (x, y[, z]) back to back; each
  *   component is restricted to covered cells and ghost-filled with the rules
  *   of Sec. 2.6 (physical faces copy the interior value).
+ * mg_divergence_order: order 2 as mg_divergence; order 4 the fourth-order
+ *   difference (-B(c+2e) + 8 B(c+e) - 8 B(c-e) + B(c-2e)) / (12 h_d) along
+ *   each dimension where both cells two away are same-level cells (this
+ *   block or a same-level neighbour, periodic wrap included), the
+ *   second-order difference beside physical and refinement faces (the grid
+ *   has one ghost layer).  MG_ERR_ARG for another order.
  * mg_project: dev_Bnew = dev_B - grad phi with second-order central
  *   differences of the current phi (dim leaf arrays back to back).
  * A cleaning step is mg_divergence, mg_set_rhs (projected to zero mean when
  * no face is Dirichlet), mg_solve and mg_project.
  */
 int mg_divergence(mg_tree *t, const double *dev_B, double *dev_divB);
+int mg_divergence_order(mg_tree *t, const double *dev_B, double *dev_divB, int order);
 int mg_project(mg_tree *t, const double *dev_B, double *dev_Bnew);
 
 /*

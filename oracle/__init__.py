@@ -69,6 +69,7 @@ def _load():
     L.or_level_blocks.argtypes = [C.c_void_p, C.c_int, _ip, _ip, _ip]
     L.or_step.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int]
     L.or_divergence.argtypes = [C.c_void_p, _dp, _dp]
+    L.or_divergence_order.argtypes = [C.c_void_p, _dp, _dp, C.c_int]
     L.or_project.argtypes = [C.c_void_p, _dp, _dp]
     _lib = L
     return L
@@ -206,11 +207,13 @@ class Oracle:
         return out
 
     # ------------------------------------------------ divergence cleaning --
-    def divergence(self, B):
-        """Second-order central divergence of a leaf vector field (dim, n_leaf)."""
+    def divergence(self, B, order=2):
+        """Central divergence of a leaf vector field (dim, n_leaf): second
+        order, or fourth order where the cells two away are same-level cells
+        (reading R14)."""
         B = np.ascontiguousarray(B, np.float64).reshape(self.dim, self.n_leaf)
         out = np.zeros(self.n_leaf)
-        if self.L.or_divergence(self._h, B.ravel(), out) != 0:
+        if self.L.or_divergence_order(self._h, B.ravel(), out, int(order)) != 0:
             raise ValueError("oracle: " + self.L.or_last_error().decode())
         return out
 

@@ -35,6 +35,10 @@
  *      V-cycle topped at that level -- Sec. 2.4 and its figure caption;
  *  R8  residual norm: composite residual on leaf cells after restricting
  *      covered cells bottom-up, volume-weighted L2 and max norm;
+ *  R14 the fourth-order divergence (Sec. 4.1) uses the fourth-order
+ *      difference along a dimension only where both cells two away are
+ *      same-level cells; elsewhere (beside physical and refinement faces,
+ *      the grid having one ghost layer) the second-order difference;
  *  R13 the optional Jacobi smoother (the one the paper's scaling runs use,
  *      Sec. 3.3; its weight is not stated) is weighted Jacobi over every
  *      cell of the level, x <- x + omega (x_GS - x) with x_GS the local
@@ -1053,16 +1057,46 @@ int or_step(void *h, int op, int l, int arg) {
 /* ------------------------------------------------ divergence cleaning --- */
 
 /*
- * Cell-centred second-order divergence of a vector field given on the leaf
- * cells (Sec. 4.1, eq. for the central-difference divergence):
- * div B = sum_d (B_d(c + e_d) - B_d(c - e_d)) / (2 h_d).  Each component is
- * restricted to covered cells and ghost-filled with the rules of Sec. 2.6
- * (refinement ghosts interpolated like phi; physical faces copy the interior
- * value).  B holds dim leaf arrays back to back.  Cartesian meshes only.
+ * Value of the vector component held in lam at the cell `off` cells away
+ * from cell (i,j,k) of block b along dimension d, when that cell lies in
+ * this block or in the same-level neighbour block (periodic wrap included);
+ * *ok = 0 when the neighbour across that face is not at this level (a
+ * physical or refinement face).
  */
-int or_divergence(void *h, const double *B, double *out) {
+static double same_level_value(const Tree *T, const Lev *lv, int b, int i, int j, int k, int d, int off, int *ok) {
+    int n = lv->n, ps = P(T, n);
+    int q[3] = {i, j, k};
+    q[d] += off;
+    if (q[d] >= 0 && q[d] < n) { *ok = 1; return lv->lam[(size_t)b * ps + pidx(T, n, q[0], q[1], q[2])]; }
+    int bq[3] = {lv->ijk[3 * b], lv->ijk[3 * b + 1], lv->ijk[3 * b + 2]};
+    int step = q[d] < 0 ? -1 : 1;
+    bq[d] += step;
+    if (bq[d] < 0 || bq[d] >= lv->nblk[d]) {
+        if (T->bct[2 * d] != BC_PER) { *ok = 0; return 0.0; }
+        bq[d] = (bq[d] + lv->nblk[d]) % lv->nblk[d];
+    }
+    int nb = lookup(lv, bq);
+    if (nb < 0) { *ok = 0; return 0.0; }
+    q[d] -= step * n;
+    *ok = 1;
+    return lv->lam[(size_t)nb * ps + pidx(T, n, q[0], q[1], q[2])];
+}
+
+/*
+ * Cell-centred divergence of a vector field given on the leaf cells
+ * (Sec. 4.1).  order 2: sum_d (B_d(c + e_d) - B_d(c - e_d)) / (2 h_d); order
+ * 4: sum_d (-B_d(c + 2e_d) + 8 B_d(c + e_d) - 8 B_d(c - e_d) + B_d(c - 2e_d))
+ * / (12 h_d) where both cells two away are same-level cells (this block or
+ * a same-level neighbour), the second-order form otherwise (reading R14:
+ * the grid carries one ghost layer).  Each component is restricted to
+ * covered cells and ghost-filled with the rules of Sec. 2.6 (refinement
+ * ghosts interpolated like phi; physical faces copy the interior value).
+ * B holds dim leaf arrays back to back.  Cartesian meshes only.
+ */
+int or_divergence_order(void *h, const double *B, double *out, int order) {
     Tree *T = h;
     if (T->geom != GEOM_CART) { snprintf(g_err, sizeof g_err, "divergence: Cartesian meshes only"); return -1; }
+    if (order != 2 && order != 4) { snprintf(g_err, sizeof g_err, "divergence: order 2 or 4"); return -1; }
     int64_t nl = or_num_leaf_cells(h);
     for (int64_t m = 0; m < nl; m++) out[m] = 0.0;
     for (int d = 0; d < T->dim; d++) {
@@ -1080,14 +1114,23 @@ int or_divergence(void *h, const double *B, double *out) {
                         for (int i = 0; i < n; i++) {
                             int qm[3] = {i, j, k}, qp[3] = {i, j, k};
                             qm[d] -= 1; qp[d] += 1;
-                            out[m++] += (x[pidx(T, n, qp[0], qp[1], qp[2])] - x[pidx(T, n, qm[0], qm[1], qm[2])]) /
-                                        (2.0 * lv->h[d]);
+                            double bp = x[pidx(T, n, qp[0], qp[1], qp[2])], bm = x[pidx(T, n, qm[0], qm[1], qm[2])];
+                            double v = (bp - bm) / (2.0 * lv->h[d]);
+                            if (order == 4) {
+                                int okp, okm;
+                                double bpp = same_level_value(T, lv, b, i, j, k, d, 2, &okp);
+                                double bmm = same_level_value(T, lv, b, i, j, k, d, -2, &okm);
+                                if (okp && okm) v = (-bpp + 8.0 * bp - 8.0 * bm + bmm) / (12.0 * lv->h[d]);
+                            }
+                            out[m++] += v;
                         }
             }
         }
     }
     return 0;
 }
+
+int or_divergence(void *h, const double *B, double *out) { return or_divergence_order(h, B, out, 2); }
 
 /*
  * Projection step B_new = B - grad phi (Sec. 4.1, eq. for the cleaned field),

@@ -161,12 +161,14 @@ class Tree:
         return cyc.value, rel.value
 
     # ------------------------------------------------ divergence cleaning --
-    def divergence(self, B):
-        """Central-difference divergence of a leaf vector field (dim, n_leaf)."""
+    def divergence(self, B, order=2):
+        """Central-difference divergence of a leaf vector field (dim, n_leaf):
+        second order, or fourth order where both cells two away are
+        same-level cells (second order beside physical and refinement faces)."""
         B = B.contiguous().view(-1)
         assert B.numel() == self.dim * self.n_leaf
         out = torch.empty(self.n_leaf, dtype=torch.float64, device="cuda")
-        check(self.L.mg_divergence(self._h, _ptr(B), _ptr(out)))
+        check(self.L.mg_divergence_order(self._h, _ptr(B), _ptr(out), int(order)))
         return out
 
     def project(self, B):
@@ -184,11 +186,13 @@ class Tree:
         per = self.n_leaf // len(lb)
         return torch.from_numpy(np.repeat([lv[int(d)] for d in lb[:, 0]], per)).cuda()
 
-    def clean(self, B, rel_tol=1e-10, max_cycles=60, precision=MG_FP64, singular=False):
-        """Divergence cleaning (Sec. 4.1): Lap phi = div B, then B - grad phi.
-        singular (no Dirichlet face): the right-hand side is first projected
-        to zero volume-weighted mean.  Returns (B_new, div B, cycles, rel)."""
-        f = self.divergence(B)
+    def clean(self, B, rel_tol=1e-10, max_cycles=60, precision=MG_FP64, singular=False, order=2):
+        """Divergence cleaning (Sec. 4.1): Lap phi = div B (second- or
+        fourth-order divergence), then B - grad phi (second order, as in the
+        paper).  singular (no Dirichlet face): the right-hand side is first
+        projected to zero volume-weighted mean.  Returns (B_new, div B,
+        cycles, rel)."""
+        f = self.divergence(B, order)
         if singular:
             vol = self.leaf_volumes()
             f = f - torch.dot(vol, f) / vol.sum()

@@ -189,7 +189,7 @@ int sweep_variant(mg_tree *t, int prec, int level);
 constexpr int kNumSweepVariants = 11;
 constexpr int kCoarseRows = 8;  // rows of one tree per CTA of the coarse apply
 bool sweep_variant_ok(mg_tree *t, int prec, int level, int variant);
-void divergence(mg_tree *t, const double *B, double *out);
+void divergence(mg_tree *t, const double *B, double *out, int order);
 void project(mg_tree *t, const double *B, double *Bout);
 // composite residual of FP64 fields on the leaves; optional outputs:
 // r64 (FP64 leaf order), f32 (FP32 into the leaf cells of an FP32 field)

@@ -1744,7 +1744,8 @@ __global__ void __launch_bounds__(kMaxThreads, 4) k_restrict_tma(KParams P, int 
 template <int D>
 __global__ void __launch_bounds__(kMaxThreads) k_div_comp(KParams P, int first, const double *__restrict__ X,
                                                           const double *__restrict__ XG, int d,
-                                                          double *__restrict__ out, long long leaf_base, int add) {
+                                                          double *__restrict__ out, long long leaf_base, int add,
+                                                          int order) {
     pdl_entry();
     __shared__ BlockDesc sb;
     stage_desc(P, first + blockIdx.x, sb);
@@ -1756,8 +1757,33 @@ __global__ void __launch_bounds__(kMaxThreads) k_div_comp(KParams P, int first, 
         int i, j, k;
         cell_of(c, n, D, i, j, k);
         const int ox = d == 0, oy = d == 1, oz = d == 2;
-        const double v = (load<double, D>(X, XG, b, i + ox, j + oy, k + oz) -
-                          load<double, D>(X, XG, b, i - ox, j - oy, k - oz)) * s2h;
+        const double bp = load<double, D>(X, XG, b, i + ox, j + oy, k + oz);
+        const double bm = load<double, D>(X, XG, b, i - ox, j - oy, k - oz);
+        double v = (bp - bm) * s2h;
+        if (order == 4) {
+            // cells two away: in this block or the same-level neighbour block
+            // across the face (fourth order only where both exist, reading R14)
+            bool okp, okm;
+            auto far = [&](int off, bool &ok) -> double {
+                I3 q{i, j, k};
+                const int qd = get(q, d) + off;
+                if (qd >= 0 && qd < n) {
+                    put(q, d, qd);
+                    ok = true;
+                    return X[b.cell_off + cidx<D>(n, q.x, q.y, q.z)];
+                }
+                const int nb = b.nbr[2 * d + (off > 0 ? 1 : 0)];
+                if (nb < 0) {
+                    ok = false;
+                    return 0.0;
+                }
+                put(q, d, qd - (off > 0 ? n : -n));
+                ok = true;
+                return X[P.B[nb].cell_off + cidx<D>(n, q.x, q.y, q.z)];
+            };
+            const double bpp = far(2, okp), bmm = far(-2, okm);
+            if (okp && okm) v = (-bpp + 8.0 * bp - 8.0 * bm + bmm) / (12.0 * L.h[d]);
+        }
         const long long m = leaf_base + (long long)blockIdx.x * C + c;
         out[m] = add ? out[m] + v : v;
     }
@@ -3343,7 +3369,7 @@ extern "C" int mg_residual_norm_noalloc(mg_tree *t, double *l2, double *linf) {
 
 namespace mg {
 
-template <int D> static void divergence_d(mg_tree *t, const double *B, double *out) {
+template <int D> static void divergence_d(mg_tree *t, const double *B, double *out, int order) {
     const KParams P = kparams(t, 1);
     for (int d = 0; d < D; d++) {
         // component d into the scratch field, covered cells and ghosts refreshed
@@ -3361,7 +3387,8 @@ template <int D> static void divergence_d(mg_tree *t, const double *B, double *o
             const int nleaf = L.nb - L.nref;
             if (nleaf <= 0) continue;
             ++t->launches;
-            launch_k(k_div_comp<D>, nleaf, threads_for(cells_of<D>(L.n)), 0, t->stream, P, L.first + L.nref, t->adj.X, t->adj.XG, d, out, leaf_base, d > 0);
+            launch_k(k_div_comp<D>, nleaf, threads_for(cells_of<D>(L.n)), 0, t->stream, P, L.first + L.nref,
+                     t->adj.X, t->adj.XG, d, out, leaf_base, d > 0, order);
             leaf_base += (long long)nleaf * cells_of<D>(L.n);
         }
     }
@@ -3383,9 +3410,9 @@ template <int D> static void project_d(mg_tree *t, const double *B, double *Bout
     }
 }
 
-void divergence(mg_tree *t, const double *B, double *out) {
-    if (t->dim == 2) divergence_d<2>(t, B, out);
-    else divergence_d<3>(t, B, out);
+void divergence(mg_tree *t, const double *B, double *out, int order) {
+    if (t->dim == 2) divergence_d<2>(t, B, out, order);
+    else divergence_d<3>(t, B, out, order);
 }
 void project(mg_tree *t, const double *B, double *Bout) {
     if (t->dim == 2) project_d<2>(t, B, Bout);

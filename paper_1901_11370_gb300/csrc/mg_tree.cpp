@@ -1010,15 +1010,18 @@ extern "C" int mg_time_sweeps(mg_tree *t, int level, int n_sweeps, int precision
     return check_cuda("time_sweeps");
 }
 
-extern "C" int mg_divergence(mg_tree *t, const double *B, double *divB) {
+extern "C" int mg_divergence_order(mg_tree *t, const double *B, double *divB, int order) {
     NEED_FINAL(t);
     if (!B || !divB) return fail(MG_ERR_ARG, "null argument");
+    if (order != 2 && order != 4) return fail(MG_ERR_ARG, "divergence order must be 2 or 4");
     if (t->geom != MG_CART) return fail(MG_ERR_UNSUPPORTED, "divergence: Cartesian meshes only");
     int rc;
     if ((rc = alloc_fields(t, t->adj, false))) return rc;
-    divergence(t, B, divB);
+    divergence(t, B, divB, order);
     return check_cuda("divergence");
 }
+
+extern "C" int mg_divergence(mg_tree *t, const double *B, double *divB) { return mg_divergence_order(t, B, divB, 2); }
 
 extern "C" int mg_project(mg_tree *t, const double *B, double *Bnew) {
     NEED_FINAL(t);

@@ -247,6 +247,32 @@ def test_divergence_cleaning_matches_oracle(mg, name):
     assert np.linalg.norm(o.divergence(Bn_o)) < 0.2 * np.linalg.norm(d_o)
 
 
+@pytest.mark.parametrize("name", ["periodic3d_amr", "dirichlet2d_amr"])
+def test_fourth_order_divergence_matches_oracle(mg, name):
+    """The fourth-order divergence (reading R14: second order beside physical
+    and refinement faces) and a cleaning step built on it, against the
+    oracle."""
+    import torch
+    from paper_1901_11370_gb300 import Tree
+    p = _clean_case(name)
+    X, Y, Z, _ = W.leaf_cell_centres(p)
+    B = np.stack([np.sin(2 * np.pi * X) * np.cos(2 * np.pi * Y), np.cos(2 * np.pi * Y + Z),
+                  np.sin(2 * np.pi * (X + Z))][:p.dim])
+    o = Oracle(p.dim, p.N, 0, p.bc_type, p.bc_val, p.base, p.lo, p.hi, p.refine, p.coarse_max)
+    t = Tree(p.dim, p.N, 0, p.bc_type, p.bc_val, p.base, p.lo, p.hi, p.refine, p.coarse_max)
+    Bg = torch.from_numpy(np.ascontiguousarray(B)).cuda()
+    d_o = o.divergence(B, order=4)
+    d_g = t.divergence(Bg, order=4).cpu().numpy()
+    assert rel_diff(d_g, d_o) < TOL
+    assert np.abs(d_o - o.divergence(B)).max() > 1e-6 * np.abs(d_o).max()  # not the second-order field
+    Bn, f, cyc, rel = t.clean(Bg, 1e-10, 60, singular=name.startswith("periodic"), order=4)
+    vol, _ = o.leaf_geometry()
+    fo = d_o - (np.dot(vol, d_o) / vol.sum() if name.startswith("periodic") else 0.0)
+    assert rel_diff(f.cpu().numpy(), fo) < TOL
+    with pytest.raises(mg.MGError):
+        t.divergence(Bg, order=3)
+
+
 def test_cleaning_autograd_matches_oracle(mg):
     """CleanB backward (uniform periodic mesh) equals the oracle's gradient,
     the cleaning of B_new - B_t (pinned against finite differences)."""

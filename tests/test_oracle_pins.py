@@ -630,6 +630,48 @@ def test_divergence_and_gradient_exact_on_linear_fields():
         np.testing.assert_allclose(comp[inner], want, atol=1e-11)
 
 
+@pytest.mark.parametrize("dim", [2, 3])
+def test_fourth_order_divergence_on_cubics(dim):
+    """The fourth-order difference of Sec. 4.1 is exact on cubics; where a
+    cell two away lies beyond a physical face the second-order difference is
+    used (reading R14), whose error on x^3 is exactly h^2 (one cell from the
+    face; the boundary cell itself depends on the ghost rule)."""
+    N, base = 4, 16
+    o = Oracle(dim, N, 0, (0,) * 6, (0.0,) * 6, (base,) * dim, (0,) * dim, (1,) * dim, np.zeros((0, 4), np.int32))
+    p = W.Problem("cub", dim, N, 0, (base,) * dim + (1,) * (3 - dim), (0,) * 3, (1,) * 3, (0,) * 6, (0,) * 6,
+                  np.zeros((0, 4), np.int32))
+    X, Y, Z, H = W.leaf_cell_centres(p)
+    coords = [X, Y, Z][:dim]
+    B = np.stack([c ** 3 for c in coords])
+    div = o.divergence(B, order=4)
+    h = 1.0 / base
+    idx = [np.rint(c / h - 0.5).astype(int) for c in coords]
+    interior = np.all([(I >= 1) & (I <= base - 2) for I in idx], axis=0)
+    want = np.zeros(o.n_leaf)
+    for c, I in zip(coords, idx):
+        near = (I == 1) | (I == base - 2)
+        want += 3 * c ** 2 + np.where(near, h * h, 0.0)
+    np.testing.assert_allclose(div[interior], want[interior], rtol=0, atol=1e-10)
+    assert (np.abs(div[interior] - sum(3 * c ** 2 for c in coords)[interior]) > 0.5 * h * h).any()
+
+
+def test_fourth_order_divergence_converges_at_fourth_order():
+    """Smooth field on a uniform periodic mesh (every cell takes the
+    fourth-order form): the error falls ~16x when h halves."""
+    errs = []
+    for base in (16, 32):
+        dim, N = 2, 4
+        o = Oracle(dim, N, 0, (PER,) * 6, (0.0,) * 6, (base, base), (0, 0), (1, 1), np.zeros((0, 4), np.int32))
+        p = W.Problem("s", dim, N, 0, (base, base, 1), (0,) * 3, (1,) * 3, (PER,) * 6, (0,) * 6,
+                      np.zeros((0, 4), np.int32))
+        X, Y, Z, H = W.leaf_cell_centres(p)
+        k = 2 * math.pi
+        B = np.stack([np.sin(k * X) * np.cos(k * Y), np.cos(k * X + 0.3) * np.sin(k * Y)])
+        exact = k * np.cos(k * X) * np.cos(k * Y) + k * np.cos(k * X + 0.3) * np.cos(k * Y)
+        errs.append(np.abs(o.divergence(B, order=4) - exact).max())
+    assert errs[0] / errs[1] > 12, errs
+
+
 def test_central_divergence_is_minus_adjoint_of_gradient_periodic():
     """On a uniform periodic mesh the central divergence and gradient satisfy
     <u, D B> = -<G u, B> (summation by parts)."""
