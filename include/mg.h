@@ -201,6 +201,18 @@ int mg_divergence_order(mg_tree *t, const double *dev_B, double *dev_divB, int o
 int mg_project(mg_tree *t, const double *dev_B, double *dev_Bnew);
 
 /*
+ * mg_clean -- one whole cleaning step on the device: f = div B
+ * (mg_divergence_order), minus its volume-weighted mean when no face is
+ * Dirichlet (the compatibility condition of the periodic/Neumann problem),
+ * phi = 0, mg_solve(rel_tol, max_cycles, FMG first, p) for Lap phi = f, then
+ * dev_Bnew = dev_B - grad phi.  dev_divB (optional, n_leaf values) receives
+ * the right-hand side f.  Returns as mg_solve (MG_ERR_NOT_CONVERGED still
+ * writes dev_Bnew).
+ */
+int mg_clean(mg_tree *t, const double *dev_B, double *dev_Bnew, double *dev_divB, int order, double rel_tol,
+             int max_cycles, const mg_params *p, int *cycles_done, double *rel_out);
+
+/*
  * Instrumentation (the paper has no counterpart; used by the benchmark).
  * mg_launch_count: number of CUDA kernels this tree has launched so far.
  * mg_time_sweeps: runs n_sweeps red-black sweeps on `level` of the FP64

@@ -186,20 +186,21 @@ class Tree:
         per = self.n_leaf // len(lb)
         return torch.from_numpy(np.repeat([lv[int(d)] for d in lb[:, 0]], per)).cuda()
 
-    def clean(self, B, rel_tol=1e-10, max_cycles=60, precision=MG_FP64, singular=False, order=2):
-        """Divergence cleaning (Sec. 4.1): Lap phi = div B (second- or
-        fourth-order divergence), then B - grad phi (second order, as in the
-        paper).  singular (no Dirichlet face): the right-hand side is first
-        projected to zero volume-weighted mean.  Returns (B_new, div B,
-        cycles, rel)."""
-        f = self.divergence(B, order)
-        if singular:
-            vol = self.leaf_volumes()
-            f = f - torch.dot(vol, f) / vol.sum()
-        self.set_rhs(f.contiguous())
-        self.set_phi(torch.zeros_like(f))
-        cyc, rel = self.solve(rel_tol, max_cycles, fmg_first=True, precision=precision, raise_on_fail=False)
-        return self.project(B), f, cyc, rel
+    def clean(self, B, rel_tol=1e-10, max_cycles=60, precision=MG_FP64, order=2, smoother=MG_SMOOTH_RBGS):
+        """Divergence cleaning (Sec. 4.1) on the device (mg_clean): f = div B
+        (second- or fourth-order), minus its volume-weighted mean when no
+        face is Dirichlet; Lap phi = f; B - grad phi (second order, as in the
+        paper).  Returns (B_new, f, cycles, rel)."""
+        B = B.contiguous().view(-1)
+        assert B.numel() == self.dim * self.n_leaf
+        Bn = torch.empty_like(B)
+        f = torch.empty(self.n_leaf, dtype=torch.float64, device="cuda")
+        p = _params(2, 2, precision, 1, smoother)
+        cyc, rel = C.c_int(), C.c_double()
+        rc = self.L.mg_clean(self._h, _ptr(B), _ptr(Bn), _ptr(f), int(order), float(rel_tol), int(max_cycles),
+                             C.byref(p), C.byref(cyc), C.byref(rel))
+        check(rc, allow=(-4,))
+        return Bn.view(self.dim, self.n_leaf), f, cyc.value, rel.value
 
     def launch_count(self):
         n = C.c_int64()

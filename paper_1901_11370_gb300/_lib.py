@@ -21,7 +21,7 @@ EXPORTS = ["mg_tree_create", "mg_tree_refine", "mg_tree_num_levels", "mg_tree_le
            "mg_set_rhs", "mg_set_eps", "mg_set_phi", "mg_get_phi", "mg_vcycle", "mg_fmg",
            "mg_residual_norm", "mg_solve", "mg_adjoint", "mg_tree_destroy", "mg_last_error",
            "mg_launch_count", "mg_time_sweeps", "mg_residual_norm_noalloc", "mg_sweep_variant",
-           "mg_divergence", "mg_divergence_order", "mg_project", "mg_set_sweep_variant",
+           "mg_divergence", "mg_divergence_order", "mg_project", "mg_clean", "mg_set_sweep_variant",
            "mg_batch_create", "mg_batch_leaf_offsets", "mg_batch_set_rhs", "mg_batch_set_eps",
            "mg_batch_set_phi", "mg_batch_get_phi", "mg_batch_vcycle", "mg_batch_fmg", "mg_batch_residual_norms",
            "mg_batch_solve", "mg_batch_launch_count", "mg_batch_num_segments", "mg_batch_segment_info",
@@ -79,6 +79,7 @@ def load():
     L.mg_set_sweep_variant.argtypes = [vp, C.c_int, C.c_int, C.c_int]
     L.mg_divergence.argtypes = [vp, vp, vp]
     L.mg_divergence_order.argtypes = [vp, vp, vp, C.c_int]
+    L.mg_clean.argtypes = [vp, vp, vp, vp, C.c_int, C.c_double, C.c_int, C.POINTER(mg_params), ip, dp]
     L.mg_project.argtypes = [vp, vp, vp]
     L.mg_batch_create.argtypes = [C.c_int, vp, vp, C.POINTER(vp)]
     L.mg_batch_leaf_offsets.argtypes = [vp, vp]

@@ -41,11 +41,11 @@ class CleanB(torch.autograd.Function):
 
     @staticmethod
     def forward(ctx, tree, B, rel_tol=1e-12, max_cycles=80):
-        Bn, _, _, _ = tree.clean(B.detach(), rel_tol, max_cycles, singular=True)
+        Bn, _, _, _ = tree.clean(B.detach(), rel_tol, max_cycles)
         ctx.tree, ctx.rel_tol, ctx.max_cycles = tree, rel_tol, max_cycles
         return Bn
 
     @staticmethod
     def backward(ctx, g):
-        gB, _, _, _ = ctx.tree.clean(g.contiguous(), ctx.rel_tol, ctx.max_cycles, singular=True)
+        gB, _, _, _ = ctx.tree.clean(g.contiguous(), ctx.rel_tol, ctx.max_cycles)
         return None, gB, None, None

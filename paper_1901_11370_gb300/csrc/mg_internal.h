@@ -202,6 +202,7 @@ void residual_wait(mg_tree *t, double *out3);
 // volume-weighted mean of a leaf-order FP64 field (synchronises the stream)
 double leaf_mean(mg_tree *t, const double *rleaf);
 void add_e_to_phi(mg_tree *t, const float *e, double *phi);
+void sub_scalar(mg_tree *t, double *x, double c, long long n);  // x[0..n) -= c
 void copy_eps_to_f32(mg_tree *t);
 // FP64 face coefficients of every cell into t->d_wface (eps ghosts current)
 void face_coef(mg_tree *t);

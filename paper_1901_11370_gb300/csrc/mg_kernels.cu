@@ -3149,6 +3149,17 @@ void residual_norm(mg_tree *t, Fields<double> &F, int homog, double *out3, doubl
     residual_wait(t, out3);
 }
 
+__global__ void k_sub_scalar(double *__restrict__ x, double c, long long n) {
+    pdl_entry();
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        x[i] -= c;
+}
+
+void sub_scalar(mg_tree *t, double *x, double c, long long n) {
+    ++t->launches;
+    launch_k(k_sub_scalar, 1216, 256, 0, t->stream, x, c, n);
+}
+
 void add_e_to_phi(mg_tree *t, const float *e, double *phi) {
     ++t->launches;
     launch_k(k_add_e, 1216, 256, 0, t->stream, e, phi, t->ncells);

@@ -1031,6 +1031,28 @@ extern "C" int mg_project(mg_tree *t, const double *B, double *Bnew) {
     return check_cuda("project");
 }
 
+
+// One divergence-cleaning step (Sec. 4.1) on the device: f = div B (order 2
+// or 4); on a problem without Dirichlet faces f loses its volume-weighted
+// mean; phi = 0; solve Lap phi = f; Bnew = B - grad phi.
+extern "C" int mg_clean(mg_tree *t, const double *B, double *Bnew, double *divB, int order, double rel_tol,
+                        int max_cycles, const mg_params *p, int *cycles_done, double *rel_out) {
+    NEED_FINAL(t);
+    if (!B || !Bnew) return fail(MG_ERR_ARG, "null argument");
+    int rc;
+    if ((rc = dalloc(&t->d_r64, t->nleaf_cells))) return rc;
+    if ((rc = mg_divergence_order(t, B, t->d_r64, order))) return rc;
+    if (t->singular) sub_scalar(t, t->d_r64, leaf_mean(t, t->d_r64), t->nleaf_cells);
+    if (divB) CK(cudaMemcpyAsync(divB, t->d_r64, sizeof(double) * t->nleaf_cells, cudaMemcpyDeviceToDevice, t->stream));
+    if ((rc = leaf_copy(t, t->f64.F, (const double *)t->d_r64, true))) return rc;
+    CK(cudaMemsetAsync(t->f64.X, 0, sizeof(double) * t->ncells, t->stream));
+    refresh<double>(t, t->f64, 0);
+    rc = mg_solve(t, rel_tol, max_cycles, 1, p, cycles_done, rel_out);
+    if (rc != MG_OK && rc != MG_ERR_NOT_CONVERGED) return rc;
+    const int rp = mg_project(t, B, Bnew);
+    return rp ? rp : rc;
+}
+
 extern "C" int mg_tree_destroy(mg_tree *t) {
     if (!t) return MG_OK;
     if (t->finalized) {

@@ -265,12 +265,35 @@ def test_fourth_order_divergence_matches_oracle(mg, name):
     d_g = t.divergence(Bg, order=4).cpu().numpy()
     assert rel_diff(d_g, d_o) < TOL
     assert np.abs(d_o - o.divergence(B)).max() > 1e-6 * np.abs(d_o).max()  # not the second-order field
-    Bn, f, cyc, rel = t.clean(Bg, 1e-10, 60, singular=name.startswith("periodic"), order=4)
+    Bn, f, cyc, rel = t.clean(Bg, 1e-10, 60, order=4)
     vol, _ = o.leaf_geometry()
     fo = d_o - (np.dot(vol, d_o) / vol.sum() if name.startswith("periodic") else 0.0)
     assert rel_diff(f.cpu().numpy(), fo) < TOL
     with pytest.raises(mg.MGError):
         t.divergence(Bg, order=3)
+
+
+@pytest.mark.parametrize("name", ["periodic3d_amr", "dirichlet2d_amr"])
+def test_clean_entry_point_matches_oracle(mg, name):
+    """mg_clean (div B, zero-mean projection on the periodic problem, solve,
+    B - grad phi, all on the device) against the oracle's cleaning solved
+    far below the tolerance."""
+    import torch
+    from paper_1901_11370_gb300 import Tree
+    p = _clean_case(name)
+    X, Y, Z, _ = W.leaf_cell_centres(p)
+    B = np.stack([np.sin(2 * np.pi * X) * np.cos(2 * np.pi * Y), np.cos(2 * np.pi * Y + Z),
+                  np.sin(2 * np.pi * (X + Z))][:p.dim])
+    o = Oracle(p.dim, p.N, 0, p.bc_type, p.bc_val, p.base, p.lo, p.hi, p.refine, p.coarse_max)
+    t = Tree(p.dim, p.N, 0, p.bc_type, p.bc_val, p.base, p.lo, p.hi, p.refine, p.coarse_max)
+    Bn, f, cyc, rel = t.clean(torch.from_numpy(np.ascontiguousarray(B)).cuda(), 1e-12, 60)
+    assert rel <= 1e-12
+    Bn_o, f_o, _ = o.clean(B, rel_tol=1e-13, max_cycles=80)
+    assert rel_diff(f.cpu().numpy(), f_o) < TOL
+    assert rel_diff(Bn.cpu().numpy(), Bn_o) < 1e-8
+    Bj, _, _, relj = t.clean(torch.from_numpy(np.ascontiguousarray(B)).cuda(), 1e-10, 80,
+                             smoother=mg.MG_SMOOTH_JACOBI)
+    assert relj <= 1e-10 and rel_diff(Bj.cpu().numpy(), Bn_o) < 1e-6
 
 
 def test_cleaning_autograd_matches_oracle(mg):
