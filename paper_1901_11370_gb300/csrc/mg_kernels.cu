@@ -1882,6 +1882,7 @@ __global__ void __launch_bounds__(kMaxThreads, 3) k_resid_tma(KParams P, int fir
     __shared__ __align__(16) LevelDesc sL;
     __shared__ int s_abort;
     __shared__ double sred[3][kMaxThreads / 32];
+    __shared__ float sredf[2][kMaxThreads / 32];
     const bool var = F.E != nullptr, wc = F.W != nullptr;  // wc: precomputed face coefficients
     const int stage_elems = DESC + 2 * C + GH + (wc ? (2 * D + 1) * C : (var ? C + GH : 0));
     T *stage0 = reinterpret_cast<T *>(smem_raw);
@@ -1918,6 +1919,12 @@ __global__ void __launch_bounds__(kMaxThreads, 3) k_resid_tma(KParams P, int fir
     const bool cyl = P.geom == MG_CYL;
     double s2 = 0, sv = 0;
     double mx = 0.0;
+    // solve-loop norms (MX off) in FP32 across all blocks of the thread: no
+    // FP64 work per block (every launch is one level of one tree, so the
+    // Cartesian cell volume is uniform; the batch's per-block slots are
+    // reduced in FP32 and scaled by thread 0)
+    float acc_r = 0.f, acc_v = 0.f;
+    double vol_u = 0;
     for (int it = 0; g < nblocks; it++, g += gridDim.x) {
         {
             uint32_t tries = 0;
@@ -1958,8 +1965,8 @@ __global__ void __launch_bounds__(kMaxThreads, 3) k_resid_tma(KParams P, int fir
         // eps * sum_f w_f |x|, far below any tolerance the solves use
         const double dg = L.diag;
         double bs2 = 0;
-        float bs2f = 0.f, s2f = 0.f, svf = 0.f;  // solve-loop norms (MX off) in FP32
         const float lo0f = P.lo0f, h0f = L.h0f, hvf = L.hvf;
+        vol_u = vol;
         for (int c = tid; c < C; c += nth) {
             const int i = c % n, j = (c / n) % n, k = D == 3 ? c / (n * n) : 0;
             const double xc = xs[c];
@@ -2009,24 +2016,35 @@ __global__ void __launch_bounds__(kMaxThreads, 3) k_resid_tma(KParams P, int fir
                 mx = fmax(mx, fabs(r));
             } else if (cyl) {
                 const float Vf = (lo0f + ((float)(b.ijk[0] * n + i) + 0.5f) * h0f) * hvf;
-                s2f = fmaf(Vf * rf, rf, s2f);
-                svf += Vf;
+                acc_r = fmaf(Vf * rf, rf, acc_r);
+                acc_v += Vf;
             } else {
-                bs2f = fmaf(rf, rf, bs2f);
+                acc_r = fmaf(rf, rf, acc_r);
             }
             if (f32) f32[b.cell_off + c] = rf;
             if (rleaf) rleaf[leaf_base + (long long)g * C + c] = r;
         }
-        if (!MX) {
-            bs2 += (double)bs2f;
-            s2 += (double)s2f;
-            sv += (double)svf;
-        }
-        if (!cyl) {
-            s2 = fma(vol, bs2, s2);
-            if (tid == 0) sv += vol * C;
-        }
-        if (per_block) {  // this block's sums into its own slot (per-tree norms of a batch)
+        if (MX && !cyl) s2 = fma(vol, bs2, s2);
+        if (!cyl && tid == 0) sv += vol * C;
+        if (per_block && !MX) {  // this block's FP32 sums into its slot, scaled once by thread 0
+            float a = acc_r, v = acc_v;
+            for (int o = 16; o > 0; o >>= 1) {
+                a += __shfl_down_sync(0xffffffffu, a, o);
+                v += __shfl_down_sync(0xffffffffu, v, o);
+            }
+            const int w = tid >> 5, lane = tid & 31, nw = (nth + 31) >> 5;
+            if (lane == 0) { sredf[0][w] = a; sredf[1][w] = v; }
+            __syncthreads();
+            if (tid == 0) {
+                float x = 0.f, y = 0.f;
+                for (int e = 0; e < nw; e++) { x += sredf[0][e]; y += sredf[1][e]; }
+                partials[3LL * g] = cyl ? (double)x : vol * (double)x;
+                partials[3LL * g + 1] = cyl ? (double)y : vol * C;
+                partials[3LL * g + 2] = 0.0;
+            }
+            __syncthreads();  // sredf is reused by the next block
+            acc_r = 0.f; acc_v = 0.f; sv = 0;
+        } else if (per_block) {  // this block's sums into its own slot (per-tree norms of a batch)
             double a = s2, bb = sv, mm = mx;
             for (int o = 16; o > 0; o >>= 1) {
                 a += __shfl_down_sync(0xffffffffu, a, o);
@@ -2051,6 +2069,10 @@ __global__ void __launch_bounds__(kMaxThreads, 3) k_resid_tma(KParams P, int fir
         return;
     }
     if (tid == 0) bulk_wait0();
+    if (!MX) {
+        s2 = cyl ? (double)acc_r : vol_u * (double)acc_r;
+        if (cyl) sv = (double)acc_v;
+    }
     for (int o = 16; o > 0; o >>= 1) {
         s2 += __shfl_down_sync(0xffffffffu, s2, o);
         sv += __shfl_down_sync(0xffffffffu, sv, o);
