@@ -66,6 +66,7 @@ struct KParams {
     int *status;          // device status word: 1 = a bounded wait gave up
     int uniform;          // 1: every block of a launch shares one level descriptor
     float lo0f;           // lo[0] in FP32 (cylindrical radius in FP32 kernels)
+    float helmf;          // lambda in FP32
 };
 
 // Coarsest level of one tree of a pool (one tree, or a batch of trees):

@@ -109,6 +109,8 @@ template <class T> __device__ __forceinline__ T lv_h0(const LevelDesc &L) { retu
 template <> __device__ __forceinline__ float lv_h0<float>(const LevelDesc &L) { return L.h0f; }
 template <class T> __device__ __forceinline__ T kp_lo0(const KParams &P) { return (T)P.lo[0]; }
 template <> __device__ __forceinline__ float kp_lo0<float>(const KParams &P) { return P.lo0f; }
+template <class T> __device__ __forceinline__ T kp_helm(const KParams &P) { return (T)P.helm; }
+template <> __device__ __forceinline__ float kp_helm<float>(const KParams &P) { return P.helmf; }
 
 // threads per CTA of the TMA sweep for NCOL colour cells per block
 __host__ __device__ constexpr int sweep_tma_threads(int ncol, bool half) {
@@ -415,7 +417,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_sweep(KParams P, int first, Fie
 
     // 2. red-black update of this colour (Sec. 2.2)
     const bool cyl = P.geom == MG_CYL;
-    const T helm = (T)P.helm;
+    const T helm = kp_helm<T>(P);
     const T w0 = lv_ih<T>(L, 0), w1 = lv_ih<T>(L, 1), w2 = lv_ih<T>(L, 2);
     const T inv_den = (T)1 / ((T)2 * (w0 + w1 + (D == 3 ? w2 : (T)0)) + helm);
     auto update = [&](int i, int j, int k, T fc) {
@@ -584,7 +586,7 @@ __global__ void __launch_bounds__(kMaxThreads, (D == 3 && NT == 16) ? 1 : 5) k_s
     if (tid == 0 && g < nblocks) issue(0, first + g);
     // level descriptor: CTA-wide copy when every block shares it, else per block
     const bool cyl = P.geom == MG_CYL;
-    const T helm = (T)P.helm;
+    const T helm = kp_helm<T>(P);
     for (int it = 0; g < nblocks; it++, g += gridDim.x) {
         {
             uint32_t tries = 0;
@@ -748,7 +750,7 @@ __global__ void __launch_bounds__(32 * WARPS) k_sweep_warp(KParams P, int first,
     if (lane == 0 && g < nblocks) issue(0, first + g);
     // level descriptor: CTA-wide copy when every block shares it, else per block
     const bool cyl = P.geom == MG_CYL;
-    const T helm = (T)P.helm;
+    const T helm = kp_helm<T>(P);
     for (int it = 0; g < nblocks; it++, g += stride) {
         bool timed_out = false;
         {
@@ -953,7 +955,7 @@ __global__ void __launch_bounds__(32 * WARPS, WARPS == 8 ? ((FG && STAGES == 2) 
         for (int q = 0; q < STAGES - 1; q++)
             if (g + q * stride < nblocks) issue(q, first + g + q * stride);
     // level descriptor: CTA-wide copy when every block shares it, else per block
-    const T helm = (T)P.helm;
+    const T helm = kp_helm<T>(P);
     for (int it = 0; g < nblocks; it++, g += stride) {
         bool timed_out = false;
         {
@@ -1096,12 +1098,12 @@ __global__ void __launch_bounds__(kMaxThreads) k_restrict(KParams P, int first, 
             if (with_res) {
                 T lap, num, den, xc;
                 stencil<T, T, D>(P, L, b, X, XG, E, EG, fi, fj, fk, lap, num, den, xc);
-                sr += Fr[b.cell_off + fc] - (lap - (T)P.helm * xc);
+                sr += Fr[b.cell_off + fc] - (lap - kp_helm<T>(P) * xc);
             }
         }
         const int pc = cidx<D>(p.n, b.poff[0] + ci, b.poff[1] + cj, b.poff[2] + ck);
-        X[p.cell_off + pc] = sx / (T)(1 << D);
-        if (with_res) Fdst[p.cell_off + pc] = sr / (T)(1 << D);
+        X[p.cell_off + pc] = sx * (T)(1.0 / (1 << D));
+        if (with_res) Fdst[p.cell_off + pc] = sr * (T)(1.0 / (1 << D));
     }
 }
 
@@ -1157,12 +1159,12 @@ __global__ void __launch_bounds__(kMaxThreads) k_restrict_push(KParams P, int fi
             T lap, num, den, xc;
             stencil<T, T, D>(P, L, b, F.X, F.XG, F.E, F.EG, fi, fj, fk, lap, num, den, xc);
             sx += xc;
-            sr += F.F[b.cell_off + cidx<D>(n, fi, fj, fk)] - (lap - (T)P.helm * xc);
+            sr += F.F[b.cell_off + cidx<D>(n, fi, fj, fk)] - (lap - kp_helm<T>(P) * xc);
         }
-        const T xv = sx / (T)(1 << D);
+        const T xv = sx * (T)(1.0 / (1 << D));
         const int pc = cidx<D>(pn, b.poff[0] + ci, b.poff[1] + cj, b.poff[2] + ck);
         F.X[p.cell_off + pc] = xv;
-        F.F[p.cell_off + pc] = sr / (T)(1 << D);
+        F.F[p.cell_off + pc] = sr * (T)(1.0 / (1 << D));
         oct[c] = xv;
     }
     __syncthreads();
@@ -1202,7 +1204,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_fas_rhs_vold(KParams P, int fir
         cell_of(c, n, D, i, j, k);
         T lap, num, den, xc;
         stencil<T, T, D>(P, L, b, F.X, F.XG, F.E, F.EG, i, j, k, lap, num, den, xc);
-        F.F[b.cell_off + c] += lap - (T)P.helm * xc;
+        F.F[b.cell_off + c] += lap - kp_helm<T>(P) * xc;
         F.V[b.cell_off + c] = xc;
     }
     for (int t = threadIdx.x; t < G; t += blockDim.x) F.VG[b.ghost_off + t] = F.XG[b.ghost_off + t];
@@ -1415,7 +1417,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_fas_tma(KParams P, int first, i
                 T lap = 0;
 #pragma unroll
                 for (int f = 0; f < 2 * D; f++) lap += es[f * C + c] * (nbv(xs, gs, i, j, k, f >> 1, f & 1) - xc);
-                fs[c] += lap - (T)P.helm * xc;
+                fs[c] += lap - kp_helm<T>(P) * xc;
                 continue;
             }
             const T ec = var ? es[c] : (T)1;
@@ -1433,7 +1435,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_fas_tma(KParams P, int first, i
                     if (cyl && d == 0) w *= qdiv<T>(lo0 + (T)(b.ijk[0] * n + i + s) * h0, ri);
                     lap += w * (nbv(xs, gs, i, j, k, d, s) - xc);
                 }
-            fs[c] += lap - (T)P.helm * xc;
+            fs[c] += lap - kp_helm<T>(P) * xc;
         }
         fence_async_smem();
         __syncthreads();
@@ -1673,7 +1675,7 @@ __global__ void __launch_bounds__(kMaxThreads, 4) k_restrict_tma(KParams P, int 
                 T lap = 0;
 #pragma unroll
                 for (int f = 0; f < 2 * D; f++) lap += es[f * C + c] * (nbv(xs, gs, i, j, k, f >> 1, f & 1) - xc);
-                rs[c] = fs[c] - (lap - (T)P.helm * xc);
+                rs[c] = fs[c] - (lap - kp_helm<T>(P) * xc);
                 continue;
             }
             const T ec = var ? es[c] : (T)1;
@@ -1691,7 +1693,7 @@ __global__ void __launch_bounds__(kMaxThreads, 4) k_restrict_tma(KParams P, int 
                     if (cyl && d == 0) w *= qdiv<T>(lo0 + (T)(b.ijk[0] * n + i + s) * h0, ri);
                     lap += w * (nbv(xs, gs, i, j, k, d, s) - xc);
                 }
-            rs[c] = fs[c] - (lap - (T)P.helm * xc);
+            rs[c] = fs[c] - (lap - kp_helm<T>(P) * xc);
         }
         __syncthreads();
         const int pn = p.n;
@@ -1705,8 +1707,8 @@ __global__ void __launch_bounds__(kMaxThreads, 4) k_restrict_tma(KParams P, int 
                 sr += rs[fc];
             }
             const int pc = cidx<D>(pn, b.poff[0] + ci, b.poff[1] + cj, b.poff[2] + ck);
-            F.X[p.cell_off + pc] = sx / (T)(1 << D);
-            F.F[p.cell_off + pc] = sr / (T)(1 << D);
+            F.X[p.cell_off + pc] = sx * (T)(1.0 / (1 << D));
+            F.F[p.cell_off + pc] = sr * (T)(1.0 / (1 << D));
         }
         __syncthreads();  // rs is reused below for the octant values
         for (int c = tid; c < M; c += nth) {
@@ -1715,7 +1717,7 @@ __global__ void __launch_bounds__(kMaxThreads, 4) k_restrict_tma(KParams P, int 
 #pragma unroll
             for (int ch = 0; ch < (1 << D); ch++)
                 sx += xs[cidx<D>(n, 2 * ci + (ch & 1), 2 * cj + ((ch >> 1) & 1), D == 3 ? 2 * ck + ((ch >> 2) & 1) : 0)];
-            rs[c] = sx / (T)(1 << D);
+            rs[c] = sx * (T)(1.0 / (1 << D));
         }
         __syncthreads();
         const int Fm = face_of<D>(m);
@@ -2413,7 +2415,7 @@ __global__ void __launch_bounds__(256) k_sweep_flat(KParams P, int first, int nb
         const int c = cidx<D>(n, i, j, k);
         T lap, num, den, xc;
         stencil<T, T, D>(P, L, b, F.X, F.XG, F.E, F.EG, i, j, k, lap, num, den, xc);
-        const T xnew = qdiv<T>(num - F.F[b.cell_off + c], den + (T)P.helm);
+        const T xnew = qdiv<T>(num - F.F[b.cell_off + c], den + kp_helm<T>(P));
         F.X[b.cell_off + c] = xnew;
         const I3 ii{i, j, k};
 #pragma unroll
@@ -2457,12 +2459,12 @@ __global__ void __launch_bounds__(256) k_restrict_flat(KParams P, int first, int
             if (with_res) {
                 T lap, num, den, xc;
                 stencil<T, T, D>(P, L, b, X, XG, E, EG, fi, fj, fk, lap, num, den, xc);
-                sr += Fr[b.cell_off + fc] - (lap - (T)P.helm * xc);
+                sr += Fr[b.cell_off + fc] - (lap - kp_helm<T>(P) * xc);
             }
         }
         const int pc = cidx<D>(p.n, b.poff[0] + ci, b.poff[1] + cj, b.poff[2] + ck);
-        X[p.cell_off + pc] = sx / (T)(1 << D);
-        if (with_res) Fdst[p.cell_off + pc] = sr / (T)(1 << D);
+        X[p.cell_off + pc] = sx * (T)(1.0 / (1 << D));
+        if (with_res) Fdst[p.cell_off + pc] = sr * (T)(1.0 / (1 << D));
     }
 }
 
@@ -2483,7 +2485,7 @@ __global__ void __launch_bounds__(256) k_fas_flat(KParams P, int first, int nblo
             cell_of(c, n, D, i, j, k);
             T lap, num, den, xc;
             stencil<T, T, D>(P, L, b, F.X, F.XG, F.E, F.EG, i, j, k, lap, num, den, xc);
-            F.F[b.cell_off + c] += lap - (T)P.helm * xc;
+            F.F[b.cell_off + c] += lap - kp_helm<T>(P) * xc;
             if (vold) F.V[b.cell_off + c] = xc;
         } else {
             const long long e = idx - ncells;
@@ -2511,7 +2513,7 @@ __global__ void __launch_bounds__(256) k_jacobi_flat(KParams P, int first, int n
         cell_of(c, n, D, i, j, k);
         T lap, num, den, xc;
         stencil<T, T, D>(P, L, b, F.X, F.XG, F.E, F.EG, i, j, k, lap, num, den, xc);
-        const T xgs = qdiv<T>(num - F.F[b.cell_off + c], den + (T)P.helm);
+        const T xgs = qdiv<T>(num - F.F[b.cell_off + c], den + kp_helm<T>(P));
         F.J[b.cell_off + c] = xc + omega * (xgs - xc);
     }
 }
@@ -2559,6 +2561,7 @@ KParams kparams(mg_tree *t, int homog) {
     P.status = t->d_status;
     P.uniform = t->is_batch ? 0 : 1;
     P.lo0f = (float)t->lo[0];
+    P.helmf = (float)t->helm;
     return P;
 }
 
