@@ -248,6 +248,24 @@ __device__ __forceinline__ T cf_ghost(const KParams &P, const LevelDesc &L, cons
     return (T)0.5 * Bp + (T)0.75 * c - (T)0.25 * dv;
 }
 
+// A sweep changes neither the coarse level nor, before its ghost pushes, the
+// interior values that the current coarse-fine ghost g = B'/2 + 3c/4 - d/4
+// was formed with.  It therefore recovers B'/2 from g and the old (c, d)
+// and forms the new ghost from B'/2 and the new (c, d), with no reads of the
+// coarser block.  The two agree with cf_ghost up to rounding.
+template <class T> __device__ __forceinline__ T cf_half_base(T g, T c, T dv) {
+    return g - (T)0.75 * c + (T)0.25 * dv;
+}
+template <class T> __device__ __forceinline__ T cf_from_half_base(T bh, T c, T dv) {
+    return bh + (T)0.75 * c - (T)0.25 * dv;
+}
+// bit f set: face f of the block borders a coarser block
+__device__ __forceinline__ int cf_faces(const BlockDesc &b, int D) {
+    int m = 0;
+    for (int f = 0; f < 2 * D; f++) m |= (b.nbr[f] <= -2) << f;
+    return m;
+}
+
 // ------------------------------------------------------------- ghosts ----
 // Face ghosts of every block in [first, first + gridDim.x) (Sec. 2.6):
 // same-level or periodic copy; physical boundary (Dirichlet 2a - x_i,
@@ -544,6 +562,7 @@ __global__ void __launch_bounds__(kMaxThreads, (D == 3 && NT == 16) ? 1 : 5) k_s
     pdl_entry();
     constexpr int n = NT, C = cells_of<D>(NT), FC = face_of<D>(NT), GH = 2 * D * FC;
     constexpr int NCOL = C / 2, TPB = sweep_tma_threads(NCOL, HALF), CPT = (NCOL + TPB - 1) / TPB;
+    constexpr int GPT = (GH + TPB - 1) / TPB;  // ghost slots per thread (launched with TPB threads)
     constexpr int DESC = (int)((sizeof(BlockDesc) + sizeof(LevelDesc)) / sizeof(T));
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bars[2];
@@ -632,6 +651,23 @@ __global__ void __launch_bounds__(kMaxThreads, (D == 3 && NT == 16) ? 1 : 5) k_s
             if (kk < 0 || kk >= n) return gi[(s ? 5 : 4) * FC + i + n * j];
             return xi[cidx<D>(n, i, j, kk)];
         };
+        // coarse-fine faces: B'/2 of this thread's ghost slots from the old
+        // interior values (see cf_half_base), before the update overwrites them
+        const int cfm = cf_faces(b, D);
+        T bh[GPT];
+        if (cfm) {
+#pragma unroll
+            for (int r = 0; r < GPT; r++) {
+                const int t = tid + r * TPB, face = t / FC;
+                if (t >= GH || !((cfm >> face) & 1)) continue;
+                const int u = t - face * FC, d = face >> 1, s = face & 1;
+                const I3 ii = face_cell<D>(n, face, u, false);
+                I3 dd = ii;
+                put(dd, d, s ? n - 2 : 1);
+                bh[r] = cf_half_base(gs[t], xs[cidx<D>(n, ii.x, ii.y, ii.z)], xs[cidx<D>(n, dd.x, dd.y, dd.z)]);
+            }
+            __syncthreads();
+        }
 #pragma unroll
         for (int r = 0; r < CPT; r++) {
             const int qi = tid + r * nth;
@@ -680,7 +716,10 @@ __global__ void __launch_bounds__(kMaxThreads, (D == 3 && NT == 16) ? 1 : 5) k_s
             bulk_commit();
         }
         // ghost pushes beside updated cells (see k_sweep)
-        for (int t = tid; t < GH; t += nth) {
+#pragma unroll
+        for (int r = 0; r < GPT; r++) {
+            const int t = tid + r * TPB;
+            if (t >= GH) continue;
             const int face = t / FC, u = t - face * FC, d = face >> 1, s = face & 1;
             const I3 ii = face_cell<D>(n, face, u, false);
             const bool updated = ((par0 + ii.x + ii.y + ii.z) & 1) == colour;
@@ -694,8 +733,8 @@ __global__ void __launch_bounds__(kMaxThreads, (D == 3 && NT == 16) ? 1 : 5) k_s
             } else {
                 I3 dd = ii;
                 put(dd, d, s ? n - 2 : 1);
-                F.XG[b.ghost_off + t] = cf_ghost<T, D>(P, L, b, face, ii, xs[cidx<D>(n, ii.x, ii.y, ii.z)],
-                                                       xs[cidx<D>(n, dd.x, dd.y, dd.z)], F.X, F.XG, nb, false);
+                F.XG[b.ghost_off + t] = cf_from_half_base(bh[r], xs[cidx<D>(n, ii.x, ii.y, ii.z)],
+                                                          xs[cidx<D>(n, dd.x, dd.y, dd.z)]);
             }
         }
     }
@@ -905,24 +944,21 @@ __global__ void __launch_bounds__(32 * WARPS, WARPS == 8 ? ((FG && STAGES == 2) 
     constexpr int STAGE = DESC + C + GH + (FG ? 0 : C);
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bars[WARPS][STAGES];
-    __shared__ __align__(16) LevelDesc sL;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     T *wst = reinterpret_cast<T *>(smem_raw) + warp * STAGES * STAGE;
     if (lane == 0) {
         for (int q = 0; q < STAGES; q++) mbar_init(&bars[warp][q], 1);
         fence_mbar_init();
     }
-    if (tid < (int)(sizeof(LevelDesc) / 4))
-        reinterpret_cast<int *>(&sL)[tid] = reinterpret_cast<const int *>(P.L + P.B[first].lev)[tid];
     __syncthreads();
-    auto issue = [&](int it, int g) {  // lane 0 only
+    // co, go, lev: the block's cell and ghost offsets and level
+    auto issue = [&](int it, int g, long long co, long long go, int lev) {  // lane 0 only
         T *st = wst + (it % STAGES) * STAGE;
-        const long long co = P.B[g].cell_off, go = P.B[g].ghost_off;
         uint64_t *bar = &bars[warp][it % STAGES];
         fence_async_smem();
         mbar_expect_tx(bar, (uint32_t)(sizeof(T) * STAGE));
         bulk_g2s(st, P.B + g, sizeof(BlockDesc), bar);
-        bulk_g2s(reinterpret_cast<char *>(st) + sizeof(BlockDesc), P.L + P.B[g].lev, sizeof(LevelDesc), bar);
+        bulk_g2s(reinterpret_cast<char *>(st) + sizeof(BlockDesc), P.L + lev, sizeof(LevelDesc), bar);
         bulk_g2s(st + DESC, F.X + co, sizeof(T) * C, bar);
         bulk_g2s(st + DESC + C, F.XG + go, sizeof(T) * GH, bar);
         if (!FG) bulk_g2s(st + DESC + C + GH, F.F + co, sizeof(T) * C, bar);
@@ -931,8 +967,22 @@ __global__ void __launch_bounds__(32 * WARPS, WARPS == 8 ? ((FG && STAGES == 2) 
     int g = blockIdx.x * WARPS + warp;
     const int sw = sizeof(T) == 4 ? (lane >> 2) & 1 : 0;  // row half order of this lane (see ld8)
     T fnx[16], fcur[16];
-    auto loadf = [&](int gb) {  // rows lane and lane + 32 of block gb
-        const T *fp = F.F + P.B[gb].cell_off;
+    // The offsets of the blocks that the next iteration's stage refill
+    // (block g + STAGES stride) and right-hand-side load (g + 2 stride)
+    // need are read one iteration ahead, so that neither waits on the
+    // descriptor table.
+    long long rco = 0, rgo = 0, fco = 0;
+    int rlev = 0;
+    auto fetch_desc = [&](int gr, int gf) {
+        if (gr < nblocks) {
+            rco = P.B[first + gr].cell_off;
+            rgo = P.B[first + gr].ghost_off;
+            rlev = P.B[first + gr].lev;
+        }
+        if (FG && gf < nblocks) fco = P.B[first + gf].cell_off;
+    };
+    auto loadf = [&](long long cell_off) {  // rows lane and lane + 32 of the block at cell_off
+        const T *fp = F.F + cell_off;
 #pragma unroll
         for (int h = 0; h < 2; h++) {
             using V = typename Vec16<T>::type;
@@ -950,11 +1000,14 @@ __global__ void __launch_bounds__(32 * WARPS, WARPS == 8 ? ((FG && STAGES == 2) 
             }
         }
     };
-    if (FG && g < nblocks) loadf(first + g);
+    if (FG && g < nblocks) loadf(P.B[first + g].cell_off);
     if (lane == 0)
         for (int q = 0; q < STAGES - 1; q++)
-            if (g + q * stride < nblocks) issue(q, first + g + q * stride);
-    // level descriptor: CTA-wide copy when every block shares it, else per block
+            if (g + q * stride < nblocks) {
+                const BlockDesc &bq = P.B[first + g + q * stride];
+                issue(q, first + g + q * stride, bq.cell_off, bq.ghost_off, bq.lev);
+            }
+    fetch_desc(g + (STAGES - 1) * stride, g + stride);
     const T helm = kp_helm<T>(P);
     for (int it = 0; g < nblocks; it++, g += stride) {
         bool timed_out = false;
@@ -974,13 +1027,14 @@ __global__ void __launch_bounds__(32 * WARPS, WARPS == 8 ? ((FG && STAGES == 2) 
         // refill the stage of block it-1 (every lane is past it) with block it+STAGES-1
         if (lane == 0 && g + (STAGES - 1) * stride < nblocks) {
             bulk_wait_read0();
-            issue(it + STAGES - 1, first + g + (STAGES - 1) * stride);
+            issue(it + STAGES - 1, first + g + (STAGES - 1) * stride, rco, rgo, rlev);
         }
         if (FG) {
 #pragma unroll
             for (int e = 0; e < 16; e++) fcur[e] = fnx[e];
-            if (g + stride < nblocks) loadf(first + g + stride);
+            if (g + stride < nblocks) loadf(fco);
         }
+        fetch_desc(g + STAGES * stride, g + 2 * stride);
         T *st = wst + (it % STAGES) * STAGE;
         const BlockDesc &b = *reinterpret_cast<const BlockDesc *>(st);
         const LevelDesc &L = *reinterpret_cast<const LevelDesc *>(reinterpret_cast<const char *>(st) + sizeof(BlockDesc));
@@ -1029,6 +1083,26 @@ __global__ void __launch_bounds__(32 * WARPS, WARPS == 8 ? ((FG && STAGES == 2) 
         }
         // every lane has read its neighbour rows: write the rows back
         __syncwarp();
+        // coarse-fine faces: B'/2 into the stage ghost slots while the rows
+        // still hold the old values (see cf_half_base)
+        const int cfm = cf_faces(b, 3);
+        if (cfm) {
+#pragma unroll 1
+            for (int face = 0; face < 6; face++) {
+                if (!((cfm >> face) & 1)) continue;
+                const int d = face >> 1, s = face & 1, edge = s ? n - 1 : 0;
+#pragma unroll
+                for (int h = 0; h < 2; h++) {
+                    const int u = 2 * lane + h, t1 = u & 7, t2 = u >> 3;
+                    const I3 ii = d == 0 ? I3{edge, t1, t2} : (d == 1 ? I3{t1, edge, t2} : I3{t1, t2, edge});
+                    I3 dd = ii;
+                    put(dd, d, s ? n - 2 : 1);
+                    gs[face * FC + u] = cf_half_base(gs[face * FC + u], xs[cidx<3>(n, ii.x, ii.y, ii.z)],
+                                                     xs[cidx<3>(n, dd.x, dd.y, dd.z)]);
+                }
+            }
+            __syncwarp();
+        }
 #pragma unroll
         for (int h = 0; h < 2; h++) st8(xs + 8 * (lane + 32 * h), newrow[h], sw);
         fence_async_smem();
@@ -1050,8 +1124,8 @@ __global__ void __launch_bounds__(32 * WARPS, WARPS == 8 ? ((FG && STAGES == 2) 
                     I3 dd = ii;
                     put(dd, d, s ? n - 2 : 1);
                     F.XG[b.ghost_off + face * FC + u] =
-                        cf_ghost<T, 3>(P, L, b, face, ii, xs[cidx<3>(n, ii.x, ii.y, ii.z)],
-                                       xs[cidx<3>(n, dd.x, dd.y, dd.z)], F.X, F.XG, nb, false);
+                        cf_from_half_base(gs[face * FC + u], xs[cidx<3>(n, ii.x, ii.y, ii.z)],
+                                          xs[cidx<3>(n, dd.x, dd.y, dd.z)]);
                 }
                 continue;
             }
