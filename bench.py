@@ -398,11 +398,14 @@ def batch_measure(args, mg, W, barrier, max_over_ranks):
     return out
 
 
-def run_profile(kind):
+def run_profile(kind, pins=""):
     """Small fixed launch sequences for ncu captures (not a benchmark):
     sweeps64 -- one red-black sweep (2 smoother + 2 ghost launches) on the
     largest level of the workload; solve32 / solve64 -- one solve after one
-    untimed warm-up solve."""
+    untimed warm-up solve.  pins ("level:variant,...") fixes the sweep kernel
+    per level after autotuning: the tuner's timings mean nothing under a
+    profiler, which slows every launch, so a capture pins what a plain run of
+    the same command printed."""
     import torch
     import paper_1901_11370_gb300 as mg
     torch.cuda.set_device(0)
@@ -411,6 +414,7 @@ def run_profile(kind):
     if kind in ("sweeps64", "sweeps32"):
         prec = mg.MG_FP64 if kind == "sweeps64" else mg.MG_FP32_DC
         tree.time_sweeps(n_sweeps=1, precision=prec)  # first use: allocation and autotuning
+        pin_sweeps(tree, prec, pins)
         torch.cuda.synchronize()
         torch.cuda.nvtx.range_push("measure")
         tree.time_sweeps(n_sweeps=1, precision=prec)
@@ -418,6 +422,8 @@ def run_profile(kind):
         torch.cuda.nvtx.range_pop()
     else:
         prec = mg.MG_FP32_DC if kind == "solve32" else mg.MG_FP64
+        tree.time_sweeps(n_sweeps=1, precision=prec)  # autotuning
+        pin_sweeps(tree, prec, pins)
         for rep in range(2):  # the second solve (graphs captured, tuning done) in the NVTX range
             tree.set_phi(zeros)
             torch.cuda.synchronize()
@@ -429,6 +435,14 @@ def run_profile(kind):
                 torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     print("profile %s done: %d launches" % (kind, tree.launch_count()))
+
+
+def pin_sweeps(tree, prec, pins):
+    for item in filter(None, pins.split(",")):
+        lev, var = (int(x) for x in item.split(":"))
+        tree.set_sweep_variant(var, level=lev, precision=prec)
+    print("sweep variants by level:", ",".join("%d:%d" % (l, tree.sweep_variant(l, prec))
+                                              for l in range(len(tree.levels()))))
 
 
 def run_profile_batch():
@@ -465,11 +479,13 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 512-tree batch measurement")
     ap.add_argument("--profile", choices=["sweeps64", "sweeps32", "solve32", "solve64", "batch32"], default=None)
+    ap.add_argument("--pin-sweeps", default="",
+                    help="with --profile sweeps*/solve*: 'level:variant,...' sweep kernels to pin after tuning")
     args = ap.parse_args()
     if args.profile == "batch32":
         run_profile_batch()
     elif args.profile:
-        run_profile(args.profile)
+        run_profile(args.profile, args.pin_sweeps)
     elif args.impl == "reference":
         run_reference(args)
     else:
