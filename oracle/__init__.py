@@ -71,6 +71,7 @@ def _load():
     L.or_divergence.argtypes = [C.c_void_p, _dp, _dp]
     L.or_divergence_order.argtypes = [C.c_void_p, _dp, _dp, C.c_int]
     L.or_project.argtypes = [C.c_void_p, _dp, _dp]
+    L.or_transfer.argtypes = [C.c_void_p, C.c_void_p]
     _lib = L
     return L
 
@@ -109,6 +110,12 @@ class Oracle:
                 o.set_eps(W.leaf_field(p, "eps"))
             o.set_rhs(W.leaf_field(p, "rhs"))
         return o
+
+    def transfer_from(self, old):
+        """phi of the oracle mesh `old` carried to this (adapted) mesh
+        (reading R15); afterwards get_phi() gives the carried field."""
+        if self.L.or_transfer(old._h, self._h) != 0:
+            raise ValueError("oracle: " + self.L.or_last_error().decode())
 
     def __del__(self):
         if getattr(self, "_h", None):

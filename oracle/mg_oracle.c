@@ -44,7 +44,12 @@
  *      cell of the level, x <- x + omega (x_GS - x) with x_GS the local
  *      solution from the old values, then a ghost refresh; omega defaults
  *      to the standard smoothing weight of the 5/7-point Laplacian, 4/5 in
- *      2D and 6/7 in 3D.
+ *      2D and 6/7 in 3D;
+ *  R15 phi carried to an adapted mesh (Sec. 2.5 leaves the data to the
+ *      caller): a leaf block that is also a block of the old mesh keeps its
+ *      values (the restriction of its former children where a refinement
+ *      was removed), a new child takes the prolongation of Sec. 2.3 of its
+ *      old parent leaf, parent ghost layer included.
  */
 #include <math.h>
 #include <stdint.h>
@@ -1163,5 +1168,73 @@ int or_project(void *h, const double *B, double *out) {
             }
         }
     }
+    return 0;
+}
+
+/* ----------------------------------------------------- mesh adaptation -- */
+
+static Lev *level_at_depth(Tree *T, int depth) {
+    for (int l = 0; l < T->nlev; l++)
+        if (T->L[l].depth == depth) return &T->L[l];
+    return NULL;
+}
+
+/*
+ * Phi carried from the mesh `hold` to the adapted mesh `hnew` (reading R15).
+ * The old mesh is refreshed first, so its covered cells hold the mean of
+ * their children and every ghost layer is filled.  Then each leaf block of
+ * the new mesh
+ *   - that is a block of the old mesh (same depth and block coordinates)
+ *     copies that block's cells;
+ *   - otherwise is a child of an old leaf block and takes, for every cell,
+ *     the prolongation of Sec. 2.3 from the parent cell c0 under it and the
+ *     parent neighbours c_d on the cell's side in each dimension d:
+ *     (2 c0 + c_x + c_y)/4 in 2D, (c0 + c_x + c_y + c_z)/4 in 3D.
+ * The new mesh is then refreshed.  Returns 0, or -1 when a new leaf block
+ * has neither source.
+ */
+int or_transfer(void *hold, void *hnew) {
+    Tree *O = hold, *T = hnew;
+    refresh(O);
+    for (int l = 0; l < T->nlev; l++) {
+        Lev *lv = &T->L[l];
+        Lev *same = level_at_depth(O, lv->depth), *up = level_at_depth(O, lv->depth - 1);
+        int n = lv->n, ps = P(T, n), nk = T->dim == 3 ? n : 1;
+        for (int b = 0; b < lv->nb; b++) {
+            if (lv->haschild[b]) continue;
+            const int *q = lv->ijk + 3 * b;
+            double *dst = lv->phi + (size_t)b * ps;
+            int ob = same ? lookup(same, q) : -1;
+            if (ob >= 0) {
+                const double *src = same->phi + (size_t)ob * P(O, same->n);
+                for (int k = 0; k < nk; k++)
+                    for (int j = 0; j < n; j++)
+                        for (int i = 0; i < n; i++) dst[pidx(T, n, i, j, k)] = src[pidx(O, n, i, j, k)];
+                continue;
+            }
+            int pq[3] = {q[0] / 2, q[1] / 2, T->dim == 3 ? q[2] / 2 : 0};
+            int pb = up ? lookup(up, pq) : -1;
+            if (pb < 0 || up->haschild[pb]) {
+                snprintf(g_err, sizeof g_err, "transfer: a new leaf block has no source block");
+                return -1;
+            }
+            int pn = up->n;
+            const double *par = up->phi + (size_t)pb * P(O, pn);
+            for (int k = 0; k < nk; k++)
+                for (int j = 0; j < n; j++)
+                    for (int i = 0; i < n; i++) {
+                        int f[3] = {i, j, k}, cc[3];
+                        for (int d = 0; d < 3; d++) cc[d] = d < T->dim ? (q[d] % 2) * (pn / 2) + f[d] / 2 : 0;
+                        double c0 = par[pidx(O, pn, cc[0], cc[1], cc[2])], nbs = 0.0;
+                        for (int d = 0; d < T->dim; d++) {
+                            int e[3] = {cc[0], cc[1], cc[2]};
+                            e[d] += ((q[d] * n + f[d]) & 1) ? 1 : -1;
+                            nbs += par[pidx(O, pn, e[0], e[1], e[2])];
+                        }
+                        dst[pidx(T, n, i, j, k)] = T->dim == 2 ? (2.0 * c0 + nbs) / 4.0 : (c0 + nbs) / 4.0;
+                    }
+        }
+    }
+    refresh(T);
     return 0;
 }
