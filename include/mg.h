@@ -128,6 +128,37 @@ int mg_set_bc_plane(mg_tree *t, int face, int level, const double *host_vals);
  * f = 0) and bind cuda_stream (a cudaStream_t, NULL = legacy default). */
 int mg_tree_finalize(mg_tree *t, void *cuda_stream);
 
+/*
+ * mg_tree_adapt -- a new mesh from a finalized tree t (Sec. 2.5, "Adapting
+ * the grid structure": the application reports the blocks it added and
+ * removed).  add holds n_add records (depth, i, j, k) of leaf blocks of t to
+ * cover by 2^D children; remove holds n_remove records of refined blocks of
+ * t whose children are all leaves, whose refinement is undone.  The base
+ * grid, boundary conditions, Helmholtz term and coarse-level rule of t are
+ * kept, and so are the boundary planes of every level depth both meshes
+ * have.  The new tree is finalized on t's stream and phi is carried over on
+ * the device: a leaf block that is also a block of t takes its values (the
+ * mean of its former children where a refinement was removed), a new child
+ * takes the prolongation of Sec. 2.3 of its parent's values, parent ghosts
+ * included.  Right-hand side and eps start at 0 and 1: set them for the
+ * new mesh.  t is not changed (its covered cells and ghosts are refreshed);
+ * *out receives the new handle, which the caller destroys.  Errors:
+ * MG_ERR_ARG (a record names no such leaf or refinement, a removed
+ * refinement has refined children, t is a batch), MG_ERR_BALANCE (the new
+ * mesh breaks 2:1 balance), MG_ERR_CUDA; on error *out is NULL.
+ */
+int mg_tree_adapt(mg_tree *t, int n_add, const int32_t *add, int n_remove, const int32_t *remove,
+                  mg_tree **out);
+
+/*
+ * mg_tree_build_times -- wall seconds of this tree's construction: out4[0]
+ * host tables (levels, neighbours, offsets), out4[1] device setup
+ * (allocation, uploads, coarsest-level inverse), out4[2] FP64 sweep
+ * autotuning at finalize, out4[3] the phi transfer of mg_tree_adapt (0 for
+ * a tree not made by it).  Host pointer; entries not reached yet are 0.
+ */
+int mg_tree_build_times(mg_tree *t, double *out4);
+
 /* Leaf fields, device pointers, leaf order (see above). mg_set_phi also
  * restricts the covered cells and refills every ghost layer. */
 int mg_set_rhs(mg_tree *t, const double *dev_f);

@@ -80,6 +80,30 @@ class Tree:
         check(self.L.mg_tree_finalize(self._h, C.c_void_p(stream)))
         self.finalized = True
 
+    def adapt(self, add=(), remove=()):
+        """A new Tree for the adapted mesh (mg_tree_adapt): add lists leaf
+        blocks (depth, i, j, k) to refine, remove lists refined blocks whose
+        children are all leaves to coarsen.  phi is carried over; set rhs
+        and eps for the new mesh."""
+        a = np.ascontiguousarray(np.asarray(add, dtype=np.int32).reshape(-1, 4))
+        r = np.ascontiguousarray(np.asarray(remove, dtype=np.int32).reshape(-1, 4))
+        h = C.c_void_p()
+        check(self.L.mg_tree_adapt(self._h, len(a), a.ctypes.data_as(C.c_void_p), len(r),
+                                   r.ctypes.data_as(C.c_void_p), C.byref(h)))
+        t = Tree.__new__(Tree)
+        t.L, t._h, t.dim, t.finalized = self.L, h, self.dim, True
+        n = C.c_int64()
+        check(self.L.mg_tree_num_leaf_cells(h, C.byref(n)))
+        t.n_leaf = n.value
+        return t
+
+    def build_times(self):
+        """Seconds: host tables, device setup, FP64 autotuning, adapt's phi
+        transfer (mg_tree_build_times)."""
+        out = (C.c_double * 4)()
+        check(self.L.mg_tree_build_times(self._h, out))
+        return tuple(out)
+
     def __del__(self):
         h = getattr(self, "_h", None)
         if h is not None and h.value:

@@ -18,6 +18,7 @@ ERRORS = {-1: "MG_ERR_ARG", -2: "MG_ERR_BALANCE", -3: "MG_ERR_CUDA", -4: "MG_ERR
 # every entry point declared in include/mg.h
 EXPORTS = ["mg_tree_create", "mg_tree_refine", "mg_tree_num_levels", "mg_tree_level_info",
            "mg_tree_num_leaf_cells", "mg_tree_leaf_blocks", "mg_set_bc_plane", "mg_tree_finalize",
+           "mg_tree_adapt", "mg_tree_build_times",
            "mg_set_rhs", "mg_set_eps", "mg_set_phi", "mg_get_phi", "mg_vcycle", "mg_fmg",
            "mg_residual_norm", "mg_solve", "mg_adjoint", "mg_tree_destroy", "mg_last_error",
            "mg_launch_count", "mg_time_sweeps", "mg_residual_norm_noalloc", "mg_sweep_variant",
@@ -64,6 +65,8 @@ def load():
     L.mg_tree_leaf_blocks.argtypes = [vp, vp]
     L.mg_set_bc_plane.argtypes = [vp, C.c_int, C.c_int, vp]
     L.mg_tree_finalize.argtypes = [vp, vp]
+    L.mg_tree_adapt.argtypes = [vp, C.c_int, vp, C.c_int, vp, C.POINTER(vp)]
+    L.mg_tree_build_times.argtypes = [vp, dp]
     for n in ("mg_set_rhs", "mg_set_eps", "mg_set_phi", "mg_get_phi"):
         getattr(L, n).argtypes = [vp, vp]
     L.mg_vcycle.argtypes = [vp, C.c_int, C.POINTER(mg_params)]

@@ -118,6 +118,9 @@ struct mg_tree {
     double lo[3] = {0, 0, 0}, hi[3] = {1, 1, 1};
     double helm = 0.0;
     std::vector<int32_t> refine;  // 4 per entry
+    // wall seconds of the mesh build: host tables, device setup, sweep
+    // autotuning (FP64, at finalize), phi transfer (a tree made by adapt)
+    double build_s[4] = {0, 0, 0, 0};
     bool built = false, finalized = false, singular = false, bc_dirty = false;
     bool var_eps = false;
     std::vector<mg::LevelHost> lev;           // levels (one tree) or segments (batch)
@@ -204,6 +207,8 @@ void residual_wait(mg_tree *t, double *out3);
 double leaf_mean(mg_tree *t, const double *rleaf);
 void add_e_to_phi(mg_tree *t, const float *e, double *phi);
 void sub_scalar(mg_tree *t, double *x, double c, long long n);  // x[0..n) -= c
+// phi of old carried to the leaf blocks nid of the adapted mesh nt (see k_transfer)
+int transfer_phi(mg_tree *old, mg_tree *nt, const std::vector<int> &nid, const std::vector<int> &src);
 void copy_eps_to_f32(mg_tree *t);
 // FP64 face coefficients of every cell into t->d_wface (eps ghosts current)
 void face_coef(mg_tree *t);

@@ -3248,6 +3248,78 @@ void residual_norm(mg_tree *t, Fields<double> &F, int homog, double *out3, doubl
     residual_wait(t, out3);
 }
 
+// ---------------------------------------------------- mesh adaptation ---
+// Carry phi to an adapted mesh (Sec. 2.5, "Adapting the grid structure").
+// New leaf block nid[q] takes, for src[q] >= 0, the cells of old block
+// src[q] (a leaf, or a block whose refinement was removed: its covered
+// cells hold the mean of its former children after a refresh); for
+// src[q] <= -2 it is a new child of old leaf block -2 - src[q] and takes
+// that block's prolongation (Sec. 2.3): (2 c0 + c_x + c_y)/4 in 2D,
+// (c0 + c_x + c_y + c_z)/4 in 3D, c_d the parent neighbour on the fine
+// cell's side, parent ghosts included.  One CTA per new leaf block.
+template <int D>
+__global__ void __launch_bounds__(256) k_transfer(const BlockDesc *__restrict__ OB, const double *__restrict__ OX,
+                                                  const double *__restrict__ OXG, const BlockDesc *__restrict__ NB,
+                                                  const int *__restrict__ nid, const int *__restrict__ src,
+                                                  double *__restrict__ NX) {
+    const BlockDesc &b = NB[nid[blockIdx.x]];
+    const int s = src[blockIdx.x], n = b.n, C = cells_of<D>(n);
+    if (s >= 0) {
+        const BlockDesc &o = OB[s];
+        for (int c = threadIdx.x; c < C; c += blockDim.x) NX[b.cell_off + c] = OX[o.cell_off + c];
+        return;
+    }
+    const BlockDesc &p = OB[-2 - s];
+    const int pn = p.n, FCp = face_of<D>(pn);
+    // parent value at (i, j, k), at most one coordinate outside the parent
+    auto pval = [&](int i, int j, int k) -> double {
+        if (i < 0) return OXG[p.ghost_off + 0 * FCp + (D == 2 ? j : j + pn * k)];
+        if (i >= pn) return OXG[p.ghost_off + 1 * FCp + (D == 2 ? j : j + pn * k)];
+        if (j < 0) return OXG[p.ghost_off + 2 * FCp + (D == 2 ? i : i + pn * k)];
+        if (j >= pn) return OXG[p.ghost_off + 3 * FCp + (D == 2 ? i : i + pn * k)];
+        if (D == 3) {
+            if (k < 0) return OXG[p.ghost_off + 4 * FCp + i + pn * j];
+            if (k >= pn) return OXG[p.ghost_off + 5 * FCp + i + pn * j];
+        }
+        return OX[p.cell_off + cidx<D>(pn, i, j, k)];
+    };
+    for (int c = threadIdx.x; c < C; c += blockDim.x) {
+        int i, j, k;
+        cell_of(c, n, D, i, j, k);
+        const int a = b.poff[0] + i / 2, e = b.poff[1] + j / 2, f = D == 3 ? b.poff[2] + k / 2 : 0;
+        const int sx = ((b.ijk[0] * n + i) & 1) ? 1 : -1, sy = ((b.ijk[1] * n + j) & 1) ? 1 : -1,
+                  sz = ((b.ijk[2] * n + k) & 1) ? 1 : -1;
+        const double v0 = pval(a, e, f);
+        double nbs = pval(a + sx, e, f);
+        nbs += pval(a, e + sy, f);
+        if (D == 3) nbs += pval(a, e, f + sz);
+        NX[b.cell_off + c] = D == 2 ? (2.0 * v0 + nbs) / 4.0 : (v0 + nbs) / 4.0;
+    }
+}
+
+int transfer_phi(mg_tree *old, mg_tree *nt, const std::vector<int> &nid, const std::vector<int> &src) {
+    refresh<double>(old, old->f64, 0);  // covered cells and ghosts of the old mesh
+    if (!nid.empty()) {
+        int *d = nullptr;
+        if (cudaMalloc((void **)&d, sizeof(int) * 2 * nid.size()) != cudaSuccess) return check_cuda("transfer alloc");
+        cudaMemcpyAsync(d, nid.data(), sizeof(int) * nid.size(), cudaMemcpyHostToDevice, nt->stream);
+        cudaMemcpyAsync(d + nid.size(), src.data(), sizeof(int) * src.size(), cudaMemcpyHostToDevice, nt->stream);
+        ++nt->launches;
+        if (nt->dim == 2)
+            launch_k(k_transfer<2>, (int)nid.size(), 128, 0, nt->stream, (const BlockDesc *)old->d_blocks,
+                     (const double *)old->f64.X, (const double *)old->f64.XG, (const BlockDesc *)nt->d_blocks,
+                     (const int *)d, (const int *)(d + nid.size()), nt->f64.X);
+        else
+            launch_k(k_transfer<3>, (int)nid.size(), 256, 0, nt->stream, (const BlockDesc *)old->d_blocks,
+                     (const double *)old->f64.X, (const double *)old->f64.XG, (const BlockDesc *)nt->d_blocks,
+                     (const int *)d, (const int *)(d + nid.size()), nt->f64.X);
+        cudaStreamSynchronize(nt->stream);
+        cudaFree(d);
+    }
+    refresh<double>(nt, nt->f64, 0);
+    return check_cuda("transfer");
+}
+
 __global__ void k_sub_scalar(double *__restrict__ x, double c, long long n) {
     pdl_entry();
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)

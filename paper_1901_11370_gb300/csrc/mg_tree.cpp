@@ -3,6 +3,8 @@
 // inverse, and the C ABI declared in include/mg.h.
 #include <algorithm>
 #include <array>
+#include <chrono>
+#include <unordered_map>
 #include <atomic>
 #include <thread>
 #include <cmath>
@@ -95,8 +97,13 @@ extern "C" int mg_tree_refine(mg_tree *t, int n, const int32_t *e) {
 // than coarse_max cells; above it the refined levels.  Per level the
 // covered blocks come first, then the leaves, each in Morton order.
 
+static double seconds_since(std::chrono::steady_clock::time_point t0) {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+}
+
 static int build(mg_tree *t) {
     if (t->built) return MG_OK;
+    const auto t0 = std::chrono::steady_clock::now();
     const int D = t->dim;
     struct Lv { int n, depth, nblk[3]; std::vector<std::array<int, 3>> b; };
     std::vector<Lv> lv;
@@ -297,6 +304,7 @@ static int build(mg_tree *t) {
     t->cvec_total = t->ns;
     t->max_nc = t->nc;
     t->built = true;
+    t->build_s[0] = seconds_since(t0);
     return MG_OK;
 }
 
@@ -558,6 +566,7 @@ extern "C" int mg_tree_finalize(mg_tree *t, void *stream) {
     if (t->finalized) return fail(MG_ERR_STATE, "already finalized");
     int rc = build(t);
     if (rc) return rc;
+    const auto t1 = std::chrono::steady_clock::now();
     annotate_segments(t);
     CK(cudaGetDevice(&t->device));
     CK(cudaDeviceGetAttribute(&t->nsm, cudaDevAttrMultiProcessorCount, t->device));
@@ -593,10 +602,16 @@ extern "C" int mg_tree_finalize(mg_tree *t, void *stream) {
         t->f64.W = t->d_wface;
         face_coef(t);
     }
+    CK(cudaStreamSynchronize(t->stream));
+    t->build_s[1] = seconds_since(t1);
+    const auto t2 = std::chrono::steady_clock::now();
     tune_sweeps<double>(t, t->f64);  // fields and ghosts are still zero here
     CK(cudaMemsetAsync(t->f64.X, 0, sizeof(double) * t->ncells, t->stream));
     refresh<double>(t, t->f64, 0);
-    return check_cuda("finalize");
+    rc = check_cuda("finalize");
+    CK(cudaStreamSynchronize(t->stream));
+    t->build_s[2] = seconds_since(t2);
+    return rc;
 }
 
 #define NEED_FINAL(t)                                                            \
@@ -604,6 +619,116 @@ extern "C" int mg_tree_finalize(mg_tree *t, void *stream) {
         if (!(t)) return fail(MG_ERR_ARG, "null tree");                           \
         if (!(t)->finalized) return fail(MG_ERR_STATE, "tree not finalized");     \
     } while (0)
+
+extern "C" int mg_tree_build_times(mg_tree *t, double *out4) {
+    if (!t || !out4) return fail(MG_ERR_ARG, "null argument");
+    for (int i = 0; i < 4; i++) out4[i] = t->build_s[i];
+    return MG_OK;
+}
+
+// ------------------------------------------------------------- adapt ----
+// A new mesh from a finalized one (Sec. 2.5, "Adapting the grid structure"):
+// the refinement list of t with the listed leaf blocks refined and the
+// listed refinements (of blocks whose children are all leaves) undone;
+// phi is carried over on the device (k_transfer).
+
+static uint64_t block_key(int depth, int i, int j, int k) {
+    return ((uint64_t)(depth + 128) << 56) | ((uint64_t)i << 36) | ((uint64_t)j << 18) | (uint64_t)k;
+}
+
+extern "C" int mg_tree_adapt(mg_tree *t, int n_add, const int32_t *add, int n_remove, const int32_t *remove,
+                             mg_tree **out) {
+    NEED_FINAL(t);
+    if (!out || n_add < 0 || n_remove < 0 || (n_add > 0 && !add) || (n_remove > 0 && !remove))
+        return fail(MG_ERR_ARG, "bad adapt arguments");
+    if (t->is_batch) return fail(MG_ERR_ARG, "adapt takes a single tree");
+    *out = nullptr;
+    const int D = t->dim;
+    // blocks of t by (depth, coordinates): global id, and whether a leaf
+    std::unordered_map<uint64_t, int> old_id;
+    old_id.reserve(t->blocks.size() * 2);
+    for (const LevelHost &L : t->lev)
+        for (int b = 0; b < L.nb; b++) {
+            const BlockDesc &q = t->blocks[L.first + b];
+            if (q.ijk[0] >= (1 << 18) || q.ijk[1] >= (1 << 18) || q.ijk[2] >= (1 << 18))
+                return fail(MG_ERR_ARG, "mesh too large to adapt");
+            old_id[block_key(L.depth, q.ijk[0], q.ijk[1], q.ijk[2])] = L.first + b;
+        }
+    auto is_leaf = [&](int g) { return !(t->blocks[g].flags & 1); };
+    auto rec = [&](const int32_t *e) { return std::array<int, 4>{e[0], e[1], e[2], D == 3 ? e[3] : 0}; };
+    auto find = [&](const std::array<int, 4> &r) -> int {
+        if (r[1] < 0 || r[2] < 0 || r[3] < 0 || r[1] >= (1 << 18) || r[2] >= (1 << 18) || r[3] >= (1 << 18))
+            return -1;
+        auto it = old_id.find(block_key(r[0], r[1], r[2], r[3]));
+        return it == old_id.end() ? -1 : it->second;
+    };
+    // refined blocks of t (depth >= 0), then the requested changes
+    std::map<std::array<int, 4>, char> ref;
+    for (size_t e = 0; e < t->refine.size() / 4; e++) ref[rec(&t->refine[4 * e])] = 1;
+    for (int r = 0; r < n_remove; r++) {
+        const auto q = rec(remove + 4 * r);
+        auto it = ref.find(q);
+        if (it == ref.end() || !it->second) return fail(MG_ERR_ARG, "removed refinement does not exist");
+        for (int c = 0; c < (1 << D); c++) {
+            const int g = find({q[0] + 1, 2 * q[1] + (c & 1), 2 * q[2] + ((c >> 1) & 1), D == 3 ? 2 * q[3] + ((c >> 2) & 1) : 0});
+            if (g < 0 || !is_leaf(g)) return fail(MG_ERR_ARG, "a removed refinement has refined children");
+        }
+        it->second = 0;
+    }
+    for (int a = 0; a < n_add; a++) {
+        const auto q = rec(add + 4 * a);
+        const int g = q[0] >= 0 ? find(q) : -1;
+        if (g < 0 || !is_leaf(g)) return fail(MG_ERR_ARG, "refined block is not a leaf of the mesh");
+        auto it = ref.find(q);
+        if (it != ref.end()) return fail(MG_ERR_ARG, "block both refined and coarsened");
+        ref[q] = 1;
+    }
+    mg_tree *nt = nullptr;
+    int rc = mg_tree_create(D, t->N, t->geom, &t->bc, t->base, t->lo, t->hi, t->coarse_max, t->helm, &nt);
+    if (rc) return rc;
+    for (const auto &kv : ref)
+        if (kv.second) nt->refine.insert(nt->refine.end(), kv.first.begin(), kv.first.end());
+    // boundary planes of the levels both meshes have (same depth, same size)
+    if ((rc = build(nt))) {
+        const std::string msg = mg_last_error();
+        mg_tree_destroy(nt);
+        return fail(rc, msg);
+    }
+    for (LevelHost &NL : nt->lev)
+        for (const LevelHost &OL : t->lev)
+            if (OL.depth == NL.depth && OL.n == NL.n)
+                for (int f = 0; f < 6; f++) NL.bc[f] = OL.bc[f];
+    if ((rc = mg_tree_finalize(nt, t->stream))) {
+        const std::string msg = mg_last_error();
+        mg_tree_destroy(nt);
+        return fail(rc, msg);
+    }
+    // source of every new leaf block: the same block of t, or its parent
+    const auto t0 = std::chrono::steady_clock::now();
+    std::vector<int> nid, src;
+    for (const LevelHost &L : nt->lev)
+        for (int b = L.nref; b < L.nb; b++) {
+            const BlockDesc &q = nt->blocks[L.first + b];
+            int g = find({L.depth, q.ijk[0], q.ijk[1], q.ijk[2]});
+            if (g < 0) {
+                const int p = find({L.depth - 1, q.ijk[0] / 2, q.ijk[1] / 2, D == 3 ? q.ijk[2] / 2 : 0});
+                if (p < 0 || !is_leaf(p)) {
+                    mg_tree_destroy(nt);
+                    return fail(MG_ERR_ARG, "adapted block without a source block");
+                }
+                g = -2 - p;
+            }
+            nid.push_back(L.first + b);
+            src.push_back(g);
+        }
+    if ((rc = transfer_phi(t, nt, nid, src))) {
+        mg_tree_destroy(nt);
+        return rc;
+    }
+    nt->build_s[3] = seconds_since(t0);
+    *out = nt;
+    return MG_OK;
+}
 
 // device status word: a bounded wait inside a kernel gave up (reported once)
 static int check_status(mg_tree *t) {
