@@ -141,7 +141,9 @@ int mg_tree_finalize(mg_tree *t, void *cuda_stream);
  * mean of its former children where a refinement was removed), a new child
  * takes the prolongation of Sec. 2.3 of its parent's values, parent ghosts
  * included.  Right-hand side and eps start at 0 and 1: set them for the
- * new mesh.  t is not changed (its covered cells and ghosts are refreshed);
+ * new mesh.  The sweep kernel of each level is the one t uses at the same
+ * depth (the default kernel at a new depth): no second autotuning.
+ * t is not changed (its covered cells and ghosts are refreshed);
  * *out receives the new handle, which the caller destroys.  Errors:
  * MG_ERR_ARG (a record names no such leaf or refinement, a removed
  * refinement has refined children, t is a batch), MG_ERR_BALANCE (the new
@@ -154,8 +156,10 @@ int mg_tree_adapt(mg_tree *t, int n_add, const int32_t *add, int n_remove, const
  * mg_tree_build_times -- wall seconds of this tree's construction: out4[0]
  * host tables (levels, neighbours, offsets), out4[1] device setup
  * (allocation, uploads, coarsest-level inverse), out4[2] FP64 sweep
- * autotuning at finalize, out4[3] the phi transfer of mg_tree_adapt (0 for
- * a tree not made by it).  Host pointer; entries not reached yet are 0.
+ * autotuning at finalize (0 for a tree made by mg_tree_adapt, which takes
+ * over the old tree's choices), out4[3] the phi transfer of mg_tree_adapt
+ * (0 for a tree not made by it).  Host pointer; entries not reached yet
+ * are 0.
  */
 int mg_tree_build_times(mg_tree *t, double *out4);
 

@@ -180,6 +180,9 @@ struct mg_tree {
     cudaStream_t cap_stream = nullptr;
     bool use_graphs = true;
     std::vector<int> sweep_choice[2];  // autotuned sweep variant per level (FP64, FP32); -1 default
+    // a tree made by adapt: sweep variants by level depth taken over from the
+    // old tree instead of autotuning (per precision; empty: tune)
+    std::map<int, int> tune_hint[2];
 };
 
 namespace mg {

@@ -97,6 +97,18 @@ extern "C" int mg_tree_refine(mg_tree *t, int n, const int32_t *e) {
 // than coarse_max cells; above it the refined levels.  Per level the
 // covered blocks come first, then the leaves, each in Morton order.
 
+// sweep variants of a tree made by adapt: the old tree's choice at the same
+// level depth (-1, the default kernel, where the depth is new)
+static bool apply_tune_hint(mg_tree *t, int prec) {
+    if (t->tune_hint[prec].empty()) return false;
+    t->sweep_choice[prec].assign(t->lev.size(), -1);
+    for (size_t l = 0; l < t->lev.size(); l++) {
+        auto it = t->tune_hint[prec].find(t->lev[l].depth);
+        if (it != t->tune_hint[prec].end()) t->sweep_choice[prec][l] = it->second;
+    }
+    return true;
+}
+
 static double seconds_since(std::chrono::steady_clock::time_point t0) {
     return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
 }
@@ -605,7 +617,7 @@ extern "C" int mg_tree_finalize(mg_tree *t, void *stream) {
     CK(cudaStreamSynchronize(t->stream));
     t->build_s[1] = seconds_since(t1);
     const auto t2 = std::chrono::steady_clock::now();
-    tune_sweeps<double>(t, t->f64);  // fields and ghosts are still zero here
+    if (!apply_tune_hint(t, 0)) tune_sweeps<double>(t, t->f64);  // fields and ghosts are still zero here
     CK(cudaMemsetAsync(t->f64.X, 0, sizeof(double) * t->ncells, t->stream));
     refresh<double>(t, t->f64, 0);
     rc = check_cuda("finalize");
@@ -698,6 +710,10 @@ extern "C" int mg_tree_adapt(mg_tree *t, int n_add, const int32_t *add, int n_re
         for (const LevelHost &OL : t->lev)
             if (OL.depth == NL.depth && OL.n == NL.n)
                 for (int f = 0; f < 6; f++) NL.bc[f] = OL.bc[f];
+    // sweep kernels: the old tree's choices by depth, no second autotuning
+    for (int prec = 0; prec < 2; prec++)
+        for (size_t l = 0; l < t->sweep_choice[prec].size() && l < t->lev.size(); l++)
+            nt->tune_hint[prec][t->lev[l].depth] = t->sweep_choice[prec][l];
     if ((rc = mg_tree_finalize(nt, t->stream))) {
         const std::string msg = mg_last_error();
         mg_tree_destroy(nt);
@@ -953,7 +969,7 @@ static int ensure_f32(mg_tree *t) {
     if (fresh) drop_graphs(t);
     if ((rc = alloc_fields(t, t->f32, t->var_eps))) return rc;
     if (t->var_eps) copy_eps_to_f32(t);
-    if (fresh) {
+    if (fresh && !apply_tune_hint(t, 1)) {
         tune_sweeps<float>(t, t->f32);  // freshly zeroed fields: the sweeps leave them zero
         if ((rc = check_cuda("tune"))) return rc;
     }
