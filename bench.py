@@ -544,6 +544,8 @@ def run_profile_batch():
         torch.cuda.synchronize()
         if rep:
             torch.cuda.nvtx.range_pop()
+    print("segments (n, group, blocks, covered, coarsest):",
+          " ".join("%d/%d/%d/%d/%d" % (q["n"], q["group"], q["nb"], q["nref"], q["coarsest"]) for q in b.segments()))
     print("profile batch32 done: %d launches" % b.launch_count())
 
 
