@@ -1645,6 +1645,194 @@ __global__ void __launch_bounds__(kMaxThreads) k_prolong_tma(KParams P, int firs
     if (tid == 0) bulk_wait0();
 }
 
+// Row-wise form of k_prolong_tma for 3D 8^3 blocks with 8^3 parents (128
+// threads).  Same staging and arithmetic; what changes is the work split,
+// because k_prolong_tma is bound by its per-cell index work:
+//  - the correction box x^H - x^H_old over the parent octant and its face
+//    halo is built one parent row (4 cells + x halo) per thread;
+//  - each thread corrects half a fine row (4 cells) with one vector load and
+//    store, and pushes the same-level and physical ghosts of its cells from
+//    registers: x faces take its row's end cell, y and z faces its 4 cells,
+//    which are contiguous in the ghost face;
+//  - refinement ghosts also need the inward cell of another row; they are
+//    formed after the barrier from shared memory, as before.
+template <class T>
+__global__ void __launch_bounds__(128) k_prolong_rows(KParams P, int first, int nblocks, Fields<T> F) {
+    pdl_entry();
+    constexpr int n = 8, C = 512, FC = 64, GH = 384;
+    constexpr int DESC = (int)((sizeof(BlockDesc) + sizeof(LevelDesc)) / sizeof(T));
+    constexpr int PD = (int)(sizeof(BlockDesc) / sizeof(T));
+    constexpr int STAGE = DESC + PD + C + 2 * (C + GH);
+    using V = typename Vec16<T>::type;
+    constexpr int VW = 16 / sizeof(T);  // elements per 16-byte vector
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t bars[2];
+    __shared__ int s_abort;
+    __shared__ __align__(16) T box[36 * 8];  // rows (c, e) of 6 used entries a, padded to 8
+    T *stage0 = reinterpret_cast<T *>(smem_raw);
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        fence_mbar_init();
+        s_abort = 0;
+    }
+    __syncthreads();
+    auto issue = [&](int it, int g) {  // thread 0 only
+        T *st = stage0 + (it & 1) * STAGE;
+        const BlockDesc *bd = P.B + g;
+        const int par = bd->parent;
+        const long long co = bd->cell_off, pco = P.B[par].cell_off, pgo = P.B[par].ghost_off;
+        uint64_t *bar = &bars[it & 1];
+        fence_async_smem();
+        mbar_expect_tx(bar, (uint32_t)(sizeof(T) * STAGE));
+        bulk_g2s(st, bd, sizeof(BlockDesc), bar);
+        bulk_g2s(reinterpret_cast<char *>(st) + sizeof(BlockDesc), P.L + bd->lev, sizeof(LevelDesc), bar);
+        bulk_g2s(st + DESC, P.B + par, sizeof(BlockDesc), bar);
+        T *d = st + DESC + PD;
+        bulk_g2s(d, F.X + co, sizeof(T) * C, bar);
+        bulk_g2s(d + C, F.X + pco, sizeof(T) * C, bar);
+        bulk_g2s(d + 2 * C, F.XG + pgo, sizeof(T) * GH, bar);
+        bulk_g2s(d + 2 * C + GH, F.V + pco, sizeof(T) * C, bar);
+        bulk_g2s(d + 3 * C + GH, F.VG + pgo, sizeof(T) * GH, bar);
+    };
+    int g = blockIdx.x;
+    if (tid == 0 && g < nblocks) issue(0, first + g);
+    // fine half-row of this thread: row r = (j, k), cells i = 4h .. 4h + 3
+    const int r = tid >> 1, h = tid & 1, j = r & 7, k = r >> 3;
+    const int cc = (j >> 1) + 1, ee = (k >> 1) + 1, sy = (j & 1) ? 1 : -1, sz = (k & 1) ? 1 : -1;
+    for (int it = 0; g < nblocks; it++, g += gridDim.x) {
+        {
+            uint32_t tries = 0;
+            while (!mbar_try_wait(&bars[it & 1], (it >> 1) & 1))
+                if (++tries > kWaitLimit) {
+                    atomicExch(P.status, 1);
+                    s_abort = 1;
+                    break;
+                }
+        }
+        __syncthreads();
+        if (s_abort) break;
+        if (tid == 0 && g + (int)gridDim.x < nblocks) {
+            bulk_wait_read0();  // the other stage's store has left shared memory
+            issue(it + 1, first + g + gridDim.x);
+        }
+        T *st = stage0 + (it & 1) * STAGE;
+        const BlockDesc &b = *reinterpret_cast<const BlockDesc *>(st);
+        const LevelDesc &L = *reinterpret_cast<const LevelDesc *>(reinterpret_cast<const char *>(st) + sizeof(BlockDesc));
+        T *xs = st + DESC + PD;
+        const T *px = xs + C, *pg = px + C, *pv = pg + GH, *pvg = pv + C;
+        // correction box: row (c, e) holds parent cells (p0 - 1 + a, pj, pk), a = 0..5
+        if (tid < 36) {
+            const int c = tid % 6, e = tid / 6, p0 = b.poff[0];
+            const int pj = b.poff[1] + c - 1, pk = b.poff[2] + e - 1;
+            const bool jin = pj >= 0 && pj < n, kin = pk >= 0 && pk < n;
+            T *row = box + tid * 8;
+            const T *xr = nullptr, *vr = nullptr;
+            if (jin && kin) {
+                const int o = 8 * (pj + 8 * pk);
+                xr = px + o + p0;
+                vr = pv + o + p0;
+                row[0] = p0 > 0 ? xr[-1] - vr[-1] : pg[pj + 8 * pk] - pvg[pj + 8 * pk];
+                row[5] = p0 + 4 < n ? xr[4] - vr[4] : pg[FC + pj + 8 * pk] - pvg[FC + pj + 8 * pk];
+            } else if (kin) {  // y-face ghost row (i along the face is contiguous)
+                const int o = (pj < 0 ? 2 : 3) * FC + p0 + 8 * pk;
+                xr = pg + o;
+                vr = pvg + o;
+            } else if (jin) {  // z-face ghost row
+                const int o = (pk < 0 ? 4 : 5) * FC + p0 + 8 * pj;
+                xr = pg + o;
+                vr = pvg + o;
+            }
+            if (xr) {  // the box's edge rows are never read
+                T xv[4], vv[4];
+#pragma unroll
+                for (int q = 0; q < 4; q += VW) {
+                    vscatter(xv + q, *reinterpret_cast<const V *>(xr + q));
+                    vscatter(vv + q, *reinterpret_cast<const V *>(vr + q));
+                }
+#pragma unroll
+                for (int q = 0; q < 4; q++) row[1 + q] = xv[q] - vv[q];
+            }
+        }
+        __syncthreads();
+        // correct this thread's 4 cells: (c0 + c_x + c_y + c_z)/4 (Sec. 2.3)
+        T v[4];
+        {
+            const T *R0 = box + (ee * 6 + cc) * 8, *Ry = box + (ee * 6 + cc + sy) * 8, *Rz = box + ((ee + sz) * 6 + cc) * 8;
+            T *xr = xs + 8 * r + 4 * h;
+#pragma unroll
+            for (int q = 0; q < 4; q += VW) vscatter(v + q, *reinterpret_cast<const V *>(xr + q));
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                const int a = ((4 * h + q) >> 1) + 1, sx = (q & 1) ? 1 : -1;
+                T nbs = R0[a + sx];
+                nbs += Ry[a];
+                nbs += Rz[a];
+                v[q] = v[q] + (R0[a] + nbs) / (T)4;
+            }
+#pragma unroll
+            for (int q = 0; q < 4; q += VW) {
+                V w;
+                if constexpr (sizeof(T) == 4) w = make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]);
+                else w = make_double2(v[q], v[q + 1]);
+                *reinterpret_cast<V *>(xr + q) = w;
+            }
+        }
+        // same-level and physical ghosts of these cells, from registers
+        {
+            const int fx = h ? 1 : 0, nbx = b.nbr[fx];  // x face: the row's end cell
+            const T ve = h ? v[3] : v[0];
+            if (nbx >= 0) F.XG[b.push[fx] + j + 8 * k] = ve;
+            else if (nbx == -1)
+                F.XG[b.ghost_off + fx * FC + j + 8 * k] =
+                    phys_ghost<T>(P, L, fx, ve, bc_value(P, L, b, 3, fx, I3{h ? n - 1 : 0, j, k}));
+            auto face4 = [&](int face, int u0, int t1) {  // 4 cells at u0.. on face, t1: their second coordinate
+                const int nb = b.nbr[face];
+                if (nb >= 0) {
+                    T *dst = F.XG + b.push[face] + u0;
+#pragma unroll
+                    for (int q = 0; q < 4; q += VW) {
+                        V w;
+                        if constexpr (sizeof(T) == 4) w = make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]);
+                        else w = make_double2(v[q], v[q + 1]);
+                        *reinterpret_cast<V *>(dst + q) = w;
+                    }
+                } else if (nb == -1) {
+                    const int d = face >> 1, edge = (face & 1) ? n - 1 : 0;
+#pragma unroll
+                    for (int q = 0; q < 4; q++) {
+                        const I3 ii = d == 1 ? I3{4 * h + q, edge, t1} : I3{4 * h + q, t1, edge};
+                        F.XG[b.ghost_off + face * FC + u0 + q] =
+                            phys_ghost<T>(P, L, face, v[q], bc_value(P, L, b, 3, face, ii));
+                    }
+                }
+            };
+            if (j == 0 || j == n - 1) face4(j ? 3 : 2, 4 * h + 8 * k, k);  // y face: u = i + 8 k
+            if (k == 0 || k == n - 1) face4(k ? 5 : 4, 4 * h + 8 * j, j);  // z face: u = i + 8 j
+        }
+        fence_async_smem();
+        __syncthreads();
+        if (tid == 0) {
+            bulk_s2g(F.X + b.cell_off, xs, sizeof(T) * C);
+            bulk_commit();
+        }
+        const int cfm = cf_faces(b, 3);
+        if (cfm)
+            for (int t = tid; t < GH; t += 128) {
+                const int face = t / FC, u = t - face * FC;
+                if (!((cfm >> face) & 1)) continue;
+                const I3 ii = face_cell<3>(n, face, u, false);
+                I3 dd = ii;
+                put(dd, face >> 1, (face & 1) ? n - 2 : 1);
+                F.XG[b.ghost_off + t] = cf_ghost<T, 3>(P, L, b, face, ii, xs[cidx<3>(n, ii.x, ii.y, ii.z)],
+                                                       xs[cidx<3>(n, dd.x, dd.y, dd.z)], F.X, F.XG, b.nbr[face], false);
+            }
+        __syncthreads();  // box and stage reads done before the next block
+    }
+    if (tid == 0) bulk_wait0();
+}
+
 // Restriction with the FAS residual for 8- and 16-cell blocks, persistent
 // and TMA-staged like the sweep: the child block (descriptor, x, ghosts, f,
 // eps) and its parent's descriptor arrive by cp.async.bulk; child residuals
@@ -2927,6 +3115,13 @@ template <class T, int D> struct Launch {
     static void prolong(mg_tree *t, const KParams &P, int l, Fields<T> &F) {
         const LevelHost &L = t->lev[l];
         ++t->launches;
+        if (D == 3 && L.n == 8 && L.parent_same_n) {
+            const size_t smt = prolong_tma_smem(L);
+            set_smem(k_prolong_rows<T>, smt);
+            const int grid = std::min(L.nb, resident_ctas(k_prolong_rows<T>, 128, smt) * t->nsm);
+            launch_k(k_prolong_rows<T>, grid, 128, smt, t->stream, P, L.first, L.nb, F);
+            return;
+        }
         if ((L.n == 8 || L.n == 16) && prolong_tma_smem(L) <= 200 * 1024) {
             const size_t smt = prolong_tma_smem(L);
             auto kern = L.n == 8 ? k_prolong_tma<T, D, 8> : k_prolong_tma<T, D, 16>;
