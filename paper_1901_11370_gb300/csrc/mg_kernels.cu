@@ -1647,11 +1647,11 @@ __global__ void __launch_bounds__(kMaxThreads) k_prolong_tma(KParams P, int firs
 
 // Row-wise form of k_prolong_tma for 3D 8^3 blocks with 8^3 parents (128
 // threads).  Same staging and arithmetic; what changes is the work split,
-// because k_prolong_tma is bound by its per-cell index work:
-//  - the correction box x^H - x^H_old over the parent octant and its face
-//    halo is built one parent row (4 cells + x halo) per thread;
+// because k_prolong_tma is bound by its per-cell index work and barriers:
 //  - each thread corrects half a fine row (4 cells) with one vector load and
-//    store, and pushes the same-level and physical ghosts of its cells from
+//    store, reading the 8 parent values x^H - x^H_old it needs straight from
+//    the staged parent (no shared correction box, no barrier for it);
+//  - it pushes the same-level and physical ghosts of its cells from
 //    registers: x faces take its row's end cell, y and z faces its 4 cells,
 //    which are contiguous in the ghost face;
 //  - refinement ghosts also need the inward cell of another row; they are
@@ -1668,9 +1668,9 @@ __global__ void __launch_bounds__(128) k_prolong_rows(KParams P, int first, int 
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bars[2];
     __shared__ int s_abort;
-    __shared__ __align__(16) T box[36 * 8];  // rows (c, e) of 6 used entries a, padded to 8
     T *stage0 = reinterpret_cast<T *>(smem_raw);
     const int tid = threadIdx.x;
+    constexpr int ISSUER = 127;  // stage copies and stores
     if (tid == 0) {
         mbar_init(&bars[0], 1);
         mbar_init(&bars[1], 1);
@@ -1678,7 +1678,7 @@ __global__ void __launch_bounds__(128) k_prolong_rows(KParams P, int first, int 
         s_abort = 0;
     }
     __syncthreads();
-    auto issue = [&](int it, int g) {  // thread 0 only
+    auto issue = [&](int it, int g) {  // thread ISSUER only
         T *st = stage0 + (it & 1) * STAGE;
         const BlockDesc *bd = P.B + g;
         const int par = bd->parent;
@@ -1697,10 +1697,10 @@ __global__ void __launch_bounds__(128) k_prolong_rows(KParams P, int first, int 
         bulk_g2s(d + 3 * C + GH, F.VG + pgo, sizeof(T) * GH, bar);
     };
     int g = blockIdx.x;
-    if (tid == 0 && g < nblocks) issue(0, first + g);
+    if (tid == ISSUER && g < nblocks) issue(0, first + g);
     // fine half-row of this thread: row r = (j, k), cells i = 4h .. 4h + 3
     const int r = tid >> 1, h = tid & 1, j = r & 7, k = r >> 3;
-    const int cc = (j >> 1) + 1, ee = (k >> 1) + 1, sy = (j & 1) ? 1 : -1, sz = (k & 1) ? 1 : -1;
+    const int sy = (j & 1) ? 1 : -1, sz = (k & 1) ? 1 : -1;
     for (int it = 0; g < nblocks; it++, g += gridDim.x) {
         {
             uint32_t tries = 0;
@@ -1713,7 +1713,7 @@ __global__ void __launch_bounds__(128) k_prolong_rows(KParams P, int first, int 
         }
         __syncthreads();
         if (s_abort) break;
-        if (tid == 0 && g + (int)gridDim.x < nblocks) {
+        if (tid == ISSUER && g + (int)gridDim.x < nblocks) {
             bulk_wait_read0();  // the other stage's store has left shared memory
             issue(it + 1, first + g + gridDim.x);
         }
@@ -1722,54 +1722,36 @@ __global__ void __launch_bounds__(128) k_prolong_rows(KParams P, int first, int 
         const LevelDesc &L = *reinterpret_cast<const LevelDesc *>(reinterpret_cast<const char *>(st) + sizeof(BlockDesc));
         T *xs = st + DESC + PD;
         const T *px = xs + C, *pg = px + C, *pv = pg + GH, *pvg = pv + C;
-        // correction box: row (c, e) holds parent cells (p0 - 1 + a, pj, pk), a = 0..5
-        if (tid < 36) {
-            const int c = tid % 6, e = tid / 6, p0 = b.poff[0];
-            const int pj = b.poff[1] + c - 1, pk = b.poff[2] + e - 1;
-            const bool jin = pj >= 0 && pj < n, kin = pk >= 0 && pk < n;
-            T *row = box + tid * 8;
-            const T *xr = nullptr, *vr = nullptr;
-            if (jin && kin) {
-                const int o = 8 * (pj + 8 * pk);
-                xr = px + o + p0;
-                vr = pv + o + p0;
-                row[0] = p0 > 0 ? xr[-1] - vr[-1] : pg[pj + 8 * pk] - pvg[pj + 8 * pk];
-                row[5] = p0 + 4 < n ? xr[4] - vr[4] : pg[FC + pj + 8 * pk] - pvg[FC + pj + 8 * pk];
-            } else if (kin) {  // y-face ghost row (i along the face is contiguous)
-                const int o = (pj < 0 ? 2 : 3) * FC + p0 + 8 * pk;
-                xr = pg + o;
-                vr = pvg + o;
-            } else if (jin) {  // z-face ghost row
-                const int o = (pk < 0 ? 4 : 5) * FC + p0 + 8 * pj;
-                xr = pg + o;
-                vr = pvg + o;
-            }
-            if (xr) {  // the box's edge rows are never read
-                T xv[4], vv[4];
-#pragma unroll
-                for (int q = 0; q < 4; q += VW) {
-                    vscatter(xv + q, *reinterpret_cast<const V *>(xr + q));
-                    vscatter(vv + q, *reinterpret_cast<const V *>(vr + q));
-                }
-#pragma unroll
-                for (int q = 0; q < 4; q++) row[1 + q] = xv[q] - vv[q];
-            }
-        }
-        __syncthreads();
-        // correct this thread's 4 cells: (c0 + c_x + c_y + c_z)/4 (Sec. 2.3)
+        // correct this thread's 4 cells, (c0 + c_x + c_y + c_z)/4 of x^H - x^H_old
+        // (Sec. 2.3): parent cells p0, p0 + 1 of row (pj, pk), their x
+        // neighbours p0 - 1, p0 + 2 and the two cells of the neighbour rows on
+        // the cells' y and z sides, parent ghosts where these leave the parent
         T v[4];
         {
-            const T *R0 = box + (ee * 6 + cc) * 8, *Ry = box + (ee * 6 + cc + sy) * 8, *Rz = box + ((ee + sz) * 6 + cc) * 8;
+            const int p0 = b.poff[0] + 2 * h, pj = b.poff[1] + (j >> 1), pk = b.poff[2] + (k >> 1);
+            auto dx = [&](const T *x, const T *o, int idx) { return x[idx] - o[idx]; };
+            const int row = 8 * (pj + 8 * pk);
+            const T xm = p0 > 0 ? dx(px, pv, row + p0 - 1) : dx(pg, pvg, pj + 8 * pk);
+            const T x0 = dx(px, pv, row + p0), x1 = dx(px, pv, row + p0 + 1);
+            const T xp = p0 + 2 < n ? dx(px, pv, row + p0 + 2) : dx(pg, pvg, FC + pj + 8 * pk);
+            const int qj = pj + sy, qk = pk + sz;
+            const int ry = qj >= 0 && qj < n ? 8 * (qj + 8 * pk) : -1, rz = qk >= 0 && qk < n ? 8 * (pj + 8 * qk) : -1;
+            const int gy = (qj < 0 ? 2 : 3) * FC + 8 * pk, gz = (qk < 0 ? 4 : 5) * FC + 8 * pj;
+            const T y0 = ry >= 0 ? dx(px, pv, ry + p0) : dx(pg, pvg, gy + p0);
+            const T y1 = ry >= 0 ? dx(px, pv, ry + p0 + 1) : dx(pg, pvg, gy + p0 + 1);
+            const T z0 = rz >= 0 ? dx(px, pv, rz + p0) : dx(pg, pvg, gz + p0);
+            const T z1 = rz >= 0 ? dx(px, pv, rz + p0 + 1) : dx(pg, pvg, gz + p0 + 1);
+            const T c0[4] = {x0, x0, x1, x1}, cx[4] = {xm, x1, x0, xp};
+            const T cy[4] = {y0, y0, y1, y1}, cz[4] = {z0, z0, z1, z1};
             T *xr = xs + 8 * r + 4 * h;
 #pragma unroll
             for (int q = 0; q < 4; q += VW) vscatter(v + q, *reinterpret_cast<const V *>(xr + q));
 #pragma unroll
             for (int q = 0; q < 4; q++) {
-                const int a = ((4 * h + q) >> 1) + 1, sx = (q & 1) ? 1 : -1;
-                T nbs = R0[a + sx];
-                nbs += Ry[a];
-                nbs += Rz[a];
-                v[q] = v[q] + (R0[a] + nbs) / (T)4;
+                T nbs = cx[q];
+                nbs += cy[q];
+                nbs += cz[q];
+                v[q] = v[q] + (c0[q] + nbs) / (T)4;
             }
 #pragma unroll
             for (int q = 0; q < 4; q += VW) {
@@ -1813,7 +1795,7 @@ __global__ void __launch_bounds__(128) k_prolong_rows(KParams P, int first, int 
         }
         fence_async_smem();
         __syncthreads();
-        if (tid == 0) {
+        if (tid == ISSUER) {
             bulk_s2g(F.X + b.cell_off, xs, sizeof(T) * C);
             bulk_commit();
         }
@@ -1828,9 +1810,9 @@ __global__ void __launch_bounds__(128) k_prolong_rows(KParams P, int first, int 
                 F.XG[b.ghost_off + t] = cf_ghost<T, 3>(P, L, b, face, ii, xs[cidx<3>(n, ii.x, ii.y, ii.z)],
                                                        xs[cidx<3>(n, dd.x, dd.y, dd.z)], F.X, F.XG, b.nbr[face], false);
             }
-        __syncthreads();  // box and stage reads done before the next block
+        __syncthreads();  // stage reads done before the next block
     }
-    if (tid == 0) bulk_wait0();
+    if (tid == ISSUER) bulk_wait0();
 }
 
 // Restriction with the FAS residual for 8- and 16-cell blocks, persistent
