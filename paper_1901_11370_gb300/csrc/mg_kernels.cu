@@ -1983,6 +1983,148 @@ __global__ void __launch_bounds__(kMaxThreads, 4) k_restrict_tma(KParams P, int 
     }
 }
 
+// Row-wise form of k_restrict_tma for 3D 8^3 blocks with 8^3 parents and
+// the constant-coefficient Cartesian operator (128 threads).  Each thread
+// takes half a fine row (4 cells): its rows and ghost rows come in with
+// vector loads, it forms the 4 child residuals (same terms and order as
+// k_restrict_tma), sums x and the residual over the cell pairs under each
+// parent cell, and two warp shuffles add the other three rows of the 2x2x2
+// children (j +- 1: lane ^ 2, k +- 1: lane ^ 16).  One thread per parent cell
+// pair then stores the means; the parent ghosts beside the octant are pushed
+// from a small shared copy, as in k_restrict_tma.
+template <class T>
+__global__ void __launch_bounds__(128) k_restrict_rows(KParams P, int first, int nblocks, Fields<T> F) {
+    pdl_entry();
+    constexpr int n = 8, C = 512, FC = 64, GH = 384;
+    constexpr int DESC = (int)((sizeof(BlockDesc) + sizeof(LevelDesc)) / sizeof(T));
+    constexpr int STAGE = 2 * DESC + 2 * C + GH;
+    using V = typename Vec16<T>::type;
+    constexpr int VW = 16 / sizeof(T);
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t bars[2];
+    __shared__ int s_abort;
+    __shared__ T oct[64];  // parent cells under the block, [ck][cj][ci]
+    T *stage0 = reinterpret_cast<T *>(smem_raw);
+    const int tid = threadIdx.x;
+    constexpr int ISSUER = 127;  // stage copies
+    if (tid == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        fence_mbar_init();
+        s_abort = 0;
+    }
+    __syncthreads();
+    auto issue = [&](int it, int g) {  // thread ISSUER only
+        T *st = stage0 + (it & 1) * STAGE;
+        const long long co = P.B[g].cell_off, go = P.B[g].ghost_off;
+        const int par = P.B[g].parent;
+        uint64_t *bar = &bars[it & 1];
+        fence_async_smem();
+        mbar_expect_tx(bar, (uint32_t)(sizeof(T) * STAGE));
+        bulk_g2s(st, P.B + g, sizeof(BlockDesc), bar);
+        bulk_g2s(reinterpret_cast<char *>(st) + sizeof(BlockDesc), P.L + P.B[g].lev, sizeof(LevelDesc), bar);
+        bulk_g2s(st + DESC, P.B + par, sizeof(BlockDesc), bar);
+        bulk_g2s(reinterpret_cast<char *>(st + DESC) + sizeof(BlockDesc), P.L + P.B[par].lev, sizeof(LevelDesc), bar);
+        bulk_g2s(st + 2 * DESC, F.X + co, sizeof(T) * C, bar);
+        bulk_g2s(st + 2 * DESC + C, F.XG + go, sizeof(T) * GH, bar);
+        bulk_g2s(st + 2 * DESC + C + GH, F.F + co, sizeof(T) * C, bar);
+    };
+    int g = blockIdx.x;
+    if (tid == ISSUER && g < nblocks) issue(0, first + g);
+    const int r = tid >> 1, h = tid & 1, j = r & 7, k = r >> 3;
+    auto ld4 = [&](const T *src, T *dst) {
+#pragma unroll
+        for (int q = 0; q < 4; q += VW) vscatter(dst + q, *reinterpret_cast<const V *>(src + q));
+    };
+    for (int it = 0; g < nblocks; it++, g += gridDim.x) {
+        {
+            uint32_t tries = 0;
+            while (!mbar_try_wait(&bars[it & 1], (it >> 1) & 1))
+                if (++tries > kWaitLimit) {
+                    atomicExch(P.status, 1);
+                    s_abort = 1;
+                    break;
+                }
+        }
+        __syncthreads();
+        if (s_abort) break;
+        if (tid == ISSUER && g + (int)gridDim.x < nblocks) issue(it + 1, first + g + gridDim.x);
+        const T *st = stage0 + (it & 1) * STAGE;
+        const BlockDesc &b = *reinterpret_cast<const BlockDesc *>(st);
+        const BlockDesc &p = *reinterpret_cast<const BlockDesc *>(st + DESC);
+        const LevelDesc &L = *reinterpret_cast<const LevelDesc *>(reinterpret_cast<const char *>(st) + sizeof(BlockDesc));
+        const LevelDesc &PL = *reinterpret_cast<const LevelDesc *>(reinterpret_cast<const char *>(st + DESC) + sizeof(BlockDesc));
+        const T *xs = st + 2 * DESC, *gs = xs + C, *fs = gs + GH;
+        const T w0 = lv_ih<T>(L, 0), w1 = lv_ih<T>(L, 1), w2 = lv_ih<T>(L, 2), helm = kp_helm<T>(P);
+        // x of cells 4h - 1 .. 4h + 4 of row (j, k) and the 4 cells of the
+        // neighbour rows (face ghost rows outside the block)
+        T xr[6], dn[4], up[4], bk[4], fw[4], f4[4];
+        ld4(xs + 8 * r + 4 * h, xr + 1);
+        xr[0] = h ? xs[8 * r + 3] : gs[j + 8 * k];
+        xr[5] = h ? gs[FC + j + 8 * k] : xs[8 * r + 4];
+        ld4(j > 0 ? xs + 8 * (r - 1) + 4 * h : gs + 2 * FC + 4 * h + 8 * k, dn);
+        ld4(j < n - 1 ? xs + 8 * (r + 1) + 4 * h : gs + 3 * FC + 4 * h + 8 * k, up);
+        ld4(k > 0 ? xs + 8 * (r - 8) + 4 * h : gs + 4 * FC + 4 * h + 8 * j, bk);
+        ld4(k < n - 1 ? xs + 8 * (r + 8) + 4 * h : gs + 5 * FC + 4 * h + 8 * j, fw);
+        ld4(fs + 8 * r + 4 * h, f4);
+        T res[4];
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            const T xc = xr[1 + q];
+            T lap = 0;
+            lap += w0 * (xr[q] - xc);
+            lap += w0 * (xr[q + 2] - xc);
+            lap += w1 * (dn[q] - xc);
+            lap += w1 * (up[q] - xc);
+            lap += w2 * (bk[q] - xc);
+            lap += w2 * (fw[q] - xc);
+            res[q] = f4[q] - (lap - helm * xc);
+        }
+        // sums under parent cells 2h, 2h + 1: this row's pairs, then rows j ^ 1, k ^ 1
+        T s4[4] = {xr[1] + xr[2], xr[3] + xr[4], res[0] + res[1], res[2] + res[3]};
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            s4[q] += __shfl_xor_sync(0xffffffffu, s4[q], 2);
+            s4[q] += __shfl_xor_sync(0xffffffffu, s4[q], 16);
+        }
+        if (!(j & 1) && !(k & 1)) {
+            const int ci = 2 * h, cj = j >> 1, ck = k >> 1;
+            const T inv = (T)(1.0 / 8);
+            const int pc = cidx<3>(n, b.poff[0] + ci, b.poff[1] + cj, b.poff[2] + ck);
+            F.X[p.cell_off + pc] = s4[0] * inv;
+            F.X[p.cell_off + pc + 1] = s4[1] * inv;
+            F.F[p.cell_off + pc] = s4[2] * inv;
+            F.F[p.cell_off + pc + 1] = s4[3] * inv;
+            oct[(ck * 4 + cj) * 4 + ci] = s4[0] * inv;
+            oct[(ck * 4 + cj) * 4 + ci + 1] = s4[1] * inv;
+        }
+        __syncthreads();
+        // parent ghosts beside the octant: faces where it meets the parent's boundary
+        if (tid < 96) {
+            const int face = tid >> 4, v = tid & 15, d = face >> 1, s = face & 1;
+            const int off = d == 0 ? b.poff[0] : d == 1 ? b.poff[1] : b.poff[2];
+            if (s ? (off + 4 == n) : (off == 0)) {
+                const int a = v & 3, c = v >> 2, e = s ? 3 : 0, e2 = s ? 2 : 1;  // octant-local
+                const I3 lo = d == 0 ? I3{e, a, c} : (d == 1 ? I3{a, e, c} : I3{a, c, e});
+                const I3 li = d == 0 ? I3{e2, a, c} : (d == 1 ? I3{a, e2, c} : I3{a, c, e2});
+                const I3 ii{b.poff[0] + lo.x, b.poff[1] + lo.y, b.poff[2] + lo.z};
+                const int u = d == 0 ? ii.y + n * ii.z : (d == 1 ? ii.x + n * ii.z : ii.x + n * ii.y);
+                const T cv = oct[(lo.z * 4 + lo.y) * 4 + lo.x];
+                const int nb = p.nbr[face];
+                if (nb >= 0) {
+                    F.XG[p.push[face] + u] = cv;
+                } else if (nb == -1) {
+                    F.XG[p.ghost_off + face * FC + u] = phys_ghost<T>(P, PL, face, cv, bc_value(P, PL, p, 3, face, ii));
+                } else {
+                    F.XG[p.ghost_off + face * FC + u] =
+                        cf_ghost<T, 3>(P, PL, p, face, ii, cv, oct[(li.z * 4 + li.y) * 4 + li.x], F.X, F.XG, nb, false);
+                }
+            }
+        }
+        __syncthreads();  // oct and stage reads done before the next block
+    }
+}
+
 // ---------------------------------------------- divergence cleaning -----
 // Second-order central differences on leaf blocks (Sec. 4.1): component d of
 // a vector field X (with ghosts) adds (X(c+e_d) - X(c-e_d)) / (2 h_d) to the
@@ -3054,6 +3196,11 @@ template <class T, int D> struct Launch {
             if (is_flat(L)) {
                 launch_k(k_restrict_flat<T, D>, flat_grid(t, (long long)L.nb * cells_of<D>(L.n / 2)), 256, 0, t->stream, P, L.first, L.nb, L.n, F.X, F.XG, F.F, F.E, F.EG, F.F, 1);
                 for (int q : L.parents) plain[q] = 1;
+            } else if (D == 3 && L.n == 8 && L.parent_same_n && !F.W && !F.E && t->geom == MG_CART) {
+                const size_t sr = 2 * sizeof(T) * (2 * C8 + GH8) + 4 * (sizeof(BlockDesc) + sizeof(LevelDesc));
+                set_smem(k_restrict_rows<T>, sr);
+                const int grid = std::min(L.nb, resident_ctas(k_restrict_rows<T>, 128, sr) * t->nsm);
+                launch_k(k_restrict_rows<T>, grid, 128, sr, t->stream, P, L.first, L.nb, F);
             } else if ((L.n == 8 || L.n == 16) && smt + sizeof(T) * C8 <= 200 * 1024) {
                 auto kern = L.n == 8 ? k_restrict_tma<T, D, 8> : k_restrict_tma<T, D, 16>;
                 const int thr = transfer_threads(threads_for(C8));
