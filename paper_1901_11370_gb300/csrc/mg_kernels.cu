@@ -1815,6 +1815,152 @@ __global__ void __launch_bounds__(128) k_prolong_rows(KParams P, int first, int 
     if (tid == ISSUER) bulk_wait0();
 }
 
+// k_prolong_rows for 2D 16^2 blocks with 16^2 parents (64 threads): thread
+// (j, q) corrects cells 4q .. 4q + 3 of fine row j, (2 c0 + c_x + c_y)/4 of
+// x^H - x^H_old from parent cells p0, p0 + 1 of row pj, their x neighbours
+// and the two cells of row pj +- 1 on the cells' y side.  Same staging and
+// arithmetic as k_prolong_tma<T, 2, 16>.
+template <class T>
+__global__ void __launch_bounds__(64) k_prolong_rows2(KParams P, int first, int nblocks, Fields<T> F) {
+    pdl_entry();
+    constexpr int n = 16, C = 256, FC = 16, GH = 64;
+    constexpr int DESC = (int)((sizeof(BlockDesc) + sizeof(LevelDesc)) / sizeof(T));
+    constexpr int PD = (int)(sizeof(BlockDesc) / sizeof(T));
+    constexpr int STAGE = DESC + PD + C + 2 * (C + GH);
+    using V = typename Vec16<T>::type;
+    constexpr int VW = 16 / sizeof(T);
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t bars[2];
+    __shared__ int s_abort;
+    T *stage0 = reinterpret_cast<T *>(smem_raw);
+    const int tid = threadIdx.x;
+    constexpr int ISSUER = 63;  // stage copies and stores
+    if (tid == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        fence_mbar_init();
+        s_abort = 0;
+    }
+    __syncthreads();
+    auto issue = [&](int it, int g) {  // thread ISSUER only
+        T *st = stage0 + (it & 1) * STAGE;
+        const BlockDesc *bd = P.B + g;
+        const int par = bd->parent;
+        const long long co = bd->cell_off, pco = P.B[par].cell_off, pgo = P.B[par].ghost_off;
+        uint64_t *bar = &bars[it & 1];
+        fence_async_smem();
+        mbar_expect_tx(bar, (uint32_t)(sizeof(T) * STAGE));
+        bulk_g2s(st, bd, sizeof(BlockDesc), bar);
+        bulk_g2s(reinterpret_cast<char *>(st) + sizeof(BlockDesc), P.L + bd->lev, sizeof(LevelDesc), bar);
+        bulk_g2s(st + DESC, P.B + par, sizeof(BlockDesc), bar);
+        T *d = st + DESC + PD;
+        bulk_g2s(d, F.X + co, sizeof(T) * C, bar);
+        bulk_g2s(d + C, F.X + pco, sizeof(T) * C, bar);
+        bulk_g2s(d + 2 * C, F.XG + pgo, sizeof(T) * GH, bar);
+        bulk_g2s(d + 2 * C + GH, F.V + pco, sizeof(T) * C, bar);
+        bulk_g2s(d + 3 * C + GH, F.VG + pgo, sizeof(T) * GH, bar);
+    };
+    int g = blockIdx.x;
+    if (tid == ISSUER && g < nblocks) issue(0, first + g);
+    const int j = tid >> 2, qd = tid & 3, sy = (j & 1) ? 1 : -1;
+    for (int it = 0; g < nblocks; it++, g += gridDim.x) {
+        {
+            uint32_t tries = 0;
+            while (!mbar_try_wait(&bars[it & 1], (it >> 1) & 1))
+                if (++tries > kWaitLimit) {
+                    atomicExch(P.status, 1);
+                    s_abort = 1;
+                    break;
+                }
+        }
+        __syncthreads();
+        if (s_abort) break;
+        if (tid == ISSUER && g + (int)gridDim.x < nblocks) {
+            bulk_wait_read0();  // the other stage's store has left shared memory
+            issue(it + 1, first + g + gridDim.x);
+        }
+        T *st = stage0 + (it & 1) * STAGE;
+        const BlockDesc &b = *reinterpret_cast<const BlockDesc *>(st);
+        const LevelDesc &L = *reinterpret_cast<const LevelDesc *>(reinterpret_cast<const char *>(st) + sizeof(BlockDesc));
+        T *xs = st + DESC + PD;
+        const T *px = xs + C, *pg = px + C, *pv = pg + GH, *pvg = pv + C;
+        T v[4];
+        {
+            const int p0 = b.poff[0] + 2 * qd, pj = b.poff[1] + (j >> 1), qj = pj + sy;
+            auto dx = [&](const T *x, const T *o, int idx) { return x[idx] - o[idx]; };
+            const int row = n * pj;
+            const T xm = p0 > 0 ? dx(px, pv, row + p0 - 1) : dx(pg, pvg, pj);
+            const T x0 = dx(px, pv, row + p0), x1 = dx(px, pv, row + p0 + 1);
+            const T xp = p0 + 2 < n ? dx(px, pv, row + p0 + 2) : dx(pg, pvg, FC + pj);
+            const int ry = qj >= 0 && qj < n ? n * qj : -1, gy = (qj < 0 ? 2 : 3) * FC;
+            const T y0 = ry >= 0 ? dx(px, pv, ry + p0) : dx(pg, pvg, gy + p0);
+            const T y1 = ry >= 0 ? dx(px, pv, ry + p0 + 1) : dx(pg, pvg, gy + p0 + 1);
+            const T c0[4] = {x0, x0, x1, x1}, cx[4] = {xm, x1, x0, xp}, cy[4] = {y0, y0, y1, y1};
+            T *xr = xs + n * j + 4 * qd;
+#pragma unroll
+            for (int q = 0; q < 4; q += VW) vscatter(v + q, *reinterpret_cast<const V *>(xr + q));
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                T nbs = cx[q];
+                nbs += cy[q];
+                v[q] = v[q] + ((T)2 * c0[q] + nbs) / (T)4;
+            }
+#pragma unroll
+            for (int q = 0; q < 4; q += VW) {
+                V w;
+                if constexpr (sizeof(T) == 4) w = make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]);
+                else w = make_double2(v[q], v[q + 1]);
+                *reinterpret_cast<V *>(xr + q) = w;
+            }
+        }
+        // same-level and physical ghosts of these cells, from registers
+        if (qd == 0 || qd == 3) {  // x faces: the row's end cells
+            const int fx = qd ? 1 : 0, nbx = b.nbr[fx];
+            const T ve = qd ? v[3] : v[0];
+            if (nbx >= 0) F.XG[b.push[fx] + j] = ve;
+            else if (nbx == -1)
+                F.XG[b.ghost_off + fx * FC + j] = phys_ghost<T>(P, L, fx, ve, bc_value(P, L, b, 2, fx, I3{qd ? n - 1 : 0, j, 0}));
+        }
+        if (j == 0 || j == n - 1) {  // y faces: 4 cells, contiguous in the ghost face (u = i)
+            const int face = j ? 3 : 2, nb = b.nbr[face];
+            if (nb >= 0) {
+                T *dst = F.XG + b.push[face] + 4 * qd;
+#pragma unroll
+                for (int q = 0; q < 4; q += VW) {
+                    V w;
+                    if constexpr (sizeof(T) == 4) w = make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]);
+                    else w = make_double2(v[q], v[q + 1]);
+                    *reinterpret_cast<V *>(dst + q) = w;
+                }
+            } else if (nb == -1) {
+#pragma unroll
+                for (int q = 0; q < 4; q++)
+                    F.XG[b.ghost_off + face * FC + 4 * qd + q] =
+                        phys_ghost<T>(P, L, face, v[q], bc_value(P, L, b, 2, face, I3{4 * qd + q, j, 0}));
+            }
+        }
+        fence_async_smem();
+        __syncthreads();
+        if (tid == ISSUER) {
+            bulk_s2g(F.X + b.cell_off, xs, sizeof(T) * C);
+            bulk_commit();
+        }
+        const int cfm = cf_faces(b, 2);
+        if (cfm)
+            for (int t = tid; t < GH; t += 64) {
+                const int face = t / FC, u = t - face * FC;
+                if (!((cfm >> face) & 1)) continue;
+                const I3 ii = face_cell<2>(n, face, u, false);
+                I3 dd = ii;
+                put(dd, face >> 1, (face & 1) ? n - 2 : 1);
+                F.XG[b.ghost_off + t] = cf_ghost<T, 2>(P, L, b, face, ii, xs[cidx<2>(n, ii.x, ii.y, ii.z)],
+                                                       xs[cidx<2>(n, dd.x, dd.y, dd.z)], F.X, F.XG, b.nbr[face], false);
+            }
+        __syncthreads();  // stage reads done before the next block
+    }
+    if (tid == ISSUER) bulk_wait0();
+}
+
 // Restriction with the FAS residual for 8- and 16-cell blocks, persistent
 // and TMA-staged like the sweep: the child block (descriptor, x, ghosts, f,
 // eps) and its parent's descriptor arrive by cp.async.bulk; child residuals
@@ -3249,6 +3395,13 @@ template <class T, int D> struct Launch {
             set_smem(k_prolong_rows<T>, smt);
             const int grid = std::min(L.nb, resident_ctas(k_prolong_rows<T>, 128, smt) * t->nsm);
             launch_k(k_prolong_rows<T>, grid, 128, smt, t->stream, P, L.first, L.nb, F);
+            return;
+        }
+        if (D == 2 && L.n == 16 && L.parent_same_n && sizeof(T) == 4) {  // FP64: the CTA-per-cell form timed faster
+            const size_t smt = prolong_tma_smem(L);
+            set_smem(k_prolong_rows2<T>, smt);
+            const int grid = std::min(L.nb, resident_ctas(k_prolong_rows2<T>, 64, smt) * t->nsm);
+            launch_k(k_prolong_rows2<T>, grid, 64, smt, t->stream, P, L.first, L.nb, F);
             return;
         }
         if ((L.n == 8 || L.n == 16) && prolong_tma_smem(L) <= 200 * 1024) {
