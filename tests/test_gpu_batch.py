@@ -207,3 +207,18 @@ def test_batch_jacobi_matches_oracle_per_tree(mg):
         o.fmg()
         o.vcycle(2)
         assert rel_diff(phi[b.offsets[i]:b.offsets[i + 1]], o.get_phi()) < TOL, p.name
+
+
+@pytest.mark.parametrize("name", ["cyl", "cart2d", "gauss3d"])
+def test_batch_mixed_precision_converges_like_fp64(mg, name):
+    """The FP32 cycles (their own restriction and prolongation kernels) cut
+    the residual per cycle as the FP64 cycles do: the defect-correction
+    solve needs at most one cycle more than the FP64 solve.  A wrong weight
+    or side in an FP32 transfer would slow it down well beyond that."""
+    probs = FORESTS[name]
+    b = make_batch(mg, probs)
+    c64, _ = b.solve(1e-10, 40)
+    import torch
+    b.set_phi(torch.zeros(b.n_leaf, dtype=torch.float64, device="cuda"))
+    c32, rel = b.solve(1e-10, 40, precision=mg.MG_FP32_DC)
+    assert (rel <= 1e-10).all() and c32 <= c64 + 1, (c32, c64)

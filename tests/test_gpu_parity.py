@@ -134,6 +134,10 @@ def test_mixed_precision_defect_correction(mg, name):
     t, o = both(mg, p)
     cyc, rel = t.solve(1e-10, 40, fmg_first=True, precision=mg.MG_FP32_DC)
     assert rel <= 1e-10
+    # the FP32 cycles converge like the FP64 ones (a wrong FP32 transfer
+    # kernel would cost cycles)
+    c64, _ = mg.Tree.from_problem(p).solve(1e-10, 40, fmg_first=True)
+    assert cyc <= c64 + 1, (cyc, c64)
     r0 = o.residual_norm()[0]  # oracle phi = 0
     o.set_phi(t.get_phi().cpu().numpy())
     r = o.residual_norm()[0]
