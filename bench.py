@@ -116,14 +116,17 @@ def kernel_sha1(name):
 
 
 def measured_traffic(kernel, fname):
-    """DRAM bytes per cell from a committed ncu summary, or None when the
-    kernel source changed since the capture."""
+    """DRAM bytes per cell from a committed ncu summary (entries of
+    "key: value" lines separated by blank lines), or None when the kernel
+    has no entry or its source changed since the capture."""
     path = os.path.join(ROOT, "profiles", fname)
     try:
-        kv = dict(ln.split(":", 1) for ln in open(path) if ":" in ln and not ln.startswith("#"))
-        kv = {k.strip(): v.strip() for k, v in kv.items()}
-        if kv.get("kernel") == kernel and kv.get("source_sha1") == kernel_sha1(kernel):
-            return float(kv["dram_bytes_per_cell"])
+        text = "".join(ln for ln in open(path) if not ln.startswith("#"))
+        for entry in text.split("\n\n"):
+            kv = dict(ln.split(":", 1) for ln in entry.splitlines() if ":" in ln)
+            kv = {k.strip(): v.strip() for k, v in kv.items()}
+            if kv.get("kernel") == kernel and kv.get("source_sha1") == kernel_sha1(kernel):
+                return float(kv["dram_bytes_per_cell"])
     except Exception:
         pass
     return None
