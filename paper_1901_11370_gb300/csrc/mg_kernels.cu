@@ -2160,23 +2160,45 @@ __global__ void __launch_bounds__(128) k_restrict_rows(KParams P, int first, int
         s_abort = 0;
     }
     __syncthreads();
-    auto issue = [&](int it, int g) {  // thread ISSUER only
+    // offsets of a block and its parent for the stage copies; the issuer
+    // reads them two iterations ahead (the block's own fields one iteration
+    // before its parent's), so that a refill never waits on the table
+    struct Src { long long co, go; int par, lev, plev; };
+    auto own = [&](int g, Src &r) {
+        if (g < nblocks) {
+            const BlockDesc &q = P.B[first + g];
+            r.co = q.cell_off; r.go = q.ghost_off; r.par = q.parent; r.lev = q.lev;
+        }
+    };
+    auto parent = [&](int g, Src &r) {
+        if (g < nblocks) r.plev = P.B[r.par].lev;
+    };
+    auto issue = [&](int it, int g, const Src &r) {  // thread ISSUER only
         T *st = stage0 + (it & 1) * STAGE;
-        const long long co = P.B[g].cell_off, go = P.B[g].ghost_off;
-        const int par = P.B[g].parent;
         uint64_t *bar = &bars[it & 1];
         fence_async_smem();
         mbar_expect_tx(bar, (uint32_t)(sizeof(T) * STAGE));
-        bulk_g2s(st, P.B + g, sizeof(BlockDesc), bar);
-        bulk_g2s(reinterpret_cast<char *>(st) + sizeof(BlockDesc), P.L + P.B[g].lev, sizeof(LevelDesc), bar);
-        bulk_g2s(st + DESC, P.B + par, sizeof(BlockDesc), bar);
-        bulk_g2s(reinterpret_cast<char *>(st + DESC) + sizeof(BlockDesc), P.L + P.B[par].lev, sizeof(LevelDesc), bar);
-        bulk_g2s(st + 2 * DESC, F.X + co, sizeof(T) * C, bar);
-        bulk_g2s(st + 2 * DESC + C, F.XG + go, sizeof(T) * GH, bar);
-        bulk_g2s(st + 2 * DESC + C + GH, F.F + co, sizeof(T) * C, bar);
+        bulk_g2s(st, P.B + first + g, sizeof(BlockDesc), bar);
+        bulk_g2s(reinterpret_cast<char *>(st) + sizeof(BlockDesc), P.L + r.lev, sizeof(LevelDesc), bar);
+        bulk_g2s(st + DESC, P.B + r.par, sizeof(BlockDesc), bar);
+        bulk_g2s(reinterpret_cast<char *>(st + DESC) + sizeof(BlockDesc), P.L + r.plev, sizeof(LevelDesc), bar);
+        bulk_g2s(st + 2 * DESC, F.X + r.co, sizeof(T) * C, bar);
+        bulk_g2s(st + 2 * DESC + C, F.XG + r.go, sizeof(T) * GH, bar);
+        bulk_g2s(st + 2 * DESC + C + GH, F.F + r.co, sizeof(T) * C, bar);
     };
     int g = blockIdx.x;
-    if (tid == ISSUER && g < nblocks) issue(0, first + g);
+    Src n1{}, n2{};
+    if (tid == ISSUER) {
+        if (g < nblocks) {
+            Src r0{};
+            own(g, r0);
+            parent(g, r0);
+            issue(0, g, r0);
+        }
+        own(g + (int)gridDim.x, n1);
+        parent(g + (int)gridDim.x, n1);
+        own(g + 2 * (int)gridDim.x, n2);
+    }
     const int r = tid >> 1, h = tid & 1, j = r & 7, k = r >> 3;
     auto ld4 = [&](const T *src, T *dst) {
 #pragma unroll
@@ -2194,7 +2216,12 @@ __global__ void __launch_bounds__(128) k_restrict_rows(KParams P, int first, int
         }
         __syncthreads();
         if (s_abort) break;
-        if (tid == ISSUER && g + (int)gridDim.x < nblocks) issue(it + 1, first + g + gridDim.x);
+        if (tid == ISSUER) {
+            if (g + (int)gridDim.x < nblocks) issue(it + 1, g + gridDim.x, n1);
+            n1 = n2;
+            parent(g + 2 * (int)gridDim.x, n1);
+            own(g + 3 * (int)gridDim.x, n2);
+        }
         const T *st = stage0 + (it & 1) * STAGE;
         const BlockDesc &b = *reinterpret_cast<const BlockDesc *>(st);
         const BlockDesc &p = *reinterpret_cast<const BlockDesc *>(st + DESC);
