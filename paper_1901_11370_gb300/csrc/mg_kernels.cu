@@ -1678,26 +1678,47 @@ __global__ void __launch_bounds__(128) k_prolong_rows(KParams P, int first, int 
         s_abort = 0;
     }
     __syncthreads();
-    auto issue = [&](int it, int g) {  // thread ISSUER only
+    // offsets of a block and its parent for the stage copies; the issuer
+    // reads them two iterations ahead (the block's own fields one iteration
+    // before its parent's), so that a refill never waits on the table
+    struct Src { long long co, pco, pgo; int par, lev; };
+    auto own = [&](int g, Src &r) {
+        if (g < nblocks) {
+            const BlockDesc &q = P.B[first + g];
+            r.co = q.cell_off; r.par = q.parent; r.lev = q.lev;
+        }
+    };
+    auto parent = [&](int g, Src &r) {
+        if (g < nblocks) { r.pco = P.B[r.par].cell_off; r.pgo = P.B[r.par].ghost_off; }
+    };
+    auto issue = [&](int it, int g, const Src &r) {  // thread ISSUER only
         T *st = stage0 + (it & 1) * STAGE;
-        const BlockDesc *bd = P.B + g;
-        const int par = bd->parent;
-        const long long co = bd->cell_off, pco = P.B[par].cell_off, pgo = P.B[par].ghost_off;
         uint64_t *bar = &bars[it & 1];
         fence_async_smem();
         mbar_expect_tx(bar, (uint32_t)(sizeof(T) * STAGE));
-        bulk_g2s(st, bd, sizeof(BlockDesc), bar);
-        bulk_g2s(reinterpret_cast<char *>(st) + sizeof(BlockDesc), P.L + bd->lev, sizeof(LevelDesc), bar);
-        bulk_g2s(st + DESC, P.B + par, sizeof(BlockDesc), bar);
+        bulk_g2s(st, P.B + first + g, sizeof(BlockDesc), bar);
+        bulk_g2s(reinterpret_cast<char *>(st) + sizeof(BlockDesc), P.L + r.lev, sizeof(LevelDesc), bar);
+        bulk_g2s(st + DESC, P.B + r.par, sizeof(BlockDesc), bar);
         T *d = st + DESC + PD;
-        bulk_g2s(d, F.X + co, sizeof(T) * C, bar);
-        bulk_g2s(d + C, F.X + pco, sizeof(T) * C, bar);
-        bulk_g2s(d + 2 * C, F.XG + pgo, sizeof(T) * GH, bar);
-        bulk_g2s(d + 2 * C + GH, F.V + pco, sizeof(T) * C, bar);
-        bulk_g2s(d + 3 * C + GH, F.VG + pgo, sizeof(T) * GH, bar);
+        bulk_g2s(d, F.X + r.co, sizeof(T) * C, bar);
+        bulk_g2s(d + C, F.X + r.pco, sizeof(T) * C, bar);
+        bulk_g2s(d + 2 * C, F.XG + r.pgo, sizeof(T) * GH, bar);
+        bulk_g2s(d + 2 * C + GH, F.V + r.pco, sizeof(T) * C, bar);
+        bulk_g2s(d + 3 * C + GH, F.VG + r.pgo, sizeof(T) * GH, bar);
     };
     int g = blockIdx.x;
-    if (tid == ISSUER && g < nblocks) issue(0, first + g);
+    Src n1{}, n2{};
+    if (tid == ISSUER) {
+        if (g < nblocks) {
+            Src r0{};
+            own(g, r0);
+            parent(g, r0);
+            issue(0, g, r0);
+        }
+        own(g + (int)gridDim.x, n1);
+        parent(g + (int)gridDim.x, n1);
+        own(g + 2 * (int)gridDim.x, n2);
+    }
     // fine half-row of this thread: row r = (j, k), cells i = 4h .. 4h + 3
     const int r = tid >> 1, h = tid & 1, j = r & 7, k = r >> 3;
     const int sy = (j & 1) ? 1 : -1, sz = (k & 1) ? 1 : -1;
@@ -1713,9 +1734,14 @@ __global__ void __launch_bounds__(128) k_prolong_rows(KParams P, int first, int 
         }
         __syncthreads();
         if (s_abort) break;
-        if (tid == ISSUER && g + (int)gridDim.x < nblocks) {
-            bulk_wait_read0();  // the other stage's store has left shared memory
-            issue(it + 1, first + g + gridDim.x);
+        if (tid == ISSUER) {
+            if (g + (int)gridDim.x < nblocks) {
+                bulk_wait_read0();  // the other stage's store has left shared memory
+                issue(it + 1, g + gridDim.x, n1);
+            }
+            n1 = n2;
+            parent(g + 2 * (int)gridDim.x, n1);
+            own(g + 3 * (int)gridDim.x, n2);
         }
         T *st = stage0 + (it & 1) * STAGE;
         const BlockDesc &b = *reinterpret_cast<const BlockDesc *>(st);
