@@ -583,14 +583,15 @@ __global__ void __launch_bounds__(kMaxThreads, (D == 3 && NT == 16) ? 1 : 5) k_s
     if (tid < (int)(sizeof(LevelDesc) / 4))
         reinterpret_cast<int *>(&sL)[tid] = reinterpret_cast<const int *>(P.L + P.B[first].lev)[tid];
     __syncthreads();
-    auto issue = [&](int it, int g) {  // thread 0 only
+    // co, go, lev: the block's cell and ghost offsets and level (thread 0
+    // reads them one iteration ahead, so that a refill does not wait on them)
+    auto issue = [&](int it, int g, long long co, long long go, int lev) {  // thread 0 only
         T *st = stage0 + (it & 1) * stage_elems;
-        const long long co = P.B[g].cell_off, go = P.B[g].ghost_off;
         uint64_t *bar = &bars[it & 1];
         fence_async_smem();
         mbar_expect_tx(bar, tx_bytes);
         bulk_g2s(st, P.B + g, sizeof(BlockDesc), bar);
-        bulk_g2s(reinterpret_cast<char *>(st) + sizeof(BlockDesc), P.L + P.B[g].lev, sizeof(LevelDesc), bar);
+        bulk_g2s(reinterpret_cast<char *>(st) + sizeof(BlockDesc), P.L + lev, sizeof(LevelDesc), bar);
         bulk_g2s(st + DESC, F.X + co, sizeof(T) * C, bar);
         bulk_g2s(st + DESC + C, F.XG + go, sizeof(T) * GH, bar);
         bulk_g2s(st + DESC + C + GH, F.F + co, sizeof(T) * C, bar);
@@ -602,7 +603,22 @@ __global__ void __launch_bounds__(kMaxThreads, (D == 3 && NT == 16) ? 1 : 5) k_s
         }
     };
     int g = blockIdx.x;
-    if (tid == 0 && g < nblocks) issue(0, first + g);
+    long long rco = 0, rgo = 0;
+    int rlev = 0;
+    auto fetch = [&](int gn) {
+        if (gn < nblocks) {
+            rco = P.B[first + gn].cell_off;
+            rgo = P.B[first + gn].ghost_off;
+            rlev = P.B[first + gn].lev;
+        }
+    };
+    if (tid == 0) {
+        if (g < nblocks) {
+            fetch(g);
+            issue(0, first + g, rco, rgo, rlev);
+        }
+        fetch(g + (int)gridDim.x);
+    }
     // level descriptor: CTA-wide copy when every block shares it, else per block
     const bool cyl = P.geom == MG_CYL;
     const T helm = kp_helm<T>(P);
@@ -620,9 +636,12 @@ __global__ void __launch_bounds__(kMaxThreads, (D == 3 && NT == 16) ? 1 : 5) k_s
         if (s_abort) break;
         // every thread is past the previous block: its stage may be refilled
         // once its bulk store has read it
-        if (tid == 0 && g + (int)gridDim.x < nblocks) {
-            bulk_wait_read0();
-            issue(it + 1, first + g + gridDim.x);
+        if (tid == 0) {
+            if (g + (int)gridDim.x < nblocks) {
+                bulk_wait_read0();
+                issue(it + 1, first + g + gridDim.x, rco, rgo, rlev);
+            }
+            fetch(g + 2 * (int)gridDim.x);
         }
         T *st = stage0 + (it & 1) * stage_elems;
         const BlockDesc &b = *reinterpret_cast<const BlockDesc *>(st);
