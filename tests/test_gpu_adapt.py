@@ -138,3 +138,23 @@ def test_adapt_rejects_bad_requests(mg):
         codes.append(e.value.code)
     assert codes == [-1, -1, -1, -1, -2]
     t0.vcycle(1)  # the old tree is still usable
+
+
+def test_adapt_periodic_3d_matches_oracle(mg):
+    """Periodic in x and y, Dirichlet in z, 3D: parent ghosts across the
+    periodic faces feed the prolongation of blocks at the domain edge."""
+    bct = (W.BC_PERIODIC,) * 4 + (W.BC_DIRICHLET,) * 2
+    ref0 = [(0, 0, 1, 1), (0, 3, 1, 1), (0, 1, 1, 1), (0, 2, 3, 0)]
+    add, rem = [(0, 0, 0, 1), (0, 0, 1, 0), (1, 0, 2, 2)], [(0, 2, 3, 0)]  # (1, 0, 2, 2) wraps to (0, 3, 1, 1)
+    p0 = problem(3, 4, 16, ref0, lin3, bc_type=bct)
+    p1 = problem(3, 4, 16, changed(ref0, add, rem), lin3, bc_type=bct)
+    x = np.random.default_rng(13).standard_normal(W.n_leaf_cells(p0))
+    t0 = mg.Tree.from_problem(p0)
+    t0.set_phi(cuda(x))
+    t1 = t0.adapt(add, rem)
+    o0 = Oracle.from_problem(p0)
+    o0.set_phi(x)
+    o1 = Oracle.from_problem(p1)
+    o1.transfer_from(o0)
+    assert rel(t1.get_phi().cpu().numpy(), o1.get_phi()) < TOL
+

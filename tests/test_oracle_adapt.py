@@ -132,3 +132,36 @@ def test_refine_then_coarsen_is_restriction_of_prolongation(dim):
     assert np.array_equal(back[~inside], x[~inside])
     assert np.abs(back[inside] - want[inside]).max() <= 1e-14 * np.abs(x).max()
     assert np.abs(back[inside] - x[inside]).max() > 1e-3  # R P is not the identity
+
+
+def test_periodic_round_trip_wraps_the_neighbours():
+    """Uniform periodic 2D mesh: refine and coarsen back a block at the
+    domain edge.  Its cells take c0 + (sum of face neighbours - 4 c0)/8 with
+    the neighbours across the periodic faces taken from the other side."""
+    N, n0 = 8, 32
+    bct = (W.BC_PERIODIC,) * 4 + (W.BC_DIRICHLET,) * 2
+    p0 = problem(2, N, n0, [], bc_type=bct)
+    p1 = problem(2, N, n0, [(0, 0, 3, 0)], bc_type=bct)
+    x = np.random.default_rng(4).standard_normal(W.n_leaf_cells(p0))
+    x -= x.mean()
+    o0 = Oracle.from_problem(p0)
+    o0.set_phi(x)
+    o1 = Oracle.from_problem(p1)
+    o1.transfer_from(o0)
+    o2 = Oracle.from_problem(p0)
+    o2.transfer_from(o1)
+    back = o2.get_phi()
+    X, Y, Z, H = W.leaf_cell_centres(p0)
+    ii = np.floor(X / H[:, 0]).astype(int)
+    jj = np.floor(Y / H[:, 1]).astype(int)
+    g = np.zeros((n0, n0))
+    g[jj, ii] = x
+    inside = (ii // N == 0) & (jj // N == 3)
+    want = x.copy()
+    for m in np.nonzero(inside)[0]:
+        i, j = ii[m], jj[m]
+        nb = g[j, (i - 1) % n0] + g[j, (i + 1) % n0] + g[(j - 1) % n0, i] + g[(j + 1) % n0, i]
+        want[m] = x[m] + (nb - 4 * x[m]) / 8.0
+    assert np.array_equal(back[~inside], x[~inside])
+    assert np.abs(back[inside] - want[inside]).max() <= 1e-14 * np.abs(x).max()
+
