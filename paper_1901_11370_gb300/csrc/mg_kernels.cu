@@ -1371,17 +1371,30 @@ __global__ void __launch_bounds__(kMaxThreads) k_ghost_tma(KParams P, int first,
         s_abort = 0;
     }
     __syncthreads();
-    auto issue = [&](int it, int g) {  // thread 0 only
+    // co, lev: the block's cell offset and level (thread 0 reads them one
+    // iteration ahead, so that a refill does not wait on them)
+    auto issue = [&](int it, int g, long long co, int lev) {  // thread 0 only
         T *st = stage0 + (it & 1) * STAGE;
         uint64_t *bar = &bars[it & 1];
         fence_async_smem();
         mbar_expect_tx(bar, (uint32_t)(sizeof(T) * STAGE));
         bulk_g2s(st, P.B + g, sizeof(BlockDesc), bar);
-        bulk_g2s(reinterpret_cast<char *>(st) + sizeof(BlockDesc), P.L + P.B[g].lev, sizeof(LevelDesc), bar);
-        bulk_g2s(st + DESC, X + P.B[g].cell_off, sizeof(T) * C, bar);
+        bulk_g2s(reinterpret_cast<char *>(st) + sizeof(BlockDesc), P.L + lev, sizeof(LevelDesc), bar);
+        bulk_g2s(st + DESC, X + co, sizeof(T) * C, bar);
     };
     int g = blockIdx.x;
-    if (tid == 0 && g < nblocks) issue(0, first + g);
+    long long rco = 0;
+    int rlev = 0;
+    auto fetch = [&](int gn) {
+        if (gn < nblocks) { rco = P.B[first + gn].cell_off; rlev = P.B[first + gn].lev; }
+    };
+    if (tid == 0) {
+        if (g < nblocks) {
+            fetch(g);
+            issue(0, first + g, rco, rlev);
+        }
+        fetch(g + (int)gridDim.x);
+    }
     for (int it = 0; g < nblocks; it++, g += gridDim.x) {
         {
             uint32_t tries = 0;
@@ -1394,7 +1407,10 @@ __global__ void __launch_bounds__(kMaxThreads) k_ghost_tma(KParams P, int first,
         }
         __syncthreads();
         if (s_abort) break;
-        if (tid == 0 && g + (int)gridDim.x < nblocks) issue(it + 1, first + g + gridDim.x);
+        if (tid == 0) {
+            if (g + (int)gridDim.x < nblocks) issue(it + 1, first + g + gridDim.x, rco, rlev);
+            fetch(g + 2 * (int)gridDim.x);
+        }
         const T *st = stage0 + (it & 1) * STAGE;
         const BlockDesc &b = *reinterpret_cast<const BlockDesc *>(st);
         const LevelDesc &L = *reinterpret_cast<const LevelDesc *>(reinterpret_cast<const char *>(st) + sizeof(BlockDesc));
@@ -1443,14 +1459,15 @@ __global__ void __launch_bounds__(kMaxThreads) k_fas_tma(KParams P, int first, i
         s_abort = 0;
     }
     __syncthreads();
-    auto issue = [&](int it, int g) {  // thread 0 only
+    // co, go, lev: the block's cell and ghost offsets and level (thread 0
+    // reads them one iteration ahead, so that a refill does not wait on them)
+    auto issue = [&](int it, int g, long long co, long long go, int lev) {  // thread 0 only
         T *st = stage0 + (it & 1) * stage_elems;
-        const long long co = P.B[g].cell_off, go = P.B[g].ghost_off;
         uint64_t *bar = &bars[it & 1];
         fence_async_smem();
         mbar_expect_tx(bar, tx_bytes);
         bulk_g2s(st, P.B + g, sizeof(BlockDesc), bar);
-        bulk_g2s(reinterpret_cast<char *>(st) + sizeof(BlockDesc), P.L + P.B[g].lev, sizeof(LevelDesc), bar);
+        bulk_g2s(reinterpret_cast<char *>(st) + sizeof(BlockDesc), P.L + lev, sizeof(LevelDesc), bar);
         bulk_g2s(st + DESC, F.X + co, sizeof(T) * C, bar);
         bulk_g2s(st + DESC + C, F.XG + go, sizeof(T) * GH, bar);
         bulk_g2s(st + DESC + C + GH, F.F + co, sizeof(T) * C, bar);
@@ -1463,7 +1480,22 @@ __global__ void __launch_bounds__(kMaxThreads) k_fas_tma(KParams P, int first, i
     };
     const bool cyl = P.geom == MG_CYL;
     int g = blockIdx.x;
-    if (tid == 0 && g < nblocks) issue(0, first + g);
+    long long rco = 0, rgo = 0;
+    int rlev = 0;
+    auto fetch = [&](int gn) {
+        if (gn < nblocks) {
+            rco = P.B[first + gn].cell_off;
+            rgo = P.B[first + gn].ghost_off;
+            rlev = P.B[first + gn].lev;
+        }
+    };
+    if (tid == 0) {
+        if (g < nblocks) {
+            fetch(g);
+            issue(0, first + g, rco, rgo, rlev);
+        }
+        fetch(g + (int)gridDim.x);
+    }
     for (int it = 0; g < nblocks; it++, g += gridDim.x) {
         {
             uint32_t tries = 0;
@@ -1476,9 +1508,12 @@ __global__ void __launch_bounds__(kMaxThreads) k_fas_tma(KParams P, int first, i
         }
         __syncthreads();
         if (s_abort) break;
-        if (tid == 0 && g + (int)gridDim.x < nblocks) {
-            bulk_wait_read0();  // the other stage's stores have left shared memory
-            issue(it + 1, first + g + gridDim.x);
+        if (tid == 0) {
+            if (g + (int)gridDim.x < nblocks) {
+                bulk_wait_read0();  // the other stage's stores have left shared memory
+                issue(it + 1, first + g + gridDim.x, rco, rgo, rlev);
+            }
+            fetch(g + 2 * (int)gridDim.x);
         }
         T *st = stage0 + (it & 1) * stage_elems;
         const BlockDesc &b = *reinterpret_cast<const BlockDesc *>(st);
