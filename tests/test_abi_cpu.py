@@ -107,3 +107,23 @@ def test_calls_out_of_order_return_state_error(lib):
     assert t.L.mg_tree_refine(t._h, 1, ref.ctypes.data_as(C.c_void_p)) == -8
     assert t.L.mg_set_rhs(t._h, None) == -8
     assert t.L.mg_vcycle(t._h, 1, None) == -8
+
+
+def test_adapt_and_build_times_on_the_host(lib):
+    """mg_tree_adapt needs a finalized tree (MG_ERR_STATE before that, and
+    MG_ERR_ARG for null arguments); mg_tree_build_times reports the host
+    table time as soon as the tables exist and nothing for device steps not
+    taken yet."""
+    import ctypes as C
+    import paper_1901_11370_gb300 as mg
+    t = mg.Tree(3, 8, 0, (0,) * 6, (0,) * 6, (64, 64, 64), (0, 0, 0), (1, 1, 1), finalize=False)
+    out = (C.c_double * 4)()
+    t.levels()  # host tables (the wrapper's leaf count has built them already)
+    assert t.L.mg_tree_build_times(t._h, out) == 0
+    assert out[0] > 0 and out[1] == out[2] == out[3] == 0
+    h = C.c_void_p()
+    add = np.array([[0, 1, 1, 1]], np.int32)
+    assert t.L.mg_tree_adapt(t._h, 1, add.ctypes.data_as(C.c_void_p), 0, None, C.byref(h)) == -8
+    assert not h.value
+    assert t.L.mg_tree_adapt(None, 0, None, 0, None, C.byref(h)) == -1
+    assert t.L.mg_tree_build_times(t._h, None) == -1
