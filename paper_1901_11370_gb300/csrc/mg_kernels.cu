@@ -3567,10 +3567,31 @@ template <class T, int D> struct Launch {
         }
     }
     // covered cells <- mean of children (finest first), then all ghosts
+    // Lowest group whose values a leaf stencil can reach: groups with leaves,
+    // the group below a level with refinement faces (the coarser cells of its
+    // ghosts) and, where that group has refinement faces too, the one below
+    // it (a refinement ghost reads the coarser block's own ghosts).  Every
+    // refresh consumer reads leaf stencils only; a V-cycle restricts into
+    // the groups below itself.
+    static int refresh_gmin(const mg_tree *t) {
+        const int ng = (int)t->groups.size();
+        std::vector<char> cf(ng, 0);
+        for (int g = 0; g < ng; g++)
+            for (int l : t->groups[g]) cf[g] |= t->lev[l].has_cf ? 1 : 0;
+        int gmin = ng;
+        for (int g = 0; g < ng; g++)
+            for (int l : t->groups[g]) {
+                const LevelHost &L = t->lev[l];
+                if (L.nb > L.nref) gmin = std::min(gmin, g);
+                if (L.has_cf && g >= 1) gmin = std::min(gmin, cf[g - 1] && g >= 2 ? g - 2 : g - 1);
+            }
+        return gmin;
+    }
     static void refresh(mg_tree *t, Fields<T> &F, int homog, int mode = 0) {
         const KParams P = kparams(t, homog);
         const int top = (int)t->groups.size() - 1;
-        for (int g = top; g >= 1; g--)
+        const int gmin = refresh_gmin(t);
+        for (int g = top; g >= 1 && g - 1 >= gmin; g--)
             for (int l : t->groups[g]) {
                 const LevelHost &L = t->lev[l];
                 if (L.coarsest) continue;
@@ -3581,7 +3602,7 @@ template <class T, int D> struct Launch {
                     launch_k(k_restrict<T, D>, L.nb, threads_for(cells_of<D>(L.n / 2)), 0, t->stream, P, L.first, F.X, F.XG,
                                                                                                  F.F, F.E, F.EG, F.F, 0);
             }
-        for (int g = 0; g <= top; g++)
+        for (int g = gmin; g <= top; g++)
             for (int l : t->groups[g]) ghost(t, P, l, F.X, F.XG, mode);
     }
     static void refresh_eps(mg_tree *t, Fields<T> &F) {
