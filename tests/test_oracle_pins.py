@@ -718,3 +718,38 @@ def test_cleaning_adjoint_is_the_cleaning_of_g_periodic():
         dB[comp, c] = 1e-3
         fd = (loss(B + dB)[0] - loss(B - dB)[0]) / 2e-3
         assert abs(fd - grad[comp, c]) < 1e-7 * (abs(grad[comp, c]) + np.abs(grad).max() * 1e-3), (fd, grad[comp, c])
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_helmholtz_term_is_minus_lambda_phi(dim):
+    """The Helmholtz form of Sec. 2.2, div(eps grad phi) - lambda phi: on the
+    same refined mesh the operators with lambda and without differ by
+    exactly -lambda x on every leaf cell (boundary and refinement ghosts do
+    not involve lambda)."""
+    N, base, lam = 4, 8, 2.5
+    ref = amr_refine(dim, N, base, (0.35, 0.6, 0.5), (0.3 if dim == 2 else 0.45,), (False,) * 3)
+    assert len(ref) > 0
+    bct = (DIR, NEU, DIR, DIR, NEU, DIR)
+    args = (dim, N, 0, bct, (0.5, -0.25, 1.0, 0.0, 0.3, 0.0), (base,) * dim, (0,) * dim, (1,) * dim, ref)
+    o0, o1 = Oracle(*args), Oracle(*args, helm=lam)
+    x = np.random.default_rng(8).standard_normal(o0.n_leaf)
+    d = o1.apply(x) - o0.apply(x)
+    np.testing.assert_allclose(d, -lam * x, rtol=0, atol=1e-12 * np.abs(o0.apply(x)).max())
+
+
+@pytest.mark.parametrize("bct", [(DIR, DIR, NEU, DIR, 0, 0), (NEU, NEU, NEU, NEU, 0, 0)])
+def test_helmholtz_vcycles_converge_to_dense_solution(bct):
+    """With lambda > 0 the V-cycle fixed point is the dense composite
+    solution, also for an all-Neumann mesh, which lambda makes regular."""
+    dim, N, base, lam = 2, 4, 8, 3.0
+    ref = amr_refine(dim, N, base, (0.35, 0.6, 0.5), (0.3,), (False,) * 3)
+    o = Oracle(dim, N, 0, bct, (0.5, -0.25, 1.0, 0.0, 0.0, 0.0), (base,) * dim, (0,) * dim, (1,) * dim, ref,
+               helm=lam)
+    f = np.random.default_rng(19).standard_normal(o.n_leaf)
+    A, b = _dense(o)
+    x_ref = np.linalg.solve(A, f - b)
+    o.set_rhs(f)
+    o.set_phi(np.zeros(o.n_leaf))
+    o.fmg()
+    o.vcycle(40)
+    np.testing.assert_allclose(o.get_phi(), x_ref, rtol=0, atol=1e-11 * np.abs(x_ref).max())
