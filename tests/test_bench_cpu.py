@@ -1,0 +1,36 @@
+"""Host logic of bench.py, no GPU: the traffic file parser finds every
+committed entry, returns its bytes per cell only while the kernel's source
+hash matches, and the kernel hashes cover one whole template each."""
+import os
+import re
+
+import bench
+
+
+def entries():
+    path = os.path.join(bench.ROOT, "profiles", "sweep_f32_traffic.txt")
+    text = "".join(ln for ln in open(path) if not ln.startswith("#"))
+    return [dict((k.strip(), v.strip()) for k, v in (ln.split(":", 1) for ln in e.splitlines() if ":" in ln))
+            for e in text.split("\n\n") if e.strip()]
+
+
+def test_traffic_entries_parse_and_follow_the_source_hash():
+    es = entries()
+    assert {e["kernel"] for e in es} == {"k_sweep_rows", "k_sweep_tma"}
+    for e in es:
+        got = bench.measured_traffic(e["kernel"], "sweep_f32_traffic.txt")
+        if e["source_sha1"] == bench.kernel_sha1(e["kernel"]):
+            assert got == float(e["dram_bytes_per_cell"])
+            assert 12.0 < got < 15.0  # at most the algorithmic 15 B/cell of an 8^3 block
+        else:
+            assert got is None
+    assert bench.measured_traffic("k_no_such_kernel", "sweep_f32_traffic.txt") is None
+
+
+def test_kernel_hash_covers_one_template():
+    src = open(os.path.join(bench.ROOT, "paper_1901_11370_gb300", "csrc", "mg_kernels.cu")).read()
+    for name in ("k_sweep_rows", "k_sweep_tma", "k_resid_tma"):
+        h = bench.kernel_sha1(name)
+        assert re.fullmatch(r"[0-9a-f]{40}", h)
+    assert bench.kernel_sha1("k_sweep_rows") != bench.kernel_sha1("k_sweep_tma")
+    assert "k_sweep_rows(" in src
