@@ -34,3 +34,12 @@ def test_kernel_hash_covers_one_template():
         assert re.fullmatch(r"[0-9a-f]{40}", h)
     assert bench.kernel_sha1("k_sweep_rows") != bench.kernel_sha1("k_sweep_tma")
     assert "k_sweep_rows(" in src
+
+
+def test_benchmark_workloads_have_their_stated_sizes():
+    """The two benchmark workloads the JSON line names: the 3D AMR tree has
+    19,827,200 leaf cells and the 512-tree cylindrical forest 54,636,032
+    (seeded generators, so these are fixed)."""
+    from synth import workloads as W
+    assert W.n_leaf_cells(bench.problem()) == 19827200
+    assert sum(W.n_leaf_cells(W.cyl_ring_tree(i)) for i in range(512)) == 54636032
