@@ -292,9 +292,14 @@ int mg_time_sweeps(mg_tree *t, int level, int n_sweeps, int precision, double ou
  * than that (for instance very many small leaf blocks) is rejected with
  * MG_ERR_ARG.  The first call on a device looks up the array's device
  * address with that device current; make that first call before any stream
- * capture.  The tree's device must be current.  All calls share the array:
- * calls that overlap on the GPU (from two threads or two streams) race on
- * it.  Synchronises the tree's stream.  The paper has no counterpart.
+ * capture.  The address is cached per device for the life of the process,
+ * so a reset of the device's primary context (cudaDeviceReset) while the
+ * library stays loaded leaves it stale.  The tree's device must be current.
+ * All calls share the array: calls that overlap on the GPU (from two
+ * threads or two streams) race on it.  Synchronises the tree's stream.
+ * Errors: MG_ERR_ARG (null tree or output, mesh beyond the scratch, another
+ * device current), MG_ERR_STATE (tree not finalized), MG_ERR_CUDA,
+ * MG_ERR_TIMEOUT, MG_ERR_NAN.  The paper has no counterpart.
  */
 int mg_residual_norm_noalloc(mg_tree *t, double *l2, double *linf);
 

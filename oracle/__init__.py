@@ -11,6 +11,7 @@ the passage of the paper it follows.
 from __future__ import annotations
 
 import ctypes as C
+import math
 import os
 import subprocess
 
@@ -72,6 +73,8 @@ def _load():
     L.or_divergence_order.argtypes = [C.c_void_p, _dp, _dp, C.c_int]
     L.or_project.argtypes = [C.c_void_p, _dp, _dp]
     L.or_transfer.argtypes = [C.c_void_p, C.c_void_p]
+    for name in ("or_apply_T", "or_eps_grad_T", "or_divergence_T", "or_gradient_T"):
+        getattr(L, name).argtypes = [C.c_void_p, _dp, _dp]
     _lib = L
     return L
 
@@ -95,7 +98,9 @@ class Oracle:
         self.L = L
         self.dim = dim
         self.cyl = geom == 1
-        self._singular = all(int(t) != 0 for t in list(bc_type)[:2 * dim])
+        # no Dirichlet face and no Helmholtz term: A has the constants as
+        # its null space (reading of the compatibility condition)
+        self._singular = all(int(t) != 0 for t in list(bc_type)[:2 * dim]) and float(helm) <= 0.0
         self._rhs = np.zeros(int(L.or_num_leaf_cells(self._h)))
         self.n_leaf = int(L.or_num_leaf_cells(self._h))
 
@@ -207,6 +212,35 @@ class Oracle:
         self.L.or_apply(self._h, np.ascontiguousarray(x, np.float64), out)
         return out
 
+    def apply_T(self, y):
+        """A^T y on the leaf cells, A the linear part of the composite operator
+        (the exact transpose of its forward steps, reading R16)."""
+        out = np.zeros(self.n_leaf)
+        self.L.or_apply_T(self._h, np.ascontiguousarray(y, np.float64), out)
+        return out
+
+    def eps_grad_T(self, lam):
+        """dL/d eps of the leaf cells on any mesh: -lambda^T d(A phi)/d eps
+        through the harmonic face coefficients, eps ghosts and covered cells."""
+        out = np.zeros(self.n_leaf)
+        self.L.or_eps_grad_T(self._h, np.ascontiguousarray(lam, np.float64), out)
+        return out
+
+    def divergence_T(self, v):
+        """D^T v, D the second-order central divergence (dim leaf arrays out)."""
+        out = np.zeros((self.dim, self.n_leaf))
+        if self.L.or_divergence_T(self._h, np.ascontiguousarray(v, np.float64), out.ravel()) != 0:
+            raise ValueError("oracle: " + self.L.or_last_error().decode())
+        return out
+
+    def gradient_T(self, u):
+        """G^T u, G the central gradient of the projection (u: dim leaf arrays)."""
+        u = np.ascontiguousarray(u, np.float64).reshape(self.dim, self.n_leaf)
+        out = np.zeros(self.n_leaf)
+        if self.L.or_gradient_T(self._h, u.ravel(), out) != 0:
+            raise ValueError("oracle: " + self.L.or_last_error().decode())
+        return out
+
     def eps_grad(self, lam):
         out = np.zeros(self.n_leaf)
         if self.L.or_eps_grad(self._h, np.ascontiguousarray(lam, np.float64), out) != 0:
@@ -289,23 +323,63 @@ class Oracle:
             hist.append(self.residual_norm()[0])
         return cycles, hist
 
-    def adjoint(self, g, n_vcycles=12):
-        """lambda = A^-T g and dL/deps for a uniform mesh, given the converged
-        phi in the tree.  A^T = A on Cartesian meshes; in the cylindrical form
-        r_i A is symmetric, so A^T = diag(r) A diag(r)^-1 and
-        A (lambda / r) = g / r.  The solve is one FMG cycle plus n_vcycles
-        V-cycles with homogeneous boundary values."""
+    def adjoint(self, g, n_vcycles=12, rel_tol=0.0):
+        """lambda = A^-T g and dL/deps, given the converged phi in the tree.
+
+        With W the cell volumes, A* = W^-1 A^T W equals A wherever W A is
+        symmetric (uniform meshes, the cylindrical form included) and is
+        close to it on refined meshes, so A's V-cycle M approximates its
+        inverse.  The iteration (reading R16): mu_0 = FMG(W^-1 g),
+        lambda_0 = W mu_0, then lambda += W M W^-1 (g - A^T lambda), with
+        homogeneous boundary values, n_vcycles times or until the
+        volume-weighted norm of W^-1 (g - A^T lambda) falls below rel_tol
+        times that of W^-1 g.  Without Dirichlet faces (and lambda = 0) A
+        has the constants as null space: g is made compatible (sum g = 0) and
+        lambda is returned as P^T lambda = lambda - W sum(lambda) / sum(W),
+        the adjoint of the zero-mean projection of f.  Returns (lambda,
+        dL/deps); last_adjoint holds (iterations, final relative residual)."""
         phi = self.get_phi()
         rhs = self._rhs.copy()
-        _, rad = self.leaf_geometry()
+        vol, _ = self.leaf_geometry()
+        vs = vol.sum()
+        gh = np.array(g, np.float64)
+        if self._singular:
+            gh = gh - vol * gh.sum() / vs
+
+        def nrm(r):
+            return math.sqrt(np.dot(vol, (r / vol) ** 2) / vs)
+
         self.set_homogeneous(True)
-        self.set_rhs(g / rad if self.cyl else g)
+        self.set_rhs(gh / vol)
         self.set_phi(np.zeros(self.n_leaf))
         self.fmg()
-        self.vcycle(n_vcycles)
-        mu = self.get_phi()
-        lam = mu * rad if self.cyl else mu
+        lam = vol * self.get_phi()
+        r0 = nrm(gh)
+        it = 0
+        while True:
+            r = gh - self.apply_T(lam)
+            rel = nrm(r) / r0 if r0 > 0 else 0.0
+            if it >= n_vcycles or rel <= rel_tol:
+                break
+            self.set_rhs(r / vol)
+            self.set_phi(np.zeros(self.n_leaf))
+            self.vcycle(1)
+            lam = lam + vol * self.get_phi()
+            it += 1
+        if self._singular:
+            lam = lam - vol * lam.sum() / vs
         self.set_homogeneous(False)
         self.set_rhs(rhs)
         self.set_phi(phi)
-        return lam, self.eps_grad(lam)
+        self.last_adjoint = (it, rel)
+        return lam, self.eps_grad_T(lam)
+
+    def clean_adjoint(self, gBn, n_vcycles=40, rel_tol=1e-13):
+        """Vector-Jacobian product of the cleaning map B -> B - G phi,
+        phi = A^-1 P D B (second-order divergence, Sec. 4.1): given
+        gBn = dL/dB_new (dim leaf arrays), dL/dB = gBn - D^T P^T A^-T Q^T G^T gBn
+        (P, Q the zero-mean projections of f and phi on a singular mesh, the
+        adjoint solve as in adjoint())."""
+        gBn = np.ascontiguousarray(gBn, np.float64).reshape(self.dim, self.n_leaf)
+        lam, _ = self.adjoint(self.gradient_T(gBn), n_vcycles, rel_tol)
+        return gBn - self.divergence_T(lam)

@@ -45,6 +45,10 @@
  *      solution from the old values, then a ghost refresh; omega defaults
  *      to the standard smoothing weight of the 5/7-point Laplacian, 4/5 in
  *      2D and 6/7 in 3D;
+ *  R16 the adjoint on refined meshes uses the exact transpose of the
+ *      composite operator: the forward steps (restriction of covered cells,
+ *      ghost fills, stencil) undone in reverse order with transposed
+ *      coefficients; A is not symmetric at refinement faces (Sec. 2.6);
  *  R15 phi carried to an adapted mesh (Sec. 2.5 leaves the data to the
  *      caller): a leaf block that is also a block of the old mesh keeps its
  *      values (the restriction of its former children where a refinement
@@ -78,6 +82,7 @@ typedef struct {
     int *poff;    /* [nb][3] offset of this block inside its parent, parent cells */
     int *haschild;/* [nb] 1 if covered by finer blocks */
     double *phi, *f, *eps, *vold, *tmp, *lam;
+    double *adj;  /* adjoint of every padded value (transposed operators) */
     double *bc[6];
 } Lev;
 
@@ -164,6 +169,7 @@ static int alloc_level(Tree *T, Lev *lv, int nb, const int *ijk) {
     lv->vold = calloc(np ? np : 1, sizeof(double));
     lv->tmp = calloc(np ? np : 1, sizeof(double));
     lv->lam = calloc(np ? np : 1, sizeof(double));
+    lv->adj = calloc(np ? np : 1, sizeof(double));
     for (size_t m = 0; m < np; m++) lv->eps[m] = 1.0;
     for (int s = 0; s < 6; s++) lv->bc[s] = NULL;
     return 0;
@@ -171,7 +177,7 @@ static int alloc_level(Tree *T, Lev *lv, int nb, const int *ijk) {
 
 static void free_level(Lev *lv) {
     free(lv->ijk); free(lv->map); free(lv->parent); free(lv->poff); free(lv->haschild);
-    free(lv->phi); free(lv->f); free(lv->eps); free(lv->vold); free(lv->tmp); free(lv->lam);
+    free(lv->phi); free(lv->f); free(lv->eps); free(lv->vold); free(lv->tmp); free(lv->lam); free(lv->adj);
     for (int s = 0; s < 6; s++) free(lv->bc[s]);
 }
 
@@ -836,7 +842,7 @@ static int64_t leaf_loop(Tree *T, double *io, int which, int dir) {
     for (int l = 0; l < T->nlev; l++) {
         Lev *lv = &T->L[l];
         int n = lv->n, ps = P(T, n), nk = T->dim == 3 ? n : 1;
-        double *X = which == 0 ? lv->phi : which == 1 ? lv->f : which == 2 ? lv->eps : lv->lam;
+        double *X = which == 0 ? lv->phi : which == 1 ? lv->f : which == 2 ? lv->eps : which == 3 ? lv->lam : lv->adj;
         for (int b = 0; b < lv->nb; b++) {
             if (lv->haschild[b]) continue;
             for (int k = 0; k < nk; k++)
@@ -1236,5 +1242,296 @@ int or_transfer(void *hold, void *hnew) {
         }
     }
     refresh(T);
+    return 0;
+}
+
+/* ------------------------------------------------ transposed operators -- */
+
+/*
+ * The adjoint of a loss through the solve needs A^T, and for divergence
+ * cleaning the transposes of the central divergence and gradient (Sec. 4.1).
+ * On refined meshes A is not symmetric (reading R16): a fine row reads the
+ * coarse cell B through its refinement ghost with weight 1/2 (Sec. 2.6),
+ * while the row of B reads the fine cells through the mean of the covered
+ * cell D, 1/2^D each.  Every forward operator here is a stencil over padded
+ * arrays after refresh_field (restriction of covered cells bottom-up, then
+ * ghost fills coarsest level first).  Its transpose runs the steps in the
+ * reverse order with transposed coefficients, accumulating into lv->adj, the
+ * adjoint of every padded value (interior and ghosts).  Only the linear part
+ * counts: boundary values and other constants have no adjoint.
+ */
+
+static void zero_adj(Tree *T) {
+    for (int l = 0; l < T->nlev; l++)
+        memset(T->L[l].adj, 0, sizeof(double) * (size_t)T->L[l].nb * P(T, T->L[l].n));
+}
+
+/*
+ * Transpose of ghost_fill(T, l, which): every ghost value's adjoint is handed
+ * to the values it was formed from and then cleared.  Same-level and periodic
+ * ghosts copy a neighbour cell (coefficient 1); physical ghosts depend on the
+ * adjacent cell with -1 (Dirichlet, 2a - x_i) or +1 (Neumann, axis; eps and
+ * vector components copy x_i); a refinement ghost g = B'/2 + 3c/4 - d/4 with
+ * B' = B + sum_t s_t (C_t - A_t)/8 (reading R3) gives 1/2 to B,
+ * +-s_t/16 to C_t and A_t (level l-1, interior or ghost), 3/4 to c and -1/4
+ * to d (eps ghosts take B alone, reading R4).
+ */
+static void ghost_fill_T(Tree *T, int l, int which) {
+    Lev *lv = &T->L[l];
+    int n = lv->n, dim = T->dim, ps = P(T, n);
+    for (int b = 0; b < lv->nb; b++) {
+        double *ab = lv->adj + (size_t)b * ps;
+        for (int d = 0; d < dim; d++)
+            for (int s = 0; s < 2; s++) {
+                int face = 2 * d + s;
+                int q[3] = {lv->ijk[3 * b], lv->ijk[3 * b + 1], lv->ijk[3 * b + 2]};
+                q[d] += s ? 1 : -1;
+                int phys = 0;
+                if (q[d] < 0 || q[d] >= lv->nblk[d]) {
+                    if (T->bct[face] == BC_PER) q[d] = (q[d] + lv->nblk[d]) % lv->nblk[d];
+                    else phys = 1;
+                }
+                int nbk = phys ? -1 : lookup(lv, q);
+                int tdim[2] = {-1, -1}, nt = 0;
+                for (int t = 0; t < dim; t++) if (t != d) tdim[nt++] = t;
+                int n1 = n, n2 = nt > 1 ? n : 1;
+                for (int u2 = 0; u2 < n2; u2++)
+                    for (int u1 = 0; u1 < n1; u1++) {
+                        int gi[3] = {0, 0, 0}, ii[3] = {0, 0, 0};
+                        gi[tdim[0]] = u1; if (nt > 1) gi[tdim[1]] = u2;
+                        memcpy(ii, gi, sizeof ii);
+                        gi[d] = s ? n : -1;
+                        ii[d] = s ? n - 1 : 0;
+                        double *g = ab + pidx(T, n, gi[0], gi[1], gi[2]);
+                        double gb = *g;
+                        *g = 0.0;
+                        double *ai = ab + pidx(T, n, ii[0], ii[1], ii[2]);
+                        if (phys) {
+                            if (which == F_EPS || which == F_VEC) *ai += gb;
+                            else *ai += T->bct[face] == BC_DIR ? -gb : gb;
+                        } else if (nbk >= 0) {
+                            int jj[3]; memcpy(jj, gi, sizeof jj);
+                            jj[d] = s ? 0 : n - 1;
+                            lv->adj[(size_t)nbk * ps + pidx(T, n, jj[0], jj[1], jj[2])] += gb;
+                        } else {
+                            Lev *cl = &T->L[l - 1];
+                            int G[3]; cell_global(lv, b, gi[0], gi[1], gi[2], G);
+                            if (G[d] < 0) G[d] += lv->ncell[d];
+                            if (G[d] >= lv->ncell[d]) G[d] -= lv->ncell[d];
+                            int Gc[3] = {G[0] / 2, G[1] / 2, G[2] / 2};
+                            int cq[3], nc = cl->n;
+                            for (int e = 0; e < 3; e++) cq[e] = e < dim ? Gc[e] / nc : 0;
+                            int cb = lookup(cl, cq);
+                            double *ca = cl->adj + (size_t)cb * P(T, nc);
+                            int lc[3];
+                            for (int e = 0; e < 3; e++) lc[e] = e < dim ? Gc[e] - cq[e] * nc : 0;
+                            if (which == F_EPS) { ca[pidx(T, nc, lc[0], lc[1], lc[2])] += gb; continue; }
+                            ca[pidx(T, nc, lc[0], lc[1], lc[2])] += 0.5 * gb;
+                            for (int a = 0; a < nt; a++) {
+                                int t = tdim[a];
+                                double sg = (G[t] & 1) ? 1.0 : -1.0;
+                                int la[3], lcc[3];
+                                memcpy(la, lc, sizeof la); memcpy(lcc, lc, sizeof lcc);
+                                la[t] -= 1; lcc[t] += 1;
+                                ca[pidx(T, nc, lcc[0], lcc[1], lcc[2])] += 0.5 * sg / 8.0 * gb;
+                                ca[pidx(T, nc, la[0], la[1], la[2])] -= 0.5 * sg / 8.0 * gb;
+                            }
+                            int dd[3]; memcpy(dd, ii, sizeof dd);
+                            dd[d] = s ? n - 2 : 1;
+                            *ai += 0.75 * gb;
+                            ab[pidx(T, n, dd[0], dd[1], dd[2])] -= 0.25 * gb;
+                        }
+                    }
+            }
+    }
+}
+
+/* Transpose of restrict_block for every block of level l: each child cell
+ * receives 1/2^D of its parent cell's adjoint (the mean of Sec. 2.3). */
+static void restrict_T(Tree *T, int l) {
+    Lev *lv = &T->L[l], *pl = &T->L[l - 1];
+    int n = lv->n, ps = P(T, n), pn = pl->n, pps = P(T, pn), dim = T->dim;
+    int m = n / 2, mk = dim == 3 ? m : 1;
+    for (int b = 0; b < lv->nb; b++) {
+        int pb = lv->parent[b];
+        const int *po = lv->poff + 3 * b;
+        for (int k = 0; k < mk; k++)
+            for (int j = 0; j < m; j++)
+                for (int i = 0; i < m; i++) {
+                    double v = pl->adj[(size_t)pb * pps + pidx(T, pn, po[0] + i, po[1] + j, po[2] + k)] / (1 << dim);
+                    for (int c = 0; c < (1 << dim); c++) {
+                        int fi = 2 * i + (c & 1), fj = 2 * j + ((c >> 1) & 1), fk = dim == 3 ? 2 * k + ((c >> 2) & 1) : 0;
+                        lv->adj[(size_t)b * ps + pidx(T, n, fi, fj, fk)] += v;
+                    }
+                }
+    }
+}
+
+/* Reverse of refresh_field: ghost fills undone finest level first, then the
+ * covered cells' adjoints handed to their children, coarsest level first.
+ * Afterwards the leaf cells of lv->adj hold the adjoint of the leaf values. */
+static void refresh_T(Tree *T, int which) {
+    for (int l = T->nlev - 1; l >= 0; l--) ghost_fill_T(T, l, which);
+    for (int l = 1; l < T->nlev; l++) restrict_T(T, l);
+}
+
+/* neighbour of cell (i,j,k) across face 2d+s in padded indexing */
+static int nbr_pidx(const Tree *T, int n, int i, int j, int k, int d, int s) {
+    int q[3] = {i, j, k};
+    q[d] += s ? 1 : -1;
+    return pidx(T, n, q[0], q[1], q[2]);
+}
+
+/*
+ * out = A^T y on the leaf cells, A the linear part of the composite
+ * operator (homogeneous boundary values): every leaf row
+ * sum_f w_f (x_nb - x_c) - lambda x_c (Sec. 2.2) hands w_f y to its
+ * neighbour value (interior or ghost) and -(sum_f w_f + lambda) y to its
+ * own cell; refresh_T then carries the ghost and covered-cell adjoints to
+ * the leaves.
+ */
+int or_apply_T(void *h, const double *y, double *out) {
+    Tree *T = h;
+    zero_adj(T);
+    int64_t m = 0;
+    for (int l = 0; l < T->nlev; l++) {
+        Lev *lv = &T->L[l];
+        int n = lv->n, ps = P(T, n), nk = T->dim == 3 ? n : 1;
+        for (int b = 0; b < lv->nb; b++) {
+            if (lv->haschild[b]) continue;
+            double *ab = lv->adj + (size_t)b * ps;
+            for (int k = 0; k < nk; k++)
+                for (int j = 0; j < n; j++)
+                    for (int i = 0; i < n; i++) {
+                        double w[6], sw = 0.0, yi = y[m++];
+                        face_weights(T, lv, b, i, j, k, w);
+                        for (int d = 0; d < T->dim; d++)
+                            for (int s = 0; s < 2; s++) {
+                                ab[nbr_pidx(T, n, i, j, k, d, s)] += w[2 * d + s] * yi;
+                                sw += w[2 * d + s];
+                            }
+                        ab[pidx(T, n, i, j, k)] -= (sw + T->helm) * yi;
+                    }
+        }
+    }
+    refresh_T(T, F_PHI);
+    leaf_loop(T, out, 4, 1);
+    return 0;
+}
+
+/*
+ * dL/d eps on the leaf cells of any mesh, given the current phi and
+ * lambda = A^-T dL/dphi: -lambda^T d(A phi)/d eps.  The row of cell c has
+ * the terms w_f (x_nb - x_c), w_f = kappa_f eps_f / h_d^2 with eps_f the
+ * harmonic mean 2 e_c e_o / (e_c + e_o) of the cell's and the neighbour's
+ * (or ghost's) coefficient (Sec. 2.2); d eps_f / d e_c = 2 e_o^2 / (e_c +
+ * e_o)^2.  The eps ghosts and covered cells (reading R4) are undone by
+ * refresh_T.  On a mesh without refinement faces this equals or_eps_grad.
+ */
+int or_eps_grad_T(void *h, const double *lam, double *out) {
+    Tree *T = h;
+    refresh(T);
+    zero_adj(T);
+    int64_t m = 0;
+    for (int l = 0; l < T->nlev; l++) {
+        Lev *lv = &T->L[l];
+        int n = lv->n, ps = P(T, n), nk = T->dim == 3 ? n : 1;
+        for (int b = 0; b < lv->nb; b++) {
+            if (lv->haschild[b]) continue;
+            const double *x = lv->phi + (size_t)b * ps, *E = lv->eps + (size_t)b * ps;
+            double *ab = lv->adj + (size_t)b * ps;
+            for (int k = 0; k < nk; k++)
+                for (int j = 0; j < n; j++)
+                    for (int i = 0; i < n; i++) {
+                        int c = pidx(T, n, i, j, k), G[3];
+                        cell_global(lv, b, i, j, k, G);
+                        double li = lam[m++];
+                        for (int d = 0; d < T->dim; d++)
+                            for (int s = 0; s < 2; s++) {
+                                int o = nbr_pidx(T, n, i, j, k, d, s);
+                                double kap = 1.0;
+                                if (T->geom == GEOM_CYL && d == 0) {
+                                    double ri = T->lo[0] + (G[0] + 0.5) * lv->h[0];
+                                    double rf = T->lo[0] + (G[0] + s) * lv->h[0];
+                                    kap = rf / ri;
+                                }
+                                double e0 = E[c], e1 = E[o], s2 = e0 + e1;
+                                double dw = -li * kap / (lv->h[d] * lv->h[d]) * (x[o] - x[c]) * 2.0 / (s2 * s2);
+                                ab[c] += dw * e1 * e1;
+                                ab[o] += dw * e0 * e0;
+                            }
+                    }
+        }
+    }
+    refresh_T(T, F_EPS);
+    leaf_loop(T, out, 4, 1);
+    return 0;
+}
+
+/*
+ * Transpose of the second-order central divergence of or_divergence
+ * (order 2): out (dim leaf arrays) = D^T v.  Each leaf row
+ * sum_d (B_d(c+e_d) - B_d(c-e_d)) / (2 h_d) hands +-v/(2 h_d) to the two
+ * values of component d; refresh_T with the vector-component ghost rules
+ * (physical faces copy the interior value) carries them to the leaves.
+ */
+int or_divergence_T(void *h, const double *v, double *out) {
+    Tree *T = h;
+    if (T->geom != GEOM_CART) { snprintf(g_err, sizeof g_err, "divergence: Cartesian meshes only"); return -1; }
+    int64_t nl = or_num_leaf_cells(h);
+    for (int d = 0; d < T->dim; d++) {
+        zero_adj(T);
+        int64_t m = 0;
+        for (int l = 0; l < T->nlev; l++) {
+            Lev *lv = &T->L[l];
+            int n = lv->n, ps = P(T, n), nk = T->dim == 3 ? n : 1;
+            for (int b = 0; b < lv->nb; b++) {
+                if (lv->haschild[b]) continue;
+                double *ab = lv->adj + (size_t)b * ps;
+                for (int k = 0; k < nk; k++)
+                    for (int j = 0; j < n; j++)
+                        for (int i = 0; i < n; i++) {
+                            double q = v[m++] / (2.0 * lv->h[d]);
+                            ab[nbr_pidx(T, n, i, j, k, d, 1)] += q;
+                            ab[nbr_pidx(T, n, i, j, k, d, 0)] -= q;
+                        }
+            }
+        }
+        refresh_T(T, F_VEC);
+        leaf_loop(T, out + (size_t)d * nl, 4, 1);
+    }
+    return 0;
+}
+
+/*
+ * Transpose of the central gradient of or_project, grad phi (dim leaf arrays
+ * u): out = G^T u on the leaf cells, the ghosts of phi taken with their
+ * linear part (homogeneous boundary values).
+ */
+int or_gradient_T(void *h, const double *u, double *out) {
+    Tree *T = h;
+    if (T->geom != GEOM_CART) { snprintf(g_err, sizeof g_err, "gradient: Cartesian meshes only"); return -1; }
+    int64_t nl = or_num_leaf_cells(h);
+    zero_adj(T);
+    for (int d = 0; d < T->dim; d++) {
+        int64_t m = 0;
+        for (int l = 0; l < T->nlev; l++) {
+            Lev *lv = &T->L[l];
+            int n = lv->n, ps = P(T, n), nk = T->dim == 3 ? n : 1;
+            for (int b = 0; b < lv->nb; b++) {
+                if (lv->haschild[b]) continue;
+                double *ab = lv->adj + (size_t)b * ps;
+                for (int k = 0; k < nk; k++)
+                    for (int j = 0; j < n; j++)
+                        for (int i = 0; i < n; i++) {
+                            double q = u[(size_t)d * nl + m++] / (2.0 * lv->h[d]);
+                            ab[nbr_pidx(T, n, i, j, k, d, 1)] += q;
+                            ab[nbr_pidx(T, n, i, j, k, d, 0)] -= q;
+                        }
+            }
+        }
+    }
+    refresh_T(T, F_PHI);
+    leaf_loop(T, out, 4, 1);
     return 0;
 }

@@ -68,6 +68,28 @@ def test_adapt_matches_oracle_transfer_and_cycles(mg, name):
     assert rel(t1.get_phi().cpu().numpy(), o1.get_phi()) < 1e-12
 
 
+@pytest.mark.parametrize("name", ["2d_coarsen_full", "3d_coarsen_full"])
+def test_adapt_after_cycles_carries_fresh_covered_cells(mg, name):
+    """The old tree is cycled first, so its covered cells below the leaf
+    stencils hold stale V-cycle values; a removed refinement must still take
+    the mean of its former children (R15)."""
+    dim, N, n0, ref0, add, rem = LINEAR_CASES[name]
+    p0 = with_rhs(problem(dim, N, n0, ref0, None), 3)
+    p1 = with_rhs(problem(dim, N, n0, changed(ref0, add, rem), None), 4)
+    x = np.random.default_rng(6).standard_normal(W.n_leaf_cells(p0))
+    t0 = mg.Tree.from_problem(p0)
+    o0 = Oracle.from_problem(p0)
+    t0.set_phi(cuda(x))
+    o0.set_phi(x)
+    t0.vcycle(2)
+    o0.vcycle(2)
+    assert rel(t0.get_phi().cpu().numpy(), o0.get_phi()) < 1e-12
+    t1 = t0.adapt(add, rem)
+    o1 = Oracle.from_problem(p1)
+    o1.transfer_from(o0)
+    assert rel(t1.get_phi().cpu().numpy(), o1.get_phi()) < 1e-12
+
+
 def test_adapt_cylindrical_matches_oracle(mg):
     bct = (W.BC_AXIS, W.BC_DIRICHLET, W.BC_DIRICHLET, W.BC_DIRICHLET, W.BC_DIRICHLET, W.BC_DIRICHLET)
     ref0 = [(0, 0, 1, 0), (0, 1, 1, 0), (0, 2, 1, 0)]

@@ -59,6 +59,12 @@ LINEAR_CASES = {
                   [(0, 2, 1, 1), (0, 1, 2, 1), (0, 1, 1, 2), (1, 3, 3, 3), (0, 0, 0, 0)], []),
     "3d_coarsen": (3, 4, 16, [(0, 1, 1, 1), (0, 2, 1, 1), (0, 1, 2, 1), (0, 1, 1, 2), (1, 3, 3, 3)],
                    [(0, 2, 2, 2)], [(1, 3, 3, 3), (0, 2, 1, 1)]),
+    # every base block refined (the base level has no leaves, the refined
+    # level no refinement faces), then one refinement removed: the coarsened
+    # block's values are covered cells below every leaf stencil of the old mesh
+    "2d_coarsen_full": (2, 8, 32, [(0, i, j, 0) for j in range(4) for i in range(4)], [], [(0, 1, 2, 0)]),
+    "3d_coarsen_full": (3, 4, 16, [(0, i, j, k) for k in range(4) for j in range(4) for i in range(4)], [],
+                        [(0, 2, 1, 1)]),
 }
 
 

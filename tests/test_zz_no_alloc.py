@@ -53,3 +53,15 @@ def test_noalloc_rejects_meshes_beyond_the_static_scratch(mg):
     assert e.value.code == -1 and "static scratch" in str(e.value)
     l2, _ = t.residual_norm()  # the allocating entry point still works on it
     assert np.isfinite(l2)
+
+
+def test_noalloc_lifecycle_errors(mg):
+    # an unfinalized tree is a call out of lifecycle order (MG_ERR_STATE), as
+    # for mg_residual_norm; no device work is enqueued
+    t = mg.Tree(2, 8, 0, (0,) * 6, (0,) * 6, (32, 32), (0, 0), (1, 1), finalize=False)
+    with pytest.raises(mg.MGError) as e:
+        t.residual_norm_noalloc()
+    assert e.value.code == -8
+    with pytest.raises(mg.MGError) as e:
+        t.residual_norm()
+    assert e.value.code == -8
