@@ -196,7 +196,8 @@ int mg_residual_norm(mg_tree *t, double *l2, double *linf, double *dev_r);
  * outer step computes r = f - A phi in FP64, runs p->inner_cycles FP32
  * V-cycles on A e = r (homogeneous boundary values, coarsest solve in FP64)
  * and adds e to phi in FP64.  *cycles_done counts outer steps, *rel_out the
- * final relative residual.  Returns MG_ERR_NOT_CONVERGED at max_cycles.
+ * final relative residual.  On a singular problem phi is returned with zero
+ * volume-weighted mean.  Returns MG_ERR_NOT_CONVERGED at max_cycles.
  */
 int mg_solve(mg_tree *t, double rel_tol, int max_cycles, int fmg_first,
              const mg_params *p, int *cycles_done, double *rel_out);
@@ -204,14 +205,43 @@ int mg_solve(mg_tree *t, double rel_tol, int max_cycles, int fmg_first,
 /*
  * mg_adjoint -- for a loss L(phi) at the current (converged) phi:
  * dev_dLdf = lambda = A^-T dev_dLdphi, and dev_dLdeps[c] = dL/d eps_c
- * through the harmonic face coefficients (Sec. 2.2).  Cartesian: A^T = A;
- * cylindrical: r_i A is symmetric, so A (lambda/r) = g/r.  The adjoint solve
- * runs one FMG cycle and n_cycles V-cycles with homogeneous boundary
- * values.  Meshes with refinement boundaries return MG_ERR_UNSUPPORTED.
- * dev_dLdeps may be NULL.  phi is left unchanged.
+ * through the harmonic face coefficients (Sec. 2.2), the eps ghosts and the
+ * coarse-level means of eps.  A is the composite operator with its boundary
+ * values held fixed.  At refinement faces A is not symmetric (the
+ * refinement ghosts of Sec. 2.6), so A^T is applied as the exact transpose
+ * of the forward steps.  lambda comes from defect correction with A's own
+ * V-cycle on the volume-weighted form (W the cell volumes):
+ * mu_0 = FMG(W^-1 g), lambda_0 = W mu_0, then n_cycles times
+ * lambda += W M W^-1 (g - A^T lambda), homogeneous boundary values.  On a
+ * problem without Dirichlet faces (lambda_helmholtz = 0) the forward map
+ * includes the zero-mean projection of f and of phi: g is made compatible
+ * (sum g = 0) and lambda is returned without its component along W.  Such a
+ * problem with variable eps and refinement faces returns MG_ERR_UNSUPPORTED
+ * (fluxes are not conserved there).  dev_dLdeps may be NULL.  phi is left
+ * unchanged; n_cycles >= 0.
  */
 int mg_adjoint(mg_tree *t, const double *dev_dLdphi, double *dev_dLdf, double *dev_dLdeps,
                const mg_params *p, int n_cycles);
+
+/*
+ * mg_adjoint_solve -- mg_adjoint iterated until the volume-weighted norm of
+ * W^-1 (g - A^T lambda) is at most rel_tol times that of W^-1 g (after the
+ * compatibility projection), or max_cycles iterations.  *cycles_done and
+ * *rel_out (optional) receive the count and the final ratio.  Returns
+ * MG_ERR_NOT_CONVERGED when max_cycles is reached first (the outputs are
+ * still written), MG_ERR_ARG for rel_tol <= 0.
+ */
+int mg_adjoint_solve(mg_tree *t, const double *dev_dLdphi, double *dev_dLdf, double *dev_dLdeps,
+                     const mg_params *p, double rel_tol, int max_cycles, int *cycles_done, double *rel_out);
+
+/*
+ * mg_apply_transpose -- dev_out = A^T dev_y on the leaf cells (leaf order),
+ * A the composite operator with homogeneous boundary values (the linear
+ * part of L phi).  The adjoint of every step of the forward operator
+ * (stencil, refinement-face ghosts of Sec. 2.6, the mean restriction of
+ * covered cells of Sec. 2.3), applied in reverse.
+ */
+int mg_apply_transpose(mg_tree *t, const double *dev_y, double *dev_out);
 
 /*
  * Divergence cleaning (Sec. 4.1, eqs. for the projection method and the
@@ -246,6 +276,20 @@ int mg_project(mg_tree *t, const double *dev_B, double *dev_Bnew);
  */
 int mg_clean(mg_tree *t, const double *dev_B, double *dev_Bnew, double *dev_divB, int order, double rel_tol,
              int max_cycles, const mg_params *p, int *cycles_done, double *rel_out);
+
+/*
+ * mg_clean_adjoint -- vector-Jacobian product of the cleaning map
+ * B -> B_new = B - grad phi, phi the solution of Lap phi = div B (second
+ * order, Sec. 4.1; zero-mean projections when no face is Dirichlet):
+ * dev_gB = dev_gBnew - D^T P^T A^-T Q^T G^T dev_gBnew, with D, G the
+ * central divergence and gradient on the mesh (refinement ghosts
+ * included) and the adjoint solve of mg_adjoint_solve (rel_tol,
+ * max_cycles).  dev_gBnew and dev_gB hold dim leaf arrays back to back and
+ * must not alias.  Cartesian meshes; the map is linear, so the result does
+ * not depend on the tree's phi.  Returns as mg_adjoint_solve.
+ */
+int mg_clean_adjoint(mg_tree *t, const double *dev_gBnew, double *dev_gB, const mg_params *p, double rel_tol,
+                     int max_cycles, int *cycles_done, double *rel_out);
 
 /*
  * Instrumentation (the paper has no counterpart; used by the benchmark).

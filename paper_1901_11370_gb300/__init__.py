@@ -260,13 +260,45 @@ class Tree:
         check(self.L.mg_time_sweeps(self._h, level, n_sweeps, precision, out))
         return tuple(out), level
 
-    def adjoint(self, g, n_cycles=12, want_eps=True, n_down=2, n_up=2, smoother=MG_SMOOTH_RBGS, omega=0.0):
+    def adjoint(self, g, n_cycles=12, want_eps=True, n_down=2, n_up=2, smoother=MG_SMOOTH_RBGS, omega=0.0,
+                rel_tol=None, max_cycles=80):
+        """(dL/df, dL/deps) for dL/dphi = g at the current phi (mg_adjoint:
+        n_cycles defect-correction iterations; with rel_tol, mg_adjoint_solve
+        until the adjoint residual is below rel_tol, raising MGError when
+        max_cycles is reached).  With rel_tol, self.last_adjoint holds
+        (iterations, final relative residual)."""
         p = _params(n_down, n_up, smoother=smoother, omega=omega)
         dLdf = torch.empty(self.n_leaf, dtype=torch.float64, device="cuda")
         dLde = torch.empty(self.n_leaf, dtype=torch.float64, device="cuda") if want_eps else None
-        check(self.L.mg_adjoint(self._h, self._leaf(g.contiguous()), _ptr(dLdf), _ptr(dLde) if want_eps else None,
-                                C.byref(p), int(n_cycles)))
+        if rel_tol is None:
+            check(self.L.mg_adjoint(self._h, self._leaf(g.contiguous()), _ptr(dLdf),
+                                    _ptr(dLde) if want_eps else None, C.byref(p), int(n_cycles)))
+        else:
+            cyc, rel = C.c_int(), C.c_double()
+            check(self.L.mg_adjoint_solve(self._h, self._leaf(g.contiguous()), _ptr(dLdf),
+                                          _ptr(dLde) if want_eps else None, C.byref(p), float(rel_tol),
+                                          int(max_cycles), C.byref(cyc), C.byref(rel)))
+            self.last_adjoint = (cyc.value, rel.value)
         return dLdf, dLde
+
+    def apply_transpose(self, y):
+        """A^T y on the leaf cells (homogeneous boundary values)."""
+        out = torch.empty(self.n_leaf, dtype=torch.float64, device="cuda")
+        check(self.L.mg_apply_transpose(self._h, self._leaf(y.contiguous()), _ptr(out)))
+        return out
+
+    def clean_adjoint(self, gBn, rel_tol=1e-12, max_cycles=80, n_down=2, n_up=2):
+        """dL/dB of the cleaning map B -> B - grad phi, Lap phi = div B
+        (mg_clean_adjoint), for gBn = dL/dB_new (dim, n_leaf)."""
+        gBn = gBn.contiguous().view(-1)
+        assert gBn.numel() == self.dim * self.n_leaf
+        out = torch.empty_like(gBn)
+        p = _params(n_down, n_up)
+        cyc, rel = C.c_int(), C.c_double()
+        check(self.L.mg_clean_adjoint(self._h, _ptr(gBn), _ptr(out), C.byref(p), float(rel_tol), int(max_cycles),
+                                      C.byref(cyc), C.byref(rel)))
+        self.last_adjoint = (cyc.value, rel.value)
+        return out.view(self.dim, self.n_leaf)
 
 
 class Batch:

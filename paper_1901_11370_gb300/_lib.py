@@ -20,7 +20,8 @@ EXPORTS = ["mg_tree_create", "mg_tree_refine", "mg_tree_num_levels", "mg_tree_le
            "mg_tree_num_leaf_cells", "mg_tree_leaf_blocks", "mg_set_bc_plane", "mg_tree_finalize",
            "mg_tree_adapt", "mg_tree_build_times",
            "mg_set_rhs", "mg_set_eps", "mg_set_phi", "mg_get_phi", "mg_vcycle", "mg_fmg",
-           "mg_residual_norm", "mg_solve", "mg_adjoint", "mg_tree_destroy", "mg_last_error",
+           "mg_residual_norm", "mg_solve", "mg_adjoint", "mg_adjoint_solve", "mg_apply_transpose",
+           "mg_clean_adjoint", "mg_tree_destroy", "mg_last_error",
            "mg_launch_count", "mg_time_sweeps", "mg_residual_norm_noalloc", "mg_sweep_variant",
            "mg_divergence", "mg_divergence_order", "mg_project", "mg_clean", "mg_set_sweep_variant",
            "mg_batch_create", "mg_batch_leaf_offsets", "mg_batch_set_rhs", "mg_batch_set_eps",
@@ -74,6 +75,9 @@ def load():
     L.mg_residual_norm.argtypes = [vp, dp, dp, vp]
     L.mg_solve.argtypes = [vp, C.c_double, C.c_int, C.c_int, C.POINTER(mg_params), ip, dp]
     L.mg_adjoint.argtypes = [vp, vp, vp, vp, C.POINTER(mg_params), C.c_int]
+    L.mg_adjoint_solve.argtypes = [vp, vp, vp, vp, C.POINTER(mg_params), C.c_double, C.c_int, ip, dp]
+    L.mg_apply_transpose.argtypes = [vp, vp, vp]
+    L.mg_clean_adjoint.argtypes = [vp, vp, vp, C.POINTER(mg_params), C.c_double, C.c_int, ip, dp]
     L.mg_tree_destroy.argtypes = [vp]
     L.mg_launch_count.argtypes = [vp, C.POINTER(C.c_int64)]
     L.mg_time_sweeps.argtypes = [vp, C.c_int, C.c_int, C.c_int, dp]

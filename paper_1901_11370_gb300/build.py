@@ -1,7 +1,7 @@
 """Compile the CUDA library libmg_gb300.so in-tree for sm_103a (nvcc).
 
 Run as ``python -m paper_1901_11370_gb300.build`` or through
-``__graft_entry__.build()``.  The two translation units are compiled in
+``__graft_entry__.build()``.  The translation units are compiled in
 parallel; the shared object lands beside this file.
 """
 import os
@@ -14,7 +14,7 @@ OUT = os.path.join(HERE, "libmg_gb300.so")
 BUILD = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC"]
-SOURCES = ["mg_kernels.cu", "mg_tree.cpp"]
+SOURCES = ["mg_kernels.cu", "mg_adjoint.cu", "mg_tree.cpp"]
 
 
 def _nvcc():

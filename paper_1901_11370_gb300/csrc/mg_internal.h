@@ -168,6 +168,9 @@ struct mg_tree {
     double *h_red = nullptr;       // pinned host copy
     long long launches = 0;        // kernels launched so far
     int *d_status = nullptr;       // device status word (0 = ok)
+    // adjoint (mg_adjoint.cu): adjoint of every pool value (cells, ghosts),
+    // lambda, the compatible right-hand side and a leaf-order scratch
+    double *d_at = nullptr, *d_atg = nullptr, *d_lam = nullptr, *d_gh = nullptr, *d_lv = nullptr;
     int nsm = 0;                   // multiprocessors of the device
     // CUDA graphs of whole cycle sequences, keyed by what they enqueue; a
     // private non-blocking stream is used for capture (the user stream may
@@ -215,8 +218,6 @@ int transfer_phi(mg_tree *old, mg_tree *nt, const std::vector<int> &nid, const s
 void copy_eps_to_f32(mg_tree *t);
 // FP64 face coefficients of every cell into t->d_wface (eps ghosts current)
 void face_coef(mg_tree *t);
-void eps_grad(mg_tree *t, const double *lam_cells, const double *phi_cells, double *out_leaf);
-void scale_by_radius(mg_tree *t, const double *in_leaf, double *out_leaf, int divide);
 KParams kparams(mg_tree *t, int homog);
 int time_sweeps(mg_tree *t, int level, int n_sweeps, int prec, double *out4);
 // batch: per-tree composite residual sums (3 per tree, on the host after wait)
@@ -224,6 +225,15 @@ void residual_enqueue_trees(mg_tree *t, Fields<double> &F, float *f32_cells, boo
 // copies between a concatenated per-tree leaf array and the pool cells
 void leaf_runs_copy(mg_tree *t, double *cells, const double *leaf, bool to_cells);
 int check_cuda(const char *what);
+// transposed operators and the adjoint solve (mg_adjoint.cu); leaf-order
+// device vectors
+int adjoint_buffers(mg_tree *t);
+void apply_transpose(mg_tree *t, const double *y, double *out);
+void eps_grad_transpose(mg_tree *t, const double *lam, double *out);
+int adjoint_dc(mg_tree *t, const double *g, double *lam, int nd, int nu, double rel_tol, int max_it, int *it_out,
+               double *rel_out);
+int clean_adjoint(mg_tree *t, const double *gBn, double *gB, int nd, int nu, double rel_tol, int max_it,
+                  int *it_out, double *rel_out);
 }  // namespace mg
 
 void mg_set_error(const std::string &msg);

@@ -2627,77 +2627,6 @@ __global__ void k_cast_f32(const double *__restrict__ a, float *__restrict__ b, 
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
         b[i] = (float)a[i];
 }
-// leaf-order vector times (divide: 1/) r_i of its cell; leaf blocks of one level
-template <int D>
-__global__ void k_scale_r(KParams P, int first, const double *__restrict__ in, double *__restrict__ out,
-                          long long leaf_base, int divide) {
-    pdl_entry();
-    __shared__ BlockDesc sb;
-    stage_desc(P, first + blockIdx.x, sb);
-    const BlockDesc &b = sb;
-    const LevelDesc &L = P.L[b.lev];
-    const int n = b.n, C = cells_of<D>(n);
-    const long long base = leaf_base + (long long)blockIdx.x * C;
-    for (int c = threadIdx.x; c < C; c += blockDim.x) {
-        const int i = c % n;
-        const double r = P.lo[0] + (b.ijk[0] * n + i + 0.5) * L.h[0];
-        out[base + c] = divide ? in[base + c] / r : in[base + c] * r;
-    }
-}
-
-// dL/d eps_c = -sum over faces of lambda^T d(A phi + b)/d eps_f * d eps_f/d eps_c
-// (harmonic face coefficient of Sec. 2.2); uniform meshes (no refinement faces).
-template <int D>
-__global__ void __launch_bounds__(kMaxThreads) k_eps_grad(KParams P, int first, const double *__restrict__ X,
-                                                          const double *__restrict__ XG,
-                                                          const double *__restrict__ Y, const double *__restrict__ YG,
-                                                          const double *__restrict__ E, const double *__restrict__ EG,
-                                                          double *__restrict__ out, long long leaf_base) {
-    pdl_entry();
-    __shared__ BlockDesc sb;
-    stage_desc(P, first + blockIdx.x, sb);
-    const BlockDesc &b = sb;
-    const LevelDesc &L = P.L[b.lev];
-    const int n = b.n, C = cells_of<D>(n);
-    for (int c = threadIdx.x; c < C; c += blockDim.x) {
-        int i, j, k;
-        cell_of(c, n, D, i, j, k);
-        const int I0 = b.ijk[0] * n + i;
-        const double xc = X[b.cell_off + c], yc = Y[b.cell_off + c];
-        const double ec = E ? E[b.cell_off + c] : 1.0;
-        double g = 0;
-        for (int d = 0; d < D; d++)
-            for (int s = 0; s < 2; s++) {
-                const int o = s ? 1 : -1;
-                const int ii = i + (d == 0 ? o : 0), jj = j + (d == 1 ? o : 0), kk = k + (d == 2 ? o : 0);
-                const double xo = load<double, D>(X, XG, b, ii, jj, kk);
-                const bool outside = (d == 0 ? ii : d == 1 ? jj : kk) < 0 || (d == 0 ? ii : d == 1 ? jj : kk) >= n;
-                const bool phys = outside && b.nbr[2 * d + s] == -1;
-                double kc = 1.0, ko = 1.0;
-                if (P.geom == MG_CYL && d == 0) {
-                    const double rf = P.lo[0] + (I0 + s) * L.h[0];
-                    const double rc = P.lo[0] + (I0 + 0.5) * L.h[0];
-                    const double ro = P.lo[0] + (I0 + (s ? 1.5 : -0.5)) * L.h[0];
-                    kc = rf / rc;
-                    ko = rf / ro;
-                }
-                const double ih2 = L.inv_h2[d];
-                double dA = yc * kc * ih2 * (xo - xc), de;
-                if (phys) {
-                    de = 1.0;
-                } else {
-                    const double yo = load<double, D>(Y, YG, b, ii, jj, kk);
-                    const double eo = E ? load<double, D>(E, EG, b, ii, jj, kk) : 1.0;
-                    dA += yo * ko * ih2 * (xc - xo);
-                    const double sm = ec + eo;
-                    de = 2.0 * eo * eo / (sm * sm);
-                }
-                g += -dA * de;
-            }
-        out[leaf_base + (long long)blockIdx.x * C + c] = g;
-    }
-}
-
 // ------------------------------------------------------------ driver ----
 
 // Face coefficients of the FP64 operator (Sec. 2.2), one thread per cell:
@@ -3727,32 +3656,6 @@ void copy_eps_to_f32(mg_tree *t) {
     launch_k(k_cast_f32, 1216, 256, 0, t->stream, t->f64.E, t->f32.E, t->ncells);
     ++t->launches;
     launch_k(k_cast_f32, 1216, 256, 0, t->stream, t->f64.EG, t->f32.EG, t->nghost);
-}
-
-void scale_by_radius(mg_tree *t, const double *in_leaf, double *out_leaf, int divide) {
-    const KParams P = kparams(t, 0);
-    long long leaf_base = 0;
-    for (size_t l = 0; l < t->lev.size(); l++) {
-        const LevelHost &L = t->lev[l];
-        const int nleaf = L.nb - L.nref;
-        if (nleaf <= 0) continue;
-        ++t->launches;
-        launch_k(k_scale_r<2>, nleaf, threads_for(L.n * L.n), 0, t->stream, P, L.first + L.nref, in_leaf, out_leaf,
-                                                                       leaf_base, divide);
-        leaf_base += (long long)nleaf * L.n * L.n;
-    }
-}
-
-void eps_grad(mg_tree *t, const double *lam_cells, const double *phi_cells, double *out_leaf) {
-    (void)phi_cells;
-    const KParams P = kparams(t, 0);
-    const LevelHost &L = t->lev.back();
-    const int nleaf = L.nb - L.nref;
-    ++t->launches;
-    if (t->dim == 2)
-        launch_k(k_eps_grad<2>, nleaf, threads_for(cells_of<2>(L.n)), 0, t->stream, P, L.first + L.nref, t->f64.X, t->f64.XG, lam_cells, t->adj.XG, t->f64.E, t->f64.EG, out_leaf, 0);
-    else
-        launch_k(k_eps_grad<3>, nleaf, threads_for(cells_of<3>(L.n)), 0, t->stream, P, L.first + L.nref, t->f64.X, t->f64.XG, lam_cells, t->adj.XG, t->f64.E, t->f64.EG, out_leaf, 0);
 }
 
 template <int D>

@@ -1059,6 +1059,17 @@ extern "C" int mg_solve(mg_tree *t, double rel_tol, int max_cycles, int fmg_firs
         return fail(MG_ERR_ARG, "unknown precision");
     }
     if ((rc = check_cuda("solve")) || (rc = check_status(t))) return rc;
+    if (t->singular && !t->is_batch && std::isfinite(rel)) {
+        // no Dirichlet face: phi is fixed up to a constant; return the
+        // solution with zero volume-weighted mean (covered cells and ghosts
+        // shift with it)
+        if ((rc = dalloc(&t->d_r64, t->nleaf_cells)) || (rc = leaf_copy(t, t->f64.X, (const double *)t->d_r64, false)))
+            return rc;
+        const double mean = leaf_mean(t, t->d_r64);
+        sub_scalar(t, t->f64.X, mean, t->ncells);
+        sub_scalar(t, t->f64.XG, mean, t->nghost);
+        if ((rc = check_cuda("solve"))) return rc;
+    }
     if (cycles_done) *cycles_done = cycles;
     if (rel_out) *rel_out = rel;
     if (!std::isfinite(rel)) return fail(MG_ERR_NAN, "residual is not finite");
@@ -1066,40 +1077,90 @@ extern "C" int mg_solve(mg_tree *t, double rel_tol, int max_cycles, int fmg_firs
     return MG_OK;
 }
 
-extern "C" int mg_adjoint(mg_tree *t, const double *g, double *dLdf, double *dLdeps, const mg_params *p,
-                          int n_cycles) {
-    NEED_FINAL(t);
-    if (!g || !dLdf) return fail(MG_ERR_ARG, "null argument");
+// The adjoint solve of mg_adjoint / mg_adjoint_solve (reading R16, see
+// mg_adjoint.cu): lambda = A^-T g by defect correction with A's V-cycle on
+// the volume-weighted form, then dL/deps through the transposed eps chain.
+static bool has_refinement_faces(const mg_tree *t) {
     for (const BlockDesc &B : t->blocks)
         for (int f = 0; f < 2 * t->dim; f++)
-            if (B.nbr[f] <= -2) return fail(MG_ERR_UNSUPPORTED, "adjoint needs a mesh without refinement faces");
-    mg_params q;
+            if (B.nbr[f] <= -2) return true;
+    return false;
+}
+
+static int adjoint_setup(mg_tree *t, const mg_params *p, mg_params *q) {
+    if (t->is_batch) return fail(MG_ERR_UNSUPPORTED, "the adjoint works on one tree, not a batch");
+    // a singular problem's compatibility condition is sum V f = 0 only where
+    // fluxes are conserved; with variable eps at refinement faces they are
+    // not (Sec. 2.6 states the identity for constant eps)
+    if (t->singular && t->var_eps && has_refinement_faces(t))
+        return fail(MG_ERR_UNSUPPORTED, "adjoint of a problem without Dirichlet faces needs constant eps on a "
+                                        "mesh with refinement faces");
     int rc;
-    if ((rc = use_params(t, p, &q, nullptr))) return rc;
+    if ((rc = use_params(t, p, q, nullptr))) return rc;
     if ((rc = alloc_fields(t, t->adj, false))) return rc;
     t->adj.E = t->f64.E;
     t->adj.W = t->f64.W;
     t->adj.EG = t->f64.EG;
-    // rhs g (Cartesian) or g / r (cylindrical: A^T = diag(r) A diag(r)^-1)
-    if (t->geom == MG_CYL) {
-        scale_by_radius(t, g, dLdf, 1);
-        if ((rc = leaf_copy(t, t->adj.F, (const double *)dLdf, true))) return rc;
-    } else {
-        if ((rc = leaf_copy(t, t->adj.F, g, true))) return rc;
-    }
-    CK(cudaMemsetAsync(t->adj.X, 0, sizeof(double) * t->ncells, t->stream));
-    CK(cudaMemsetAsync(t->adj.XG, 0, sizeof(double) * t->nghost, t->stream));
-    fmg<double>(t, t->adj, q.n_down, q.n_up, 1);
-    const int top = (int)t->groups.size() - 1;
-    for (int c = 0; c < n_cycles; c++) vcycle<double>(t, t->adj, top, q.n_down, q.n_up, 1);
-    if ((rc = leaf_copy(t, t->adj.X, (const double *)dLdf, false))) return rc;
-    if (t->geom == MG_CYL) {
-        scale_by_radius(t, dLdf, dLdf, 0);
-        if ((rc = leaf_copy(t, t->adj.X, (const double *)dLdf, true))) return rc;
-        refresh<double>(t, t->adj, 1);
-    }
-    if (dLdeps) eps_grad(t, t->adj.X, t->f64.X, dLdeps);
-    return check_cuda("adjoint");
+    return adjoint_buffers(t);
+}
+
+static int adjoint_run(mg_tree *t, const double *g, double *dLdf, double *dLdeps, const mg_params *p, double rel_tol,
+                       int max_cycles, int *cycles_done, double *rel_out) {
+    NEED_FINAL(t);
+    if (!g || !dLdf) return fail(MG_ERR_ARG, "null argument");
+    if (max_cycles < 0) return fail(MG_ERR_ARG, "negative cycle count");
+    mg_params q;
+    int rc, it = 0;
+    double rel = 0.0;
+    if ((rc = adjoint_setup(t, p, &q))) return rc;
+    if ((rc = adjoint_dc(t, g, dLdf, q.n_down, q.n_up, rel_tol, max_cycles, &it, &rel))) return rc;
+    if (dLdeps) eps_grad_transpose(t, dLdf, dLdeps);
+    if ((rc = check_cuda("adjoint")) || (rc = check_status(t))) return rc;
+    if (cycles_done) *cycles_done = it;
+    if (rel_out) *rel_out = rel;
+    if (!std::isfinite(rel)) return fail(MG_ERR_NAN, "adjoint residual is not finite");
+    if (rel_tol > 0 && rel > rel_tol) return fail(MG_ERR_NOT_CONVERGED, "adjoint: max_cycles reached");
+    return MG_OK;
+}
+
+extern "C" int mg_adjoint(mg_tree *t, const double *g, double *dLdf, double *dLdeps, const mg_params *p,
+                          int n_cycles) {
+    return adjoint_run(t, g, dLdf, dLdeps, p, 0.0, n_cycles, nullptr, nullptr);
+}
+
+extern "C" int mg_adjoint_solve(mg_tree *t, const double *g, double *dLdf, double *dLdeps, const mg_params *p,
+                                double rel_tol, int max_cycles, int *cycles_done, double *rel_out) {
+    if (!(rel_tol > 0)) return fail(MG_ERR_ARG, "rel_tol must be positive");
+    return adjoint_run(t, g, dLdf, dLdeps, p, rel_tol, max_cycles, cycles_done, rel_out);
+}
+
+extern "C" int mg_apply_transpose(mg_tree *t, const double *y, double *out) {
+    NEED_FINAL(t);
+    if (!y || !out) return fail(MG_ERR_ARG, "null argument");
+    if (t->is_batch) return fail(MG_ERR_UNSUPPORTED, "the transpose works on one tree, not a batch");
+    int rc;
+    if ((rc = adjoint_buffers(t))) return rc;
+    apply_transpose(t, y, out);
+    return check_cuda("apply_transpose");
+}
+
+extern "C" int mg_clean_adjoint(mg_tree *t, const double *gBnew, double *gB, const mg_params *p, double rel_tol,
+                                int max_cycles, int *cycles_done, double *rel_out) {
+    NEED_FINAL(t);
+    if (!gBnew || !gB || gBnew == gB) return fail(MG_ERR_ARG, "null or aliased argument");
+    if (t->geom != MG_CART) return fail(MG_ERR_UNSUPPORTED, "divergence cleaning: Cartesian meshes only");
+    if (!(rel_tol > 0) || max_cycles < 0) return fail(MG_ERR_ARG, "rel_tol must be positive, max_cycles >= 0");
+    mg_params q;
+    int rc, it = 0;
+    double rel = 0.0;
+    if ((rc = adjoint_setup(t, p, &q))) return rc;
+    if ((rc = clean_adjoint(t, gBnew, gB, q.n_down, q.n_up, rel_tol, max_cycles, &it, &rel))) return rc;
+    if ((rc = check_status(t))) return rc;
+    if (cycles_done) *cycles_done = it;
+    if (rel_out) *rel_out = rel;
+    if (!std::isfinite(rel)) return fail(MG_ERR_NAN, "adjoint residual is not finite");
+    if (rel > rel_tol) return fail(MG_ERR_NOT_CONVERGED, "clean adjoint: max_cycles reached");
+    return MG_OK;
 }
 
 extern "C" int mg_launch_count(mg_tree *t, int64_t *n) {
@@ -1205,6 +1266,7 @@ extern "C" int mg_tree_destroy(mg_tree *t) {
         cudaFree(t->d_r64); cudaFree(t->d_wface); cudaFree(t->d_jac64); cudaFree(t->d_jac32); cudaFree(t->d_minv); cudaFree(t->d_cvec); cudaFree(t->d_partials); cudaFree(t->d_red); cudaFree(t->d_status); cudaFree(t->d_tcoarse); cudaFree(t->d_coarse_chunks);
         cudaFreeHost(t->h_red);
         cudaFree(t->d_runs); cudaFree(t->d_slot_off); cudaFree(t->d_slots); cudaFree(t->d_tree3);
+        cudaFree(t->d_at); cudaFree(t->d_atg); cudaFree(t->d_lam); cudaFree(t->d_gh); cudaFree(t->d_lv);
         cudaFreeHost(t->h_tree3);
         drop_graphs(t);
         if (t->cap_stream) cudaStreamDestroy(t->cap_stream);

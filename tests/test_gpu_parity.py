@@ -179,10 +179,15 @@ def test_adjoint_matches_oracle(mg, case):
     assert rel_diff(ge.cpu().numpy(), ge_o) < 1e-10
 
 
-def test_adjoint_rejects_refined_mesh(mg):
+def test_adjoint_rejects_singular_variable_eps_on_refined_mesh(mg):
+    """Without Dirichlet faces the compatibility condition sum V f = 0 needs
+    conserved fluxes, which variable eps at refinement faces breaks: the
+    adjoint says so (MG_ERR_UNSUPPORTED) instead of returning a gradient."""
     import torch
     from paper_1901_11370_gb300 import MGError
-    p = CASES["gauss3d_amr"]
+    q = CASES["periodic2d_amr_eps"]
+    p = W.Problem("per_neu", 2, 4, 0, q.base, q.lo, q.hi, (2, 2, 1, 1, 0, 0), (0,) * 6, q.refine, 512,
+                  rhs=q.rhs, eps=q.eps)
     t, _ = both(mg, p)
     with pytest.raises(MGError) as e:
         t.adjoint(torch.zeros(t.n_leaf, dtype=torch.float64, device="cuda"))
