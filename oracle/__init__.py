@@ -30,7 +30,11 @@ def build(force=False):
     """Compile the oracle into a shared library beside its source."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + ".%d.tmp" % os.getpid()
-        subprocess.check_call(["gcc", "-O2", "-std=c99", "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"])
+        base = ["gcc", "-O2", "-std=c99", "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"]
+        try:  # OpenMP over the blocks of a level where the compiler has it
+            subprocess.check_call(base[:1] + ["-fopenmp"] + base[1:], stderr=subprocess.DEVNULL)
+        except subprocess.CalledProcessError:
+            subprocess.check_call(base)
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -73,10 +77,17 @@ def _load():
     L.or_divergence_order.argtypes = [C.c_void_p, _dp, _dp, C.c_int]
     L.or_project.argtypes = [C.c_void_p, _dp, _dp]
     L.or_transfer.argtypes = [C.c_void_p, C.c_void_p]
+    L.or_set_threads.argtypes = [C.c_int]
     for name in ("or_apply_T", "or_eps_grad_T", "or_divergence_T", "or_gradient_T"):
         getattr(L, name).argtypes = [C.c_void_p, _dp, _dp]
     _lib = L
     return L
+
+
+def set_threads(n=0):
+    """Threads of the oracle's block loops (n <= 0: leave as is); returns
+    the count in use.  Results do not depend on it."""
+    return int(_load().or_set_threads(int(n)))
 
 
 class Oracle:
@@ -308,7 +319,8 @@ class Oracle:
     # ---------------------------------------------------- composite solve --
     def solve(self, rel_tol=1e-10, max_cycles=50, fmg_first=True):
         """phi = 0, then (optionally) one FMG cycle and V-cycles until the
-        composite residual drops by rel_tol.  Returns (cycles, history)."""
+        composite residual drops by rel_tol; a singular problem's phi is
+        returned with zero volume-weighted mean.  Returns (cycles, history)."""
         self.set_phi(np.zeros(self.n_leaf))
         r0, _ = self.residual_norm()
         hist = [r0]
@@ -321,6 +333,10 @@ class Oracle:
             self.vcycle(1)
             cycles += 1
             hist.append(self.residual_norm()[0])
+        if self._singular:  # the solution with zero volume-weighted mean (reading c10)
+            vol, _ = self.leaf_geometry()
+            x = self.get_phi()
+            self.set_phi(x - np.dot(vol, x) / vol.sum())
         return cycles, hist
 
     def adjoint(self, g, n_vcycles=12, rel_tol=0.0):

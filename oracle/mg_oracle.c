@@ -60,6 +60,9 @@
 #include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #ifndef M_PI
 #define M_PI 3.14159265358979323846
@@ -402,6 +405,7 @@ static void ghost_fill(Tree *T, int l, int which) {
     Lev *lv = &T->L[l];
     int n = lv->n, dim = T->dim, ps = P(T, n);
     double *X = fld(lv, which);
+#pragma omp parallel for schedule(static)
     for (int b = 0; b < lv->nb; b++) {
         double *xb = X + (size_t)b * ps;
         for (int d = 0; d < dim; d++)
@@ -534,6 +538,7 @@ static double apply_L(const Tree *T, const Lev *lv, const double *X, int b, int 
 static void smooth_colour(Tree *T, int l, int colour) {
     Lev *lv = &T->L[l];
     int n = lv->n, ps = P(T, n), nk = T->dim == 3 ? n : 1;
+#pragma omp parallel for schedule(static)
     for (int b = 0; b < lv->nb; b++) {
         double *x = lv->phi + (size_t)b * ps, *f = lv->f + (size_t)b * ps;
         for (int k = 0; k < nk; k++)
@@ -567,6 +572,7 @@ static void smooth_jacobi(Tree *T, int l) {
     int n = lv->n, ps = P(T, n), nk = T->dim == 3 ? n : 1;
     double *old = malloc(sizeof(double) * (size_t)lv->nb * ps);
     memcpy(old, lv->phi, sizeof(double) * (size_t)lv->nb * ps);
+#pragma omp parallel for schedule(static)
     for (int b = 0; b < lv->nb; b++) {
         const double *xo = old + (size_t)b * ps;
         double *x = lv->phi + (size_t)b * ps, *f = lv->f + (size_t)b * ps;
@@ -635,6 +641,7 @@ static void restrict_block(Tree *T, int l, int b, const double *Xf, double *Xc, 
  */
 static void restrict_fas(Tree *T, int l) {
     Lev *lv = &T->L[l], *pl = &T->L[l - 1];
+#pragma omp parallel for schedule(static)
     for (int b = 0; b < lv->nb; b++) {
         restrict_block(T, l, b, NULL, pl->tmp, 1);
         restrict_block(T, l, b, lv->phi, pl->phi, 0);
@@ -643,6 +650,7 @@ static void restrict_fas(Tree *T, int l) {
     size_t np = (size_t)pl->nb * P(T, pl->n);
     memcpy(pl->vold, pl->phi, np * sizeof(double));
     int pn = pl->n, pps = P(T, pn), nk = T->dim == 3 ? pn : 1;
+#pragma omp parallel for schedule(static)
     for (int b = 0; b < pl->nb; b++) {
         if (!pl->haschild[b]) continue;
         for (int k = 0; k < nk; k++)
@@ -664,6 +672,7 @@ static void restrict_fas(Tree *T, int l) {
 static void prolong_correct(Tree *T, int l) {
     Lev *lv = &T->L[l], *pl = &T->L[l - 1];
     int n = lv->n, ps = P(T, n), pn = pl->n, pps = P(T, pn), dim = T->dim, nk = dim == 3 ? n : 1;
+#pragma omp parallel for schedule(static)
     for (int b = 0; b < lv->nb; b++) {
         int pb = lv->parent[b];
         const int *po = lv->poff + 3 * b;
@@ -829,6 +838,7 @@ int or_fmg(void *h) {
 static void refresh_field(Tree *T, int which) {
     for (int l = T->nlev - 1; l >= 1; l--) {
         Lev *lv = &T->L[l];
+#pragma omp parallel for schedule(static)
         for (int b = 0; b < lv->nb; b++) restrict_block(T, l, b, fld(lv, which), fld(&T->L[l - 1], which), 0);
     }
     for (int l = 0; l < T->nlev; l++) ghost_fill(T, l, which);
@@ -905,27 +915,55 @@ void or_residual_norm(void *h, double *l2, double *linf, double *res) {
     Tree *T = h;
     refresh(T);
     double s2 = 0.0, sv = 0.0, mx = 0.0;
-    int64_t m = 0;
+    int64_t m0 = 0;
     for (int l = 0; l < T->nlev; l++) {
         Lev *lv = &T->L[l];
-        int n = lv->n, ps = P(T, n), nk = T->dim == 3 ? n : 1;
+        int n = lv->n, ps = P(T, n), nk = T->dim == 3 ? n : 1, cpb = C(T, n);
+        /* leaf-order offset of every leaf block, then the blocks in parallel
+         * with per-block sums added in block order (independent of threads) */
+        int64_t *off = malloc(sizeof(int64_t) * (lv->nb ? lv->nb : 1));
+        double *bs = calloc(3 * (size_t)(lv->nb ? lv->nb : 1), sizeof(double));
+        int64_t m = m0;
+        for (int b = 0; b < lv->nb; b++) { off[b] = m; if (!lv->haschild[b]) m += cpb; }
+#pragma omp parallel for schedule(static)
         for (int b = 0; b < lv->nb; b++) {
             if (lv->haschild[b]) continue;
+            int64_t q = off[b];
             for (int k = 0; k < nk; k++)
                 for (int j = 0; j < n; j++)
                     for (int i = 0; i < n; i++) {
                         int G[3]; cell_global(lv, b, i, j, k, G);
                         double r = lv->f[(size_t)b * ps + pidx(T, n, i, j, k)] - apply_L(T, lv, lv->phi, b, i, j, k);
                         double V = cell_volume(T, lv, G);
-                        s2 += V * r * r; sv += V;
-                        if (fabs(r) > mx) mx = fabs(r);
-                        if (res) res[m] = r;
-                        m++;
+                        bs[3 * b] += V * r * r; bs[3 * b + 1] += V;
+                        if (fabs(r) > bs[3 * b + 2]) bs[3 * b + 2] = fabs(r);
+                        if (res) res[q] = r;
+                        q++;
                     }
         }
+        for (int b = 0; b < lv->nb; b++) {
+            s2 += bs[3 * b]; sv += bs[3 * b + 1];
+            if (bs[3 * b + 2] > mx) mx = bs[3 * b + 2];
+        }
+        free(off); free(bs);
+        m0 = m;
     }
     *l2 = sqrt(s2 / sv);
     *linf = mx;
+}
+
+/* Number of threads for the block loops (OpenMP over the blocks of a
+ * level; within a colour the updates are order-independent, so every
+ * result is the same for any thread count).  n <= 0 keeps the current
+ * setting.  Returns the count in use (1 without OpenMP). */
+int or_set_threads(int n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
 }
 
 /* composite operator on a leaf vector: out = L x (x clobbers phi) */
