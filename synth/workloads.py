@@ -422,3 +422,122 @@ def cyl_ring_tree(seed, N=16, kmin=2, kmax=32, force_k=None):
     return Problem("cyl_%d_k%d_l%d" % (seed, k, nlev), 2, N, GEOM_CYL, (n, n, 1),
                    (0.0, 0.0, 0.0), (1.0, 1.0, 1.0), bct, (0.0,) * 6, ref, 1024,
                    rhs=rhs, eps=eps)
+
+
+def kolmogorov_field(n, seed, dim=3):
+    """dim-component periodic Gaussian field on n^dim cells whose component
+    spectra fall as |B_k|^2 ~ k^(-11/3) (shell spectrum E(k) ~ k^(-5/3)) for
+    integer wavenumbers 1 <= |k| <= n/2, zero elsewhere, random phases (the
+    FFT of white noise), not projected; scaled so that mean |B|^2 = 1.
+    Returns float64 [dim, n, ..., n] indexed [component, x, y, z]."""
+    rng = np.random.default_rng(seed)
+    k = np.fft.fftfreq(n, d=1.0 / n)
+    kr = np.fft.rfftfreq(n, d=1.0 / n)
+    ks = np.meshgrid(*([k] * (dim - 1) + [kr]), indexing="ij")
+    kk = np.sqrt(sum(q * q for q in ks))
+    amp = np.zeros_like(kk)
+    band = (kk >= 1.0) & (kk <= n / 2)
+    amp[band] = kk[band] ** (-11.0 / 6.0)
+    del ks, kk, band
+    out = np.empty((dim,) + (n,) * dim)
+    for c in range(dim):
+        w = rng.standard_normal((n,) * dim)
+        out[c] = np.fft.irfftn(np.fft.rfftn(w) * amp, s=(n,) * dim)
+    out /= math.sqrt(np.mean(np.sum(out * out, axis=0)))
+    return out
+
+
+class CleanInputs:
+    """Config 5 inputs: a periodic 3D field B = B_turb + B_blob on an octree
+    refined where |B| is large, and the target field B_t of the loss.
+
+    B_turb is kolmogorov_field on the base grid (seed); on refined cells it
+    takes the value of the base cell that contains them (the prolongation of
+    the input is piecewise constant, an input definition).  The blob is the
+    non-solenoidal field grad(A exp(-|x - x_b|^2 / w^2)), evaluated at every
+    leaf cell centre, with x_b drawn from U[0.25, 0.75]^3 and A scaled so
+    that its peak magnitude is `peak` times the rms of B_turb.  Refinement:
+    depth 1 covers the base blocks whose max |B| is in the top `frac` of
+    all base blocks, depth 2 likewise among the depth-1 blocks, then 2:1
+    balance (periodic)."""
+
+    def __init__(self, n=512, N=16, seed=0, levels=2, frac=0.1, w=0.05, peak=3.0, target_seed=3):
+        self.n, self.N, self.seed, self.w, self.target_seed = n, N, seed, w, target_seed
+        rng = np.random.default_rng(seed + 7919)
+        self.xb = tuple(rng.uniform(0.25, 0.75, size=3))
+        # peak of |grad(A exp(-r^2/w^2))| = A sqrt(2) exp(-1/2) / w at r = w / sqrt(2)
+        self.A = peak * w / (math.sqrt(2.0) * math.exp(-0.5))
+        self.turb = kolmogorov_field(n, seed)
+        nb0 = n // N
+        h0 = 1.0 / n
+        # depth 0: max |B| per base block, B = turb + blob at the base cell centres
+        a = (np.arange(n) + 0.5) * h0
+        mag = self._magnitude(self.turb, a)
+        bmax = mag.reshape(nb0, N, nb0, N, nb0, N).max(axis=(1, 3, 5))
+        del mag
+        sets = {}
+        cur = np.argwhere(bmax >= np.quantile(bmax, 1.0 - frac))
+        for depth in range(levels):
+            sets[depth] = {tuple(int(x) for x in q) for q in cur}
+            if depth + 1 == levels:
+                break
+            # children of the refined blocks, max |B| of each over its cells
+            kids = np.array([(2 * i + (c & 1), 2 * j + ((c >> 1) & 1), 2 * k + (c >> 2))
+                             for (i, j, k) in sorted(sets[depth]) for c in range(8)], np.int64)
+            hd = h0 / 2 ** (depth + 1)
+            m = np.empty(len(kids))
+            li = np.arange(N)
+            for q, (i, j, k) in enumerate(kids):
+                gi, gj, gk = i * N + li, j * N + li, k * N + li
+                xs, ys, zs = (gi + 0.5) * hd, (gj + 0.5) * hd, (gk + 0.5) * hd
+                sh = depth + 1
+                bt = self.turb[:, (gi >> sh)[:, None, None], (gj >> sh)[None, :, None], (gk >> sh)[None, None, :]]
+                bb = self._blob(xs[:, None, None], ys[None, :, None], zs[None, None, :])
+                m[q] = np.sqrt(((bt + bb) ** 2).sum(axis=0)).max()
+            cur = kids[m >= np.quantile(m, 1.0 - frac)]
+        self.refine = sets_to_refine(balance(3, (nb0,) * 3, (True,) * 3, sets))
+        self.problem = Problem("clean3d_%d_b%d_l%d" % (n, N, levels), 3, N, GEOM_CART, (n,) * 3, (0.0,) * 3,
+                               (1.0,) * 3, (BC_PERIODIC,) * 6, (0.0,) * 6, self.refine, 512)
+
+    def _blob(self, X, Y, Z):
+        dx, dy, dz = X - self.xb[0], Y - self.xb[1], Z - self.xb[2]
+        e = self.A * np.exp(-(dx * dx + dy * dy + dz * dz) / self.w ** 2) * (-2.0 / self.w ** 2)
+        return np.stack(np.broadcast_arrays(e * dx, e * dy, e * dz))
+
+    def _magnitude(self, turb, a):
+        out = np.empty(turb.shape[1:])
+        for k in range(len(a)):
+            bb = self._blob(a[:, None], a[None, :], a[k])
+            out[:, :, k] = np.sqrt(((turb[:, :, :, k] + bb) ** 2).sum(axis=0))
+        return out
+
+    def leaf_fields(self, with_blob=True, field=None):
+        """B on the leaf cells, [3, n_leaf] in leaf order: the base-grid field
+        at the base cell containing each leaf cell, plus the blob at the leaf
+        cell centre (with_blob)."""
+        p = self.problem
+        lb = leaf_blocks(p)
+        N, nc = self.N, self.N ** 3
+        turb = self.turb if field is None else field
+        out = np.empty((3, len(lb) * nc))
+        li = np.arange(N)
+        ck, cj, ci = np.meshgrid(li, li, li, indexing="ij")
+        ci, cj, ck = ci.ravel(), cj.ravel(), ck.ravel()
+        for depth in np.unique(lb[:, 0]):
+            sel = np.nonzero(lb[:, 0] == depth)[0]
+            for s0 in range(0, len(sel), 4096):
+                part = sel[s0:s0 + 4096]
+                I = (lb[part, 1][:, None] * N + ci[None, :]).ravel()
+                J = (lb[part, 2][:, None] * N + cj[None, :]).ravel()
+                K = (lb[part, 3][:, None] * N + ck[None, :]).ravel()
+                idx = (part[:, None] * nc + np.arange(nc)[None, :]).ravel()
+                d = int(depth)
+                out[:, idx] = turb[:, I >> d, J >> d, K >> d]
+                if with_blob:
+                    h = 1.0 / (self.n * 2 ** d)
+                    out[:, idx] += self._blob((I + 0.5) * h, (J + 0.5) * h, (K + 0.5) * h)
+        return out
+
+    def target(self):
+        """B_t: the seeded turbulent field alone (target_seed), on the leaves."""
+        return self.leaf_fields(with_blob=False, field=kolmogorov_field(self.n, self.target_seed))
