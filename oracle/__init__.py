@@ -53,6 +53,7 @@ def _load():
     L.or_num_levels.argtypes = [C.c_void_p]
     L.or_level_info.argtypes = [C.c_void_p, C.c_int, _ip, _dp]
     L.or_set_cycle.argtypes = [C.c_void_p, C.c_int, C.c_int]
+    L.or_set_schedule.argtypes = [C.c_void_p, C.c_int, _ip, _ip]
     L.or_set_smoother.argtypes = [C.c_void_p, C.c_int, C.c_double]
     L.or_set_homogeneous.argtypes = [C.c_void_p, C.c_int]
     L.or_num_leaf_cells.restype = C.c_int64
@@ -199,6 +200,16 @@ class Oracle:
     # ------------------------------------------------------------ cycles --
     def set_cycle(self, n_down=2, n_up=2):
         self.L.or_set_cycle(self._h, n_down, n_up)
+
+    def set_schedule(self, down=None, up=None):
+        """Smoothing steps per level (level 0 coarsest; entries < 0 keep
+        set_cycle's); None clears the schedule."""
+        if down is None:
+            self.L.or_set_schedule(self._h, 0, np.zeros(1, np.int32), np.zeros(1, np.int32))
+            return
+        d = np.ascontiguousarray(down, np.int32)
+        u = np.ascontiguousarray(up, np.int32)
+        self.L.or_set_schedule(self._h, len(d), d, u)
 
     def set_smoother(self, jacobi=False, omega=0.0):
         """Red-black Gauss-Seidel (default) or weighted Jacobi (omega <= 0:

@@ -99,6 +99,7 @@ typedef struct {
     Lev *L;
     int homog; /* 1: physical boundary values treated as zero */
     int n_down, n_up;
+    int *sched;     /* optional per-level steps: sched[2l] down, sched[2l+1] up (< 0: n_down / n_up) */
     int smoother;   /* 0 red-black Gauss-Seidel, 1 weighted Jacobi (R13) */
     double omega;   /* Jacobi weight */
     /* coarsest-level dense factorisation */
@@ -188,7 +189,7 @@ void or_destroy(void *h) {
     Tree *T = h;
     if (!T) return;
     for (int l = 0; l < T->nlev; l++) free_level(&T->L[l]);
-    free(T->L); free(T->lu); free(T->piv); free(T);
+    free(T->L); free(T->lu); free(T->piv); free(T->sched); free(T);
 }
 
 static void ghost_fill(Tree *T, int l, int which);
@@ -354,6 +355,23 @@ int or_level_info(void *h, int l, int *out /* n, depth, nb, nblk[3], ncell[3] */
     return 0;
 }
 void or_set_cycle(void *h, int n_down, int n_up) { Tree *T = h; T->n_down = n_down; T->n_up = n_up; }
+/* N_down / N_up of Sec. 2.4 chosen per level: down[l], up[l] for levels
+ * 0..n-1 (values < 0 keep or_set_cycle's); n = 0 clears the schedule */
+void or_set_schedule(void *h, int n, const int *down, const int *up) {
+    Tree *T = h;
+    free(T->sched);
+    T->sched = NULL;
+    if (n <= 0) return;
+    T->sched = malloc(sizeof(int) * 2 * T->nlev);
+    for (int l = 0; l < T->nlev; l++) {
+        T->sched[2 * l] = l < n ? down[l] : -1;
+        T->sched[2 * l + 1] = l < n ? up[l] : -1;
+    }
+}
+static int steps(const Tree *T, int l, int up) {
+    int v = T->sched ? T->sched[2 * l + up] : -1;
+    return v >= 0 ? v : (up ? T->n_up : T->n_down);
+}
 /* smoother 0: red-black Gauss-Seidel; 1: weighted Jacobi with weight omega
  * (omega <= 0: 4/5 in 2D, 6/7 in 3D) -- reading R13 */
 void or_set_smoother(void *h, int smoother, double omega) {
@@ -805,13 +823,13 @@ static void coarse_solve(Tree *T) {
 /* V-cycle topped at level `top` (Sec. 2.4). */
 static void vcycle_top(Tree *T, int top) {
     for (int l = top; l >= 1; l--) {
-        smooth(T, l, T->n_down);
+        smooth(T, l, steps(T, l, 0));
         restrict_fas(T, l);
     }
     coarse_solve(T);
     for (int l = 1; l <= top; l++) {
         prolong_correct(T, l);
-        smooth(T, l, T->n_up);
+        smooth(T, l, steps(T, l, 1));
     }
 }
 

@@ -753,3 +753,30 @@ def test_helmholtz_vcycles_converge_to_dense_solution(bct):
     o.fmg()
     o.vcycle(40)
     np.testing.assert_allclose(o.get_phi(), x_ref, rtol=0, atol=1e-11 * np.abs(x_ref).max())
+
+
+def test_per_level_schedule():
+    """N_down / N_up per level (Sec. 2.4 fixes one pair for all levels): a
+    schedule repeating set_cycle's pair is the same cycle bit for bit, a
+    uniform (1, 3) schedule equals set_cycle(1, 3), and a mixed schedule
+    still converges to the composite solution of the dense LU."""
+    p = W.cfg2_gauss3d(base=16, N=4, radii=(0.3,), sigma=0.1)
+
+    def run(setup):
+        o = Oracle.from_problem(p)
+        setup(o)
+        o.fmg()
+        o.vcycle(2)
+        return o.get_phi()
+
+    nl = len(Oracle.from_problem(p).levels())
+    base = run(lambda o: None)
+    assert np.array_equal(base, run(lambda o: o.set_schedule([2] * nl, [2] * nl)))
+    a = run(lambda o: o.set_cycle(1, 3))
+    b = run(lambda o: o.set_schedule([1] * nl, [3] * nl))
+    assert np.array_equal(a, b) and not np.array_equal(a, base)
+    mixed = ([-1] + [1, 3, 2, 1][: nl - 1] + [2] * max(0, nl - 5), [-1] + [3, 1, 2, 2][: nl - 1] + [1] * max(0, nl - 5))
+    o = Oracle.from_problem(p)
+    o.set_schedule(*mixed)
+    cyc, hist = o.solve(1e-12, 60)
+    assert hist[-1] <= 1e-12 * hist[0]
