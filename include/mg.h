@@ -292,6 +292,34 @@ int mg_clean_adjoint(mg_tree *t, const double *dev_gBnew, double *dev_gB, const 
                      int max_cycles, int *cycles_done, double *rel_out);
 
 /*
+ * mg_set_schedule -- N_down / N_up of Sec. 2.4 chosen per level: down[l],
+ * up[l] smoothing steps on level l = 0..n-1 (level 0 the coarsest, solved
+ * exactly, so its entries are not used; 0..16, or -1 to keep the n_down /
+ * n_up of the call's mg_params).  n = 0 clears the schedule.  Host arrays.
+ * Applies to every later cycle of the tree (mg_vcycle, mg_fmg, mg_solve,
+ * the adjoint).  mg_get_schedule writes the current per-level values (-1
+ * where none is set) for levels 0..n-1.
+ */
+int mg_set_schedule(mg_tree *t, int n, const int *host_down, const int *host_up);
+int mg_get_schedule(mg_tree *t, int n, int *host_down, int *host_up);
+
+/*
+ * mg_tune_schedule -- autotuner of the sweeps per level: times full solves
+ * of the tree's current problem (phi = 0, FMG first, mg_solve to rel_tol in
+ * `precision`) for candidate schedules -- (n_down, n_up) in {1, 2, 3} set
+ * separately for the levels holding leaves and for the coarser levels, and
+ * for MG_FP32_DC one or two inner cycles per outer step -- each run three
+ * times (the first captures the graphs), and keeps the fastest candidate
+ * that converges (mg_set_schedule).  *inner_cycles_out receives its inner
+ * cycle count (pass it in mg_params.inner_cycles), *ms_out its solve time.
+ * phi is restored afterwards.  MG_ERR_NOT_CONVERGED when no candidate
+ * reaches rel_tol within max_cycles.  The paper has no counterpart (it
+ * fixes N_down = N_up = 2).
+ */
+int mg_tune_schedule(mg_tree *t, double rel_tol, int max_cycles, int precision, int *inner_cycles_out,
+                     double *ms_out);
+
+/*
  * Instrumentation (the paper has no counterpart; used by the benchmark).
  * mg_launch_count: number of CUDA kernels this tree has launched so far.
  * mg_time_sweeps: runs n_sweeps red-black sweeps on `level` of the FP64
@@ -305,6 +333,14 @@ int mg_clean_adjoint(mg_tree *t, const double *dev_gBnew, double *dev_gB, const 
  * fill (read the source cells, write the ghosts once).  Synchronises.
  */
 int mg_launch_count(mg_tree *t, int64_t *n);
+/* mg_set_wait_limit: polls of every bounded wait in this tree's staged
+ * kernels before the wait gives up (polls < 0: the default, 2^20, a few
+ * milliseconds).  A kernel whose wait gives up sets the tree's status word,
+ * lets its own copies in flight land (under the default bound) and returns;
+ * the call that launched it returns MG_ERR_TIMEOUT and clears the word.
+ * polls = 0 makes every staged kernel give up at once, which exercises that
+ * path: no solve is meaningful until the limit is restored. */
+int mg_set_wait_limit(mg_tree *t, int64_t polls);
 /* mg_sweep_variant: the sweep kernel variant in use for a level and
  * precision (MG_FP64 / MG_FP32_DC): 0 persistent CTA-per-block TMA,
  * 1 CTA-per-block plain loads, 2 / 3 warp-per-block TMA (8 / 4 warps),

@@ -231,6 +231,34 @@ class Tree:
         check(self.L.mg_launch_count(self._h, C.byref(n)))
         return n.value
 
+    def set_wait_limit(self, polls=None):
+        """Polls of the kernels' bounded waits (mg_set_wait_limit); None
+        restores the default, 0 makes every staged kernel give up at once."""
+        check(self.L.mg_set_wait_limit(self._h, -1 if polls is None else int(polls)))
+
+    def set_schedule(self, down=None, up=None):
+        """Smoothing steps per level (mg_set_schedule); None clears it."""
+        if down is None:
+            check(self.L.mg_set_schedule(self._h, 0, None, None))
+            return
+        d = np.ascontiguousarray(down, np.int32)
+        u = np.ascontiguousarray(up, np.int32)
+        check(self.L.mg_set_schedule(self._h, len(d), d.ctypes.data_as(C.c_void_p), u.ctypes.data_as(C.c_void_p)))
+
+    def schedule(self):
+        n = len(self.levels())
+        d, u = np.zeros(n, np.int32), np.zeros(n, np.int32)
+        check(self.L.mg_get_schedule(self._h, n, d.ctypes.data_as(C.c_void_p), u.ctypes.data_as(C.c_void_p)))
+        return d, u
+
+    def tune_schedule(self, rel_tol=1e-10, max_cycles=60, precision=MG_FP32_DC):
+        """Autotune the sweeps per level and the inner cycles by timed solves
+        (mg_tune_schedule); returns (inner_cycles, ms per solve)."""
+        inner, ms = C.c_int(), C.c_double()
+        check(self.L.mg_tune_schedule(self._h, float(rel_tol), int(max_cycles), int(precision), C.byref(inner),
+                                      C.byref(ms)))
+        return inner.value, ms.value
+
     SWEEP_VARIANTS = {0: "k_sweep_tma (CTA per block)", 1: "k_sweep (plain loads)", 2: "k_sweep_warp<8 warps>",
                       3: "k_sweep_warp<4 warps>", 4: "k_sweep_rows<8 warps, 2 stages>",
                       5: "k_sweep_rows<4 warps, 3 stages>", 6: "k_sweep_flat (thread per colour cell)",

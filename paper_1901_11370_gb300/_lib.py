@@ -21,8 +21,9 @@ EXPORTS = ["mg_tree_create", "mg_tree_refine", "mg_tree_num_levels", "mg_tree_le
            "mg_tree_adapt", "mg_tree_build_times",
            "mg_set_rhs", "mg_set_eps", "mg_set_phi", "mg_get_phi", "mg_vcycle", "mg_fmg",
            "mg_residual_norm", "mg_solve", "mg_adjoint", "mg_adjoint_solve", "mg_apply_transpose",
-           "mg_clean_adjoint", "mg_tree_destroy", "mg_last_error",
-           "mg_launch_count", "mg_time_sweeps", "mg_residual_norm_noalloc", "mg_sweep_variant",
+           "mg_clean_adjoint", "mg_set_schedule", "mg_get_schedule", "mg_tune_schedule", "mg_tree_destroy",
+           "mg_last_error",
+           "mg_launch_count", "mg_set_wait_limit", "mg_time_sweeps", "mg_residual_norm_noalloc", "mg_sweep_variant",
            "mg_divergence", "mg_divergence_order", "mg_project", "mg_clean", "mg_set_sweep_variant",
            "mg_batch_create", "mg_batch_leaf_offsets", "mg_batch_set_rhs", "mg_batch_set_eps",
            "mg_batch_set_phi", "mg_batch_get_phi", "mg_batch_vcycle", "mg_batch_fmg", "mg_batch_residual_norms",
@@ -78,8 +79,12 @@ def load():
     L.mg_adjoint_solve.argtypes = [vp, vp, vp, vp, C.POINTER(mg_params), C.c_double, C.c_int, ip, dp]
     L.mg_apply_transpose.argtypes = [vp, vp, vp]
     L.mg_clean_adjoint.argtypes = [vp, vp, vp, C.POINTER(mg_params), C.c_double, C.c_int, ip, dp]
+    L.mg_set_schedule.argtypes = [vp, C.c_int, vp, vp]
+    L.mg_get_schedule.argtypes = [vp, C.c_int, vp, vp]
+    L.mg_tune_schedule.argtypes = [vp, C.c_double, C.c_int, C.c_int, ip, dp]
     L.mg_tree_destroy.argtypes = [vp]
     L.mg_launch_count.argtypes = [vp, C.POINTER(C.c_int64)]
+    L.mg_set_wait_limit.argtypes = [vp, C.c_int64]
     L.mg_time_sweeps.argtypes = [vp, C.c_int, C.c_int, C.c_int, dp]
     L.mg_residual_norm_noalloc.argtypes = [vp, dp, dp]
     L.mg_sweep_variant.argtypes = [vp, C.c_int, C.c_int, ip]

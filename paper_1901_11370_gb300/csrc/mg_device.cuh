@@ -4,6 +4,7 @@
 // ghosts, the 5/7-point row, the ghost rules of Sec. 2.6 and the launch
 // helper.  Not part of the public ABI.
 #pragma once
+#include <atomic>
 #include <cmath>
 #include <cstdint>
 #include <cstdlib>
@@ -65,6 +66,15 @@ static int pdl_mode() {
     return mode;
 }
 static bool g_pdl_ok = true;
+// first failed kernel launch since the last check_cuda (0: none), with the
+// kernel and configuration it was launched with
+inline std::atomic<int> g_launch_error{0};
+struct LaunchFail {
+    const void *kern;
+    unsigned grid, block;
+    size_t smem;
+};
+inline LaunchFail g_launch_fail{};
 template <class... KArgs, class... Args>
 static void launch_k(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, Args... args) {
     cudaLaunchConfig_t cfg = {};
@@ -77,11 +87,17 @@ static void launch_k(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem,
     at[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = at;
     cfg.numAttrs = (pdl_mode() && g_pdl_ok) ? 1 : 0;
-    if (cudaLaunchKernelEx(&cfg, kern, ((KArgs)args)...) != cudaSuccess && cfg.numAttrs) {
+    cudaError_t e = cudaLaunchKernelEx(&cfg, kern, ((KArgs)args)...);
+    if (e != cudaSuccess && cfg.numAttrs) {
         cudaGetLastError();  // attribute refused: plain launches from now on
         g_pdl_ok = false;
         cfg.numAttrs = 0;
-        cudaLaunchKernelEx(&cfg, kern, ((KArgs)args)...);
+        e = cudaLaunchKernelEx(&cfg, kern, ((KArgs)args)...);
+    }
+    if (e != cudaSuccess) {  // kept until check_cuda reports it (a capture would otherwise drop it)
+        int none = 0;
+        if (g_launch_error.compare_exchange_strong(none, (int)e))
+            g_launch_fail = {(const void *)kern, grid.x, block.x, smem};
     }
 }
 

@@ -12,6 +12,10 @@
 
 namespace mg {
 
+// polls of a bounded mbarrier wait before a kernel gives up, sets the status
+// word and returns (a few milliseconds)
+constexpr uint32_t kDefaultWaitLimit = 1u << 20;
+
 // Per-block descriptor, one per block of every level (device table).
 // Storage is interior-only, block-major, x fastest; face ghosts live in a
 // separate array: block g owns 2*D faces of n^(D-1) values each at
@@ -67,6 +71,7 @@ struct KParams {
     int uniform;          // 1: every block of a launch shares one level descriptor
     float lo0f;           // lo[0] in FP32 (cylindrical radius in FP32 kernels)
     float helmf;          // lambda in FP32
+    uint32_t wait_limit;  // polls of a bounded wait before it gives up (0: at once)
 };
 
 // Coarsest level of one tree of a pool (one tree, or a batch of trees):
@@ -168,6 +173,7 @@ struct mg_tree {
     double *h_red = nullptr;       // pinned host copy
     long long launches = 0;        // kernels launched so far
     int *d_status = nullptr;       // device status word (0 = ok)
+    uint32_t wait_limit = mg::kDefaultWaitLimit;  // bounded-wait polls (mg_set_wait_limit)
     // adjoint (mg_adjoint.cu): adjoint of every pool value (cells, ghosts),
     // lambda, the compatible right-hand side and a leaf-order scratch
     double *d_at = nullptr, *d_atg = nullptr, *d_lam = nullptr, *d_gh = nullptr, *d_lv = nullptr;
@@ -183,6 +189,10 @@ struct mg_tree {
     cudaStream_t cap_stream = nullptr;
     bool use_graphs = true;
     std::vector<int> sweep_choice[2];  // autotuned sweep variant per level (FP64, FP32); -1 default
+    // smoothing steps per level (mg_set_schedule / mg_tune_schedule); an
+    // entry < 0, or no entry, takes the cycle's n_down / n_up
+    std::vector<int> sched_down, sched_up;
+    std::string sched_key;             // graph-key suffix of the schedule
     // a tree made by adapt: sweep variants by level depth taken over from the
     // old tree instead of autotuning (per precision; empty: tune)
     std::map<int, int> tune_hint[2];
@@ -225,6 +235,7 @@ void residual_enqueue_trees(mg_tree *t, Fields<double> &F, float *f32_cells, boo
 // copies between a concatenated per-tree leaf array and the pool cells
 void leaf_runs_copy(mg_tree *t, double *cells, const double *leaf, bool to_cells);
 int check_cuda(const char *what);
+std::string take_launch_error();  // first failed kernel launch since the last check ("" if none), cleared
 // transposed operators and the adjoint solve (mg_adjoint.cu); leaf-order
 // device vectors
 int adjoint_buffers(mg_tree *t);

@@ -18,6 +18,7 @@
 
 #include "mg_internal.h"
 #include "mg_device.cuh"
+#include "mg_exact.h"
 
 namespace mg {
 
@@ -325,7 +326,15 @@ __device__ __forceinline__ void bulk_wait0() { asm volatile("cp.async.bulk.wait_
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
 
-static constexpr uint32_t kWaitLimit = 1u << 20;
+static constexpr uint32_t kWaitLimit = kDefaultWaitLimit;
+
+// Bounded wait on an mbarrier phase: true once it completed, false after
+// `limit` polls (limit 0 gives up at once; a test setting of the tree).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, uint32_t limit) {
+    for (uint32_t tries = 0; tries < limit; tries++)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
 
 // HALF: half as many threads per CTA (two colour cells each), which wastes
 // less at the CTA barriers on levels with few blocks per SM.
@@ -396,17 +405,17 @@ __global__ void __launch_bounds__(kMaxThreads, (D == 3 && NT == 16) ? 1 : 5) k_s
     const bool cyl = P.geom == MG_CYL;
     const T helm = kp_helm<T>(P);
     for (int it = 0; g < nblocks; it++, g += gridDim.x) {
-        {
-            uint32_t tries = 0;
-            while (!mbar_try_wait(&bars[it & 1], (it >> 1) & 1))
-                if (++tries > kWaitLimit) {
-                    atomicExch(P.status, 1);
-                    s_abort = 1;
-                    break;
-                }
+        if (!mbar_wait_bounded(&bars[it & 1], (it >> 1) & 1, P.wait_limit)) {
+            atomicExch(P.status, 1);
+            s_abort = 1;
         }
         __syncthreads();
-        if (s_abort) break;
+        if (s_abort) {
+            // the copy this wait was for may still be landing in shared
+            // memory: let it arrive (normal bound) before the CTA exits
+            if (tid == 0) mbar_wait_bounded(&bars[it & 1], (it >> 1) & 1, kWaitLimit);
+            break;
+        }
         // every thread is past the previous block: its stage may be refilled
         // once its bulk store has read it
         if (tid == 0) {
@@ -583,17 +592,12 @@ __global__ void __launch_bounds__(32 * WARPS) k_sweep_warp(KParams P, int first,
     const bool cyl = P.geom == MG_CYL;
     const T helm = kp_helm<T>(P);
     for (int it = 0; g < nblocks; it++, g += stride) {
-        bool timed_out = false;
-        {
-            uint32_t tries = 0;
-            while (!mbar_try_wait(&bars[warp][it & 1], (it >> 1) & 1))
-                if (++tries > kWaitLimit) {
-                    timed_out = true;
-                    break;
-                }
-        }
+        const bool timed_out = !mbar_wait_bounded(&bars[warp][it & 1], (it >> 1) & 1, P.wait_limit);
         if (__any_sync(0xffffffffu, timed_out)) {
-            if (lane == 0) atomicExch(P.status, 1);
+            if (lane == 0) {  // let this warp's copy in flight land before it leaves
+                atomicExch(P.status, 1);
+                mbar_wait_bounded(&bars[warp][it & 1], (it >> 1) & 1, kWaitLimit);
+            }
             break;
         }
         __syncwarp();
@@ -802,17 +806,16 @@ __global__ void __launch_bounds__(32 * WARPS, WARPS == 8 ? ((FG && STAGES == 2) 
     fetch_desc(g + (STAGES - 1) * stride, g + stride);
     const T helm = kp_helm<T>(P);
     for (int it = 0; g < nblocks; it++, g += stride) {
-        bool timed_out = false;
-        {
-            uint32_t tries = 0;
-            while (!mbar_try_wait(&bars[warp][it % STAGES], (it / STAGES) & 1))
-                if (++tries > kWaitLimit) {
-                    timed_out = true;
-                    break;
-                }
-        }
+        const bool timed_out = !mbar_wait_bounded(&bars[warp][it % STAGES], (it / STAGES) & 1, P.wait_limit);
         if (__any_sync(0xffffffffu, timed_out)) {
-            if (lane == 0) atomicExch(P.status, 1);
+            if (lane == 0) {
+                // copies in flight: the blocks of iterations it .. it + STAGES - 2
+                // that exist; let them land (normal bound) before the warp leaves
+                atomicExch(P.status, 1);
+                for (int q = 0; q < STAGES - 1; q++)
+                    if (g + q * stride < nblocks)
+                        mbar_wait_bounded(&bars[warp][(it + q) % STAGES], ((it + q) / STAGES) & 1, kWaitLimit);
+            }
             break;
         }
         __syncwarp();
@@ -1169,17 +1172,17 @@ __global__ void __launch_bounds__(kMaxThreads) k_ghost_tma(KParams P, int first,
         fetch(g + (int)gridDim.x);
     }
     for (int it = 0; g < nblocks; it++, g += gridDim.x) {
-        {
-            uint32_t tries = 0;
-            while (!mbar_try_wait(&bars[it & 1], (it >> 1) & 1))
-                if (++tries > kWaitLimit) {
-                    atomicExch(P.status, 1);
-                    s_abort = 1;
-                    break;
-                }
+        if (!mbar_wait_bounded(&bars[it & 1], (it >> 1) & 1, P.wait_limit)) {
+            atomicExch(P.status, 1);
+            s_abort = 1;
         }
         __syncthreads();
-        if (s_abort) break;
+        if (s_abort) {
+            // the copy this wait was for may still be landing in shared
+            // memory: let it arrive (normal bound) before the CTA exits
+            if (tid == 0) mbar_wait_bounded(&bars[it & 1], (it >> 1) & 1, kWaitLimit);
+            break;
+        }
         if (tid == 0) {
             if (g + (int)gridDim.x < nblocks) issue(it + 1, first + g + gridDim.x, rco, rlev);
             fetch(g + 2 * (int)gridDim.x);
@@ -1270,17 +1273,17 @@ __global__ void __launch_bounds__(kMaxThreads) k_fas_tma(KParams P, int first, i
         fetch(g + (int)gridDim.x);
     }
     for (int it = 0; g < nblocks; it++, g += gridDim.x) {
-        {
-            uint32_t tries = 0;
-            while (!mbar_try_wait(&bars[it & 1], (it >> 1) & 1))
-                if (++tries > kWaitLimit) {
-                    atomicExch(P.status, 1);
-                    s_abort = 1;
-                    break;
-                }
+        if (!mbar_wait_bounded(&bars[it & 1], (it >> 1) & 1, P.wait_limit)) {
+            atomicExch(P.status, 1);
+            s_abort = 1;
         }
         __syncthreads();
-        if (s_abort) break;
+        if (s_abort) {
+            // the copy this wait was for may still be landing in shared
+            // memory: let it arrive (normal bound) before the CTA exits
+            if (tid == 0) mbar_wait_bounded(&bars[it & 1], (it >> 1) & 1, kWaitLimit);
+            break;
+        }
         if (tid == 0) {
             if (g + (int)gridDim.x < nblocks) {
                 bulk_wait_read0();  // the other stage's stores have left shared memory
@@ -1404,17 +1407,17 @@ __global__ void __launch_bounds__(kMaxThreads) k_prolong_tma(KParams P, int firs
     if (tid == 0 && g < nblocks) issue(0, first + g);
     auto bid = [](int a, int c, int e) { return D == 2 ? c * B + a : (e * B + c) * B + a; };
     for (int it = 0; g < nblocks; it++, g += gridDim.x) {
-        {
-            uint32_t tries = 0;
-            while (!mbar_try_wait(&bars[it & 1], (it >> 1) & 1))
-                if (++tries > kWaitLimit) {
-                    atomicExch(P.status, 1);
-                    s_abort = 1;
-                    break;
-                }
+        if (!mbar_wait_bounded(&bars[it & 1], (it >> 1) & 1, P.wait_limit)) {
+            atomicExch(P.status, 1);
+            s_abort = 1;
         }
         __syncthreads();
-        if (s_abort) break;
+        if (s_abort) {
+            // the copy this wait was for may still be landing in shared
+            // memory: let it arrive (normal bound) before the CTA exits
+            if (tid == 0) mbar_wait_bounded(&bars[it & 1], (it >> 1) & 1, kWaitLimit);
+            break;
+        }
         if (tid == 0 && g + (int)gridDim.x < nblocks) {
             bulk_wait_read0();  // the other stage's store has left shared memory
             issue(it + 1, first + g + gridDim.x);
@@ -1550,17 +1553,17 @@ __global__ void __launch_bounds__(128) k_prolong_rows(KParams P, int first, int 
     const int r = tid >> 1, h = tid & 1, j = r & 7, k = r >> 3;
     const int sy = (j & 1) ? 1 : -1, sz = (k & 1) ? 1 : -1;
     for (int it = 0; g < nblocks; it++, g += gridDim.x) {
-        {
-            uint32_t tries = 0;
-            while (!mbar_try_wait(&bars[it & 1], (it >> 1) & 1))
-                if (++tries > kWaitLimit) {
-                    atomicExch(P.status, 1);
-                    s_abort = 1;
-                    break;
-                }
+        if (!mbar_wait_bounded(&bars[it & 1], (it >> 1) & 1, P.wait_limit)) {
+            atomicExch(P.status, 1);
+            s_abort = 1;
         }
         __syncthreads();
-        if (s_abort) break;
+        if (s_abort) {
+            // the copy this wait was for may still be landing in shared
+            // memory: let it arrive (normal bound) before the CTA exits
+            if (tid == 0) mbar_wait_bounded(&bars[it & 1], (it >> 1) & 1, kWaitLimit);
+            break;
+        }
         if (tid == ISSUER) {
             if (g + (int)gridDim.x < nblocks) {
                 bulk_wait_read0();  // the other stage's store has left shared memory
@@ -1717,17 +1720,17 @@ __global__ void __launch_bounds__(64) k_prolong_rows2(KParams P, int first, int 
     if (tid == ISSUER && g < nblocks) issue(0, first + g);
     const int j = tid >> 2, qd = tid & 3, sy = (j & 1) ? 1 : -1;
     for (int it = 0; g < nblocks; it++, g += gridDim.x) {
-        {
-            uint32_t tries = 0;
-            while (!mbar_try_wait(&bars[it & 1], (it >> 1) & 1))
-                if (++tries > kWaitLimit) {
-                    atomicExch(P.status, 1);
-                    s_abort = 1;
-                    break;
-                }
+        if (!mbar_wait_bounded(&bars[it & 1], (it >> 1) & 1, P.wait_limit)) {
+            atomicExch(P.status, 1);
+            s_abort = 1;
         }
         __syncthreads();
-        if (s_abort) break;
+        if (s_abort) {
+            // the copy this wait was for may still be landing in shared
+            // memory: let it arrive (normal bound) before the CTA exits
+            if (tid == 0) mbar_wait_bounded(&bars[it & 1], (it >> 1) & 1, kWaitLimit);
+            break;
+        }
         if (tid == ISSUER && g + (int)gridDim.x < nblocks) {
             bulk_wait_read0();  // the other stage's store has left shared memory
             issue(it + 1, first + g + gridDim.x);
@@ -1874,17 +1877,17 @@ __global__ void __launch_bounds__(kMaxThreads, 4) k_restrict_tma(KParams P, int 
     // level descriptor: CTA-wide copy when every block shares it, else per block
     const bool cyl = P.geom == MG_CYL;
     for (int it = 0; g < nblocks; it++, g += gridDim.x) {
-        {
-            uint32_t tries = 0;
-            while (!mbar_try_wait(&bars[it & 1], (it >> 1) & 1))
-                if (++tries > kWaitLimit) {
-                    atomicExch(P.status, 1);
-                    s_abort = 1;
-                    break;
-                }
+        if (!mbar_wait_bounded(&bars[it & 1], (it >> 1) & 1, P.wait_limit)) {
+            atomicExch(P.status, 1);
+            s_abort = 1;
         }
         __syncthreads();
-        if (s_abort) break;
+        if (s_abort) {
+            // the copy this wait was for may still be landing in shared
+            // memory: let it arrive (normal bound) before the CTA exits
+            if (tid == 0) mbar_wait_bounded(&bars[it & 1], (it >> 1) & 1, kWaitLimit);
+            break;
+        }
         if (tid == 0 && g + (int)gridDim.x < nblocks) issue(it + 1, first + g + gridDim.x);
         const T *st = stage0 + (it & 1) * stage_elems;
         const BlockDesc &b = *reinterpret_cast<const BlockDesc *>(st);
@@ -2058,17 +2061,17 @@ __global__ void __launch_bounds__(128) k_restrict_rows(KParams P, int first, int
         for (int q = 0; q < 4; q += VW) vscatter(dst + q, *reinterpret_cast<const V *>(src + q));
     };
     for (int it = 0; g < nblocks; it++, g += gridDim.x) {
-        {
-            uint32_t tries = 0;
-            while (!mbar_try_wait(&bars[it & 1], (it >> 1) & 1))
-                if (++tries > kWaitLimit) {
-                    atomicExch(P.status, 1);
-                    s_abort = 1;
-                    break;
-                }
+        if (!mbar_wait_bounded(&bars[it & 1], (it >> 1) & 1, P.wait_limit)) {
+            atomicExch(P.status, 1);
+            s_abort = 1;
         }
         __syncthreads();
-        if (s_abort) break;
+        if (s_abort) {
+            // the copy this wait was for may still be landing in shared
+            // memory: let it arrive (normal bound) before the CTA exits
+            if (tid == 0) mbar_wait_bounded(&bars[it & 1], (it >> 1) & 1, kWaitLimit);
+            break;
+        }
         if (tid == ISSUER) {
             if (g + (int)gridDim.x < nblocks) issue(it + 1, g + gridDim.x, n1);
             n1 = n2;
@@ -2282,6 +2285,23 @@ __global__ void __launch_bounds__(kMaxThreads) k_resnorm(KParams P, int first, F
 // is formed in FP64 with the difference form sum_d w_d ((x_- - x_c) +
 // (x_+ - x_c)) (rounding error ~ eps |grad x| h rather than eps |x|).  Writes per-CTA partials (sum V r^2, sum V,
 // max |r|) and optionally r (leaf order) and (float) r into FP32 cells.
+// FP64 form of the constant-coefficient residual f - (sum_d w_d (x_d- + x_d+)
+// - diag x_c), for the cells the integer sum declines (non-cubic cells, or
+// inputs outside the normal range).  Not inlined: a short branch inlined into
+// the cell loop is evaluated under a predicate for every cell, spending the
+// FP64 pipe even where the integer sum was taken.
+__device__ __noinline__ double resid_const_fp64(double xc, double a0, double a1, double b0, double b1, double c0,
+                                                double c1, double f, double w0, double w1, double w2, double dg) {
+    double sx = w0 * (a0 + a1);
+    sx = fma(w1, b0 + b1, sx);
+    sx = fma(w2, c0 + c1, sx);
+    return f - fma(-dg, xc, sx);
+}
+
+// S 2^(emax - 1080) in FP64 arithmetic, for a result outside the normal range
+// (not inlined, for the reason above).
+__device__ __noinline__ double unfix_wide(int64_t S, int emax) { return ldexp((double)S, emax - 1080); }
+
 template <int D, int NT, bool MX = true>
 __global__ void __launch_bounds__(kMaxThreads, 3) k_resid_tma(KParams P, int first, int nblocks, Fields<double> F,
                                                               double *__restrict__ partials,
@@ -2297,6 +2317,7 @@ __global__ void __launch_bounds__(kMaxThreads, 3) k_resid_tma(KParams P, int fir
     __shared__ int s_abort;
     __shared__ double sred[3][kMaxThreads / 32];
     __shared__ float sredf[2][kMaxThreads / 32];
+    __shared__ int semax[kMaxThreads / 32];
     const bool var = F.E != nullptr, wc = F.W != nullptr;  // wc: precomputed face coefficients
     const int stage_elems = DESC + 2 * C + GH + (wc ? (2 * D + 1) * C : (var ? C + GH : 0));
     T *stage0 = reinterpret_cast<T *>(smem_raw);
@@ -2340,24 +2361,25 @@ __global__ void __launch_bounds__(kMaxThreads, 3) k_resid_tma(KParams P, int fir
     float acc_r = 0.f, acc_v = 0.f;
     double vol_u = 0;
     for (int it = 0; g < nblocks; it++, g += gridDim.x) {
-        {
-            uint32_t tries = 0;
-            while (!mbar_try_wait(&bars[it & 1], (it >> 1) & 1))
-                if (++tries > kWaitLimit) {
-                    atomicExch(P.status, 1);
-                    s_abort = 1;
-                    break;
-                }
+        if (!mbar_wait_bounded(&bars[it & 1], (it >> 1) & 1, P.wait_limit)) {
+            atomicExch(P.status, 1);
+            s_abort = 1;
         }
         __syncthreads();
-        if (s_abort) break;
+        if (s_abort) {
+            // the copy this wait was for may still be landing in shared
+            // memory: let it arrive (normal bound) before the CTA exits
+            if (tid == 0) mbar_wait_bounded(&bars[it & 1], (it >> 1) & 1, kWaitLimit);
+            break;
+        }
         if (tid == 0 && g + (int)gridDim.x < nblocks) issue(it + 1, first + g + gridDim.x);
-        const T *st = stage0 + (it & 1) * stage_elems;
+        T *st = stage0 + (it & 1) * stage_elems;
         const BlockDesc &b = *reinterpret_cast<const BlockDesc *>(st);
         const LevelDesc &L = *reinterpret_cast<const LevelDesc *>(reinterpret_cast<const char *>(st) + sizeof(BlockDesc));
         const double w0 = L.inv_h2[0], w1 = L.inv_h2[1], w2 = L.inv_h2[2];
         const double vol = L.vol;
-        const T *xs = st + DESC, *gs = xs + C, *fs = gs + GH, *es = fs + C, *egs = es + C;
+        T *xs = st + DESC;
+        const T *gs = xs + C, *fs = gs + GH, *es = fs + C, *egs = es + C;
         auto nbv = [&](const T *xi, const T *gi, int i, int j, int k, int d, int s) -> T {
             const int o = s ? 1 : -1;
             if (d == 0) {
@@ -2378,21 +2400,72 @@ __global__ void __launch_bounds__(kMaxThreads, 3) k_resid_tma(KParams P, int fir
         // are GB300's scarcest resource here; the rounding stays at
         // eps * sum_f w_f |x|, far below any tolerance the solves use
         const double dg = L.diag;
+        // Cubic cells, constant coefficient, no Helmholtz term: the stencil
+        // sum in exact integer arithmetic (mg_exact.h).  The block's values
+        // and ghosts are aligned once to their largest exponent, in place in
+        // the stage; per cell that leaves integer adds, one FP64 FMA and an
+        // integer rounding to FP32 (GB300's FP64 pipe is 1/64 of FP32).
+        const bool iso = !var && !cyl && helm0 && w0 == w1 && (D == 2 || w0 == w2);
+        int em = 0x7FF;
+        if (iso) {
+            int e = 1;
+            for (int q = tid; q < C + GH; q += nth) e = max(e, mg_expo(xs[q]));
+            e = __reduce_max_sync(0xffffffffu, e);
+            if ((tid & 31) == 0) semax[tid >> 5] = e;
+            __syncthreads();
+            em = 1;
+            for (int w = 0; w < (nth >> 5); w++) em = max(em, semax[w]);
+            if (em != 0x7FF) {  // a non-finite value anywhere: the FP64 form below
+                int64_t *xq = reinterpret_cast<int64_t *>(xs);
+                for (int q = tid; q < C + GH; q += nth) xq[q] = mg_fix(xs[q], em);
+            }
+            __syncthreads();
+        }
+        const int64_t *xi = reinterpret_cast<const int64_t *>(xs), *gi = xi + C;
+        auto nbi = [&](int i, int j, int k, int d, int s) -> int64_t {
+            const int o = s ? 1 : -1;
+            if (d == 0) {
+                const int ii = i + o;
+                if (ii < 0 || ii >= n) return gi[(s ? 1 : 0) * FC + (D == 2 ? j : j + n * k)];
+                return xi[cidx<D>(n, ii, j, k)];
+            }
+            if (d == 1) {
+                const int jj = j + o;
+                if (jj < 0 || jj >= n) return gi[(s ? 3 : 2) * FC + (D == 2 ? i : i + n * k)];
+                return xi[cidx<D>(n, i, jj, k)];
+            }
+            const int kk = k + o;
+            if (kk < 0 || kk >= n) return gi[(s ? 5 : 4) * FC + i + n * j];
+            return xi[cidx<D>(n, i, j, kk)];
+        };
         double bs2 = 0;
         const float lo0f = P.lo0f, h0f = L.h0f, hvf = L.hvf;
         vol_u = vol;
         for (int c = tid; c < C; c += nth) {
             const int i = c % n, j = (c / n) % n, k = D == 3 ? c / (n * n) : 0;
-            const double xc = xs[c];
             double lap;  // A x + lambda x (the residual below subtracts lambda x)
             double r;
-            if (!var && !cyl) {
-                double sx = w0 * (nbv(xs, gs, i, j, k, 0, 0) + nbv(xs, gs, i, j, k, 0, 1));
-                sx = fma(w1, nbv(xs, gs, i, j, k, 1, 0) + nbv(xs, gs, i, j, k, 1, 1), sx);
-                if (D == 3) sx = fma(w2, nbv(xs, gs, i, j, k, 2, 0) + nbv(xs, gs, i, j, k, 2, 1), sx);
-                r = fs[c] - fma(-dg, xc, sx);
+            float rf = 0.f;
+            bool have_rf = false;
+            if (iso && em != 0x7FF) {
+                int64_t S = -(int64_t)(2 * D) * xi[c];
+#pragma unroll
+                for (int f = 0; f < 2 * D; f++) S += nbi(i, j, k, f >> 1, f & 1);
+                double sd;
+                if (!mg_unfix(S, em, sd)) sd = unfix_wide(S, em);  // outside the normal range
+                r = fma(-w0, sd, fs[c]);
+                rf = mg_to_float(r);
+                have_rf = true;
+                lap = 0;
+            } else if (!var && !cyl) {
+                const double xc = xs[c];
+                r = resid_const_fp64(xc, nbv(xs, gs, i, j, k, 0, 0), nbv(xs, gs, i, j, k, 0, 1),
+                                     nbv(xs, gs, i, j, k, 1, 0), nbv(xs, gs, i, j, k, 1, 1),
+                                     D == 3 ? nbv(xs, gs, i, j, k, 2, 0) : 0.0, D == 3 ? nbv(xs, gs, i, j, k, 2, 1) : 0.0,
+                                     fs[c], w0, w1, D == 3 ? w2 : 0.0, dg);
                 lap = 0;
             } else if (wc) {
+                const double xc = xs[c];
                 const double *ws = es + c;  // coefficients [face][cell], the diagonal last
                 double sx = ws[0] * nbv(xs, gs, i, j, k, 0, 0);
 #pragma unroll
@@ -2400,6 +2473,7 @@ __global__ void __launch_bounds__(kMaxThreads, 3) k_resid_tma(KParams P, int fir
                 r = fs[c] - fma(-ws[2 * D * C], xc, sx);
                 lap = 0;
             } else {
+                const double xc = xs[c];
                 const double ec = var ? es[c] : 1.0;
                 double ri = 0;
                 if (cyl) ri = P.lo[0] + (b.ijk[0] * n + i + 0.5) * L.h[0];
@@ -2418,7 +2492,7 @@ __global__ void __launch_bounds__(kMaxThreads, 3) k_resid_tma(KParams P, int fir
                     }
                 r = helm0 ? fs[c] - lap : fs[c] - (lap - P.helm * xc);
             }
-            const float rf = (float)r;
+            if (!have_rf) rf = (float)r;
             if (MX) {
                 if (cyl) {
                     const double V = 2.0 * M_PI * (P.lo[0] + (b.ijk[0] * n + i + 0.5) * L.h[0]) * L.h[0] * L.h[1];
@@ -2617,10 +2691,31 @@ __global__ void k_coarse_apply_b(const TreeCoarse *__restrict__ TC, const int2 *
 }
 
 // --------------------------------------------------- elementwise ops ----
+// phi64 += e32 (the defect-correction update).  The widening of e is exact
+// and done with integer operations (mg_from_float; GB300 runs the
+// conversion instruction on its FP64 pipe), leaving one FP64 add per cell.
 __global__ void k_add_e(const float *__restrict__ e, double *__restrict__ x, long long n) {
     pdl_entry();
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-        x[i] += (double)e[i];
+        x[i] += mg_from_float(e[i]);
+}
+// The same on the leaf cells only (one contiguous range per level or
+// segment): covered cells are restored from their children before the next
+// residual, and the levels below the leaves are rebuilt by every cycle.
+constexpr int kMaxLeafRanges = 96;
+struct LeafRanges {
+    int n;
+    long long start[kMaxLeafRanges], len[kMaxLeafRanges];
+};
+__global__ void k_add_e_leaf(LeafRanges R, const float *__restrict__ e, double *__restrict__ x) {
+    pdl_entry();
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (int r = 0; r < R.n; r++) {
+        double *xr = x + R.start[r];
+        const float *er = e + R.start[r];
+        for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < R.len[r]; i += stride)
+            xr[i] += mg_from_float(er[i]);
+    }
 }
 __global__ void k_cast_f32(const double *__restrict__ a, float *__restrict__ b, long long n) {
     pdl_entry();
@@ -2903,11 +2998,29 @@ KParams kparams(mg_tree *t, int homog) {
     P.uniform = t->is_batch ? 0 : 1;
     P.lo0f = (float)t->lo[0];
     P.helmf = (float)t->helm;
+    P.wait_limit = t->wait_limit;
     return P;
 }
 
+// The dynamic shared-memory ceiling of a kernel is a property of the kernel,
+// shared by every tree and launch site: it only ever rises, so a launch
+// asking for less never lowers it under another launch that needs more.  It
+// is raised for any request, not only above 48 KB: the kernel's static
+// shared memory counts against the same default limit.
 template <class K> static void set_smem(K kernel, size_t bytes) {
-    if (bytes > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (bytes == 0) return;
+    static std::mutex mu;
+    static std::vector<std::pair<const void *, size_t>> ceil;
+    std::lock_guard<std::mutex> lock(mu);
+    for (auto &c : ceil)
+        if (c.first == (const void *)kernel) {
+            if (c.second >= bytes) return;
+            c.second = bytes;
+            cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+            return;
+        }
+    ceil.push_back({(const void *)kernel, bytes});
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
 // resident CTAs per SM of a kernel at (threads, dynamic smem), queried once
@@ -3093,12 +3206,16 @@ template <class T, int D> struct Launch {
             std::vector<int> cands;
             for (int cand = 0; cand < kNumSweepVariants; cand++)
                 if (cand_ok(t, (int)l, F, cand)) cands.push_back(cand);
-            // warm-up (clocks, caches, first-launch costs), then the minimum
-            // over three interleaved rounds of four launches per candidate
+            // warm-up (clocks, caches, first-launch costs), then the median
+            // of five interleaved rounds of four launches per candidate; of
+            // the candidates within 3 % of the fastest median the lowest
+            // variant number wins, so near-ties resolve the same way in
+            // every process
             for (int cand : cands)
                 for (int w = 0; w < 4; w++) sweep_cand(t, P, (int)l, F, w & 1, cand);
-            std::vector<float> best(cands.size(), 1e30f);
-            for (int round = 0; round < 3; round++)
+            constexpr int kRounds = 5;
+            std::vector<std::vector<float>> times(cands.size());
+            for (int round = 0; round < kRounds; round++)
                 for (size_t ci = 0; ci < cands.size(); ci++) {
                     cudaEventRecord(e0, t->stream);
                     for (int w = 0; w < 4; w++) sweep_cand(t, P, (int)l, F, w & 1, cands[ci]);
@@ -3106,11 +3223,17 @@ template <class T, int D> struct Launch {
                     cudaEventSynchronize(e1);
                     float ms = 0;
                     cudaEventElapsedTime(&ms, e0, e1);
-                    best[ci] = std::min(best[ci], ms);
+                    times[ci].push_back(ms);
                 }
+            std::vector<float> med(cands.size());
             float bmin = 1e30f;
+            for (size_t ci = 0; ci < cands.size(); ci++) {
+                std::sort(times[ci].begin(), times[ci].end());
+                med[ci] = times[ci][kRounds / 2];
+                bmin = std::min(bmin, med[ci]);
+            }
             for (size_t ci = 0; ci < cands.size(); ci++)
-                if (best[ci] < bmin) { bmin = best[ci]; t->sweep_choice[prec][l] = cands[ci]; }
+                if (med[ci] <= 1.03f * bmin) { t->sweep_choice[prec][l] = cands[ci]; break; }
         }
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
@@ -3242,11 +3365,17 @@ template <class T, int D> struct Launch {
         for (size_t l = 0; l < t->lev.size(); l++)
             if (t->lev[l].coarsest && t->lev[l].group <= top) ghost(t, P, (int)l, F.X, F.XG, 0);
     }
+    // smoothing steps on level l: the per-level schedule where one is set
+    // (mg_set_schedule), else the cycle's n_down / n_up
+    static int steps(const mg_tree *t, int l, int n, bool down) {
+        const std::vector<int> &s = down ? t->sched_down : t->sched_up;
+        return (l < (int)s.size() && s[l] >= 0) ? s[l] : n;
+    }
     static void vcycle(mg_tree *t, Fields<T> &F, int top, int nd, int nu, int homog, int strict = 0) {
         const KParams P = kparams(t, homog);
         for (int g = top; g >= 1; g--) {
             for (int l : t->groups[g])
-                if (!t->lev[l].coarsest) smooth(t, P, l, F, nd);
+                if (!t->lev[l].coarsest) smooth(t, P, l, F, steps(t, l, nd, true));
             restrict_group(t, P, g, F);
         }
         coarse(t, P, F, top, strict);
@@ -3254,7 +3383,7 @@ template <class T, int D> struct Launch {
             for (int l : t->groups[g])
                 if (!t->lev[l].coarsest) {
                     prolong(t, P, l, F);
-                    smooth(t, P, l, F, nu);
+                    smooth(t, P, l, F, steps(t, l, nu, false));
                 }
     }
     static void fmg(mg_tree *t, Fields<T> &F, int nd, int nu, int homog) {
@@ -3647,7 +3776,19 @@ void sub_scalar(mg_tree *t, double *x, double c, long long n) {
 
 void add_e_to_phi(mg_tree *t, const float *e, double *phi) {
     ++t->launches;
-    launch_k(k_add_e, 1216, 256, 0, t->stream, e, phi, t->ncells);
+    LeafRanges R;
+    R.n = 0;
+    for (const LevelHost &L : t->lev) {
+        if (L.nb <= L.nref) continue;
+        if (R.n == kMaxLeafRanges) {  // more leaf ranges than the parameter block holds: every cell
+            launch_k(k_add_e, 1216, 256, 0, t->stream, e, phi, t->ncells);
+            return;
+        }
+        R.start[R.n] = t->blocks[L.first + L.nref].cell_off;
+        R.len[R.n] = (long long)(L.nb - L.nref) * (t->dim == 2 ? L.n * L.n : L.n * L.n * L.n);
+        R.n++;
+    }
+    launch_k(k_add_e_leaf, 1216, 256, 0, t->stream, R, e, phi);
 }
 
 void copy_eps_to_f32(mg_tree *t) {
@@ -3896,13 +4037,34 @@ void project(mg_tree *t, const double *B, double *Bout) {
     else project_d<3>(t, B, Bout);
 }
 
+// "kernel name <<<grid, block, smem>>>" of the recorded failed launch
+static std::string launch_fail_text() {
+    const char *name = nullptr;
+    if (cudaFuncGetName(&name, g_launch_fail.kern) != cudaSuccess || !name) name = "?";
+    cudaGetLastError();
+    return std::string(name) + " <<<" + std::to_string(g_launch_fail.grid) + ", " +
+           std::to_string(g_launch_fail.block) + ", " + std::to_string(g_launch_fail.smem) + " B>>>";
+}
+
 int check_cuda(const char *what) {
     cudaError_t e = cudaGetLastError();
+    const int le = g_launch_error.exchange(0);
+    std::string where;
+    if (le) {
+        where = " (launch of " + launch_fail_text() + ")";
+        if (e == cudaSuccess) e = (cudaError_t)le;
+    }
     if (e != cudaSuccess) {
-        mg_set_error(std::string(what) + ": " + cudaGetErrorString(e));
+        mg_set_error(std::string(what) + ": " + cudaGetErrorString(e) + where);
         return MG_ERR_CUDA;
     }
     return MG_OK;
+}
+
+std::string take_launch_error() {
+    const int le = g_launch_error.exchange(0);
+    if (!le) return std::string();
+    return std::string(cudaGetErrorString((cudaError_t)le)) + " in " + launch_fail_text();
 }
 
 }  // namespace mg

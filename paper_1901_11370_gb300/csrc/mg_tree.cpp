@@ -753,7 +753,7 @@ static int check_status(mg_tree *t) {
     CK(cudaMemcpy(&st, t->d_status, sizeof(int), cudaMemcpyDeviceToHost));
     if (st) {
         CK(cudaMemset(t->d_status, 0, sizeof(int)));
-        return fail(MG_ERR_TIMEOUT, "a bounded wait in a sweep kernel expired");
+        return fail(MG_ERR_TIMEOUT, "a bounded wait in a kernel expired");
     }
     return MG_OK;
 }
@@ -780,10 +780,15 @@ template <class Fn> static int run_graph(mg_tree *t, const std::string &key, Fn 
         t->stream = t->cap_stream;
         cudaError_t e = cudaStreamBeginCapture(t->cap_stream, cudaStreamCaptureModeRelaxed);
         if (e == cudaSuccess) enqueue();
+        const std::string le = take_launch_error();  // a launch refused during capture is missing from the graph
         cudaGraph_t g = nullptr;
         cudaError_t e2 = cudaStreamEndCapture(t->cap_stream, &g);
         t->stream = user;
         cudaGetLastError();
+        if (!le.empty()) {
+            if (g) cudaGraphDestroy(g);
+            return fail(MG_ERR_CUDA, "kernel launch failed while capturing " + key + ": " + le);
+        }
         if (e != cudaSuccess || e2 != cudaSuccess || !g) {
             if (g) cudaGraphDestroy(g);
             t->use_graphs = false;  // capture unavailable: launch directly from now on
@@ -920,7 +925,7 @@ static int use_params(mg_tree *t, const mg_params *p, mg_params *q, std::string 
     char buf[96];
     snprintf(buf, sizeof(buf), ":%d:%d:s%d:%a", q->n_down, q->n_up, q->smoother,
              q->smoother == MG_SMOOTH_JACOBI ? om : 0.0);
-    if (key) *key = buf;
+    if (key) *key = buf + t->sched_key;
     return MG_OK;
 }
 
@@ -1160,6 +1165,131 @@ extern "C" int mg_clean_adjoint(mg_tree *t, const double *gBnew, double *gB, con
     if (rel_out) *rel_out = rel;
     if (!std::isfinite(rel)) return fail(MG_ERR_NAN, "adjoint residual is not finite");
     if (rel > rel_tol) return fail(MG_ERR_NOT_CONVERGED, "clean adjoint: max_cycles reached");
+    return MG_OK;
+}
+
+extern "C" int mg_set_schedule(mg_tree *t, int n, const int *down, const int *up) {
+    if (!t) return fail(MG_ERR_ARG, "null tree");
+    if (n < 0 || (n > 0 && (!down || !up))) return fail(MG_ERR_ARG, "bad schedule arguments");
+    if (!t->built) {
+        int rc;
+        if ((rc = build(t))) return rc;
+    }
+    if (n > (int)t->lev.size()) return fail(MG_ERR_ARG, "schedule longer than the level count");
+    for (int l = 0; l < n; l++)
+        if (down[l] < -1 || up[l] < -1 || down[l] > 16 || up[l] > 16)
+            return fail(MG_ERR_ARG, "smoothing steps per level must lie in [-1, 16]");
+    t->sched_down.assign(down, down + n);
+    t->sched_up.assign(up, up + n);
+    t->sched_key.clear();
+    if (n) {
+        t->sched_key = ":S";
+        for (int l = 0; l < n; l++) t->sched_key += std::to_string(down[l]) + "," + std::to_string(up[l]) + ";";
+    }
+    return MG_OK;
+}
+
+extern "C" int mg_get_schedule(mg_tree *t, int n, int *down, int *up) {
+    if (!t || n < 0 || (n > 0 && (!down || !up))) return fail(MG_ERR_ARG, "bad schedule arguments");
+    for (int l = 0; l < n; l++) {
+        down[l] = l < (int)t->sched_down.size() ? t->sched_down[l] : -1;
+        up[l] = l < (int)t->sched_up.size() ? t->sched_up[l] : -1;
+    }
+    return MG_OK;
+}
+
+// mg_tune_schedule: time full solves of the tree's current problem for a
+// set of candidate schedules and keep the fastest that converges.
+extern "C" int mg_tune_schedule(mg_tree *t, double rel_tol, int max_cycles, int precision, int *inner_out,
+                                double *ms_out) {
+    NEED_FINAL(t);
+    if (t->is_batch) return fail(MG_ERR_UNSUPPORTED, "schedule tuning works on one tree");
+    if (!(rel_tol > 0) || max_cycles < 1) return fail(MG_ERR_ARG, "rel_tol > 0 and max_cycles >= 1 required");
+    if (precision != MG_FP64 && precision != MG_FP32_DC) return fail(MG_ERR_ARG, "unknown precision");
+    const int nl = (int)t->lev.size();
+    int lmin = nl;  // lowest level with leaves: the "leaf" levels are lmin..nl-1
+    for (int l = 0; l < nl; l++)
+        if (t->lev[l].nb > t->lev[l].nref) { lmin = l; break; }
+    struct Cand { int dl, ul, dc, uc, inner; };
+    std::vector<Cand> cands = {{2, 2, 2, 2, 1}, {1, 1, 1, 1, 1}, {1, 2, 1, 2, 1}, {2, 1, 2, 1, 1}, {3, 3, 3, 3, 1},
+                               {1, 1, 2, 2, 1}, {2, 2, 1, 1, 1}, {1, 1, 3, 3, 1}, {1, 2, 2, 2, 1}};
+    if (precision == MG_FP32_DC) cands.push_back({2, 2, 2, 2, 2});
+    // save phi (cells and ghosts) to restore it afterwards
+    double *save = nullptr;
+    CK(cudaMalloc((void **)&save, sizeof(double) * (size_t)(t->ncells + t->nghost)));
+    CK(cudaMemcpyAsync(save, t->f64.X, sizeof(double) * t->ncells, cudaMemcpyDeviceToDevice, t->stream));
+    CK(cudaMemcpyAsync(save + t->ncells, t->f64.XG, sizeof(double) * t->nghost, cudaMemcpyDeviceToDevice, t->stream));
+    const std::vector<int> old_down = t->sched_down, old_up = t->sched_up;
+    const std::string old_key = t->sched_key;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    double best = 1e300;
+    int best_i = -1, rc = MG_OK;
+    std::string report;  // every candidate's outcome, for the error message
+    for (size_t i = 0; i < cands.size() && rc == MG_OK; i++) {
+        const Cand &c = cands[i];
+        std::vector<int> d(nl), u(nl);
+        for (int l = 0; l < nl; l++) {
+            d[l] = l >= lmin ? c.dl : c.dc;
+            u[l] = l >= lmin ? c.ul : c.uc;
+        }
+        mg_set_schedule(t, nl, d.data(), u.data());
+        mg_params q{2, 2, precision, c.inner, MG_SMOOTH_RBGS, 0.0};
+        float fastest = 1e30f;
+        bool ok = true;
+        for (int rep = 0; rep < 3 && ok; rep++) {  // the first run captures the graphs
+            cudaMemsetAsync(t->f64.X, 0, sizeof(double) * t->ncells, t->stream);
+            refresh<double>(t, t->f64, 0);
+            cudaEventRecord(e0, t->stream);
+            int cyc = 0;
+            double rel = 0;
+            const int r = mg_solve(t, rel_tol, max_cycles, 1, &q, &cyc, &rel);
+            cudaEventRecord(e1, t->stream);
+            cudaEventSynchronize(e1);
+            if (r == MG_ERR_NOT_CONVERGED || r == MG_ERR_NAN) ok = false;
+            else if (r != MG_OK) rc = r;
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rep) fastest = std::min(fastest, ms);
+            if (rep == 0 || r != MG_OK) {
+                char buf[128];
+                snprintf(buf, sizeof buf, " [%d,%d|%d,%d x%d: rc %d, %d cycles, rel %.2e]", c.dl, c.ul, c.dc, c.uc,
+                         c.inner, r, cyc, rel);
+                report += buf;
+            }
+        }
+        if (ok && rc == MG_OK && fastest < best) { best = fastest; best_i = (int)i; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    CK(cudaMemcpyAsync(t->f64.X, save, sizeof(double) * t->ncells, cudaMemcpyDeviceToDevice, t->stream));
+    CK(cudaMemcpyAsync(t->f64.XG, save + t->ncells, sizeof(double) * t->nghost, cudaMemcpyDeviceToDevice, t->stream));
+    CK(cudaStreamSynchronize(t->stream));
+    cudaFree(save);
+    if (rc != MG_OK || best_i < 0) {
+        t->sched_down = old_down;
+        t->sched_up = old_up;
+        t->sched_key = old_key;
+        return rc != MG_OK ? rc : fail(MG_ERR_NOT_CONVERGED, "no candidate schedule reached rel_tol:" + report);
+    }
+    const Cand &c = cands[best_i];
+    std::vector<int> d(nl), u(nl);
+    for (int l = 0; l < nl; l++) {
+        d[l] = l >= lmin ? c.dl : c.dc;
+        u[l] = l >= lmin ? c.ul : c.uc;
+    }
+    mg_set_schedule(t, nl, d.data(), u.data());
+    if (inner_out) *inner_out = c.inner;
+    if (ms_out) *ms_out = best;
+    return MG_OK;
+}
+
+extern "C" int mg_set_wait_limit(mg_tree *t, int64_t polls) {
+    if (!t) return fail(MG_ERR_ARG, "null tree");
+    if (polls > 0xFFFFFFFFll) return fail(MG_ERR_ARG, "wait limit above 2^32 - 1");
+    t->wait_limit = polls < 0 ? kDefaultWaitLimit : (uint32_t)polls;
+    drop_graphs(t);  // captured launches carry the old limit
     return MG_OK;
 }
 

@@ -376,3 +376,35 @@ def test_jacobi_mixed_precision_solve(mg):
     assert o.residual_norm()[0] <= 1.5e-10 * r0
     with pytest.raises(mg.MGError):
         t.vcycle(1, smoother=mg.MG_SMOOTH_JACOBI, omega=1.5)
+
+
+@pytest.mark.parametrize("name", ["gauss3d_amr", "cyl_amr", "varcoef3d_b16"])
+def test_per_level_schedule_matches_oracle(mg, name):
+    """A non-default schedule of smoothing steps per level (mg_set_schedule)
+    runs the same cycles as the oracle's per-level schedule."""
+    p = CASES[name]
+    t, o = both(mg, p)
+    nl = len(o.levels())
+    down = [(l % 3) + 1 for l in range(nl)]
+    up = [3 - (l % 3) for l in range(nl)]
+    t.set_schedule(down, up)
+    o.set_schedule(down, up)
+    assert list(t.schedule()[0]) == down
+    t.fmg(); o.fmg()
+    t.vcycle(2); o.vcycle(2)
+    assert rel_diff(t.get_phi().cpu().numpy(), o.get_phi()) < TOL
+
+
+def test_schedule_tuner_picks_a_converging_schedule(mg):
+    import torch
+    p = CASES["varcoef3d_b16"]
+    t, o = both(mg, p)
+    inner, ms = t.tune_schedule(1e-10, 60, mg.MG_FP32_DC)
+    assert inner in (1, 2) and ms > 0
+    d, u = t.schedule()
+    assert (d >= 0).all() and (u >= 0).all()
+    t.set_phi(torch.zeros(t.n_leaf, dtype=torch.float64, device="cuda"))
+    cyc, rel = t.solve(1e-10, 60, precision=mg.MG_FP32_DC, inner_cycles=inner)
+    o.set_phi(t.get_phi().cpu().numpy())
+    r0 = Oracle.from_problem(p).residual_norm()[0]
+    assert rel <= 1e-10 and o.residual_norm()[0] <= 1.05e-10 * r0
