@@ -139,62 +139,86 @@ def dist_env():
     return world, rank, local
 
 
-def oracle_baseline(p, n_leaf):
-    """FP64 oracle on a bounded sample: cycles to 1e-10 from the oracle's own
-    solve of the 32^3-base variant of the mesh (same radii and seed), times
-    the oracle's measured cost of one V-cycle plus one residual norm on the
-    full workload (FMG counted as one V-cycle, which favours the oracle)."""
-    from oracle import Oracle
-    from synth import workloads as W
-    small = W.cfg2_gauss3d(base=32, N=8, seed=0)
-    os_ = Oracle.from_problem(small)
-    cycles, _ = os_.solve(TOL, MAX_CYCLES)
-    del os_
-    o = Oracle.from_problem(p)
+def oracle_solve_time(o, threads):
+    """Wall seconds of one full FP64 oracle solve from phi = 0 to a composite
+    relative residual of 1e-10 (FMG, then V-cycles, the schedule the GPU
+    runs), with `threads` threads over the blocks of each level."""
+    import oracle
+    used = oracle.set_threads(threads)
     t0 = time.perf_counter()
-    o.vcycle(1)
-    t1 = time.perf_counter()
-    o.residual_norm()
-    t2 = time.perf_counter()
-    per = (t1 - t0) + (t2 - t1)
-    value = n_leaf / (cycles * per)
-    return {"value": value, "unit": "unknowns/s", "cores": 1, "kind": "oracle",
-            "sample": "1 FAS V-cycle (%.1f s) + 1 residual norm (%.1f s) of the FP64 C oracle on the full "
-                      "%d-unknown workload, scaled by the %d cycles the oracle needs to 1e-10 on the "
-                      "32^3-base variant" % (t1 - t0, t2 - t1, n_leaf, cycles)}
+    cycles, hist = o.solve(TOL, MAX_CYCLES)
+    dt = time.perf_counter() - t0
+    return dt, cycles, hist[-1] / hist[0], used
+
+
+def oracle_baseline(p, n_leaf):
+    """The FP64 C oracle timed on this host: the full solve of the benchmark
+    workload to 1e-10, once on every host core (OpenMP over the blocks of a
+    level; the result is bit-identical for any thread count) and once on a
+    single core.  Mesh construction and input setup are not timed."""
+    from oracle import Oracle
+    o = Oracle.from_problem(p)
+    cores = os.cpu_count() or 1
+    dt_all, cyc, rel, used = oracle_solve_time(o, cores)
+    dt_one, cyc1, _, _ = oracle_solve_time(o, 1)
+    import oracle
+    oracle.set_threads(cores)
+    return {"value": n_leaf / dt_all, "unit": "unknowns/s", "cores": used, "kind": "oracle",
+            "host_cpus": cores, "cycles_to_tol": cyc, "final_rel_residual": rel, "seconds": dt_all,
+            "sample": "one full solve (FMG + %d V-cycles to 1e-10) of the FP64 C oracle on the full %d-unknown "
+                      "workload, %d threads" % (cyc - 1, n_leaf, used),
+            "single_thread": {"value": n_leaf / dt_one, "cores": 1, "seconds": dt_one, "cycles_to_tol": cyc1}}
 
 
 def run_reference(args):
+    """The reference arm: the FP64 C oracle (the paper's method written out
+    plainly), one full solve to 1e-10 of the benchmark workload per step on
+    every host core.  Rank 0 alone under torchrun."""
     world, rank, _ = dist_env()
     if rank != 0:
         return
+    import oracle
+    from oracle import Oracle
     from synth import workloads as W
     p = problem()
     n_leaf = W.n_leaf_cells(p)
-    from oracle import Oracle
-    small = W.cfg2_gauss3d(base=32, N=8, seed=0)
-    cycles, _ = Oracle.from_problem(small).solve(TOL, MAX_CYCLES)
     o = Oracle.from_problem(p)
-    times = []
+    cores = os.cpu_count() or 1
+    times, cyc, rel, used = [], 0, 0.0, 1
     for s in range(args.warmup + args.steps):
-        t0 = time.perf_counter()
-        o.vcycle(1)
-        o.residual_norm()
-        dt = time.perf_counter() - t0
+        dt, cyc, rel, used = oracle_solve_time(o, cores)
         if s >= args.warmup:
             times.append(dt)
     per = sum(times) / len(times)
-    value = n_leaf / (cycles * per)
-    sample = ("each step: 1 FAS V-cycle + 1 residual norm of the FP64 C oracle on the full %d-unknown "
-              "workload (%.2f s); unknowns/s scaled by the %d cycles to 1e-10 the oracle needs on the "
-              "32^3-base variant" % (n_leaf, per, cycles))
+    value = n_leaf / per
+    sample = ("each step: one full solve (FMG + %d V-cycles, phi = 0 to 1e-10 relative residual) of the FP64 C "
+              "oracle on the full %d-unknown workload, %d threads" % (cyc - 1, n_leaf, used))
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "unknowns/s", "n_gpus": world,
-           "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3 * cycles,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-           "data": "synthetic", "config": {"workload": WORKLOAD, "unknowns": n_leaf, "parallelism": "single core"},
-           "cpu_baseline": {"value": value, "unit": "unknowns/s", "cores": 1, "kind": "oracle", "sample": sample},
+           "data": "synthetic", "config": {"workload": WORKLOAD, "unknowns": n_leaf, "cycles_to_tol": cyc,
+                                          "final_rel_residual": rel, "parallelism": "%d host threads" % used},
+           "cpu_baseline": {"value": value, "unit": "unknowns/s", "cores": used, "kind": "oracle", "sample": sample},
            "e2e": {"value": value, "unit": "unknowns/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
+
+
+def solve_alg_bytes(levels, n_leaf, cycles, precision, dim=3):
+    """Algorithmic HBM bytes of one solve by the per-cell minimum traffic of
+    a V(2,2) cycle (each sweep reads x and f once and writes x once; the
+    transfers read and write each level once; constant coefficient):
+    FP64 cycles 136 B per cell of every level (3D) plus the composite
+    residual (read phi, f: 16 B per leaf); FP32 cycles in FP64 defect
+    correction 68 B per level cell (4 sweeps x 12 + residual/restriction 8 +
+    prolongation 8 + coarse terms 4) plus, per leaf, the FP64 residual (read
+    phi and f, write the FP32 defect: 20 B) and update (read e, phi, write
+    phi: 20 B).  FMG counts as one cycle."""
+    level_cells = sum(l["nb"] * l["n"] ** dim for l in levels)
+    if precision == "fp64":
+        per = (136 if dim == 3 else 144) * level_cells + 16 * n_leaf
+    else:
+        per = (68 if dim == 3 else 72) * level_cells + 40 * n_leaf
+    return cycles * per, level_cells
 
 
 def run_ours(args):
@@ -317,11 +341,18 @@ def run_ours(args):
     e2e_ms = max_over_ranks(e0.elapsed_time(e1) / args.steps)
     assert torch.equal(out_host[(args.steps - 1) % 2], phi_dev[(args.steps - 1) % 2].cpu())
 
-    # roofline of the dominant kernel (fused red-black sweep) on the largest level
+    # roofline of the dominant kernel (fused red-black sweep) on the largest
+    # level.  Algorithmic bytes: 12 B per cell per FP32 sweep (read x and f
+    # once, write x once), i.e. 6 B per cell for one colour launch, 12 B in
+    # FP64; the DRAM bytes ncu measured for the same launch are reported
+    # beside it
     (ms_s, ms_g, b_s, b_g), lev = tree.time_sweeps(n_sweeps=8, precision=mg.MG_FP32_DC)
     (ms_s64, _, b_s64, _), _ = tree.time_sweeps(n_sweeps=4, precision=mg.MG_FP64)
     peak, peak_kind = peak_hbm()
-    achieved = b_s / (ms_s * 1e-3) / 1e9
+    lv = tree.levels()[lev]
+    lev_cells = lv["nb"] * lv["n"] ** 3
+    alg = 6.0 * lev_cells
+    achieved = alg / (ms_s * 1e-3) / 1e9
     var32 = tree.sweep_variant(lev, mg.MG_FP32_DC)
     var64 = tree.sweep_variant(lev, mg.MG_FP64)
     kname = {0: "k_sweep_tma", 1: "k_sweep", 2: "k_sweep_warp", 3: "k_sweep_warp", 4: "k_sweep_rows",
@@ -329,8 +360,10 @@ def run_ours(args):
              9: "k_sweep_rows", 10: "k_sweep_tma"}.get(var32, "k_sweep")
     traffic = measured_traffic(kname, "sweep_f32_traffic.txt")
     if traffic is not None:
-        lv = tree.levels()[lev]
-        traffic *= lv["nb"] * lv["n"] ** 3
+        traffic *= lev_cells
+    levels = tree.levels()
+    sb32, level_cells = solve_alg_bytes(levels, n, cyc_mixed, "fp32_dc")
+    sb64, _ = solve_alg_bytes(levels, n, cyc64, "fp64")
 
     total_unknowns = n * world
     value = total_unknowns / (ms_mixed * 1e-3)
@@ -354,15 +387,26 @@ def run_ours(args):
         "roofline": {"bound": "hbm", "kernel": "%s, FP32, one colour, level %d (autotuned variant %d: %s)" % (
                          kname, lev, var32, tree.SWEEP_VARIANTS.get(var32)),
                      "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": traffic, "alg_bytes_per_launch": b_s,
+                     "frac": achieved / peak, "traffic": traffic,
+                     "alg_bytes_per_launch": alg, "alg_bytes_per_cell": 6.0, "level_cells": lev_cells,
                      "ms_per_launch": ms_s,
-                     "fp64_sweep": {"ms_per_launch": ms_s64, "achieved_GBs": b_s64 / (ms_s64 * 1e-3) / 1e9,
+                     "achieved_dram_GBs": None if traffic is None else traffic / (ms_s * 1e-3) / 1e9,
+                     "achieved_dram_frac": None if traffic is None else traffic / (ms_s * 1e-3) / 1e9 / peak,
+                     "fp64_sweep": {"ms_per_launch": ms_s64, "alg_bytes_per_cell": 12.0,
+                                    "achieved_GBs": 12.0 * lev_cells / (ms_s64 * 1e-3) / 1e9,
                                     "variant": tree.SWEEP_VARIANTS.get(var64)},
-                     "ghost_fill_ms_per_launch": ms_g, "ghost_fill_achieved_GBs": b_g / (ms_g * 1e-3) / 1e9},
+                     "ghost_fill_ms_per_launch": ms_g, "ghost_fill_achieved_GBs": b_g / (ms_g * 1e-3) / 1e9,
+                     "solve": {"alg_bytes_fp32_dc": sb32, "alg_bytes_fp64": sb64, "level_cells": level_cells,
+                               "frac_fp32_dc": sb32 / (ms_mixed * 1e-3) / 1e9 / peak,
+                               "frac_fp64": sb64 / (ms64 * 1e-3) / 1e9 / peak}},
     }
     if not args.no_batch:
         del tree
         result["batch"] = batch_measure(args, mg, W, barrier, max_over_ranks)
+    if not args.no_cfg3:
+        result["cfg3"] = cfg3_measure(args, mg, W, barrier, max_over_ranks)
+    if args.cfg5_base > 0:
+        result["cfg5"] = cfg5_measure(args, mg, W, barrier, max_over_ranks, args.cfg5_base)
     if not args.no_mesh and rank == 0:
         try:
             result["mesh"] = mesh_measure(mg)
@@ -374,6 +418,121 @@ def run_ours(args):
         print(json.dumps(result))
     if dist is not None:
         dist.destroy_process_group()
+
+
+CFG3_WORKLOAD = ("3D variable-coefficient Poisson, 256^3 uniform in 16^3 blocks, eps = 100 inside a seeded sphere "
+                 "of radius 0.25 and 1 outside, Neumann on the x faces and periodic in y and z, right-hand side a "
+                 "zero-mean Gaussian random field (correlation length 0.05)")
+
+
+def cfg3_measure(args, mg, W, barrier, max_over_ranks):
+    """The variable-coefficient workload at its stated size: FP32 cycles in
+    FP64 defect correction and plain FP64, each from phi = 0 to 1e-10 (the
+    zero-mean solution of this singular problem); the relative difference of
+    the two solutions; and the adjoint of L = 1/2 sum V (phi - t)^2 (t an
+    independent Gaussian random field, seed 1, scaled to rms(phi)) solved to
+    a relative adjoint residual of 1e-10, dL/df and dL/deps both returned."""
+    import torch
+    world, _, _ = dist_env()
+    p = W.cfg3_varcoef3d()
+    t = mg.Tree.from_problem(p)
+    n = t.n_leaf
+    zeros = torch.zeros(n, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    steps = max(1, min(args.steps, 3))
+    out = {"workload": CFG3_WORKLOAD, "unknowns": n * world}
+    phis = {}
+    for name, prec in (("fp32_dc", mg.MG_FP32_DC), ("fp64", mg.MG_FP64)):
+        t.set_phi(zeros)
+        t.solve(TOL, 80, fmg_first=True, precision=prec)
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            t.set_phi(zeros)
+            cyc, rel = t.solve(TOL, 80, fmg_first=True, precision=prec)
+        e1.record(stream)
+        barrier()
+        ms = max_over_ranks(e0.elapsed_time(e1) / steps)
+        phis[name] = t.get_phi().clone()
+        out[name] = {"value": n * world / (ms * 1e-3), "unit": "unknowns/s", "ms_per_step": ms, "cycles_to_tol": cyc,
+                     "final_rel_residual": rel}
+    d = phis["fp32_dc"] - phis["fp64"]
+    out["fp32_dc_vs_fp64_rel_err"] = float(d.norm() / phis["fp64"].norm())
+    g1 = W.random_field(256, 0.05, 1, 3)
+    I, J, K, _ = W.leaf_cell_index(p)
+    tgt = torch.from_numpy(g1[I, J, K]).cuda()
+    phi = phis["fp64"]
+    tgt *= phi.pow(2).mean().sqrt() / tgt.pow(2).mean().sqrt()
+    g = (phi - tgt) / n
+    t.set_phi(phi)
+    t.adjoint(g, rel_tol=TOL, max_cycles=120)
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    t.adjoint(g, rel_tol=TOL, max_cycles=120)
+    e1.record(stream)
+    barrier()
+    ms = max_over_ranks(e0.elapsed_time(e1))
+    it, rel = t.last_adjoint
+    out["adjoint"] = {"ms": ms, "iterations": it, "final_rel_residual": rel, "unknowns_per_s": n * world / (ms * 1e-3),
+                      "outputs": "dL/df and dL/deps (FP64)"}
+    del t
+    torch.cuda.empty_cache()
+    return out
+
+
+CFG5_WORKLOAD = ("3D divergence cleaning on a periodic %d^3-base octree of 16^3 blocks, 2 levels refined where max |B| "
+                 "of a block is in the top 10%%, B a k^-5/3 Gaussian field (rms 1) plus a non-solenoidal blob "
+                 "(peak 3 rms, width 0.05); FP32 cycles in FP64 defect correction to 1e-10, then the adjoint of "
+                 "L = 1/2 sum V |B_new - B_t|^2")
+
+
+def cfg5_measure(args, mg, W, barrier, max_over_ranks, base):
+    """The cleaning workload: inputs from the seeded generator (k^-5/3 field
+    plus blob, refinement by the |B| decile; not timed), one cleaning step
+    (div B, zero-mean projection, FP32 + FP64 defect-correction solve to
+    1e-10, B - grad phi: mg_clean) and the adjoint pass for
+    L = 1/2 sum V |B_new - B_t|^2 with B_t an independent k^-5/3 field
+    (mg_clean_adjoint to an adjoint residual of 1e-10), each timed with CUDA
+    events after one warm-up run."""
+    import torch
+    world, _, _ = dist_env()
+    t0 = time.perf_counter()
+    ci = W.CleanInputs(n=base, N=16)
+    p = ci.problem
+    B = torch.from_numpy(ci.leaf_fields()).cuda()
+    Bt = torch.from_numpy(ci.target()).cuda()
+    gen_s = time.perf_counter() - t0
+    t = mg.Tree.from_problem(p)
+    n = t.n_leaf
+    vol = t.leaf_volumes()
+    stream = torch.cuda.current_stream()
+    out = {"workload": CFG5_WORKLOAD % base, "unknowns": n * world, "refinements": len(ci.refine),
+           "input_generation_s": gen_s}
+
+    def timed(fn):
+        fn()
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r = fn()
+        e1.record(stream)
+        barrier()
+        return max_over_ranks(e0.elapsed_time(e1)), r
+
+    ms, (Bn, f, cyc, rel) = timed(lambda: t.clean(B, TOL, 60, precision=mg.MG_FP32_DC))
+    out["clean"] = {"ms": ms, "value": n * world / (ms * 1e-3), "unit": "unknowns/s", "cycles_to_tol": cyc,
+                    "final_rel_residual": rel, "div_B_l2_before": float(f.norm()),
+                    "precision": "FP32 V(2,2) cycles in FP64 defect correction"}
+    gBn = vol * (Bn - Bt)
+    ms, gB = timed(lambda: t.clean_adjoint(gBn, TOL, 80))
+    it, rel = t.last_adjoint
+    out["adjoint"] = {"ms": ms, "unknowns_per_s": n * world / (ms * 1e-3), "iterations": it,
+                      "final_rel_residual": rel, "outputs": "dL/dB (3 FP64 components)"}
+    del t, B, Bt, Bn, gBn, gB, f
+    torch.cuda.empty_cache()
+    return out
 
 
 BATCH_WORKLOAD = ("batch of 512 independent 2D cylindrical (r,z) trees, side 16k cells with k ~ U{2..32} in 16^2 "
@@ -561,6 +720,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 512-tree batch measurement")
     ap.add_argument("--no-mesh", action="store_true", help="skip the 1024^3 mesh construction measurement")
+    ap.add_argument("--no-cfg3", action="store_true", help="skip the 256^3 variable-coefficient workload")
+    ap.add_argument("--cfg5-base", type=int, default=512,
+                    help="base grid of the divergence-cleaning workload (0: skip it)")
     ap.add_argument("--profile", choices=["sweeps64", "sweeps32", "solve32", "solve64", "batch32"], default=None)
     ap.add_argument("--pin-sweeps", default="",
                     help="with --profile sweeps*/solve*: 'level:variant,...' sweep kernels to pin after tuning")

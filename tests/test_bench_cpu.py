@@ -43,3 +43,14 @@ def test_benchmark_workloads_have_their_stated_sizes():
     from synth import workloads as W
     assert W.n_leaf_cells(bench.problem()) == 19827200
     assert sum(W.n_leaf_cells(W.cyl_ring_tree(i)) for i in range(512)) == 54636032
+
+
+def test_solve_algorithmic_bytes():
+    """Per-solve algorithmic bytes: per level cell 136 B (FP64 V(2,2), 3D) or
+    68 B (FP32 cycle), per leaf 16 B (FP64 composite residual) or 40 B (FP64
+    residual and update of the defect correction), times the cycles."""
+    lv = [{"nb": 1, "n": 8}, {"nb": 8, "n": 8}]
+    b64, cells = bench.solve_alg_bytes(lv, 4096, 3, "fp64")
+    assert cells == 4608 and b64 == 3 * (136 * 4608 + 16 * 4096)
+    b32, _ = bench.solve_alg_bytes(lv, 4096, 3, "fp32_dc")
+    assert b32 == 3 * (68 * 4608 + 40 * 4096)
