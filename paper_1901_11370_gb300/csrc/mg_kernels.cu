@@ -2445,8 +2445,6 @@ __global__ void __launch_bounds__(kMaxThreads, 3) k_resid_tma(KParams P, int fir
             const int i = c % n, j = (c / n) % n, k = D == 3 ? c / (n * n) : 0;
             double lap;  // A x + lambda x (the residual below subtracts lambda x)
             double r;
-            float rf = 0.f;
-            bool have_rf = false;
             if (iso && em != 0x7FF) {
                 int64_t S = -(int64_t)(2 * D) * xi[c];
 #pragma unroll
@@ -2454,8 +2452,6 @@ __global__ void __launch_bounds__(kMaxThreads, 3) k_resid_tma(KParams P, int fir
                 double sd;
                 if (!mg_unfix(S, em, sd)) sd = unfix_wide(S, em);  // outside the normal range
                 r = fma(-w0, sd, fs[c]);
-                rf = mg_to_float(r);
-                have_rf = true;
                 lap = 0;
             } else if (!var && !cyl) {
                 const double xc = xs[c];
@@ -2492,7 +2488,7 @@ __global__ void __launch_bounds__(kMaxThreads, 3) k_resid_tma(KParams P, int fir
                     }
                 r = helm0 ? fs[c] - lap : fs[c] - (lap - P.helm * xc);
             }
-            if (!have_rf) rf = (float)r;
+            const float rf = mg_to_float(r);  // integer rounding: no FP64-pipe conversion
             if (MX) {
                 if (cyl) {
                     const double V = 2.0 * M_PI * (P.lo[0] + (b.ijk[0] * n + i + 0.5) * L.h[0]) * L.h[0] * L.h[1];
