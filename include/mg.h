@@ -74,14 +74,25 @@ enum { MG_SMOOTH_RBGS = 0, MG_SMOOTH_JACOBI = 1 };
  * defect-correction loop (mg_solve only); inner_cycles is the number of FP32
  * V-cycles per outer FP64 residual.  smoother MG_SMOOTH_RBGS or
  * MG_SMOOTH_JACOBI; omega the Jacobi weight (<= 0: 4/5 in 2D, 6/7 in 3D;
- * at most 1).  A NULL mg_params means 2 / 2, FP64, one inner cycle, red-black
- * Gauss-Seidel. */
+ * at most 1).  coarse_mode MG_COARSE_EXACT solves the coarsest level
+ * exactly (dense FP64 inverse); MG_COARSE_SMOOTH is the paper's coarse-grid
+ * solve: red-black Gauss-Seidel sweeps of the coarsest level (FP64) until
+ * max |r| there is at most coarse_abs_tol or at most coarse_rel_tol times its
+ * value before the first sweep, or coarse_max_it sweeps (values <= 0 take the
+ * paper's defaults 1e-8, 1e-8, 1000); it needs the coarsest level of each
+ * tree to fit one CTA's shared memory (MG_ERR_UNSUPPORTED otherwise).  A
+ * NULL mg_params means 2 / 2, FP64, one inner cycle, red-black Gauss-Seidel,
+ * exact coarsest solve. */
+enum { MG_COARSE_EXACT = 0, MG_COARSE_SMOOTH = 1 };
 typedef struct {
     int n_down, n_up;
     int precision;
     int inner_cycles;
     int smoother;
     double omega;
+    int coarse_mode;
+    int coarse_max_it;
+    double coarse_abs_tol, coarse_rel_tol;
 } mg_params;
 
 /*

@@ -54,6 +54,7 @@ def _load():
     L.or_level_info.argtypes = [C.c_void_p, C.c_int, _ip, _dp]
     L.or_set_cycle.argtypes = [C.c_void_p, C.c_int, C.c_int]
     L.or_set_schedule.argtypes = [C.c_void_p, C.c_int, _ip, _ip]
+    L.or_set_coarse_mode.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_double, C.c_int]
     L.or_set_smoother.argtypes = [C.c_void_p, C.c_int, C.c_double]
     L.or_set_homogeneous.argtypes = [C.c_void_p, C.c_int]
     L.or_num_leaf_cells.restype = C.c_int64
@@ -210,6 +211,11 @@ class Oracle:
         d = np.ascontiguousarray(down, np.int32)
         u = np.ascontiguousarray(up, np.int32)
         self.L.or_set_schedule(self._h, len(d), d, u)
+
+    def set_coarse_mode(self, smooth=False, abs_tol=1e-8, rel_tol=1e-8, max_it=1000):
+        """Coarsest-level solve: exact (default) or the paper's smoothing to
+        an absolute / relative max-norm threshold (Sec. 2.4, reading R20)."""
+        self.L.or_set_coarse_mode(self._h, 1 if smooth else 0, float(abs_tol), float(rel_tol), int(max_it))
 
     def set_smoother(self, jacobi=False, omega=0.0):
         """Red-black Gauss-Seidel (default) or weighted Jacobi (omega <= 0:

@@ -49,6 +49,9 @@
  *      composite operator: the forward steps (restriction of covered cells,
  *      ghost fills, stencil) undone in reverse order with transposed
  *      coefficients; A is not symmetric at refinement faces (Sec. 2.6);
+ *  R20 the paper's coarse-grid solve (Sec. 2.4) is red-black smoothing of
+ *      the coarsest level until max |r| meets an absolute or relative
+ *      threshold or N_max sweeps; the max norm is this oracle's reading;
  *  R15 phi carried to an adapted mesh (Sec. 2.5 leaves the data to the
  *      caller): a leaf block that is also a block of the old mesh keeps its
  *      values (the restriction of its former children where a refinement
@@ -104,6 +107,11 @@ typedef struct {
     double omega;   /* Jacobi weight */
     /* coarsest-level dense factorisation */
     int nc, nsys, singular, lu_ok;
+    /* coarsest-level solve: 0 exact (dense LU), 1 smoothing as in Sec. 2.4
+     * (reading R20): up to coarse_max_it sweeps until max |r| is at most
+     * coarse_abs or coarse_rel times its value before the first sweep */
+    int coarse_mode, coarse_max_it;
+    double coarse_abs, coarse_rel;
     double *lu;
     int *piv;
 } Tree;
@@ -794,8 +802,89 @@ static void lu_solve(const Tree *T, double *x) {
  * problem without Dirichlet faces the bordered system also imposes
  * sum V (v + dv) = 0.
  */
+/* max |f - L v| over the coarsest level (ghosts current) */
+static double coarse_max_res(Tree *T) {
+    Lev *lv = &T->L[0];
+    int n = lv->n, ps = P(T, n), nk = T->dim == 3 ? n : 1;
+    double mx = 0.0;
+    for (int b = 0; b < lv->nb; b++)
+        for (int k = 0; k < nk; k++)
+            for (int j = 0; j < n; j++)
+                for (int i = 0; i < n; i++) {
+                    double r = lv->f[(size_t)b * ps + pidx(T, n, i, j, k)] - apply_L(T, lv, lv->phi, b, i, j, k);
+                    if (fabs(r) > mx) mx = fabs(r);
+                }
+    return mx;
+}
+
+/* volume-weighted mean of a field over the coarsest level */
+static double coarse_mean(Tree *T, const double *X) {
+    Lev *lv = &T->L[0];
+    int n = lv->n, ps = P(T, n), nk = T->dim == 3 ? n : 1;
+    double sv = 0.0, s = 0.0;
+    for (int b = 0; b < lv->nb; b++)
+        for (int k = 0; k < nk; k++)
+            for (int j = 0; j < n; j++)
+                for (int i = 0; i < n; i++) {
+                    int G[3]; cell_global(lv, b, i, j, k, G);
+                    double V = cell_volume(T, lv, G);
+                    s += V * X[(size_t)b * ps + pidx(T, n, i, j, k)];
+                    sv += V;
+                }
+    return s / sv;
+}
+
+static void coarse_add(Tree *T, double *X, double c) {
+    Lev *lv = &T->L[0];
+    int n = lv->n, ps = P(T, n), nk = T->dim == 3 ? n : 1;
+    for (int b = 0; b < lv->nb; b++)
+        for (int k = 0; k < nk; k++)
+            for (int j = 0; j < n; j++)
+                for (int i = 0; i < n; i++) X[(size_t)b * ps + pidx(T, n, i, j, k)] += c;
+}
+
+/*
+ * The coarse-grid solve the paper describes (Sec. 2.4, reading R20):
+ * red-black Gauss-Seidel sweeps on the coarsest level, up to coarse_max_it,
+ * until max |f - L v| is at most coarse_abs or at most coarse_rel times its
+ * value before the first sweep.  On a problem without Dirichlet faces the
+ * level's right-hand side is first projected to zero volume-weighted mean
+ * (the constants are in the null space, so smoothing cannot remove that
+ * part of the residual), and v is returned with zero mean, as the bordered
+ * exact solve returns it.
+ */
+static void coarse_smooth(Tree *T) {
+    Lev *lv = &T->L[0];
+    if (T->singular) coarse_add(T, lv->f, -coarse_mean(T, lv->f));
+    ghost_fill(T, 0, F_PHI);
+    double r0 = coarse_max_res(T);
+    for (int it = 0; it < T->coarse_max_it; it++) {
+        if (r0 <= T->coarse_abs) break;
+        smooth_colour(T, 0, 0);
+        smooth_colour(T, 0, 1);
+        double r = coarse_max_res(T);
+        if (r <= T->coarse_abs || r <= T->coarse_rel * r0) break;
+    }
+    if (T->singular) {
+        coarse_add(T, lv->phi, -coarse_mean(T, lv->phi));
+        ghost_fill(T, 0, F_PHI);
+    }
+}
+
+void or_set_coarse_mode(void *h, int mode, double abs_tol, double rel_tol, int max_it) {
+    Tree *T = h;
+    T->coarse_mode = mode;
+    T->coarse_abs = abs_tol;
+    T->coarse_rel = rel_tol;
+    T->coarse_max_it = max_it;
+}
+
 static void coarse_solve(Tree *T) {
     Lev *lv = &T->L[0];
+    if (T->coarse_mode == 1) {
+        coarse_smooth(T);
+        return;
+    }
     if (!T->lu_ok) factor_coarse(T);
     int n = lv->n, ps = P(T, n), cpb = C(T, n), nk = T->dim == 3 ? n : 1;
     double *x = calloc(T->nsys, sizeof(double));

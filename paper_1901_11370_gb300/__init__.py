@@ -17,6 +17,7 @@ from ._lib import MGError, check  # noqa: F401
 MG_CART, MG_CYL = 0, 1
 MG_FP64, MG_FP32_DC = 0, 1
 MG_SMOOTH_RBGS, MG_SMOOTH_JACOBI = 0, 1
+MG_COARSE_EXACT, MG_COARSE_SMOOTH = 0, 1
 
 
 def _ptr(t: torch.Tensor):
@@ -24,8 +25,10 @@ def _ptr(t: torch.Tensor):
     return C.c_void_p(t.data_ptr())
 
 
-def _params(n_down=2, n_up=2, precision=MG_FP64, inner_cycles=1, smoother=MG_SMOOTH_RBGS, omega=0.0):
-    return _lib.mg_params(n_down, n_up, precision, inner_cycles, smoother, float(omega))
+def _params(n_down=2, n_up=2, precision=MG_FP64, inner_cycles=1, smoother=MG_SMOOTH_RBGS, omega=0.0,
+            coarse_mode=MG_COARSE_EXACT, coarse_max_it=1000, coarse_abs_tol=1e-8, coarse_rel_tol=1e-8):
+    return _lib.mg_params(n_down, n_up, precision, inner_cycles, smoother, float(omega), int(coarse_mode),
+                          int(coarse_max_it), float(coarse_abs_tol), float(coarse_rel_tol))
 
 
 class Tree:
@@ -154,12 +157,12 @@ class Tree:
         return out
 
     # ------------------------------------------------------------- cycles --
-    def vcycle(self, n=1, n_down=2, n_up=2, smoother=MG_SMOOTH_RBGS, omega=0.0):
-        p = _params(n_down, n_up, smoother=smoother, omega=omega)
+    def vcycle(self, n=1, n_down=2, n_up=2, smoother=MG_SMOOTH_RBGS, omega=0.0, coarse_mode=MG_COARSE_EXACT):
+        p = _params(n_down, n_up, smoother=smoother, omega=omega, coarse_mode=coarse_mode)
         check(self.L.mg_vcycle(self._h, n, C.byref(p)))
 
-    def fmg(self, n_down=2, n_up=2, smoother=MG_SMOOTH_RBGS, omega=0.0):
-        p = _params(n_down, n_up, smoother=smoother, omega=omega)
+    def fmg(self, n_down=2, n_up=2, smoother=MG_SMOOTH_RBGS, omega=0.0, coarse_mode=MG_COARSE_EXACT):
+        p = _params(n_down, n_up, smoother=smoother, omega=omega, coarse_mode=coarse_mode)
         check(self.L.mg_fmg(self._h, C.byref(p)))
 
     def residual_norm(self, want_res=False):
@@ -176,8 +179,8 @@ class Tree:
         return l2.value, li.value
 
     def solve(self, rel_tol=1e-10, max_cycles=50, fmg_first=True, precision=MG_FP64, inner_cycles=1,
-              n_down=2, n_up=2, raise_on_fail=True, smoother=MG_SMOOTH_RBGS, omega=0.0):
-        p = _params(n_down, n_up, precision, inner_cycles, smoother, omega)
+              n_down=2, n_up=2, raise_on_fail=True, smoother=MG_SMOOTH_RBGS, omega=0.0, coarse_mode=MG_COARSE_EXACT):
+        p = _params(n_down, n_up, precision, inner_cycles, smoother, omega, coarse_mode)
         cyc, rel = C.c_int(), C.c_double()
         rc = self.L.mg_solve(self._h, float(rel_tol), int(max_cycles), int(bool(fmg_first)), C.byref(p),
                              C.byref(cyc), C.byref(rel))
@@ -372,12 +375,12 @@ class Batch:
         check(self.L.mg_batch_get_phi(self._h, self._leaf(out)))
         return out
 
-    def vcycle(self, n=1, n_down=2, n_up=2, smoother=MG_SMOOTH_RBGS, omega=0.0):
-        p = _params(n_down, n_up, smoother=smoother, omega=omega)
+    def vcycle(self, n=1, n_down=2, n_up=2, smoother=MG_SMOOTH_RBGS, omega=0.0, coarse_mode=MG_COARSE_EXACT):
+        p = _params(n_down, n_up, smoother=smoother, omega=omega, coarse_mode=coarse_mode)
         check(self.L.mg_batch_vcycle(self._h, n, C.byref(p)))
 
-    def fmg(self, n_down=2, n_up=2, smoother=MG_SMOOTH_RBGS, omega=0.0):
-        p = _params(n_down, n_up, smoother=smoother, omega=omega)
+    def fmg(self, n_down=2, n_up=2, smoother=MG_SMOOTH_RBGS, omega=0.0, coarse_mode=MG_COARSE_EXACT):
+        p = _params(n_down, n_up, smoother=smoother, omega=omega, coarse_mode=coarse_mode)
         check(self.L.mg_batch_fmg(self._h, C.byref(p)))
 
     def residual_norms(self):
@@ -387,8 +390,8 @@ class Batch:
         return l2, li
 
     def solve(self, rel_tol=1e-10, max_cycles=50, fmg_first=True, precision=MG_FP64, inner_cycles=1,
-              n_down=2, n_up=2, raise_on_fail=True, smoother=MG_SMOOTH_RBGS, omega=0.0):
-        p = _params(n_down, n_up, precision, inner_cycles, smoother, omega)
+              n_down=2, n_up=2, raise_on_fail=True, smoother=MG_SMOOTH_RBGS, omega=0.0, coarse_mode=MG_COARSE_EXACT):
+        p = _params(n_down, n_up, precision, inner_cycles, smoother, omega, coarse_mode)
         cyc = C.c_int()
         rel = np.zeros(len(self.trees))
         rc = self.L.mg_batch_solve(self._h, float(rel_tol), int(max_cycles), int(bool(fmg_first)), C.byref(p),

@@ -43,7 +43,8 @@ class mg_bc(C.Structure):
 
 class mg_params(C.Structure):
     _fields_ = [("n_down", C.c_int), ("n_up", C.c_int), ("precision", C.c_int), ("inner_cycles", C.c_int),
-                ("smoother", C.c_int), ("omega", C.c_double)]
+                ("smoother", C.c_int), ("omega", C.c_double), ("coarse_mode", C.c_int), ("coarse_max_it", C.c_int),
+                ("coarse_abs_tol", C.c_double), ("coarse_rel_tol", C.c_double)]
 
 
 _lib = None

@@ -161,6 +161,10 @@ struct mg_tree {
     double *d_jac64 = nullptr;     // Jacobi scratch, FP64 and FP32 cycles
     float *d_jac32 = nullptr;
     int smoother = MG_SMOOTH_RBGS; // of the current call (mg_params)
+    int coarse_mode = MG_COARSE_EXACT;  // coarsest-level solve of the current call
+    int coarse_max_it = 1000;
+    double coarse_abs = 1e-8, coarse_rel = 1e-8;
+    int coarse_pad = 0;            // padded cells of the largest coarsest level (smoothing mode)
     double omega = 0.8;            // Jacobi weight of the current call
     double *d_minv = nullptr;      // coarsest-level inverses, row-major ns x ns per tree
     long long minv_total = 0, cvec_total = 0;

@@ -2667,6 +2667,195 @@ __global__ void __launch_bounds__(1024) k_coarse_resid_b(KParams P, const TreeCo
     }
 }
 
+// The coarse-grid solve of the paper (Sec. 2.4): red-black Gauss-Seidel on
+// the coarsest level until max |f - L x| is at most abs_tol, or at most
+// rel_tol times its value before the first sweep, or max_it sweeps.  One CTA
+// per tree: the tree's coarsest level is a complete grid, held in shared
+// memory (FP64, as the coarsest solve always is) with one layer of padding
+// that takes the ghost rules of Sec. 2.6 (periodic wrap, Dirichlet
+// 2a - x_i, Neumann x_i -/+ h b, axis x_i; the coefficient copies x_i).
+// Without Dirichlet faces f is first projected to zero volume-weighted mean
+// and x returned with zero mean.
+struct CoarseSmooth {
+    double abs_tol, rel_tol;
+    int max_it;
+};
+template <class T, int D>
+__global__ void __launch_bounds__(1024) k_coarse_gs(KParams P, const TreeCoarse *__restrict__ TC, int top, int strict,
+                                                    Fields<T> F, CoarseSmooth cs) {
+    pdl_entry();
+    const TreeCoarse tc = TC[blockIdx.x];
+    if (strict ? tc.group >= top : tc.group > top) return;
+    const LevelDesc &L = P.L[tc.lvl];
+    const int n = tc.n, C = cells_of<D>(n);
+    const int nx = L.ncell[0], ny = L.ncell[1], nz = D == 3 ? L.ncell[2] : 1;
+    const int px = nx + 2, py = ny + 2, pz = D == 3 ? nz + 2 : 1;
+    const int npad = px * py * pz;
+    extern __shared__ __align__(16) double sm[];
+    double *sx = sm, *sf = sx + npad, *se = sf + npad;  // se only with variable eps
+    const bool var = F.E != nullptr, cyl = P.geom == MG_CYL;
+    __shared__ double red[32];
+    auto pad = [&](int I, int J, int K) { return ((D == 3 ? (K + 1) : 0) * py + (J + 1)) * px + (I + 1); };
+    auto vol = [&](int I) {
+        double V = 1.0;
+        for (int d = 0; d < D; d++) V *= L.h[d];
+        if (cyl) V = 2.0 * M_PI * (P.lo[0] + (I + 0.5) * L.h[0]) * L.h[0] * L.h[1];
+        return V;
+    };
+    // block-wide reductions (sum or max) of one value per thread
+    auto reduce = [&](double v, bool mx) {
+        for (int o = 16; o > 0; o >>= 1) {
+            const double w = __shfl_down_sync(0xffffffffu, v, o);
+            v = mx ? fmax(v, w) : v + w;
+        }
+        __syncthreads();
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+        __syncthreads();
+        double a = mx ? 0.0 : 0.0;
+        for (int e = 0; e < (int)(blockDim.x >> 5); e++) a = mx ? fmax(a, red[e]) : a + red[e];
+        return a;
+    };
+    for (int row = threadIdx.x; row < tc.nc; row += blockDim.x) {
+        const BlockDesc &b = P.B[tc.first + row / C];
+        int i, j, k;
+        cell_of(row % C, n, D, i, j, k);
+        const int q = pad(b.ijk[0] * n + i, b.ijk[1] * n + j, D == 3 ? b.ijk[2] * n + k : 0);
+        sx[q] = (double)F.X[b.cell_off + row % C];
+        sf[q] = (double)F.F[b.cell_off + row % C];
+        if (var) se[q] = (double)F.E[b.cell_off + row % C];
+    }
+    __syncthreads();
+    // the padding layer of x (and once of eps) from the interior
+    auto fill = [&](double *A, bool coef) {
+        const int nface = 2 * (ny * nz) + 2 * (nx * nz) + (D == 3 ? 2 * nx * ny : 0);
+        for (int t = threadIdx.x; t < nface; t += blockDim.x) {
+            int face, u = t, a, c;
+            if (u < 2 * ny * nz) { face = u / (ny * nz); u %= ny * nz; a = u % ny; c = u / ny; }
+            else if ((u -= 2 * ny * nz) < 2 * nx * nz) { face = 2 + u / (nx * nz); u %= nx * nz; a = u % nx; c = u / nx; }
+            else { u -= 2 * nx * nz; face = 4 + u / (nx * ny); u %= nx * ny; a = u % nx; c = u / nx; }
+            const int d = face >> 1, s = face & 1, N = d == 0 ? nx : (d == 1 ? ny : nz);
+            int I, J, K;  // interior cell beside the padding cell
+            if (d == 0) { I = s ? nx - 1 : 0; J = a; K = c; }
+            else if (d == 1) { I = a; J = s ? ny - 1 : 0; K = c; }
+            else { I = a; J = c; K = s ? nz - 1 : 0; }
+            int gI = I + (d == 0 ? (s ? 1 : -1) : 0), gJ = J + (d == 1 ? (s ? 1 : -1) : 0),
+                gK = K + (d == 2 ? (s ? 1 : -1) : 0);
+            const double xi = A[pad(I, J, K)];
+            double g;
+            if (P.bct[face] == MG_BC_PERIODIC) {
+                int wI = I, wJ = J, wK = K;  // the cell on the other side of the domain
+                if (d == 0) wI = s ? 0 : nx - 1;
+                else if (d == 1) wJ = s ? 0 : ny - 1;
+                else wK = s ? 0 : nz - 1;
+                g = A[pad(wI, wJ, wK)];
+            } else if (coef) {
+                g = xi;
+            } else {
+                double a0 = 0.0;
+                if (!P.homog) {
+                    const int t1 = d == 0 ? 1 : 0, t2 = D == 2 ? -1 : (d == 2 ? 1 : 2);
+                    const int G1 = t1 == 0 ? I : J, G2 = t2 < 0 ? 0 : (t2 == 1 ? J : K);
+                    a0 = L.bc_off[face] < 0 ? P.bcv[face]
+                                            : P.bcplanes[L.bc_off[face] + G1 + (t2 >= 0 ? (long long)L.ncell[t1] * G2 : 0)];
+                }
+                switch (P.bct[face]) {
+                case MG_BC_DIRICHLET: g = 2.0 * a0 - xi; break;
+                case MG_BC_NEUMANN: g = s ? xi + L.h[d] * a0 : xi - L.h[d] * a0; break;
+                default: g = xi; break;
+                }
+            }
+            (void)N;
+            A[pad(gI, gJ, gK)] = g;
+        }
+    };
+    if (var) fill(se, true);
+    fill(sx, false);
+    __syncthreads();
+    // row weights of cell (I,J,K) (Sec. 2.2): sum w x_nb and sum w
+    auto row_terms = [&](int I, int J, int K, double &num, double &den) {
+        const int q = pad(I, J, K);
+        num = 0.0;
+        den = 0.0;
+        const double ec = var ? se[q] : 1.0;
+        const double ri = P.lo[0] + (I + 0.5) * L.h[0];
+#pragma unroll
+        for (int d = 0; d < D; d++)
+#pragma unroll
+            for (int s = 0; s < 2; s++) {
+                const int o = s ? 1 : -1;
+                const int qn = pad(I + (d == 0 ? o : 0), J + (d == 1 ? o : 0), K + (d == 2 ? o : 0));
+                double w = L.inv_h2[d];
+                if (var) w *= 2.0 * ec * se[qn] / (ec + se[qn]);
+                if (cyl && d == 0) w *= (P.lo[0] + (I + s) * L.h[0]) / ri;
+                num += w * sx[qn];
+                den += w;
+            }
+    };
+    const int ncell = nx * ny * nz;
+    auto max_res = [&]() {
+        double m = 0.0;
+        for (int c = threadIdx.x; c < ncell; c += blockDim.x) {
+            const int I = c % nx, J = (c / nx) % ny, K = D == 3 ? c / (nx * ny) : 0;
+            double num, den;
+            row_terms(I, J, K, num, den);
+            const double xc = sx[pad(I, J, K)];
+            m = fmax(m, fabs(sf[pad(I, J, K)] - (num - den * xc - P.helm * xc)));
+        }
+        return reduce(m, true);
+    };
+    auto mean = [&](const double *A) {
+        double a = 0.0, v = 0.0;
+        for (int c = threadIdx.x; c < ncell; c += blockDim.x) {
+            const int I = c % nx, J = (c / nx) % ny, K = D == 3 ? c / (nx * ny) : 0;
+            const double V = vol(I);
+            a += V * A[pad(I, J, K)];
+            v += V;
+        }
+        const double sa = reduce(a, false);
+        const double sv = reduce(v, false);
+        return sa / sv;
+    };
+    if (tc.singular) {
+        const double mf = mean(sf);
+        for (int c = threadIdx.x; c < ncell; c += blockDim.x) {
+            const int I = c % nx, J = (c / nx) % ny, K = D == 3 ? c / (nx * ny) : 0;
+            sf[pad(I, J, K)] -= mf;
+        }
+        __syncthreads();
+    }
+    const double r0 = max_res();
+    for (int it = 0; it < cs.max_it && r0 > cs.abs_tol; it++) {
+        for (int colour = 0; colour < 2; colour++) {
+            for (int c = threadIdx.x; c < ncell; c += blockDim.x) {
+                const int I = c % nx, J = (c / nx) % ny, K = D == 3 ? c / (nx * ny) : 0;
+                if (((I + J + K) & 1) != colour) continue;
+                double num, den;
+                row_terms(I, J, K, num, den);
+                sx[pad(I, J, K)] = (num - sf[pad(I, J, K)]) / (den + P.helm);
+            }
+            __syncthreads();
+            fill(sx, false);
+            __syncthreads();
+        }
+        const double r = max_res();
+        if (r <= cs.abs_tol || r <= cs.rel_tol * r0) break;
+    }
+    if (tc.singular) {
+        const double mx = mean(sx);
+        for (int c = threadIdx.x; c < ncell; c += blockDim.x) {
+            const int I = c % nx, J = (c / nx) % ny, K = D == 3 ? c / (nx * ny) : 0;
+            sx[pad(I, J, K)] -= mx;
+        }
+        __syncthreads();
+    }
+    for (int row = threadIdx.x; row < tc.nc; row += blockDim.x) {
+        const BlockDesc &b = P.B[tc.first + row / C];
+        int i, j, k;
+        cell_of(row % C, n, D, i, j, k);
+        F.X[b.cell_off + row % C] = (T)sx[pad(b.ijk[0] * n + i, b.ijk[1] * n + j, D == 3 ? b.ijk[2] * n + k : 0)];
+    }
+}
+
 // One CTA per chunk of kCoarseRows rows of one tree (chunk list built on
 // the host), one warp per row.
 template <class T>
@@ -3354,6 +3543,16 @@ template <class T, int D> struct Launch {
     // (strict) or at most `top`; then ghost fills of the coarsest segments
     static void coarse(mg_tree *t, const KParams &P, Fields<T> &F, int top, int strict) {
         const int ntr = (int)t->tcoarse.size();
+        if (t->coarse_mode == 1) {  // the paper's smoothing of the coarsest level
+            const size_t sm = sizeof(double) * (size_t)t->coarse_pad * (F.E ? 3 : 2);
+            set_smem(k_coarse_gs<T, D>, sm);
+            ++t->launches;
+            launch_k(k_coarse_gs<T, D>, ntr, 1024, sm, t->stream, P, t->d_tcoarse, top, strict, F,
+                     CoarseSmooth{t->coarse_abs, t->coarse_rel, t->coarse_max_it});
+            for (size_t l = 0; l < t->lev.size(); l++)
+                if (t->lev[l].coarsest && t->lev[l].group <= top) ghost(t, P, (int)l, F.X, F.XG, 0);
+            return;
+        }
         ++t->launches;
         launch_k(k_coarse_resid_b<T, D>, ntr, 1024, 0, t->stream, P, t->d_tcoarse, top, strict, F, t->d_cvec);
         ++t->launches;

@@ -898,8 +898,27 @@ extern "C" int mg_set_eps(mg_tree *t, const double *e) {
 
 static void params_or_default(const mg_params *p, mg_params *q) {
     if (p) *q = *p;
-    else { q->n_down = 2; q->n_up = 2; q->precision = MG_FP64; q->inner_cycles = 1; q->smoother = MG_SMOOTH_RBGS; q->omega = 0; }
+    else {
+        *q = mg_params{};
+        q->n_down = 2; q->n_up = 2; q->precision = MG_FP64; q->inner_cycles = 1; q->smoother = MG_SMOOTH_RBGS;
+        q->coarse_mode = MG_COARSE_EXACT;
+    }
     if (q->inner_cycles < 1) q->inner_cycles = 1;
+    if (q->coarse_max_it <= 0) q->coarse_max_it = 1000;
+    if (!(q->coarse_abs_tol > 0)) q->coarse_abs_tol = 1e-8;
+    if (!(q->coarse_rel_tol > 0)) q->coarse_rel_tol = 1e-8;
+}
+
+// padded cells ((n_d + 2) per dimension) of the largest coarsest level
+static int coarse_padded_cells(const mg_tree *t) {
+    long long mx = 0;
+    for (const TreeCoarse &tc : t->tcoarse) {
+        const LevelHost &L = t->is_batch ? t->tl[tc.lvl] : t->lev[tc.lvl];
+        long long c = 1;
+        for (int d = 0; d < t->dim; d++) c *= L.ncell[d] + 2;
+        mx = std::max(mx, c);
+    }
+    return (int)std::min<long long>(mx, 1 << 30);
 }
 
 // Parameters of one call: defaults, validation, the smoother and its Jacobi
@@ -913,6 +932,17 @@ static int use_params(mg_tree *t, const mg_params *p, mg_params *q, std::string 
     q->omega = om;
     t->smoother = q->smoother;
     t->omega = om;
+    if (q->coarse_mode != MG_COARSE_EXACT && q->coarse_mode != MG_COARSE_SMOOTH)
+        return fail(MG_ERR_ARG, "unknown coarse_mode");
+    if (q->coarse_mode == MG_COARSE_SMOOTH) {
+        t->coarse_pad = coarse_padded_cells(t);
+        if ((size_t)t->coarse_pad * sizeof(double) * (t->var_eps ? 3 : 2) > 200 * 1024)
+            return fail(MG_ERR_UNSUPPORTED, "coarsest level too large for the smoothing coarse solve (one CTA)");
+    }
+    t->coarse_mode = q->coarse_mode;
+    t->coarse_max_it = q->coarse_max_it;
+    t->coarse_abs = q->coarse_abs_tol;
+    t->coarse_rel = q->coarse_rel_tol;
     int rc;
     if (q->smoother == MG_SMOOTH_JACOBI) {
         if ((rc = dalloc(&t->d_jac64, t->ncells))) return rc;
@@ -922,9 +952,10 @@ static int use_params(mg_tree *t, const mg_params *p, mg_params *q, std::string 
             t->f32.J = t->d_jac32;
         }
     }
-    char buf[96];
-    snprintf(buf, sizeof(buf), ":%d:%d:s%d:%a", q->n_down, q->n_up, q->smoother,
-             q->smoother == MG_SMOOTH_JACOBI ? om : 0.0);
+    char buf[192];
+    snprintf(buf, sizeof(buf), ":%d:%d:s%d:%a:c%d:%d:%a:%a", q->n_down, q->n_up, q->smoother,
+             q->smoother == MG_SMOOTH_JACOBI ? om : 0.0, q->coarse_mode, q->coarse_max_it, q->coarse_abs_tol,
+             q->coarse_rel_tol);
     if (key) *key = buf + t->sched_key;
     return MG_OK;
 }
@@ -1235,7 +1266,7 @@ extern "C" int mg_tune_schedule(mg_tree *t, double rel_tol, int max_cycles, int 
             u[l] = l >= lmin ? c.ul : c.uc;
         }
         mg_set_schedule(t, nl, d.data(), u.data());
-        mg_params q{2, 2, precision, c.inner, MG_SMOOTH_RBGS, 0.0};
+        mg_params q{2, 2, precision, c.inner, MG_SMOOTH_RBGS, 0.0, MG_COARSE_EXACT, 0, 0.0, 0.0};
         float fastest = 1e30f;
         bool ok = true;
         for (int rep = 0; rep < 3 && ok; rep++) {  // the first run captures the graphs

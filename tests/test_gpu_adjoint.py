@@ -172,3 +172,22 @@ def test_unconverged_forward_raises(mg):
     with pytest.raises(MGError) as e:
         MGSolve.apply(t, f, None, 1e-12, 2)
     assert e.value.code == -4
+
+
+def test_cleaning_workload_variant_matches_oracle(mg):
+    """The cleaning workload's generator at a 64^3 base (8^3 blocks): the
+    cleaning step and its adjoint pass against the oracle."""
+    W_ = W
+    ci = W_.CleanInputs(n=64, N=8)
+    p = ci.problem
+    B, Bt = ci.leaf_fields(), ci.target()
+    t, o = mg.Tree.from_problem(p), Oracle.from_problem(p)
+    Bn, f, cyc, rel = t.clean(cuda(B), 1e-12, 80)
+    Bn_o, f_o, _ = o.clean(B, rel_tol=1e-13, max_cycles=80)
+    assert rel_diff(f.cpu().numpy(), f_o) < 1e-12
+    assert rel_diff(Bn.cpu().numpy(), Bn_o) < 1e-9
+    vol, _ = o.leaf_geometry()
+    g = vol * (Bn_o - Bt)
+    a = t.clean_adjoint(cuda(g), 1e-12, 80).cpu().numpy()
+    b = o.clean_adjoint(g, 80, 1e-13)
+    assert rel_diff(a, b) < 1e-9

@@ -222,3 +222,21 @@ def test_batch_mixed_precision_converges_like_fp64(mg, name):
     b.set_phi(torch.zeros(b.n_leaf, dtype=torch.float64, device="cuda"))
     c32, rel = b.solve(1e-10, 40, precision=mg.MG_FP32_DC)
     assert (rel <= 1e-10).all() and c32 <= c64 + 1, (c32, c64)
+
+
+@pytest.mark.parametrize("name", ["cyl", "periodic3d"])
+def test_batch_paper_coarse_solve_matches_oracle_per_tree(mg, name):
+    """The paper's coarse-grid smoothing (one CTA per tree's coarsest level)
+    in a batch: every tree matches the oracle run with the same coarse solve."""
+    probs = FORESTS[name]
+    b = make_batch(mg, probs)
+    b.fmg(coarse_mode=mg.MG_COARSE_SMOOTH)
+    b.vcycle(2, coarse_mode=mg.MG_COARSE_SMOOTH)
+    phi = b.get_phi().cpu().numpy()
+    for i, p in enumerate(probs):
+        o = Oracle.from_problem(p)
+        o.set_coarse_mode(True)
+        o.fmg()
+        o.vcycle(2)
+        d = rel_diff(phi[b.offsets[i]:b.offsets[i + 1]], o.get_phi())
+        assert d < TOL, (p.name, d)

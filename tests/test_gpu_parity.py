@@ -408,3 +408,27 @@ def test_schedule_tuner_picks_a_converging_schedule(mg):
     o.set_phi(t.get_phi().cpu().numpy())
     r0 = Oracle.from_problem(p).residual_norm()[0]
     assert rel <= 1e-10 and o.residual_norm()[0] <= 1.05e-10 * r0
+
+
+@pytest.mark.parametrize("name", ["cfg1_2d", "gauss3d_amr", "varcoef3d_singular", "cyl_amr", "periodic2d_amr_eps"])
+def test_paper_coarse_solve_matches_oracle(mg, name):
+    """The paper's coarse-grid solve (red-black smoothing of the coarsest
+    level to 1e-8 absolute / relative, at most 1000 sweeps) on both sides:
+    FMG and V-cycles agree to 1e-12, and a mixed-precision solve reaches
+    1e-10 by the oracle's residual."""
+    import torch
+    p = CASES[name]
+    t, o = both(mg, p)
+    o.set_coarse_mode(True)
+    t.fmg(coarse_mode=mg.MG_COARSE_SMOOTH)
+    o.fmg()
+    t.vcycle(3, coarse_mode=mg.MG_COARSE_SMOOTH)
+    o.vcycle(3)
+    assert rel_diff(t.get_phi().cpu().numpy(), o.get_phi()) < TOL
+    t.set_phi(torch.zeros(t.n_leaf, dtype=torch.float64, device="cuda"))
+    cyc, rel = t.solve(1e-10, 60, precision=mg.MG_FP32_DC, coarse_mode=mg.MG_COARSE_SMOOTH)
+    assert rel <= 1e-10
+    o2 = Oracle.from_problem(p)
+    r0 = o2.residual_norm()[0]
+    o2.set_phi(t.get_phi().cpu().numpy())
+    assert o2.residual_norm()[0] <= 1.5e-10 * r0

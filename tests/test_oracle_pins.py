@@ -780,3 +780,30 @@ def test_per_level_schedule():
     o.set_schedule(*mixed)
     cyc, hist = o.solve(1e-12, 60)
     assert hist[-1] <= 1e-12 * hist[0]
+
+
+def test_paper_coarse_solve_reaches_the_composite_solution():
+    """The paper's coarse-grid solve (Sec. 2.4: smoothing sweeps on the
+    coarsest level to an absolute or relative threshold, reading R20) in
+    place of the exact one: the V-cycles still converge to the dense
+    composite solution (2D Dirichlet, 3D refined, a singular variable-eps
+    problem with its zero-mean solution); with max_it = 0 the coarsest
+    level is left as it was, so the cycles stall."""
+    cases = [W.cfg1_poisson2d(n=32, N=8), W.cfg2_gauss3d(base=16, N=4, radii=(0.3,), sigma=0.1),
+             W.cfg3_varcoef3d(n=16, N=4, contrast=10.0)]
+    for p in cases:
+        exact = Oracle.from_problem(p)
+        exact.solve(1e-13, 80)
+        o = Oracle.from_problem(p)
+        o.set_coarse_mode(True)
+        cyc, hist = o.solve(1e-12, 80)
+        assert hist[-1] <= 1e-12 * hist[0], (p.name, cyc)
+        x, xr = o.get_phi(), exact.get_phi()
+        assert np.abs(x - xr).max() <= 1e-9 * np.abs(xr).max(), p.name
+    o = Oracle.from_problem(cases[0])
+    o.set_coarse_mode(True, max_it=0)
+    o.fmg()
+    o.vcycle(6)
+    r, _ = o.residual_norm()
+    r0 = Oracle.from_problem(cases[0]).residual_norm()[0]
+    assert r > 1e-4 * r0
