@@ -439,12 +439,23 @@ def kolmogorov_field(n, seed, dim=3):
     band = (kk >= 1.0) & (kk <= n / 2)
     amp[band] = kk[band] ** (-11.0 / 6.0)
     del ks, kk, band
+    import scipy.fft as sfft
     out = np.empty((dim,) + (n,) * dim)
     for c in range(dim):
         w = rng.standard_normal((n,) * dim)
-        out[c] = np.fft.irfftn(np.fft.rfftn(w) * amp, s=(n,) * dim)
+        out[c] = sfft.irfftn(sfft.rfftn(w, workers=-1) * amp, s=(n,) * dim, workers=-1)
     out /= math.sqrt(np.mean(np.sum(out * out, axis=0)))
     return out
+
+
+def _parallel_chunks(fn, n, chunk):
+    """fn(lo, hi) over [0, n) in chunks on a thread pool (numpy releases the
+    GIL in its array kernels); results in chunk order."""
+    from concurrent.futures import ThreadPoolExecutor
+    import os
+    spans = [(a, min(a + chunk, n)) for a in range(0, n, chunk)]
+    with ThreadPoolExecutor(max_workers=os.cpu_count() or 1) as ex:
+        return list(ex.map(lambda ab: fn(*ab), spans))
 
 
 class CleanInputs:
@@ -485,15 +496,20 @@ class CleanInputs:
             kids = np.array([(2 * i + (c & 1), 2 * j + ((c >> 1) & 1), 2 * k + (c >> 2))
                              for (i, j, k) in sorted(sets[depth]) for c in range(8)], np.int64)
             hd = h0 / 2 ** (depth + 1)
-            m = np.empty(len(kids))
             li = np.arange(N)
-            for q, (i, j, k) in enumerate(kids):
-                gi, gj, gk = i * N + li, j * N + li, k * N + li
-                xs, ys, zs = (gi + 0.5) * hd, (gj + 0.5) * hd, (gk + 0.5) * hd
-                sh = depth + 1
-                bt = self.turb[:, (gi >> sh)[:, None, None], (gj >> sh)[None, :, None], (gk >> sh)[None, None, :]]
-                bb = self._blob(xs[:, None, None], ys[None, :, None], zs[None, None, :])
-                m[q] = np.sqrt(((bt + bb) ** 2).sum(axis=0)).max()
+            sh = depth + 1
+
+            def kid_max(lo, hi, kids=kids, hd=hd, sh=sh):
+                m = np.empty(hi - lo)
+                for q in range(lo, hi):
+                    i, j, k = kids[q]
+                    gi, gj, gk = i * N + li, j * N + li, k * N + li
+                    bt = self.turb[:, (gi >> sh)[:, None, None], (gj >> sh)[None, :, None], (gk >> sh)[None, None, :]]
+                    bb = self._blob(((gi + 0.5) * hd)[:, None, None], ((gj + 0.5) * hd)[None, :, None],
+                                    ((gk + 0.5) * hd)[None, None, :])
+                    m[q - lo] = np.sqrt(((bt + bb) ** 2).sum(axis=0)).max()
+                return m
+            m = np.concatenate(_parallel_chunks(kid_max, len(kids), 512))
             cur = kids[m >= np.quantile(m, 1.0 - frac)]
         self.refine = sets_to_refine(balance(3, (nb0,) * 3, (True,) * 3, sets))
         self.problem = Problem("clean3d_%d_b%d_l%d" % (n, N, levels), 3, N, GEOM_CART, (n,) * 3, (0.0,) * 3,
@@ -506,9 +522,12 @@ class CleanInputs:
 
     def _magnitude(self, turb, a):
         out = np.empty(turb.shape[1:])
-        for k in range(len(a)):
-            bb = self._blob(a[:, None], a[None, :], a[k])
-            out[:, :, k] = np.sqrt(((turb[:, :, :, k] + bb) ** 2).sum(axis=0))
+
+        def slab(lo, hi):
+            for k in range(lo, hi):
+                bb = self._blob(a[:, None], a[None, :], a[k])
+                out[:, :, k] = np.sqrt(((turb[:, :, :, k] + bb) ** 2).sum(axis=0))
+        _parallel_chunks(slab, len(a), 8)
         return out
 
     def leaf_fields(self, with_blob=True, field=None):
@@ -523,19 +542,19 @@ class CleanInputs:
         li = np.arange(N)
         ck, cj, ci = np.meshgrid(li, li, li, indexing="ij")
         ci, cj, ck = ci.ravel(), cj.ravel(), ck.ravel()
-        for depth in np.unique(lb[:, 0]):
-            sel = np.nonzero(lb[:, 0] == depth)[0]
-            for s0 in range(0, len(sel), 4096):
-                part = sel[s0:s0 + 4096]
-                I = (lb[part, 1][:, None] * N + ci[None, :]).ravel()
-                J = (lb[part, 2][:, None] * N + cj[None, :]).ravel()
-                K = (lb[part, 3][:, None] * N + ck[None, :]).ravel()
-                idx = (part[:, None] * nc + np.arange(nc)[None, :]).ravel()
-                d = int(depth)
-                out[:, idx] = turb[:, I >> d, J >> d, K >> d]
-                if with_blob:
-                    h = 1.0 / (self.n * 2 ** d)
-                    out[:, idx] += self._blob((I + 0.5) * h, (J + 0.5) * h, (K + 0.5) * h)
+        def fill(lo, hi):
+            # leaf blocks [lo, hi) are one contiguous range of leaf cells
+            part = np.arange(lo, hi)
+            d = lb[part, 0][:, None]
+            I = lb[part, 1][:, None] * N + ci[None, :]
+            J = lb[part, 2][:, None] * N + cj[None, :]
+            K = lb[part, 3][:, None] * N + ck[None, :]
+            v = turb[:, I >> d, J >> d, K >> d].reshape(3, -1)
+            if with_blob:
+                h = 1.0 / (self.n * 2.0 ** d)
+                v += self._blob((I + 0.5) * h, (J + 0.5) * h, (K + 0.5) * h).reshape(3, -1)
+            out[:, lo * nc:hi * nc] = v
+        _parallel_chunks(fill, len(lb), 256)
         return out
 
     def target(self):
