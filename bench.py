@@ -572,6 +572,7 @@ def batch_measure(args, mg, W, barrier, max_over_ranks):
         dist.all_reduce(tt)
         total = int(tt.item())
     out = {"workload": BATCH_WORKLOAD, "trees": 512, "unknowns": total, "segments": len(b.segments()),
+           "coarse": b.coarse_info(),
            "parallelism": "single GPU" if world == 1 else
            "%d ranks, trees split by unknowns, no data exchange while solving" % world}
     steps = max(1, min(args.steps, 3))
@@ -684,15 +685,16 @@ def pin_sweeps(tree, prec, pins):
                                               for l in range(len(tree.levels()))))
 
 
-def run_profile_batch():
-    """One mixed-precision solve of the 512-tree batch after a warm-up solve,
-    the second inside the NVTX range "measure" (for ncu launch lists)."""
+def run_profile_batch(ntrees=512):
+    """One mixed-precision solve of the batch (the first `ntrees` trees of
+    the 512-tree forest) after a warm-up solve, the second inside the NVTX
+    range "measure" (for ncu launch lists and single-kernel captures)."""
     import numpy as np
     import torch
     import paper_1901_11370_gb300 as mg
     from synth import workloads as W
     torch.cuda.set_device(0)
-    probs = [W.cyl_ring_tree(i) for i in range(512)]
+    probs = [W.cyl_ring_tree(i) for i in range(ntrees)]
     b = mg.Batch([mg.Tree.from_problem(q, finalize=False) for q in probs])
     b.set_eps(torch.from_numpy(np.concatenate([W.leaf_field(q, "eps") for q in probs])).cuda())
     b.set_rhs(torch.from_numpy(np.concatenate([W.leaf_field(q, "rhs") for q in probs])).cuda())
@@ -724,11 +726,12 @@ def main():
     ap.add_argument("--cfg5-base", type=int, default=512,
                     help="base grid of the divergence-cleaning workload (0: skip it)")
     ap.add_argument("--profile", choices=["sweeps64", "sweeps32", "solve32", "solve64", "batch32"], default=None)
+    ap.add_argument("--trees", type=int, default=512, help="with --profile batch32: trees of the forest to use")
     ap.add_argument("--pin-sweeps", default="",
                     help="with --profile sweeps*/solve*: 'level:variant,...' sweep kernels to pin after tuning")
     args = ap.parse_args()
     if args.profile == "batch32":
-        run_profile_batch()
+        run_profile_batch(args.trees)
     elif args.profile:
         run_profile(args.profile, args.pin_sweeps)
     elif args.impl == "reference":

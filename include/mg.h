@@ -402,7 +402,12 @@ int mg_tree_destroy(mg_tree *t);
  * residual step is one launch over the blocks of all trees (the trees'
  * cycles are those of Sec. 2.4, run side by side), each tree keeps its own
  * exact coarsest-level solve, and a whole cycle plus its per-tree residual
- * norms is replayed as one CUDA graph.
+ * norms is replayed as one CUDA graph.  In a batch of two or more trees a
+ * tree whose coarsest level has a Dirichlet face and a non-periodic
+ * dimension of at least 4 cells, across which a plane holds at most 64
+ * cells, is solved by a block-tridiagonal factorisation over those planes
+ * (2 nc P values read and FMAs per solve, P cells per plane) instead of
+ * the dense inverse (nc^2); both are exact FP64 solves.
  *
  * mg_batch_create -- merge n trees into a batch with its own device
  *   storage on `stream`.  The trees are read (mesh, refinement, boundary
@@ -453,6 +458,10 @@ int mg_batch_launch_count(mg_batch *b, int64_t *n);
 int mg_batch_num_segments(mg_batch *b, int *nseg, int *ngroups);
 int mg_batch_segment_info(mg_batch *b, int seg, int32_t host_info[6]);
 int mg_batch_time_sweeps(mg_batch *b, int segment, int n_sweeps, int precision, double host_out[4]);
+/* mg_batch_coarse_info -- the coarsest-level solves: host_out = {trees
+ * solved by a dense inverse, trees solved in block-tridiagonal form, bytes
+ * of the dense inverses, bytes of the block-tridiagonal plane records}. */
+int mg_batch_coarse_info(mg_batch *b, int64_t host_out[4]);
 
 /* mg_batch_destroy -- free the batch (synchronises its stream). */
 int mg_batch_destroy(mg_batch *b);

@@ -415,6 +415,13 @@ class Batch:
                             coarsest=bool(info[4]), parent_same_n=bool(info[5])))
         return out
 
+    def coarse_info(self):
+        """Coarsest-level solves: trees with a dense inverse, trees in
+        block-tridiagonal form, and the bytes each form stores."""
+        out = np.zeros(4, np.int64)
+        check(self.L.mg_batch_coarse_info(self._h, out.ctypes.data_as(C.c_void_p)))
+        return dict(dense=int(out[0]), block=int(out[1]), dense_bytes=int(out[2]), block_bytes=int(out[3]))
+
     def time_sweeps(self, segment=-1, n_sweeps=4, precision=MG_FP64):
         seg = self.segments()
         if segment < 0:

@@ -75,7 +75,9 @@ struct KParams {
 };
 
 // Coarsest level of one tree of a pool (one tree, or a batch of trees):
-// a contiguous range of blocks solved exactly by its dense inverse.
+// a contiguous range of blocks solved exactly, by its dense inverse or, in
+// a pool of several trees, by the block-tridiagonal factorisation over the
+// planes of one non-periodic dimension (bt_n > 0).
 struct TreeCoarse {
     int first, nb, n;     // blocks of the coarsest level
     int nc, ns;           // cells, system size (nc + 1 when bordered)
@@ -83,9 +85,35 @@ struct TreeCoarse {
     int group;            // group index of the coarsest level
     int lvl;              // index of its level descriptor
     long long cell0;      // first cell of the level
-    long long minv_off;   // offset of the ns x ns inverse (row-major)
+    long long minv_off;   // offset of the ns x ns inverse (row-major), dense form
     long long cvec_off;   // offset of the residual vector (ns)
+    int bt_n, bt_P;       // planes and cells per plane (0: dense form)
+    int bt_dim;           // dimension across the planes
+    int bt_pad;
+    long long bt_off;     // offset of the bt_n FP64 plane records (bt_stride(bt_P) doubles each)
+    long long bt_off32;   // offset of the bt_n FP32 plane records (bt32_stride(bt_P) floats each)
+    long long perm_off;   // offset of the plane-order -> row map (nc ints)
 };
+
+// Plane records of the block-tridiagonal coarsest solve (16-byte aligned).
+// FP64 (FP64 cycles): S_j^-1 stored column by column (element (p, k) at
+// k P + p), then the coupling of plane j to plane j-1 (diagonal of A_j, P
+// values), then that of plane j to plane j+1 (diagonal of C_j, P values).
+// FP32 (FP32 cycles, whose whole cycle runs in FP32 inside the FP64 defect
+// correction): S_j^-1 rounded to FP32 row by row with the padded row
+// stride bt32_row(P) (zero padding), then A_{j+1} (P values, padded to 4),
+// then C_{j-1} (the same), each coupling stored on the plane whose solve
+// produces the value it multiplies.
+constexpr int kBtriMaxPlane = 64;  // largest plane (cells) in the block form
+__host__ __device__ inline int bt_stride(int P) { return (P * P + 2 * P + 1) & ~1; }
+__host__ __device__ inline int bt_round4(int P) { return (P + 3) & ~3; }
+// a multiple of 4 floats that is 4 mod 8: 128-bit row reads of 8
+// consecutive lanes fall into distinct bank groups
+__host__ __device__ inline int bt32_row(int P) {
+    const int r = bt_round4(P);
+    return (r % 8) ? r : r + 4;
+}
+__host__ __device__ inline int bt32_stride(int P) { return P * bt32_row(P) + 2 * bt_round4(P); }
 
 template <class T>
 struct Fields {
@@ -135,6 +163,8 @@ struct mg_tree {
     mg::TreeCoarse *d_tcoarse = nullptr;
     int2 *d_coarse_chunks = nullptr;          // (tree, first row) per chunk of the coarse apply
     int n_coarse_chunks = 0;
+    int2 *d_bt_chunks = nullptr;              // (tree, first cell) per chunk of the block-form residual
+    int n_bt_chunks = 0;
     bool is_batch = false;
     int max_nc = 0;                           // largest coarsest-level system
     // batch only: leaf runs (pool cell, concatenated leaf index, count) for
@@ -168,6 +198,12 @@ struct mg_tree {
     double omega = 0.8;            // Jacobi weight of the current call
     double *d_minv = nullptr;      // coarsest-level inverses, row-major ns x ns per tree
     long long minv_total = 0, cvec_total = 0;
+    double *d_bt = nullptr;        // plane records of the block-tridiagonal trees (FP64)
+    float *d_bt32 = nullptr;       // the same rounded to FP32 (FP32 cycles)
+    int *d_btperm = nullptr;       // their plane-order -> row maps
+    int *d_btlist = nullptr;       // indices of the block-tridiagonal trees
+    long long bt_total = 0, bt_total32 = 0, btperm_total = 0;
+    int n_btri = 0, bt_pmax = 0, bt_ncmax = 0;
     int nc = 0, ns = 0;            // coarsest cells, system size (nc + singular) -- one tree
     bool minv_ok = false;
     double *d_cvec = nullptr;      // coarsest residual vector (ns)
@@ -212,6 +248,7 @@ template <class T> void tune_sweeps(mg_tree *t, Fields<T> &F);
 int sweep_variant(mg_tree *t, int prec, int level);
 constexpr int kNumSweepVariants = 11;
 constexpr int kCoarseRows = 8;  // rows of one tree per CTA of the coarse apply
+constexpr int kBtResidCells = 256;  // cells per CTA of the block-form coarsest residual
 bool sweep_variant_ok(mg_tree *t, int prec, int level, int variant);
 void divergence(mg_tree *t, const double *B, double *out, int order);
 void project(mg_tree *t, const double *B, double *Bout);

@@ -2639,7 +2639,7 @@ __global__ void __launch_bounds__(1024) k_coarse_resid_b(KParams P, const TreeCo
                                                           int strict, Fields<T> F, double *__restrict__ cvec) {
     pdl_entry();
     const TreeCoarse tc = TC[blockIdx.x];
-    if (strict ? tc.group >= top : tc.group > top) return;
+    if (tc.bt_n || (strict ? tc.group >= top : tc.group > top)) return;  // block form: k_coarse_btri
     const int n = tc.n, C = cells_of<D>(n);
     double wx = 0;
     for (int row = threadIdx.x; row < tc.nc; row += blockDim.x) {
@@ -2873,6 +2873,311 @@ __global__ void k_coarse_apply_b(const TreeCoarse *__restrict__ TC, const int2 *
     for (int c = lane; c < tc.ns; c += 32) sacc += mr[c] * cvec[tc.cvec_off + c];
     for (int o = 16; o > 0; o >>= 1) sacc += __shfl_down_sync(0xffffffffu, sacc, o);
     if (lane == 0) X[tc.cell0 + row] = (T)((double)X[tc.cell0 + row] + sacc);
+}
+
+// Block-tridiagonal coarsest solves (one CTA per tree, trees listed on the
+// host, largest first), residual included: r = f - (L x - lambda x) on the
+// tree's coarsest cells, then dx = M^-1 r by the plane recursion
+//   forwards   w_j = S_j^-1 (r_j - A_j w_{j-1}),
+//   backwards  x_j = w_j - S_j^-1 (C_j x_{j+1}),   x_{NP-1} = w_{NP-1},
+// and x + dx written back.  Arithmetic and plane records are of the cycle's
+// type T: FP64 cycles use the FP64 factors and the precomputed FP64 face
+// coefficients (or 1/h^2); FP32 cycles the factors rounded to FP32 and the
+// FP32 stencil the rest of their cycle uses.  GB300's FP64 unit holds a warp
+// for about 64 cycles per instruction (FP32 FMAs take under 5), so the
+// layout keeps the instructions besides the P^2 FMAs of each plane few:
+// warp q of the CTA owns columns [k0, k1) of every plane (lane = row for the
+// products); the input u of a plane is formed by the owner of each column
+// from the previous plane's partial sums (one add per extra warp and one
+// coupling FMA) and reaches the other lanes by shuffles, so each plane
+// costs one barrier.  The plane records (S_j^-1 column by column, then
+// A_j, C_j) are staged into a ring of `ring` shared-memory slots, one bulk
+// copy (cp.async.bulk, mbarrier completion) per record issued ring - 1
+// planes ahead by thread 0; the visit order is planes 0 .. NP-1, then
+// NP-2 .. 0.  Every mbarrier wait is bounded: on expiry the kernel raises
+// P.status, lets the copies in flight land and the CTA stops.
+constexpr int kBtriMaxRing = 7;
+constexpr int kBtriThreads = 128;  // at most four warps (one per SM sub-partition)
+__device__ __forceinline__ double tfma(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float tfma(float a, float b, float c) { return fmaf(a, b, c); }
+template <class T> __device__ __forceinline__ const T *bt_records(const double *b64, const float *b32);
+template <> __device__ __forceinline__ const double *bt_records<double>(const double *b64, const float *) { return b64; }
+template <> __device__ __forceinline__ const float *bt_records<float>(const double *, const float *b32) { return b32; }
+
+// r = f - (L x - lambda x) at one coarsest cell, in T
+template <class T, int D>
+__device__ __forceinline__ T coarse_resid(const KParams &P, const BlockDesc &b, int c, const Fields<T> &F,
+                                          const double *__restrict__ W64) {
+    const int n = b.n, C = cells_of<D>(n);
+    int ci, cj, ck;
+    cell_of(c, n, D, ci, cj, ck);
+    const LevelDesc &L = P.L[b.lev];
+    if constexpr (sizeof(T) == 8) {
+        const double *wc = W64 ? W64 + b.cell_off * (2 * D + 1) + c : nullptr;
+        double acc = 0, wsum = 0;
+#pragma unroll
+        for (int d = 0; d < D; d++)
+#pragma unroll
+            for (int s = 0; s < 2; s++) {
+                const int o = s ? 1 : -1;
+                const double xn = load<T, D>(F.X, F.XG, b, ci + (d == 0 ? o : 0), cj + (d == 1 ? o : 0),
+                                             ck + (d == 2 ? o : 0));
+                const double wf = wc ? wc[(2 * d + s) * C] : L.inv_h2[d];
+                acc = fma(wf, xn, acc);
+                wsum += wf;
+            }
+        const double diag = wc ? wc[2 * D * C] : wsum + P.helm;
+        return F.F[b.cell_off + c] - fma(-diag, (double)F.X[b.cell_off + c], acc);
+    } else {
+        float lap, num, den, xc;
+        stencil<float, T, D>(P, L, b, F.X, F.XG, F.E, F.EG, ci, cj, ck, lap, num, den, xc);
+        return F.F[b.cell_off + c] - (lap - P.helmf * xc);
+    }
+}
+
+// Residual of the block-form trees' coarsest cells in plane order, one
+// thread per cell: r (of the cycle's type T) into the tree's coarsest
+// vector (viewed as T).
+template <class T, int D>
+__global__ void __launch_bounds__(kBtResidCells) k_coarse_resid_bt(KParams P, const TreeCoarse *__restrict__ TC,
+                                                                   const int2 *__restrict__ chunks, int top,
+                                                                   int strict, Fields<T> F,
+                                                                   const double *__restrict__ W64,
+                                                                   const int *__restrict__ perm,
+                                                                   double *__restrict__ cvec) {
+    pdl_entry();
+    const int2 ch = chunks[blockIdx.x];  // (tree, first cell)
+    const TreeCoarse tc = TC[ch.x];
+    if (strict ? tc.group >= top : tc.group > top) return;
+    const int i = ch.y + threadIdx.x;
+    if (i >= tc.nc) return;
+    const int row = perm[tc.perm_off + i], C = cells_of<D>(tc.n);
+    T *rb = reinterpret_cast<T *>(cvec) + (sizeof(double) / sizeof(T)) * tc.cvec_off;
+    rb[i] = coarse_resid<T, D>(P, P.B[tc.first + row / C], row % C, F, W64);
+}
+
+// FP32 form of the plane recursion, one warp per tree: lane p owns row p
+// (and p + 32) of every plane, so w_j[p], x_j[p] and the couplings that
+// act on them stay in the lane; only the input u of each plane is shared
+// (two buffers, zero padded).  Products read 4 coefficients of the row
+// and 4 inputs per 128-bit shared load; the ring of plane records is
+// filled by bulk copies as in k_coarse_btri.
+template <int D>
+__global__ void __launch_bounds__(32) k_coarse_btri_f32(KParams P, const TreeCoarse *__restrict__ TC,
+                                                        const int *__restrict__ list, int top, int strict,
+                                                        float *__restrict__ X, const double *__restrict__ cvec,
+                                                        const float *__restrict__ bt32,
+                                                        const int *__restrict__ perm, int ring, int slot) {
+    pdl_entry();
+    const TreeCoarse tc = TC[list[blockIdx.x]];
+    if (strict ? tc.group >= top : tc.group > top) return;
+    const int Pp = tc.bt_P, NP = tc.bt_n, nc = tc.nc, NV = 2 * NP - 1;
+    const int st = bt32_stride(Pp), row = bt32_row(Pp), r4 = bt_round4(Pp), lane = threadIdx.x;
+    extern __shared__ __align__(16) unsigned char bt_smem[];
+    __shared__ __align__(8) uint64_t bars[kBtriMaxRing];
+    float *sm = reinterpret_cast<float *>(bt_smem);
+    float *us = sm + (size_t)ring * slot;  // plane inputs: 2 buffers of kBtriMaxPlane
+    float *r = us + 2 * kBtriMaxPlane;     // residual, plane order
+    float *w = r + nc;                     // w_j, then x_j
+    const float *rec = bt32 + tc.bt_off32;
+    const int *pm = perm + tc.perm_off;
+    const float *rb = reinterpret_cast<const float *>(cvec) + 2 * tc.cvec_off;
+    const uint32_t bytes = (uint32_t)(sizeof(float) * st);
+    if (lane == 0) {
+        for (int s = 0; s < ring; s++) mbar_init(&bars[s], 1);
+        fence_mbar_init();
+    }
+    for (int q = lane; q < 2 * kBtriMaxPlane; q += 32) us[q] = 0.0f;
+    __syncwarp();
+    auto issue = [&](int v, int s) {  // lane 0: the record of visit v into slot s
+        const int j = v < NP ? v : 2 * NP - 2 - v;
+        mbar_expect_tx(&bars[s], bytes);
+        bulk_g2s(sm + (size_t)s * slot, rec + (size_t)j * st, bytes, &bars[s]);
+    };
+    if (lane == 0)
+        for (int v = 0; v < ring - 1 && v < NV; v++) issue(v, v);
+    for (int i = lane; i < nc; i += 32) r[i] = rb[i];
+    __syncwarp();
+    for (int p = lane; p < Pp; p += 32) us[p] = r[p];  // u of plane 0 = r_0
+    __syncwarp();
+    int sv = 0;       // ring slot of visit v
+    uint32_t ph = 0;  // phase parity of that slot
+    for (int v = 0; v < NV; v++) {
+        const bool ok = mbar_wait_bounded(&bars[sv], ph, P.wait_limit);
+        if (!__all_sync(0xffffffffu, ok)) {
+            // copies issued for visits v .. v + ring - 2 may still be landing:
+            // let them arrive (normal bound) before the CTA exits
+            if (lane == 0) {
+                atomicExch(P.status, 1);
+                int s = sv;
+                uint32_t q = ph;
+                for (int u = v; u < NV && u <= v + ring - 2; u++) {
+                    mbar_wait_bounded(&bars[s], q, kWaitLimit);
+                    if (++s == ring) { s = 0; q ^= 1; }
+                }
+            }
+            return;
+        }
+        if (lane == 0 && v + ring - 1 < NV) issue(v + ring - 1, sv == 0 ? ring - 1 : sv - 1);  // slot of visit v-1
+        const float *R = sm + (size_t)sv * slot;
+        const float *lo = R + (size_t)Pp * row, *up = lo + r4;  // A_{j+1}, C_{j-1}
+        const int j = v < NP ? v : 2 * NP - 2 - v;
+        const float *ub = us + (v & 1) * kBtriMaxPlane;
+        float *un = us + ((v + 1) & 1) * kBtriMaxPlane;
+        for (int pb = 0; pb < Pp; pb += 32) {
+            const int p = pb + lane;
+            const float *Rr = R + (size_t)(p < Pp ? p : 0) * row;  // idle lanes read row 0
+            float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+            for (int q = 0; q < Pp; q += 4) {
+                const float4 rv = *reinterpret_cast<const float4 *>(Rr + q);
+                const float4 uv = *reinterpret_cast<const float4 *>(ub + q);
+                a0 = fmaf(rv.x, uv.x, a0);
+                a1 = fmaf(rv.y, uv.y, a1);
+                a2 = fmaf(rv.z, uv.z, a2);
+                a3 = fmaf(rv.w, uv.w, a3);
+            }
+            const float acc = (a0 + a1) + (a2 + a3);
+            if (p < Pp) {
+                if (v < NP) {  // w_j = S_j^-1 u_j
+                    w[j * Pp + p] = acc;
+                    un[p] = j + 1 < NP ? fmaf(-lo[p], acc, r[(j + 1) * Pp + p])  // u_{j+1} = r_{j+1} - A_{j+1} w_j
+                                       : up[p] * acc;                           // x_{NP-1} = w_{NP-1}
+                } else {  // x_j = w_j - S_j^-1 C_j x_{j+1}
+                    const float x = w[j * Pp + p] - acc;
+                    w[j * Pp + p] = x;
+                    if (j > 0) un[p] = up[p] * x;
+                }
+            }
+        }
+        __syncwarp();
+        if (++sv == ring) { sv = 0; ph ^= 1; }
+    }
+    for (int i = lane; i < nc; i += 32) X[tc.cell0 + pm[i]] += w[i];
+}
+
+template <class T, int D>
+__global__ void __launch_bounds__(kBtriThreads) k_coarse_btri(KParams P, const TreeCoarse *__restrict__ TC,
+                                                              const int *__restrict__ list, int top, int strict,
+                                                              Fields<T> F, const double *__restrict__ cvec,
+                                                              const double *__restrict__ bt64,
+                                                              const float *__restrict__ bt32,
+                                                              const int *__restrict__ perm, int ring, int slot) {
+    pdl_entry();
+    const TreeCoarse tc = TC[list[blockIdx.x]];
+    if (strict ? tc.group >= top : tc.group > top) return;
+    const int Pp = tc.bt_P, NP = tc.bt_n, nc = tc.nc, st = bt_stride(Pp), NV = 2 * NP - 1;
+    const int tid = threadIdx.x, lane = tid & 31, nw = blockDim.x >> 5, wq = tid >> 5;
+    const int k0 = wq * Pp / nw, k1 = (wq + 1) * Pp / nw, m = k1 - k0;  // this warp's columns (m <= 32)
+    extern __shared__ __align__(16) unsigned char bt_smem[];
+    __shared__ __align__(8) uint64_t bars[kBtriMaxRing];
+    __shared__ int s_abort;
+    T *sm = reinterpret_cast<T *>(bt_smem);
+    T *r = sm + (size_t)ring * slot;  // residual, plane order
+    T *w = r + nc;                    // w_j, then x_j
+    T *part = w + nc;                 // partial sums: 2 buffers of nw x Pp
+    const T *rec = bt_records<T>(bt64, bt32) + (sizeof(T) == 8 ? tc.bt_off : tc.bt_off32);
+    const int *pm = perm + tc.perm_off;
+    const uint32_t bytes = (uint32_t)(sizeof(T) * st);
+    if (tid == 0) {
+        for (int s = 0; s < ring; s++) mbar_init(&bars[s], 1);
+        fence_mbar_init();
+        s_abort = 0;
+    }
+    __syncthreads();
+    auto issue = [&](int v, int s) {  // thread 0: the record of visit v into slot s
+        const int j = v < NP ? v : 2 * NP - 2 - v;
+        mbar_expect_tx(&bars[s], bytes);
+        bulk_g2s(sm + (size_t)s * slot, rec + (size_t)j * st, bytes, &bars[s]);
+    };
+    if (tid == 0)
+        for (int v = 0; v < ring - 1 && v < NV; v++) issue(v, v);
+    {  // residual of the coarsest cells, plane order (k_coarse_resid_bt)
+        const T *rb = reinterpret_cast<const T *>(cvec) + (sizeof(double) / sizeof(T)) * tc.cvec_off;
+        for (int i = tid; i < nc; i += blockDim.x) r[i] = rb[i];
+    }
+    int sv = 0;       // ring slot of visit v
+    uint32_t ph = 0;  // phase parity of that slot
+    for (int v = 0; v < NV; v++) {
+        if (!mbar_wait_bounded(&bars[sv], ph, P.wait_limit)) {
+            atomicExch(P.status, 1);
+            s_abort = 1;
+        }
+        __syncthreads();  // the record is in; every thread is past visit v-1
+        if (s_abort) {
+            // copies issued for visits v .. v + ring - 2 may still be landing:
+            // let them arrive (normal bound) before the CTA exits
+            if (tid == 0) {
+                int s = sv;
+                uint32_t q = ph;
+                for (int u = v; u < NV && u <= v + ring - 2; u++) {
+                    mbar_wait_bounded(&bars[s], q, kWaitLimit);
+                    if (++s == ring) { s = 0; q ^= 1; }
+                }
+            }
+            return;
+        }
+        if (tid == 0 && v + ring - 1 < NV) issue(v + ring - 1, sv == 0 ? ring - 1 : sv - 1);  // slot of visit v-1
+        const T *R = sm + (size_t)sv * slot;
+        const int j = v < NP ? v : 2 * NP - 2 - v;
+        const T *pprev = part + (size_t)((v - 1) & 1) * nw * Pp;
+        T u = 0;
+        const int k = k0 + lane;
+        if (lane < m) {
+            if (v < NP) {  // u = r_j - A_j w_{j-1}; w_{j-1} is complete now
+                u = r[j * Pp + k];
+                if (j > 0) {
+                    T sum = pprev[k];
+                    for (int q = 1; q < nw; q++) sum += pprev[q * Pp + k];
+                    w[(j - 1) * Pp + k] = sum;
+                    u = tfma(-R[Pp * Pp + k], sum, u);
+                }
+            } else {  // u = C_j x_{j+1}; x_{j+1} is complete now
+                T sum = pprev[k];
+                for (int q = 1; q < nw; q++) sum += pprev[q * Pp + k];
+                const T x = j + 1 == NP - 1 ? sum : w[(j + 1) * Pp + k] - sum;
+                w[(j + 1) * Pp + k] = x;
+                u = R[Pp * Pp + Pp + k] * x;
+            }
+        }
+        T *pcur = part + (size_t)(v & 1) * nw * Pp;
+        for (int pb = 0; pb < Pp; pb += 32) {  // all lanes take part in the shuffles
+            const int p = pb + lane;
+            const T *Rp = R + k0 * Pp + (p < Pp ? p : 0);  // idle lanes read row 0
+            T acc;
+            if constexpr (sizeof(T) == 8) {  // one chain: FP64 FMAs do not overlap within a warp
+                T a0 = 0;
+                for (int q = 0; q < m; q++) a0 = tfma(Rp[q * Pp], __shfl_sync(0xffffffffu, u, q), a0);
+                acc = a0;
+            } else {
+                T a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+                int q = 0;
+                for (; q + 4 <= m; q += 4) {
+                    const T u0 = __shfl_sync(0xffffffffu, u, q), u1 = __shfl_sync(0xffffffffu, u, q + 1);
+                    const T u2 = __shfl_sync(0xffffffffu, u, q + 2), u3 = __shfl_sync(0xffffffffu, u, q + 3);
+                    a0 = tfma(Rp[q * Pp], u0, a0);
+                    a1 = tfma(Rp[(q + 1) * Pp], u1, a1);
+                    a2 = tfma(Rp[(q + 2) * Pp], u2, a2);
+                    a3 = tfma(Rp[(q + 3) * Pp], u3, a3);
+                }
+                for (; q < m; q++) a0 = tfma(Rp[q * Pp], __shfl_sync(0xffffffffu, u, q), a0);
+                acc = (a0 + a1) + (a2 + a3);
+            }
+            if (p < Pp) pcur[wq * Pp + p] = acc;
+        }
+        if (++sv == ring) { sv = 0; ph ^= 1; }
+    }
+    __syncthreads();
+    {  // x_0 = w_0 - S_0^-1 C_0 x_1
+        const T *pl = part + (size_t)((NV - 1) & 1) * nw * Pp;
+        const int k = k0 + lane;
+        if (lane < m) {
+            T sum = pl[k];
+            for (int q = 1; q < nw; q++) sum += pl[q * Pp + k];
+            w[k] -= sum;
+        }
+    }
+    __syncthreads();
+    for (int i = tid; i < nc; i += blockDim.x) F.X[tc.cell0 + pm[i]] += w[i];
 }
 
 // --------------------------------------------------- elementwise ops ----
@@ -3553,10 +3858,42 @@ template <class T, int D> struct Launch {
                 if (t->lev[l].coarsest && t->lev[l].group <= top) ghost(t, P, (int)l, F.X, F.XG, 0);
             return;
         }
-        ++t->launches;
-        launch_k(k_coarse_resid_b<T, D>, ntr, 1024, 0, t->stream, P, t->d_tcoarse, top, strict, F, t->d_cvec);
-        ++t->launches;
-        launch_k(k_coarse_apply_b<T>, t->n_coarse_chunks, 32 * kCoarseRows, 0, t->stream, t->d_tcoarse, t->d_coarse_chunks, top, strict, t->d_minv, t->d_cvec, F.X);
+        if (t->n_coarse_chunks) {  // trees with a dense inverse
+            ++t->launches;
+            launch_k(k_coarse_resid_b<T, D>, ntr, 1024, 0, t->stream, P, t->d_tcoarse, top, strict, F, t->d_cvec);
+            ++t->launches;
+            launch_k(k_coarse_apply_b<T>, t->n_coarse_chunks, 32 * kCoarseRows, 0, t->stream, t->d_tcoarse,
+                     t->d_coarse_chunks, top, strict, t->d_minv, t->d_cvec, F.X);
+        }
+        if (t->n_btri) {
+            ++t->launches;
+            launch_k(k_coarse_resid_bt<T, D>, t->n_bt_chunks, kBtResidCells, 0, t->stream, P, t->d_tcoarse,
+                     t->d_bt_chunks, top, strict, F, (const double *)t->d_wface, (const int *)t->d_btperm,
+                     t->d_cvec);
+            ++t->launches;
+            if constexpr (sizeof(T) == 4) {  // one warp per tree; ring of about 40 KB
+                const int slot = bt32_stride(t->bt_pmax);
+                const int ring = std::max(2, std::min(kBtriMaxRing, (int)(40960 / (sizeof(float) * slot))));
+                const size_t sm = sizeof(float) * ((size_t)ring * slot + 2 * kBtriMaxPlane + 2 * (size_t)t->bt_ncmax);
+                set_smem(k_coarse_btri_f32<D>, sm);
+                launch_k(k_coarse_btri_f32<D>, t->n_btri, 32, sm, t->stream, P, t->d_tcoarse, t->d_btlist, top,
+                         strict, F.X, (const double *)t->d_cvec, (const float *)t->d_bt32,
+                         (const int *)t->d_btperm, ring, slot);
+            } else {
+                // two warps per tree with two or more trees per SM (the FP64
+                // units are then busy with other trees), else four; ring of
+                // about 40 KB
+                const int slot = bt_stride(t->bt_pmax);
+                const int ring = std::max(2, std::min(kBtriMaxRing, (int)(40960 / (sizeof(double) * slot))));
+                const int threads = t->n_btri >= 2 * t->nsm ? 64 : kBtriThreads;
+                const size_t sm = sizeof(double) * ((size_t)ring * slot + 2 * (size_t)t->bt_ncmax +
+                                                    2 * (threads / 32) * (size_t)t->bt_pmax);
+                set_smem(k_coarse_btri<T, D>, sm);
+                launch_k(k_coarse_btri<T, D>, t->n_btri, threads, sm, t->stream, P, t->d_tcoarse, t->d_btlist,
+                         top, strict, F, (const double *)t->d_cvec, (const double *)t->d_bt,
+                         (const float *)t->d_bt32, (const int *)t->d_btperm, ring, slot);
+            }
+        }
         for (size_t l = 0; l < t->lev.size(); l++)
             if (t->lev[l].coarsest && t->lev[l].group <= top) ghost(t, P, (int)l, F.X, F.XG, 0);
     }

@@ -1,6 +1,7 @@
 // mg_tree.cpp -- host side of the GB300 octree geometric multigrid: mesh and
-// level construction (Sec. 2.5), device tables, the dense coarsest-level
-// inverse, and the C ABI declared in include/mg.h.
+// level construction (Sec. 2.5), device tables, the coarsest-level factors
+// (dense inverse, block-tridiagonal form), and the C ABI declared in
+// include/mg.h.
 #include <algorithm>
 #include <array>
 #include <chrono>
@@ -437,18 +438,16 @@ static int upload_bc(mg_tree *t) {
     return MG_OK;
 }
 
-// Dense inverse of the coarsest-level operator with homogeneous boundary
-// values (bordered by sum V x = 0 when the problem has no Dirichlet face),
-// assembled row by row from the 5/7-point stencil and inverted by
-// Gauss-Jordan elimination with partial pivoting (FP64, host).
-// Dense inverse of one tree's coarsest-level operator with homogeneous
-// boundary values (bordered by sum V x = 0 when the problem has no
-// Dirichlet face), assembled row by row from the 5/7-point stencil and
-// inverted by Gauss-Jordan elimination with partial pivoting (FP64, host).
-static std::string coarse_inverse_one(const mg_tree *t, const TreeCoarse &tc, const LevelHost &L,
-                                      const double *eps, double *Inv) {
+// The coarsest-level operator with homogeneous boundary values, assembled
+// from the 5/7-point stencil (bordered by sum V x = 0 when the problem has
+// no Dirichlet face): emit(row, col, value) adds value to M[row][col];
+// rows and columns are tree-local cells in block order (b C + c), col == nc
+// is the border.
+template <class Emit>
+static void assemble_coarse(const mg_tree *t, const TreeCoarse &tc, const LevelHost &L, const double *eps,
+                            Emit emit) {
     const int D = t->dim;
-    const int n = L.n, C = (int)ipow(n, D), nc = tc.nc, ns = tc.ns;
+    const int n = L.n, C = (int)ipow(n, D), nc = tc.nc;
     std::vector<int> rowmap((size_t)L.ncell[0] * L.ncell[1] * L.ncell[2]);
     auto cellkey = [&](const int *G) { return ((size_t)G[2] * L.ncell[1] + G[1]) * L.ncell[0] + G[0]; };
     for (int b = 0; b < tc.nb; b++) {
@@ -458,7 +457,6 @@ static std::string coarse_inverse_one(const mg_tree *t, const TreeCoarse &tc, co
             rowmap[cellkey(G)] = b * C + c;
         }
     }
-    std::vector<double> M((size_t)ns * ns, 0.0);
     for (int b = 0; b < tc.nb; b++) {
         const BlockDesc &B = t->blocks[tc.first + b];
         for (int c = 0; c < C; c++) {
@@ -480,51 +478,152 @@ static std::string coarse_inverse_one(const mg_tree *t, const TreeCoarse &tc, co
                     w *= 2.0 * ec * eo / (ec + eo);
                     if (t->geom == MG_CYL && d == 0) w *= (t->lo[0] + (G[0] + s) * L.h[0]) / ri;
                     if (!phys) {
-                        M[(size_t)row * ns + col] += w;
-                        M[(size_t)row * ns + row] -= w;
+                        emit(row, col, w);
+                        emit(row, row, -w);
                     } else if (t->bc.type[2 * d + s] == MG_BC_DIRICHLET) {
-                        M[(size_t)row * ns + row] -= 2.0 * w;
+                        emit(row, row, -2.0 * w);
                     }
                 }
-            M[(size_t)row * ns + row] -= t->helm;
+            emit(row, row, -t->helm);
             if (tc.singular) {
                 double V = 1.0;
                 for (int d = 0; d < D; d++) V *= L.h[d];
                 if (t->geom == MG_CYL) V = 2.0 * M_PI * ri * L.h[0] * L.h[1];
-                M[(size_t)row * ns + nc] = 1.0;
-                M[(size_t)nc * ns + row] = V;
+                emit(row, nc, 1.0);
+                emit(nc, row, V);
             }
         }
     }
-    // Gauss-Jordan on [M | I]
-    for (size_t i = 0; i < (size_t)ns * ns; i++) Inv[i] = 0.0;
-    for (int i = 0; i < ns; i++) Inv[(size_t)i * ns + i] = 1.0;
-    for (int c = 0; c < ns; c++) {
+}
+
+// In-place inverse of the m x m row-major matrix A by Gauss-Jordan
+// elimination with partial pivoting; A is overwritten, Inv receives A^-1.
+static bool gauss_jordan(std::vector<double> &A, double *Inv, int m) {
+    for (size_t i = 0; i < (size_t)m * m; i++) Inv[i] = 0.0;
+    for (int i = 0; i < m; i++) Inv[(size_t)i * m + i] = 1.0;
+    for (int c = 0; c < m; c++) {
         int p = c;
-        for (int r = c + 1; r < ns; r++)
-            if (std::fabs(M[(size_t)r * ns + c]) > std::fabs(M[(size_t)p * ns + c])) p = r;
-        if (M[(size_t)p * ns + c] == 0.0) return "coarsest-level matrix is singular";
+        for (int r = c + 1; r < m; r++)
+            if (std::fabs(A[(size_t)r * m + c]) > std::fabs(A[(size_t)p * m + c])) p = r;
+        if (A[(size_t)p * m + c] == 0.0) return false;
         if (p != c)
-            for (int e = 0; e < ns; e++) {
-                std::swap(M[(size_t)c * ns + e], M[(size_t)p * ns + e]);
-                std::swap(Inv[(size_t)c * ns + e], Inv[(size_t)p * ns + e]);
+            for (int e = 0; e < m; e++) {
+                std::swap(A[(size_t)c * m + e], A[(size_t)p * m + e]);
+                std::swap(Inv[(size_t)c * m + e], Inv[(size_t)p * m + e]);
             }
-        const double piv = 1.0 / M[(size_t)c * ns + c];
-        for (int e = 0; e < ns; e++) { M[(size_t)c * ns + e] *= piv; Inv[(size_t)c * ns + e] *= piv; }
-        for (int r = 0; r < ns; r++) {
+        const double piv = 1.0 / A[(size_t)c * m + c];
+        for (int e = 0; e < m; e++) { A[(size_t)c * m + e] *= piv; Inv[(size_t)c * m + e] *= piv; }
+        for (int r = 0; r < m; r++) {
             if (r == c) continue;
-            const double m = M[(size_t)r * ns + c];
-            if (m == 0.0) continue;
-            for (int e = 0; e < ns; e++) {
-                M[(size_t)r * ns + e] -= m * M[(size_t)c * ns + e];
-                Inv[(size_t)r * ns + e] -= m * Inv[(size_t)c * ns + e];
+            const double f = A[(size_t)r * m + c];
+            if (f == 0.0) continue;
+            for (int e = 0; e < m; e++) {
+                A[(size_t)r * m + e] -= f * A[(size_t)c * m + e];
+                Inv[(size_t)r * m + e] -= f * Inv[(size_t)c * m + e];
             }
         }
+    }
+    return true;
+}
+
+// Dense inverse of one tree's coarsest-level operator (FP64, host).
+static std::string coarse_inverse_one(const mg_tree *t, const TreeCoarse &tc, const LevelHost &L,
+                                      const double *eps, double *Inv) {
+    const int ns = tc.ns;
+    std::vector<double> M((size_t)ns * ns, 0.0);
+    assemble_coarse(t, tc, L, eps, [&](int r, int c, double v) { M[(size_t)r * ns + c] += v; });
+    if (!gauss_jordan(M, Inv, ns)) return "coarsest-level matrix is singular";
+    return "";
+}
+
+// Plane of cell `row` (block order) across dimension bt_dim, and its index
+// within the plane (the other dimensions lexicographically, lowest first).
+static void plane_of(const mg_tree *t, const TreeCoarse &tc, const LevelHost &L, int row, int &j, int &p) {
+    const int D = t->dim, n = L.n, C = (int)ipow(n, D), c = row % C;
+    const BlockDesc &B = t->blocks[tc.first + row / C];
+    const int G[3] = {B.ijk[0] * n + c % n, B.ijk[1] * n + (c / n) % n, D == 3 ? B.ijk[2] * n + c / (n * n) : 0};
+    j = G[tc.bt_dim];
+    p = 0;
+    for (int d = D - 1; d >= 0; d--)
+        if (d != tc.bt_dim) p = p * L.ncell[d] + G[d];
+}
+
+// Block-tridiagonal factorisation of one tree's coarsest-level operator
+// over the planes j = 0 .. NP-1 of dimension bt_dim: with A_j, C_j the
+// (diagonal) couplings of plane j to planes j-1, j+1 and B_j the operator
+// within plane j, S_0 = B_0, S_j = B_j - A_j S_{j-1}^-1 C_{j-1}, and the
+// solve M x = r runs z_j = r_j - A_j S_{j-1}^-1 z_{j-1} forwards, then
+// x_j = S_j^-1 (z_j - C_j x_{j+1}) backwards.  Writes the plane records
+// (S_j^-1 column by column, then the diagonals of A_j and C_j) and the
+// plane-order -> row map.
+static std::string coarse_btri_one(const mg_tree *t, const TreeCoarse &tc, const LevelHost &L, const double *eps,
+                                   double *rec, int *perm) {
+    const int P = tc.bt_P, NP = tc.bt_n, nc = tc.nc, st = bt_stride(P);
+    std::vector<int> pos(nc);
+    for (int row = 0; row < nc; row++) {
+        int j, p;
+        plane_of(t, tc, L, row, j, p);
+        if (j < 0 || j >= NP || p < 0 || p >= P) return "internal: plane index out of range";
+        pos[row] = j * P + p;
+        perm[j * P + p] = row;
+    }
+    std::vector<double> B((size_t)NP * P * P, 0.0), A((size_t)NP * P, 0.0), Cu((size_t)NP * P, 0.0);
+    bool ok = true;
+    assemble_coarse(t, tc, L, eps, [&](int r, int c, double v) {
+        if (r >= nc || c >= nc) { ok = false; return; }  // bordered systems keep the dense form
+        const int jr = pos[r] / P, pr = pos[r] % P, jc = pos[c] / P, pc = pos[c] % P;
+        if (jc == jr) B[((size_t)jr * P + pr) * P + pc] += v;
+        else if (jc == jr - 1 && pc == pr) A[(size_t)jr * P + pr] += v;
+        else if (jc == jr + 1 && pc == pr) Cu[(size_t)jr * P + pr] += v;
+        else ok = false;
+    });
+    if (!ok) return "internal: coarsest operator is not block tridiagonal across the planes";
+    std::vector<double> S((size_t)P * P), Sinv((size_t)P * P), prev((size_t)P * P);
+    for (int j = 0; j < NP; j++) {
+        for (int p = 0; p < P; p++)
+            for (int q = 0; q < P; q++) {
+                double v = B[((size_t)j * P + p) * P + q];
+                if (j > 0) v -= A[(size_t)j * P + p] * prev[(size_t)p * P + q] * Cu[(size_t)(j - 1) * P + q];
+                S[(size_t)p * P + q] = v;
+            }
+        if (!gauss_jordan(S, Sinv.data(), P)) return "coarsest-level matrix is singular";
+        double *R = rec + (size_t)j * st;
+        for (int k = 0; k < P; k++)
+            for (int p = 0; p < P; p++) R[(size_t)k * P + p] = Sinv[(size_t)p * P + k];
+        for (int p = 0; p < P; p++) {
+            R[P * P + p] = A[(size_t)j * P + p];       // zero on plane 0
+            R[P * P + P + p] = Cu[(size_t)j * P + p];  // zero on the last plane
+        }
+        for (int e = P * P + 2 * P; e < st; e++) R[e] = 0.0;
+        prev.swap(Sinv);
     }
     return "";
 }
 
-// Inverses of every tree's coarsest level (trees in parallel host threads).
+// Chooses the block-tridiagonal form for one tree of a pool of several
+// trees: a non-singular coarsest level with a non-periodic dimension of at
+// least 4 planes whose planes hold at most kBtriMaxPlane cells (the longest
+// such dimension).  Its forward and backward sweeps cost 2 nc P FMAs and
+// bytes against nc^2 for the dense inverse.  A single tree keeps the dense
+// inverse, whose rows are applied by many CTAs at once.
+static void coarse_plan(const mg_tree *src, TreeCoarse &tc, const LevelHost &L, bool pool) {
+    tc.bt_n = tc.bt_P = tc.bt_dim = 0;
+    if (!pool || tc.singular) return;
+    int best = -1;
+    for (int d = 0; d < src->dim; d++) {
+        if (src->bc.type[2 * d] == MG_BC_PERIODIC) continue;
+        const int np = L.ncell[d];
+        if (np < 4 || tc.nc / np > kBtriMaxPlane) continue;
+        if (best < 0 || np > L.ncell[best]) best = d;
+    }
+    if (best < 0) return;
+    tc.bt_dim = best;
+    tc.bt_n = L.ncell[best];
+    tc.bt_P = tc.nc / tc.bt_n;
+}
+
+// Coarsest-level factors of every tree (trees in parallel host threads):
+// dense inverses, and plane records of the block-tridiagonal trees.
 int build_coarse_inverse(mg_tree *t) {
     std::vector<double> eps;
     if (t->var_eps) {
@@ -532,7 +631,9 @@ int build_coarse_inverse(mg_tree *t) {
         eps.resize(t->ncells);
         CK(cudaMemcpy(eps.data(), t->f64.E, sizeof(double) * t->ncells, cudaMemcpyDeviceToHost));
     }
-    std::vector<double> inv(t->minv_total);
+    std::vector<double> inv(t->minv_total), bt(t->bt_total);
+    std::vector<float> bt32(t->bt_total32);
+    std::vector<int> perm(t->btperm_total);
     std::vector<std::string> errs(t->tcoarse.size());
     const int nthr = (int)std::max<unsigned>(1, std::min<unsigned>(std::thread::hardware_concurrency(), 64));
     std::atomic<int> next(0);
@@ -540,7 +641,26 @@ int build_coarse_inverse(mg_tree *t) {
         for (int i = next++; i < (int)t->tcoarse.size(); i = next++) {
             const TreeCoarse &tc = t->tcoarse[i];
             const LevelHost &L = t->is_batch ? t->tl[tc.lvl] : t->lev[tc.lvl];
-            errs[i] = coarse_inverse_one(t, tc, L, t->var_eps ? eps.data() + tc.cell0 : nullptr, inv.data() + tc.minv_off);
+            const double *e = t->var_eps ? eps.data() + tc.cell0 : nullptr;
+            if (!tc.bt_n) {
+                errs[i] = coarse_inverse_one(t, tc, L, e, inv.data() + tc.minv_off);
+                continue;
+            }
+            errs[i] = coarse_btri_one(t, tc, L, e, bt.data() + tc.bt_off, perm.data() + tc.perm_off);
+            const int Pp = tc.bt_P, st = bt_stride(Pp), st32 = bt32_stride(Pp), row = bt32_row(Pp);
+            const int r4 = bt_round4(Pp);
+            for (int j = 0; j < tc.bt_n; j++) {  // FP32 records, padding zero
+                const double *R = bt.data() + tc.bt_off + (size_t)j * st;
+                float *Q = bt32.data() + tc.bt_off32 + (size_t)j * st32;
+                for (int q = 0; q < st32; q++) Q[q] = 0.0f;
+                for (int p = 0; p < Pp; p++) {
+                    for (int k = 0; k < Pp; k++) Q[(size_t)p * row + k] = (float)R[(size_t)k * Pp + p];
+                    if (j + 1 < tc.bt_n)  // A_{j+1}: the next plane's record holds it at P^2 + p
+                        Q[(size_t)Pp * row + p] = (float)R[(size_t)st + (size_t)Pp * Pp + p];
+                    if (j > 0)  // C_{j-1}: the previous plane's record holds it at P^2 + P + p
+                        Q[(size_t)Pp * row + r4 + p] = (float)R[-(ptrdiff_t)st + (ptrdiff_t)Pp * Pp + Pp + p];
+                }
+            }
         }
     };
     std::vector<std::thread> pool;
@@ -550,7 +670,15 @@ int build_coarse_inverse(mg_tree *t) {
     for (auto &e : errs)
         if (!e.empty()) return fail(MG_ERR_ARG, e);
     if (!t->d_minv) CK(cudaMalloc((void **)&t->d_minv, sizeof(double) * (size_t)std::max(1LL, t->minv_total)));
-    CK(cudaMemcpy(t->d_minv, inv.data(), sizeof(double) * (size_t)t->minv_total, cudaMemcpyHostToDevice));
+    if (t->minv_total) CK(cudaMemcpy(t->d_minv, inv.data(), sizeof(double) * (size_t)t->minv_total, cudaMemcpyHostToDevice));
+    if (t->bt_total) {
+        if (!t->d_bt) CK(cudaMalloc((void **)&t->d_bt, sizeof(double) * (size_t)t->bt_total));
+        if (!t->d_bt32) CK(cudaMalloc((void **)&t->d_bt32, sizeof(float) * (size_t)t->bt_total32));
+        if (!t->d_btperm) CK(cudaMalloc((void **)&t->d_btperm, sizeof(int) * (size_t)t->btperm_total));
+        CK(cudaMemcpy(t->d_bt, bt.data(), sizeof(double) * (size_t)t->bt_total, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(t->d_bt32, bt32.data(), sizeof(float) * (size_t)t->bt_total32, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(t->d_btperm, perm.data(), sizeof(int) * (size_t)t->btperm_total, cudaMemcpyHostToDevice));
+    }
     t->minv_ok = true;
     return MG_OK;
 }
@@ -597,13 +725,39 @@ extern "C" int mg_tree_finalize(mg_tree *t, void *stream) {
     if ((rc = dalloc(&t->d_cvec, t->cvec_total))) return rc;
     CK(cudaMalloc((void **)&t->d_tcoarse, sizeof(TreeCoarse) * t->tcoarse.size()));
     CK(cudaMemcpy(t->d_tcoarse, t->tcoarse.data(), sizeof(TreeCoarse) * t->tcoarse.size(), cudaMemcpyHostToDevice));
-    {  // work list of the coarse apply: kCoarseRows rows of one tree per CTA
+    {  // work lists of the coarse solve: kCoarseRows rows of one dense tree
+       // per CTA; one CTA per block-tridiagonal tree
         std::vector<int2> ch;
-        for (size_t i = 0; i < t->tcoarse.size(); i++)
-            for (int r = 0; r < t->tcoarse[i].nc; r += kCoarseRows) ch.push_back(make_int2((int)i, r));
+        std::vector<int> bl;
+        t->bt_pmax = t->bt_ncmax = 0;
+        for (size_t i = 0; i < t->tcoarse.size(); i++) {
+            const TreeCoarse &tc = t->tcoarse[i];
+            if (tc.bt_n) {
+                bl.push_back((int)i);
+                t->bt_pmax = std::max(t->bt_pmax, tc.bt_P);
+                t->bt_ncmax = std::max(t->bt_ncmax, tc.nc);
+                continue;
+            }
+            for (int r = 0; r < tc.nc; r += kCoarseRows) ch.push_back(make_int2((int)i, r));
+        }
+        // largest first: CTAs start in list order, so the SMs each get a
+        // share of the large trees
+        std::stable_sort(bl.begin(), bl.end(), [&](int a, int b) {
+            const TreeCoarse &A = t->tcoarse[a], &B = t->tcoarse[b];
+            return (long long)A.nc * A.bt_P > (long long)B.nc * B.bt_P;
+        });
+        std::vector<int2> bc;  // block-form residual: kBtResidCells cells of one tree per CTA
+        for (int i : bl)
+            for (int r = 0; r < t->tcoarse[i].nc; r += kBtResidCells) bc.push_back(make_int2(i, r));
+        t->n_bt_chunks = (int)bc.size();
+        CK(cudaMalloc((void **)&t->d_bt_chunks, sizeof(int2) * std::max<size_t>(1, bc.size())));
+        if (!bc.empty()) CK(cudaMemcpy(t->d_bt_chunks, bc.data(), sizeof(int2) * bc.size(), cudaMemcpyHostToDevice));
         t->n_coarse_chunks = (int)ch.size();
+        t->n_btri = (int)bl.size();
         CK(cudaMalloc((void **)&t->d_coarse_chunks, sizeof(int2) * std::max<size_t>(1, ch.size())));
-        CK(cudaMemcpy(t->d_coarse_chunks, ch.data(), sizeof(int2) * ch.size(), cudaMemcpyHostToDevice));
+        if (!ch.empty()) CK(cudaMemcpy(t->d_coarse_chunks, ch.data(), sizeof(int2) * ch.size(), cudaMemcpyHostToDevice));
+        CK(cudaMalloc((void **)&t->d_btlist, sizeof(int) * std::max<size_t>(1, bl.size())));
+        if (!bl.empty()) CK(cudaMemcpy(t->d_btlist, bl.data(), sizeof(int) * bl.size(), cudaMemcpyHostToDevice));
     }
     CK(cudaMallocHost((void **)&t->h_red, 3 * sizeof(double)));
     CK(cudaStreamCreateWithFlags(&t->cap_stream, cudaStreamNonBlocking));
@@ -1425,6 +1579,7 @@ extern "C" int mg_tree_destroy(mg_tree *t) {
         free_fields(t->f32, true);
         cudaFree(t->d_blocks); cudaFree(t->d_levels); cudaFree(t->d_bcplanes);
         cudaFree(t->d_r64); cudaFree(t->d_wface); cudaFree(t->d_jac64); cudaFree(t->d_jac32); cudaFree(t->d_minv); cudaFree(t->d_cvec); cudaFree(t->d_partials); cudaFree(t->d_red); cudaFree(t->d_status); cudaFree(t->d_tcoarse); cudaFree(t->d_coarse_chunks);
+        cudaFree(t->d_bt); cudaFree(t->d_bt32); cudaFree(t->d_btperm); cudaFree(t->d_btlist); cudaFree(t->d_bt_chunks);
         cudaFreeHost(t->h_red);
         cudaFree(t->d_runs); cudaFree(t->d_slot_off); cudaFree(t->d_slots); cudaFree(t->d_tree3);
         cudaFree(t->d_at); cudaFree(t->d_atg); cudaFree(t->d_lam); cudaFree(t->d_gh); cudaFree(t->d_lv);
@@ -1552,7 +1707,7 @@ static int merge_trees(mg_tree *P, int n, mg_tree *const *trees) {
         }
     // coarsest level of every tree
     P->tcoarse.clear();
-    P->minv_total = P->cvec_total = 0;
+    P->minv_total = P->cvec_total = P->bt_total = P->bt_total32 = P->btperm_total = 0;
     P->max_nc = 0;
     for (int i = 0; i < n; i++) {
         const mg_tree *T = trees[i];
@@ -1569,10 +1724,20 @@ static int merge_trees(mg_tree *P, int n, mg_tree *const *trees) {
         tc.group = G - (int)T->lev.size();
         tc.lvl = tl_off[i];
         tc.cell0 = P->blocks[tc.first].cell_off;
-        tc.minv_off = P->minv_total;
         tc.cvec_off = P->cvec_total;
-        P->minv_total += (long long)tc.ns * tc.ns;
         P->cvec_total += tc.ns;
+        coarse_plan(T, tc, L0, n > 1);
+        if (tc.bt_n) {
+            tc.bt_off = P->bt_total;
+            tc.bt_off32 = P->bt_total32;
+            tc.perm_off = P->btperm_total;
+            P->bt_total += (long long)tc.bt_n * bt_stride(tc.bt_P);
+            P->bt_total32 += (long long)tc.bt_n * bt32_stride(tc.bt_P);
+            P->btperm_total += tc.nc;
+        } else {
+            tc.minv_off = P->minv_total;
+            P->minv_total += (long long)tc.ns * tc.ns;
+        }
         P->max_nc = std::max(P->max_nc, tc.nc);
         P->tcoarse.push_back(tc);
     }
@@ -1814,6 +1979,17 @@ extern "C" int mg_batch_launch_count(mg_batch *b, int64_t *n) {
 extern "C" int mg_batch_time_sweeps(mg_batch *b, int level, int n_sweeps, int precision, double out[4]) {
     NEED_BATCH(b);
     return mg_time_sweeps(b->pool, level, n_sweeps, precision, out);
+}
+
+extern "C" int mg_batch_coarse_info(mg_batch *b, int64_t out[4]) {
+    NEED_BATCH(b);
+    if (!out) return fail(MG_ERR_ARG, "null output");
+    const mg_tree *P = b->pool;
+    out[0] = (int64_t)P->tcoarse.size() - P->n_btri;
+    out[1] = P->n_btri;
+    out[2] = (int64_t)sizeof(double) * P->minv_total;
+    out[3] = (int64_t)sizeof(double) * P->bt_total;
+    return MG_OK;
 }
 
 extern "C" int mg_batch_num_segments(mg_batch *b, int *nseg, int *ngroups) {

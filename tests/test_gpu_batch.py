@@ -240,3 +240,40 @@ def test_batch_paper_coarse_solve_matches_oracle_per_tree(mg, name):
         o.vcycle(2)
         d = rel_diff(phi[b.offsets[i]:b.offsets[i + 1]], o.get_phi())
         assert d < TOL, (p.name, d)
+
+
+def test_batch_coarse_forms(mg):
+    """Dirichlet trees of a batch take the block-tridiagonal coarsest solve
+    (2 nc P values against nc^2 for the dense inverse); the periodic,
+    singular trees keep the dense inverse; a batch of one keeps it too.
+    Parity of both forms is the per-tree oracle comparison above."""
+    cyl = make_batch(mg, FORESTS["cyl"]).coarse_info()
+    assert cyl["dense"] == 0 and cyl["block"] == len(FORESTS["cyl"]) and cyl["dense_bytes"] == 0
+    per = make_batch(mg, FORESTS["periodic3d"]).coarse_info()
+    assert per["block"] == 0 and per["dense"] == len(FORESTS["periodic3d"])
+    one = make_batch(mg, FORESTS["cyl"][:1]).coarse_info()
+    assert one["block"] == 0 and one["dense"] == 1
+    # the 31 x 31 coarsest level of a k = 31 tree: 31 planes of 31 cells
+    big = make_batch(mg, [W.cyl_ring_tree(7, force_k=31), W.cyl_ring_tree(8, force_k=31)]).coarse_info()
+    nc, P = 31 * 31, 31
+    stride = (P * P + 2 * P + 1) & ~1  # plane record: S_j^-1, two couplings, padded to even
+    assert big["block"] == 2 and big["block_bytes"] == 2 * 31 * stride * 8
+    assert 2 * nc * nc * 8 >= 10 * big["block_bytes"]
+
+
+def test_batch_block_coarse_solve_matches_dense(mg):
+    """The block-tridiagonal coarsest solve of a tree equals the dense one of
+    the same tree run alone (a batch of one) after FMG and V-cycles, to
+    rounding, for large and small coarsest levels."""
+    probs = [W.cyl_ring_tree(7, force_k=31), W.cyl_ring_tree(9, force_k=5), W.cyl_ring_tree(10, force_k=17)]
+    b = make_batch(mg, probs)
+    assert b.coarse_info()["block"] == 3
+    b.fmg()
+    b.vcycle(2)
+    phi = b.get_phi().cpu().numpy()
+    for i, p in enumerate(probs):
+        one = make_batch(mg, [p])
+        one.fmg()
+        one.vcycle(2)
+        s = slice(b.offsets[i], b.offsets[i + 1])
+        assert rel_diff(phi[s], one.get_phi().cpu().numpy()) < TOL, p.name
