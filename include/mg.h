@@ -118,9 +118,32 @@ int mg_tree_create(int dim, int block_size, int geometry, const mg_bc *bc,
  */
 int mg_tree_refine(mg_tree *t, int n, const int32_t *host_entries);
 
-/* Mesh queries (build the host tables if not built yet; no device work).
+/*
+ * Mesh construction (Sec. 2.5): the block tables (levels, Morton order with
+ * covered blocks first, offsets, parents, face neighbours) are built at the
+ * first query or at finalize, on the current CUDA device when there is one
+ * (kernels and one radix sort per level; the block table stays on the
+ * device for finalize), else on the host.  Both give identical tables.
+ * mg_tree_build_on -- before the build: where = 0 device when present,
+ *   1 host, 2 device (MG_ERR_UNSUPPORTED without a device); MG_ERR_STATE
+ *   once built.
+ * mg_tree_built_on -- builds if needed; *where = 1 host, 2 device.
+ * mg_tree_block_table -- builds if needed; *nblocks = blocks of all levels;
+ *   host_out (NULL: count only) receives 24 int64 per block in global id
+ *   order: cell offset, ghost offset, N, level, flags (bit 0: covered),
+ *   parent id (-1 on level 0), block coordinates [3], offset inside the
+ *   parent in parent cells [3], face neighbours [6] (>= 0 same-level id,
+ *   -1 physical face, <= -2 the coarser block -2 - v), ghost push slots [6]
+ *   (first ghost value of the neighbour's opposite face, -1 if none).
+ *   A refine entry naming no block gives MG_ERR_ARG; a mesh that is not 2:1
+ *   balanced across faces, MG_ERR_BALANCE.
+ *
+ * Mesh queries (build the tables if not built yet).
  * level_info: info[0..8] = N_l, depth, blocks, blocks per dim[3], cells per
  * dim[3]; h[3] cell size.  Level 0 is the coarsest. */
+int mg_tree_build_on(mg_tree *t, int where);
+int mg_tree_built_on(mg_tree *t, int *where);
+int mg_tree_block_table(mg_tree *t, int64_t *nblocks, int64_t *host_out);
 int mg_tree_num_levels(mg_tree *t, int *nlev);
 int mg_tree_level_info(mg_tree *t, int level, int32_t info[9], double h[3]);
 int mg_tree_num_leaf_cells(mg_tree *t, int64_t *n);
@@ -165,7 +188,8 @@ int mg_tree_adapt(mg_tree *t, int n_add, const int32_t *add, int n_remove, const
 
 /*
  * mg_tree_build_times -- wall seconds of this tree's construction: out4[0]
- * host tables (levels, neighbours, offsets), out4[1] device setup
+ * the mesh tables (levels, neighbours, offsets; on the device or the host,
+ * mg_tree_built_on), out4[1] device setup
  * (allocation, uploads, coarsest-level inverse), out4[2] FP64 sweep
  * autotuning at finalize (0 for a tree made by mg_tree_adapt, which takes
  * over the old tree's choices), out4[3] the phi transfer of mg_tree_adapt

@@ -35,7 +35,7 @@ class Tree:
     """One quadtree/octree mesh and its device fields."""
 
     def __init__(self, dim, N, geom, bc_type, bc_val, base, lo, hi, refine=None, coarse_max=512,
-                 helm=0.0, finalize=True):
+                 helm=0.0, finalize=True, build_on=0):
         L = _lib.load()
         self.L = L
         bc = _lib.mg_bc((C.c_int * 6)(*[int(x) for x in bc_type]), (C.c_double * 6)(*[float(x) for x in bc_val]))
@@ -49,6 +49,8 @@ class Tree:
         if refine is not None and len(refine):
             ref = np.ascontiguousarray(refine, dtype=np.int32).reshape(-1, 4)
             check(L.mg_tree_refine(self._h, len(ref), ref.ctypes.data_as(C.c_void_p)))
+        if build_on:  # 1: host mesh tables, 2: device (default: device when present)
+            check(L.mg_tree_build_on(self._h, int(build_on)))
         n = C.c_int64()
         check(L.mg_tree_num_leaf_cells(self._h, C.byref(n)))
         self.n_leaf = n.value
@@ -57,12 +59,12 @@ class Tree:
             self.finalize()
 
     @classmethod
-    def from_problem(cls, p, set_fields=True, device="cuda", finalize=True):
+    def from_problem(cls, p, set_fields=True, device="cuda", finalize=True, build_on=0):
         """Tree of a synthetic problem with its boundary planes; finalize=False
         leaves it on the host (e.g. as a member of a Batch, which copies it)."""
         from synth import workloads as W
         t = cls(p.dim, p.N, p.geom, p.bc_type, p.bc_val, p.base, p.lo, p.hi, p.refine, p.coarse_max,
-                finalize=False)
+                finalize=False, build_on=build_on)
         if p.bc is not None:
             for l, info in enumerate(t.levels()):
                 for face in range(2 * p.dim):
@@ -77,6 +79,21 @@ class Tree:
                 t.set_eps(torch.from_numpy(W.leaf_field(p, "eps")).to(device))
             t.set_rhs(torch.from_numpy(W.leaf_field(p, "rhs")).to(device))
         return t
+
+    def built_on(self):
+        """Where the mesh tables were built: "host" or "device"."""
+        w = C.c_int()
+        check(self.L.mg_tree_built_on(self._h, C.byref(w)))
+        return "device" if w.value == 2 else "host"
+
+    def block_table(self):
+        """The block descriptors (mg_tree_block_table): int64 array of shape
+        (blocks, 24)."""
+        n = C.c_int64()
+        check(self.L.mg_tree_block_table(self._h, C.byref(n), None))
+        out = np.zeros((n.value, 24), np.int64)
+        check(self.L.mg_tree_block_table(self._h, C.byref(n), out.ctypes.data_as(C.c_void_p)))
+        return out
 
     def finalize(self):
         stream = torch.cuda.current_stream().cuda_stream
@@ -101,7 +118,7 @@ class Tree:
         return t
 
     def build_times(self):
-        """Seconds: host tables, device setup, FP64 autotuning, adapt's phi
+        """Seconds: mesh tables (device or host), device setup, FP64 autotuning, adapt's phi
         transfer (mg_tree_build_times)."""
         out = (C.c_double * 4)()
         check(self.L.mg_tree_build_times(self._h, out))

@@ -16,7 +16,8 @@ ERRORS = {-1: "MG_ERR_ARG", -2: "MG_ERR_BALANCE", -3: "MG_ERR_CUDA", -4: "MG_ERR
           -9: "MG_ERR_UNSUPPORTED"}
 
 # every entry point declared in include/mg.h
-EXPORTS = ["mg_tree_create", "mg_tree_refine", "mg_tree_num_levels", "mg_tree_level_info",
+EXPORTS = ["mg_tree_create", "mg_tree_refine", "mg_tree_build_on", "mg_tree_built_on", "mg_tree_block_table",
+           "mg_tree_num_levels", "mg_tree_level_info",
            "mg_tree_num_leaf_cells", "mg_tree_leaf_blocks", "mg_set_bc_plane", "mg_tree_finalize",
            "mg_tree_adapt", "mg_tree_build_times",
            "mg_set_rhs", "mg_set_eps", "mg_set_phi", "mg_get_phi", "mg_vcycle", "mg_fmg",
@@ -66,6 +67,9 @@ def load():
     L.mg_tree_level_info.argtypes = [vp, C.c_int, vp, dp]
     L.mg_tree_num_leaf_cells.argtypes = [vp, C.POINTER(C.c_int64)]
     L.mg_tree_leaf_blocks.argtypes = [vp, vp]
+    L.mg_tree_build_on.argtypes = [vp, C.c_int]
+    L.mg_tree_built_on.argtypes = [vp, ip]
+    L.mg_tree_block_table.argtypes = [vp, vp, vp]
     L.mg_set_bc_plane.argtypes = [vp, C.c_int, C.c_int, vp]
     L.mg_tree_finalize.argtypes = [vp, vp]
     L.mg_tree_adapt.argtypes = [vp, C.c_int, vp, C.c_int, vp, C.POINTER(vp)]

@@ -14,7 +14,7 @@ OUT = os.path.join(HERE, "libmg_gb300.so")
 BUILD = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC"]
-SOURCES = ["mg_kernels.cu", "mg_adjoint.cu", "mg_tree.cpp"]
+SOURCES = ["mg_kernels.cu", "mg_adjoint.cu", "mg_build.cu", "mg_tree.cpp"]
 
 
 def _nvcc():

@@ -115,6 +115,24 @@ __host__ __device__ inline int bt32_row(int P) {
 }
 __host__ __device__ inline int bt32_stride(int P) { return P * bt32_row(P) + 2 * bt_round4(P); }
 
+// Morton code of block coordinates (21 bits each: i at bit 3b, j at 3b+1,
+// k at 3b+2), the order of blocks within a level.
+__host__ __device__ inline uint64_t morton3(int i, int j, int k) {
+    uint64_t c = 0;
+    for (int b = 0; b < 21; b++) {
+        c |= (uint64_t)((i >> b) & 1) << (3 * b);
+        c |= (uint64_t)((j >> b) & 1) << (3 * b + 1);
+        c |= (uint64_t)((k >> b) & 1) << (3 * b + 2);
+    }
+    return c;
+}
+
+// Level skeleton of the mesh construction: block size, depth and block grid.
+struct LvSkel {
+    int n = 0, depth = 0;
+    int nblk[3] = {1, 1, 1};
+};
+
 template <class T>
 struct Fields {
     T *X = nullptr, *XG = nullptr;   // solution: interior + ghosts
@@ -198,6 +216,9 @@ struct mg_tree {
     double omega = 0.8;            // Jacobi weight of the current call
     double *d_minv = nullptr;      // coarsest-level inverses, row-major ns x ns per tree
     long long minv_total = 0, cvec_total = 0;
+    int build_where = 0;           // mesh tables: 0 device when present, 1 host, 2 device (mg_tree_build_on)
+    bool built_on_device = false;
+    mg::BlockDesc *d_blocks_built = nullptr;  // block table left on the device by the device build
     double *d_bt = nullptr;        // plane records of the block-tridiagonal trees (FP64)
     float *d_bt32 = nullptr;       // the same rounded to FP32 (FP32 cycles)
     int *d_btperm = nullptr;       // their plane-order -> row maps
@@ -239,6 +260,11 @@ struct mg_tree {
 };
 
 namespace mg {
+// mesh construction (mg_tree.cpp, mg_build.cu)
+std::vector<LvSkel> level_skeleton(const mg_tree *t, int maxdepth);
+int max_refine_depth(const mg_tree *t);
+void fill_levels(mg_tree *t, const std::vector<LvSkel> &lv, const std::vector<int> &nb, const std::vector<int> &nref);
+int build_tables_device(mg_tree *t);
 // cycle driver and kernels (mg_kernels.cu); all enqueue on t->stream
 template <class T> void vcycle(mg_tree *t, Fields<T> &F, int top, int nd, int nu, int homog);
 template <class T> void fmg(mg_tree *t, Fields<T> &F, int nd, int nu, int homog);

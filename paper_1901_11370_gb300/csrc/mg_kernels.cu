@@ -2405,7 +2405,12 @@ __global__ void __launch_bounds__(kMaxThreads, 3) k_resid_tma(KParams P, int fir
         // and ghosts are aligned once to their largest exponent, in place in
         // the stage; per cell that leaves integer adds, one FP64 FMA and an
         // integer rounding to FP32 (GB300's FP64 pipe is 1/64 of FP32).
+        // The aligned values go to a padded (n+2)^D array (interior at
+        // (i+1, j+1, k+1), each face ghost at its outside position), so that
+        // a cell's six neighbours are fixed offsets with no branch.
         const bool iso = !var && !cyl && helm0 && w0 == w1 && (D == 2 || w0 == w2);
+        constexpr int W = n + 2, W2 = D == 3 ? W * W : 0;
+        int64_t *xp = reinterpret_cast<int64_t *>(stage0 + 2 * stage_elems);  // allocated when !var && !wc
         int em = 0x7FF;
         if (iso) {
             int e = 1;
@@ -2416,28 +2421,15 @@ __global__ void __launch_bounds__(kMaxThreads, 3) k_resid_tma(KParams P, int fir
             em = 1;
             for (int w = 0; w < (nth >> 5); w++) em = max(em, semax[w]);
             if (em != 0x7FF) {  // a non-finite value anywhere: the FP64 form below
-                int64_t *xq = reinterpret_cast<int64_t *>(xs);
-                for (int q = tid; q < C + GH; q += nth) xq[q] = mg_fix(xs[q], em);
+                for (int q = tid; q < C + GH; q += nth) {
+                    I3 p3;
+                    if (q < C) p3 = I3{q % n, (q / n) % n, D == 3 ? q / (n * n) : 0};
+                    else p3 = face_cell<D>(n, (q - C) / FC, (q - C) % FC, true);
+                    xp[(D == 3 ? (p3.z + 1) * W2 : 0) + (p3.y + 1) * W + p3.x + 1] = mg_fix(xs[q], em);
+                }
             }
             __syncthreads();
         }
-        const int64_t *xi = reinterpret_cast<const int64_t *>(xs), *gi = xi + C;
-        auto nbi = [&](int i, int j, int k, int d, int s) -> int64_t {
-            const int o = s ? 1 : -1;
-            if (d == 0) {
-                const int ii = i + o;
-                if (ii < 0 || ii >= n) return gi[(s ? 1 : 0) * FC + (D == 2 ? j : j + n * k)];
-                return xi[cidx<D>(n, ii, j, k)];
-            }
-            if (d == 1) {
-                const int jj = j + o;
-                if (jj < 0 || jj >= n) return gi[(s ? 3 : 2) * FC + (D == 2 ? i : i + n * k)];
-                return xi[cidx<D>(n, i, jj, k)];
-            }
-            const int kk = k + o;
-            if (kk < 0 || kk >= n) return gi[(s ? 5 : 4) * FC + i + n * j];
-            return xi[cidx<D>(n, i, j, kk)];
-        };
         double bs2 = 0;
         const float lo0f = P.lo0f, h0f = L.h0f, hvf = L.hvf;
         vol_u = vol;
@@ -2446,9 +2438,9 @@ __global__ void __launch_bounds__(kMaxThreads, 3) k_resid_tma(KParams P, int fir
             double lap;  // A x + lambda x (the residual below subtracts lambda x)
             double r;
             if (iso && em != 0x7FF) {
-                int64_t S = -(int64_t)(2 * D) * xi[c];
-#pragma unroll
-                for (int f = 0; f < 2 * D; f++) S += nbi(i, j, k, f >> 1, f & 1);
+                const int64_t *xc = xp + (D == 3 ? (k + 1) * W2 : 0) + (j + 1) * W + i + 1;
+                int64_t S = (xc[-1] + xc[1]) + (xc[-W] + xc[W]) - (int64_t)(2 * D) * xc[0];
+                if (D == 3) S += xc[-W2] + xc[W2];
                 double sd;
                 if (!mg_unfix(S, em, sd)) sd = unfix_wide(S, em);  // outside the normal range
                 r = fma(-w0, sd, fs[c]);
@@ -3625,8 +3617,11 @@ template <class T, int D> struct Launch {
         sweep_cand(t, P, l, F, colour, cand);
         (void)L;
     }
-    static void sweep_cand(mg_tree *t, const KParams &P, int l, Fields<T> &F, int colour, int cand) {
+    // nbx: the first nbx blocks of the level only (the autotuner's timed
+    // subset of a very large level); -1 for the whole level
+    static void sweep_cand(mg_tree *t, const KParams &P, int l, Fields<T> &F, int colour, int cand, int nbx = -1) {
         const LevelHost &L = t->lev[l];
+        const int nb = nbx >= 0 ? std::min(L.nb, nbx) : L.nb;
         const int n = L.n;
         ++t->launches;
         const size_t sm = cand_smem(t, l, F, cand);
@@ -3636,15 +3631,15 @@ template <class T, int D> struct Launch {
             auto kern = n == 8 ? (half ? k_sweep_tma<T, D, 8, true> : k_sweep_tma<T, D, 8>)
                                : (half ? k_sweep_tma<T, D, 16, true> : k_sweep_tma<T, D, 16>);
             const int thr = sweep_tma_threads(cells_of<D>(n) / 2, half);
-            const int grid = std::min(L.nb, resident_ctas(kern, thr, sm) * t->nsm);
-            launch_k(kern, grid, thr, sm, t->stream, P, L.first, L.nb, F, colour);
+            const int grid = std::min(nb, resident_ctas(kern, thr, sm) * t->nsm);
+            launch_k(kern, grid, thr, sm, t->stream, P, L.first, nb, F, colour);
             return;
         }
         case 2: case 3: {
             const int W = cand == 2 ? 8 : 4;
             auto kern = cand == 2 ? k_sweep_warp<T, D, 8> : k_sweep_warp<T, D, 4>;
-            const int grid = std::min((L.nb + W - 1) / W, resident_ctas(kern, 32 * W, sm) * t->nsm);
-            launch_k(kern, grid, 32 * W, sm, t->stream, P, L.first, L.nb, F, colour);
+            const int grid = std::min((nb + W - 1) / W, resident_ctas(kern, 32 * W, sm) * t->nsm);
+            launch_k(kern, grid, 32 * W, sm, t->stream, P, L.first, nb, F, colour);
             return;
         }
         case 4: case 5: case 7: case 8: case 9: {
@@ -3654,14 +3649,14 @@ template <class T, int D> struct Launch {
                           : cand == 7 ? k_sweep_rows<T, 8, 3, true> : cand == 8 ? k_sweep_rows<T, 4, 4, true>
                                       : k_sweep_rows<T, 8, 2, true>;
                 set_smem(kern, sm);
-                const int grid = std::min((L.nb + W - 1) / W, resident_ctas(kern, 32 * W, sm) * t->nsm);
-                launch_k(kern, grid, 32 * W, sm, t->stream, P, L.first, L.nb, F, colour);
+                const int grid = std::min((nb + W - 1) / W, resident_ctas(kern, 32 * W, sm) * t->nsm);
+                launch_k(kern, grid, 32 * W, sm, t->stream, P, L.first, nb, F, colour);
             }
             return;
         }
         case 6: {
             const int ncol = (n & 1) ? cells_of<D>(n) : cells_of<D>(n) / 2;
-            launch_k(k_sweep_flat<T, D>, flat_grid(t, (long long)L.nb * ncol), 256, 0, t->stream, P, L.first, L.nb, n, F,
+            launch_k(k_sweep_flat<T, D>, flat_grid(t, (long long)nb * ncol), 256, 0, t->stream, P, L.first, nb, n, F,
                                                                                           colour);
             return;
         }
@@ -3670,13 +3665,13 @@ template <class T, int D> struct Launch {
             const size_t smp = sizeof(T) * pad * (F.E ? 2 : 1);
             const int th = threads_for((n & 1) ? cells_of<D>(n) : cells_of<D>(n) / 2);
             if (n == 8) {
-                launch_k(k_sweep<T, D, 8>, L.nb, th, smp, t->stream, P, L.first, F, colour);
+                launch_k(k_sweep<T, D, 8>, nb, th, smp, t->stream, P, L.first, F, colour);
             } else if (n == 16) {
                 set_smem(k_sweep<T, D, 16>, smp);
-                launch_k(k_sweep<T, D, 16>, L.nb, th, smp, t->stream, P, L.first, F, colour);
+                launch_k(k_sweep<T, D, 16>, nb, th, smp, t->stream, P, L.first, F, colour);
             } else {
                 set_smem(k_sweep<T, D, 0>, smp);
-                launch_k(k_sweep<T, D, 0>, L.nb, th, smp, t->stream, P, L.first, F, colour);
+                launch_k(k_sweep<T, D, 0>, nb, th, smp, t->stream, P, L.first, F, colour);
             }
         }
         }
@@ -3701,14 +3696,18 @@ template <class T, int D> struct Launch {
             // the candidates within 3 % of the fastest median the lowest
             // variant number wins, so near-ties resolve the same way in
             // every process
+            // a level above kTuneCells cells is timed on its first blocks
+            // (per-block costs do not change with the count beyond that)
+            constexpr long long kTuneCells = 32LL << 20;
+            const int nbx = (int)std::min<long long>(t->lev[l].nb, std::max<long long>(1, kTuneCells / cells_of<D>(t->lev[l].n)));
             for (int cand : cands)
-                for (int w = 0; w < 4; w++) sweep_cand(t, P, (int)l, F, w & 1, cand);
+                for (int w = 0; w < 4; w++) sweep_cand(t, P, (int)l, F, w & 1, cand, nbx);
             constexpr int kRounds = 5;
             std::vector<std::vector<float>> times(cands.size());
             for (int round = 0; round < kRounds; round++)
                 for (size_t ci = 0; ci < cands.size(); ci++) {
                     cudaEventRecord(e0, t->stream);
-                    for (int w = 0; w < 4; w++) sweep_cand(t, P, (int)l, F, w & 1, cands[ci]);
+                    for (int w = 0; w < 4; w++) sweep_cand(t, P, (int)l, F, w & 1, cands[ci], nbx);
                     cudaEventRecord(e1, t->stream);
                     cudaEventSynchronize(e1);
                     float ms = 0;
@@ -4044,8 +4043,9 @@ template void refresh_eps<float>(mg_tree *, Fields<float> &);
 // bytes of the two stages of k_resid_tma for n-cell blocks
 template <int D> static size_t resid_smem(int n, const Fields<double> &F) {
     const int C = cells_of<D>(n), GH = 2 * D * face_of<D>(n);
+    const size_t padded = (!F.W && !F.E) ? sizeof(int64_t) * cells_of<D>(n + 2) : 0;  // exact-sum stencil array
     return 2 * (sizeof(BlockDesc) + sizeof(LevelDesc) +
-                sizeof(double) * (2 * C + GH + (F.W ? (2 * D + 1) * C : (F.E ? C + GH : 0))));
+                sizeof(double) * (2 * C + GH + (F.W ? (2 * D + 1) * C : (F.E ? C + GH : 0)))) + padded;
 }
 
 template <int D>

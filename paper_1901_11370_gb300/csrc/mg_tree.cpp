@@ -37,16 +37,6 @@ static int fail(int code, const std::string &msg) {
     return code;
 }
 
-static uint64_t morton3(int i, int j, int k) {
-    uint64_t c = 0;
-    for (int b = 0; b < 21; b++) {
-        c |= (uint64_t)((i >> b) & 1) << (3 * b);
-        c |= (uint64_t)((j >> b) & 1) << (3 * b + 1);
-        c |= (uint64_t)((k >> b) & 1) << (3 * b + 2);
-    }
-    return c;
-}
-
 static long long ipow(int n, int d) { return d == 2 ? (long long)n * n : (long long)n * n * n; }
 
 // ------------------------------------------------------------ create ----
@@ -114,104 +104,55 @@ static double seconds_since(std::chrono::steady_clock::time_point t0) {
     return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
 }
 
-static int build(mg_tree *t) {
-    if (t->built) return MG_OK;
-    const auto t0 = std::chrono::steady_clock::now();
+// Level skeleton: the coarse levels (block count halved while every count
+// is even, then block size halved while the level holds more than
+// coarse_max cells), the base grid, and maxdepth + 1 refined levels.
+std::vector<LvSkel> mg::level_skeleton(const mg_tree *t, int maxdepth) {
     const int D = t->dim;
-    struct Lv { int n, depth, nblk[3]; std::vector<std::array<int, 3>> b; };
-    std::vector<Lv> lv;
+    std::vector<LvSkel> coarse;
     int nb0[3] = {1, 1, 1};
     for (int d = 0; d < D; d++) nb0[d] = t->base[d] / t->N;
-    {
-        std::vector<Lv> coarse;
-        int n = t->N, b[3] = {nb0[0], nb0[1], nb0[2]};
-        while (true) {
-            long long cells = 1;
-            bool even = true;
-            for (int d = 0; d < D; d++) { cells *= (long long)n * b[d]; if (b[d] % 2) even = false; }
-            if (even) for (int d = 0; d < D; d++) b[d] /= 2;
-            else if (cells > t->coarse_max && n % 2 == 0) n /= 2;
-            else break;
-            Lv c;
-            c.n = n; c.depth = -(int)coarse.size() - 1;
-            for (int d = 0; d < 3; d++) c.nblk[d] = b[d];
-            coarse.push_back(c);
-            if (coarse.size() > 60) break;
-        }
-        std::reverse(coarse.begin(), coarse.end());
-        lv = coarse;
-        Lv base;
-        base.n = t->N; base.depth = 0;
-        for (int d = 0; d < 3; d++) base.nblk[d] = nb0[d];
-        lv.push_back(base);
-        for (auto &L : lv)
-            for (int k = 0; k < L.nblk[2]; k++)
-                for (int j = 0; j < L.nblk[1]; j++)
-                    for (int i = 0; i < L.nblk[0]; i++) L.b.push_back({i, j, k});
+    int n = t->N, b[3] = {nb0[0], nb0[1], nb0[2]};
+    while (true) {
+        long long cells = 1;
+        bool even = true;
+        for (int d = 0; d < D; d++) { cells *= (long long)n * b[d]; if (b[d] % 2) even = false; }
+        if (even) for (int d = 0; d < D; d++) b[d] /= 2;
+        else if (cells > t->coarse_max && n % 2 == 0) n /= 2;
+        else break;
+        LvSkel c;
+        c.n = n; c.depth = -(int)coarse.size() - 1;
+        for (int d = 0; d < 3; d++) c.nblk[d] = b[d];
+        coarse.push_back(c);
+        if (coarse.size() > 60) break;
     }
-    const int ibase = (int)lv.size() - 1;
+    std::reverse(coarse.begin(), coarse.end());
+    std::vector<LvSkel> lv = coarse;
+    LvSkel base;
+    base.n = t->N; base.depth = 0;
+    for (int d = 0; d < 3; d++) base.nblk[d] = nb0[d];
+    lv.push_back(base);
+    for (int r = 0; r <= maxdepth; r++) {
+        LvSkel c;
+        c.n = t->N; c.depth = r + 1;
+        for (int d = 0; d < 3; d++) c.nblk[d] = d < D ? 2 * lv.back().nblk[d] : 1;
+        lv.push_back(c);
+    }
+    return lv;
+}
+
+int mg::max_refine_depth(const mg_tree *t) {
     int maxdepth = -1;
     for (size_t e = 0; e < t->refine.size() / 4; e++) maxdepth = std::max(maxdepth, t->refine[4 * e]);
-    for (int r = 0; r <= maxdepth; r++) {
-        const Lv &P = lv[ibase + r];
-        std::vector<char> exists((size_t)P.nblk[0] * P.nblk[1] * P.nblk[2], 0), done(exists.size(), 0);
-        for (auto &q : P.b) exists[((size_t)q[2] * P.nblk[1] + q[1]) * P.nblk[0] + q[0]] = 1;
-        Lv C;
-        C.n = t->N; C.depth = r + 1;
-        for (int d = 0; d < 3; d++) C.nblk[d] = d < D ? 2 * P.nblk[d] : 1;
-        for (size_t e = 0; e < t->refine.size() / 4; e++) {
-            if (t->refine[4 * e] != r) continue;
-            int q[3] = {t->refine[4 * e + 1], t->refine[4 * e + 2], D == 3 ? t->refine[4 * e + 3] : 0};
-            bool ok = true;
-            for (int d = 0; d < 3; d++) ok = ok && q[d] >= 0 && q[d] < P.nblk[d];
-            size_t m = ok ? ((size_t)q[2] * P.nblk[1] + q[1]) * P.nblk[0] + q[0] : 0;
-            if (!ok || !exists[m]) return fail(MG_ERR_ARG, "refined block does not exist");
-            if (done[m]) continue;
-            done[m] = 1;
-            for (int c = 0; c < (1 << D); c++)
-                C.b.push_back({2 * q[0] + (c & 1), 2 * q[1] + ((c >> 1) & 1), D == 3 ? 2 * q[2] + ((c >> 2) & 1) : 0});
-        }
-        if (C.b.empty()) return fail(MG_ERR_ARG, "refinement depths must be contiguous");
-        lv.push_back(C);
-    }
-    const int nl = (int)lv.size();
-    // dense coordinate maps and "has children" flags
-    std::vector<std::vector<int>> map(nl);
-    std::vector<std::vector<char>> haschild(nl);
-    auto key = [&](int l, int i, int j, int k) { return ((size_t)k * lv[l].nblk[1] + j) * lv[l].nblk[0] + i; };
-    for (int l = 0; l < nl; l++) {
-        map[l].assign((size_t)lv[l].nblk[0] * lv[l].nblk[1] * lv[l].nblk[2], -1);
-        haschild[l].assign(lv[l].b.size(), 0);
-        for (size_t b = 0; b < lv[l].b.size(); b++) map[l][key(l, lv[l].b[b][0], lv[l].b[b][1], lv[l].b[b][2])] = (int)b;
-    }
-    auto parent_of = [&](int l, const std::array<int, 3> &q, int *pq, int *poff) {
-        const bool same = lv[l - 1].n == lv[l].n;
-        for (int d = 0; d < 3; d++) {
-            pq[d] = d < D ? (same ? q[d] / 2 : q[d]) : 0;
-            poff[d] = d < D ? (same ? (q[d] % 2) * (lv[l].n / 2) : 0) : 0;
-        }
-    };
-    for (int l = 1; l < nl; l++)
-        for (auto &q : lv[l].b) {
-            int pq[3], po[3];
-            parent_of(l, q, pq, po);
-            haschild[l - 1][map[l - 1][key(l - 1, pq[0], pq[1], pq[2])]] = 1;
-        }
-    // order: covered blocks, then leaves, Morton within each group
-    std::vector<std::vector<int>> order(nl);
-    for (int l = 0; l < nl; l++) {
-        std::vector<int> &o = order[l];
-        o.resize(lv[l].b.size());
-        for (size_t b = 0; b < o.size(); b++) o[b] = (int)b;
-        std::sort(o.begin(), o.end(), [&](int a, int c) {
-            if (haschild[l][a] != haschild[l][c]) return haschild[l][a] > haschild[l][c];
-            return morton3(lv[l].b[a][0], lv[l].b[a][1], lv[l].b[a][2]) <
-                   morton3(lv[l].b[c][0], lv[l].b[c][1], lv[l].b[c][2]);
-        });
-    }
-    // global ids and offsets
+    return maxdepth;
+}
+
+// Level descriptors from the skeleton and the block counts: 32-element
+// (128/256-byte) aligned cell and ghost ranges, global ids level by level.
+void mg::fill_levels(mg_tree *t, const std::vector<LvSkel> &lv, const std::vector<int> &nb,
+                 const std::vector<int> &nref) {
+    const int D = t->dim, nl = (int)lv.size();
     t->lev.assign(nl, LevelHost());
-    std::vector<std::vector<int>> gid(nl);
     int g = 0;
     long long co = 0, go = 0, leaf = 0;
     for (int l = 0; l < nl; l++) {
@@ -223,18 +164,15 @@ static int build(mg_tree *t) {
             L.h[d] = d < D ? (t->hi[d] - t->lo[d]) / L.ncell[d] : 1.0;
         }
         L.first = g;
-        L.nb = (int)lv[l].b.size();
-        L.nref = 0;
-        for (int b = 0; b < L.nb; b++) L.nref += haschild[l][b];
-        co = (co + 31) / 32 * 32;  // 32-element (128/256-byte) aligned levels
+        L.nb = nb[l];
+        L.nref = nref[l];
+        co = (co + 31) / 32 * 32;
         go = (go + 31) / 32 * 32;
         L.cell_first = co;
         L.ghost_first = go;
         L.ncells = L.nb * ipow(L.n, D);
         L.nghost = L.nb * 2LL * D * (D == 2 ? L.n : (long long)L.n * L.n);
         leaf += (long long)(L.nb - L.nref) * ipow(L.n, D);
-        gid[l].assign(L.nb, -1);
-        for (int r = 0; r < L.nb; r++) gid[l][order[l][r]] = g + r;
         g += L.nb;
         co += L.ncells;
         go += L.nghost;
@@ -242,6 +180,87 @@ static int build(mg_tree *t) {
     t->ncells = co;
     t->nghost = go;
     t->nleaf_cells = leaf;
+}
+
+// Block tables on the host: per level, the blocks (the coarse levels and the
+// base grid whole, refined levels from the refine entries), covered blocks
+// first and Morton order within each group, then per block its offsets,
+// parent and face neighbours (same level, physical, or one level coarser).
+static int build_tables_host(mg_tree *t) {
+    const int D = t->dim;
+    const int maxdepth = max_refine_depth(t);
+    const std::vector<LvSkel> sk = level_skeleton(t, maxdepth);
+    const int nl = (int)sk.size(), ibase = nl - 1 - (maxdepth + 1);
+    std::vector<std::vector<std::array<int, 3>>> lb(nl);
+    for (int l = 0; l <= ibase; l++)
+        for (int k = 0; k < sk[l].nblk[2]; k++)
+            for (int j = 0; j < sk[l].nblk[1]; j++)
+                for (int i = 0; i < sk[l].nblk[0]; i++) lb[l].push_back({i, j, k});
+    for (int r = 0; r <= maxdepth; r++) {
+        const LvSkel &P = sk[ibase + r];
+        std::vector<char> exists((size_t)P.nblk[0] * P.nblk[1] * P.nblk[2], 0), done(exists.size(), 0);
+        for (auto &q : lb[ibase + r]) exists[((size_t)q[2] * P.nblk[1] + q[1]) * P.nblk[0] + q[0]] = 1;
+        std::vector<std::array<int, 3>> &C = lb[ibase + r + 1];
+        for (size_t e = 0; e < t->refine.size() / 4; e++) {
+            if (t->refine[4 * e] != r) continue;
+            int q[3] = {t->refine[4 * e + 1], t->refine[4 * e + 2], D == 3 ? t->refine[4 * e + 3] : 0};
+            bool ok = true;
+            for (int d = 0; d < 3; d++) ok = ok && q[d] >= 0 && q[d] < P.nblk[d];
+            size_t m = ok ? ((size_t)q[2] * P.nblk[1] + q[1]) * P.nblk[0] + q[0] : 0;
+            if (!ok || !exists[m]) return fail(MG_ERR_ARG, "refined block does not exist");
+            if (done[m]) continue;
+            done[m] = 1;
+            for (int c = 0; c < (1 << D); c++)
+                C.push_back({2 * q[0] + (c & 1), 2 * q[1] + ((c >> 1) & 1), D == 3 ? 2 * q[2] + ((c >> 2) & 1) : 0});
+        }
+        if (C.empty()) return fail(MG_ERR_ARG, "refinement depths must be contiguous");
+    }
+    // dense coordinate maps and "has children" flags
+    std::vector<std::vector<int>> map(nl);
+    std::vector<std::vector<char>> haschild(nl);
+    auto key = [&](int l, int i, int j, int k) { return ((size_t)k * sk[l].nblk[1] + j) * sk[l].nblk[0] + i; };
+    for (int l = 0; l < nl; l++) {
+        map[l].assign((size_t)sk[l].nblk[0] * sk[l].nblk[1] * sk[l].nblk[2], -1);
+        haschild[l].assign(lb[l].size(), 0);
+        for (size_t b = 0; b < lb[l].size(); b++) map[l][key(l, lb[l][b][0], lb[l][b][1], lb[l][b][2])] = (int)b;
+    }
+    auto parent_of = [&](int l, const std::array<int, 3> &q, int *pq, int *poff) {
+        const bool same = sk[l - 1].n == sk[l].n;
+        for (int d = 0; d < 3; d++) {
+            pq[d] = d < D ? (same ? q[d] / 2 : q[d]) : 0;
+            poff[d] = d < D ? (same ? (q[d] % 2) * (sk[l].n / 2) : 0) : 0;
+        }
+    };
+    for (int l = 1; l < nl; l++)
+        for (auto &q : lb[l]) {
+            int pq[3], po[3];
+            parent_of(l, q, pq, po);
+            haschild[l - 1][map[l - 1][key(l - 1, pq[0], pq[1], pq[2])]] = 1;
+        }
+    // order: covered blocks, then leaves, Morton within each group (one
+    // 64-bit key per block: the leaf flag above the 63-bit Morton code)
+    std::vector<std::vector<int>> order(nl);
+    std::vector<int> nb(nl), nref(nl, 0);
+    for (int l = 0; l < nl; l++) {
+        std::vector<std::pair<uint64_t, int>> kv(lb[l].size());
+        for (size_t b = 0; b < kv.size(); b++) {
+            nref[l] += haschild[l][b];
+            kv[b] = {((uint64_t)(haschild[l][b] ? 0 : 1) << 63) | morton3(lb[l][b][0], lb[l][b][1], lb[l][b][2]),
+                     (int)b};
+        }
+        std::sort(kv.begin(), kv.end());
+        order[l].resize(kv.size());
+        for (size_t r = 0; r < kv.size(); r++) order[l][r] = kv[r].second;
+        nb[l] = (int)kv.size();
+    }
+    fill_levels(t, sk, nb, nref);
+    std::vector<std::vector<int>> gid(nl);
+    for (int l = 0; l < nl; l++) {
+        gid[l].assign(nb[l], -1);
+        for (int r = 0; r < nb[l]; r++) gid[l][order[l][r]] = t->lev[l].first + r;
+    }
+    int g = 0;
+    for (int l = 0; l < nl; l++) g += nb[l];
     t->blocks.assign(g, BlockDesc());
     for (int l = 0; l < nl; l++) {
         const LevelHost &L = t->lev[l];
@@ -249,7 +268,7 @@ static int build(mg_tree *t) {
         for (int r = 0; r < L.nb; r++) {
             const int b = order[l][r];
             BlockDesc &B = t->blocks[L.first + r];
-            const auto &q = lv[l].b[b];
+            const auto &q = lb[l][b];
             B.cell_off = L.cell_first + r * C;
             B.ghost_off = L.ghost_first + r * F;
             B.n = L.n;
@@ -281,7 +300,7 @@ static int build(mg_tree *t) {
                         continue;
                     }
                     // no same-level neighbour: the region one level coarser must exist (2:1)
-                    if (l == 0 || lv[l - 1].n != L.n) return fail(MG_ERR_BALANCE, "incomplete coarse level");
+                    if (l == 0 || sk[l - 1].n != L.n) return fail(MG_ERR_BALANCE, "incomplete coarse level");
                     int cq[3] = {0, 0, 0};
                     for (int e = 0; e < D; e++) cq[e] = nq[e] / 2;
                     const int cm = map[l - 1][key(l - 1, cq[0], cq[1], cq[2])];
@@ -290,6 +309,30 @@ static int build(mg_tree *t) {
                 }
         }
     }
+    return MG_OK;
+}
+
+// Device build where a CUDA device is present and the tree has not asked
+// for the host build (mg_tree_build_on); the two give identical tables.
+static bool use_device_build(const mg_tree *t) {
+    if (t->build_where == 1) return false;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || n == 0) {
+        cudaGetLastError();
+        return false;
+    }
+    return true;
+}
+
+static int build(mg_tree *t) {
+    if (t->built) return MG_OK;
+    const auto t0 = std::chrono::steady_clock::now();
+    const int D = t->dim;
+    const bool dev = use_device_build(t);
+    int rc = dev ? build_tables_device(t) : build_tables_host(t);
+    if (rc) return rc;
+    t->built_on_device = dev;
+    const int nl = (int)t->lev.size();
     // red and black must alternate across periodic faces on every smoothed
     // level (the fused sweep relies on it); the coarsest level is solved directly
     for (int l = 1; l < nl; l++)
@@ -318,6 +361,44 @@ static int build(mg_tree *t) {
     t->max_nc = t->nc;
     t->built = true;
     t->build_s[0] = seconds_since(t0);
+    return MG_OK;
+}
+
+extern "C" int mg_tree_build_on(mg_tree *t, int where) {
+    if (!t || where < 0 || where > 2) return fail(MG_ERR_ARG, "bad arguments");
+    if (t->built) return fail(MG_ERR_STATE, "the mesh is already built");
+    if (where == 2) {
+        int n = 0;
+        if (cudaGetDeviceCount(&n) != cudaSuccess || n == 0) {
+            cudaGetLastError();
+            return fail(MG_ERR_UNSUPPORTED, "no CUDA device for the device mesh build");
+        }
+    }
+    t->build_where = where;
+    return MG_OK;
+}
+
+extern "C" int mg_tree_built_on(mg_tree *t, int *where) {
+    if (!t || !where) return fail(MG_ERR_ARG, "null argument");
+    int rc = build(t);
+    if (rc) return rc;
+    *where = t->built_on_device ? 2 : 1;
+    return MG_OK;
+}
+
+extern "C" int mg_tree_block_table(mg_tree *t, int64_t *nblocks, int64_t *out) {
+    if (!t || !nblocks) return fail(MG_ERR_ARG, "null argument");
+    int rc = build(t);
+    if (rc) return rc;
+    *nblocks = (int64_t)t->blocks.size();
+    if (!out) return MG_OK;
+    for (size_t g = 0; g < t->blocks.size(); g++) {
+        const BlockDesc &B = t->blocks[g];
+        int64_t *o = out + 24 * g;
+        o[0] = B.cell_off; o[1] = B.ghost_off; o[2] = B.n; o[3] = B.lev; o[4] = B.flags; o[5] = B.parent;
+        for (int d = 0; d < 3; d++) { o[6 + d] = B.ijk[d]; o[9 + d] = B.poff[d]; }
+        for (int f = 0; f < 6; f++) { o[12 + f] = B.nbr[f]; o[18 + f] = B.push[f]; }
+    }
     return MG_OK;
 }
 
@@ -711,8 +792,13 @@ extern "C" int mg_tree_finalize(mg_tree *t, void *stream) {
     CK(cudaGetDevice(&t->device));
     CK(cudaDeviceGetAttribute(&t->nsm, cudaDevAttrMultiProcessorCount, t->device));
     t->stream = (cudaStream_t)stream;
-    CK(cudaMalloc((void **)&t->d_blocks, sizeof(BlockDesc) * t->blocks.size()));
-    CK(cudaMemcpy(t->d_blocks, t->blocks.data(), sizeof(BlockDesc) * t->blocks.size(), cudaMemcpyHostToDevice));
+    if (t->d_blocks_built) {  // the device build's table (same entries as t->blocks)
+        t->d_blocks = t->d_blocks_built;
+        t->d_blocks_built = nullptr;
+    } else {
+        CK(cudaMalloc((void **)&t->d_blocks, sizeof(BlockDesc) * t->blocks.size()));
+        CK(cudaMemcpy(t->d_blocks, t->blocks.data(), sizeof(BlockDesc) * t->blocks.size(), cudaMemcpyHostToDevice));
+    }
     if ((rc = upload_bc(t))) return rc;
     if ((rc = alloc_fields(t, t->f64, false))) return rc;
     int maxleaf = 0;
@@ -1572,6 +1658,7 @@ extern "C" int mg_clean(mg_tree *t, const double *B, double *Bnew, double *divB,
 
 extern "C" int mg_tree_destroy(mg_tree *t) {
     if (!t) return MG_OK;
+    if (t->d_blocks_built) cudaFree(t->d_blocks_built);
     if (t->finalized) {
         cudaStreamSynchronize(t->stream);
         free_fields(t->f64, true);
