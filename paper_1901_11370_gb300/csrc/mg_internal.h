@@ -282,13 +282,14 @@ void project(mg_tree *t, const double *B, double *Bout);
 // r64 (FP64 leaf order), f32 (FP32 into the leaf cells of an FP32 field)
 void residual_norm(mg_tree *t, Fields<double> &F, int homog, double *out3, double *r64_leaf,
                    float *f32_cells);
-// want_max: also the max norm (solve loops read only the L2 norm)
+// want_max: also the max norm (solve loops read only the L2 norm); e_add:
+// first apply the defect-correction update phi += e on the leaves (fused
+// into the refresh before the residual)
 void residual_enqueue(mg_tree *t, Fields<double> &F, int homog, double *r64_leaf, float *f32_cells,
-                      bool want_max = false);
+                      bool want_max = false, const float *e_add = nullptr);
 void residual_wait(mg_tree *t, double *out3);
 // volume-weighted mean of a leaf-order FP64 field (synchronises the stream)
 double leaf_mean(mg_tree *t, const double *rleaf);
-void add_e_to_phi(mg_tree *t, const float *e, double *phi);
 void sub_scalar(mg_tree *t, double *x, double c, long long n);  // x[0..n) -= c
 // phi of old carried to the leaf blocks nid of the adapted mesh nt (see k_transfer)
 int transfer_phi(mg_tree *old, mg_tree *nt, const std::vector<int> &nid, const std::vector<int> &src);
@@ -298,7 +299,8 @@ void face_coef(mg_tree *t);
 KParams kparams(mg_tree *t, int homog);
 int time_sweeps(mg_tree *t, int level, int n_sweeps, int prec, double *out4);
 // batch: per-tree composite residual sums (3 per tree, on the host after wait)
-void residual_enqueue_trees(mg_tree *t, Fields<double> &F, float *f32_cells, bool want_max);
+void residual_enqueue_trees(mg_tree *t, Fields<double> &F, float *f32_cells, bool want_max,
+                            const float *e_add = nullptr);
 // copies between a concatenated per-tree leaf array and the pool cells
 void leaf_runs_copy(mg_tree *t, double *cells, const double *leaf, bool to_cells);
 int check_cuda(const char *what);

@@ -976,6 +976,66 @@ __global__ void __launch_bounds__(kMaxThreads) k_restrict(KParams P, int first, 
     }
 }
 
+// The defect-correction update fused into the covered-cell refresh: for one
+// block of a level (one CTA each; the level's first nref blocks are
+// covered), a leaf block first takes phi += e (e the FP32 correction,
+// widened exactly with integer operations) and writes phi back; then every
+// block restricts its values into the parent cells under it (mean of the
+// 2^D children, summed in the same order as k_restrict, so the result is
+// the one of the update followed by the plain refresh).  Fine cells are
+// read and written coalesced, kUpdCells per thread with every load issued
+// before the first use (bytes in flight against DRAM latency), and staged
+// in shared memory for the parent means.
+constexpr int kUpdCells = 4;
+template <int D>
+__global__ void __launch_bounds__(256) k_update_restrict(KParams P, int first, int nref, double *__restrict__ X,
+                                                         const float *__restrict__ e) {
+    pdl_entry();
+    __shared__ BlockDesc sb;
+    stage_desc(P, first + blockIdx.x, sb);
+    const BlockDesc &b = sb;
+    const BlockDesc &p = P.B[b.parent];
+    const int n = b.n, m = n / 2, C = cells_of<D>(n), M = cells_of<D>(m);
+    const bool leaf = (int)blockIdx.x >= nref;
+    extern __shared__ double xs[];
+    double *xb = X + b.cell_off;
+    const float *eb = e + b.cell_off;
+    for (int c0 = threadIdx.x; c0 < C; c0 += kUpdCells * blockDim.x) {
+        double xv[kUpdCells];
+        float ev[kUpdCells];
+#pragma unroll
+        for (int k = 0; k < kUpdCells; k++) {
+            const int c = c0 + k * blockDim.x;
+            if (c < C) {
+                xv[k] = xb[c];
+                ev[k] = leaf ? eb[c] : 0.0f;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < kUpdCells; k++) {
+            const int c = c0 + k * blockDim.x;
+            if (c < C) {
+                double x = xv[k];
+                if (leaf) {
+                    x += mg_from_float(ev[k]);
+                    xb[c] = x;
+                }
+                xs[c] = x;
+            }
+        }
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < M; c += blockDim.x) {
+        int ci, cj, ck;
+        cell_of(c, m, D, ci, cj, ck);
+        double sx = 0;
+#pragma unroll
+        for (int ch = 0; ch < (1 << D); ch++)
+            sx += xs[cidx<D>(n, 2 * ci + (ch & 1), 2 * cj + ((ch >> 1) & 1), D == 3 ? 2 * ck + ((ch >> 2) & 1) : 0)];
+        X[p.cell_off + cidx<D>(p.n, b.poff[0] + ci, b.poff[1] + cj, b.poff[2] + ck)] = sx * (1.0 / (1 << D));
+    }
+}
+
 // ------------------------------------------- transfers with ghost pushes ---
 // Push the ghosts that depend on the cells of one face of block b after those
 // cells changed: the same-level neighbour's slot opposite each cell, or the
@@ -3173,17 +3233,13 @@ __global__ void __launch_bounds__(kBtriThreads) k_coarse_btri(KParams P, const T
 }
 
 // --------------------------------------------------- elementwise ops ----
-// phi64 += e32 (the defect-correction update).  The widening of e is exact
-// and done with integer operations (mg_from_float; GB300 runs the
-// conversion instruction on its FP64 pipe), leaving one FP64 add per cell.
-__global__ void k_add_e(const float *__restrict__ e, double *__restrict__ x, long long n) {
-    pdl_entry();
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-        x[i] += mg_from_float(e[i]);
-}
-// The same on the leaf cells only (one contiguous range per level or
-// segment): covered cells are restored from their children before the next
-// residual, and the levels below the leaves are rebuilt by every cycle.
+// phi64 += e32 (the defect-correction update) on leaf cells (one contiguous
+// range per level or segment) of the segments that k_update_restrict does
+// not cover; covered cells are restored from their children before the
+// next residual, and the levels below the leaves are rebuilt by every
+// cycle.  The widening of e is exact and done with integer operations
+// (mg_from_float; GB300 runs the conversion instruction on its FP64 pipe),
+// leaving one FP64 add per cell.
 constexpr int kMaxLeafRanges = 96;
 struct LeafRanges {
     int n;
@@ -3198,6 +3254,27 @@ __global__ void k_add_e_leaf(LeafRanges R, const float *__restrict__ e, double *
         for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < R.len[r]; i += stride)
             xr[i] += mg_from_float(er[i]);
     }
+}
+// phi += e on the leaf cells of the listed segments (chunks of
+// kMaxLeafRanges ranges per launch; covered cells are never touched)
+static void enqueue_add_leaf(mg_tree *t, const std::vector<int> &segs, const float *e, double *phi) {
+    LeafRanges R;
+    R.n = 0;
+    auto flush = [&]() {
+        if (!R.n) return;
+        ++t->launches;
+        launch_k(k_add_e_leaf, 1216, 256, 0, t->stream, R, e, phi);
+        R.n = 0;
+    };
+    for (int l : segs) {
+        const LevelHost &L = t->lev[l];
+        if (L.nb <= L.nref) continue;
+        if (R.n == kMaxLeafRanges) flush();
+        R.start[R.n] = t->blocks[L.first + L.nref].cell_off;
+        R.len[R.n] = (long long)(L.nb - L.nref) * (t->dim == 2 ? L.n * L.n : L.n * L.n * L.n);
+        R.n++;
+    }
+    flush();
 }
 __global__ void k_cast_f32(const double *__restrict__ a, float *__restrict__ b, long long n) {
     pdl_entry();
@@ -3952,14 +4029,33 @@ template <class T, int D> struct Launch {
     // full: every group, for readers of covered cells other than leaf
     // stencils (the transfer of phi to an adapted mesh copies a coarsened
     // block's covered cells, which may lie below every leaf stencil)
-    static void refresh(mg_tree *t, Fields<T> &F, int homog, int mode = 0, bool full = false) {
+    // e_add (FP64 fields only): the defect-correction update phi += e on
+    // the leaf cells, fused into the restriction of the segments it passes
+    // (k_update_restrict) and done first elsewhere
+    static void refresh(mg_tree *t, Fields<T> &F, int homog, int mode = 0, bool full = false,
+                        const float *e_add = nullptr) {
         const KParams P = kparams(t, homog);
         const int top = (int)t->groups.size() - 1;
         const int gmin = full ? 0 : refresh_gmin(t);
+        std::vector<char> updated(t->lev.size(), 0);
         for (int g = top; g >= 1 && g - 1 >= gmin; g--)
             for (int l : t->groups[g]) {
                 const LevelHost &L = t->lev[l];
                 if (L.coarsest) continue;
+                if constexpr (sizeof(T) == 8) {
+                    if (e_add && L.nb > L.nref) {
+                        updated[l] = 1;
+                        if (L.n >= 4) {
+                            const int C = cells_of<D>(L.n);
+                            ++t->launches;
+                            const int thr = std::max(32, std::min(256, (C / kUpdCells + 31) / 32 * 32));
+                            launch_k(k_update_restrict<D>, L.nb, thr, sizeof(double) * C, t->stream, P, L.first, L.nref, F.X,
+                                     e_add);
+                            continue;
+                        }
+                        enqueue_add_leaf(t, {l}, e_add, F.X);  // before this segment's restriction reads it
+                    }
+                }
                 ++t->launches;
                 if (is_flat(L))
                     launch_k(k_restrict_flat<T, D>, flat_grid(t, (long long)L.nb * cells_of<D>(L.n / 2)), 256, 0, t->stream, P, L.first, L.nb, L.n, F.X, F.XG, F.F, F.E, F.EG, F.F, 0);
@@ -3967,6 +4063,14 @@ template <class T, int D> struct Launch {
                     launch_k(k_restrict<T, D>, L.nb, threads_for(cells_of<D>(L.n / 2)), 0, t->stream, P, L.first, F.X, F.XG,
                                                                                                  F.F, F.E, F.EG, F.F, 0);
             }
+        if constexpr (sizeof(T) == 8) {
+            if (e_add) {  // leaf segments no restriction above passed
+                std::vector<int> rest;
+                for (size_t l = 0; l < t->lev.size(); l++)
+                    if (!updated[l] && t->lev[l].nb > t->lev[l].nref) rest.push_back((int)l);
+                enqueue_add_leaf(t, rest, e_add, F.X);
+            }
+        }
         for (int g = gmin; g <= top; g++)
             for (int l : t->groups[g]) ghost(t, P, l, F.X, F.XG, mode);
     }
@@ -4050,8 +4154,8 @@ template <int D> static size_t resid_smem(int n, const Fields<double> &F) {
 
 template <int D>
 static void residual_norm_d(mg_tree *t, Fields<double> &F, int homog, double *out3, double *r64_leaf,
-                            float *f32_cells, bool want_max = true) {
-    Launch<double, D>::refresh(t, F, homog);
+                            float *f32_cells, bool want_max = true, const float *e_add = nullptr) {
+    Launch<double, D>::refresh(t, F, homog, 0, false, e_add);
     const KParams P = kparams(t, homog);
     int slot = 0;
     long long leaf_base = 0;
@@ -4086,15 +4190,17 @@ static void residual_norm_d(mg_tree *t, Fields<double> &F, int homog, double *ou
 
 // enqueue only (no synchronisation: usable inside a stream capture); the
 // reduced values land in the pinned t->h_red
-void residual_enqueue(mg_tree *t, Fields<double> &F, int homog, double *r64_leaf, float *f32_cells, bool want_max) {
-    if (t->dim == 2) residual_norm_d<2>(t, F, homog, nullptr, r64_leaf, f32_cells, want_max);
-    else residual_norm_d<3>(t, F, homog, nullptr, r64_leaf, f32_cells, want_max);
+void residual_enqueue(mg_tree *t, Fields<double> &F, int homog, double *r64_leaf, float *f32_cells, bool want_max,
+                      const float *e_add) {
+    if (t->dim == 2) residual_norm_d<2>(t, F, homog, nullptr, r64_leaf, f32_cells, want_max, e_add);
+    else residual_norm_d<3>(t, F, homog, nullptr, r64_leaf, f32_cells, want_max, e_add);
 }
 
 // Batch: composite residual with one partial per leaf block, reduced per
 // tree into d_tree3 (3 values per tree), copied to the pinned t->h_tree3.
-template <int D> static void residual_trees_d(mg_tree *t, Fields<double> &F, float *f32, bool want_max) {
-    Launch<double, D>::refresh(t, F, 0);
+template <int D> static void residual_trees_d(mg_tree *t, Fields<double> &F, float *f32, bool want_max,
+                                             const float *e_add) {
+    Launch<double, D>::refresh(t, F, 0, 0, false, e_add);
     const KParams P = kparams(t, 0);
     int slot = 0;
     for (size_t l = 0; l < t->lev.size(); l++) {
@@ -4143,9 +4249,9 @@ void leaf_runs_copy(mg_tree *t, double *cells, const double *leaf, bool to_cells
     launch_k(k_runs_copy, t->n_runs, 256, 0, t->stream, t->d_runs, cells, const_cast<double *>(leaf), to_cells ? 1 : 0);
 }
 
-void residual_enqueue_trees(mg_tree *t, Fields<double> &F, float *f32_cells, bool want_max) {
-    if (t->dim == 2) residual_trees_d<2>(t, F, f32_cells, want_max);
-    else residual_trees_d<3>(t, F, f32_cells, want_max);
+void residual_enqueue_trees(mg_tree *t, Fields<double> &F, float *f32_cells, bool want_max, const float *e_add) {
+    if (t->dim == 2) residual_trees_d<2>(t, F, f32_cells, want_max, e_add);
+    else residual_trees_d<3>(t, F, f32_cells, want_max, e_add);
 }
 
 void residual_wait(mg_tree *t, double *out3) {
@@ -4304,23 +4410,6 @@ __global__ void k_sub_scalar(double *__restrict__ x, double c, long long n) {
 void sub_scalar(mg_tree *t, double *x, double c, long long n) {
     ++t->launches;
     launch_k(k_sub_scalar, 1216, 256, 0, t->stream, x, c, n);
-}
-
-void add_e_to_phi(mg_tree *t, const float *e, double *phi) {
-    ++t->launches;
-    LeafRanges R;
-    R.n = 0;
-    for (const LevelHost &L : t->lev) {
-        if (L.nb <= L.nref) continue;
-        if (R.n == kMaxLeafRanges) {  // more leaf ranges than the parameter block holds: every cell
-            launch_k(k_add_e, 1216, 256, 0, t->stream, e, phi, t->ncells);
-            return;
-        }
-        R.start[R.n] = t->blocks[L.first + L.nref].cell_off;
-        R.len[R.n] = (long long)(L.nb - L.nref) * (t->dim == 2 ? L.n * L.n : L.n * L.n * L.n);
-        R.n++;
-    }
-    launch_k(k_add_e_leaf, 1216, 256, 0, t->stream, R, e, phi);
 }
 
 void copy_eps_to_f32(mg_tree *t) {

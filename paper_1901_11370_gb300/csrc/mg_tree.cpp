@@ -1322,8 +1322,7 @@ extern "C" int mg_solve(mg_tree *t, double rel_tol, int max_cycles, int fmg_firs
                 } else {
                     for (int c = 0; c < q.inner_cycles; c++) vcycle<float>(t, t->f32, top, q.n_down, q.n_up, 1);
                 }
-                add_e_to_phi(t, t->f32.X, t->f64.X);
-                residual_enqueue(t, t->f64, 0, nullptr, t->f32.F);
+                residual_enqueue(t, t->f64, 0, nullptr, t->f32.F, false, t->f32.X);  // phi += e, refresh, residual
             });
             if (rc) return rc;
             residual_wait(t, o);
@@ -2038,8 +2037,7 @@ extern "C" int mg_batch_solve(mg_batch *b, double rel_tol, int max_cycles, int f
                 } else {
                     for (int c = 0; c < q.inner_cycles; c++) vcycle<float>(t, t->f32, top, q.n_down, q.n_up, 1);
                 }
-                add_e_to_phi(t, t->f32.X, t->f64.X);
-                residual_enqueue_trees(t, t->f64, t->f32.F, false);
+                residual_enqueue_trees(t, t->f64, t->f32.F, false, t->f32.X);  // phi += e, refresh, residual
             });
             if (rc) return rc;
             cycles++;
