@@ -2363,7 +2363,7 @@ __device__ __noinline__ double resid_const_fp64(double xc, double a0, double a1,
 __device__ __noinline__ double unfix_wide(int64_t S, int emax) { return ldexp((double)S, emax - 1080); }
 
 template <int D, int NT, bool MX = true>
-__global__ void __launch_bounds__(kMaxThreads, 3) k_resid_tma(KParams P, int first, int nblocks, Fields<double> F,
+__global__ void __launch_bounds__(kMaxThreads, NT == 8 ? 4 : 3) k_resid_tma(KParams P, int first, int nblocks, Fields<double> F,
                                                               double *__restrict__ partials,
                                                               double *__restrict__ rleaf, long long leaf_base,
                                                               float *__restrict__ f32, int per_block = 0) {
