@@ -133,13 +133,19 @@ struct LvSkel {
     int nblk[3] = {1, 1, 1};
 };
 
+// Precomputed FP64 operator coefficients per cell (variable eps or the
+// cylindrical form): the 2D face weights, the row diagonal (sum of the
+// weights + lambda) and its reciprocal (the Gauss-Seidel divisor, so that
+// an FP64 sweep multiplies instead of dividing).
+__host__ __device__ constexpr int wstride(int D) { return 2 * D + 2; }
+
 template <class T>
 struct Fields {
     T *X = nullptr, *XG = nullptr;   // solution: interior + ghosts
     T *F = nullptr;                  // right-hand side (interior)
     T *E = nullptr, *EG = nullptr;   // coefficient: interior + ghosts (nullptr: eps = 1)
     T *V = nullptr, *VG = nullptr;   // FAS copy v_old: interior + ghosts
-    T *W = nullptr;                  // face coefficients + diagonal, 2D + 1 per cell ([face][cell] per block)
+    T *W = nullptr;                  // face coefficients, diagonal, 1 / diagonal: wstride(D) per cell ([slot][cell] per block)
     T *J = nullptr;                  // Jacobi scratch (cells), owned by the tree
 };
 

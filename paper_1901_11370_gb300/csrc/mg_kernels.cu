@@ -378,7 +378,9 @@ __global__ void __launch_bounds__(kMaxThreads, (D == 3 && NT == 16) ? 1 : 5) k_s
         bulk_g2s(st + DESC + C, F.XG + go, sizeof(T) * GH, bar);
         bulk_g2s(st + DESC + C + GH, F.F + co, sizeof(T) * C, bar);
         if (wc) {
-            bulk_g2s(st + DESC + 2 * C + GH, F.W + co * (2 * D + 1), sizeof(T) * (2 * D + 1) * C, bar);
+            // face weights, then 1 / diagonal (slot 2D + 1) in the place of the diagonal
+            bulk_g2s(st + DESC + 2 * C + GH, F.W + co * wstride(D), sizeof(T) * 2 * D * C, bar);
+            bulk_g2s(st + DESC + 2 * C + GH + 2 * D * C, F.W + co * wstride(D) + (2 * D + 1) * C, sizeof(T) * C, bar);
         } else if (var) {
             bulk_g2s(st + DESC + 2 * C + GH, F.E + co, sizeof(T) * C, bar);
             bulk_g2s(st + DESC + 3 * C + GH, F.EG + go, sizeof(T) * GH, bar);
@@ -483,12 +485,12 @@ __global__ void __launch_bounds__(kMaxThreads, (D == 3 && NT == 16) ? 1 : 5) k_s
                         w1 * (nbv(xs, gs, i, j, k, 1, 0) + nbv(xs, gs, i, j, k, 1, 1));
                 if (D == 3) num += w2 * (nbv(xs, gs, i, j, k, 2, 0) + nbv(xs, gs, i, j, k, 2, 1));
                 xnew = (num - fs[c]) * inv_den;
-            } else if (wc) {  // same terms and order as below, coefficients read
+            } else if (wc) {  // same terms and order as below, coefficients read, 1 / diagonal precomputed
                 const T *ws = es + c;
                 T num = ws[0] * nbv(xs, gs, i, j, k, 0, 0);
 #pragma unroll
                 for (int f = 1; f < 2 * D; f++) num += ws[f * C] * nbv(xs, gs, i, j, k, f >> 1, f & 1);
-                xnew = qdiv<T>(num - fs[c], ws[2 * D * C]);
+                xnew = (num - fs[c]) * ws[2 * D * C];
             } else {
                 const T ec = var ? es[c] : (T)1;
                 T num = 0, den = 0, ri = 0;
@@ -1308,7 +1310,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_fas_tma(KParams P, int first, i
         bulk_g2s(st + DESC + C, F.XG + go, sizeof(T) * GH, bar);
         bulk_g2s(st + DESC + C + GH, F.F + co, sizeof(T) * C, bar);
         if (wc) {
-            bulk_g2s(st + DESC + 2 * C + GH, F.W + co * (2 * D + 1), sizeof(T) * 2 * D * C, bar);
+            bulk_g2s(st + DESC + 2 * C + GH, F.W + co * wstride(D), sizeof(T) * 2 * D * C, bar);
         } else if (var) {
             bulk_g2s(st + DESC + 2 * C + GH, F.E + co, sizeof(T) * C, bar);
             bulk_g2s(st + DESC + 3 * C + GH, F.EG + go, sizeof(T) * GH, bar);
@@ -1926,7 +1928,7 @@ __global__ void __launch_bounds__(kMaxThreads, 4) k_restrict_tma(KParams P, int 
         bulk_g2s(st + 2 * DESC + C, F.XG + go, sizeof(T) * GH, bar);
         bulk_g2s(st + 2 * DESC + C + GH, F.F + co, sizeof(T) * C, bar);
         if (wc) {
-            bulk_g2s(st + 2 * DESC + 2 * C + GH, F.W + co * (2 * D + 1), sizeof(T) * 2 * D * C, bar);
+            bulk_g2s(st + 2 * DESC + 2 * C + GH, F.W + co * wstride(D), sizeof(T) * 2 * D * C, bar);
         } else if (var) {
             bulk_g2s(st + 2 * DESC + 2 * C + GH, F.E + co, sizeof(T) * C, bar);
             bulk_g2s(st + 2 * DESC + 3 * C + GH, F.EG + go, sizeof(T) * GH, bar);
@@ -2363,7 +2365,7 @@ __device__ __noinline__ double resid_const_fp64(double xc, double a0, double a1,
 __device__ __noinline__ double unfix_wide(int64_t S, int emax) { return ldexp((double)S, emax - 1080); }
 
 template <int D, int NT, bool MX = true>
-__global__ void __launch_bounds__(kMaxThreads, NT == 8 ? 4 : 3) k_resid_tma(KParams P, int first, int nblocks, Fields<double> F,
+__global__ void __launch_bounds__(kMaxThreads, (NT == 8 || D == 2) ? 4 : 3) k_resid_tma(KParams P, int first, int nblocks, Fields<double> F,
                                                               double *__restrict__ partials,
                                                               double *__restrict__ rleaf, long long leaf_base,
                                                               float *__restrict__ f32, int per_block = 0) {
@@ -2402,7 +2404,7 @@ __global__ void __launch_bounds__(kMaxThreads, NT == 8 ? 4 : 3) k_resid_tma(KPar
         bulk_g2s(st + DESC + C, F.XG + go, sizeof(T) * GH, bar);
         bulk_g2s(st + DESC + C + GH, F.F + co, sizeof(T) * C, bar);
         if (wc) {
-            bulk_g2s(st + DESC + 2 * C + GH, F.W + co * (2 * D + 1), sizeof(T) * (2 * D + 1) * C, bar);
+            bulk_g2s(st + DESC + 2 * C + GH, F.W + co * wstride(D), sizeof(T) * (2 * D + 1) * C, bar);
         } else if (var) {
             bulk_g2s(st + DESC + 2 * C + GH, F.E + co, sizeof(T) * C, bar);
             bulk_g2s(st + DESC + 3 * C + GH, F.EG + go, sizeof(T) * GH, bar);
@@ -2513,12 +2515,13 @@ __global__ void __launch_bounds__(kMaxThreads, NT == 8 ? 4 : 3) k_resid_tma(KPar
                                      fs[c], w0, w1, D == 3 ? w2 : 0.0, dg);
                 lap = 0;
             } else if (wc) {
+                // r = f + w_diag x_c - sum_f w_f x_f: 2D + 1 FMAs, the FP64
+                // issue cost of the variable-coefficient residual
                 const double xc = xs[c];
                 const double *ws = es + c;  // coefficients [face][cell], the diagonal last
-                double sx = ws[0] * nbv(xs, gs, i, j, k, 0, 0);
+                r = fma(ws[2 * D * C], xc, fs[c]);
 #pragma unroll
-                for (int f = 1; f < 2 * D; f++) sx = fma(ws[f * C], nbv(xs, gs, i, j, k, f >> 1, f & 1), sx);
-                r = fs[c] - fma(-ws[2 * D * C], xc, sx);
+                for (int f = 0; f < 2 * D; f++) r = fma(-ws[f * C], nbv(xs, gs, i, j, k, f >> 1, f & 1), r);
                 lap = 0;
             } else {
                 const double xc = xs[c];
@@ -2965,7 +2968,7 @@ __device__ __forceinline__ T coarse_resid(const KParams &P, const BlockDesc &b, 
     cell_of(c, n, D, ci, cj, ck);
     const LevelDesc &L = P.L[b.lev];
     if constexpr (sizeof(T) == 8) {
-        const double *wc = W64 ? W64 + b.cell_off * (2 * D + 1) + c : nullptr;
+        const double *wc = W64 ? W64 + b.cell_off * wstride(D) + c : nullptr;
         double acc = 0, wsum = 0;
 #pragma unroll
         for (int d = 0; d < D; d++)
@@ -3305,7 +3308,7 @@ __global__ void __launch_bounds__(256) k_face_coef(KParams P, int first, int nbl
         const double ec = E ? E[b.cell_off + c] : 1.0;
         double ri = 0;
         if (cyl) ri = P.lo[0] + (b.ijk[0] * n + i + 0.5) * L.h[0];
-        double *w_out = W + b.cell_off * (2 * D + 1) + c;
+        double *w_out = W + b.cell_off * wstride(D) + c;
         double wsum = 0;
 #pragma unroll
         for (int d = 0; d < D; d++)
@@ -3323,6 +3326,7 @@ __global__ void __launch_bounds__(256) k_face_coef(KParams P, int first, int nbl
                 wsum += w;
             }
         w_out[2 * D * C] = wsum + P.helm;  // diagonal of the row
+        w_out[(2 * D + 1) * C] = 1.0 / (wsum + P.helm);  // its reciprocal
     }
 }
 

@@ -850,7 +850,7 @@ extern "C" int mg_tree_finalize(mg_tree *t, void *stream) {
     t->finalized = true;
     if ((rc = build_coarse_inverse(t))) return rc;
     if (t->geom == MG_CYL) {  // r-face factors: precomputed FP64 face coefficients
-        if ((rc = dalloc(&t->d_wface, t->ncells * (2 * t->dim + 1)))) return rc;
+        if ((rc = dalloc(&t->d_wface, t->ncells * wstride(t->dim)))) return rc;
         t->f64.W = t->d_wface;
         face_coef(t);
     }
@@ -1122,7 +1122,7 @@ extern "C" int mg_set_eps(mg_tree *t, const double *e) {
     t->var_eps = true;
     if ((rc = leaf_copy(t, t->f64.E, e, true))) return rc;
     refresh_eps<double>(t, t->f64);
-    if ((rc = dalloc(&t->d_wface, t->ncells * (2 * t->dim + 1)))) return rc;
+    if ((rc = dalloc(&t->d_wface, t->ncells * wstride(t->dim)))) return rc;
     t->f64.W = t->d_wface;  // precomputed FP64 face coefficients for the residual
     face_coef(t);
     t->adj.E = t->f64.E;
