@@ -203,21 +203,32 @@ def run_reference(args):
     print(json.dumps(out))
 
 
-def solve_alg_bytes(levels, n_leaf, cycles, precision, dim=3):
+def solve_alg_bytes(levels, n_leaf, cycles, precision, dim=3, down=None, up=None, inner=1):
     """Algorithmic HBM bytes of one solve by the per-cell minimum traffic of
-    a V(2,2) cycle (each sweep reads x and f once and writes x once; the
-    transfers read and write each level once; constant coefficient):
-    FP64 cycles 136 B per cell of every level (3D) plus the composite
-    residual (read phi, f: 16 B per leaf); FP32 cycles in FP64 defect
-    correction 68 B per level cell (4 sweeps x 12 + residual/restriction 8 +
-    prolongation 8 + coarse terms 4) plus, per leaf, the FP64 residual (read
-    phi and f, write the FP32 defect: 20 B) and update (read e, phi, write
-    phi: 20 B).  FMG counts as one cycle."""
-    level_cells = sum(l["nb"] * l["n"] ** dim for l in levels)
-    if precision == "fp64":
-        per = (136 if dim == 3 else 144) * level_cells + 16 * n_leaf
-    else:
-        per = (68 if dim == 3 else 72) * level_cells + 40 * n_leaf
+    its cycles (each sweep reads x and f once and writes x once; the
+    transfers read and write each level once; constant coefficient), for
+    the schedule the solve ran (down[l] + up[l] sweeps on level l, -1 or
+    None meaning 2; `inner` V-cycles per outer step): per level cell and
+    cycle, FP32 cycles 12 B per sweep + 20 B (3D; 24 in 2D) for the
+    residual, restriction, prolongation and coarse terms, FP64 cycles 24 B
+    per sweep + 40 B (48 in 2D) -- 68 and 136 B at V(2,2) in 3D.  Per outer
+    step and leaf, FP32 cycles in FP64 defect correction add the FP64
+    residual (read phi and f, write the FP32 defect: 20 B) and the update
+    (read e, phi, write phi: 20 B); FP64 solves the composite residual (read
+    phi, f: 16 B).  The coarsest level is solved directly (no sweeps).  FMG
+    counts as one outer step."""
+    def steps(a, l):
+        return 2 if a is None or l >= len(a) or a[l] < 0 else int(a[l])
+    per_cycle, level_cells = 0, 0
+    for l, L in enumerate(levels):
+        cells = L["nb"] * L["n"] ** dim
+        level_cells += cells
+        sw = 0 if l == 0 else steps(down, l) + steps(up, l)
+        if precision == "fp64":
+            per_cycle += cells * (24 * sw + (40 if dim == 3 else 48))
+        else:
+            per_cycle += cells * (12 * sw + (20 if dim == 3 else 24))
+    per = inner * per_cycle + (16 if precision == "fp64" else 40) * n_leaf
     return cycles * per, level_cells
 
 
@@ -256,9 +267,21 @@ def run_ours(args):
     zeros = torch.zeros(n, dtype=torch.float64, device="cuda")
     stream = torch.cuda.current_stream()
 
+    # sweeps per level and inner cycles per outer step: the schedule
+    # autotuner (mg_tune_schedule), once per precision, untimed like the
+    # sweep-kernel autotuner; each precision is timed with its own choice
+    sched = {}
+    for prec in (mg.MG_FP32_DC, mg.MG_FP64):
+        tree.set_schedule()
+        inner, _ = tree.tune_schedule(TOL, MAX_CYCLES, prec)
+        d, u = tree.schedule()
+        sched[prec] = (d.copy(), u.copy(), inner)
+
     def solve(prec):
+        d, u, inner = sched[prec]
+        tree.set_schedule(d, u)
         tree.set_phi(zeros)
-        return tree.solve(TOL, MAX_CYCLES, fmg_first=True, precision=prec)
+        return tree.solve(TOL, MAX_CYCLES, fmg_first=True, precision=prec, inner_cycles=inner)
 
     def timed(prec, steps):
         barrier()
@@ -312,7 +335,7 @@ def run_ours(args):
         tree.set_rhs(rhs_dev[s])
         used[s].record(stream)
         tree.set_phi(zeros)
-        tree.solve(TOL, MAX_CYCLES, fmg_first=True, precision=mg.MG_FP32_DC)
+        tree.solve(TOL, MAX_CYCLES, fmg_first=True, precision=mg.MG_FP32_DC, inner_cycles=sched[mg.MG_FP32_DC][2])
         stream.wait_event(down[s])
         tree.get_phi(out=phi_dev[s])
         done[s].record(stream)
@@ -329,6 +352,7 @@ def run_ours(args):
             e2e_step(k)
         stream.wait_event(down[(steps - 1) % 2])
 
+    tree.set_schedule(*sched[mg.MG_FP32_DC][:2])
     e2e_run(2)
     torch.cuda.synchronize()
     barrier()
@@ -362,8 +386,10 @@ def run_ours(args):
     if traffic is not None:
         traffic *= lev_cells
     levels = tree.levels()
-    sb32, level_cells = solve_alg_bytes(levels, n, cyc_mixed, "fp32_dc")
-    sb64, _ = solve_alg_bytes(levels, n, cyc64, "fp64")
+    sb32, level_cells = solve_alg_bytes(levels, n, cyc_mixed, "fp32_dc", down=sched[mg.MG_FP32_DC][0],
+                                        up=sched[mg.MG_FP32_DC][1], inner=sched[mg.MG_FP32_DC][2])
+    sb64, _ = solve_alg_bytes(levels, n, cyc64, "fp64", down=sched[mg.MG_FP64][0], up=sched[mg.MG_FP64][1],
+                              inner=sched[mg.MG_FP64][2])
 
     total_unknowns = n * world
     value = total_unknowns / (ms_mixed * 1e-3)
@@ -372,7 +398,12 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": ms_mixed, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "unknowns": n, "global_batch": world, "precision":
-                   "FP32 red-black GS V(2,2) cycles inside FP64 defect correction, FP64 coarsest solve",
+                   "FP32 red-black GS cycles inside FP64 defect correction, FP64 coarsest solve",
+                   "schedule": {name: {"down": [int(v) for v in sched[prec][0]], "up": [int(v) for v in sched[prec][1]],
+                                       "inner_cycles": int(sched[prec][2])}
+                                for name, prec in (("fp32_dc", mg.MG_FP32_DC), ("fp64", mg.MG_FP64))},
+                   "schedule_from": "mg_tune_schedule (sweeps per level and inner cycles, timed solves to 1e-10; "
+                                    "level 0 is solved directly)",
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "l2": "inputs larger than L2: working set ~%.1f GB (FP64 + FP32 fields) vs 129 MB L2, "
                          "no flush" % (n * 60 / 1e9),
@@ -561,9 +592,11 @@ def batch_measure(args, mg, W, barrier, max_over_ranks):
     zeros = torch.zeros(b.n_leaf, dtype=torch.float64, device="cuda")
     stream = torch.cuda.current_stream()
 
+    inner = {}
+
     def solve(prec):
         b.set_phi(zeros)
-        return b.solve(TOL, MAX_CYCLES, fmg_first=True, precision=prec)
+        return b.solve(TOL, MAX_CYCLES, fmg_first=True, precision=prec, inner_cycles=inner[prec])
 
     total = b.n_leaf
     if world > 1:
@@ -577,6 +610,9 @@ def batch_measure(args, mg, W, barrier, max_over_ranks):
            "%d ranks, trees split by unknowns, no data exchange while solving" % world}
     steps = max(1, min(args.steps, 3))
     for name, prec in (("fp32_dc", mg.MG_FP32_DC), ("fp64", mg.MG_FP64)):
+        # sweeps per segment and inner cycles: the batch schedule autotuner,
+        # untimed, right before this precision is timed
+        inner[prec], _ = b.tune_schedule(TOL, MAX_CYCLES, prec)
         solve(prec)
         barrier()
         l0 = b.launch_count()
@@ -592,6 +628,7 @@ def batch_measure(args, mg, W, barrier, max_over_ranks):
             rels = gather_tree_values(rels, mine, 512)
             cyc = int(max_over_ranks(float(cyc)))
         out[name] = {"value": total / (ms * 1e-3), "unit": "unknowns/s", "ms_per_step": ms, "cycles_to_tol": cyc,
+                     "inner_cycles": inner[prec],
                      "max_final_rel_residual": float(max(rels)), "gpu_launches_per_step": (b.launch_count() - l0) / steps}
     out["fp32_dc_over_fp64"] = out["fp32_dc"]["value"] / out["fp64"]["value"]
     (ms_s, _, b_s, _), seg = b.time_sweeps(n_sweeps=8, precision=mg.MG_FP32_DC)

@@ -343,9 +343,10 @@ int mg_get_schedule(mg_tree *t, int n, int *host_down, int *host_up);
  * of the tree's current problem (phi = 0, FMG first, mg_solve to rel_tol in
  * `precision`) for candidate schedules -- (n_down, n_up) in {1, 2, 3} set
  * separately for the levels holding leaves and for the coarser levels, and
- * for MG_FP32_DC one or two inner cycles per outer step -- each run three
+ * for MG_FP32_DC one to three inner cycles per outer step -- each run three
  * times (the first captures the graphs), and keeps the fastest candidate
- * that converges (mg_set_schedule).  *inner_cycles_out receives its inner
+ * that converges (mg_set_schedule).  A batch pool gives MG_ERR_ARG (use
+ * mg_batch_tune_schedule).  *inner_cycles_out receives its inner
  * cycle count (pass it in mg_params.inner_cycles), *ms_out its solve time.
  * phi is restored afterwards.  MG_ERR_NOT_CONVERGED when no candidate
  * reaches rel_tol within max_cycles.  The paper has no counterpart (it
@@ -482,6 +483,12 @@ int mg_batch_launch_count(mg_batch *b, int64_t *n);
 int mg_batch_num_segments(mg_batch *b, int *nseg, int *ngroups);
 int mg_batch_segment_info(mg_batch *b, int seg, int32_t host_info[6]);
 int mg_batch_time_sweeps(mg_batch *b, int segment, int n_sweeps, int precision, double host_out[4]);
+/* mg_batch_tune_schedule -- mg_tune_schedule for a batch: the candidates
+ * are timed as mg_batch_solve runs (every tree to rel_tol) and the chosen
+ * schedule applies to the batch's segments (leaf segments and those above
+ * the lowest one take the leaf sweeps). */
+int mg_batch_tune_schedule(mg_batch *b, double rel_tol, int max_cycles, int precision, int *inner_cycles_out,
+                           double *ms_out);
 /* mg_batch_coarse_info -- the coarsest-level solves: host_out = {trees
  * solved by a dense inverse, trees solved in block-tridiagonal form, bytes
  * of the dense inverses, bytes of the block-tridiagonal plane records}. */

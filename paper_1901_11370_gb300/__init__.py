@@ -432,6 +432,14 @@ class Batch:
                             coarsest=bool(info[4]), parent_same_n=bool(info[5])))
         return out
 
+    def tune_schedule(self, rel_tol=1e-10, max_cycles=60, precision=MG_FP32_DC):
+        """Autotune the sweeps per segment and the inner cycles by timed batch
+        solves (mg_batch_tune_schedule); returns (inner_cycles, ms per solve)."""
+        inner, ms = C.c_int(), C.c_double()
+        check(self.L.mg_batch_tune_schedule(self._h, float(rel_tol), int(max_cycles), int(precision),
+                                            C.byref(inner), C.byref(ms)))
+        return inner.value, ms.value
+
     def coarse_info(self):
         """Coarsest-level solves: trees with a dense inverse, trees in
         block-tridiagonal form, and the bytes each form stores."""

@@ -29,7 +29,7 @@ EXPORTS = ["mg_tree_create", "mg_tree_refine", "mg_tree_build_on", "mg_tree_buil
            "mg_batch_create", "mg_batch_leaf_offsets", "mg_batch_set_rhs", "mg_batch_set_eps",
            "mg_batch_set_phi", "mg_batch_get_phi", "mg_batch_vcycle", "mg_batch_fmg", "mg_batch_residual_norms",
            "mg_batch_solve", "mg_batch_launch_count", "mg_batch_num_segments", "mg_batch_segment_info",
-           "mg_batch_time_sweeps", "mg_batch_coarse_info", "mg_batch_destroy"]
+           "mg_batch_time_sweeps", "mg_batch_coarse_info", "mg_batch_tune_schedule", "mg_batch_destroy"]
 
 
 class MGError(RuntimeError):
@@ -111,6 +111,7 @@ def load():
     L.mg_batch_segment_info.argtypes = [vp, C.c_int, vp]
     L.mg_batch_time_sweeps.argtypes = [vp, C.c_int, C.c_int, C.c_int, dp]
     L.mg_batch_coarse_info.argtypes = [vp, vp]
+    L.mg_batch_tune_schedule.argtypes = [vp, C.c_double, C.c_int, C.c_int, ip, dp]
     L.mg_batch_destroy.argtypes = [vp]
     L.mg_last_error.restype = C.c_char_p
     _lib = L

@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <array>
 #include <chrono>
+#include <functional>
 #include <unordered_map>
 #include <atomic>
 #include <thread>
@@ -1468,12 +1469,14 @@ extern "C" int mg_get_schedule(mg_tree *t, int n, int *down, int *up) {
     return MG_OK;
 }
 
-// mg_tune_schedule: time full solves of the tree's current problem for a
-// set of candidate schedules and keep the fastest that converges.
-extern "C" int mg_tune_schedule(mg_tree *t, double rel_tol, int max_cycles, int precision, int *inner_out,
-                                double *ms_out) {
-    NEED_FINAL(t);
-    if (t->is_batch) return fail(MG_ERR_UNSUPPORTED, "schedule tuning works on one tree");
+// Schedule autotuner: time full solves of the current problem (one tree,
+// or the pool of a batch through its own solve) for a set of candidate
+// schedules and keep the fastest that converges.  Levels (segments) from
+// the lowest one holding leaves upwards take the candidate's leaf sweeps,
+// those below its coarse sweeps.
+using SolveFn = std::function<int(const mg_params *, int *, double *)>;
+static int tune_schedule_impl(mg_tree *t, double rel_tol, int max_cycles, int precision, int *inner_out,
+                              double *ms_out, const SolveFn &solve) {
     if (!(rel_tol > 0) || max_cycles < 1) return fail(MG_ERR_ARG, "rel_tol > 0 and max_cycles >= 1 required");
     if (precision != MG_FP64 && precision != MG_FP32_DC) return fail(MG_ERR_ARG, "unknown precision");
     const int nl = (int)t->lev.size();
@@ -1483,7 +1486,10 @@ extern "C" int mg_tune_schedule(mg_tree *t, double rel_tol, int max_cycles, int 
     struct Cand { int dl, ul, dc, uc, inner; };
     std::vector<Cand> cands = {{2, 2, 2, 2, 1}, {1, 1, 1, 1, 1}, {1, 2, 1, 2, 1}, {2, 1, 2, 1, 1}, {3, 3, 3, 3, 1},
                                {1, 1, 2, 2, 1}, {2, 2, 1, 1, 1}, {1, 1, 3, 3, 1}, {1, 2, 2, 2, 1}};
-    if (precision == MG_FP32_DC) cands.push_back({2, 2, 2, 2, 2});
+    if (precision == MG_FP32_DC)  // more FP32 cycles per FP64 residual and update
+        for (const Cand &c : {Cand{2, 2, 2, 2, 2}, Cand{1, 2, 1, 2, 2}, Cand{2, 1, 2, 1, 2}, Cand{1, 1, 1, 1, 2},
+                              Cand{2, 2, 2, 2, 3}})
+            cands.push_back(c);
     // save phi (cells and ghosts) to restore it afterwards
     double *save = nullptr;
     CK(cudaMalloc((void **)&save, sizeof(double) * (size_t)(t->ncells + t->nghost)));
@@ -1514,7 +1520,7 @@ extern "C" int mg_tune_schedule(mg_tree *t, double rel_tol, int max_cycles, int 
             cudaEventRecord(e0, t->stream);
             int cyc = 0;
             double rel = 0;
-            const int r = mg_solve(t, rel_tol, max_cycles, 1, &q, &cyc, &rel);
+            const int r = solve(&q, &cyc, &rel);
             cudaEventRecord(e1, t->stream);
             cudaEventSynchronize(e1);
             if (r == MG_ERR_NOT_CONVERGED || r == MG_ERR_NAN) ok = false;
@@ -1553,6 +1559,16 @@ extern "C" int mg_tune_schedule(mg_tree *t, double rel_tol, int max_cycles, int 
     if (inner_out) *inner_out = c.inner;
     if (ms_out) *ms_out = best;
     return MG_OK;
+}
+
+extern "C" int mg_tune_schedule(mg_tree *t, double rel_tol, int max_cycles, int precision, int *inner_out,
+                                double *ms_out) {
+    NEED_FINAL(t);
+    if (t->is_batch) return fail(MG_ERR_ARG, "a batch pool: use mg_batch_tune_schedule");
+    return tune_schedule_impl(t, rel_tol, max_cycles, precision, inner_out, ms_out,
+                              [&](const mg_params *q, int *cyc, double *rel) {
+                                  return mg_solve(t, rel_tol, max_cycles, 1, q, cyc, rel);
+                              });
 }
 
 extern "C" int mg_set_wait_limit(mg_tree *t, int64_t polls) {
@@ -2054,6 +2070,18 @@ extern "C" int mg_batch_solve(mg_batch *b, double rel_tol, int max_cycles, int f
     if (!std::isfinite(worst)) return fail(MG_ERR_NAN, "residual is not finite");
     if (worst > rel_tol) return fail(MG_ERR_NOT_CONVERGED, "max_cycles reached");
     return MG_OK;
+}
+
+extern "C" int mg_batch_tune_schedule(mg_batch *b, double rel_tol, int max_cycles, int precision, int *inner_out,
+                                      double *ms_out) {
+    NEED_BATCH(b);
+    std::vector<double> rel(b->ntrees);
+    return tune_schedule_impl(b->pool, rel_tol, max_cycles, precision, inner_out, ms_out,
+                              [&](const mg_params *q, int *cyc, double *worst) {
+                                  const int r = mg_batch_solve(b, rel_tol, max_cycles, 1, q, cyc, rel.data());
+                                  *worst = rel.empty() ? 0.0 : *std::max_element(rel.begin(), rel.end());
+                                  return r;
+                              });
 }
 
 extern "C" int mg_batch_launch_count(mg_batch *b, int64_t *n) {

@@ -47,10 +47,15 @@ def test_benchmark_workloads_have_their_stated_sizes():
 
 def test_solve_algorithmic_bytes():
     """Per-solve algorithmic bytes: per level cell 136 B (FP64 V(2,2), 3D) or
-    68 B (FP32 cycle), per leaf 16 B (FP64 composite residual) or 40 B (FP64
-    residual and update of the defect correction), times the cycles."""
+    68 B (FP32 cycle) -- 24 or 12 B per sweep plus 40 or 20 B of transfers;
+    the directly solved coarsest level has no sweeps -- per leaf 16 B (FP64
+    composite residual) or 40 B (FP64 residual and update of the defect
+    correction), times the outer steps; a schedule changes the sweeps per
+    level and inner cycles repeat the cycle part."""
     lv = [{"nb": 1, "n": 8}, {"nb": 8, "n": 8}]
     b64, cells = bench.solve_alg_bytes(lv, 4096, 3, "fp64")
-    assert cells == 4608 and b64 == 3 * (136 * 4608 + 16 * 4096)
+    assert cells == 4608 and b64 == 3 * (40 * 512 + 136 * 4096 + 16 * 4096)
     b32, _ = bench.solve_alg_bytes(lv, 4096, 3, "fp32_dc")
-    assert b32 == 3 * (68 * 4608 + 40 * 4096)
+    assert b32 == 3 * (20 * 512 + 68 * 4096 + 40 * 4096)
+    b32s, _ = bench.solve_alg_bytes(lv, 4096, 3, "fp32_dc", down=[-1, 1], up=[-1, 2], inner=2)
+    assert b32s == 3 * (2 * (20 * 512 + 56 * 4096) + 40 * 4096)

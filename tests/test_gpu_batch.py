@@ -277,3 +277,26 @@ def test_batch_block_coarse_solve_matches_dense(mg):
         one.vcycle(2)
         s = slice(b.offsets[i], b.offsets[i + 1])
         assert rel_diff(phi[s], one.get_phi().cpu().numpy()) < TOL, p.name
+
+
+def test_batch_schedule_tuner(mg):
+    """The batch schedule autotuner keeps a schedule with which every tree
+    reaches the tolerance; the tuned solve's phi passes the oracle's
+    residual check, and phi is left as it was."""
+    import torch
+    probs = FORESTS["cyl"]
+    b = make_batch(mg, probs)
+    x = torch.from_numpy(np.random.default_rng(3).standard_normal(b.n_leaf)).cuda()
+    b.set_phi(x)
+    inner, ms = b.tune_schedule(1e-9, 60, mg.MG_FP32_DC)
+    assert inner in (1, 2, 3) and ms > 0
+    assert torch.equal(b.get_phi(), x)
+    b.set_phi(torch.zeros_like(x))
+    cyc, rel = b.solve(1e-9, 60, precision=mg.MG_FP32_DC, inner_cycles=inner)
+    assert (rel <= 1e-9).all()
+    phi = b.get_phi().cpu().numpy()
+    for i, p in enumerate(probs):
+        o = Oracle.from_problem(p)
+        r0, _ = o.residual_norm()
+        o.set_phi(phi[b.offsets[i]:b.offsets[i + 1]])
+        assert o.residual_norm()[0] <= 1.05e-9 * r0, p.name
