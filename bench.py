@@ -677,7 +677,7 @@ def mesh_measure(mg):
     return out
 
 
-def run_profile(kind, pins=""):
+def run_profile(kind, pins="", inner=1, up=-1):
     """Small fixed launch sequences for ncu captures (not a benchmark):
     sweeps64 -- one red-black sweep (2 smoother + 2 ghost launches) on the
     largest level of the workload; solve32 / solve64 -- one solve after one
@@ -708,7 +708,8 @@ def run_profile(kind, pins=""):
             torch.cuda.synchronize()
             if rep:
                 torch.cuda.nvtx.range_push("measure")
-            tree.solve(TOL, MAX_CYCLES, fmg_first=True, precision=prec)
+            tree.solve(TOL, MAX_CYCLES, fmg_first=True, precision=prec, inner_cycles=inner,
+                       n_up=up if up > 0 else 2)
             torch.cuda.synchronize()
             if rep:
                 torch.cuda.nvtx.range_pop()
@@ -724,7 +725,7 @@ def pin_sweeps(tree, prec, pins):
                                               for l in range(len(tree.levels()))))
 
 
-def run_profile_batch(ntrees=512):
+def run_profile_batch(ntrees=512, inner=1):
     """One mixed-precision solve of the batch (the first `ntrees` trees of
     the 512-tree forest) after a warm-up solve, the second inside the NVTX
     range "measure" (for ncu launch lists and single-kernel captures)."""
@@ -743,7 +744,7 @@ def run_profile_batch(ntrees=512):
         torch.cuda.synchronize()
         if rep:
             torch.cuda.nvtx.range_push("measure")
-        b.solve(TOL, MAX_CYCLES, fmg_first=True, precision=mg.MG_FP32_DC)
+        b.solve(TOL, MAX_CYCLES, fmg_first=True, precision=mg.MG_FP32_DC, inner_cycles=inner)
         torch.cuda.synchronize()
         if rep:
             torch.cuda.nvtx.range_pop()
@@ -766,13 +767,17 @@ def main():
                     help="base grid of the divergence-cleaning workload (0: skip it)")
     ap.add_argument("--profile", choices=["sweeps64", "sweeps32", "solve32", "solve64", "batch32"], default=None)
     ap.add_argument("--trees", type=int, default=512, help="with --profile batch32: trees of the forest to use")
+    ap.add_argument("--inner", type=int, default=1,
+                    help="with --profile solve* / batch32: FP32 cycles per outer step (the tuned schedule's choice)")
+    ap.add_argument("--n-up", type=int, default=-1,
+                    help="with --profile solve*: post-smoothing sweeps (the tuned schedule's choice; default 2)")
     ap.add_argument("--pin-sweeps", default="",
                     help="with --profile sweeps*/solve*: 'level:variant,...' sweep kernels to pin after tuning")
     args = ap.parse_args()
     if args.profile == "batch32":
-        run_profile_batch(args.trees)
+        run_profile_batch(args.trees, args.inner)
     elif args.profile:
-        run_profile(args.profile, args.pin_sweeps)
+        run_profile(args.profile, args.pin_sweeps, args.inner, args.n_up)
     elif args.impl == "reference":
         run_reference(args)
     else:
