@@ -3349,18 +3349,31 @@ void face_coef(mg_tree *t) {
 // of the levels below the base grid) run one thread per work item across
 // all blocks of the segment instead of one CTA per block.  Same arithmetic
 // as the CTA kernels, read straight from global memory.
+// One launch covers several such segments of a group (FlatSegs: per
+// segment its first block, block count, block size and first work item).
 constexpr int kFlatCells = 16;
+constexpr int kMaxFlatSegs = 16;
+struct FlatSegs {
+    int nseg;
+    int first[kMaxFlatSegs], nb[kMaxFlatSegs], n[kMaxFlatSegs];
+    long long off[kMaxFlatSegs + 1];  // work items of segments 0..s-1
+};
+__device__ __forceinline__ int flat_seg(const FlatSegs &S, long long gi) {
+    int s = 0;
+    while (s + 1 < S.nseg && gi >= S.off[s + 1]) s++;
+    return s;
+}
 
 // ghost slot t of every block: as k_ghost
 template <class T, int D>
-__global__ void __launch_bounds__(256) k_ghost_flat(KParams P, int first, int nblocks, int n, T *__restrict__ X,
-                                                    T *__restrict__ XG, int mode) {
+__global__ void __launch_bounds__(256) k_ghost_flat(KParams P, FlatSegs S, T *__restrict__ X, T *__restrict__ XG,
+                                                    int mode) {
     pdl_entry();
-    const int F = face_of<D>(n), G = 2 * D * F;
-    const long long total = (long long)nblocks * G;
-    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
-         idx += (long long)gridDim.x * blockDim.x) {
-        const int g = first + (int)(idx / G), t = (int)(idx % G);
+    for (long long gi = blockIdx.x * (long long)blockDim.x + threadIdx.x; gi < S.off[S.nseg];
+         gi += (long long)gridDim.x * blockDim.x) {
+        const int sg = flat_seg(S, gi), n = S.n[sg], F = face_of<D>(n), G = 2 * D * F;
+        const long long idx = gi - S.off[sg];
+        const int g = S.first[sg] + (int)(idx / G), t = (int)(idx % G);
         const BlockDesc &b = P.B[g];
         const LevelDesc &L = P.L[b.lev];
         const int face = t / F, u = t - face * F, d = face >> 1, s = face & 1;
@@ -3391,13 +3404,14 @@ __global__ void __launch_bounds__(256) k_ghost_flat(KParams P, int first, int nb
 // refinement faces; reads touch only slots of the other colour, as in the
 // CTA sweep)
 template <class T, int D>
-__global__ void __launch_bounds__(256) k_sweep_flat(KParams P, int first, int nblocks, int n, Fields<T> F, int colour) {
+__global__ void __launch_bounds__(256) k_sweep_flat(KParams P, FlatSegs S, Fields<T> F, int colour) {
     pdl_entry();
-    const int C = cells_of<D>(n), Fc = face_of<D>(n), ncol = (n & 1) ? C : C / 2;
-    const long long total = (long long)nblocks * ncol;
-    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
-         idx += (long long)gridDim.x * blockDim.x) {
-        const int g = first + (int)(idx / ncol), qi = (int)(idx % ncol);
+    for (long long gi = blockIdx.x * (long long)blockDim.x + threadIdx.x; gi < S.off[S.nseg];
+         gi += (long long)gridDim.x * blockDim.x) {
+        const int sg = flat_seg(S, gi), n = S.n[sg];
+        const int C = cells_of<D>(n), Fc = face_of<D>(n), ncol = (n & 1) ? C : C / 2;
+        const long long idx = gi - S.off[sg];
+        const int g = S.first[sg] + (int)(idx / ncol), qi = (int)(idx % ncol);
         const BlockDesc &b = P.B[g];
         const LevelDesc &L = P.L[b.lev];
         const int par0 = (b.ijk[0] + b.ijk[1] + b.ijk[2]) * n;
@@ -3434,16 +3448,16 @@ __global__ void __launch_bounds__(256) k_sweep_flat(KParams P, int first, int nb
 // covered cells <- mean of their children, one thread per parent cell
 // (with_res: mean child residual into Fdst); as k_restrict, no ghost push
 template <class T, int D>
-__global__ void __launch_bounds__(256) k_restrict_flat(KParams P, int first, int nblocks, int n, T *__restrict__ X,
+__global__ void __launch_bounds__(256) k_restrict_flat(KParams P, FlatSegs S, T *__restrict__ X,
                                                        const T *__restrict__ XG, const T *__restrict__ Fr,
                                                        const T *__restrict__ E, const T *__restrict__ EG,
                                                        T *__restrict__ Fdst, int with_res) {
     pdl_entry();
-    const int m = n / 2, M = cells_of<D>(m);
-    const long long total = (long long)nblocks * M;
-    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
-         idx += (long long)gridDim.x * blockDim.x) {
-        const int g = first + (int)(idx / M), c = (int)(idx % M);
+    for (long long gi = blockIdx.x * (long long)blockDim.x + threadIdx.x; gi < S.off[S.nseg];
+         gi += (long long)gridDim.x * blockDim.x) {
+        const int sg = flat_seg(S, gi), n = S.n[sg], m = n / 2, M = cells_of<D>(m);
+        const long long idx = gi - S.off[sg];
+        const int g = S.first[sg] + (int)(idx / M), c = (int)(idx % M);
         const BlockDesc &b = P.B[g];
         const LevelDesc &L = P.L[b.lev];
         const BlockDesc &p = P.B[b.parent];
@@ -3470,12 +3484,13 @@ __global__ void __launch_bounds__(256) k_restrict_flat(KParams P, int first, int
 // covered cells: f^H += L^H v^H (Sec. 2.4); vold also keeps v_old = v^H and
 // its ghosts (items past the cells copy the ghost slots)
 template <class T, int D>
-__global__ void __launch_bounds__(256) k_fas_flat(KParams P, int first, int nblocks, int n, Fields<T> F, int vold) {
+__global__ void __launch_bounds__(256) k_fas_flat(KParams P, FlatSegs S, Fields<T> F, int vold) {
     pdl_entry();
-    const int C = cells_of<D>(n), G = 2 * D * face_of<D>(n);
-    const long long ncells = (long long)nblocks * C, total = ncells + (vold ? (long long)nblocks * G : 0);
-    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
-         idx += (long long)gridDim.x * blockDim.x) {
+    for (long long gi = blockIdx.x * (long long)blockDim.x + threadIdx.x; gi < S.off[S.nseg];
+         gi += (long long)gridDim.x * blockDim.x) {
+        const int sg = flat_seg(S, gi), n = S.n[sg], first = S.first[sg];
+        const int C = cells_of<D>(n), G = 2 * D * face_of<D>(n);
+        const long long ncells = (long long)S.nb[sg] * C, idx = gi - S.off[sg];
         if (idx < ncells) {
             const int g = first + (int)(idx / C), c = (int)(idx % C);
             const BlockDesc &b = P.B[g];
@@ -3520,13 +3535,13 @@ __global__ void __launch_bounds__(256) k_jacobi_flat(KParams P, int first, int n
 // coarse-grid correction x^h += P(x^H - x^H_old) (as k_prolong), one
 // thread per fine cell, no ghost push (a ghost fill follows)
 template <class T, int D>
-__global__ void __launch_bounds__(256) k_prolong_flat(KParams P, int first, int nblocks, int n, Fields<T> F) {
+__global__ void __launch_bounds__(256) k_prolong_flat(KParams P, FlatSegs S, Fields<T> F) {
     pdl_entry();
-    const int C = cells_of<D>(n);
-    const long long total = (long long)nblocks * C;
-    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
-         idx += (long long)gridDim.x * blockDim.x) {
-        const int g = first + (int)(idx / C), c = (int)(idx % C);
+    for (long long gi = blockIdx.x * (long long)blockDim.x + threadIdx.x; gi < S.off[S.nseg];
+         gi += (long long)gridDim.x * blockDim.x) {
+        const int sg = flat_seg(S, gi), n = S.n[sg], C = cells_of<D>(n);
+        const long long idx = gi - S.off[sg];
+        const int g = S.first[sg] + (int)(idx / C), c = (int)(idx % C);
         const BlockDesc &b = P.B[g];
         const BlockDesc &p = P.B[b.parent];
         int i, j, k;
@@ -3625,6 +3640,86 @@ template <class T, int D> struct Launch {
     static int flat_grid(mg_tree *t, long long items) {
         return (int)std::max<long long>(1, std::min<long long>((items + 255) / 256, 8LL * t->nsm));
     }
+    // work items per block of the flat kernels
+    enum { FK_GHOST, FK_SWEEP, FK_RESTRICT, FK_FAS_VOLD, FK_PROLONG };
+    static long long flat_items(int kind, int n) {
+        const int C = cells_of<D>(n), G = 2 * D * face_of<D>(n);
+        switch (kind) {
+        case FK_GHOST: return G;
+        case FK_SWEEP: return (n & 1) ? C : C / 2;
+        case FK_RESTRICT: return cells_of<D>(n / 2);
+        case FK_FAS_VOLD: return C + G;
+        default: return C;
+        }
+    }
+    // flat launches over the segments ls (their covered blocks only when
+    // nref_only), at most kMaxFlatSegs segments per launch; launch(S, items)
+    // enqueues one kernel
+    template <class Fn>
+    static void flat_launches(mg_tree *t, const std::vector<int> &ls, int kind, bool nref_only, Fn launch,
+                              int nb_cap = -1) {
+        FlatSegs S;
+        S.nseg = 0;
+        S.off[0] = 0;
+        auto flush = [&]() {
+            if (!S.nseg) return;
+            ++t->launches;
+            launch(S, S.off[S.nseg]);
+            S.nseg = 0;
+        };
+        for (int l : ls) {
+            const LevelHost &L = t->lev[l];
+            int nb = nref_only ? L.nref : L.nb;
+            if (nb_cap >= 0) nb = std::min(nb, nb_cap);
+            if (nb <= 0) continue;
+            if (S.nseg == kMaxFlatSegs) flush();
+            S.first[S.nseg] = L.first;
+            S.nb[S.nseg] = nb;
+            S.n[S.nseg] = L.n;
+            S.off[S.nseg + 1] = S.off[S.nseg] + (long long)nb * flat_items(kind, L.n);
+            S.nseg++;
+        }
+        flush();
+    }
+    // one segment (nb blocks from its first), for the per-segment call sites
+    static FlatSegs one_seg(const LevelHost &L, int nb, int kind) {
+        FlatSegs S;
+        S.nseg = 1;
+        S.first[0] = L.first;
+        S.nb[0] = nb;
+        S.n[0] = L.n;
+        S.off[0] = 0;
+        S.off[1] = (long long)nb * flat_items(kind, L.n);
+        return S;
+    }
+    static void ghost_flat(mg_tree *t, const KParams &P, const std::vector<int> &ls, T *X, T *XG, int mode) {
+        flat_launches(t, ls, FK_GHOST, false, [&](const FlatSegs &S, long long items) {
+            launch_k(k_ghost_flat<T, D>, flat_grid(t, items), 256, 0, t->stream, P, S, X, XG, mode);
+        });
+    }
+    static void sweep_flat(mg_tree *t, const KParams &P, const std::vector<int> &ls, Fields<T> &F, int colour,
+                           int nb_cap = -1) {
+        flat_launches(t, ls, FK_SWEEP, false, [&](const FlatSegs &S, long long items) {
+            launch_k(k_sweep_flat<T, D>, flat_grid(t, items), 256, 0, t->stream, P, S, F, colour);
+        }, nb_cap);
+    }
+    static void restrict_flat(mg_tree *t, const KParams &P, const std::vector<int> &ls, T *X, const T *XG,
+                              const T *Fr, const T *E, const T *EG, T *Fdst, int with_res) {
+        flat_launches(t, ls, FK_RESTRICT, false, [&](const FlatSegs &S, long long items) {
+            launch_k(k_restrict_flat<T, D>, flat_grid(t, items), 256, 0, t->stream, P, S, X, XG, Fr, E, EG, Fdst,
+                     with_res);
+        });
+    }
+    static void fas_flat(mg_tree *t, const KParams &P, const std::vector<int> &ls, Fields<T> &F) {
+        flat_launches(t, ls, FK_FAS_VOLD, true, [&](const FlatSegs &S, long long items) {
+            launch_k(k_fas_flat<T, D>, flat_grid(t, items), 256, 0, t->stream, P, S, F, 1);
+        });
+    }
+    static void prolong_flat(mg_tree *t, const KParams &P, const std::vector<int> &ls, Fields<T> &F) {
+        flat_launches(t, ls, FK_PROLONG, false, [&](const FlatSegs &S, long long items) {
+            launch_k(k_prolong_flat<T, D>, flat_grid(t, items), 256, 0, t->stream, P, S, F);
+        });
+    }
     static void ghost(mg_tree *t, const KParams &P, int l, T *X, T *XG, int mode) {
         const LevelHost &L = t->lev[l];
         if (L.nb == 0) return;
@@ -3641,7 +3736,8 @@ template <class T, int D> struct Launch {
             }
         }
         if (is_flat(L)) {
-            launch_k(k_ghost_flat<T, D>, flat_grid(t, (long long)L.nb * 2 * D * face_of<D>(L.n)), 256, 0, t->stream, P, L.first, L.nb, L.n, X, XG, mode);
+            const FlatSegs S = one_seg(L, L.nb, FK_GHOST);
+            launch_k(k_ghost_flat<T, D>, flat_grid(t, S.off[1]), 256, 0, t->stream, P, S, X, XG, mode);
             return;
         }
         launch_k(k_ghost<T, D>, L.nb, threads_for(2 * D * face_of<D>(L.n)), 0, t->stream, P, L.first, X, XG, mode);
@@ -3737,8 +3833,8 @@ template <class T, int D> struct Launch {
         }
         case 6: {
             const int ncol = (n & 1) ? cells_of<D>(n) : cells_of<D>(n) / 2;
-            launch_k(k_sweep_flat<T, D>, flat_grid(t, (long long)nb * ncol), 256, 0, t->stream, P, L.first, nb, n, F,
-                                                                                          colour);
+            const FlatSegs S = one_seg(L, nb, FK_SWEEP);
+            launch_k(k_sweep_flat<T, D>, flat_grid(t, (long long)nb * ncol), 256, 0, t->stream, P, S, F, colour);
             return;
         }
         default: {
@@ -3834,17 +3930,20 @@ template <class T, int D> struct Launch {
         // parent segments fed by a restriction without ghost push get a
         // ghost fill before their FAS right-hand side
         std::vector<char> plain(t->lev.size(), 0);
+        std::vector<int> flat;  // flat segments: shared launches below
         for (int l : t->groups[g]) {
             const LevelHost &L = t->lev[l];
             if (L.coarsest) continue;
+            if (is_flat(L)) {
+                flat.push_back(l);
+                for (int q : L.parents) plain[q] = 1;
+                continue;
+            }
             ++t->launches;
             const int C8 = cells_of<D>(L.n), GH8 = 2 * D * face_of<D>(L.n);
             const size_t smt = 2 * (2 * (sizeof(BlockDesc) + sizeof(LevelDesc)) +
                                     sizeof(T) * (2 * C8 + GH8 + (F.W ? 2 * D * C8 : (F.E ? C8 + GH8 : 0))));
-            if (is_flat(L)) {
-                launch_k(k_restrict_flat<T, D>, flat_grid(t, (long long)L.nb * cells_of<D>(L.n / 2)), 256, 0, t->stream, P, L.first, L.nb, L.n, F.X, F.XG, F.F, F.E, F.EG, F.F, 1);
-                for (int q : L.parents) plain[q] = 1;
-            } else if (D == 3 && L.n == 8 && L.parent_same_n && !F.W && !F.E && t->geom == MG_CART) {
+            if (D == 3 && L.n == 8 && L.parent_same_n && !F.W && !F.E && t->geom == MG_CART) {
                 const size_t sr = 2 * sizeof(T) * (2 * C8 + GH8) + 4 * (sizeof(BlockDesc) + sizeof(LevelDesc));
                 set_smem(k_restrict_rows<T>, sr);
                 const int grid = std::min(L.nb, resident_ctas(k_restrict_rows<T>, 128, sr) * t->nsm);
@@ -3862,11 +3961,21 @@ template <class T, int D> struct Launch {
                 for (int q : L.parents) plain[q] = 1;
             }
         }
+        if (!flat.empty()) restrict_flat(t, P, flat, F.X, F.XG, F.F, F.E, F.EG, F.F, 1);
+        std::vector<int> flat_ghost, flat_fas;
         for (int c : t->groups[g - 1])
-            if (plain[c]) ghost(t, P, c, F.X, F.XG, 0);
+            if (plain[c]) {
+                if (is_flat(t->lev[c])) flat_ghost.push_back(c);
+                else ghost(t, P, c, F.X, F.XG, 0);
+            }
+        if (!flat_ghost.empty()) ghost_flat(t, P, flat_ghost, F.X, F.XG, 0);
         for (int c : t->groups[g - 1]) {
             const LevelHost &C = t->lev[c];
             if (C.nref <= 0) continue;
+            if (is_flat(C)) {
+                flat_fas.push_back(c);
+                continue;
+            }
             ++t->launches;
             const int Cc = cells_of<D>(C.n), Gc = 2 * D * face_of<D>(C.n);
             const size_t smf = 2 * (sizeof(BlockDesc) + sizeof(LevelDesc) +
@@ -3877,11 +3986,11 @@ template <class T, int D> struct Launch {
                 const int thr = transfer_threads(threads_for(cells_of<D>(C.n)));
                 const int grid = std::min(C.nref, resident_ctas(kern, thr, smf) * t->nsm);
                 launch_k(kern, grid, thr, smf, t->stream, P, C.first, C.nref, F);
-            } else if (is_flat(C))
-                launch_k(k_fas_flat<T, D>, flat_grid(t, (long long)C.nref * (cells_of<D>(C.n) + 2 * D * face_of<D>(C.n))), 256, 0, t->stream, P, C.first, C.nref, C.n, F, 1);
-            else
+            } else {
                 launch_k(k_fas_rhs_vold<T, D>, C.nref, threads_for(cells_of<D>(C.n)), 0, t->stream, P, C.first, F);
+            }
         }
+        if (!flat_fas.empty()) fas_flat(t, P, flat_fas, F);
     }
     static size_t prolong_tma_smem(const LevelHost &L) {
         const int n = L.n, pn = L.parent_same_n ? n : n / 2;
@@ -3916,7 +4025,8 @@ template <class T, int D> struct Launch {
             return;
         }
         if (is_flat(L)) {
-            launch_k(k_prolong_flat<T, D>, flat_grid(t, (long long)L.nb * cells_of<D>(L.n)), 256, 0, t->stream, P, L.first, L.nb, L.n, F);
+            const FlatSegs S = one_seg(L, L.nb, FK_PROLONG);
+            launch_k(k_prolong_flat<T, D>, flat_grid(t, S.off[1]), 256, 0, t->stream, P, S, F);
             ghost(t, P, l, F.X, F.XG, 0);
             return;
         }
@@ -3934,8 +4044,7 @@ template <class T, int D> struct Launch {
             ++t->launches;
             launch_k(k_coarse_gs<T, D>, ntr, 1024, sm, t->stream, P, t->d_tcoarse, top, strict, F,
                      CoarseSmooth{t->coarse_abs, t->coarse_rel, t->coarse_max_it});
-            for (size_t l = 0; l < t->lev.size(); l++)
-                if (t->lev[l].coarsest && t->lev[l].group <= top) ghost(t, P, (int)l, F.X, F.XG, 0);
+            coarse_ghosts(t, P, F, top);
             return;
         }
         if (t->n_coarse_chunks) {  // trees with a dense inverse
@@ -3974,8 +4083,7 @@ template <class T, int D> struct Launch {
                          (const float *)t->d_bt32, (const int *)t->d_btperm, ring, slot);
             }
         }
-        for (size_t l = 0; l < t->lev.size(); l++)
-            if (t->lev[l].coarsest && t->lev[l].group <= top) ghost(t, P, (int)l, F.X, F.XG, 0);
+        coarse_ghosts(t, P, F, top);
     }
     // smoothing steps on level l: the per-level schedule where one is set
     // (mg_set_schedule), else the cycle's n_down / n_up
@@ -3983,20 +4091,53 @@ template <class T, int D> struct Launch {
         const std::vector<int> &s = down ? t->sched_down : t->sched_up;
         return (l < (int)s.size() && s[l] >= 0) ? s[l] : n;
     }
+    // the sweep variant segment l runs (the autotuner's pick, else the default)
+    static int chosen_cand(mg_tree *t, int l, Fields<T> &F) {
+        const int prec = sizeof(T) == 4 ? 1 : 0;
+        int cand = (int)t->sweep_choice[prec].size() > l ? t->sweep_choice[prec][l] : -1;
+        if (cand < 0 || !cand_ok(t, l, F, cand)) cand = default_cand(t, l, F);
+        return cand;
+    }
+    // smoothing of every non-coarsest segment of group g; segments on the
+    // flat sweep with the same step count share each colour launch (the
+    // segments of a group are independent trees' levels)
+    static void smooth_group(mg_tree *t, const KParams &P, int g, Fields<T> &F, int n, bool down) {
+        std::map<int, std::vector<int>> flat;  // step count -> segments
+        const bool jac = t->smoother == MG_SMOOTH_JACOBI && F.J;
+        for (int l : t->groups[g]) {
+            if (t->lev[l].coarsest) continue;
+            const int st = steps(t, l, n, down);
+            if (!jac && chosen_cand(t, l, F) == 6) flat[st].push_back(l);
+            else smooth(t, P, l, F, st);
+        }
+        for (auto &kv : flat)
+            for (int s = 0; s < kv.first; s++)
+                for (int colour = 0; colour < 2; colour++) sweep_flat(t, P, kv.second, F, colour);
+    }
+    // prolongation into every non-coarsest segment of group g (flat
+    // segments in shared launches, then their ghosts)
+    static void prolong_group(mg_tree *t, const KParams &P, int g, Fields<T> &F) {
+        std::vector<int> flat;
+        for (int l : t->groups[g]) {
+            if (t->lev[l].coarsest) continue;
+            if (is_flat(t->lev[l])) flat.push_back(l);
+            else prolong(t, P, l, F);
+        }
+        if (flat.empty()) return;
+        prolong_flat(t, P, flat, F);
+        ghost_flat(t, P, flat, F.X, F.XG, 0);
+    }
     static void vcycle(mg_tree *t, Fields<T> &F, int top, int nd, int nu, int homog, int strict = 0) {
         const KParams P = kparams(t, homog);
         for (int g = top; g >= 1; g--) {
-            for (int l : t->groups[g])
-                if (!t->lev[l].coarsest) smooth(t, P, l, F, steps(t, l, nd, true));
+            smooth_group(t, P, g, F, nd, true);
             restrict_group(t, P, g, F);
         }
         coarse(t, P, F, top, strict);
-        for (int g = 1; g <= top; g++)
-            for (int l : t->groups[g])
-                if (!t->lev[l].coarsest) {
-                    prolong(t, P, l, F);
-                    smooth(t, P, l, F, steps(t, l, nu, false));
-                }
+        for (int g = 1; g <= top; g++) {
+            prolong_group(t, P, g, F);
+            smooth_group(t, P, g, F, nu, false);
+        }
     }
     static void fmg(mg_tree *t, Fields<T> &F, int nd, int nu, int homog) {
         const KParams P = kparams(t, homog);
@@ -4004,10 +4145,20 @@ template <class T, int D> struct Launch {
         for (int g = top; g >= 1; g--) restrict_group(t, P, g, F);
         coarse(t, P, F, top, 0);
         for (int g = 1; g <= top; g++) {
-            for (int l : t->groups[g])
-                if (!t->lev[l].coarsest) prolong(t, P, l, F);
+            prolong_group(t, P, g, F);
             vcycle(t, F, g, nd, nu, homog, 1);
         }
+    }
+    // ghosts of the coarsest segments of groups up to top (after their
+    // solve); flat segments in shared launches
+    static void coarse_ghosts(mg_tree *t, const KParams &P, Fields<T> &F, int top) {
+        std::vector<int> flat;
+        for (size_t l = 0; l < t->lev.size(); l++) {
+            if (!t->lev[l].coarsest || t->lev[l].group > top || t->lev[l].nb == 0) continue;
+            if (is_flat(t->lev[l])) flat.push_back((int)l);
+            else ghost(t, P, (int)l, F.X, F.XG, 0);
+        }
+        if (!flat.empty()) ghost_flat(t, P, flat, F.X, F.XG, 0);
     }
     // covered cells <- mean of children (finest first), then all ghosts
     // Lowest group whose values a leaf stencil can reach: groups with leaves,
@@ -4062,7 +4213,8 @@ template <class T, int D> struct Launch {
                 }
                 ++t->launches;
                 if (is_flat(L))
-                    launch_k(k_restrict_flat<T, D>, flat_grid(t, (long long)L.nb * cells_of<D>(L.n / 2)), 256, 0, t->stream, P, L.first, L.nb, L.n, F.X, F.XG, F.F, F.E, F.EG, F.F, 0);
+                    launch_k(k_restrict_flat<T, D>, flat_grid(t, (long long)L.nb * cells_of<D>(L.n / 2)), 256, 0,
+                             t->stream, P, one_seg(L, L.nb, FK_RESTRICT), F.X, F.XG, F.F, F.E, F.EG, F.F, 0);
                 else
                     launch_k(k_restrict<T, D>, L.nb, threads_for(cells_of<D>(L.n / 2)), 0, t->stream, P, L.first, F.X, F.XG,
                                                                                                  F.F, F.E, F.EG, F.F, 0);
@@ -4087,7 +4239,9 @@ template <class T, int D> struct Launch {
                 if (L.coarsest) continue;
                 ++t->launches;
                 if (is_flat(L))
-                    launch_k(k_restrict_flat<T, D>, flat_grid(t, (long long)L.nb * cells_of<D>(L.n / 2)), 256, 0, t->stream, P, L.first, L.nb, L.n, F.E, F.EG, nullptr, nullptr, nullptr, nullptr, 0);
+                    launch_k(k_restrict_flat<T, D>, flat_grid(t, (long long)L.nb * cells_of<D>(L.n / 2)), 256, 0,
+                             t->stream, P, one_seg(L, L.nb, FK_RESTRICT), F.E, F.EG, nullptr, nullptr, nullptr,
+                             nullptr, 0);
                 else
                     launch_k(k_restrict<T, D>, L.nb, threads_for(cells_of<D>(L.n / 2)), 0, t->stream, P, L.first, F.E, F.EG, nullptr, nullptr, nullptr, nullptr, 0);
             }
