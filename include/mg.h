@@ -75,7 +75,9 @@ enum { MG_SMOOTH_RBGS = 0, MG_SMOOTH_JACOBI = 1 };
  * V-cycles per outer FP64 residual.  smoother MG_SMOOTH_RBGS or
  * MG_SMOOTH_JACOBI; omega the Jacobi weight (<= 0: 4/5 in 2D, 6/7 in 3D;
  * at most 1).  coarse_mode MG_COARSE_EXACT solves the coarsest level
- * exactly (dense FP64 inverse); MG_COARSE_SMOOTH is the paper's coarse-grid
+ * exactly (a dense FP64 inverse; in a batch, the block-tridiagonal form
+ * described at mg_batch_create, FP32 inside FP32 cycles); MG_COARSE_SMOOTH
+ * is the paper's coarse-grid
  * solve: red-black Gauss-Seidel sweeps of the coarsest level (FP64) until
  * max |r| there is at most coarse_abs_tol or at most coarse_rel_tol times its
  * value before the first sweep, or coarse_max_it sweeps (values <= 0 take the
@@ -103,7 +105,8 @@ typedef struct {
  * 2D); lo/hi the domain corners; coarse_max_cells: below the base the block
  * count is halved while every count is even, then the block size is halved
  * while a level holds more than this many cells; the last level is solved
- * exactly (dense FP64).  helmholtz: lambda >= 0.  *out receives the handle.
+ * exactly (mg_params.coarse_mode).  helmholtz: lambda >= 0.  *out receives
+ * the handle.
  */
 int mg_tree_create(int dim, int block_size, int geometry, const mg_bc *bc,
                    const int base_cells[3], const double lo[3], const double hi[3],
@@ -432,7 +435,11 @@ int mg_tree_destroy(mg_tree *t);
  * dimension of at least 4 cells, across which a plane holds at most 64
  * cells, is solved by a block-tridiagonal factorisation over those planes
  * (2 nc P values read and FMAs per solve, P cells per plane) instead of
- * the dense inverse (nc^2); both are exact FP64 solves.
+ * the dense inverse (nc^2).  Both are direct solves: in FP64 for FP64
+ * cycles; inside the FP32 cycles of MG_FP32_DC the block form uses its
+ * factors rounded to FP32 (the cycle is FP32 throughout and the outer FP64
+ * defect correction removes its error).  Flat segments (blocks of at most
+ * 16 cells) of a group share one launch per step.
  *
  * mg_batch_create -- merge n trees into a batch with its own device
  *   storage on `stream`.  The trees are read (mesh, refinement, boundary

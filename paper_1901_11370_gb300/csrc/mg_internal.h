@@ -175,7 +175,7 @@ struct mg_tree {
     double lo[3] = {0, 0, 0}, hi[3] = {1, 1, 1};
     double helm = 0.0;
     std::vector<int32_t> refine;  // 4 per entry
-    // wall seconds of the mesh build: host tables, device setup, sweep
+    // wall seconds of the mesh build: mesh tables, device setup, sweep
     // autotuning (FP64, at finalize), phi transfer (a tree made by adapt)
     double build_s[4] = {0, 0, 0, 0};
     bool built = false, finalized = false, singular = false, bc_dirty = false;
