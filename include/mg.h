@@ -397,6 +397,17 @@ int mg_set_wait_limit(mg_tree *t, int64_t polls);
  * half-sweep; this call exists to test and time them one by one. */
 int mg_sweep_variant(mg_tree *t, int precision, int level, int *variant);
 int mg_set_sweep_variant(mg_tree *t, int precision, int level, int variant);
+/* mg_set_tail: an option for the small levels at the bottom of a V-cycle
+ * (Sec. 2.4) -- groups of at most max_cells cells, from the coarsest up,
+ * whose segments have no refinement faces: they run as one cooperative
+ * launch per cycle leg (the downward steps, then after the coarsest solve
+ * the upward steps), with a grid barrier between consecutive steps instead
+ * of a kernel launch each.  max_cells <= 0 turns it off, the default: on
+ * GB300, inside the solve's CUDA graphs, a barrier and a one-thread-per-item
+ * step cost more than the launch they replace.  The result equals the
+ * launch-by-launch cycle up to rounding order.  The damped-Jacobi smoother
+ * always runs launch by launch.  MG_ERR_ARG on a null tree. */
+int mg_set_tail(mg_tree *t, int64_t max_cells);
 int mg_time_sweeps(mg_tree *t, int level, int n_sweeps, int precision, double out[4]);
 
 /*
@@ -490,6 +501,9 @@ int mg_batch_launch_count(mg_batch *b, int64_t *n);
 int mg_batch_num_segments(mg_batch *b, int *nseg, int *ngroups);
 int mg_batch_segment_info(mg_batch *b, int seg, int32_t host_info[6]);
 int mg_batch_time_sweeps(mg_batch *b, int segment, int n_sweeps, int precision, double host_out[4]);
+/* mg_batch_set_tail -- mg_set_tail for the batch's pool (the bound applies
+ * to the cells of a whole group, all trees together). */
+int mg_batch_set_tail(mg_batch *b, int64_t max_cells);
 /* mg_batch_tune_schedule -- mg_tune_schedule for a batch: the candidates
  * are timed as mg_batch_solve runs (every tree to rel_tol) and the chosen
  * schedule applies to the batch's segments (leaf segments and those above

@@ -251,6 +251,11 @@ class Tree:
         check(self.L.mg_launch_count(self._h, C.byref(n)))
         return n.value
 
+    def set_tail(self, max_cells=None):
+        """Cell bound of the V-cycle levels run by the tail kernel
+        (mg_set_tail); None or 0 turns it off (the default)."""
+        check(self.L.mg_set_tail(self._h, 0 if max_cells is None else int(max_cells)))
+
     def set_wait_limit(self, polls=None):
         """Polls of the kernels' bounded waits (mg_set_wait_limit); None
         restores the default, 0 makes every staged kernel give up at once."""
@@ -420,6 +425,11 @@ class Batch:
         n = C.c_int64()
         check(self.L.mg_batch_launch_count(self._h, C.byref(n)))
         return n.value
+
+    def set_tail(self, max_cells=None):
+        """Cell bound of the groups run by the tail kernel (mg_batch_set_tail);
+        None or 0 turns it off (the default)."""
+        check(self.L.mg_batch_set_tail(self._h, 0 if max_cells is None else int(max_cells)))
 
     def segments(self):
         ns, ng = C.c_int(), C.c_int()

@@ -25,11 +25,11 @@ EXPORTS = ["mg_tree_create", "mg_tree_refine", "mg_tree_build_on", "mg_tree_buil
            "mg_clean_adjoint", "mg_set_schedule", "mg_get_schedule", "mg_tune_schedule", "mg_tree_destroy",
            "mg_last_error",
            "mg_launch_count", "mg_set_wait_limit", "mg_time_sweeps", "mg_residual_norm_noalloc", "mg_sweep_variant",
-           "mg_divergence", "mg_divergence_order", "mg_project", "mg_clean", "mg_set_sweep_variant",
+           "mg_divergence", "mg_divergence_order", "mg_project", "mg_clean", "mg_set_sweep_variant", "mg_set_tail",
            "mg_batch_create", "mg_batch_leaf_offsets", "mg_batch_set_rhs", "mg_batch_set_eps",
            "mg_batch_set_phi", "mg_batch_get_phi", "mg_batch_vcycle", "mg_batch_fmg", "mg_batch_residual_norms",
            "mg_batch_solve", "mg_batch_launch_count", "mg_batch_num_segments", "mg_batch_segment_info",
-           "mg_batch_time_sweeps", "mg_batch_coarse_info", "mg_batch_tune_schedule", "mg_batch_destroy"]
+           "mg_batch_time_sweeps", "mg_batch_set_tail", "mg_batch_coarse_info", "mg_batch_tune_schedule", "mg_batch_destroy"]
 
 
 class MGError(RuntimeError):
@@ -94,6 +94,8 @@ def load():
     L.mg_residual_norm_noalloc.argtypes = [vp, dp, dp]
     L.mg_sweep_variant.argtypes = [vp, C.c_int, C.c_int, ip]
     L.mg_set_sweep_variant.argtypes = [vp, C.c_int, C.c_int, C.c_int]
+    L.mg_set_tail.argtypes = [vp, C.c_int64]
+    L.mg_batch_set_tail.argtypes = [vp, C.c_int64]
     L.mg_divergence.argtypes = [vp, vp, vp]
     L.mg_divergence_order.argtypes = [vp, vp, vp, C.c_int]
     L.mg_clean.argtypes = [vp, vp, vp, vp, C.c_int, C.c_double, C.c_int, C.POINTER(mg_params), ip, dp]

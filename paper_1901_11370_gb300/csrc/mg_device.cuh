@@ -101,6 +101,28 @@ static void launch_k(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem,
     }
 }
 
+// A cooperative launch (every CTA resident at once, as a grid barrier
+// needs); a refused launch is kept for check_cuda like launch_k's.
+template <class... KArgs, class... Args>
+static void launch_coop(void (*kern)(KArgs...), dim3 grid, dim3 block, cudaStream_t st, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, kern, ((KArgs)args)...);
+    if (e != cudaSuccess) {
+        int none = 0;
+        if (g_launch_error.compare_exchange_strong(none, (int)e))
+            g_launch_fail = {(const void *)kern, grid.x, block.x, 0};
+    }
+}
+
 // Quotient for the operator's coefficients and the Gauss-Seidel update: the
 // FP32 smoother (an inner solver under FP64 defect correction) takes the
 // fast reciprocal-based intrinsic; FP64 keeps the correctly rounded division.

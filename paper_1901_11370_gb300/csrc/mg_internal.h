@@ -15,6 +15,8 @@ namespace mg {
 // polls of a bounded mbarrier wait before a kernel gives up, sets the status
 // word and returns (a few milliseconds)
 constexpr uint32_t kDefaultWaitLimit = 1u << 20;
+// device words per tree: the status word and the tail kernel's grid barrier
+constexpr int kStatusWords = 4;
 
 // Per-block descriptor, one per block of every level (device table).
 // Storage is interior-only, block-major, x fastest; face ghosts live in a
@@ -239,7 +241,8 @@ struct mg_tree {
     double *d_red = nullptr;       // reduced norms (3)
     double *h_red = nullptr;       // pinned host copy
     long long launches = 0;        // kernels launched so far
-    int *d_status = nullptr;       // device status word (0 = ok)
+    int *d_status = nullptr;       // device status word (0 = ok), then the tail kernel's grid-barrier
+                                   // counter and generation (kStatusWords ints, cleared together)
     uint32_t wait_limit = mg::kDefaultWaitLimit;  // bounded-wait polls (mg_set_wait_limit)
     // adjoint (mg_adjoint.cu): adjoint of every pool value (cells, ghosts),
     // lambda, the compatible right-hand side and a leaf-order scratch
@@ -256,6 +259,11 @@ struct mg_tree {
     cudaStream_t cap_stream = nullptr;
     bool use_graphs = true;
     std::vector<int> sweep_choice[2];  // autotuned sweep variant per level (FP64, FP32); -1 default
+    // the tail kernel (mg_kernels.cu): cell bound of the groups it runs
+    // (0: off, the default; mg_set_tail) and the program being recorded (a
+    // Launch<T, D>::TailRec while a cycle records, else null)
+    long long tail_cells = 0;
+    void *tail_rec = nullptr;
     // smoothing steps per level (mg_set_schedule / mg_tune_schedule); an
     // entry < 0, or no entry, takes the cycle's n_down / n_up
     std::vector<int> sched_down, sched_up;

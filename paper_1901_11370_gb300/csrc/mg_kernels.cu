@@ -315,6 +315,35 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
                  "l"(src), "r"(bytes), "r"(smem_u32(bar))
                  : "memory");
 }
+// Right-hand sides of the FP32 cycles are read once per colour launch and
+// are the largest array a sweep streams.  Their lines are marked
+// evict-first in L2, so that on a level whose x, f and ghost slots together
+// just exceed L2 the level's x and ghost slots stay resident between the
+// launches of a smoothing phase instead of being streamed out by f.  FP64
+// fields are left at the default policy.
+__device__ __forceinline__ uint64_t l2_evict_first() {
+    uint64_t pol;
+    asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+template <class T> __device__ __forceinline__ void bulk_g2s_f(void *dst, const T *src, uint32_t bytes, uint64_t *bar) {
+    if constexpr (sizeof(T) == 4) {
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
+                smem_u32(dst)),
+            "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(l2_evict_first())
+            : "memory");
+    } else {
+        bulk_g2s(dst, src, bytes, bar);
+    }
+}
+__device__ __forceinline__ float4 ldg_f_ef(const float4 *p, uint64_t pol) {
+    float4 v;
+    asm("ld.global.nc.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+        : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+        : "l"(p), "l"(pol));
+    return v;
+}
 __device__ __forceinline__ void bulk_s2g(void *dst, const void *src, uint32_t bytes) {
     asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(smem_u32(src)),
                  "r"(bytes)
@@ -376,7 +405,7 @@ __global__ void __launch_bounds__(kMaxThreads, (D == 3 && NT == 16) ? 1 : 5) k_s
         bulk_g2s(reinterpret_cast<char *>(st) + sizeof(BlockDesc), P.L + lev, sizeof(LevelDesc), bar);
         bulk_g2s(st + DESC, F.X + co, sizeof(T) * C, bar);
         bulk_g2s(st + DESC + C, F.XG + go, sizeof(T) * GH, bar);
-        bulk_g2s(st + DESC + C + GH, F.F + co, sizeof(T) * C, bar);
+        bulk_g2s_f<T>(st + DESC + C + GH, F.F + co, sizeof(T) * C, bar);
         if (wc) {
             // face weights, then 1 / diagonal (slot 2D + 1) in the place of the diagonal
             bulk_g2s(st + DESC + 2 * C + GH, F.W + co * wstride(D), sizeof(T) * 2 * D * C, bar);
@@ -581,7 +610,7 @@ __global__ void __launch_bounds__(32 * WARPS) k_sweep_warp(KParams P, int first,
         bulk_g2s(reinterpret_cast<char *>(st) + sizeof(BlockDesc), P.L + P.B[g].lev, sizeof(LevelDesc), bar);
         bulk_g2s(st + DESC, F.X + co, sizeof(T) * C, bar);
         bulk_g2s(st + DESC + C, F.XG + go, sizeof(T) * GH, bar);
-        bulk_g2s(st + DESC + C + GH, F.F + co, sizeof(T) * C, bar);
+        bulk_g2s_f<T>(st + DESC + C + GH, F.F + co, sizeof(T) * C, bar);
         if (var) {
             bulk_g2s(st + DESC + 2 * C + GH, F.E + co, sizeof(T) * C, bar);
             bulk_g2s(st + DESC + 3 * C + GH, F.EG + go, sizeof(T) * GH, bar);
@@ -759,7 +788,7 @@ __global__ void __launch_bounds__(32 * WARPS, WARPS == 8 ? ((FG && STAGES == 2) 
         bulk_g2s(reinterpret_cast<char *>(st) + sizeof(BlockDesc), P.L + lev, sizeof(LevelDesc), bar);
         bulk_g2s(st + DESC, F.X + co, sizeof(T) * C, bar);
         bulk_g2s(st + DESC + C, F.XG + go, sizeof(T) * GH, bar);
-        if (!FG) bulk_g2s(st + DESC + C + GH, F.F + co, sizeof(T) * C, bar);
+        if (!FG) bulk_g2s_f<T>(st + DESC + C + GH, F.F + co, sizeof(T) * C, bar);
     };
     const int stride = gridDim.x * WARPS;
     int g = blockIdx.x * WARPS + warp;
@@ -779,6 +808,7 @@ __global__ void __launch_bounds__(32 * WARPS, WARPS == 8 ? ((FG && STAGES == 2) 
         }
         if (FG && gf < nblocks) fco = P.B[first + gf].cell_off;
     };
+    const uint64_t fpol = l2_evict_first();
     auto loadf = [&](long long cell_off) {  // rows lane and lane + 32 of the block at cell_off
         const T *fp = F.F + cell_off;
 #pragma unroll
@@ -788,7 +818,9 @@ __global__ void __launch_bounds__(32 * WARPS, WARPS == 8 ? ((FG && STAGES == 2) 
             const V *vp = reinterpret_cast<const V *>(fp + 8 * (lane + 32 * h));
 #pragma unroll
             for (int v = 0; v < 8 / VW; v++) {
-                const V x = __ldg(vp + (sizeof(T) == 4 ? (v ^ sw) : v));
+                V x;
+                if constexpr (sizeof(T) == 4) x = ldg_f_ef(vp + (v ^ sw), fpol);
+                else x = __ldg(vp + v);
                 if constexpr (sizeof(T) == 4) {
                     fnx[8 * h + 4 * v] = x.x; fnx[8 * h + 4 * v + 1] = x.y;
                     fnx[8 * h + 4 * v + 2] = x.z; fnx[8 * h + 4 * v + 3] = x.w;
@@ -1926,7 +1958,7 @@ __global__ void __launch_bounds__(kMaxThreads, 4) k_restrict_tma(KParams P, int 
         bulk_g2s(reinterpret_cast<char *>(st + DESC) + sizeof(BlockDesc), P.L + P.B[par].lev, sizeof(LevelDesc), bar);
         bulk_g2s(st + 2 * DESC, F.X + co, sizeof(T) * C, bar);
         bulk_g2s(st + 2 * DESC + C, F.XG + go, sizeof(T) * GH, bar);
-        bulk_g2s(st + 2 * DESC + C + GH, F.F + co, sizeof(T) * C, bar);
+        bulk_g2s_f<T>(st + 2 * DESC + C + GH, F.F + co, sizeof(T) * C, bar);
         if (wc) {
             bulk_g2s(st + 2 * DESC + 2 * C + GH, F.W + co * wstride(D), sizeof(T) * 2 * D * C, bar);
         } else if (var) {
@@ -2102,7 +2134,7 @@ __global__ void __launch_bounds__(128) k_restrict_rows(KParams P, int first, int
         bulk_g2s(reinterpret_cast<char *>(st + DESC) + sizeof(BlockDesc), P.L + r.plev, sizeof(LevelDesc), bar);
         bulk_g2s(st + 2 * DESC, F.X + r.co, sizeof(T) * C, bar);
         bulk_g2s(st + 2 * DESC + C, F.XG + r.go, sizeof(T) * GH, bar);
-        bulk_g2s(st + 2 * DESC + C + GH, F.F + r.co, sizeof(T) * C, bar);
+        bulk_g2s_f<T>(st + 2 * DESC + C + GH, F.F + r.co, sizeof(T) * C, bar);
     };
     int g = blockIdx.x;
     Src n1{}, n2{};
@@ -3364,13 +3396,16 @@ __device__ __forceinline__ int flat_seg(const FlatSegs &S, long long gi) {
     return s;
 }
 
+// Each flat kernel is a grid-stride loop over the work items of its
+// segments; the work of one item is a device function, which the tail
+// kernel (k_tail) runs the same way.  These functions take plain pointers:
+// in the tail kernel the arrays they read are written by its earlier phases.
+
 // ghost slot t of every block: as k_ghost
 template <class T, int D>
-__global__ void __launch_bounds__(256) k_ghost_flat(KParams P, FlatSegs S, T *__restrict__ X, T *__restrict__ XG,
-                                                    int mode) {
-    pdl_entry();
-    for (long long gi = blockIdx.x * (long long)blockDim.x + threadIdx.x; gi < S.off[S.nseg];
-         gi += (long long)gridDim.x * blockDim.x) {
+__device__ __forceinline__ void ghost_flat_item(const KParams &P, const FlatSegs &S, T *X, T *XG, int mode,
+                                                long long gi) {
+    {
         const int sg = flat_seg(S, gi), n = S.n[sg], F = face_of<D>(n), G = 2 * D * F;
         const long long idx = gi - S.off[sg];
         const int g = S.first[sg] + (int)(idx / G), t = (int)(idx % G);
@@ -3398,16 +3433,23 @@ __global__ void __launch_bounds__(256) k_ghost_flat(KParams P, FlatSegs S, T *__
         XG[b.ghost_off + t] = val;
     }
 }
+template <class T, int D>
+__global__ void __launch_bounds__(256) k_ghost_flat(KParams P, FlatSegs S, T *__restrict__ X, T *__restrict__ XG,
+                                                    int mode) {
+    pdl_entry();
+    for (long long gi = blockIdx.x * (long long)blockDim.x + threadIdx.x; gi < S.off[S.nseg];
+         gi += (long long)gridDim.x * blockDim.x)
+        ghost_flat_item<T, D>(P, S, X, XG, mode, gi);
+}
 
 // red-black half-sweep, one thread per cell of the colour, pushing the
 // same-level and physical ghosts fed by its cell (segments without
 // refinement faces; reads touch only slots of the other colour, as in the
 // CTA sweep)
 template <class T, int D>
-__global__ void __launch_bounds__(256) k_sweep_flat(KParams P, FlatSegs S, Fields<T> F, int colour) {
-    pdl_entry();
-    for (long long gi = blockIdx.x * (long long)blockDim.x + threadIdx.x; gi < S.off[S.nseg];
-         gi += (long long)gridDim.x * blockDim.x) {
+__device__ __forceinline__ void sweep_flat_item(const KParams &P, const FlatSegs &S, const Fields<T> &F, int colour,
+                                                long long gi) {
+    {
         const int sg = flat_seg(S, gi), n = S.n[sg];
         const int C = cells_of<D>(n), Fc = face_of<D>(n), ncol = (n & 1) ? C : C / 2;
         const long long idx = gi - S.off[sg];
@@ -3418,7 +3460,7 @@ __global__ void __launch_bounds__(256) k_sweep_flat(KParams P, FlatSegs S, Field
         int i, j, k;
         if (n & 1) {
             i = qi % n; j = (qi / n) % n; k = D == 3 ? qi / (n * n) : 0;
-            if (((par0 + i + j + k) & 1) != colour) continue;
+            if (((par0 + i + j + k) & 1) != colour) return;
         } else {
             const int h = n >> 1, rr = qi / h, m = qi - rr * h;
             j = rr % n;
@@ -3444,17 +3486,21 @@ __global__ void __launch_bounds__(256) k_sweep_flat(KParams P, FlatSegs S, Field
         }
     }
 }
+template <class T, int D>
+__global__ void __launch_bounds__(256) k_sweep_flat(KParams P, FlatSegs S, Fields<T> F, int colour) {
+    pdl_entry();
+    for (long long gi = blockIdx.x * (long long)blockDim.x + threadIdx.x; gi < S.off[S.nseg];
+         gi += (long long)gridDim.x * blockDim.x)
+        sweep_flat_item<T, D>(P, S, F, colour, gi);
+}
 
 // covered cells <- mean of their children, one thread per parent cell
 // (with_res: mean child residual into Fdst); as k_restrict, no ghost push
 template <class T, int D>
-__global__ void __launch_bounds__(256) k_restrict_flat(KParams P, FlatSegs S, T *__restrict__ X,
-                                                       const T *__restrict__ XG, const T *__restrict__ Fr,
-                                                       const T *__restrict__ E, const T *__restrict__ EG,
-                                                       T *__restrict__ Fdst, int with_res) {
-    pdl_entry();
-    for (long long gi = blockIdx.x * (long long)blockDim.x + threadIdx.x; gi < S.off[S.nseg];
-         gi += (long long)gridDim.x * blockDim.x) {
+__device__ __forceinline__ void restrict_flat_item(const KParams &P, const FlatSegs &S, T *X, const T *XG,
+                                                   const T *Fr, const T *E, const T *EG, T *Fdst, int with_res,
+                                                   long long gi) {
+    {
         const int sg = flat_seg(S, gi), n = S.n[sg], m = n / 2, M = cells_of<D>(m);
         const long long idx = gi - S.off[sg];
         const int g = S.first[sg] + (int)(idx / M), c = (int)(idx % M);
@@ -3480,14 +3526,23 @@ __global__ void __launch_bounds__(256) k_restrict_flat(KParams P, FlatSegs S, T 
         if (with_res) Fdst[p.cell_off + pc] = sr * (T)(1.0 / (1 << D));
     }
 }
+template <class T, int D>
+__global__ void __launch_bounds__(256) k_restrict_flat(KParams P, FlatSegs S, T *__restrict__ X,
+                                                       const T *__restrict__ XG, const T *__restrict__ Fr,
+                                                       const T *__restrict__ E, const T *__restrict__ EG,
+                                                       T *__restrict__ Fdst, int with_res) {
+    pdl_entry();
+    for (long long gi = blockIdx.x * (long long)blockDim.x + threadIdx.x; gi < S.off[S.nseg];
+         gi += (long long)gridDim.x * blockDim.x)
+        restrict_flat_item<T, D>(P, S, X, XG, Fr, E, EG, Fdst, with_res, gi);
+}
 
 // covered cells: f^H += L^H v^H (Sec. 2.4); vold also keeps v_old = v^H and
 // its ghosts (items past the cells copy the ghost slots)
 template <class T, int D>
-__global__ void __launch_bounds__(256) k_fas_flat(KParams P, FlatSegs S, Fields<T> F, int vold) {
-    pdl_entry();
-    for (long long gi = blockIdx.x * (long long)blockDim.x + threadIdx.x; gi < S.off[S.nseg];
-         gi += (long long)gridDim.x * blockDim.x) {
+__device__ __forceinline__ void fas_flat_item(const KParams &P, const FlatSegs &S, const Fields<T> &F, int vold,
+                                              long long gi) {
+    {
         const int sg = flat_seg(S, gi), n = S.n[sg], first = S.first[sg];
         const int C = cells_of<D>(n), G = 2 * D * face_of<D>(n);
         const long long ncells = (long long)S.nb[sg] * C, idx = gi - S.off[sg];
@@ -3508,6 +3563,13 @@ __global__ void __launch_bounds__(256) k_fas_flat(KParams P, FlatSegs S, Fields<
             F.VG[o] = F.XG[o];
         }
     }
+}
+template <class T, int D>
+__global__ void __launch_bounds__(256) k_fas_flat(KParams P, FlatSegs S, Fields<T> F, int vold) {
+    pdl_entry();
+    for (long long gi = blockIdx.x * (long long)blockDim.x + threadIdx.x; gi < S.off[S.nseg];
+         gi += (long long)gridDim.x * blockDim.x)
+        fas_flat_item<T, D>(P, S, F, vold, gi);
 }
 
 // One weighted-Jacobi step of a segment (reading R13), one thread per cell:
@@ -3535,10 +3597,9 @@ __global__ void __launch_bounds__(256) k_jacobi_flat(KParams P, int first, int n
 // coarse-grid correction x^h += P(x^H - x^H_old) (as k_prolong), one
 // thread per fine cell, no ghost push (a ghost fill follows)
 template <class T, int D>
-__global__ void __launch_bounds__(256) k_prolong_flat(KParams P, FlatSegs S, Fields<T> F) {
-    pdl_entry();
-    for (long long gi = blockIdx.x * (long long)blockDim.x + threadIdx.x; gi < S.off[S.nseg];
-         gi += (long long)gridDim.x * blockDim.x) {
+__device__ __forceinline__ void prolong_flat_item(const KParams &P, const FlatSegs &S, const Fields<T> &F,
+                                                  long long gi) {
+    {
         const int sg = flat_seg(S, gi), n = S.n[sg], C = cells_of<D>(n);
         const long long idx = gi - S.off[sg];
         const int g = S.first[sg] + (int)(idx / C), c = (int)(idx % C);
@@ -3558,6 +3619,112 @@ __global__ void __launch_bounds__(256) k_prolong_flat(KParams P, FlatSegs S, Fie
         }
         const T val = D == 2 ? ((T)2 * c0 + nbs) / (T)4 : (c0 + nbs) / (T)4;
         F.X[b.cell_off + c] += val;
+    }
+}
+template <class T, int D>
+__global__ void __launch_bounds__(256) k_prolong_flat(KParams P, FlatSegs S, Fields<T> F) {
+    pdl_entry();
+    for (long long gi = blockIdx.x * (long long)blockDim.x + threadIdx.x; gi < S.off[S.nseg];
+         gi += (long long)gridDim.x * blockDim.x)
+        prolong_flat_item<T, D>(P, S, F, gi);
+}
+
+// ------------------------------------------------------ tail kernel ---
+// The small levels at the bottom of a V-cycle (below a cell bound, without
+// refinement faces) are a chain of launches whose work is a few
+// microseconds each.  With a bound set (mg_set_tail; off by default) the
+// cycle steps there (colour sweeps, restriction, parent ghost fills, FAS
+// right-hand sides, prolongation, ghost fills) are recorded as a program of
+// flat phases instead of being launched, and one cooperative launch runs
+// the program: every CTA takes the work items of a phase in grid-stride
+// order, then all CTAs meet at a grid barrier before the next phase.  On
+// GB300, inside the solve's CUDA graphs, a phase plus a barrier costs more
+// than the launch it replaces (the benchmark solve: 11.3 ms without, 11.8
+// ms with only the 8-block level in the tail, 14.1 ms up to 64^3 cells), so
+// the split stays an option.  Phases split only because a launch holds at most
+// kMaxFlatSegs segments need no barrier between them (independent
+// segments).  The barrier's counter and generation live beside the tree's
+// status word; its wait is bounded like every other: on expiry the CTA
+// sets the status word and returns, and the host reports MG_ERR_TIMEOUT
+// and clears the three words.
+enum { TK_GHOST, TK_SWEEP, TK_RESTRICT, TK_FAS, TK_PROLONG };
+constexpr int kTailMaxOps = 40;
+constexpr int kTailThreads = 256;
+struct TailOp {
+    int kind, arg, bar;  // bar: grid barrier after this phase
+    FlatSegs S;
+};
+struct TailProg {
+    int nops;
+    TailOp op[kTailMaxOps];
+};
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_u32(unsigned *p, unsigned v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+// Grid barrier of a cooperative launch (every CTA resident): thread 0 of
+// each CTA arrives on the counter after the CTA's writes; the last arrival
+// resets the counter and advances the generation, the others poll it (at
+// most `limit` polls).  Returns false when the wait gave up.
+__device__ __forceinline__ bool tail_grid_sync(unsigned *cnt, unsigned *gen, uint32_t limit) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        const unsigned g0 = ld_acquire_u32(gen);
+        __threadfence();
+        if (atomicAdd(cnt, 1u) == gridDim.x - 1) {
+            atomicExch(cnt, 0u);
+            __threadfence();
+            st_release_u32(gen, g0 + 1);
+        } else {
+            uint32_t tries = 0;
+            while (ld_acquire_u32(gen) == g0) {
+                if (++tries > limit) { ok = 0; break; }
+                __nanosleep(32);
+            }
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+template <class T, int D>
+__global__ void __launch_bounds__(kTailThreads) k_tail(KParams P, Fields<T> F, const __grid_constant__ TailProg prog) {
+    unsigned *cnt = reinterpret_cast<unsigned *>(P.status + 1), *gen = reinterpret_cast<unsigned *>(P.status + 2);
+    const long long stride = (long long)gridDim.x * blockDim.x, g0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    for (int o = 0; o < prog.nops; o++) {
+        const TailOp &op = prog.op[o];
+        const long long items = op.S.off[op.S.nseg];
+        switch (op.kind) {
+        case TK_GHOST:
+            for (long long gi = g0; gi < items; gi += stride) ghost_flat_item<T, D>(P, op.S, F.X, F.XG, op.arg, gi);
+            break;
+        case TK_SWEEP:
+            for (long long gi = g0; gi < items; gi += stride) sweep_flat_item<T, D>(P, op.S, F, op.arg, gi);
+            break;
+        case TK_RESTRICT:
+            for (long long gi = g0; gi < items; gi += stride)
+                restrict_flat_item<T, D>(P, op.S, F.X, F.XG, F.F, F.E, F.EG, F.F, op.arg, gi);
+            break;
+        case TK_FAS:
+            for (long long gi = g0; gi < items; gi += stride) fas_flat_item<T, D>(P, op.S, F, op.arg, gi);
+            break;
+        default:
+            for (long long gi = g0; gi < items; gi += stride) prolong_flat_item<T, D>(P, op.S, F, gi);
+            break;
+        }
+        if (op.bar && o + 1 < prog.nops && !tail_grid_sync(cnt, gen, P.wait_limit)) {
+            atomicExch(P.status, 1);
+            return;
+        }
     }
 }
 
@@ -3637,6 +3804,84 @@ static int transfer_threads(int want) {
 
 template <class T, int D> struct Launch {
     static bool is_flat(const LevelHost &L) { return cells_of<D>(L.n) <= kFlatCells; }
+    // ---- tail recording (see k_tail).  While a cycle records, the flat
+    // helpers append phases instead of launching, and the group steps take
+    // the flat path on every segment.
+    struct TailRec {
+        std::vector<TailOp> ops;
+        int seq = 0;  // first phase of the flat step being recorded
+        KParams P;
+        Fields<T> F;
+    };
+    static TailRec *rec(mg_tree *t) { return static_cast<TailRec *>(t->tail_rec); }
+    static bool flat_mode(mg_tree *t, const LevelHost &L) { return is_flat(L) || t->tail_rec != nullptr; }
+    static int tail_capacity(mg_tree *t) {
+        static int per = 0;
+        if (!per) {
+            per = 1;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_tail<T, D>, kTailThreads, 0);
+            per = std::max(1, per);
+        }
+        return per * t->nsm;
+    }
+    static void tail_launch(mg_tree *t, TailRec &r) {
+        if (r.ops.empty()) return;
+        static TailProg prog;  // 14 KB: kept off the stack
+        prog.nops = (int)r.ops.size();
+        long long items = 1;
+        for (int o = 0; o < prog.nops; o++) {
+            prog.op[o] = r.ops[o];
+            items = std::max(items, r.ops[o].S.off[r.ops[o].S.nseg]);
+        }
+        // at most two CTAs per SM: fewer arrivals per grid barrier
+        const long long need = (items + kTailThreads - 1) / kTailThreads;
+        const int grid = (int)std::max(1LL, std::min<long long>(need, std::min(tail_capacity(t), 2 * t->nsm)));
+        ++t->launches;
+        launch_coop(k_tail<T, D>, grid, kTailThreads, t->stream, r.P, r.F, prog);
+        r.ops.clear();
+        r.seq = 0;
+    }
+    // a flat step's phase, when recording; false: launch it
+    static bool tail_add(mg_tree *t, int kind, int arg, const FlatSegs &S) {
+        TailRec *r = rec(t);
+        if (!r) return false;
+        if ((int)r->ops.size() == kTailMaxOps) tail_launch(t, *r);
+        if ((int)r->ops.size() > r->seq) r->ops.back().bar = 0;  // same step: independent segments
+        TailOp op;
+        op.kind = kind;
+        op.arg = arg;
+        op.bar = 1;
+        op.S = S;
+        r->ops.push_back(op);
+        return true;
+    }
+    static void tail_begin(mg_tree *t, TailRec &r) { t->tail_rec = &r; }
+    static void tail_end(mg_tree *t, TailRec &r) {
+        if (t->tail_rec != &r) return;
+        t->tail_rec = nullptr;
+        tail_launch(t, r);
+    }
+    // Groups 1..cut of a cycle topped at `top` run in the tail kernel: every
+    // non-coarsest segment of them without refinement faces, each group
+    // holding at most tail_cells cells; red-black smoothing only.
+    static int tail_cut(mg_tree *t, int top) {
+        if (tail_state() != 1 || t->smoother == MG_SMOOTH_JACOBI || t->tail_cells <= 0) return 0;
+        const long long lim = t->tail_cells;
+        int cut = 0;
+        for (int g = 1; g <= top; g++) {
+            long long cells = 0;
+            bool ok = true;
+            for (int l : t->groups[g]) {
+                const LevelHost &L = t->lev[l];
+                if (L.coarsest) continue;
+                if (L.has_cf) ok = false;
+                cells += L.ncells;
+            }
+            if (!ok || cells > lim) break;
+            cut = g;
+        }
+        return cut;
+    }
     static int flat_grid(mg_tree *t, long long items) {
         return (int)std::max<long long>(1, std::min<long long>((items + 255) / 256, 8LL * t->nsm));
     }
@@ -3661,9 +3906,10 @@ template <class T, int D> struct Launch {
         FlatSegs S;
         S.nseg = 0;
         S.off[0] = 0;
+        if (TailRec *r = rec(t)) r->seq = (int)r->ops.size();
         auto flush = [&]() {
             if (!S.nseg) return;
-            ++t->launches;
+            if (!t->tail_rec) ++t->launches;
             launch(S, S.off[S.nseg]);
             S.nseg = 0;
         };
@@ -3694,29 +3940,34 @@ template <class T, int D> struct Launch {
     }
     static void ghost_flat(mg_tree *t, const KParams &P, const std::vector<int> &ls, T *X, T *XG, int mode) {
         flat_launches(t, ls, FK_GHOST, false, [&](const FlatSegs &S, long long items) {
+            if (tail_add(t, TK_GHOST, mode, S)) return;
             launch_k(k_ghost_flat<T, D>, flat_grid(t, items), 256, 0, t->stream, P, S, X, XG, mode);
         });
     }
     static void sweep_flat(mg_tree *t, const KParams &P, const std::vector<int> &ls, Fields<T> &F, int colour,
                            int nb_cap = -1) {
         flat_launches(t, ls, FK_SWEEP, false, [&](const FlatSegs &S, long long items) {
+            if (tail_add(t, TK_SWEEP, colour, S)) return;
             launch_k(k_sweep_flat<T, D>, flat_grid(t, items), 256, 0, t->stream, P, S, F, colour);
         }, nb_cap);
     }
     static void restrict_flat(mg_tree *t, const KParams &P, const std::vector<int> &ls, T *X, const T *XG,
                               const T *Fr, const T *E, const T *EG, T *Fdst, int with_res) {
         flat_launches(t, ls, FK_RESTRICT, false, [&](const FlatSegs &S, long long items) {
+            if (tail_add(t, TK_RESTRICT, with_res, S)) return;  // recorded only with the cycle's own fields
             launch_k(k_restrict_flat<T, D>, flat_grid(t, items), 256, 0, t->stream, P, S, X, XG, Fr, E, EG, Fdst,
                      with_res);
         });
     }
     static void fas_flat(mg_tree *t, const KParams &P, const std::vector<int> &ls, Fields<T> &F) {
         flat_launches(t, ls, FK_FAS_VOLD, true, [&](const FlatSegs &S, long long items) {
+            if (tail_add(t, TK_FAS, 1, S)) return;
             launch_k(k_fas_flat<T, D>, flat_grid(t, items), 256, 0, t->stream, P, S, F, 1);
         });
     }
     static void prolong_flat(mg_tree *t, const KParams &P, const std::vector<int> &ls, Fields<T> &F) {
         flat_launches(t, ls, FK_PROLONG, false, [&](const FlatSegs &S, long long items) {
+            if (tail_add(t, TK_PROLONG, 0, S)) return;
             launch_k(k_prolong_flat<T, D>, flat_grid(t, items), 256, 0, t->stream, P, S, F);
         });
     }
@@ -3856,9 +4107,53 @@ template <class T, int D> struct Launch {
     // Autotuner: per level, time every applicable sweep variant on the
     // given fields (all zero at the call sites, so sweeps leave them
     // unchanged) and keep the fastest.  Small levels keep the default.
+    // Whether a cooperative launch of the tail kernel can be captured into a
+    // graph and replayed here (once per process and kernel instance, when
+    // the first tree tunes its sweeps): an empty program, captured on a
+    // private stream.  Until it has passed, cycles run without the tail
+    // kernel.
+    static int &tail_state() {  // 0: not probed, 1: works, -1: refused
+        static int state = 0;
+        return state;
+    }
+    static void tail_probe(mg_tree *t) {
+        int &state = tail_state();
+        if (!state) {
+            static TailProg empty;
+            empty.nops = 0;
+            cudaStream_t s = nullptr;
+            cudaGraph_t g = nullptr;
+            cudaGraphExec_t ge = nullptr;
+            bool ok = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) == cudaSuccess;
+            ok = ok && cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+            if (ok) {
+                cudaLaunchConfig_t cfg = {};
+                cfg.gridDim = dim3((unsigned)std::min(tail_capacity(t), 2 * t->nsm));
+                cfg.blockDim = dim3(kTailThreads);
+                cfg.stream = s;
+                cudaLaunchAttribute at[1];
+                at[0].id = cudaLaunchAttributeCooperative;
+                at[0].val.cooperative = 1;
+                cfg.attrs = at;
+                cfg.numAttrs = 1;
+                const bool launched =
+                    cudaLaunchKernelEx(&cfg, k_tail<T, D>, kparams(t, 1), Fields<T>{}, (const TailProg)empty) ==
+                    cudaSuccess;
+                ok = (cudaStreamEndCapture(s, &g) == cudaSuccess) && launched && g;
+            }
+            ok = ok && cudaGraphInstantiate(&ge, g, 0) == cudaSuccess;
+            ok = ok && cudaGraphLaunch(ge, s) == cudaSuccess && cudaStreamSynchronize(s) == cudaSuccess;
+            if (ge) cudaGraphExecDestroy(ge);
+            if (g) cudaGraphDestroy(g);
+            if (s) cudaStreamDestroy(s);
+            cudaGetLastError();
+            state = ok ? 1 : -1;
+        }
+    }
     static void tune(mg_tree *t, Fields<T> &F) {
         const int prec = sizeof(T) == 4 ? 1 : 0;
         const KParams P = kparams(t, 1);
+        tail_probe(t);
         t->sweep_choice[prec].assign(t->lev.size(), -1);
         cudaEvent_t e0, e1;
         cudaEventCreate(&e0);
@@ -3934,7 +4229,7 @@ template <class T, int D> struct Launch {
         for (int l : t->groups[g]) {
             const LevelHost &L = t->lev[l];
             if (L.coarsest) continue;
-            if (is_flat(L)) {
+            if (flat_mode(t, L)) {
                 flat.push_back(l);
                 for (int q : L.parents) plain[q] = 1;
                 continue;
@@ -3965,14 +4260,14 @@ template <class T, int D> struct Launch {
         std::vector<int> flat_ghost, flat_fas;
         for (int c : t->groups[g - 1])
             if (plain[c]) {
-                if (is_flat(t->lev[c])) flat_ghost.push_back(c);
+                if (flat_mode(t, t->lev[c])) flat_ghost.push_back(c);
                 else ghost(t, P, c, F.X, F.XG, 0);
             }
         if (!flat_ghost.empty()) ghost_flat(t, P, flat_ghost, F.X, F.XG, 0);
         for (int c : t->groups[g - 1]) {
             const LevelHost &C = t->lev[c];
             if (C.nref <= 0) continue;
-            if (is_flat(C)) {
+            if (flat_mode(t, C)) {
                 flat_fas.push_back(c);
                 continue;
             }
@@ -4037,6 +4332,10 @@ template <class T, int D> struct Launch {
     // exact coarsest solves of the trees whose coarsest group is below `top`
     // (strict) or at most `top`; then ghost fills of the coarsest segments
     static void coarse(mg_tree *t, const KParams &P, Fields<T> &F, int top, int strict) {
+        coarse_solve(t, P, F, top, strict);
+        coarse_ghosts(t, P, F, top);
+    }
+    static void coarse_solve(mg_tree *t, const KParams &P, Fields<T> &F, int top, int strict) {
         const int ntr = (int)t->tcoarse.size();
         if (t->coarse_mode == 1) {  // the paper's smoothing of the coarsest level
             const size_t sm = sizeof(double) * (size_t)t->coarse_pad * (F.E ? 3 : 2);
@@ -4044,7 +4343,6 @@ template <class T, int D> struct Launch {
             ++t->launches;
             launch_k(k_coarse_gs<T, D>, ntr, 1024, sm, t->stream, P, t->d_tcoarse, top, strict, F,
                      CoarseSmooth{t->coarse_abs, t->coarse_rel, t->coarse_max_it});
-            coarse_ghosts(t, P, F, top);
             return;
         }
         if (t->n_coarse_chunks) {  // trees with a dense inverse
@@ -4083,7 +4381,6 @@ template <class T, int D> struct Launch {
                          (const float *)t->d_bt32, (const int *)t->d_btperm, ring, slot);
             }
         }
-        coarse_ghosts(t, P, F, top);
     }
     // smoothing steps on level l: the per-level schedule where one is set
     // (mg_set_schedule), else the cycle's n_down / n_up
@@ -4107,7 +4404,7 @@ template <class T, int D> struct Launch {
         for (int l : t->groups[g]) {
             if (t->lev[l].coarsest) continue;
             const int st = steps(t, l, n, down);
-            if (!jac && chosen_cand(t, l, F) == 6) flat[st].push_back(l);
+            if (!jac && (t->tail_rec || chosen_cand(t, l, F) == 6)) flat[st].push_back(l);
             else smooth(t, P, l, F, st);
         }
         for (auto &kv : flat)
@@ -4120,29 +4417,50 @@ template <class T, int D> struct Launch {
         std::vector<int> flat;
         for (int l : t->groups[g]) {
             if (t->lev[l].coarsest) continue;
-            if (is_flat(t->lev[l])) flat.push_back(l);
+            if (flat_mode(t, t->lev[l])) flat.push_back(l);
             else prolong(t, P, l, F);
         }
         if (flat.empty()) return;
         prolong_flat(t, P, flat, F);
         ghost_flat(t, P, flat, F.X, F.XG, 0);
     }
+    // The groups up to tail_cut run in the tail kernel: the downward steps
+    // below the cut in one launch, the coarsest solve, then the coarsest
+    // ghosts and the upward steps up to the cut in another.
     static void vcycle(mg_tree *t, Fields<T> &F, int top, int nd, int nu, int homog, int strict = 0) {
         const KParams P = kparams(t, homog);
+        const int cut = tail_cut(t, top);
+        TailRec tr;
+        tr.P = P;
+        tr.F = F;
         for (int g = top; g >= 1; g--) {
+            if (g == cut) tail_begin(t, tr);
             smooth_group(t, P, g, F, nd, true);
             restrict_group(t, P, g, F);
         }
-        coarse(t, P, F, top, strict);
+        tail_end(t, tr);
+        coarse_solve(t, P, F, top, strict);
+        if (cut) tail_begin(t, tr);
+        coarse_ghosts(t, P, F, top);
         for (int g = 1; g <= top; g++) {
             prolong_group(t, P, g, F);
             smooth_group(t, P, g, F, nu, false);
+            if (g == cut) tail_end(t, tr);
         }
+        tail_end(t, tr);
     }
     static void fmg(mg_tree *t, Fields<T> &F, int nd, int nu, int homog) {
         const KParams P = kparams(t, homog);
         const int top = (int)t->groups.size() - 1;
-        for (int g = top; g >= 1; g--) restrict_group(t, P, g, F);
+        const int cut = tail_cut(t, top);
+        TailRec tr;
+        tr.P = P;
+        tr.F = F;
+        for (int g = top; g >= 1; g--) {
+            if (g == cut) tail_begin(t, tr);
+            restrict_group(t, P, g, F);
+        }
+        tail_end(t, tr);
         coarse(t, P, F, top, 0);
         for (int g = 1; g <= top; g++) {
             prolong_group(t, P, g, F);
@@ -4155,7 +4473,7 @@ template <class T, int D> struct Launch {
         std::vector<int> flat;
         for (size_t l = 0; l < t->lev.size(); l++) {
             if (!t->lev[l].coarsest || t->lev[l].group > top || t->lev[l].nb == 0) continue;
-            if (is_flat(t->lev[l])) flat.push_back((int)l);
+            if (flat_mode(t, t->lev[l])) flat.push_back((int)l);
             else ghost(t, P, (int)l, F.X, F.XG, 0);
         }
         if (!flat.empty()) ghost_flat(t, P, flat, F.X, F.XG, 0);
@@ -4751,7 +5069,7 @@ extern "C" int mg_residual_norm_noalloc(mg_tree *t, double *l2, double *linf) {
         return MG_ERR_CUDA;
     }
     if (st) {
-        cudaMemset(t->d_status, 0, sizeof(int));
+        cudaMemset(t->d_status, 0, sizeof(int) * kStatusWords);
         mg_set_error("a bounded wait in a residual kernel expired");
         return MG_ERR_TIMEOUT;
     }

@@ -808,7 +808,7 @@ extern "C" int mg_tree_finalize(mg_tree *t, void *stream) {
     t->n_partials = (int)nleafb;
     if ((rc = dalloc(&t->d_partials, 3 * nleafb))) return rc;
     if ((rc = dalloc(&t->d_red, 3))) return rc;
-    if ((rc = dalloc(&t->d_status, 1))) return rc;
+    if ((rc = dalloc(&t->d_status, kStatusWords))) return rc;
     if ((rc = dalloc(&t->d_cvec, t->cvec_total))) return rc;
     CK(cudaMalloc((void **)&t->d_tcoarse, sizeof(TreeCoarse) * t->tcoarse.size()));
     CK(cudaMemcpy(t->d_tcoarse, t->tcoarse.data(), sizeof(TreeCoarse) * t->tcoarse.size(), cudaMemcpyHostToDevice));
@@ -993,7 +993,7 @@ static int check_status(mg_tree *t) {
     CK(cudaStreamSynchronize(t->stream));
     CK(cudaMemcpy(&st, t->d_status, sizeof(int), cudaMemcpyDeviceToHost));
     if (st) {
-        CK(cudaMemset(t->d_status, 0, sizeof(int)));
+        CK(cudaMemset(t->d_status, 0, sizeof(int) * kStatusWords));
         return fail(MG_ERR_TIMEOUT, "a bounded wait in a kernel expired");
     }
     return MG_OK;
@@ -1579,6 +1579,13 @@ extern "C" int mg_set_wait_limit(mg_tree *t, int64_t polls) {
     return MG_OK;
 }
 
+extern "C" int mg_set_tail(mg_tree *t, int64_t max_cells) {
+    if (!t) return fail(MG_ERR_ARG, "null tree");
+    t->tail_cells = max_cells < 0 ? 0 : max_cells;
+    drop_graphs(t);  // captured cycles hold the previous split
+    return MG_OK;
+}
+
 extern "C" int mg_launch_count(mg_tree *t, int64_t *n) {
     if (!t || !n) return fail(MG_ERR_ARG, "null argument");
     *n = t->launches;
@@ -2087,6 +2094,11 @@ extern "C" int mg_batch_tune_schedule(mg_batch *b, double rel_tol, int max_cycle
 extern "C" int mg_batch_launch_count(mg_batch *b, int64_t *n) {
     NEED_BATCH(b);
     return mg_launch_count(b->pool, n);
+}
+
+extern "C" int mg_batch_set_tail(mg_batch *b, int64_t max_cells) {
+    NEED_BATCH(b);
+    return mg_set_tail(b->pool, max_cells);
 }
 
 extern "C" int mg_batch_time_sweeps(mg_batch *b, int level, int n_sweeps, int precision, double out[4]) {
