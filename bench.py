@@ -717,6 +717,33 @@ def run_profile(kind, pins="", inner=1, up=-1):
     print("profile %s done: %d launches" % (kind, tree.launch_count()))
 
 
+def run_profile_cfg3(kind, steps=2):
+    """The 256^3 variable-coefficient workload (contrast 100) for ncu launch
+    lists: `steps` outer steps of a solve from phi = 0 (FMG first) after one
+    untimed warm-up of the same call, the second inside the NVTX range
+    "measure"; cfg3_32 runs FP32 cycles in FP64 defect correction, cfg3_64
+    plain FP64."""
+    import torch
+    import paper_1901_11370_gb300 as mg
+    from synth import workloads as W
+    torch.cuda.set_device(0)
+    tree = mg.Tree.from_problem(W.cfg3_varcoef3d())
+    prec = mg.MG_FP32_DC if kind == "cfg3_32" else mg.MG_FP64
+    zeros = torch.zeros(tree.n_leaf, dtype=torch.float64, device="cuda")
+    for rep in range(2):
+        tree.set_phi(zeros)
+        torch.cuda.synchronize()
+        if rep:
+            torch.cuda.nvtx.range_push("measure")
+        tree.solve(1e-30, steps, fmg_first=True, precision=prec, raise_on_fail=False)
+        torch.cuda.synchronize()
+        if rep:
+            torch.cuda.nvtx.range_pop()
+    print("sweep variants by level:", ",".join("%d:%d" % (l, tree.sweep_variant(l, prec))
+                                              for l in range(len(tree.levels()))))
+    print("profile %s done: %d launches" % (kind, tree.launch_count()))
+
+
 def pin_sweeps(tree, prec, pins):
     for item in filter(None, pins.split(",")):
         lev, var = (int(x) for x in item.split(":"))
@@ -765,7 +792,8 @@ def main():
     ap.add_argument("--no-cfg3", action="store_true", help="skip the 256^3 variable-coefficient workload")
     ap.add_argument("--cfg5-base", type=int, default=512,
                     help="base grid of the divergence-cleaning workload (0: skip it)")
-    ap.add_argument("--profile", choices=["sweeps64", "sweeps32", "solve32", "solve64", "batch32"], default=None)
+    ap.add_argument("--profile", choices=["sweeps64", "sweeps32", "solve32", "solve64", "batch32", "cfg3_32", "cfg3_64"],
+                    default=None)
     ap.add_argument("--trees", type=int, default=512, help="with --profile batch32: trees of the forest to use")
     ap.add_argument("--inner", type=int, default=1,
                     help="with --profile solve* / batch32: FP32 cycles per outer step (the tuned schedule's choice)")
@@ -776,6 +804,8 @@ def main():
     args = ap.parse_args()
     if args.profile == "batch32":
         run_profile_batch(args.trees, args.inner)
+    elif args.profile in ("cfg3_32", "cfg3_64"):
+        run_profile_cfg3(args.profile)
     elif args.profile:
         run_profile(args.profile, args.pin_sweeps, args.inner, args.n_up)
     elif args.impl == "reference":
