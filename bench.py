@@ -735,7 +735,7 @@ def run_profile_cfg3(kind, steps=2):
         torch.cuda.synchronize()
         if rep:
             torch.cuda.nvtx.range_push("measure")
-        tree.solve(1e-30, steps, fmg_first=True, precision=prec, raise_on_fail=False)
+        tree.solve(TOL, steps, fmg_first=True, precision=prec, raise_on_fail=False)  # stops after `steps`
         torch.cuda.synchronize()
         if rep:
             torch.cuda.nvtx.range_pop()
