@@ -169,7 +169,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_sweep(KParams P, int first, Fie
             sx[sid(q.x, q.y, q.z)] = F.XG[b.ghost_off + t];
         }
     }
-    if (var) {
+    if (var && !F.W) {
         for (int c = tid; c < C; c += nth) {
             const int i = c % n, j = (c / n) % n, k = D == 3 ? c / (n * n) : 0;
             se[sid(i, j, k)] = F.E[b.cell_off + c];
@@ -212,10 +212,22 @@ __global__ void __launch_bounds__(kMaxThreads) k_sweep(KParams P, int first, Fie
     const T helm = kp_helm<T>(P);
     const T w0 = lv_ih<T>(L, 0), w1 = lv_ih<T>(L, 1), w2 = lv_ih<T>(L, 2);
     const T inv_den = (T)1 / ((T)2 * (w0 + w1 + (D == 3 ? w2 : (T)0)) + helm);
+    const T *W = F.W;  // FP64 face coefficients (variable eps or cylindrical form), else null
     auto update = [&](int i, int j, int k, T fc) {
         const int c0 = sid(i, j, k);
         T xnew;
-        if (!var && !cyl) {
+        if (W) {  // the coefficients and 1 / diagonal precomputed: no division
+            const T *ws = W + b.cell_off * wstride(D) + cidx<D>(n, i, j, k);
+            T num = ws[0] * sx[c0 - 1];
+            num += ws[C] * sx[c0 + 1];
+            num += ws[2 * C] * sx[c0 - sy];
+            num += ws[3 * C] * sx[c0 + sy];
+            if (D == 3) {
+                num += ws[4 * C] * sx[c0 - sz];
+                num += ws[5 * C] * sx[c0 + sz];
+            }
+            xnew = (num - fc) * ws[(2 * D + 1) * C];
+        } else if (!var && !cyl) {
             T num = w0 * (sx[c0 - 1] + sx[c0 + 1]) + w1 * (sx[c0 - sy] + sx[c0 + sy]);
             if (D == 3) num += w2 * (sx[c0 - sz] + sx[c0 + sz]);
             xnew = (num - fc) * inv_den;
@@ -1119,10 +1131,21 @@ __global__ void __launch_bounds__(kMaxThreads) k_restrict_push(KParams P, int fi
 #pragma unroll 1
         for (int ch = 0; ch < (1 << D); ch++) {
             const int fi = 2 * ci + (ch & 1), fj = 2 * cj + ((ch >> 1) & 1), fk = D == 3 ? 2 * ck + ((ch >> 2) & 1) : 0;
+            const int fc = cidx<D>(n, fi, fj, fk);
+            if constexpr (sizeof(T) == 8) {
+                if (F.W) {  // precomputed face coefficients (no FP64 division)
+                    double dg;
+                    const double s = row_w<D>(b, F.X, F.XG, F.W, fi, fj, fk, dg);
+                    const double xc = F.X[b.cell_off + fc];
+                    sx += xc;
+                    sr += fma(dg, xc, F.F[b.cell_off + fc]) - s;
+                    continue;
+                }
+            }
             T lap, num, den, xc;
             stencil<T, T, D>(P, L, b, F.X, F.XG, F.E, F.EG, fi, fj, fk, lap, num, den, xc);
             sx += xc;
-            sr += F.F[b.cell_off + cidx<D>(n, fi, fj, fk)] - (lap - kp_helm<T>(P) * xc);
+            sr += F.F[b.cell_off + fc] - (lap - kp_helm<T>(P) * xc);
         }
         const T xv = sx * (T)(1.0 / (1 << D));
         const int pc = cidx<D>(pn, b.poff[0] + ci, b.poff[1] + cj, b.poff[2] + ck);
@@ -1165,6 +1188,16 @@ __global__ void __launch_bounds__(kMaxThreads) k_fas_rhs_vold(KParams P, int fir
     for (int c = threadIdx.x; c < C; c += blockDim.x) {
         int i, j, k;
         cell_of(c, n, D, i, j, k);
+        if constexpr (sizeof(T) == 8) {
+            if (F.W) {  // precomputed face coefficients (no FP64 division)
+                double dg;
+                const double s = row_w<D>(b, F.X, F.XG, F.W, i, j, k, dg);
+                const double xc = F.X[b.cell_off + c];
+                F.F[b.cell_off + c] += fma(-dg, xc, s);
+                F.V[b.cell_off + c] = xc;
+                continue;
+            }
+        }
         T lap, num, den, xc;
         stencil<T, T, D>(P, L, b, F.X, F.XG, F.E, F.EG, i, j, k, lap, num, den, xc);
         F.F[b.cell_off + c] += lap - kp_helm<T>(P) * xc;
@@ -2344,16 +2377,28 @@ __global__ void __launch_bounds__(kMaxThreads) k_resnorm(KParams P, int first, F
     for (int c = threadIdx.x; c < C; c += blockDim.x) {
         int i, j, k;
         cell_of(c, n, D, i, j, k);
-        double lap, num, den, xc;
-        stencil<double, double, D>(P, L, b, F.X, F.XG, F.E, F.EG, i, j, k, lap, num, den, xc);
-        const double r = F.F[b.cell_off + c] - (lap - P.helm * xc);
+        double r;
+        if (F.W) {  // precomputed face coefficients: f + diag x_c - sum_f w_f x_f, as k_resid_tma
+            const double *ws = F.W + b.cell_off * wstride(D) + c;
+            r = fma(ws[2 * D * C], F.X[b.cell_off + c], F.F[b.cell_off + c]);
+#pragma unroll
+            for (int f = 0; f < 2 * D; f++) {
+                const int d = f >> 1, o = (f & 1) ? 1 : -1;
+                r = fma(-ws[f * C], load<double, D>(F.X, F.XG, b, i + (d == 0 ? o : 0), j + (d == 1 ? o : 0),
+                                                    k + (d == 2 ? o : 0)), r);
+            }
+        } else {
+            double lap, num, den, xc;
+            stencil<double, double, D>(P, L, b, F.X, F.XG, F.E, F.EG, i, j, k, lap, num, den, xc);
+            r = F.F[b.cell_off + c] - (lap - P.helm * xc);
+        }
         double V = vol;
         if (P.geom == MG_CYL) V = 2.0 * M_PI * (P.lo[0] + (b.ijk[0] * n + i + 0.5) * L.h[0]) * L.h[0] * L.h[1];
         s2 += V * r * r;
         sv += V;
         mx = fmax(mx, fabs(r));
         if (rleaf) rleaf[leaf_base + (b.cell_off - cell_base) + c] = r;
-        if (f32) f32[b.cell_off + c] = (float)r;
+        if (f32) f32[b.cell_off + c] = mg_to_float(r);  // integer rounding: no FP64-pipe conversion
     }
     for (int o = 16; o > 0; o >>= 1) {
         s2 += __shfl_down_sync(0xffffffffu, s2, o);
