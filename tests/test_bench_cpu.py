@@ -16,7 +16,8 @@ def entries():
 
 def test_traffic_entries_parse_and_follow_the_source_hash():
     es = entries()
-    assert {e["kernel"] for e in es} == {"k_sweep_rows", "k_sweep_tma"}
+    kernels = {e["kernel"] for e in es}
+    assert "k_sweep_rows" in kernels and kernels <= {"k_sweep_rows", "k_sweep_tma"}
     for e in es:
         got = bench.measured_traffic(e["kernel"], "sweep_f32_traffic.txt")
         if e["source_sha1"] == bench.kernel_sha1(e["kernel"]):
