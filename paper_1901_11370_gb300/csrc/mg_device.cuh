@@ -188,28 +188,30 @@ __device__ __forceinline__ void stencil(const KParams &P, const LevelDesc &L, co
     }
 }
 
-// The FP64 operator row from the precomputed face coefficients W (variable
-// eps or the cylindrical form; wstride(D) slots per cell, [slot][cell]
-// within a block: the 2D face weights in face order, the diagonal -- the
-// weights' sum plus lambda -- and its reciprocal): s = sum_f w_f x_f and
-// the diagonal, so that A x - lambda x = s - diag x_c and the residual is
-// f + diag x_c - s.  No division: GB300 spends about ten FP64 instructions
-// on one, and the on-the-fly harmonic means take six per cell.
+// The FP64 operator from the precomputed face coefficients W (variable eps
+// or the cylindrical form; wstride(D) slots per cell, [slot][cell] within
+// a block: the 2D face weights in face order, the diagonal -- the weights'
+// sum plus lambda -- and its reciprocal), in the difference form of
+// `stencil`: lap = sum_f w_f (x_f - x_c), the same terms in the same order
+// as the on-the-fly form (whose weights W holds), so the result is the
+// same and its rounding stays at eps |w| |x_f - x_c|.  No division: GB300
+// spends about ten FP64 instructions on one, and the on-the-fly harmonic
+// means take six per cell.
 template <int D>
-__device__ __forceinline__ double row_w(const BlockDesc &b, const double *X, const double *XG, const double *W,
-                                        int i, int j, int k, double &diag) {
+__device__ __forceinline__ double lap_w(const BlockDesc &b, const double *X, const double *XG, const double *W,
+                                        int i, int j, int k, double xc) {
     const int n = b.n, C = cells_of<D>(n);
     const double *ws = W + b.cell_off * wstride(D) + cidx<D>(n, i, j, k);
-    double s = ws[0] * load<double, D>(X, XG, b, i - 1, j, k);
-    s = fma(ws[C], load<double, D>(X, XG, b, i + 1, j, k), s);
-    s = fma(ws[2 * C], load<double, D>(X, XG, b, i, j - 1, k), s);
-    s = fma(ws[3 * C], load<double, D>(X, XG, b, i, j + 1, k), s);
+    double lap = 0;
+    lap += ws[0] * (load<double, D>(X, XG, b, i - 1, j, k) - xc);
+    lap += ws[C] * (load<double, D>(X, XG, b, i + 1, j, k) - xc);
+    lap += ws[2 * C] * (load<double, D>(X, XG, b, i, j - 1, k) - xc);
+    lap += ws[3 * C] * (load<double, D>(X, XG, b, i, j + 1, k) - xc);
     if (D == 3) {
-        s = fma(ws[4 * C], load<double, D>(X, XG, b, i, j, k - 1), s);
-        s = fma(ws[5 * C], load<double, D>(X, XG, b, i, j, k + 1), s);
+        lap += ws[4 * C] * (load<double, D>(X, XG, b, i, j, k - 1) - xc);
+        lap += ws[5 * C] * (load<double, D>(X, XG, b, i, j, k + 1) - xc);
     }
-    diag = ws[2 * D * C];
-    return s;
+    return lap;
 }
 
 __device__ __forceinline__ void cell_of(int c, int n, int D, int &i, int &j, int &k) {

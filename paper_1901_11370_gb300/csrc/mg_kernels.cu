@@ -1134,11 +1134,9 @@ __global__ void __launch_bounds__(kMaxThreads) k_restrict_push(KParams P, int fi
             const int fc = cidx<D>(n, fi, fj, fk);
             if constexpr (sizeof(T) == 8) {
                 if (F.W) {  // precomputed face coefficients (no FP64 division)
-                    double dg;
-                    const double s = row_w<D>(b, F.X, F.XG, F.W, fi, fj, fk, dg);
                     const double xc = F.X[b.cell_off + fc];
                     sx += xc;
-                    sr += fma(dg, xc, F.F[b.cell_off + fc]) - s;
+                    sr += F.F[b.cell_off + fc] - (lap_w<D>(b, F.X, F.XG, F.W, fi, fj, fk, xc) - P.helm * xc);
                     continue;
                 }
             }
@@ -1190,10 +1188,8 @@ __global__ void __launch_bounds__(kMaxThreads) k_fas_rhs_vold(KParams P, int fir
         cell_of(c, n, D, i, j, k);
         if constexpr (sizeof(T) == 8) {
             if (F.W) {  // precomputed face coefficients (no FP64 division)
-                double dg;
-                const double s = row_w<D>(b, F.X, F.XG, F.W, i, j, k, dg);
                 const double xc = F.X[b.cell_off + c];
-                F.F[b.cell_off + c] += fma(-dg, xc, s);
+                F.F[b.cell_off + c] += lap_w<D>(b, F.X, F.XG, F.W, i, j, k, xc) - P.helm * xc;
                 F.V[b.cell_off + c] = xc;
                 continue;
             }
@@ -2378,15 +2374,9 @@ __global__ void __launch_bounds__(kMaxThreads) k_resnorm(KParams P, int first, F
         int i, j, k;
         cell_of(c, n, D, i, j, k);
         double r;
-        if (F.W) {  // precomputed face coefficients: f + diag x_c - sum_f w_f x_f, as k_resid_tma
-            const double *ws = F.W + b.cell_off * wstride(D) + c;
-            r = fma(ws[2 * D * C], F.X[b.cell_off + c], F.F[b.cell_off + c]);
-#pragma unroll
-            for (int f = 0; f < 2 * D; f++) {
-                const int d = f >> 1, o = (f & 1) ? 1 : -1;
-                r = fma(-ws[f * C], load<double, D>(F.X, F.XG, b, i + (d == 0 ? o : 0), j + (d == 1 ? o : 0),
-                                                    k + (d == 2 ? o : 0)), r);
-            }
+        if (F.W) {  // precomputed face coefficients (the weights of the form below)
+            const double xc = F.X[b.cell_off + c];
+            r = F.F[b.cell_off + c] - (lap_w<D>(b, F.X, F.XG, F.W, i, j, k, xc) - P.helm * xc);
         } else {
             double lap, num, den, xc;
             stencil<double, double, D>(P, L, b, F.X, F.XG, F.E, F.EG, i, j, k, lap, num, den, xc);
