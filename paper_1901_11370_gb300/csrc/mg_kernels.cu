@@ -2355,8 +2355,11 @@ __global__ void __launch_bounds__(kMaxThreads) k_grad_sub(KParams P, int first, 
 // ------------------------------------------------------ residual norm ---
 // Composite residual on leaf blocks [first, first + gridDim.x): per-CTA
 // partial sums of V r^2 and V and the max |r| (warp shuffles, then shared
-// memory); optional r in leaf order and (float) r into FP32 cells.
-template <int D>
+// memory); optional r in leaf order and (float) r into FP32 cells.  MX off
+// (the solve loops, which read only the L2 norm): r^2 accumulated in FP32
+// from the FP32-rounded residual and scaled by the block's cell volume once,
+// no max -- the FP64 work per cell is then the operator alone.
+template <int D, bool MX = true>
 __global__ void __launch_bounds__(kMaxThreads) k_resnorm(KParams P, int first, Fields<double> F,
                                                          double *__restrict__ partials,
                                                          double *__restrict__ rleaf, long long leaf_base,
@@ -2367,7 +2370,9 @@ __global__ void __launch_bounds__(kMaxThreads) k_resnorm(KParams P, int first, F
     const BlockDesc &b = sb;
     const LevelDesc &L = P.L[b.lev];
     const int n = b.n, C = cells_of<D>(n);
+    const bool cyl = P.geom == MG_CYL, helm0 = P.helm == 0.0;
     double s2 = 0, sv = 0, mx = 0;
+    float acc_r = 0.f, acc_v = 0.f;
     double vol = 1.0;
     for (int d = 0; d < D; d++) vol *= L.h[d];
     for (int c = threadIdx.x; c < C; c += blockDim.x) {
@@ -2376,19 +2381,47 @@ __global__ void __launch_bounds__(kMaxThreads) k_resnorm(KParams P, int first, F
         double r;
         if (F.W) {  // precomputed face coefficients (the weights of the form below)
             const double xc = F.X[b.cell_off + c];
-            r = F.F[b.cell_off + c] - (lap_w<D>(b, F.X, F.XG, F.W, i, j, k, xc) - P.helm * xc);
+            const double lap = lap_w<D>(b, F.X, F.XG, F.W, i, j, k, xc);
+            r = helm0 ? F.F[b.cell_off + c] - lap : F.F[b.cell_off + c] - (lap - P.helm * xc);
         } else {
             double lap, num, den, xc;
             stencil<double, double, D>(P, L, b, F.X, F.XG, F.E, F.EG, i, j, k, lap, num, den, xc);
             r = F.F[b.cell_off + c] - (lap - P.helm * xc);
         }
-        double V = vol;
-        if (P.geom == MG_CYL) V = 2.0 * M_PI * (P.lo[0] + (b.ijk[0] * n + i + 0.5) * L.h[0]) * L.h[0] * L.h[1];
-        s2 += V * r * r;
-        sv += V;
-        mx = fmax(mx, fabs(r));
+        const float rf = mg_to_float(r);  // integer rounding: no FP64-pipe conversion
+        if (MX) {
+            double V = vol;
+            if (cyl) V = 2.0 * M_PI * (P.lo[0] + (b.ijk[0] * n + i + 0.5) * L.h[0]) * L.h[0] * L.h[1];
+            s2 += V * r * r;
+            sv += V;
+            mx = fmax(mx, fabs(r));
+        } else if (cyl) {
+            const float Vf = (P.lo0f + ((float)(b.ijk[0] * n + i) + 0.5f) * L.h0f) * L.hvf;
+            acc_r = fmaf(Vf * rf, rf, acc_r);
+            acc_v += Vf;
+        } else {
+            acc_r = fmaf(rf, rf, acc_r);
+        }
         if (rleaf) rleaf[leaf_base + (b.cell_off - cell_base) + c] = r;
-        if (f32) f32[b.cell_off + c] = mg_to_float(r);  // integer rounding: no FP64-pipe conversion
+        if (f32) f32[b.cell_off + c] = rf;
+    }
+    if (!MX) {
+        for (int o = 16; o > 0; o >>= 1) {
+            acc_r += __shfl_down_sync(0xffffffffu, acc_r, o);
+            acc_v += __shfl_down_sync(0xffffffffu, acc_v, o);
+        }
+        __shared__ float shf[2][kMaxThreads / 32];
+        const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = (blockDim.x + 31) >> 5;
+        if (lane == 0) { shf[0][w] = acc_r; shf[1][w] = acc_v; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float a = 0.f, v = 0.f;
+            for (int e = 0; e < nw; e++) { a += shf[0][e]; v += shf[1][e]; }
+            partials[3 * blockIdx.x] = cyl ? (double)a : vol * (double)a;
+            partials[3 * blockIdx.x + 1] = cyl ? (double)v : vol * C;
+            partials[3 * blockIdx.x + 2] = 0.0;
+        }
+        return;
     }
     for (int o = 16; o > 0; o >>= 1) {
         s2 += __shfl_down_sync(0xffffffffu, s2, o);
@@ -3828,13 +3861,17 @@ static int threads_for(int cells) {
 // parent octant, then face cells), so small CTAs waste less at barriers.
 // 128 threads measured best on GB300 (mixed solve of the 20M-unknown tree:
 // 19.8 ms at 256, 18.8 at 128, 19.1 at 64); MG_TRANSFER_THREADS overrides.
-static int transfer_threads(int want) {
+// Threads per CTA of the staged transfer kernels: 128, where several CTAs
+// share an SM (their phases are uneven, and 256-thread CTAs lost more at
+// the barriers); blocks of 16^3 cells and more, whose double-buffered
+// stages leave room for one CTA per SM, take kMaxThreads.
+static int transfer_threads(int want, int cells) {
     static int cap = [] {
         const char *e = std::getenv("MG_TRANSFER_THREADS");
         const int v = e ? std::atoi(e) : 128;
         return (v >= 32 && v <= kMaxThreads && v % 32 == 0) ? v : 128;
     }();
-    return std::min(want, cap);
+    return std::min(want, cells >= 4096 ? kMaxThreads : cap);
 }
 
 template <class T, int D> struct Launch {
@@ -4015,7 +4052,7 @@ template <class T, int D> struct Launch {
             if (smt <= 200 * 1024) {
                 auto kern = L.n == 8 ? k_ghost_tma<T, D, 8> : k_ghost_tma<T, D, 16>;
                 set_smem(kern, smt);
-                const int thr = transfer_threads(threads_for(2 * D * face_of<D>(L.n)));
+                const int thr = transfer_threads(threads_for(2 * D * face_of<D>(L.n)), cells_of<D>(L.n));
                 const int grid = std::min(L.nb, resident_ctas(kern, thr, smt) * t->nsm);
                 launch_k(kern, grid, thr, smt, t->stream, P, L.first, L.nb, X, XG, mode);
                 return;
@@ -4280,7 +4317,7 @@ template <class T, int D> struct Launch {
                 launch_k(k_restrict_rows<T>, grid, 128, sr, t->stream, P, L.first, L.nb, F);
             } else if ((L.n == 8 || L.n == 16) && smt + sizeof(T) * C8 <= 200 * 1024) {
                 auto kern = L.n == 8 ? k_restrict_tma<T, D, 8> : k_restrict_tma<T, D, 16>;
-                const int thr = transfer_threads(threads_for(C8));
+                const int thr = transfer_threads(threads_for(C8), C8);
                 const int grid = std::min(L.nb, resident_ctas(kern, thr, smt) * t->nsm);
                 launch_k(kern, grid, thr, smt, t->stream, P, L.first, L.nb, F);
             } else if (L.n >= 4) {
@@ -4313,7 +4350,7 @@ template <class T, int D> struct Launch {
             if ((C.n == 8 || C.n == 16) && smf <= 200 * 1024) {
                 auto kern = C.n == 8 ? k_fas_tma<T, D, 8> : k_fas_tma<T, D, 16>;
                 set_smem(kern, smf);
-                const int thr = transfer_threads(threads_for(cells_of<D>(C.n)));
+                const int thr = transfer_threads(threads_for(cells_of<D>(C.n)), cells_of<D>(C.n));
                 const int grid = std::min(C.nref, resident_ctas(kern, thr, smf) * t->nsm);
                 launch_k(kern, grid, thr, smf, t->stream, P, C.first, C.nref, F);
             } else {
@@ -4349,7 +4386,7 @@ template <class T, int D> struct Launch {
             const size_t smt = prolong_tma_smem(L);
             auto kern = L.n == 8 ? k_prolong_tma<T, D, 8> : k_prolong_tma<T, D, 16>;
             set_smem(kern, smt);
-            const int thr = transfer_threads(threads_for(cells_of<D>(L.n) / 2));
+            const int thr = transfer_threads(threads_for(cells_of<D>(L.n) / 2), cells_of<D>(L.n));
             const int grid = std::min(L.nb, resident_ctas(kern, thr, smt) * t->nsm);
             launch_k(kern, grid, thr, smt, t->stream, P, L.first, L.nb, F, L.parent_same_n ? L.n : L.n / 2);
             return;
@@ -4687,8 +4724,8 @@ static void residual_norm_d(mg_tree *t, Fields<double> &F, int homog, double *ou
                                                leaf_base, f32_cells, 0);
             slot += grid;
         } else {
-            launch_k(k_resnorm<D>, nleaf, threads_for(C), 0, t->stream, P, L.first + L.nref, F, t->d_partials + 3 * slot,
-                                                                  r64_leaf, leaf_base, cell_base, f32_cells);
+            launch_k(want_max ? k_resnorm<D, true> : k_resnorm<D, false>, nleaf, threads_for(C), 0, t->stream, P,
+                     L.first + L.nref, F, t->d_partials + 3 * slot, r64_leaf, leaf_base, cell_base, f32_cells);
             slot += nleaf;
         }
         leaf_base += (long long)nleaf * cells_of<D>(L.n);
