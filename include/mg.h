@@ -346,7 +346,7 @@ int mg_get_schedule(mg_tree *t, int n, int *host_down, int *host_up);
  * of the tree's current problem (phi = 0, FMG first, mg_solve to rel_tol in
  * `precision`) for candidate schedules -- (n_down, n_up) in {1, 2, 3} set
  * separately for the levels holding leaves and for the coarser levels, and
- * for MG_FP32_DC one to three inner cycles per outer step -- each run three
+ * for MG_FP32_DC one to four inner cycles per outer step -- each run three
  * times (the first captures the graphs), and keeps the fastest candidate
  * that converges (mg_set_schedule).  A batch pool gives MG_ERR_ARG (use
  * mg_batch_tune_schedule).  *inner_cycles_out receives its inner

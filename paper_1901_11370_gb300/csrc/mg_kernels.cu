@@ -2358,9 +2358,13 @@ __global__ void __launch_bounds__(kMaxThreads) k_grad_sub(KParams P, int first, 
 // memory); optional r in leaf order and (float) r into FP32 cells.  MX off
 // (the solve loops, which read only the L2 norm): r^2 accumulated in FP32
 // from the FP32-rounded residual and scaled by the block's cell volume once,
-// no max -- the FP64 work per cell is then the operator alone.
-template <int D, bool MX = true>
-__global__ void __launch_bounds__(kMaxThreads) k_resnorm(KParams P, int first, Fields<double> F,
+// no max -- the FP64 work per cell is then the operator alone.  NT > 0: the
+// block size at compile time and kMaxThreads threads, so that a thread's
+// cells form a fixed loop the compiler unrolls (the loads of several cells
+// are in flight before their FP64 arithmetic, which on GB300 holds a warp
+// for many cycles per instruction).
+template <int D, bool MX = true, int NT = 0>
+__global__ void __launch_bounds__(kMaxThreads, 2) k_resnorm(KParams P, int first, Fields<double> F,
                                                          double *__restrict__ partials,
                                                          double *__restrict__ rleaf, long long leaf_base,
                                                          long long cell_base, float *__restrict__ f32) {
@@ -2369,13 +2373,18 @@ __global__ void __launch_bounds__(kMaxThreads) k_resnorm(KParams P, int first, F
     stage_desc(P, first + blockIdx.x, sb);
     const BlockDesc &b = sb;
     const LevelDesc &L = P.L[b.lev];
-    const int n = b.n, C = cells_of<D>(n);
+    const int n = NT ? NT : b.n, C = cells_of<D>(n);
     const bool cyl = P.geom == MG_CYL, helm0 = P.helm == 0.0;
     double s2 = 0, sv = 0, mx = 0;
     float acc_r = 0.f, acc_v = 0.f;
     double vol = 1.0;
     for (int d = 0; d < D; d++) vol *= L.h[d];
-    for (int c = threadIdx.x; c < C; c += blockDim.x) {
+    constexpr int PER = NT ? (cells_of<D>(NT) + kMaxThreads - 1) / kMaxThreads : 1;
+    const int stride = NT ? kMaxThreads : (int)blockDim.x;
+#pragma unroll 4
+    for (int q = 0; q < (NT ? PER : (C + stride - 1) / stride); q++) {
+        const int c = threadIdx.x + q * stride;
+        if (c >= C) break;
         int i, j, k;
         cell_of(c, n, D, i, j, k);
         double r;
@@ -4724,8 +4733,13 @@ static void residual_norm_d(mg_tree *t, Fields<double> &F, int homog, double *ou
                                                leaf_base, f32_cells, 0);
             slot += grid;
         } else {
-            launch_k(want_max ? k_resnorm<D, true> : k_resnorm<D, false>, nleaf, threads_for(C), 0, t->stream, P,
-                     L.first + L.nref, F, t->d_partials + 3 * slot, r64_leaf, leaf_base, cell_base, f32_cells);
+            if (D == 3 && L.n == 16)
+                launch_k(want_max ? k_resnorm<D, true, 16> : k_resnorm<D, false, 16>, nleaf, kMaxThreads, 0,
+                         t->stream, P, L.first + L.nref, F, t->d_partials + 3 * slot, r64_leaf, leaf_base, cell_base,
+                         f32_cells);
+            else
+                launch_k(want_max ? k_resnorm<D, true> : k_resnorm<D, false>, nleaf, threads_for(C), 0, t->stream, P,
+                         L.first + L.nref, F, t->d_partials + 3 * slot, r64_leaf, leaf_base, cell_base, f32_cells);
             slot += nleaf;
         }
         leaf_base += (long long)nleaf * cells_of<D>(L.n);

@@ -1488,7 +1488,7 @@ static int tune_schedule_impl(mg_tree *t, double rel_tol, int max_cycles, int pr
                                {1, 1, 2, 2, 1}, {2, 2, 1, 1, 1}, {1, 1, 3, 3, 1}, {1, 2, 2, 2, 1}};
     if (precision == MG_FP32_DC)  // more FP32 cycles per FP64 residual and update
         for (const Cand &c : {Cand{2, 2, 2, 2, 2}, Cand{1, 2, 1, 2, 2}, Cand{2, 1, 2, 1, 2}, Cand{1, 1, 1, 1, 2},
-                              Cand{2, 2, 2, 2, 3}})
+                              Cand{2, 2, 2, 2, 3}, Cand{2, 2, 2, 2, 4}})
             cands.push_back(c);
     // save phi (cells and ghosts) to restore it afterwards
     double *save = nullptr;
