@@ -400,7 +400,7 @@ def test_schedule_tuner_picks_a_converging_schedule(mg):
     p = CASES["varcoef3d_b16"]
     t, o = both(mg, p)
     inner, ms = t.tune_schedule(1e-10, 60, mg.MG_FP32_DC)
-    assert inner in (1, 2, 3) and ms > 0
+    assert inner in (1, 2, 3, 4) and ms > 0
     d, u = t.schedule()
     assert (d >= 0).all() and (u >= 0).all()
     t.set_phi(torch.zeros(t.n_leaf, dtype=torch.float64, device="cuda"))
