@@ -327,12 +327,13 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
                  "l"(src), "r"(bytes), "r"(smem_u32(bar))
                  : "memory");
 }
-// Right-hand sides of the FP32 cycles are read once per colour launch and
-// are the largest array a sweep streams.  Their lines are marked
-// evict-first in L2, so that on a level whose x, f and ghost slots together
-// just exceed L2 the level's x and ghost slots stay resident between the
-// launches of a smoothing phase instead of being streamed out by f.  FP64
-// fields are left at the default policy.
+// Right-hand sides and coefficients (eps and its ghosts) of the FP32 cycles
+// are read-only during smoothing and read once per colour launch: they are
+// the largest arrays a sweep streams.  Their lines are marked evict-first
+// in L2, so that on a level whose fields together exceed L2 the level's x
+// and ghost slots stay resident between the launches of a smoothing phase
+// instead of being streamed out by f and eps.  FP64 fields are left at the
+// default policy.
 __device__ __forceinline__ uint64_t l2_evict_first() {
     uint64_t pol;
     asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
@@ -423,8 +424,8 @@ __global__ void __launch_bounds__(kMaxThreads, (D == 3 && NT == 16) ? 1 : 5) k_s
             bulk_g2s(st + DESC + 2 * C + GH, F.W + co * wstride(D), sizeof(T) * 2 * D * C, bar);
             bulk_g2s(st + DESC + 2 * C + GH + 2 * D * C, F.W + co * wstride(D) + (2 * D + 1) * C, sizeof(T) * C, bar);
         } else if (var) {
-            bulk_g2s(st + DESC + 2 * C + GH, F.E + co, sizeof(T) * C, bar);
-            bulk_g2s(st + DESC + 3 * C + GH, F.EG + go, sizeof(T) * GH, bar);
+            bulk_g2s_f<T>(st + DESC + 2 * C + GH, F.E + co, sizeof(T) * C, bar);
+            bulk_g2s_f<T>(st + DESC + 3 * C + GH, F.EG + go, sizeof(T) * GH, bar);
         }
     };
     int g = blockIdx.x;
@@ -624,8 +625,8 @@ __global__ void __launch_bounds__(32 * WARPS) k_sweep_warp(KParams P, int first,
         bulk_g2s(st + DESC + C, F.XG + go, sizeof(T) * GH, bar);
         bulk_g2s_f<T>(st + DESC + C + GH, F.F + co, sizeof(T) * C, bar);
         if (var) {
-            bulk_g2s(st + DESC + 2 * C + GH, F.E + co, sizeof(T) * C, bar);
-            bulk_g2s(st + DESC + 3 * C + GH, F.EG + go, sizeof(T) * GH, bar);
+            bulk_g2s_f<T>(st + DESC + 2 * C + GH, F.E + co, sizeof(T) * C, bar);
+            bulk_g2s_f<T>(st + DESC + 3 * C + GH, F.EG + go, sizeof(T) * GH, bar);
         }
     };
     const int stride = gridDim.x * WARPS;
@@ -1991,8 +1992,8 @@ __global__ void __launch_bounds__(kMaxThreads, 4) k_restrict_tma(KParams P, int 
         if (wc) {
             bulk_g2s(st + 2 * DESC + 2 * C + GH, F.W + co * wstride(D), sizeof(T) * 2 * D * C, bar);
         } else if (var) {
-            bulk_g2s(st + 2 * DESC + 2 * C + GH, F.E + co, sizeof(T) * C, bar);
-            bulk_g2s(st + 2 * DESC + 3 * C + GH, F.EG + go, sizeof(T) * GH, bar);
+            bulk_g2s_f<T>(st + 2 * DESC + 2 * C + GH, F.E + co, sizeof(T) * C, bar);
+            bulk_g2s_f<T>(st + 2 * DESC + 3 * C + GH, F.EG + go, sizeof(T) * GH, bar);
         }
     };
     int g = blockIdx.x;
@@ -2364,7 +2365,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_grad_sub(KParams P, int first, 
 // are in flight before their FP64 arithmetic, which on GB300 holds a warp
 // for many cycles per instruction).
 template <int D, bool MX = true, int NT = 0>
-__global__ void __launch_bounds__(kMaxThreads, 2) k_resnorm(KParams P, int first, Fields<double> F,
+__global__ void __launch_bounds__(kMaxThreads, NT ? 3 : 2) k_resnorm(KParams P, int first, Fields<double> F,
                                                          double *__restrict__ partials,
                                                          double *__restrict__ rleaf, long long leaf_base,
                                                          long long cell_base, float *__restrict__ f32) {
@@ -2381,7 +2382,7 @@ __global__ void __launch_bounds__(kMaxThreads, 2) k_resnorm(KParams P, int first
     for (int d = 0; d < D; d++) vol *= L.h[d];
     constexpr int PER = NT ? (cells_of<D>(NT) + kMaxThreads - 1) / kMaxThreads : 1;
     const int stride = NT ? kMaxThreads : (int)blockDim.x;
-#pragma unroll 4
+#pragma unroll 2
     for (int q = 0; q < (NT ? PER : (C + stride - 1) / stride); q++) {
         const int c = threadIdx.x + q * stride;
         if (c >= C) break;
