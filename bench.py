@@ -504,17 +504,23 @@ def cfg3_measure(args, mg, W, barrier, max_over_ranks):
     tgt *= phi.pow(2).mean().sqrt() / tgt.pow(2).mean().sqrt()
     g = (phi - tgt) / n
     t.set_phi(phi)
-    t.adjoint(g, rel_tol=TOL, max_cycles=120)
-    barrier()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    t.adjoint(g, rel_tol=TOL, max_cycles=120)
-    e1.record(stream)
-    barrier()
-    ms = max_over_ranks(e0.elapsed_time(e1))
-    it, rel = t.last_adjoint
-    out["adjoint"] = {"ms": ms, "iterations": it, "final_rel_residual": rel, "unknowns_per_s": n * world / (ms * 1e-3),
-                      "outputs": "dL/df and dL/deps (FP64)"}
+    lams = {}
+    for key, prec in (("adjoint", mg.MG_FP32_DC), ("adjoint_fp64", mg.MG_FP64)):
+        t.adjoint(g, rel_tol=TOL, max_cycles=120, precision=prec)
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        lams[key] = t.adjoint(g, rel_tol=TOL, max_cycles=120, precision=prec)[0]
+        e1.record(stream)
+        barrier()
+        ms = max_over_ranks(e0.elapsed_time(e1))
+        it, rel = t.last_adjoint
+        out[key] = {"ms": ms, "iterations": it, "final_rel_residual": rel,
+                    "unknowns_per_s": n * world / (ms * 1e-3), "outputs": "dL/df and dL/deps (FP64)",
+                    "precision": ("FP32 V(2,2) cycles in the FP64 defect correction of the adjoint"
+                                  if prec == mg.MG_FP32_DC else "FP64 V(2,2) cycles")}
+    out["adjoint"]["rel_diff_vs_fp64"] = float((lams["adjoint"] - lams["adjoint_fp64"]).norm()
+                                               / lams["adjoint_fp64"].norm())
     del t
     torch.cuda.empty_cache()
     return out
@@ -564,11 +570,17 @@ def cfg5_measure(args, mg, W, barrier, max_over_ranks, base):
                     "final_rel_residual": rel, "div_B_l2_before": float(f.norm()),
                     "precision": "FP32 V(2,2) cycles in FP64 defect correction"}
     gBn = vol * (Bn - Bt)
-    ms, gB = timed(lambda: t.clean_adjoint(gBn, TOL, 80))
+    ms, gB = timed(lambda: t.clean_adjoint(gBn, TOL, 80, precision=mg.MG_FP32_DC))
     it, rel = t.last_adjoint
     out["adjoint"] = {"ms": ms, "unknowns_per_s": n * world / (ms * 1e-3), "iterations": it,
-                      "final_rel_residual": rel, "outputs": "dL/dB (3 FP64 components)"}
-    del t, B, Bt, Bn, gBn, gB, f
+                      "final_rel_residual": rel, "outputs": "dL/dB (3 FP64 components)",
+                      "precision": "FP32 V(2,2) cycles in the FP64 defect correction of the adjoint"}
+    ms64, gB64 = timed(lambda: t.clean_adjoint(gBn, TOL, 80))
+    it64, rel64 = t.last_adjoint
+    out["adjoint_fp64"] = {"ms": ms64, "unknowns_per_s": n * world / (ms64 * 1e-3), "iterations": it64,
+                           "final_rel_residual": rel64,
+                           "rel_diff_vs_fp32_dc": float((gB - gB64).norm() / gB64.norm())}
+    del t, B, Bt, Bn, gBn, gB, gB64, f
     torch.cuda.empty_cache()
     return out
 

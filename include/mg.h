@@ -256,7 +256,12 @@ int mg_solve(mg_tree *t, double rel_tol, int max_cycles, int fmg_first,
  * (sum g = 0) and lambda is returned without its component along W.  Such a
  * problem with variable eps and refinement faces returns MG_ERR_UNSUPPORTED
  * (fluxes are not conserved there).  dev_dLdeps may be NULL.  phi is left
- * unchanged; n_cycles >= 0.
+ * unchanged; n_cycles >= 0.  p->precision = MG_FP32_DC makes M an FP32
+ * V-cycle on the FP32 copy of W^-1 (g - A^T lambda) (the tree's FP32 fields,
+ * allocated on first use), the transpose, residual and update staying FP64
+ * (north star (1) applied to the adjoint solve): the same fixed point,
+ * reached in about as many iterations at the cost of FP32 cycles.  The
+ * FMG start is FP64 in both forms.
  */
 int mg_adjoint(mg_tree *t, const double *dev_dLdphi, double *dev_dLdf, double *dev_dLdeps,
                const mg_params *p, int n_cycles);

@@ -314,13 +314,14 @@ class Tree:
         return tuple(out), level
 
     def adjoint(self, g, n_cycles=12, want_eps=True, n_down=2, n_up=2, smoother=MG_SMOOTH_RBGS, omega=0.0,
-                rel_tol=None, max_cycles=80):
+                rel_tol=None, max_cycles=80, precision=MG_FP64):
         """(dL/df, dL/deps) for dL/dphi = g at the current phi (mg_adjoint:
         n_cycles defect-correction iterations; with rel_tol, mg_adjoint_solve
         until the adjoint residual is below rel_tol, raising MGError when
         max_cycles is reached).  With rel_tol, self.last_adjoint holds
-        (iterations, final relative residual)."""
-        p = _params(n_down, n_up, smoother=smoother, omega=omega)
+        (iterations, final relative residual).  precision=MG_FP32_DC: FP32
+        V-cycles inside the FP64 defect correction."""
+        p = _params(n_down, n_up, precision, smoother=smoother, omega=omega)
         dLdf = torch.empty(self.n_leaf, dtype=torch.float64, device="cuda")
         dLde = torch.empty(self.n_leaf, dtype=torch.float64, device="cuda") if want_eps else None
         if rel_tol is None:
@@ -340,13 +341,14 @@ class Tree:
         check(self.L.mg_apply_transpose(self._h, self._leaf(y.contiguous()), _ptr(out)))
         return out
 
-    def clean_adjoint(self, gBn, rel_tol=1e-12, max_cycles=80, n_down=2, n_up=2):
+    def clean_adjoint(self, gBn, rel_tol=1e-12, max_cycles=80, n_down=2, n_up=2, precision=MG_FP64):
         """dL/dB of the cleaning map B -> B - grad phi, Lap phi = div B
-        (mg_clean_adjoint), for gBn = dL/dB_new (dim, n_leaf)."""
+        (mg_clean_adjoint), for gBn = dL/dB_new (dim, n_leaf); precision as
+        for adjoint."""
         gBn = gBn.contiguous().view(-1)
         assert gBn.numel() == self.dim * self.n_leaf
         out = torch.empty_like(gBn)
-        p = _params(n_down, n_up)
+        p = _params(n_down, n_up, precision)
         cyc, rel = C.c_int(), C.c_double()
         check(self.L.mg_clean_adjoint(self._h, _ptr(gBn), _ptr(out), C.byref(p), float(rel_tol), int(max_cycles),
                                       C.byref(cyc), C.byref(rel)))

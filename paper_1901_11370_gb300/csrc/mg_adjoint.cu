@@ -470,7 +470,7 @@ void eps_grad_transpose(mg_tree *t, const double *lam, double *out) {
 // compatible (sum g = 0) and lambda returned as lambda - W sum(lambda) / sum W.
 template <int D>
 static int adjoint_dc_d(mg_tree *t, const double *g, double *lam, int nd, int nu, double rel_tol, int max_it,
-                        int *it_out, double *rel_out) {
+                        int *it_out, double *rel_out, bool fp32) {
     const KParams P = kparams(t, 1);
     double s[2];
     cudaMemcpyAsync(t->d_gh, g, sizeof(double) * (size_t)t->nleaf_cells, cudaMemcpyDeviceToDevice, t->stream);
@@ -492,9 +492,17 @@ static int adjoint_dc_d(mg_tree *t, const double *g, double *lam, int nd, int nu
         Adj<D>::vec(t, P, V_RESID, t->d_gh, t->d_lv, nullptr, nullptr, t->adj.F, 0.0, s);
         rel = r0 > 0 ? std::sqrt(s[0] / s[1]) / r0 : 0.0;
         if (it >= max_it || rel <= rel_tol || !std::isfinite(rel)) break;
-        cudaMemsetAsync(t->adj.X, 0, sizeof(double) * (size_t)t->ncells, t->stream);
-        cudaMemsetAsync(t->adj.XG, 0, sizeof(double) * (size_t)t->nghost, t->stream);
-        vcycle<double>(t, t->adj, top, nd, nu, 1);
+        if (fp32) {  // the FP32 V-cycle on the residual's FP32 copy (north star (1) for the adjoint)
+            narrow_f32(t, t->adj.F, t->f32.F, t->ncells);
+            cudaMemsetAsync(t->f32.X, 0, sizeof(float) * (size_t)t->ncells, t->stream);
+            cudaMemsetAsync(t->f32.XG, 0, sizeof(float) * (size_t)t->nghost, t->stream);
+            vcycle<float>(t, t->f32, top, nd, nu, 1);
+            widen_f64(t, t->f32.X, t->adj.X, t->ncells);
+        } else {
+            cudaMemsetAsync(t->adj.X, 0, sizeof(double) * (size_t)t->ncells, t->stream);
+            cudaMemsetAsync(t->adj.XG, 0, sizeof(double) * (size_t)t->nghost, t->stream);
+            vcycle<double>(t, t->adj, top, nd, nu, 1);
+        }
         Adj<D>::vec(t, P, V_ADD, nullptr, nullptr, lam, t->adj.X, nullptr, 0.0, nullptr);
         it++;
     }
@@ -508,9 +516,9 @@ static int adjoint_dc_d(mg_tree *t, const double *g, double *lam, int nd, int nu
 }
 
 int adjoint_dc(mg_tree *t, const double *g, double *lam, int nd, int nu, double rel_tol, int max_it, int *it_out,
-               double *rel_out) {
-    return t->dim == 2 ? adjoint_dc_d<2>(t, g, lam, nd, nu, rel_tol, max_it, it_out, rel_out)
-                       : adjoint_dc_d<3>(t, g, lam, nd, nu, rel_tol, max_it, it_out, rel_out);
+               double *rel_out, bool fp32) {
+    return t->dim == 2 ? adjoint_dc_d<2>(t, g, lam, nd, nu, rel_tol, max_it, it_out, rel_out, fp32)
+                       : adjoint_dc_d<3>(t, g, lam, nd, nu, rel_tol, max_it, it_out, rel_out, fp32);
 }
 
 // Vector-Jacobian product of the cleaning map B -> B - G phi, phi the
@@ -519,7 +527,7 @@ int adjoint_dc(mg_tree *t, const double *g, double *lam, int nd, int nu, double 
 // singular problem applied inside adjoint_dc.
 template <int D>
 static int clean_adjoint_d(mg_tree *t, const double *gBn, double *gB, int nd, int nu, double rel_tol, int max_it,
-                           int *it_out, double *rel_out) {
+                           int *it_out, double *rel_out, bool fp32) {
     const KParams P = kparams(t, 1);
     const long long nl = t->nleaf_cells;
     // u = G^T gBn into gB's first component (free until the end)
@@ -527,7 +535,7 @@ static int clean_adjoint_d(mg_tree *t, const double *gBn, double *gB, int nd, in
     Adj<D>::refresh_T(t, P, G_PHI);
     double *u = gB;
     cells_to_leaf(t, t->d_at, u);
-    int rc = adjoint_dc_d<D>(t, u, t->d_lam, nd, nu, rel_tol, max_it, it_out, rel_out);
+    int rc = adjoint_dc_d<D>(t, u, t->d_lam, nd, nu, rel_tol, max_it, it_out, rel_out, fp32);
     if (rc) return rc;
     for (int d = 0; d < D; d++) {
         Adj<D>::stencil(t, P, T_DIV, d, t->d_lam, nullptr, nullptr, nullptr, nullptr);
@@ -539,9 +547,9 @@ static int clean_adjoint_d(mg_tree *t, const double *gBn, double *gB, int nd, in
 }
 
 int clean_adjoint(mg_tree *t, const double *gBn, double *gB, int nd, int nu, double rel_tol, int max_it, int *it_out,
-                  double *rel_out) {
-    return t->dim == 2 ? clean_adjoint_d<2>(t, gBn, gB, nd, nu, rel_tol, max_it, it_out, rel_out)
-                       : clean_adjoint_d<3>(t, gBn, gB, nd, nu, rel_tol, max_it, it_out, rel_out);
+                  double *rel_out, bool fp32) {
+    return t->dim == 2 ? clean_adjoint_d<2>(t, gBn, gB, nd, nu, rel_tol, max_it, it_out, rel_out, fp32)
+                       : clean_adjoint_d<3>(t, gBn, gB, nd, nu, rel_tol, max_it, it_out, rel_out, fp32);
 }
 
 }  // namespace mg

@@ -308,6 +308,9 @@ void sub_scalar(mg_tree *t, double *x, double c, long long n);  // x[0..n) -= c
 // phi of old carried to the leaf blocks nid of the adapted mesh nt (see k_transfer)
 int transfer_phi(mg_tree *old, mg_tree *nt, const std::vector<int> &nid, const std::vector<int> &src);
 void copy_eps_to_f32(mg_tree *t);
+// whole-field copies FP64 -> FP32 (rounded to nearest) and FP32 -> FP64 (exact)
+void narrow_f32(mg_tree *t, const double *a, float *b, long long n);
+void widen_f64(mg_tree *t, const float *a, double *b, long long n);
 // FP64 face coefficients of every cell into t->d_wface (eps ghosts current)
 void face_coef(mg_tree *t);
 KParams kparams(mg_tree *t, int homog);
@@ -324,10 +327,12 @@ std::string take_launch_error();  // first failed kernel launch since the last c
 int adjoint_buffers(mg_tree *t);
 void apply_transpose(mg_tree *t, const double *y, double *out);
 void eps_grad_transpose(mg_tree *t, const double *lam, double *out);
+// fp32: FP32 V-cycles (the tree's FP32 set, allocated) as the approximate
+// inverse inside the FP64 defect correction, else FP64 V-cycles
 int adjoint_dc(mg_tree *t, const double *g, double *lam, int nd, int nu, double rel_tol, int max_it, int *it_out,
-               double *rel_out);
+               double *rel_out, bool fp32 = false);
 int clean_adjoint(mg_tree *t, const double *gBn, double *gB, int nd, int nu, double rel_tol, int max_it,
-                  int *it_out, double *rel_out);
+                  int *it_out, double *rel_out, bool fp32 = false);
 }  // namespace mg
 
 void mg_set_error(const std::string &msg);

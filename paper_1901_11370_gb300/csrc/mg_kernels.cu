@@ -3394,6 +3394,27 @@ __global__ void k_cast_f32(const double *__restrict__ a, float *__restrict__ b, 
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
         b[i] = (float)a[i];
 }
+// Whole-field copies between the FP64 and FP32 sets, rounded to nearest /
+// widened exactly with integer operations (GB300 runs the conversion
+// instructions on its FP64 pipe)
+__global__ void k_narrow(const double *__restrict__ a, float *__restrict__ b, long long n) {
+    pdl_entry();
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        b[i] = mg_to_float(a[i]);
+}
+__global__ void k_widen(const float *__restrict__ a, double *__restrict__ b, long long n) {
+    pdl_entry();
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        b[i] = mg_from_float(a[i]);
+}
+void narrow_f32(mg_tree *t, const double *a, float *b, long long n) {
+    ++t->launches;
+    launch_k(k_narrow, 8 * t->nsm, 256, 0, t->stream, a, b, n);
+}
+void widen_f64(mg_tree *t, const float *a, double *b, long long n) {
+    ++t->launches;
+    launch_k(k_widen, 8 * t->nsm, 256, 0, t->stream, a, b, n);
+}
 // ------------------------------------------------------------ driver ----
 
 // Face coefficients of the FP64 operator (Sec. 2.2), one thread per cell:

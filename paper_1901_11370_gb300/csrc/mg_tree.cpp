@@ -1373,6 +1373,7 @@ static int adjoint_setup(mg_tree *t, const mg_params *p, mg_params *q) {
                                         "mesh with refinement faces");
     int rc;
     if ((rc = use_params(t, p, q, nullptr))) return rc;
+    if (q->precision == MG_FP32_DC && (rc = ensure_f32(t))) return rc;
     if ((rc = alloc_fields(t, t->adj, false))) return rc;
     t->adj.E = t->f64.E;
     t->adj.W = t->f64.W;
@@ -1389,7 +1390,8 @@ static int adjoint_run(mg_tree *t, const double *g, double *dLdf, double *dLdeps
     int rc, it = 0;
     double rel = 0.0;
     if ((rc = adjoint_setup(t, p, &q))) return rc;
-    if ((rc = adjoint_dc(t, g, dLdf, q.n_down, q.n_up, rel_tol, max_cycles, &it, &rel))) return rc;
+    if ((rc = adjoint_dc(t, g, dLdf, q.n_down, q.n_up, rel_tol, max_cycles, &it, &rel, q.precision == MG_FP32_DC)))
+        return rc;
     if (dLdeps) eps_grad_transpose(t, dLdf, dLdeps);
     if ((rc = check_cuda("adjoint")) || (rc = check_status(t))) return rc;
     if (cycles_done) *cycles_done = it;
@@ -1430,7 +1432,9 @@ extern "C" int mg_clean_adjoint(mg_tree *t, const double *gBnew, double *gB, con
     int rc, it = 0;
     double rel = 0.0;
     if ((rc = adjoint_setup(t, p, &q))) return rc;
-    if ((rc = clean_adjoint(t, gBnew, gB, q.n_down, q.n_up, rel_tol, max_cycles, &it, &rel))) return rc;
+    if ((rc = clean_adjoint(t, gBnew, gB, q.n_down, q.n_up, rel_tol, max_cycles, &it, &rel,
+                            q.precision == MG_FP32_DC)))
+        return rc;
     if ((rc = check_status(t))) return rc;
     if (cycles_done) *cycles_done = it;
     if (rel_out) *rel_out = rel;

@@ -110,6 +110,25 @@ def test_adjoint_solve_reaches_tolerance(mg, name):
     assert np.sqrt(np.dot(vol, (r / vol) ** 2) / vol.sum()) <= 2e-12 * np.sqrt(np.dot(vol, (gh / vol) ** 2) / vol.sum())
 
 
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_mixed_precision_adjoint_solve_matches_oracle(mg, name):
+    """FP32 V-cycles as the approximate inverse inside the FP64 defect
+    correction of the adjoint: the same fixed point, checked like the FP64
+    form (against the oracle's lambda and by the oracle's transpose)."""
+    p = CASES[name]
+    t, o = both(mg, p)
+    t.fmg(); t.vcycle(2)
+    g = np.random.default_rng(3).standard_normal(o.n_leaf)
+    lam, geps = t.adjoint(cuda(g), rel_tol=1e-12, max_cycles=60, precision=mg.MG_FP32_DC)
+    it, rel = t.last_adjoint
+    assert rel <= 1e-12 and it <= 40
+    lam_o, _ = o.adjoint(g, 60, 1e-13)
+    assert rel_diff(lam.cpu().numpy(), lam_o) < 1e-9
+    lam64, geps64 = t.adjoint(cuda(g), rel_tol=1e-12, max_cycles=60)
+    assert rel_diff(lam.cpu().numpy(), lam64.cpu().numpy()) < 1e-9
+    assert rel_diff(geps.cpu().numpy(), geps64.cpu().numpy()) < 1e-8
+
+
 @pytest.mark.parametrize("name", ["periodic3d_amr_b4", "dirichlet2d_amr"])
 def test_clean_adjoint_matches_oracle(mg, name):
     if name == "dirichlet2d_amr":
@@ -190,4 +209,6 @@ def test_cleaning_workload_variant_matches_oracle(mg):
     g = vol * (Bn_o - Bt)
     a = t.clean_adjoint(cuda(g), 1e-12, 80).cpu().numpy()
     b = o.clean_adjoint(g, 80, 1e-13)
+    a32 = t.clean_adjoint(cuda(g), 1e-12, 80, precision=mg.MG_FP32_DC).cpu().numpy()
+    assert rel_diff(a32, b) < 1e-9
     assert rel_diff(a, b) < 1e-9
