@@ -1608,8 +1608,10 @@ __global__ void __launch_bounds__(kMaxThreads) k_prolong_tma(KParams P, int firs
 //  - it pushes the same-level and physical ghosts of its cells from
 //    registers: x faces take its row's end cell, y and z faces its 4 cells,
 //    which are contiguous in the ghost face;
-//  - refinement ghosts also need the inward cell of another row; they are
-//    formed after the barrier from shared memory, as before.
+//  - it stores its corrected cells to global memory itself, so a block
+//    without refinement faces takes no barrier beyond the stage wait;
+//  - refinement ghosts also need the inward cell of another row; on blocks
+//    that have them they are formed after a barrier from shared memory.
 template <class T>
 __global__ void __launch_bounds__(128) k_prolong_rows(KParams P, int first, int nblocks, Fields<T> F) {
     pdl_entry();
@@ -1707,6 +1709,7 @@ __global__ void __launch_bounds__(128) k_prolong_rows(KParams P, int first, int 
         // neighbours p0 - 1, p0 + 2 and the two cells of the neighbour rows on
         // the cells' y and z sides, parent ghosts where these leave the parent
         T v[4];
+        const int cfm = cf_faces(b, 3);
         {
             const int p0 = b.poff[0] + 2 * h, pj = b.poff[1] + (j >> 1), pk = b.poff[2] + (k >> 1);
             auto dx = [&](const T *x, const T *o, int idx) { return x[idx] - o[idx]; };
@@ -1733,12 +1736,17 @@ __global__ void __launch_bounds__(128) k_prolong_rows(KParams P, int first, int 
                 nbs += cz[q];
                 v[q] = v[q] + (c0[q] + nbs) / (T)4;
             }
+            // the corrected cells go straight to global memory (16-byte
+            // stores, a warp's rows contiguous); the stage keeps them only
+            // where refinement ghosts read other rows below
+            V *xg = reinterpret_cast<V *>(F.X + b.cell_off + 8 * r + 4 * h);
 #pragma unroll
             for (int q = 0; q < 4; q += VW) {
                 V w;
                 if constexpr (sizeof(T) == 4) w = make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]);
                 else w = make_double2(v[q], v[q + 1]);
-                *reinterpret_cast<V *>(xr + q) = w;
+                xg[q / VW] = w;
+                if (cfm) *reinterpret_cast<V *>(xr + q) = w;
             }
         }
         // same-level and physical ghosts of these cells, from registers
@@ -1773,14 +1781,8 @@ __global__ void __launch_bounds__(128) k_prolong_rows(KParams P, int first, int 
             if (j == 0 || j == n - 1) face4(j ? 3 : 2, 4 * h + 8 * k, k);  // y face: u = i + 8 k
             if (k == 0 || k == n - 1) face4(k ? 5 : 4, 4 * h + 8 * j, j);  // z face: u = i + 8 j
         }
-        fence_async_smem();
-        __syncthreads();
-        if (tid == ISSUER) {
-            bulk_s2g(F.X + b.cell_off, xs, sizeof(T) * C);
-            bulk_commit();
-        }
-        const int cfm = cf_faces(b, 3);
-        if (cfm)
+        if (cfm) {
+            __syncthreads();  // the updated rows in the stage
             for (int t = tid; t < GH; t += 128) {
                 const int face = t / FC, u = t - face * FC;
                 if (!((cfm >> face) & 1)) continue;
@@ -1790,7 +1792,9 @@ __global__ void __launch_bounds__(128) k_prolong_rows(KParams P, int first, int 
                 F.XG[b.ghost_off + t] = cf_ghost<T, 3>(P, L, b, face, ii, xs[cidx<3>(n, ii.x, ii.y, ii.z)],
                                                        xs[cidx<3>(n, dd.x, dd.y, dd.z)], F.X, F.XG, b.nbr[face], false);
             }
-        __syncthreads();  // stage reads done before the next block
+        }
+        // no barrier here: the next iteration's wait barrier already orders
+        // this block's stage reads before the refill of this stage
     }
     if (tid == ISSUER) bulk_wait0();
 }
