@@ -143,8 +143,12 @@ template <class T> __device__ __forceinline__ T kp_helm(const KParams &P) { retu
 template <> __device__ __forceinline__ float kp_helm<float>(const KParams &P) { return P.helmf; }
 
 // threads per CTA of the TMA sweep for NCOL colour cells per block
+// Threads of the staged sweep for a block of 2 ncol cells: one per colour
+// cell up to kMaxThreads; 3D 16^3 blocks (2048 colour cells), whose
+// double-buffered stage leaves room for one CTA per SM, take twice that.
 __host__ __device__ constexpr int sweep_tma_threads(int ncol, bool half) {
-    const int full = ncol < 32 ? 32 : (ncol > kMaxThreads ? kMaxThreads : ncol);
+    const int cap = ncol >= 2048 ? 2 * kMaxThreads : kMaxThreads;
+    const int full = ncol < 32 ? 32 : (ncol > cap ? cap : ncol);
     return half ? (full / 2 < 32 ? 32 : full / 2) : full;
 }
 

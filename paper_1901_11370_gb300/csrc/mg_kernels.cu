@@ -381,7 +381,7 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
 // HALF: half as many threads per CTA (two colour cells each), which wastes
 // less at the CTA barriers on levels with few blocks per SM.
 template <class T, int D, int NT, bool HALF = false>
-__global__ void __launch_bounds__(kMaxThreads, (D == 3 && NT == 16) ? 1 : 5) k_sweep_tma(KParams P, int first, int nblocks, Fields<T> F,
+__global__ void __launch_bounds__(sweep_tma_threads(cells_of<D>(NT) / 2, HALF), (D == 3 && NT == 16) ? 1 : 5) k_sweep_tma(KParams P, int first, int nblocks, Fields<T> F,
                                                            int colour) {
     pdl_entry();
     constexpr int n = NT, C = cells_of<D>(NT), FC = face_of<D>(NT), GH = 2 * D * FC;
@@ -4120,7 +4120,8 @@ template <class T, int D> struct Launch {
         switch (cand) {
         case 0: return (n == 8 || n == 16) ? 2 * stage_tma : 0;
         case 10:  // half-width TMA sweep: only where it differs from candidate 0
-            return ((n == 8 || n == 16) && cells_of<D>(n) / 2 >= 64 && cells_of<D>(n) / 2 <= 2 * kMaxThreads)
+            return ((n == 8 || n == 16) &&
+                    sweep_tma_threads(cells_of<D>(n) / 2, true) != sweep_tma_threads(cells_of<D>(n) / 2, false))
                        ? 2 * stage_tma : 0;
         case 1: return 1;
         case 2: return n == 8 ? 16 * stage : 0;
