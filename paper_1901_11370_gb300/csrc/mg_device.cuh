@@ -143,6 +143,13 @@ template <class T> __device__ __forceinline__ T kp_helm(const KParams &P) { retu
 template <> __device__ __forceinline__ float kp_helm<float>(const KParams &P) { return P.helmf; }
 
 // threads per CTA of the TMA sweep for NCOL colour cells per block
+// Largest CTA of the staged transfer kernels (restriction, prolongation,
+// FAS right-hand side, ghost fill): 3D 16^3 blocks run one 512-thread CTA
+// per SM, every other block size at most kMaxThreads.
+__host__ __device__ constexpr int transfer_bound(int D, int NT) {
+    return (D == 3 && NT == 16) ? 2 * kMaxThreads : kMaxThreads;
+}
+
 // Threads of the staged sweep for a block of 2 ncol cells: one per colour
 // cell up to kMaxThreads; 3D 16^3 blocks (2048 colour cells), whose
 // double-buffered stage leaves room for one CTA per SM, take twice that.

@@ -1253,7 +1253,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_prolong_push(KParams P, int fir
 // of the level are contiguous.  Every slot of a launch has exactly one
 // writer; refinement ghosts read only the coarser level.  mode as k_ghost.
 template <class T, int D, int NT>
-__global__ void __launch_bounds__(kMaxThreads) k_ghost_tma(KParams P, int first, int nblocks, T *__restrict__ X,
+__global__ void __launch_bounds__(transfer_bound(D, NT)) k_ghost_tma(KParams P, int first, int nblocks, T *__restrict__ X,
                                                            T *__restrict__ XG, int mode) {
     pdl_entry();
     constexpr int n = NT, C = cells_of<D>(NT), FC = face_of<D>(NT), GH = 2 * D * FC;
@@ -1340,7 +1340,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_ghost_tma(KParams P, int first,
 // staged block, its ghosts (and eps); f^H, v_old = x^H and its ghosts leave
 // by bulk stores.  Same arithmetic as the stencil helper.
 template <class T, int D, int NT>
-__global__ void __launch_bounds__(kMaxThreads) k_fas_tma(KParams P, int first, int nblocks, Fields<T> F) {
+__global__ void __launch_bounds__(transfer_bound(D, NT)) k_fas_tma(KParams P, int first, int nblocks, Fields<T> F) {
     pdl_entry();
     constexpr int n = NT, C = cells_of<D>(NT), FC = face_of<D>(NT), GH = 2 * D * FC;
     constexpr int DESC = (int)((sizeof(BlockDesc) + sizeof(LevelDesc)) / sizeof(T));
@@ -1487,7 +1487,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_fas_tma(KParams P, int first, i
 // k_prolong_push.  pn is the parent block size (NT or NT/2, uniform per
 // launch).  Bounded waits as in the sweeps.
 template <class T, int D, int NT>
-__global__ void __launch_bounds__(kMaxThreads) k_prolong_tma(KParams P, int first, int nblocks, Fields<T> F, int pn) {
+__global__ void __launch_bounds__(transfer_bound(D, NT)) k_prolong_tma(KParams P, int first, int nblocks, Fields<T> F, int pn) {
     pdl_entry();
     constexpr int n = NT, m = NT / 2, C = cells_of<D>(NT), FC = face_of<D>(NT), B = m + 2;
     constexpr int BOX = D == 2 ? B * B : B * B * B;
@@ -1952,7 +1952,7 @@ __global__ void __launch_bounds__(64) k_prolong_rows2(KParams P, int first, int 
 // the mean of its children and the parent-level ghosts are pushed (see
 // k_restrict_push).
 template <class T, int D, int NT>
-__global__ void __launch_bounds__(kMaxThreads, 4) k_restrict_tma(KParams P, int first, int nblocks, Fields<T> F) {
+__global__ void __launch_bounds__(transfer_bound(D, NT), (D == 3 && NT == 16) ? 1 : 4) k_restrict_tma(KParams P, int first, int nblocks, Fields<T> F) {
     pdl_entry();
     constexpr int n = NT, m = NT / 2, C = cells_of<D>(NT), FC = face_of<D>(NT), GH = 2 * D * FC;
     constexpr int M = cells_of<D>(m);
@@ -3898,15 +3898,15 @@ static int threads_for(int cells) {
 // 19.8 ms at 256, 18.8 at 128, 19.1 at 64); MG_TRANSFER_THREADS overrides.
 // Threads per CTA of the staged transfer kernels: 128, where several CTAs
 // share an SM (their phases are uneven, and 256-thread CTAs lost more at
-// the barriers); blocks of 16^3 cells and more, whose double-buffered
-// stages leave room for one CTA per SM, take kMaxThreads.
+// the barriers); blocks of 16^3 cells, whose double-buffered stages leave
+// room for one CTA per SM, take transfer_bound (512).
 static int transfer_threads(int want, int cells) {
     static int cap = [] {
         const char *e = std::getenv("MG_TRANSFER_THREADS");
         const int v = e ? std::atoi(e) : 128;
         return (v >= 32 && v <= kMaxThreads && v % 32 == 0) ? v : 128;
     }();
-    return std::min(want, cells >= 4096 ? kMaxThreads : cap);
+    return cells >= 4096 ? 2 * kMaxThreads : std::min(want, cap);
 }
 
 template <class T, int D> struct Launch {
