@@ -259,7 +259,7 @@ int mg_solve(mg_tree *t, double rel_tol, int max_cycles, int fmg_first,
  * unchanged; n_cycles >= 0.  p->precision = MG_FP32_DC makes M an FP32
  * V-cycle on the FP32 copy of W^-1 (g - A^T lambda) (the tree's FP32 fields,
  * allocated on first use), the transpose, residual and update staying FP64
- * (north star (1) applied to the adjoint solve): the same fixed point,
+ * (the split of the forward solve's defect correction): the same fixed point,
  * reached in about as many iterations at the cost of FP32 cycles.  The
  * FMG start is FP64 in both forms.
  */

@@ -492,7 +492,7 @@ static int adjoint_dc_d(mg_tree *t, const double *g, double *lam, int nd, int nu
         Adj<D>::vec(t, P, V_RESID, t->d_gh, t->d_lv, nullptr, nullptr, t->adj.F, 0.0, s);
         rel = r0 > 0 ? std::sqrt(s[0] / s[1]) / r0 : 0.0;
         if (it >= max_it || rel <= rel_tol || !std::isfinite(rel)) break;
-        if (fp32) {  // the FP32 V-cycle on the residual's FP32 copy (north star (1) for the adjoint)
+        if (fp32) {  // the FP32 V-cycle on the residual's FP32 copy, as in the forward solve's defect correction
             narrow_f32(t, t->adj.F, t->f32.F, t->ncells);
             cudaMemsetAsync(t->f32.X, 0, sizeof(float) * (size_t)t->ncells, t->stream);
             cudaMemsetAsync(t->f32.XG, 0, sizeof(float) * (size_t)t->nghost, t->stream);
